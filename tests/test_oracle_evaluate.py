@@ -1,0 +1,159 @@
+"""Pins for the oracle's Evaluate (Algorithm 4 with the pruning rule of
+eq. (2.5)): the cases in which ASKIT reduces to the direct sum of eq. (1.1),
+the closed-form count of directly evaluated leaves, the bounds of Section 3
+on visited nodes, an independent list-form evaluation, linearity in w, and
+the trend of the error with the skeleton size (Table 4)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_0260_gb300 import workloads as wl
+
+
+def _data(N=512, d=4, seed=0):
+    rng = np.random.default_rng(seed)
+    X = (rng.standard_normal((N, d)) + rng.integers(0, 4, (N, 1)) * 3.0).astype(np.float32)
+    W = rng.standard_normal((N, 1))
+    return X, W
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_full_rank_skeletons_reproduce_direct_sum():
+    X, W = _data()
+    T = oracle.Tree(X, oracle.Config(leaf_size=32, kappa=8, s_max=100000, id_tol=0.0, h=1.0))
+    T.set_weights(W)
+    U = T.evaluate()
+    assert rel(U, oracle.direct(X, W, 1.0, 0.5, targets=np.arange(len(X)))) < 1e-13
+
+
+def test_pruning_off_is_direct_sum():
+    X, W = _data(seed=1)
+    T = oracle.Tree(X, oracle.Config(leaf_size=32, kappa=8, s_max=4, id_tol=0.0, h=1.0, prune=0))
+    T.set_weights(W)
+    assert rel(T.evaluate(), oracle.direct(X, W, 1.0, 0.5, targets=np.arange(len(X)))) < 1e-13
+
+
+def test_all_neighbors_means_nothing_prunes():
+    X, W = _data(N=128, seed=2)
+    T = oracle.Tree(X, oracle.Config(leaf_size=16, kappa=127, s_max=4, id_tol=0.0, h=1.0))
+    T.set_weights(W)
+    U, near, far = T.evaluate(counts=True)
+    assert (far == 0).all() and (near == 8).all()
+    assert rel(U, oracle.direct(X, W, 1.0, 0.5, targets=np.arange(128))) < 1e-13
+
+
+def test_single_leaf_is_direct_sum():
+    X, W = _data(N=100, seed=3)
+    T = oracle.Tree(X, oracle.Config(leaf_size=128, kappa=5, s_max=4, h=1.0))
+    assert T.L == 0
+    T.set_weights(W)
+    assert rel(T.evaluate(), oracle.direct(X, W, 1.0, 0.5, targets=np.arange(100))) < 1e-13
+
+
+def _lists(T, i):
+    """Near leaves and far nodes of target i from the definition of U_i."""
+    ids, _ = T.knn()
+    perm = T.perm()
+    c = T.counts()
+    L = T.L
+    leafof = np.zeros(T.N, np.int64)
+    for a in range(1 << L, 2 << L):
+        leafof[perm[c["start"][a]: c["start"][a] + c["size"][a]]] = a
+    near = sorted({int(leafof[j]) for j in [i] + list(ids[i])})
+    U = set()
+    for lf in near:
+        a = lf
+        while a >= 1:
+            U.add(a)
+            a //= 2
+    far = sorted({b ^ 1 for b in U if b > 1 and (b ^ 1) not in U})
+    return near, far, leafof
+
+
+def test_visited_counts_closed_form_and_bounds():
+    X, W = _data(N=1024, seed=4)
+    cfg = oracle.Config(leaf_size=32, kappa=10, s_max=8, id_tol=1e-3, h=1.0)
+    T = oracle.Tree(X, cfg)
+    T.set_weights(W)
+    _, near, far = T.evaluate(counts=True)
+    for i in range(0, 1024, 37):
+        nl, fl, _ = _lists(T, i)
+        assert near[i] == len(nl) and far[i] == len(fl)
+    assert (near <= cfg.kappa + 1).all()
+    assert (far <= (cfg.kappa + 1) * T.L).all()
+
+
+def test_list_form_equals_recursive_form():
+    H2 = float(np.float32(1.2)) ** 2     # bandwidths are FP32 inputs
+    X, W = _data(N=1024, seed=5)
+    T = oracle.Tree(X, oracle.Config(leaf_size=32, kappa=10, s_max=8, id_tol=1e-3, h=1.2))
+    T.set_weights(W)
+    U = T.evaluate()
+    c = T.counts()
+    perm = T.perm()
+    X64 = X.astype(np.float64)
+    for i in range(0, 1024, 53):
+        nl, fl, _ = _lists(T, i)
+        u = 0.0
+        for a in nl:
+            js = perm[c["start"][a]: c["start"][a] + c["size"][a]]
+            u += np.exp(-0.5 * ((X64[js] - X64[i]) ** 2).sum(1) / H2) @ W[js, 0]
+        for a in fl:
+            nd = T.node(a)
+            u += np.exp(-0.5 * ((X64[nd["skel"]] - X64[i]) ** 2).sum(1) / H2) @ nd["wsk"][:, 0]
+        assert abs(u - U[i, 0]) <= 1e-12 * max(1.0, abs(u))
+
+
+def test_linear_in_weights_and_multiple_rhs():
+    X, W = _data(N=512, seed=6)
+    T = oracle.Tree(X, oracle.Config(leaf_size=32, kappa=8, s_max=6, id_tol=1e-4, h=1.0))
+    rng = np.random.default_rng(0)
+    W2 = rng.standard_normal((512, 3))
+    T.set_weights(W2)
+    U = T.evaluate()
+    for q in range(3):
+        T.set_weights(W2[:, q:q + 1])
+        assert np.allclose(T.evaluate()[:, 0], U[:, q], rtol=1e-12, atol=1e-12)
+
+
+def test_error_falls_with_skeleton_size():
+    w = wl.SMALL_MIXTURE.scaled(2048)
+    X, W = w.make_points(), w.make_weights().astype(np.float64)
+    tg = np.arange(0, 2048, 4)
+    ref = oracle.direct(X, W, 1.0, 0.5, targets=tg)
+    errs = []
+    for s in (2, 8, 32):
+        T = oracle.Tree(X, oracle.Config(leaf_size=64, kappa=8, s_max=s, id_tol=0.0, h=1.0))
+        T.set_weights(W)
+        errs.append(rel(T.evaluate(tg), ref))
+    assert errs[0] > errs[1] > errs[2]
+
+
+def test_out_of_sample_reductions():
+    X, W = _data(N=512, seed=7)
+    rng = np.random.default_rng(1)
+    Y = (X[rng.integers(0, 512, 40)] + 0.1 * rng.standard_normal((40, 4))).astype(np.float32)
+    ref = oracle.direct(X, W, 1.0, 0.5, Y=Y)
+    T = oracle.Tree(X, oracle.Config(leaf_size=32, kappa=8, s_max=100000, id_tol=0.0, h=1.0))
+    T.set_weights(W)
+    U, knn, near, far = T.evaluate_oos(Y, counts=True)
+    assert rel(U, ref) < 1e-13
+    D = ((Y[:, None, :].astype(np.float64) - X[None].astype(np.float64)) ** 2).sum(-1)
+    for q in range(40):
+        assert np.array_equal(knn[q], np.lexsort((np.arange(512), D[q]))[:8])
+    T0 = oracle.Tree(X, oracle.Config(leaf_size=32, kappa=8, s_max=4, id_tol=0.0, h=1.0, prune=0))
+    T0.set_weights(W)
+    assert rel(T0.evaluate_oos(Y), ref) < 1e-13
+
+
+def test_variable_bandwidth_kth_neighbor():
+    X, W = _data(N=256, seed=8)
+    T = oracle.Tree(X, oracle.Config(leaf_size=32, kappa=8, s_max=100000, id_tol=0.0, bw_mode=2, bw_k=4))
+    ids, dd = oracle.knn_exact(X, 8)
+    h = np.sqrt(dd[:, 3]).astype(np.float32)
+    assert np.array_equal(T.hsrc(), h)
+    T.set_weights(W)
+    assert rel(T.evaluate(), oracle.direct(X, W, h, 0.5, targets=np.arange(256))) < 1e-13
