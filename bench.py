@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""ASKIT evaluation throughput on one GB300 (or N replicas under torchrun).
+
+Workload: the 64-D manifold case -- N = 1,048,576 points x = A z + 0.01 e,
+z ~ N(0, I_6), A a seeded 64 x 6 Gaussian matrix with orthonormal columns,
+w ~ N(0, 1), Gaussian h = 0.35 (exp(-r^2 / 2h^2)), leaf size m = 512,
+kappa = 32 neighbors by random-projection trees, s <= 256, ID tolerance 1e-4.
+
+One step = one pass of the evaluation hot path over a new weight vector:
+weights into tree order and the upward pass of skeleton weights
+(askit_set_weights), then Evaluate at all N points (askit_evaluate).  The tree,
+kNN, skeletons and work lists are built once (setup, reported separately).
+Metric: evaluated targets per second (whole job = all ranks).
+
+--impl reference times the CPU oracle (plain FP64 C) on the host cores on a
+bounded sample of the same workload and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ASKIT eval targets/s at rel.err <=1e-4 vs plain FP32 on 1 GB300"
+UNIT = "targets/s"
+SM_COUNT = 152
+MUFU_PER_SM_CLK = 16          # ex2 per SM per clock (4 SM sub-partitions x 4)
+FP32_LANES_PER_SM = 128
+TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense tensor-rate ratio
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="tf32x3", choices=["simt_fp32", "tf32x3", "bf16x3"])
+    ap.add_argument("--n", type=int, default=0, help="override N (smaller runs; not a bench line)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-n", type=int, default=65536)
+    ap.add_argument("--cpu-targets", type=int, default=4096)
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_1410_0260_gb300 import workloads as wl
+    w = wl.MANIFOLD_1M_64
+    return w.scaled(args.n) if args.n else w
+
+
+def askit_config(w, precision):
+    from paper_1410_0260_gb300 import askit
+    return askit.Config(leaf_size=w.leaf_size, kappa=w.kappa, knn_mode=w.knn_mode, rp_iters=w.rp_iters,
+                        s_max=w.s_max, s_min=w.s_min, id_tol=w.id_tol, h=w.h, bw_mode=w.bw_mode,
+                        bw_k=w.bw_k, seed=w.seed, precision=precision)
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+class OracleSample:
+    """The oracle as it stands, on the host cores: ASKIT setup on a bounded
+    instance of the same recipe (N = cpu_n points), then Evaluate (Algorithm 4)
+    timed on a fixed sample of its targets."""
+
+    def __init__(self, args, w):
+        import oracle
+        self.oracle = oracle
+        ws = w.scaled(args.cpu_n)
+        X, W = ws.make_points(), ws.make_weights()
+        cfg = oracle.Config(leaf_size=ws.leaf_size, kappa=ws.kappa, knn_mode=ws.knn_mode,
+                            rp_iters=ws.rp_iters, s_max=ws.s_max, s_min=ws.s_min, id_tol=ws.id_tol, h=ws.h,
+                            bw_mode=ws.bw_mode, bw_k=ws.bw_k, seed=ws.seed)
+        t0 = time.perf_counter()
+        self.tree = oracle.Tree(X, cfg)
+        self.tree.set_weights(W.astype(np.float64))
+        self.setup_s = time.perf_counter() - t0
+        n = min(args.cpu_targets, args.cpu_n)
+        self.tg = np.random.default_rng(7).choice(args.cpu_n, size=n, replace=False)
+        self.sample = (f"oracle Evaluate (Algorithm 4, FP64 C, OpenMP over targets) on {n} targets of a "
+                       f"N={args.cpu_n} instance of the same manifold recipe (d={ws.d}, m={ws.leaf_size}, "
+                       f"kappa={ws.kappa}, s<={ws.s_max}); oracle setup {self.setup_s:.1f}s not timed")
+
+    def step(self) -> float:
+        t0 = time.perf_counter()
+        self.tree.evaluate(self.tg)
+        return time.perf_counter() - t0
+
+    def summary(self, seconds) -> dict:
+        dt = statistics.median(seconds)
+        return {"value": len(self.tg) / dt, "unit": UNIT, "cores": self.oracle.num_threads(), "kind": "oracle",
+                "sample": self.sample, "seconds": dt}
+
+
+def cpu_baseline(args, w, steps=3):
+    o = OracleSample(args, w)
+    return o.summary([o.step() for _ in range(steps)])
+
+
+def run_reference(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    w = workload(args)
+    o = OracleSample(args, w)
+    for _ in range(args.warmup):
+        o.step()
+    base = o.summary([o.step() for _ in range(args.steps)])
+    value = base["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": base["seconds"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "N": w.N, "d": w.d, "m": w.leaf_size,
+                                            "kappa": w.kappa, "s_max": w.s_max, "h": w.h},
+            "cpu_baseline": {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    from paper_1410_0260_gb300 import askit
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = workload(args)
+    X = w.make_points()
+    W = w.make_weights()
+    N = w.N
+    Xd = torch.from_numpy(X).to(dev)
+    Wd = torch.from_numpy(W).to(dev)
+    U = torch.empty((N, 1), dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tree = askit.Tree(Xd, askit_config(w, args.precision))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    info = tree.info()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        tree.set_weights(Wd)
+        tree.evaluate(U)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    tree.sync()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    # the dominant kernel alone (Evaluate), timed on the launching stream
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        tree.evaluate(U)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms_eval = e2.elapsed_time(e3) / args.steps
+    clk = clocks.stop()
+    tree.sync()
+    if world > 1:
+        t = torch.tensor([ms, ms_eval], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_eval = float(t[0]), float(t[1])
+    ms_step = ms / args.steps
+    value = world * N / (ms_step / 1e3)
+
+    # end to end through the public host-buffer call: H2D of w, set_weights,
+    # Evaluate, D2H of u, every step
+    e2e = None
+    if not args.no_e2e:
+        Wh = torch.from_numpy(W).pin_memory()
+        Uh = torch.empty((N, 1), dtype=torch.float32).pin_memory()
+        for _ in range(2):
+            tree.evaluate_host_ptr(Wh.data_ptr(), 1, Uh.data_ptr())
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            tree.evaluate_host_ptr(Wh.data_ptr(), 1, Uh.data_ptr())
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t[0])
+        e2e = {"value": world * N * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(W.nbytes),
+               "d2h_bytes_per_step": int(N * 4)}
+
+    # roofline of the Evaluate kernel
+    peaks = measured_peaks()
+    P = info["pairs_algorithmic"]
+    d = w.d
+    sec = ms_eval / 1e3
+    smax = (clk or {}).get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0
+    mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * smax * 1e6
+    if args.precision == "simt_fp32":
+        # two FP32 lane operations per pair and coordinate (subtract, fused multiply-add)
+        alu_peak = SM_COUNT * FP32_LANES_PER_SM * smax * 1e6
+        roof = {"bound": "alu", "achieved": P * 2 * d / sec / 1e12, "peak": alu_peak / 1e12,
+                "unit": "Tops/s", "peak_source": "152 SMs x 128 FP32 lanes x max SM clock"}
+    else:
+        bf16 = (peaks or {}).get("bf16_tflops", 1900.0)
+        tpeak = bf16 * (TF32_OVER_BF16 if args.precision == "tf32x3" else 1.0)
+        t_tensor = P * 3 * 2 * d / (tpeak * 1e12)
+        t_mufu = P / mufu_peak
+        if t_tensor >= t_mufu:
+            roof = {"bound": "tensor", "achieved": P * 3 * 2 * d / sec / 1e12, "peak": tpeak, "unit": "TFLOP/s",
+                    "peak_source": ("measured bf16 burst x 1.1/2.25 (TF32)" if args.precision == "tf32x3"
+                                    else "measured bf16 burst") + (" of measured" if peaks else " of fallback")}
+        else:
+            roof = {"bound": "alu", "achieved": P / sec / 1e12, "peak": mufu_peak / 1e12, "unit": "Tex2/s",
+                    "peak_source": "MUFU ex2: 152 SMs x 16/clk x max SM clock"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = "eval_simt_kernel" if args.precision == "simt_fp32" else "eval_tc_kernel"
+    roof["ms_per_launch"] = ms_eval
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args, w)
+        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    launches_per_step = 1 + info["L"] + 2
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"simt_fp32": "f32", "tf32x3": "tf32x3", "bf16x3": "bf16x3"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": w.name, "N": N, "d": d, "m": w.leaf_size, "kappa": w.kappa,
+                       "knn": "rp-trees x%d" % w.rp_iters, "s_max": w.s_max, "id_tol": w.id_tol, "h": w.h,
+                       "r": 1, "precision": args.precision, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (coordinates %.0f MB)" % (N * info["d_pad"] * 4 / 1e6)},
+            "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk, "roofline": roof,
+            "cpu_baseline": cpu,
+            "work": {"pairs_algorithmic": P, "pairs_computed": info["pairs_computed"],
+                     "near_per_target": info["near_total"] / N, "far_per_target": info["far_total"] / N,
+                     "items": info["n_items"], "blocks": info["n_blocks"], "entries": info["n_entries"], "L": info["L"],
+                     "skeleton_rows": info["skel_total"], "setup_s": setup_s,
+                     "device_gb": info["device_bytes"] / 1e9}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    tree.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * askit.h -- C ABI of the GB300 ASKIT evaluation library (libaskit.so).
+ *
+ * ASKIT (March, Xiao & Biros, "ASKIT: Approximate Skeletonization
+ * Kernel-Independent Treecode in High Dimensions") approximates the kernel
+ * sums of eq. (1.1),
+ *
+ *     u_i = sum_j K(x_i, x_j) w_j,   K(x, y) = exp(-c ||x - y||^2 / h_y^2),
+ *
+ * (the Gaussian of Section 4; c = 1 in the paper, c = 1/2 gives the usual
+ * exp(-r^2 / 2h^2)) by a binary tree, the kNN graph (pruning rule eq. (2.5))
+ * and sampled interpolative decompositions of every node (Section 2.1,
+ * Algorithm 3).  Algorithm 5 splits the method into a setup (tree, kNN,
+ * node neighbor lists, skeletonization) and Evaluate (Algorithm 4), which is
+ * the per-weight-vector cost; this library runs both on one GPU.
+ *
+ * Conventions
+ *  - Every pointer argument named *_dev is a device pointer owned by the
+ *    caller; the library reads or writes it on `stream` and never frees it.
+ *    *_host pointers are host memory owned by the caller.
+ *  - Matrices are row-major with a leading dimension (ld*) in elements.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *  - Calls are stream-ordered.  askit_setup, askit_get_* and askit_sync
+ *    block the host; askit_set_weights, askit_evaluate and
+ *    askit_evaluate_targets only enqueue work.
+ *  - Errors are returned as askit_status, never by aborting; the message of
+ *    the last failure on the calling thread is askit_last_error().  A kernel
+ *    that gives up a bounded wait sets a sticky status that askit_sync
+ *    reports as ASKIT_ERR_TIMEOUT.
+ *  - A tree is not thread-safe: calls on one tree must not race.
+ */
+#ifndef ASKIT_H
+#define ASKIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct askit_tree_s *askit_tree;
+
+typedef enum {
+    ASKIT_OK = 0,
+    ASKIT_ERR_INVALID_ARG = 1,
+    ASKIT_ERR_OOM = 2,
+    ASKIT_ERR_CUDA = 3,
+    ASKIT_ERR_TIMEOUT = 4,
+    ASKIT_ERR_NOT_READY = 5,
+    ASKIT_ERR_UNSUPPORTED = 6
+} askit_status;
+
+/* Distance-contraction precision of Evaluate. */
+enum {
+    ASKIT_PREC_SIMT_FP32 = 0, /* plain FP32 difference form on CUDA cores */
+    ASKIT_PREC_TF32X3 = 1,    /* tcgen05 tensor cores, 3xTF32 split, FP32 accumulate */
+    ASKIT_PREC_BF16X3 = 2     /* tcgen05 tensor cores, BF16x3 split, FP32 accumulate */
+};
+
+/* Bandwidth of the Gaussian (Section 4: constant h, or h_j per source). */
+enum {
+    ASKIT_BW_CONSTANT = 0, /* h_j = h */
+    ASKIT_BW_ARRAY = 1,    /* h_j from the caller's array */
+    ASKIT_BW_KNN = 2       /* h_j = distance from x_j to its bw_k-th nearest neighbor */
+};
+
+typedef struct {
+    int32_t leaf_size;   /* m: points per leaf (Section 3); >= 2 */
+    int32_t kappa;       /* kappa: nearest neighbors per point, self excluded; 1..32 */
+    int32_t knn_mode;    /* 0 exact kNN, 1 random-projection trees (Section 2.2) */
+    int32_t rp_iters;    /* number of random-projection trees (knn_mode 1) */
+    int32_t rp_leaf;     /* points per RP leaf; 0 = max(2 kappa + 2, m) */
+    int32_t s_max;       /* largest skeleton (Section 3, s) */
+    int32_t s_min;       /* smallest skeleton (adaptive rank floor) */
+    int32_t ell_extra;   /* sampled rows ell = s_max + ell_extra (paper: 20) */
+    int32_t prune;       /* 1: neighbor pruning eq. (2.5); 0: every leaf direct */
+    int32_t bw_mode;     /* ASKIT_BW_* */
+    int32_t bw_k;        /* neighbor rank for ASKIT_BW_KNN (1..kappa) */
+    int32_t precision;   /* ASKIT_PREC_* used by askit_evaluate */
+    double id_tol;       /* rank cut: first k with |R_kk| <= id_tol |R_00| */
+    double kernel_scale; /* c in exp(-c r^2 / h^2) */
+    double h;            /* constant bandwidth (ASKIT_BW_CONSTANT) */
+    uint64_t seed;       /* Philox key for RP directions and row sampling */
+} askit_params;
+
+/* Fill `p` with defaults (m = 128, kappa = 16, exact kNN, s_max = 64,
+ * ell_extra = 20, prune = 1, constant h = 1, c = 1/2, id_tol = 1e-6,
+ * TF32x3 evaluation, seed = 1). */
+void askit_default_params(askit_params *p);
+
+/*
+ * Setup: Algorithm 5 up to Evaluate -- kNN (Section 2.2, exact or RP
+ * trees), the median-split binary tree (Section 2.2), node neighbor lists
+ * (Algorithm 2), sampled targets (eq. (2.4)), skeletons and interpolation
+ * matrices by FP64 pivoted QR (Section 2.1, Algorithm 3), and the
+ * evaluation work lists of every target tile (pruning rule eq. (2.5)).
+ *
+ *   X_dev   [N, d] FP32 points (row stride ldx >= d), read during the call only.
+ *   h_dev   [N] FP32 per-point bandwidth for ASKIT_BW_ARRAY, else NULL.
+ *   knn_dev optional [N, kappa] int32 caller-given neighbor ids (the paper's
+ *           N(X) argument of Algorithm 5, self excluded), or NULL to compute.
+ *   out     receives the tree handle (library-owned; askit_destroy frees it).
+ * Errors: INVALID_ARG for N < 1, d < 1, m < 2, kappa outside 1..min(32, N-1),
+ * s_max < 1, non-positive h or id_tol < 0; OOM when device memory runs out;
+ * UNSUPPORTED for N >= 2^31.  Blocks until the setup is complete.
+ */
+askit_status askit_setup(const float *X_dev, int64_t N, int32_t d, int64_t ldx,
+                         const float *h_dev, const int32_t *knn_dev,
+                         const askit_params *p, void *stream, askit_tree *out);
+
+/*
+ * New weight vectors: stores W in tree order and runs the upward pass of
+ * skeleton weights w~_a = w(S_a) + P_a w(R) (Section 2.1, Algorithm 3),
+ * level by level from the leaves up.
+ *   W_dev [N, r] FP32 (row stride ldw >= r), in the caller's point order;
+ *   read on `stream` before the call's work completes.  1 <= r <= 64.
+ */
+askit_status askit_set_weights(askit_tree t, const float *W_dev, int32_t r, int64_t ldw,
+                               void *stream);
+
+/*
+ * Evaluate (Algorithm 4) at every point: U_dev [N, r] FP32 (row stride
+ * ldu >= r) receives u_i in the caller's point order.  Near-field leaves
+ * are summed directly, pruned nodes through their skeletons; the work runs
+ * as one persistent launch over all (target tile, source block) items.
+ * Requires askit_set_weights first (NOT_READY otherwise).
+ */
+askit_status askit_evaluate(askit_tree t, float *U_dev, int64_t ldu, void *stream);
+
+/*
+ * Evaluate at out-of-sample targets Y (the paper takes targets = sources;
+ * here the prune set of y is its exact kappa nearest sources, eq. (2.5)
+ * with {i} replaced by nothing).  Y_dev [T, d] FP32 (stride ldy),
+ * U_dev [T, r] FP32 (stride ldu).  Allocates per-call work lists and
+ * blocks the host until they are built.
+ */
+askit_status askit_evaluate_targets(askit_tree t, const float *Y_dev, int64_t T, int64_t ldy,
+                                    float *U_dev, int64_t ldu, void *stream);
+
+/*
+ * End-to-end call on host memory: copies W_host [N, r] (stride ldw) to the
+ * device, runs askit_set_weights and askit_evaluate, copies u back into
+ * U_host [N, r] (stride ldu) and waits for completion.
+ */
+askit_status askit_evaluate_host(askit_tree t, const float *W_host, int32_t r, int64_t ldw,
+                                 float *U_host, int64_t ldu, void *stream);
+
+/* Precision of subsequent askit_evaluate calls (ASKIT_PREC_*). */
+askit_status askit_set_precision(askit_tree t, int32_t precision);
+
+/* Sizes and work counts (host call). */
+typedef struct {
+    int64_t N;
+    int32_t d, d_pad, L, kappa, r;
+    int64_t n_nodes;          /* heap slots, 2^(L+1) */
+    int64_t skel_total;       /* sum of skeleton sizes over non-root nodes */
+    int64_t skel_rows_padded; /* rows of the skeleton coordinate pool */
+    int64_t n_blocks;         /* source sub-blocks (<= 128 rows of a leaf or a skeleton) */
+    int64_t n_items;          /* work items: a sub-block against <= 128 targets needing it */
+    int64_t n_entries;        /* (target, sub-block) pairs */
+    int64_t pairs_algorithmic;/* sum over targets of near + far source points */
+    int64_t pairs_computed;   /* 128 x 128 target-source slots the items cover */
+    int64_t near_total, far_total; /* sum over targets of |Near(i)| and |Far(i)| */
+    int64_t device_bytes;     /* library-owned device memory */
+} askit_info;
+askit_status askit_get_info(askit_tree t, askit_info *info);
+
+/* Structures for inspection and bit-exact checks (host call, blocks).
+ * `which` and the host buffer's layout:
+ *   ASKIT_STRUCT_PERM      int32 [N]          leaf order -> point id
+ *   ASKIT_STRUCT_KNN       int32 [N, kappa]   neighbor ids, sorted by (D, id)
+ *   ASKIT_STRUCT_KNN_DIST  double [N, kappa]  FP64 squared distances
+ *   ASKIT_STRUCT_SKEL_S    int32 [n_nodes]    skeleton size per heap node
+ *   ASKIT_STRUCT_SKEL_IDS  int32 [skel_total] skeleton point ids, nodes in heap order
+ *   ASKIT_STRUCT_NL_CNT    int32 [n_nodes]    node neighbor-list length
+ *   ASKIT_STRUCT_NL_IDS    int32 [n_nodes, ell_max] node neighbor lists (padded with -1)
+ *   ASKIT_STRUCT_TROWS     int32 [n_nodes, ell_max] sampled target rows (padded with -1)
+ *   ASKIT_STRUCT_HSRC      float [N]          bandwidth of each point
+ *   ASKIT_STRUCT_P         double [sum s (c - s)] interpolation matrices, heap order
+ *   ASKIT_STRUCT_NCOL      int32 [n_nodes]    columns c of each node's ID
+ *   ASKIT_STRUCT_WSKEL     float [skel_total, r] skeleton weights, heap order
+ * `bytes` must equal the buffer's size; INVALID_ARG otherwise. */
+enum {
+    ASKIT_STRUCT_PERM = 0, ASKIT_STRUCT_KNN = 1, ASKIT_STRUCT_KNN_DIST = 2,
+    ASKIT_STRUCT_SKEL_S = 3, ASKIT_STRUCT_SKEL_IDS = 4, ASKIT_STRUCT_NL_CNT = 5,
+    ASKIT_STRUCT_NL_IDS = 6, ASKIT_STRUCT_TROWS = 7, ASKIT_STRUCT_HSRC = 8,
+    ASKIT_STRUCT_P = 9, ASKIT_STRUCT_NCOL = 10, ASKIT_STRUCT_WSKEL = 11
+};
+askit_status askit_get_structure(askit_tree t, int32_t which, void *host, size_t bytes);
+
+/* Waits for the tree's work on `stream` and reports sticky kernel errors. */
+askit_status askit_sync(askit_tree t, void *stream);
+
+/* Frees the tree and everything it owns (waits for its work first). */
+askit_status askit_destroy(askit_tree t);
+
+const char *askit_status_string(askit_status s);
+const char *askit_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ASKIT_H */

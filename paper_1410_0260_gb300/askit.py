@@ -1,0 +1,238 @@
+"""Python binding of libaskit.so (the C ABI in include/askit.h).
+
+Argument marshalling only: PyTorch supplies device memory and the stream;
+every step of setup and evaluation runs in the library's CUDA kernels.  There
+is no CPU path: if the shared library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libaskit.so")
+_lock = threading.Lock()
+_lib = None
+
+PREC_SIMT_FP32, PREC_TF32X3, PREC_BF16X3 = 0, 1, 2
+PRECISIONS = {"simt_fp32": PREC_SIMT_FP32, "tf32x3": PREC_TF32X3, "bf16x3": PREC_BF16X3}
+BW_CONSTANT, BW_ARRAY, BW_KNN = 0, 1, 2
+(STRUCT_PERM, STRUCT_KNN, STRUCT_KNN_DIST, STRUCT_SKEL_S, STRUCT_SKEL_IDS, STRUCT_NL_CNT,
+ STRUCT_NL_IDS, STRUCT_TROWS, STRUCT_HSRC, STRUCT_P, STRUCT_NCOL, STRUCT_WSKEL) = range(12)
+
+EXPORTS = ["askit_default_params", "askit_setup", "askit_set_weights", "askit_evaluate",
+           "askit_evaluate_targets", "askit_evaluate_host", "askit_set_precision", "askit_get_info",
+           "askit_get_structure", "askit_sync", "askit_destroy", "askit_status_string",
+           "askit_last_error"]
+
+
+class AskitError(RuntimeError):
+    pass
+
+
+class Params(C.Structure):
+    _fields_ = [("leaf_size", C.c_int32), ("kappa", C.c_int32), ("knn_mode", C.c_int32),
+                ("rp_iters", C.c_int32), ("rp_leaf", C.c_int32), ("s_max", C.c_int32),
+                ("s_min", C.c_int32), ("ell_extra", C.c_int32), ("prune", C.c_int32),
+                ("bw_mode", C.c_int32), ("bw_k", C.c_int32), ("precision", C.c_int32),
+                ("id_tol", C.c_double), ("kernel_scale", C.c_double), ("h", C.c_double),
+                ("seed", C.c_uint64)]
+
+
+class Info(C.Structure):
+    _fields_ = [("N", C.c_int64), ("d", C.c_int32), ("d_pad", C.c_int32), ("L", C.c_int32),
+                ("kappa", C.c_int32), ("r", C.c_int32), ("n_nodes", C.c_int64),
+                ("skel_total", C.c_int64), ("skel_rows_padded", C.c_int64), ("n_blocks", C.c_int64),
+                ("n_items", C.c_int64), ("n_entries", C.c_int64), ("pairs_algorithmic", C.c_int64), ("pairs_computed", C.c_int64),
+                ("near_total", C.c_int64), ("far_total", C.c_int64), ("device_bytes", C.c_int64)]
+
+
+def load(path: str | None = None):
+    """Load libaskit.so (built by build.py / __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise AskitError(f"libaskit.so not built ({p}); run __graft_entry__.build()")
+            L = C.CDLL(p)
+            V, I64, I32, D = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+            L.askit_default_params.argtypes = [C.POINTER(Params)]
+            L.askit_setup.argtypes = [V, I64, I32, I64, V, V, C.POINTER(Params), V, C.POINTER(V)]
+            L.askit_set_weights.argtypes = [V, V, I32, I64, V]
+            L.askit_evaluate.argtypes = [V, V, I64, V]
+            L.askit_evaluate_targets.argtypes = [V, V, I64, I64, V, I64, V]
+            L.askit_evaluate_host.argtypes = [V, V, I32, I64, V, I64, V]
+            L.askit_set_precision.argtypes = [V, I32]
+            L.askit_get_info.argtypes = [V, C.POINTER(Info)]
+            L.askit_get_structure.argtypes = [V, I32, V, C.c_size_t]
+            L.askit_sync.argtypes = [V, V]
+            L.askit_destroy.argtypes = [V]
+            L.askit_status_string.restype = C.c_char_p
+            L.askit_status_string.argtypes = [C.c_int]
+            L.askit_last_error.restype = C.c_char_p
+            for name in EXPORTS:
+                if name not in ("askit_status_string", "askit_last_error", "askit_default_params"):
+                    getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        L = load()
+        raise AskitError(f"{L.askit_status_string(rc).decode()}: {L.askit_last_error().decode()}")
+
+
+def _stream(stream=None) -> C.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev_f32(a: torch.Tensor, name: str) -> torch.Tensor:
+    if not (isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == torch.float32):
+        raise AskitError(f"{name} must be a CUDA float32 tensor")
+    if a.dim() == 1:
+        a = a.view(-1, 1)
+    if a.stride(1) != 1:
+        a = a.contiguous()
+    return a
+
+
+@dataclass
+class Config:
+    """ASKIT parameters (Section 3: m, kappa, s, ell; Section 4: h)."""
+    leaf_size: int = 128
+    kappa: int = 16
+    knn_mode: int = 0
+    rp_iters: int = 4
+    rp_leaf: int = 0
+    s_max: int = 64
+    s_min: int = 1
+    ell_extra: int = 20
+    prune: int = 1
+    bw_mode: int = BW_CONSTANT
+    bw_k: int = 16
+    precision: str = "tf32x3"
+    id_tol: float = 1e-6
+    kernel_scale: float = 0.5
+    h: float = 1.0
+    seed: int = 1
+
+    def to_c(self) -> Params:
+        return Params(self.leaf_size, self.kappa, self.knn_mode, self.rp_iters, self.rp_leaf, self.s_max,
+                      self.s_min, self.ell_extra, self.prune, self.bw_mode, self.bw_k,
+                      PRECISIONS[self.precision], self.id_tol, self.kernel_scale, self.h, self.seed)
+
+
+class Tree:
+    """A skeletonized ASKIT tree resident on the GPU."""
+
+    def __init__(self, X: torch.Tensor, cfg: Config, h: torch.Tensor | None = None,
+                 knn: torch.Tensor | None = None, stream=None):
+        L = load()
+        X = _dev_f32(X, "X")
+        self.N, self.d = X.shape
+        self.cfg = cfg
+        self.device = X.device
+        p = cfg.to_c()
+        hp = None
+        if h is not None:
+            h = _dev_f32(h, "h").contiguous()
+            hp = C.c_void_p(h.data_ptr())
+        kp = None
+        if knn is not None:
+            knn = knn.to(device=X.device, dtype=torch.int32).contiguous()
+            kp = C.c_void_p(knn.data_ptr())
+        out = C.c_void_p()
+        with torch.cuda.device(X.device):
+            _check(L.askit_setup(C.c_void_p(X.data_ptr()), self.N, self.d, X.stride(0), hp, kp,
+                                 C.byref(p), _stream(stream), C.byref(out)))
+        self._t = out
+        self.r = 0
+
+    def close(self):
+        if getattr(self, "_t", None):
+            load().askit_destroy(self._t)
+            self._t = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ calls
+    def set_precision(self, precision: str):
+        _check(load().askit_set_precision(self._t, PRECISIONS[precision]))
+
+    def set_weights(self, W: torch.Tensor, stream=None):
+        W = _dev_f32(W, "W")
+        _check(load().askit_set_weights(self._t, C.c_void_p(W.data_ptr()), W.shape[1], W.stride(0),
+                                        _stream(stream)))
+        self._W = W   # keep alive until the stream has consumed it
+        self.r = W.shape[1]
+
+    def evaluate(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.N, max(self.r, 1)), dtype=torch.float32, device=self.device)
+        out = _dev_f32(out, "out")
+        _check(load().askit_evaluate(self._t, C.c_void_p(out.data_ptr()), out.stride(0), _stream(stream)))
+        return out
+
+    def evaluate_targets(self, Y: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        Y = _dev_f32(Y, "Y")
+        if out is None:
+            out = torch.empty((Y.shape[0], max(self.r, 1)), dtype=torch.float32, device=self.device)
+        _check(load().askit_evaluate_targets(self._t, C.c_void_p(Y.data_ptr()), Y.shape[0], Y.stride(0),
+                                             C.c_void_p(out.data_ptr()), out.stride(0), _stream(stream)))
+        return out
+
+    def evaluate_host(self, W: np.ndarray, out: np.ndarray | None = None, stream=None) -> np.ndarray:
+        W = np.ascontiguousarray(W, dtype=np.float32).reshape(self.N, -1)
+        r = W.shape[1]
+        if out is None:
+            out = np.empty((self.N, r), np.float32)
+        _check(load().askit_evaluate_host(self._t, W.ctypes.data_as(C.c_void_p), r, r,
+                                          out.ctypes.data_as(C.c_void_p), out.shape[1], _stream(stream)))
+        self.r = r
+        return out
+
+    def evaluate_host_ptr(self, W_ptr: int, r: int, U_ptr: int, stream=None):
+        """End-to-end call on caller-owned (e.g. pinned) host buffers."""
+        _check(load().askit_evaluate_host(self._t, C.c_void_p(W_ptr), r, r, C.c_void_p(U_ptr), r,
+                                          _stream(stream)))
+        self.r = r
+
+    def sync(self, stream=None):
+        _check(load().askit_sync(self._t, _stream(stream)))
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(load().askit_get_info(self._t, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in Info._fields_}
+
+    def structure(self, which: int) -> np.ndarray:
+        inf = self.info()
+        N, kappa, nn = inf["N"], inf["kappa"], inf["n_nodes"]
+        ell = self.cfg.s_max + self.cfg.ell_extra
+        shapes = {STRUCT_PERM: ((N,), np.int32), STRUCT_KNN: ((N, kappa), np.int32),
+                  STRUCT_KNN_DIST: ((N, kappa), np.float64), STRUCT_SKEL_S: ((nn,), np.int32),
+                  STRUCT_SKEL_IDS: ((inf["skel_total"],), np.int32), STRUCT_NL_CNT: ((nn,), np.int32),
+                  STRUCT_NL_IDS: ((nn, ell), np.int32), STRUCT_TROWS: ((nn, ell), np.int32),
+                  STRUCT_HSRC: ((N,), np.float32), STRUCT_NCOL: ((nn,), np.int32),
+                  STRUCT_WSKEL: ((inf["skel_total"], max(inf["r"], 1)), np.float32)}
+        if which == STRUCT_P:
+            s = self.structure(STRUCT_SKEL_S).astype(np.int64)
+            c = self.structure(STRUCT_NCOL).astype(np.int64)
+            shape, dt = ((int((s * (c - s)).sum()),), np.float64)
+        else:
+            shape, dt = shapes[which]
+        a = np.zeros(shape, dt)
+        _check(load().askit_get_structure(self._t, which, a.ctypes.data_as(C.c_void_p), a.nbytes))
+        return a

@@ -1,0 +1,511 @@
+// C ABI of the GB300 ASKIT library: validation, the setup pipeline of
+// Algorithm 5 (kNN, tree, node lists, samples, skeletons, work lists), the
+// per-weight-vector upward pass and Evaluate, and structure export.
+#include <float.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <string>
+
+#include "askit_impl.cuh"
+
+static thread_local std::string g_err;
+
+void askit_set_error(const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+namespace {
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+__global__ void fill_f32(float *a, int64_t n, float v) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < n) a[q] = v;
+}
+
+__global__ void h_from_knn(const double *knnd, int64_t N, int kappa, int k, float *h) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j < N) h[j] = (float)__dsqrt_rn(knnd[j * kappa + (k - 1)]);
+}
+
+__global__ void leafof_kernel(const int32_t *perm, const int32_t *nstart, const int32_t *nsize,
+                              int64_t a0, int32_t *leafof) {
+    int64_t a = a0 + blockIdx.x;
+    for (int q = threadIdx.x; q < nsize[a]; q += blockDim.x) leafof[perm[nstart[a] + q]] = (int32_t)a;
+}
+
+// Caller-given neighbor ids must lie in [0, N) and exclude the point itself.
+__global__ void check_knn_kernel(const int32_t *knn, int64_t N, int kappa, int *bad) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N * kappa) return;
+    int32_t j = knn[e];
+    if (j < 0 || j >= N || j == e / kappa) atomicExch(bad, 1);
+}
+
+__global__ void pos_kernel(const int32_t *perm, int64_t N, int32_t *pos) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < N) pos[perm[q]] = (int32_t)q;
+}
+
+// Order out-of-sample queries by the tree position of their nearest source
+// (so a tile's targets share near and far blocks): key (pos << 32) | q.
+__global__ void oos_keys_kernel(const int32_t *knn, int kappa, const int32_t *pos, int64_t T,
+                                uint64_t *keys, int32_t *vals) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= T) return;
+    keys[q] = ((uint64_t)pos[knn[q * kappa]] << 32) | (uint64_t)q;
+    vals[q] = (int32_t)q;
+}
+
+__global__ void gather_knn_kernel(const int32_t *knn, int kappa, const int32_t *order, int64_t T,
+                                  int32_t *out) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= T * kappa) return;
+    int64_t q = e / kappa;
+    out[e] = knn[(int64_t)order[q] * kappa + (e % kappa)];
+}
+
+__global__ void gather_y_kernel(const float *Y, int64_t ldy, int d, int d_pad, const int32_t *order,
+                                int64_t T, int64_t T_pad, float *out, float *nrm) {
+    int64_t row = blockIdx.x;
+    if (row >= T_pad) return;
+    int64_t q = row < T ? order[row] : -1;
+    for (int k = threadIdx.x; k < d_pad; k += blockDim.x)
+        out[row * d_pad + k] = (q >= 0 && k < d) ? Y[q * ldy + k] : 0.f;
+    if (threadIdx.x == 0) {
+        double acc = 0.0;
+        if (q >= 0)
+            for (int k = 0; k < d; ++k) acc += (double)Y[q * ldy + k] * Y[q * ldy + k];
+        nrm[row] = (float)acc;
+    }
+}
+
+askit_status validate(const askit_params *p, int64_t N, int32_t d, int64_t ldx, const float *h_dev) {
+    if (!p) { askit_set_error("params is NULL"); return ASKIT_ERR_INVALID_ARG; }
+    if (N < 1 || d < 1 || ldx < d) { askit_set_error("need N >= 1, d >= 1, ldx >= d"); return ASKIT_ERR_INVALID_ARG; }
+    if (N >= ((int64_t)1 << 31) - 1024) { askit_set_error("N must be below 2^31"); return ASKIT_ERR_UNSUPPORTED; }
+    if (p->leaf_size < 2) { askit_set_error("leaf_size must be >= 2"); return ASKIT_ERR_INVALID_ARG; }
+    if (p->kappa < 1 || p->kappa > 32 || p->kappa > N - 1) {
+        askit_set_error("kappa must be in 1..min(32, N-1)");
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    if (p->s_max < 1 || p->s_min < 0 || p->ell_extra < 0) { askit_set_error("need s_max >= 1, s_min >= 0, ell_extra >= 0"); return ASKIT_ERR_INVALID_ARG; }
+    if (!(p->id_tol >= 0.0) || !(p->kernel_scale > 0.0)) { askit_set_error("need id_tol >= 0 and kernel_scale > 0"); return ASKIT_ERR_INVALID_ARG; }
+    if (p->bw_mode == ASKIT_BW_CONSTANT && !(p->h > 0.0)) { askit_set_error("h must be > 0"); return ASKIT_ERR_INVALID_ARG; }
+    if (p->bw_mode == ASKIT_BW_ARRAY && !h_dev) { askit_set_error("ASKIT_BW_ARRAY needs h_dev"); return ASKIT_ERR_INVALID_ARG; }
+    if (p->bw_mode == ASKIT_BW_KNN && (p->bw_k < 1 || p->bw_k > p->kappa)) { askit_set_error("bw_k must be in 1..kappa"); return ASKIT_ERR_INVALID_ARG; }
+    if (p->bw_mode < 0 || p->bw_mode > 2) { askit_set_error("bad bw_mode"); return ASKIT_ERR_INVALID_ARG; }
+    if (p->knn_mode < 0 || p->knn_mode > 1) { askit_set_error("bad knn_mode"); return ASKIT_ERR_INVALID_ARG; }
+    if (p->knn_mode == 1 && p->rp_iters < 1) { askit_set_error("rp_iters must be >= 1"); return ASKIT_ERR_INVALID_ARG; }
+    if (p->precision < 0 || p->precision > 2) { askit_set_error("bad precision"); return ASKIT_ERR_INVALID_ARG; }
+    return ASKIT_OK;
+}
+
+askit_status setup_impl(askit_tree t, const float *X_dev, int64_t ldx, const float *h_dev,
+                        const int32_t *knn_dev, cudaStream_t s) {
+    const int64_t N = t->N;
+    const int d = t->d, kappa = t->kappa;
+    ASK_TRY(t->arena.alloc(&t->X, (size_t)N * d));
+    ASK_CUDA(cudaMemcpy2DAsync(t->X, sizeof(float) * d, X_dev, sizeof(float) * ldx, sizeof(float) * d, N,
+                               cudaMemcpyDeviceToDevice, s));
+    // nearest neighbors (Section 2.2)
+    ASK_TRY(t->arena.alloc(&t->knn, (size_t)N * kappa));
+    ASK_TRY(t->arena.alloc(&t->knnd, (size_t)N * kappa));
+    if (knn_dev) {
+        ASK_CUDA(cudaMemcpyAsync(t->knn, knn_dev, sizeof(int32_t) * N * kappa, cudaMemcpyDeviceToDevice, s));
+        int *bad = nullptr, hbad = 0;
+        ASK_TRY(t->arena.alloc(&bad, 1));
+        ASK_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        check_knn_kernel<<<nblk(N * kappa, 256), 256, 0, s>>>(t->knn, N, kappa, bad);
+        ASK_LAUNCH();
+        ASK_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        ASK_CUDA(cudaStreamSynchronize(s));
+        t->arena.release(bad);
+        if (hbad) { askit_set_error("knn_dev holds an id outside [0, N) or the point itself"); return ASKIT_ERR_INVALID_ARG; }
+        ASK_TRY(knn_dist_gpu(t->X, N, d, kappa, t->knn, t->knnd, s));
+    } else if (t->prm.knn_mode == 0) {
+        ASK_TRY(knn_exact_gpu(t->X, N, d, kappa, nullptr, N, t->knn, t->knnd, s));
+    } else {
+        ASK_TRY(knn_rp_gpu(t->X, N, d, kappa, t->prm.rp_iters, t->rp_leaf, t->prm.seed, t->knn, t->knnd, s));
+    }
+    // bandwidth of every source point (Section 4)
+    ASK_TRY(t->arena.alloc(&t->hsrc, N));
+    if (t->prm.bw_mode == ASKIT_BW_CONSTANT) {
+        fill_f32<<<nblk(N, 256), 256, 0, s>>>(t->hsrc, N, (float)t->prm.h);
+    } else if (t->prm.bw_mode == ASKIT_BW_ARRAY) {
+        ASK_CUDA(cudaMemcpyAsync(t->hsrc, h_dev, sizeof(float) * N, cudaMemcpyDeviceToDevice, s));
+    } else {
+        h_from_knn<<<nblk(N, 256), 256, 0, s>>>(t->knnd, N, kappa, t->prm.bw_k, t->hsrc);
+    }
+    ASK_LAUNCH();
+    // the ASKIT tree (Section 2.2)
+    t->L = tree_depth(N, t->prm.leaf_size);
+    t->n_nodes = (int64_t)2 << t->L;
+    tree_ranges(N, t->L, t->h_start, t->h_size);
+    ASK_TRY(t->arena.alloc(&t->perm, N));
+    ASK_TRY(t->arena.alloc(&t->pos, N));
+    ASK_TRY(t->arena.alloc(&t->leafof, N));
+    ASK_TRY(build_tree_gpu(t->X, N, d, t->L, 0, 0, 0, t->perm, s));
+    {
+        std::vector<int32_t> hs(t->n_nodes), hz(t->n_nodes);
+        for (int64_t a = 0; a < t->n_nodes; ++a) { hs[a] = (int32_t)t->h_start[a]; hz[a] = (int32_t)t->h_size[a]; }
+        ASK_TRY(t->arena.alloc(&t->nstart, t->n_nodes));
+        ASK_TRY(t->arena.alloc(&t->nsize, t->n_nodes));
+        ASK_CUDA(cudaMemcpyAsync(t->nstart, hs.data(), sizeof(int32_t) * t->n_nodes, cudaMemcpyHostToDevice, s));
+        ASK_CUDA(cudaMemcpyAsync(t->nsize, hz.data(), sizeof(int32_t) * t->n_nodes, cudaMemcpyHostToDevice, s));
+        int64_t a0 = (int64_t)1 << t->L;
+        leafof_kernel<<<(unsigned)a0, 128, 0, s>>>(t->perm, t->nstart, t->nsize, a0, t->leafof);
+        pos_kernel<<<nblk(N, 256), 256, 0, s>>>(t->perm, N, t->pos);
+        ASK_LAUNCH();
+        ASK_CUDA(cudaStreamSynchronize(s));
+    }
+    // node neighbor lists, sampled targets, skeletons (Algorithms 2, 3)
+    const int64_t nn = t->n_nodes;
+    t->ell_max = t->prm.s_max + t->prm.ell_extra;
+    ASK_TRY(t->arena.alloc(&t->nl_cnt, nn));
+    ASK_TRY(t->arena.alloc(&t->nl_ids, (size_t)nn * t->ell_max));
+    ASK_TRY(t->arena.alloc(&t->nl_key, (size_t)nn * t->ell_max));
+    ASK_TRY(t->arena.alloc(&t->trows, (size_t)nn * t->ell_max));
+    ASK_TRY(t->arena.alloc(&t->d_s, nn));
+    ASK_TRY(t->arena.alloc(&t->d_ncol, nn));
+    ASK_CUDA(cudaMemsetAsync(t->nl_cnt, 0, sizeof(int32_t) * nn, s));
+    ASK_CUDA(cudaMemsetAsync(t->nl_ids, 0xff, sizeof(int32_t) * nn * t->ell_max, s));
+    ASK_CUDA(cudaMemsetAsync(t->trows, 0xff, sizeof(int32_t) * nn * t->ell_max, s));
+    ASK_CUDA(cudaMemsetAsync(t->d_ncol, 0, sizeof(int32_t) * nn, s));
+    ASK_TRY(build_node_lists(t, s));
+    ASK_TRY(build_samples(t, s));
+    ASK_TRY(skeletonize(t, s));
+    if (t->L == 0) {
+        // a single leaf: no skeletons, empty pools
+        t->h_skoff.assign(nn + 1, 0); t->h_pivoff.assign(nn + 1, 0);
+        t->h_poff.assign(nn + 1, 0); t->h_spool.assign(nn + 1, 0);
+        ASK_TRY(t->arena.alloc(&t->skel_ids, 1)); ASK_TRY(t->arena.alloc(&t->piv, 1));
+        ASK_TRY(t->arena.alloc(&t->P64, 1)); ASK_TRY(t->arena.alloc(&t->P32, 1));
+        ASK_TRY(t->arena.alloc(&t->d_poff, nn + 1)); ASK_TRY(t->arena.alloc(&t->d_skoff, nn + 1));
+        ASK_TRY(t->arena.alloc(&t->d_pivoff, nn + 1)); ASK_TRY(t->arena.alloc(&t->d_spool, nn + 1));
+        ASK_CUDA(cudaMemsetAsync(t->d_poff, 0, sizeof(int64_t) * (nn + 1), s));
+        ASK_CUDA(cudaMemsetAsync(t->d_skoff, 0, sizeof(int64_t) * (nn + 1), s));
+        ASK_CUDA(cudaMemsetAsync(t->d_pivoff, 0, sizeof(int64_t) * (nn + 1), s));
+        ASK_CUDA(cudaMemsetAsync(t->d_spool, 0, sizeof(int64_t) * (nn + 1), s));
+        ASK_CUDA(cudaMemsetAsync(t->d_s, 0, sizeof(int32_t) * nn, s));
+    }
+    // evaluation operands and the in-sample work lists (eq. (2.5), Algorithm 4)
+    ASK_TRY(build_eval_operands(t, s));
+    ASK_TRY(build_tc_operands(t, s));
+    {
+        // prune sets: {i} U N_i as leaves; with pruning off, every leaf
+        int stride = t->prm.prune ? kappa + 1 : (int)((int64_t)1 << t->L);
+        int32_t *sets = nullptr;
+        ASK_CUDA(cudaMalloc(&sets, sizeof(int32_t) * N * stride));
+        askit_status rc = insample_prune_sets(t, sets, s);
+        if (rc == ASKIT_OK)
+            rc = build_work_lists(t, sets, stride, N, t->wl, t->arena, s);
+        cudaFree(sets);
+        ASK_TRY(rc);
+    }
+    ASK_TRY(t->arena.alloc(&t->d_status, 4));
+    ASK_TRY(t->arena.alloc(&t->d_ticket, 4));
+    ASK_CUDA(cudaMemsetAsync(t->d_status, 0, sizeof(int) * 4, s));
+    ASK_CUDA(cudaMemsetAsync(t->d_ticket, 0, sizeof(int) * 4, s));
+    ASK_CUDA(cudaStreamSynchronize(s));
+    return ASKIT_OK;
+}
+
+// Evaluate over one set of work lists: every (target, sub-block) entry's
+// partial sum, then each target's entries summed in their fixed order.
+askit_status run_eval(askit_tree t, int precision, const float *Xq, int64_t ldq, const WorkLists &w,
+                      float *partial, const int32_t *out_rows, float *U, int64_t ldu, cudaStream_t s) {
+    if (precision == ASKIT_PREC_SIMT_FP32)
+        ASK_TRY(eval_simt(t, Xq, ldq, w, partial, s));
+    else
+        ASK_TRY(eval_tc(t, precision, Xq, ldq, w, partial, s));
+    return reduce_partials(w, partial, t->r, out_rows, U, ldu, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+void askit_default_params(askit_params *p) {
+    if (!p) return;
+    p->leaf_size = 128;
+    p->kappa = 16;
+    p->knn_mode = 0;
+    p->rp_iters = 4;
+    p->rp_leaf = 0;
+    p->s_max = 64;
+    p->s_min = 1;
+    p->ell_extra = 20;
+    p->prune = 1;
+    p->bw_mode = ASKIT_BW_CONSTANT;
+    p->bw_k = 16;
+    p->precision = ASKIT_PREC_TF32X3;
+    p->id_tol = 1e-6;
+    p->kernel_scale = 0.5;
+    p->h = 1.0;
+    p->seed = 1;
+}
+
+const char *askit_status_string(askit_status s) {
+    switch (s) {
+        case ASKIT_OK: return "ok";
+        case ASKIT_ERR_INVALID_ARG: return "invalid argument";
+        case ASKIT_ERR_OOM: return "out of device memory";
+        case ASKIT_ERR_CUDA: return "CUDA error";
+        case ASKIT_ERR_TIMEOUT: return "device wait timed out";
+        case ASKIT_ERR_NOT_READY: return "not ready";
+        case ASKIT_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *askit_last_error(void) { return g_err.c_str(); }
+
+askit_status askit_setup(const float *X_dev, int64_t N, int32_t d, int64_t ldx, const float *h_dev,
+                         const int32_t *knn_dev, const askit_params *p, void *stream, askit_tree *out) {
+    if (!out || !X_dev) { askit_set_error("X_dev and out must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
+    *out = nullptr;
+    ASK_TRY(validate(p, N, d, ldx, h_dev));
+    askit_tree t = new askit_tree_s();
+    t->prm = *p;
+    t->N = N;
+    t->d = d;
+    t->d_pad = (d + 31) / 32 * 32;
+    t->kappa = p->kappa;
+    t->rp_leaf = p->rp_leaf > 0 ? p->rp_leaf : std::max(2 * p->kappa + 2, p->leaf_size);
+    if (t->prm.knn_mode == 1 && t->rp_leaf < 2 * p->kappa + 2) {
+        delete t;
+        askit_set_error("rp_leaf must be >= 2 kappa + 2");
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    t->precision = p->precision;
+    if (!p->prune && (N << tree_depth(N, p->leaf_size)) > ((int64_t)1 << 28)) {
+        delete t;
+        askit_set_error("prune = 0 lists every leaf for every target; N x leaves must stay below 2^28");
+        return ASKIT_ERR_UNSUPPORTED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    askit_status rc = setup_impl(t, X_dev, ldx, h_dev, knn_dev, s);
+    if (rc != ASKIT_OK) {
+        cudaStreamSynchronize(s);
+        eval_tc_free(t);
+        t->arena.free_all();
+        delete t;
+        return rc;
+    }
+    *out = t;
+    return ASKIT_OK;
+}
+
+askit_status askit_set_weights(askit_tree t, const float *W_dev, int32_t r, int64_t ldw, void *stream) {
+    if (!t || !W_dev) { askit_set_error("tree and W_dev must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
+    if (r < 1 || r > 64 || ldw < r) { askit_set_error("need 1 <= r <= 64 and ldw >= r"); return ASKIT_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (r != t->r) {
+        if (t->Wt) t->arena.release(t->Wt);
+        if (t->Ws) t->arena.release(t->Ws);
+        t->Wt = t->Ws = nullptr;
+        int64_t srows = std::max<int64_t>(t->spool_rows, 1) + 256;
+        if (t->partial) t->arena.release(t->partial);
+        t->partial = nullptr;
+        ASK_TRY(t->arena.alloc(&t->Wt, (size_t)t->N_pad * r));
+        ASK_TRY(t->arena.alloc(&t->Ws, (size_t)srows * r));
+        ASK_TRY(t->arena.alloc(&t->partial, (size_t)t->wl.n_entries * r));
+        ASK_CUDA(cudaMemsetAsync(t->Wt, 0, sizeof(float) * t->N_pad * r, s));
+        ASK_CUDA(cudaMemsetAsync(t->Ws, 0, sizeof(float) * srows * r, s));
+        t->r = r;
+    }
+    ASK_TRY(upward_weights(t, W_dev, r, ldw, s));
+    t->weights_ready = true;
+    return ASKIT_OK;
+}
+
+askit_status askit_set_precision(askit_tree t, int32_t precision) {
+    if (!t || precision < 0 || precision > 2) { askit_set_error("bad tree or precision"); return ASKIT_ERR_INVALID_ARG; }
+    t->precision = precision;
+    return ASKIT_OK;
+}
+
+askit_status askit_evaluate(askit_tree t, float *U_dev, int64_t ldu, void *stream) {
+    if (!t || !U_dev) { askit_set_error("tree and U_dev must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
+    if (!t->weights_ready) { askit_set_error("askit_set_weights has not been called"); return ASKIT_ERR_NOT_READY; }
+    if (ldu < t->r) { askit_set_error("ldu < r"); return ASKIT_ERR_INVALID_ARG; }
+    return run_eval(t, t->precision, t->Xt, t->d_pad, t->wl, t->partial, t->perm, U_dev, ldu,
+                    (cudaStream_t)stream);
+}
+
+askit_status askit_evaluate_targets(askit_tree t, const float *Y_dev, int64_t T, int64_t ldy, float *U_dev,
+                                    int64_t ldu, void *stream) {
+    if (!t || !Y_dev || !U_dev) { askit_set_error("tree, Y_dev and U_dev must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
+    if (!t->weights_ready) { askit_set_error("askit_set_weights has not been called"); return ASKIT_ERR_NOT_READY; }
+    if (T < 1 || ldy < t->d || ldu < t->r) { askit_set_error("need T >= 1, ldy >= d, ldu >= r"); return ASKIT_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int kappa = t->kappa, d = t->d;
+    DevArena tmp;
+    float *Yc = nullptr, *Yt = nullptr, *nrm = nullptr;
+    int32_t *ids = nullptr, *ids_s = nullptr, *order = nullptr, *vals = nullptr, *sets = nullptr;
+    double *dist = nullptr;
+    uint64_t *keys = nullptr, *keys_s = nullptr;
+    void *cub = nullptr;
+    size_t cb = 0;
+    WorkLists w;
+    float *partial = nullptr;
+    int64_t T_pad = (T + ASK_TILE_M - 1) / ASK_TILE_M * ASK_TILE_M;
+    askit_status rc = ASKIT_OK;
+#define OTRY(x) do { rc = (x); if (rc != ASKIT_OK) goto out; } while (0)
+    OTRY(tmp.alloc(&Yc, (size_t)T * d));
+    if (cudaMemcpy2DAsync(Yc, sizeof(float) * d, Y_dev, sizeof(float) * ldy, sizeof(float) * d, T,
+                          cudaMemcpyDeviceToDevice, s) != cudaSuccess) { askit_set_error("copy Y"); rc = ASKIT_ERR_CUDA; goto out; }
+    OTRY(tmp.alloc(&ids, (size_t)T * kappa));
+    OTRY(tmp.alloc(&dist, (size_t)T * kappa));
+    OTRY(knn_exact_gpu(t->X, t->N, d, kappa, Yc, T, ids, dist, s));
+    OTRY(tmp.alloc(&keys, T)); OTRY(tmp.alloc(&keys_s, T));
+    OTRY(tmp.alloc(&vals, T)); OTRY(tmp.alloc(&order, T));
+    oos_keys_kernel<<<nblk(T, 256), 256, 0, s>>>(ids, kappa, t->pos, T, keys, vals);
+    OTRY(sort_u64_i32(nullptr, nullptr, nullptr, nullptr, T, nullptr, &cb, s));
+    OTRY(tmp.alloc((char **)&cub, cb));
+    OTRY(sort_u64_i32(keys, keys_s, vals, order, T, cub, &cb, s));
+    OTRY(tmp.alloc(&ids_s, (size_t)T * kappa));
+    gather_knn_kernel<<<nblk(T * kappa, 256), 256, 0, s>>>(ids, kappa, order, T, ids_s);
+    OTRY(tmp.alloc(&Yt, (size_t)T_pad * t->d_pad));
+    OTRY(tmp.alloc(&nrm, T_pad));
+    gather_y_kernel<<<(unsigned)T_pad, 128, 0, s>>>(Yc, d, d, t->d_pad, order, T, T_pad, Yt, nrm);
+    OTRY(tmp.alloc(&sets, (size_t)T * kappa));
+    OTRY(oos_prune_sets(t, ids_s, T, kappa, sets, s));
+    OTRY(build_work_lists(t, sets, kappa, T, w, tmp, s));
+    OTRY(tmp.alloc(&partial, (size_t)w.n_entries * t->r));
+    OTRY(run_eval(t, t->precision, Yt, t->d_pad, w, partial, order, U_dev, ldu, s));
+    if (cudaStreamSynchronize(s) != cudaSuccess) { askit_set_error("out-of-sample evaluate: %s", cudaGetErrorString(cudaGetLastError())); rc = ASKIT_ERR_CUDA; }
+out:
+#undef OTRY
+    cudaStreamSynchronize(s);
+    tmp.free_all();
+    return rc;
+}
+
+askit_status askit_evaluate_host(askit_tree t, const float *W_host, int32_t r, int64_t ldw, float *U_host,
+                                 int64_t ldu, void *stream) {
+    if (!t || !W_host || !U_host) { askit_set_error("tree, W_host and U_host must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
+    if (r < 1 || r > 64 || ldw < r || ldu < r) { askit_set_error("need 1 <= r <= 64, ldw >= r, ldu >= r"); return ASKIT_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    static thread_local DevArena io;
+    static thread_local float *dW = nullptr, *dU = nullptr;
+    static thread_local size_t cap = 0;
+    size_t need = (size_t)t->N * r;
+    if (need > cap) {
+        io.free_all();
+        ASK_TRY(io.alloc(&dW, need));
+        ASK_TRY(io.alloc(&dU, need));
+        cap = need;
+    }
+    ASK_CUDA(cudaMemcpy2DAsync(dW, sizeof(float) * r, W_host, sizeof(float) * ldw, sizeof(float) * r, t->N,
+                               cudaMemcpyHostToDevice, s));
+    ASK_TRY(askit_set_weights(t, dW, r, r, stream));
+    ASK_TRY(askit_evaluate(t, dU, r, stream));
+    ASK_CUDA(cudaMemcpy2DAsync(U_host, sizeof(float) * ldu, dU, sizeof(float) * r, sizeof(float) * r, t->N,
+                               cudaMemcpyDeviceToHost, s));
+    ASK_CUDA(cudaStreamSynchronize(s));
+    return askit_sync(t, stream);
+}
+
+askit_status askit_get_info(askit_tree t, askit_info *info) {
+    if (!t || !info) { askit_set_error("tree and info must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
+    info->N = t->N;
+    info->d = t->d;
+    info->d_pad = t->d_pad;
+    info->L = t->L;
+    info->kappa = t->kappa;
+    info->r = t->r;
+    info->n_nodes = t->n_nodes;
+    info->skel_total = t->skel_total;
+    info->skel_rows_padded = t->spool_rows;
+    info->n_blocks = t->wl.n_blocks;
+    info->n_items = t->wl.n_items;
+    info->n_entries = t->wl.n_entries;
+    info->pairs_algorithmic = t->wl.pairs_alg;
+    info->pairs_computed = t->wl.pairs_cmp;
+    info->near_total = t->wl.near_tot;
+    info->far_total = t->wl.far_tot;
+    info->device_bytes = (int64_t)t->arena.bytes;
+    return ASKIT_OK;
+}
+
+askit_status askit_get_structure(askit_tree t, int32_t which, void *host, size_t bytes) {
+    if (!t || !host) { askit_set_error("tree and host must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
+    const int64_t N = t->N, nn = t->n_nodes;
+    const void *src = nullptr;
+    size_t want = 0;
+    std::vector<int32_t> tmp;
+    switch (which) {
+        case ASKIT_STRUCT_PERM: src = t->perm; want = sizeof(int32_t) * N; break;
+        case ASKIT_STRUCT_KNN: src = t->knn; want = sizeof(int32_t) * N * t->kappa; break;
+        case ASKIT_STRUCT_KNN_DIST: src = t->knnd; want = sizeof(double) * N * t->kappa; break;
+        case ASKIT_STRUCT_SKEL_S:
+            tmp.assign(t->h_s.begin(), t->h_s.end());
+            tmp.resize(nn, 0);
+            want = sizeof(int32_t) * nn;
+            if (bytes != want) break;
+            memcpy(host, tmp.data(), want);
+            return ASKIT_OK;
+        case ASKIT_STRUCT_NCOL:
+            tmp.assign(t->h_ncol.begin(), t->h_ncol.end());
+            tmp.resize(nn, 0);
+            want = sizeof(int32_t) * nn;
+            if (bytes != want) break;
+            memcpy(host, tmp.data(), want);
+            return ASKIT_OK;
+        case ASKIT_STRUCT_SKEL_IDS: src = t->skel_ids; want = sizeof(int32_t) * t->skel_total; break;
+        case ASKIT_STRUCT_NL_CNT: src = t->nl_cnt; want = sizeof(int32_t) * nn; break;
+        case ASKIT_STRUCT_NL_IDS: src = t->nl_ids; want = sizeof(int32_t) * nn * t->ell_max; break;
+        case ASKIT_STRUCT_TROWS: src = t->trows; want = sizeof(int32_t) * nn * t->ell_max; break;
+        case ASKIT_STRUCT_HSRC: src = t->hsrc; want = sizeof(float) * N; break;
+        case ASKIT_STRUCT_P: src = t->P64; want = sizeof(double) * t->p_total; break;
+        case ASKIT_STRUCT_WSKEL: {
+            if (!t->weights_ready) { askit_set_error("no weights set"); return ASKIT_ERR_NOT_READY; }
+            want = sizeof(float) * t->skel_total * t->r;
+            if (bytes != want) break;
+            float *h = (float *)host;
+            for (int64_t a = 2; a < nn; ++a) {
+                if (!t->h_s[a]) continue;
+                ASK_CUDA(cudaMemcpy(h + t->h_skoff[a] * t->r, t->Ws + t->h_spool[a] * t->r,
+                                    sizeof(float) * t->h_s[a] * t->r, cudaMemcpyDeviceToHost));
+            }
+            return ASKIT_OK;
+        }
+        default: askit_set_error("unknown structure %d", which); return ASKIT_ERR_INVALID_ARG;
+    }
+    if (bytes != want) {
+        askit_set_error("structure %d needs %zu bytes, got %zu", which, want, bytes);
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    if (want) ASK_CUDA(cudaMemcpy(host, src, want, cudaMemcpyDeviceToHost));
+    return ASKIT_OK;
+}
+
+askit_status askit_sync(askit_tree t, void *stream) {
+    if (!t) { askit_set_error("tree is NULL"); return ASKIT_ERR_INVALID_ARG; }
+    ASK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int st = 0;
+    ASK_CUDA(cudaMemcpy(&st, t->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st == ASK_DEV_TIMEOUT) { askit_set_error("a kernel gave up a bounded wait"); return ASKIT_ERR_TIMEOUT; }
+    if (st != ASK_DEV_OK) { askit_set_error("kernel status %d", st); return ASKIT_ERR_CUDA; }
+    return ASKIT_OK;
+}
+
+askit_status askit_destroy(askit_tree t) {
+    if (!t) return ASKIT_OK;
+    cudaDeviceSynchronize();
+    eval_tc_free(t);
+    t->arena.free_all();
+    delete t;
+    return ASKIT_OK;
+}
+
+}  // extern "C"

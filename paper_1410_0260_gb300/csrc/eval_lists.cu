@@ -1,0 +1,535 @@
+// Evaluation operands and work lists.
+//
+// Algorithm 4 visits, for target i, exactly the nodes of
+//   U_i = union over j in {i} U N_i of the ancestors of leaf(j)
+// (eq. (2.5): those nodes cannot be pruned).  The leaves of U_i are summed
+// directly (Near(i)); every child of a node of U_i that is not itself in U_i
+// is pruned and contributes through its skeleton (Far(i)).  The GPU groups
+// targets into tiles of 128 consecutive rows and turns the union of the
+// tile's Near and Far sets into work items (tile, source block, 128-bit mask
+// of the targets that need the block); one persistent kernel then runs all
+// items.  Source blocks are contiguous rows: a leaf's points in the
+// tree-ordered coordinate array, or a node's skeleton in the skeleton pool.
+#include <limits.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include <cuda_bf16.h>
+
+#include "askit_impl.cuh"
+
+namespace {
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// Tree-ordered, zero-padded coordinates, squared norms (FP64 sum, rounded)
+// and the per-source exponent scale c log2(e) / h_j^2.
+__global__ void gather_rows_kernel(const float *X, int d, int d_pad, const int32_t *ids, int64_t n,
+                                   int64_t n_rows, const float *hsrc, double kscale, float *out,
+                                   float *nrm, float *sc) {
+    int64_t row = blockIdx.x;
+    if (row >= n_rows) return;
+    int32_t id = row < n ? ids[row] : -1;
+    for (int k = threadIdx.x; k < d_pad; k += blockDim.x)
+        out[row * d_pad + k] = (id >= 0 && k < d) ? X[(int64_t)id * d + k] : 0.0f;
+    if (threadIdx.x == 0) {
+        double acc = 0.0;
+        if (id >= 0)
+            for (int k = 0; k < d; ++k) acc += (double)X[(int64_t)id * d + k] * X[(int64_t)id * d + k];
+        nrm[row] = (float)acc;
+        if (sc) {
+            double h = id >= 0 ? (double)hsrc[id] : 1.0;
+            sc[row] = id >= 0 ? (float)(kscale * 1.4426950408889634 / (h * h)) : 0.0f;
+        }
+    }
+}
+
+// Skeleton pool row ids: rows [spool[a], spool[a] + s_a) hold S_a, the
+// padding up to a multiple of ASK_ROW_PAD is empty (-1).
+__global__ void spool_ids_kernel(int64_t n_nodes, const int64_t *spool, const int64_t *skoff,
+                                 const int32_t *s, const int32_t *skel_ids, int32_t *rows) {
+    int64_t a = 2 + blockIdx.x;
+    if (a >= n_nodes) return;
+    int64_t r0 = spool[a], r1 = spool[a + 1];
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        int64_t q = r - r0;
+        rows[r] = q < s[a] ? skel_ids[skoff[a] + q] : -1;
+    }
+}
+
+// Prune set of each in-sample target (tree position q): the sorted distinct
+// leaves of {i} U N_i, padded with INT_MAX to kappa + 1 entries.
+__global__ void insample_sets_kernel(const int32_t *perm, const int32_t *leafof, const int32_t *knn,
+                                     int64_t N, int kappa, int32_t *sets) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= N) return;
+    int32_t i = perm[q];
+    int32_t *o = sets + q * (kappa + 1);
+    int n = 0;
+    for (int z = -1; z < kappa; ++z) {
+        int32_t lf = leafof[z < 0 ? i : knn[(int64_t)i * kappa + z]];
+        int p = n;
+        bool dup = false;
+        for (int u = 0; u < n; ++u) dup |= (o[u] == lf);
+        if (dup) continue;
+        while (p > 0 && o[p - 1] > lf) { o[p] = o[p - 1]; --p; }
+        o[p] = lf;
+        ++n;
+    }
+    for (int u = n; u < kappa + 1; ++u) o[u] = INT_MAX;
+}
+
+// Pruning switched off: every leaf is near for every target.
+__global__ void all_leaves_sets_kernel(int64_t N, int L, int32_t *sets) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t M = (int64_t)1 << L;
+    if (e >= N * M) return;
+    sets[e] = (int32_t)(M + e % M);
+}
+
+// Out-of-sample prune sets: distinct leaves of N_y (no self term).
+__global__ void oos_sets_kernel(const int32_t *leafof, const int32_t *knn, int64_t T, int kappa,
+                                int stride, int32_t *sets) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= T) return;
+    int32_t *o = sets + q * stride;
+    int n = 0;
+    for (int z = 0; z < kappa; ++z) {
+        int32_t lf = leafof[knn[q * kappa + z]];
+        int p = n;
+        bool dup = false;
+        for (int u = 0; u < n; ++u) dup |= (o[u] == lf);
+        if (dup) continue;
+        while (p > 0 && o[p - 1] > lf) { o[p] = o[p - 1]; --p; }
+        o[p] = lf;
+        ++n;
+    }
+    for (int u = n; u < stride; ++u) o[u] = INT_MAX;
+}
+
+// Near and Far sets of one target from its sorted prune leaves.  Near =
+// the leaves; Far = for each depth, the sibling of every distinct ancestor
+// at that depth when the sibling is not itself an ancestor of a near leaf.
+// emit(node, far) is called once per node of Near(i) and Far(i).
+template <class F>
+__device__ __forceinline__ void walk_lists(const int32_t *set, int stride, int L, F emit) {
+    int n = 0;
+    while (n < stride && set[n] != INT_MAX) ++n;
+    for (int u = 0; u < n; ++u) emit(set[u], false);
+    for (int depth = L; depth >= 1; --depth) {
+        int sh = L - depth;
+        for (int u = 0; u < n; ++u) {
+            int32_t b = set[u] >> sh;
+            if (u > 0 && (set[u - 1] >> sh) == b) continue;   // ancestor already handled
+            int32_t sib = b ^ 1;
+            bool inU = false;
+            for (int w = 0; w < n && !inU; ++w) inU = ((set[w] >> sh) == sib);
+            if (!inU) emit(sib, true);
+        }
+    }
+}
+
+// Source rows of a node's block: a leaf's points (near) or its skeleton (far).
+__device__ __forceinline__ int block_rows(int32_t node, bool far, const int32_t *nsize, const int32_t *s) {
+    return far ? s[node] : nsize[node];
+}
+
+// Entries are (target, source sub-block of <= ASK_BLK_N rows) pairs; the key
+// of a sub-block is (node << 5) | (chunk << 1) | far.
+__device__ __forceinline__ uint32_t sub_key(int32_t node, int chunk, bool far) {
+    return ((uint32_t)node << 5) | ((uint32_t)chunk << 1) | (far ? 1u : 0u);
+}
+
+__global__ void count_kernel(const int32_t *sets, int stride, int64_t T, int L, const int32_t *nsize,
+                             const int32_t *s, int64_t *cnt, int64_t *nearc, int64_t *farc, int64_t *pairs) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= T) return;
+    int64_t c = 0, nf = 0, nn = 0, pr = 0;
+    walk_lists(sets + q * stride, stride, L, [&](int32_t node, bool far) {
+        int rows = block_rows(node, far, nsize, s);
+        c += (rows + ASK_BLK_N - 1) / ASK_BLK_N;
+        pr += rows;
+        if (far) ++nf; else ++nn;
+    });
+    cnt[q] = c;
+    nearc[q] = nn;
+    farc[q] = nf;
+    pairs[q] = pr;
+}
+
+__global__ void emit_kernel(const int32_t *sets, int stride, int64_t T, int L, const int32_t *nsize,
+                            const int32_t *s, const int64_t *off, uint64_t *keys, int64_t *vals) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= T) return;
+    int64_t o = off[q];
+    walk_lists(sets + q * stride, stride, L, [&](int32_t node, bool far) {
+        int rows = block_rows(node, far, nsize, s);
+        for (int ch = 0; ch * ASK_BLK_N < rows; ++ch) {
+            keys[o] = ((uint64_t)sub_key(node, ch, far) << 32) | (uint64_t)q;
+            vals[o] = o;
+            ++o;
+        }
+    });
+}
+
+// After sorting by (sub-block, target): slot of every emitted entry, the
+// target of every sorted entry, and the first entry of every sub-block.
+__global__ void scatter_kernel(const uint64_t *keys, const int64_t *emit_of, int64_t n, int64_t *slot_of_emit,
+                               int32_t *tgt, int64_t *bflag) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    slot_of_emit[emit_of[e]] = e;
+    tgt[e] = (int32_t)(uint32_t)keys[e];
+    bflag[e] = (e == 0 || (keys[e] >> 32) != (keys[e - 1] >> 32)) ? 1 : 0;
+}
+
+// Block index (inclusive scan of bflag minus one) and block starts.
+__global__ void block_start_kernel(const int64_t *bflag, const int64_t *bidx_excl, int64_t n, int64_t *bstart) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    if (bflag[e]) bstart[bidx_excl[e]] = e;
+}
+
+__global__ void item_flag_kernel(const int64_t *bflag, const int64_t *bidx_excl, const int64_t *bstart, int64_t n,
+                                 int64_t *iflag) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    int64_t b = bidx_excl[e] + bflag[e] - 1;
+    iflag[e] = ((e - bstart[b]) % ASK_TILE_M) == 0 ? 1 : 0;
+}
+
+__global__ void build_items_kernel(const uint64_t *keys, const int64_t *bflag, const int64_t *bidx_excl,
+                                   const int64_t *iflag, const int64_t *iidx_excl, int64_t n, int64_t nb,
+                                   const int64_t *bstart, const int32_t *nstart, const int32_t *nsize,
+                                   const int64_t *spool, const int32_t *s, const int32_t *leaf_cbase,
+                                   const int32_t *node_cbase, int64_t leaf0, EvalItem *items, int32_t *block_off) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    int64_t b = bidx_excl[e] + bflag[e] - 1;
+    if (bflag[e]) block_off[b] = (int32_t)iidx_excl[e];
+    if (e == 0) block_off[nb] = (int32_t)(iidx_excl[n - 1] + iflag[n - 1]);
+    if (!iflag[e]) return;
+    uint32_t key = (uint32_t)(keys[e] >> 32);
+    int32_t node = (int32_t)(key >> 5);
+    int chunk = (int)((key >> 1) & 15);
+    bool far = key & 1;
+    int rows = far ? s[node] : nsize[node];
+    int64_t bend = (b + 1 < nb) ? bstart[b + 1] : n;
+    EvalItem x;
+    x.row0 = (far ? (int32_t)spool[node] : nstart[node]) + chunk * ASK_BLK_N;
+    x.nrows = min(ASK_BLK_N, rows - chunk * ASK_BLK_N) | (far ? (int32_t)0x80000000 : 0);
+    x.e0 = (int32_t)e;
+    x.cnt = (int32_t)((bend - e) < ASK_TILE_M ? (bend - e) : ASK_TILE_M);
+    x.cidx = (far ? node_cbase[node] : leaf_cbase[node - leaf0]) + chunk;
+    x.pad_[0] = x.pad_[1] = x.pad_[2] = 0;
+    items[iidx_excl[e]] = x;
+}
+
+__global__ void reduce_partials_kernel(const float *partial, const int64_t *off, const int64_t *slot_of_emit,
+                                       int64_t T, int r, const int32_t *out_rows, float *U, int64_t ldu) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= T * r) return;
+    int64_t q = t / r;
+    int z = (int)(t % r);
+    float acc = 0.f;
+    for (int64_t o = off[q]; o < off[q + 1]; ++o) acc += partial[slot_of_emit[o] * r + z];
+    U[(int64_t)out_rows[q] * ldu + z] = acc;
+}
+
+}  // namespace
+
+askit_status build_eval_operands(askit_tree t, cudaStream_t s) {
+    const int64_t N = t->N;
+    t->N_pad = (N + ASK_TILE_M - 1) / ASK_TILE_M * ASK_TILE_M + 256;
+    ASK_TRY(t->arena.alloc(&t->Xt, (size_t)t->N_pad * t->d_pad));
+    ASK_TRY(t->arena.alloc(&t->nrm_t, t->N_pad));
+    ASK_TRY(t->arena.alloc(&t->sc_t, t->N_pad));
+    gather_rows_kernel<<<(unsigned)t->N_pad, 128, 0, s>>>(t->X, t->d, t->d_pad, t->perm, N, t->N_pad, t->hsrc,
+                                                         t->prm.kernel_scale, t->Xt, t->nrm_t, t->sc_t);
+    ASK_LAUNCH();
+    int64_t rows = std::max<int64_t>(t->spool_rows, 1) + 256;
+    int32_t *ids = nullptr;
+    ASK_TRY(t->arena.alloc(&ids, rows));
+    ASK_CUDA(cudaMemsetAsync(ids, 0xff, sizeof(int32_t) * rows, s));
+    if (t->n_nodes > 2)
+        spool_ids_kernel<<<(unsigned)(t->n_nodes - 2), 128, 0, s>>>(t->n_nodes, t->d_spool, t->d_skoff, t->d_s,
+                                                                   t->skel_ids, ids);
+    ASK_LAUNCH();
+    ASK_TRY(t->arena.alloc(&t->Xs, (size_t)rows * t->d_pad));
+    ASK_TRY(t->arena.alloc(&t->nrm_s, rows));
+    ASK_TRY(t->arena.alloc(&t->sc_s, rows));
+    gather_rows_kernel<<<(unsigned)rows, 128, 0, s>>>(t->X, t->d, t->d_pad, ids, rows, rows, t->hsrc,
+                                                     t->prm.kernel_scale, t->Xs, t->nrm_s, t->sc_s);
+    ASK_LAUNCH();
+    ASK_CUDA(cudaStreamSynchronize(s));
+    t->arena.release(ids);
+    return ASKIT_OK;
+}
+
+// One CTA per source sub-block: its center (FP64 mean of the valid rows,
+// rounded), the centered rows split for the tensor cores -- TF32: hi = the
+// FP32 value with the 13 low mantissa bits cleared, lo = x - hi; BF16: hi =
+// bf16(x), lo = bf16(x - hi) -- and the squared norms of the centered rows.
+__global__ void tc_prep_kernel(const float *X, int d_pad, const int64_t *sb_row0, const int32_t *sb_nrows,
+                               int64_t rows_total, float *cent, float *Xhi, float *Xlo, uint16_t *Bhi,
+                               uint16_t *Blo, float *nrmc) {
+    int g = blockIdx.x;
+    int64_t r0 = sb_row0[g];
+    int nr = sb_nrows[g];
+    __shared__ float c[TC_K];
+    for (int k = threadIdx.x; k < TC_K; k += blockDim.x) {
+        double acc = 0.0;
+        if (k < d_pad)
+            for (int q = 0; q < nr; ++q) acc += (double)X[(r0 + q) * d_pad + k];
+        c[k] = nr > 0 ? (float)(acc / nr) : 0.f;
+        cent[(int64_t)g * TC_K + k] = c[k];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < ASK_BLK_N; q += blockDim.x) {
+        int64_t row = r0 + q;
+        if (row >= rows_total) break;
+        bool valid = q < nr;
+        double nn = 0.0;
+        for (int k = 0; k < TC_K; ++k) {
+            float x = (valid && k < d_pad) ? X[row * d_pad + k] - c[k] : 0.f;
+            nn += (double)x * x;
+            float hi = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+            Xhi[row * TC_K + k] = hi;
+            Xlo[row * TC_K + k] = x - hi;
+            __nv_bfloat16 bh = __float2bfloat16_rn(x);
+            __nv_bfloat16 bl = __float2bfloat16_rn(x - __bfloat162float(bh));
+            Bhi[row * TC_K + k] = *reinterpret_cast<uint16_t *>(&bh);
+            Blo[row * TC_K + k] = *reinterpret_cast<uint16_t *>(&bl);
+        }
+        nrmc[row] = (float)nn;
+    }
+}
+
+askit_status build_tc_operands(askit_tree t, cudaStream_t s) {
+    const int64_t nn = t->n_nodes, M = (int64_t)1 << t->L;
+    std::vector<int32_t> lcb(M), ncb(nn, 0);
+    std::vector<int64_t> r0;
+    std::vector<int32_t> nr;
+    for (int64_t l = 0; l < M; ++l) {
+        lcb[l] = (int32_t)r0.size();
+        int64_t a = M + l, sz = t->h_size[a];
+        for (int64_t ch = 0; ch * ASK_BLK_N < sz; ++ch) {
+            r0.push_back(t->h_start[a] + ch * ASK_BLK_N);
+            nr.push_back((int32_t)std::min<int64_t>(ASK_BLK_N, sz - ch * ASK_BLK_N));
+        }
+    }
+    int64_t n_leaf_sub = (int64_t)r0.size();
+    for (int64_t a = 2; a < nn; ++a) {
+        ncb[a] = (int32_t)(r0.size() - n_leaf_sub);
+        int64_t sz = t->h_s[a];
+        for (int64_t ch = 0; ch * ASK_BLK_N < sz; ++ch) {
+            r0.push_back(t->h_spool[a] + ch * ASK_BLK_N);
+            nr.push_back((int32_t)std::min<int64_t>(ASK_BLK_N, sz - ch * ASK_BLK_N));
+        }
+    }
+    for (int64_t a = 2; a < nn; ++a) ncb[a] += (int32_t)n_leaf_sub;
+    t->n_sub = (int64_t)r0.size();
+    ASK_TRY(t->arena.alloc(&t->leaf_cbase, M));
+    ASK_TRY(t->arena.alloc(&t->node_cbase, nn));
+    ASK_CUDA(cudaMemcpyAsync(t->leaf_cbase, lcb.data(), sizeof(int32_t) * M, cudaMemcpyHostToDevice, s));
+    ASK_CUDA(cudaMemcpyAsync(t->node_cbase, ncb.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice, s));
+    if (t->d > TC_K) return ASKIT_OK;   // the tensor-core operands cover d <= TC_K
+    int64_t *d_r0 = nullptr;
+    int32_t *d_nr = nullptr;
+    ASK_CUDA(cudaMalloc(&d_r0, sizeof(int64_t) * std::max<int64_t>(1, t->n_sub)));
+    ASK_CUDA(cudaMalloc(&d_nr, sizeof(int32_t) * std::max<int64_t>(1, t->n_sub)));
+    ASK_CUDA(cudaMemcpyAsync(d_r0, r0.data(), sizeof(int64_t) * t->n_sub, cudaMemcpyHostToDevice, s));
+    ASK_CUDA(cudaMemcpyAsync(d_nr, nr.data(), sizeof(int32_t) * t->n_sub, cudaMemcpyHostToDevice, s));
+    t->srows = std::max<int64_t>(t->spool_rows, 1) + 256;
+    ASK_TRY(t->arena.alloc(&t->cent, (size_t)std::max<int64_t>(1, t->n_sub) * TC_K));
+    ASK_TRY(t->arena.alloc(&t->Xt_hi, (size_t)t->N_pad * TC_K));
+    ASK_TRY(t->arena.alloc(&t->Xt_lo, (size_t)t->N_pad * TC_K));
+    ASK_TRY(t->arena.alloc(&t->Xs_hi, (size_t)t->srows * TC_K));
+    ASK_TRY(t->arena.alloc(&t->Xs_lo, (size_t)t->srows * TC_K));
+    ASK_TRY(t->arena.alloc(&t->Xt_bhi, (size_t)t->N_pad * TC_K));
+    ASK_TRY(t->arena.alloc(&t->Xt_blo, (size_t)t->N_pad * TC_K));
+    ASK_TRY(t->arena.alloc(&t->Xs_bhi, (size_t)t->srows * TC_K));
+    ASK_TRY(t->arena.alloc(&t->Xs_blo, (size_t)t->srows * TC_K));
+    ASK_TRY(t->arena.alloc(&t->nrmc_t, t->N_pad));
+    ASK_TRY(t->arena.alloc(&t->nrmc_s, t->srows));
+    ASK_TRY(t->arena.alloc(&t->Ct, t->N_pad));
+    ASK_TRY(t->arena.alloc(&t->Cs, t->srows));
+    ASK_CUDA(cudaMemsetAsync(t->Xt_hi, 0, sizeof(float) * t->N_pad * TC_K, s));
+    ASK_CUDA(cudaMemsetAsync(t->Xt_lo, 0, sizeof(float) * t->N_pad * TC_K, s));
+    ASK_CUDA(cudaMemsetAsync(t->Xs_hi, 0, sizeof(float) * t->srows * TC_K, s));
+    ASK_CUDA(cudaMemsetAsync(t->Xs_lo, 0, sizeof(float) * t->srows * TC_K, s));
+    ASK_CUDA(cudaMemsetAsync(t->Xt_bhi, 0, sizeof(uint16_t) * t->N_pad * TC_K, s));
+    ASK_CUDA(cudaMemsetAsync(t->Xt_blo, 0, sizeof(uint16_t) * t->N_pad * TC_K, s));
+    ASK_CUDA(cudaMemsetAsync(t->Xs_bhi, 0, sizeof(uint16_t) * t->srows * TC_K, s));
+    ASK_CUDA(cudaMemsetAsync(t->Xs_blo, 0, sizeof(uint16_t) * t->srows * TC_K, s));
+    ASK_CUDA(cudaMemsetAsync(t->nrmc_t, 0, sizeof(float) * t->N_pad, s));
+    ASK_CUDA(cudaMemsetAsync(t->nrmc_s, 0, sizeof(float) * t->srows, s));
+    if (n_leaf_sub > 0)
+        tc_prep_kernel<<<(unsigned)n_leaf_sub, 128, 0, s>>>(t->Xt, t->d_pad, d_r0, d_nr, t->N_pad, t->cent, t->Xt_hi,
+                                                          t->Xt_lo, t->Xt_bhi, t->Xt_blo, t->nrmc_t);
+    if (t->n_sub > n_leaf_sub)
+        tc_prep_kernel<<<(unsigned)(t->n_sub - n_leaf_sub), 128, 0, s>>>(
+            t->Xs, t->d_pad, d_r0 + n_leaf_sub, d_nr + n_leaf_sub, t->srows, t->cent + n_leaf_sub * TC_K, t->Xs_hi,
+            t->Xs_lo, t->Xs_bhi, t->Xs_blo, t->nrmc_s);
+    ASK_LAUNCH();
+    ASK_CUDA(cudaStreamSynchronize(s));
+    cudaFree(d_r0);
+    cudaFree(d_nr);
+    return ASKIT_OK;
+}
+
+askit_status insample_prune_sets(askit_tree t, int32_t *sets, cudaStream_t s) {
+    if (!t->prm.prune) {
+        int64_t n = t->N << t->L;
+        all_leaves_sets_kernel<<<nblk(n, 256), 256, 0, s>>>(t->N, t->L, sets);
+        ASK_LAUNCH();
+        return ASKIT_OK;
+    }
+    insample_sets_kernel<<<nblk(t->N, 128), 128, 0, s>>>(t->perm, t->leafof, t->knn, t->N, t->kappa, sets);
+    ASK_LAUNCH();
+    return ASKIT_OK;
+}
+
+askit_status oos_prune_sets(askit_tree t, const int32_t *knn, int64_t T, int stride, int32_t *sets,
+                            cudaStream_t s) {
+    oos_sets_kernel<<<nblk(T, 128), 128, 0, s>>>(t->leafof, knn, T, t->kappa, stride, sets);
+    ASK_LAUNCH();
+    return ASKIT_OK;
+}
+
+// Work lists for T targets (slot order) with the given prune sets: every
+// (target, source sub-block) pair becomes an entry; entries are sorted by
+// (sub-block, target); each sub-block's entries are cut into items of up to
+// ASK_TILE_M targets.  partial[e] receives the sub-block's contribution to
+// the entry's target; reduce() then sums each target's entries in emission
+// order (Near leaves ascending, then Far nodes from the deepest level up),
+// which is fixed, so the result does not depend on scheduling.
+askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, int64_t T, WorkLists &wlst,
+                              DevArena &arena, cudaStream_t s) {
+    int64_t *cnt = nullptr, *nearc = nullptr, *farc = nullptr, *pairs = nullptr, *vals = nullptr, *emit_of = nullptr;
+    int64_t *bflag = nullptr, *bidx = nullptr, *bstart = nullptr, *iflag = nullptr, *iidx = nullptr;
+    uint64_t *keys = nullptr, *keys_s = nullptr;
+    void *tmp = nullptr;
+    size_t tb = 0, tb2 = 0;
+    askit_status rc = ASKIT_OK;
+    cudaError_t e = cudaSuccess;
+    int64_t total = 0, nb = 0, nit = 0;
+    std::vector<int64_t> h_near(T), h_far(T), h_pairs(T);
+    WorkLists &w = wlst;
+    w.T = T;
+#define WCHK(x) do { e = (x); if (e != cudaSuccess) goto fail; } while (0)
+#define WTRY(x) do { rc = (x); if (rc != ASKIT_OK) goto out; } while (0)
+    WCHK(cudaMalloc(&cnt, sizeof(int64_t) * (T + 1)));
+    WCHK(cudaMalloc(&nearc, sizeof(int64_t) * T));
+    WCHK(cudaMalloc(&farc, sizeof(int64_t) * T));
+    WCHK(cudaMalloc(&pairs, sizeof(int64_t) * T));
+    WTRY(arena.alloc(&w.off, T + 1));
+    WCHK(cudaMemsetAsync(cnt + T, 0, sizeof(int64_t), s));
+    count_kernel<<<nblk(T, 128), 128, 0, s>>>(sets, stride, T, t->L, t->nsize, t->d_s, cnt, nearc, farc, pairs);
+    WCHK(cudaGetLastError());
+    WTRY(scan_i64(nullptr, nullptr, T + 1, nullptr, &tb, s));
+    WCHK(cudaMalloc(&tmp, tb));
+    WTRY(scan_i64(cnt, w.off, T + 1, tmp, &tb, s));
+    WCHK(cudaMemcpyAsync(&total, w.off + T, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    WCHK(cudaMemcpyAsync(h_near.data(), nearc, sizeof(int64_t) * T, cudaMemcpyDeviceToHost, s));
+    WCHK(cudaMemcpyAsync(h_far.data(), farc, sizeof(int64_t) * T, cudaMemcpyDeviceToHost, s));
+    WCHK(cudaMemcpyAsync(h_pairs.data(), pairs, sizeof(int64_t) * T, cudaMemcpyDeviceToHost, s));
+    WCHK(cudaStreamSynchronize(s));
+    cudaFree(tmp);
+    tmp = nullptr;
+    w.n_entries = total;
+    WCHK(cudaMalloc(&keys, sizeof(uint64_t) * total));
+    WCHK(cudaMalloc(&keys_s, sizeof(uint64_t) * total));
+    WCHK(cudaMalloc(&vals, sizeof(int64_t) * total));
+    WCHK(cudaMalloc(&emit_of, sizeof(int64_t) * total));
+    emit_kernel<<<nblk(T, 128), 128, 0, s>>>(sets, stride, T, t->L, t->nsize, t->d_s, w.off, keys, vals);
+    WCHK(cudaGetLastError());
+    WTRY(sort_u64_i64(nullptr, nullptr, nullptr, nullptr, total, nullptr, &tb, s));
+    WTRY(scan_i64(nullptr, nullptr, total, nullptr, &tb2, s));
+    tb = std::max(tb, tb2);
+    WCHK(cudaMalloc(&tmp, tb));
+    WTRY(sort_u64_i64(keys, keys_s, vals, emit_of, total, tmp, &tb, s));
+    WTRY(arena.alloc(&w.slot_of_emit, total));
+    WTRY(arena.alloc(&w.tgt, total));
+    WCHK(cudaMalloc(&bflag, sizeof(int64_t) * total));
+    WCHK(cudaMalloc(&bidx, sizeof(int64_t) * total));
+    WCHK(cudaMalloc(&iflag, sizeof(int64_t) * total));
+    WCHK(cudaMalloc(&iidx, sizeof(int64_t) * total));
+    scatter_kernel<<<nblk(total, 256), 256, 0, s>>>(keys_s, emit_of, total, w.slot_of_emit, w.tgt, bflag);
+    WCHK(cudaGetLastError());
+    WTRY(scan_i64(bflag, bidx, total, tmp, &tb, s));
+    {
+        int64_t lastb = 0, lastf = 0;
+        WCHK(cudaMemcpyAsync(&lastb, bidx + total - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        WCHK(cudaMemcpyAsync(&lastf, bflag + total - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        WCHK(cudaStreamSynchronize(s));
+        nb = lastb + lastf;
+    }
+    WCHK(cudaMalloc(&bstart, sizeof(int64_t) * nb));
+    block_start_kernel<<<nblk(total, 256), 256, 0, s>>>(bflag, bidx, total, bstart);
+    item_flag_kernel<<<nblk(total, 256), 256, 0, s>>>(bflag, bidx, bstart, total, iflag);
+    WCHK(cudaGetLastError());
+    WTRY(scan_i64(iflag, iidx, total, tmp, &tb, s));
+    {
+        int64_t lasti = 0, lastf = 0;
+        WCHK(cudaMemcpyAsync(&lasti, iidx + total - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        WCHK(cudaMemcpyAsync(&lastf, iflag + total - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        WCHK(cudaStreamSynchronize(s));
+        nit = lasti + lastf;
+    }
+    WTRY(arena.alloc(&w.items, nit));
+    WTRY(arena.alloc(&w.block_off, nb + 1));
+    build_items_kernel<<<nblk(total, 256), 256, 0, s>>>(keys_s, bflag, bidx, iflag, iidx, total, nb, bstart, t->nstart,
+                                                        t->nsize, t->d_spool, t->d_s, t->leaf_cbase, t->node_cbase,
+                                                        (int64_t)1 << t->L, w.items, w.block_off);
+    WCHK(cudaGetLastError());
+    {
+        std::vector<EvalItem> hi(nit);
+        std::vector<int32_t> boff(nb + 1);
+        WCHK(cudaMemcpyAsync(hi.data(), w.items, sizeof(EvalItem) * nit, cudaMemcpyDeviceToHost, s));
+        WCHK(cudaMemcpyAsync(boff.data(), w.block_off, sizeof(int32_t) * (nb + 1), cudaMemcpyDeviceToHost, s));
+        WCHK(cudaStreamSynchronize(s));
+        std::vector<int64_t> cost(nb, 0);
+        int64_t pc = 0;
+        for (int64_t b = 0; b < nb; ++b)
+            for (int32_t it = boff[b]; it < boff[b + 1]; ++it) {
+                cost[b] += ASK_TILE_M * ASK_BLK_N;
+                pc += (int64_t)ASK_TILE_M * ASK_BLK_N;
+            }
+        std::vector<int32_t> order(nb);
+        for (int64_t b = 0; b < nb; ++b) order[b] = (int32_t)b;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
+        WTRY(arena.alloc(&w.block_order, nb));
+        WCHK(cudaMemcpyAsync(w.block_order, order.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
+        WCHK(cudaStreamSynchronize(s));
+        int64_t sn = 0, sf = 0, pa = 0;
+        for (int64_t q = 0; q < T; ++q) { sn += h_near[q]; sf += h_far[q]; pa += h_pairs[q]; }
+        w.n_items = nit;
+        w.n_blocks = nb;
+        w.pairs_alg = pa;
+        w.pairs_cmp = pc;
+        w.near_tot = sn;
+        w.far_tot = sf;
+    }
+    goto out;
+fail:
+    askit_set_error("work lists: %s", cudaGetErrorString(e));
+    rc = e == cudaErrorMemoryAllocation ? ASKIT_ERR_OOM : ASKIT_ERR_CUDA;
+out:
+#undef WCHK
+#undef WTRY
+    cudaStreamSynchronize(s);
+    cudaFree(cnt); cudaFree(nearc); cudaFree(farc); cudaFree(pairs); cudaFree(vals); cudaFree(emit_of);
+    cudaFree(bflag); cudaFree(bidx); cudaFree(bstart); cudaFree(iflag); cudaFree(iidx);
+    cudaFree(keys); cudaFree(keys_s); cudaFree(tmp);
+    return rc;
+}
+
+askit_status reduce_partials(const WorkLists &w, const float *partial, int r, const int32_t *out_rows, float *U,
+                             int64_t ldu, cudaStream_t s) {
+    if (w.T == 0) return ASKIT_OK;
+    reduce_partials_kernel<<<nblk(w.T * r, 256), 256, 0, s>>>(partial, w.off, w.slot_of_emit, w.T, r, out_rows, U, ldu);
+    ASK_LAUNCH();
+    return ASKIT_OK;
+}

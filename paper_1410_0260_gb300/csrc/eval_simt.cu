@@ -1,0 +1,113 @@
+// Evaluate (Algorithm 4) on CUDA cores in plain FP32: the reference
+// precision the split tensor-core paths are measured against.
+//
+// One block per source sub-block (a leaf's points, evaluated directly, or a
+// node's skeleton, Algorithm 4 lines 1-2), looping over the sub-block's
+// items; thread t of an item owns one target and adds
+//     sum_j exp(-c ||x - y_j||^2 / h_j^2) w_j
+// over the sub-block's rows, with the distance in difference form (no
+// cancellation) and the exponent on exp2f.  The sum is the entry's partial.
+#include "askit_impl.cuh"
+
+namespace {
+
+constexpr int CH = 32;    // source rows per staged chunk
+constexpr int DK = 64;    // coordinates per staged slice
+
+template <int RMAX>
+__global__ void __launch_bounds__(ASK_TILE_M) eval_simt_kernel(
+    const float *__restrict__ Xq, int64_t ldq, const EvalItem *__restrict__ items,
+    const int32_t *__restrict__ block_off, const int32_t *__restrict__ block_order,
+    const int32_t *__restrict__ tgt, float *__restrict__ partial, const float *__restrict__ Xt,
+    const float *__restrict__ Xs, const float *__restrict__ sc_t, const float *__restrict__ sc_s,
+    const float *__restrict__ Wt, const float *__restrict__ Ws, int d_pad, int r) {
+    __shared__ float ys[CH][DK + 1];
+    __shared__ float ysc[CH];
+    __shared__ float yw[CH][RMAX];
+    const int b = block_order[blockIdx.x];
+    const int tid = threadIdx.x;
+    for (int it = block_off[b]; it < block_off[b + 1]; ++it) {
+        const EvalItem item = items[it];
+        const bool far = item.nrows < 0;
+        const int nrows = item.nrows & 0x7fffffff;
+        const bool mine = tid < item.cnt;
+        const float *xrow = Xq + (mine ? (int64_t)tgt[item.e0 + tid] : 0) * ldq;
+        const float *Y = far ? Xs : Xt;
+        const float *SC = far ? sc_s : sc_t;
+        const float *WW = far ? Ws : Wt;
+        float acc[RMAX];
+#pragma unroll
+        for (int z = 0; z < RMAX; ++z) acc[z] = 0.f;
+        float xr[DK];
+        for (int j0 = 0; j0 < nrows; j0 += CH) {
+            const int nj = min(CH, nrows - j0);
+            float D[CH];
+#pragma unroll
+            for (int j = 0; j < CH; ++j) D[j] = 0.f;
+            for (int k0 = 0; k0 < d_pad; k0 += DK) {
+                __syncthreads();
+                for (int e = tid; e < CH * DK; e += ASK_TILE_M) {
+                    int j = e / DK, k = e % DK;
+                    ys[j][k] = (j < nj && k0 + k < d_pad) ? Y[(int64_t)(item.row0 + j0 + j) * d_pad + k0 + k] : 0.f;
+                }
+                if (k0 == 0) {
+                    for (int e = tid; e < CH; e += ASK_TILE_M) ysc[e] = e < nj ? SC[item.row0 + j0 + e] : 0.f;
+                    for (int e = tid; e < CH * RMAX; e += ASK_TILE_M) {
+                        int j = e / RMAX, z = e % RMAX;
+                        yw[j][z] = (j < nj && z < r) ? WW[(int64_t)(item.row0 + j0 + j) * r + z] : 0.f;
+                    }
+                }
+                __syncthreads();
+                if (mine) {
+#pragma unroll
+                    for (int k = 0; k < DK; ++k) xr[k] = k0 + k < d_pad ? xrow[k0 + k] : 0.f;
+#pragma unroll
+                    for (int j = 0; j < CH; ++j) {
+                        float a = 0.f;
+#pragma unroll
+                        for (int k = 0; k < DK; ++k) {
+                            float t = xr[k] - ys[j][k];
+                            a = fmaf(t, t, a);
+                        }
+                        D[j] += a;
+                    }
+                }
+            }
+            if (mine) {
+#pragma unroll
+                for (int j = 0; j < CH; ++j) {
+                    if (j < nj) {
+                        float kv = exp2f(-ysc[j] * D[j]);
+#pragma unroll
+                        for (int z = 0; z < RMAX; ++z) acc[z] = fmaf(kv, yw[j][z], acc[z]);
+                    }
+                }
+            }
+        }
+        if (mine) {
+            float *p = partial + (int64_t)(item.e0 + tid) * r;
+#pragma unroll
+            for (int z = 0; z < RMAX; ++z)
+                if (z < r) p[z] = acc[z];
+        }
+    }
+}
+
+}  // namespace
+
+askit_status eval_simt(askit_tree t, const float *Xq, int64_t ldq, const WorkLists &w, float *partial,
+                       cudaStream_t s) {
+    if (w.n_blocks == 0) return ASKIT_OK;
+    int r = t->r;
+#define LAUNCH(R)                                                                                   \
+    eval_simt_kernel<R><<<(unsigned)w.n_blocks, ASK_TILE_M, 0, s>>>(                                \
+        Xq, ldq, w.items, w.block_off, w.block_order, w.tgt, partial, t->Xt, t->Xs, t->sc_t,        \
+        t->sc_s, t->Wt, t->Ws, t->d_pad, r)
+    if (r <= 1) LAUNCH(1);
+    else if (r <= 4) LAUNCH(4);
+    else if (r <= 16) LAUNCH(16);
+    else LAUNCH(64);
+#undef LAUNCH
+    ASK_LAUNCH();
+    return ASKIT_OK;
+}

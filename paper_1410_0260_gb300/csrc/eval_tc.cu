@@ -1,0 +1,529 @@
+// Evaluate (Algorithm 4) on the tcgen05 tensor cores.
+//
+// Work item = one source sub-block (<= 128 rows of a leaf's points for the
+// direct near field, or of a node's skeleton for the far field) against up
+// to 128 targets that all need it (see eval_lists.cu).  For each item
+//
+//     G = X' Y'^T           (tcgen05.mma, 128 x 128 x 64, FP32 accumulators in TMEM)
+//     r^2 = |x'|^2 + |y'|^2 - 2 G
+//     partial_t = sum_j exp2(-c log2(e) r^2 / h_j^2) w_j
+//
+// where x' = x - c_b and y' = y - c_b are centered on the sub-block's mean
+// c_b, which keeps the norm expansion's cancellation error at the scale of
+// the sub-block instead of the data set.  The contraction is split in three
+// products (hi*hi + hi*lo + lo*hi) of TF32 or BF16 parts with FP32
+// accumulation.
+//
+// One CTA per SM, warp-specialized, 288 threads:
+//   warps 0-3  loaders: gather the item's target rows (coalesced 16-byte
+//              loads), center and split them, and store them in the
+//              128-byte-swizzled K-major layout the tensor core reads (two
+//              shared-memory stages);
+//   warps 4-7  epilogue: tcgen05.ld of their 32 TMEM lanes (one row each),
+//              exponent on MUFU.EX2, reduction against the weights;
+//   warp 8     one thread issues the TMA loads of the sub-block (centered,
+//              pre-split rows) and the tcgen05.mma instructions, and commits
+//              them to mbarriers.
+// Two TMEM accumulators (2 x 128 columns) let the MMAs of item i+1 run
+// while the epilogue drains item i.  Every mbarrier wait is bounded: on
+// timeout the kernel records ASK_DEV_TIMEOUT, all roles leave their loops,
+// and TMEM is freed before the kernel returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "askit_impl.cuh"
+
+namespace {
+
+constexpr int TC_THREADS = 288;
+constexpr int TILE_ROWS = 128;                  // M = N = 128
+constexpr int REGION = TILE_ROWS * 128;         // one 128-row x 128-byte swizzled region (16 KB)
+constexpr uint32_t TMEM_COLS = 256;             // two 128-column FP32 accumulators
+constexpr int SPIN_LIMIT = 1 << 26;
+
+// Precision traits: element bytes, swizzle regions per operand (TC_K
+// elements x element bytes / 128), MMA K steps, tcgen05 operand format.
+template <int P> struct Prec;
+template <> struct Prec<ASKIT_PREC_TF32X3> {
+    static constexpr int EB = 4, NREG = 2, KSTEPS = 8;   // K = 8 per MMA
+    static constexpr uint32_t FMT = 2;                   // TF32 in .kind::tf32
+};
+template <> struct Prec<ASKIT_PREC_BF16X3> {
+    static constexpr int EB = 2, NREG = 1, KSTEPS = 4;   // K = 16 per MMA
+    static constexpr uint32_t FMT = 1;                   // BF16 in .kind::f16
+};
+
+// Instruction descriptor of .kind::tf32 / .kind::f16: D = F32 (bits 4-5),
+// A and B format (bits 7-9, 10-12), both K-major, N >> 3 (bits 17-22),
+// M >> 4 (bits 24-28).
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, int M, int N) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Shared-memory matrix descriptor for a K-major operand in the 128-byte
+// swizzle: start address >> 4, leading-byte offset (unused for this layout,
+// 1), stride-byte offset 1024 B between 8-row core-matrix groups, the
+// descriptor version bit 46, swizzle mode 2 (128 B) in bits 61-63.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on the phase of the given parity.  Returns false when the
+// kernel is aborting (another role timed out) or this wait timed out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *status) {
+    for (int it = 0; it < SPIN_LIMIT; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 1023) == 1023 && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    atomicExch(status, ASK_DEV_TIMEOUT);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+template <int P>
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+    if constexpr (P == ASKIT_PREC_TF32X3) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+    }
+}
+
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes (one row per thread).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Shared-memory plan (offsets from a 1024-byte aligned base).
+template <int P>
+struct Smem {
+    static constexpr int OPB = Prec<P>::NREG * REGION;    // one operand (hi or lo) of one tile
+    static constexpr int B_HI = 0, B_LO = OPB;
+    static constexpr int A0 = 2 * OPB;                     // stage s: hi at A0 + s*2*OPB, lo at + OPB
+    static constexpr int TILES = 6 * OPB;
+    static constexpr int ANORM = TILES;                    // float [2][128] centered target norms
+    static constexpr int RC_MAX = 16;
+    static constexpr int BAR = ANORM + 2 * 128 * 4;        // 10 mbarriers
+    static constexpr int MISC = BAR + 10 * 8;              // tmem address, abort flag
+    static constexpr int BYTES = MISC + 16;
+};
+
+struct TcArgs {
+    const EvalItem *items;
+    const int32_t *block_off, *block_order;
+    int64_t n_blocks;
+    const int32_t *tgt;       // entry -> target slot
+    const float *Xq;          // target coordinates [*, ldq]
+    int64_t ldq;
+    int d_pad;
+    const float *cent;        // [n_sub, TC_K]
+    const float4 *Ct, *Cs;    // per source row {c log2(e) / h^2, -(that) |y'|^2, w_0, 0}
+    const float *Wt, *Ws;
+    int r;
+    float *partial;
+    int *status;
+};
+
+template <int P, int RC>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_constant__ CUtensorMap map_t_lo,
+               const __grid_constant__ CUtensorMap map_s_hi, const __grid_constant__ CUtensorMap map_s_lo,
+               const TcArgs args) {
+    using S = Smem<P>;
+    constexpr int EB = Prec<P>::EB, NREG = Prec<P>::NREG, KSTEPS = Prec<P>::KSTEPS;
+    constexpr uint32_t IDESC = make_idesc(Prec<P>::FMT, TILE_ROWS, TILE_ROWS);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(sm);
+    float *a_norm = reinterpret_cast<float *>(sm + S::ANORM);
+    const uint32_t bar0 = sbase + S::BAR;
+    auto BAR_A_FULL = [&](int s) { return bar0 + 8 * s; };
+    auto BAR_A_EMPTY = [&](int s) { return bar0 + 8 * (2 + s); };
+    const uint32_t BAR_B_FULL = bar0 + 8 * 4, BAR_B_EMPTY = bar0 + 8 * 5;
+    auto BAR_T_FULL = [&](int a) { return bar0 + 8 * (6 + a); };
+    auto BAR_T_EMPTY = [&](int a) { return bar0 + 8 * (8 + a); };
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + S::MISC);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + S::MISC + 4);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        mbar_init(BAR_A_FULL(0), 128);
+        mbar_init(BAR_A_FULL(1), 128);
+        mbar_init(BAR_A_EMPTY(0), 1);
+        mbar_init(BAR_A_EMPTY(1), 1);
+        mbar_init(BAR_B_FULL, 1);
+        mbar_init(BAR_B_EMPTY, 1);
+        mbar_init(BAR_T_FULL(0), 1);
+        mbar_init(BAR_T_FULL(1), 1);
+        mbar_init(BAR_T_EMPTY(0), 128);
+        mbar_init(BAR_T_EMPTY(1), 128);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp < 4) {
+        // ------------------------------------------------------------ loaders
+        constexpr int CPR = TC_K / 4;            // 16-byte source chunks (4 floats) per row
+        constexpr int RPP = 32 / CPR;            // rows per warp pass
+        const int c4 = lane % CPR;               // this lane's 4 columns: 4*c4 .. 4*c4+3
+        const int rsub = lane / CPR;
+        int li = 0;
+        for (int64_t bi = blockIdx.x; bi < args.n_blocks && !*abort_flag; bi += gridDim.x) {
+            const int b = args.block_order[bi];
+            for (int it = args.block_off[b]; it < args.block_off[b + 1]; ++it, ++li) {
+                const int s = li & 1;
+                const uint32_t par = ((li >> 1) & 1) ^ 1;
+                if (!mbar_wait(BAR_A_EMPTY(s), par, abort_flag, args.status)) goto loader_done;
+                if (!mbar_wait(BAR_T_EMPTY(s), par, abort_flag, args.status)) goto loader_done;
+                const EvalItem item = args.items[it];
+                const float4 cen = *reinterpret_cast<const float4 *>(args.cent + (int64_t)item.cidx * TC_K + 4 * c4);
+                uint8_t *ahi = sm + S::A0 + s * 2 * S::OPB;
+                uint8_t *alo = ahi + S::OPB;
+#pragma unroll 4
+                for (int pass = 0; pass < 32 / RPP; ++pass) {
+                    const int row = warp * 32 + pass * RPP + rsub;
+                    const bool valid = row < item.cnt && 4 * c4 < args.d_pad;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (valid) {
+                        const int64_t slot = args.tgt[item.e0 + row];
+                        v = __ldg(reinterpret_cast<const float4 *>(args.Xq + slot * args.ldq + 4 * c4));
+                        v.x -= cen.x; v.y -= cen.y; v.z -= cen.z; v.w -= cen.w;
+                    }
+                    float nn = v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
+#pragma unroll
+                    for (int o = CPR / 2; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+                    if (c4 == 0) a_norm[s * 128 + row] = nn;
+                    if constexpr (P == ASKIT_PREC_TF32X3) {
+                        float4 hi, lo;
+                        hi.x = __uint_as_float(__float_as_uint(v.x) & 0xffffe000u);
+                        hi.y = __uint_as_float(__float_as_uint(v.y) & 0xffffe000u);
+                        hi.z = __uint_as_float(__float_as_uint(v.z) & 0xffffe000u);
+                        hi.w = __uint_as_float(__float_as_uint(v.w) & 0xffffe000u);
+                        lo.x = v.x - hi.x; lo.y = v.y - hi.y; lo.z = v.z - hi.z; lo.w = v.w - hi.w;
+                        const int reg = c4 >> 3, chunk = c4 & 7;
+                        const int off = reg * REGION + row * 128 + ((chunk ^ (row & 7)) << 4);
+                        *reinterpret_cast<float4 *>(ahi + off) = hi;
+                        *reinterpret_cast<float4 *>(alo + off) = lo;
+                    } else {
+                        __nv_bfloat16 h0 = __float2bfloat16_rn(v.x), h1 = __float2bfloat16_rn(v.y);
+                        __nv_bfloat16 h2 = __float2bfloat16_rn(v.z), h3 = __float2bfloat16_rn(v.w);
+                        __nv_bfloat16 l0 = __float2bfloat16_rn(v.x - __bfloat162float(h0));
+                        __nv_bfloat16 l1 = __float2bfloat16_rn(v.y - __bfloat162float(h1));
+                        __nv_bfloat16 l2 = __float2bfloat16_rn(v.z - __bfloat162float(h2));
+                        __nv_bfloat16 l3 = __float2bfloat16_rn(v.w - __bfloat162float(h3));
+                        uint2 hv, lv;
+                        hv.x = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                        hv.y = (uint32_t)__bfloat16_as_ushort(h2) | ((uint32_t)__bfloat16_as_ushort(h3) << 16);
+                        lv.x = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                        lv.y = (uint32_t)__bfloat16_as_ushort(l2) | ((uint32_t)__bfloat16_as_ushort(l3) << 16);
+                        const int off = row * 128 + (((c4 >> 1) ^ (row & 7)) << 4) + (c4 & 1) * 8;
+                        *reinterpret_cast<uint2 *>(ahi + off) = hv;
+                        *reinterpret_cast<uint2 *>(alo + off) = lv;
+                    }
+                }
+                // generic-proxy stores -> visible to the tensor core's async proxy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(BAR_A_FULL(s));
+            }
+        }
+    loader_done:;
+    } else if (warp < 8) {
+        // ----------------------------------------------------------- epilogue
+        const int row = tid - 128;                 // TMEM lane = target row of the item
+        const int q = warp & 3;                    // this warp's TMEM lane quadrant
+        int li = 0;
+        for (int64_t bi = blockIdx.x; bi < args.n_blocks && !*abort_flag; bi += gridDim.x) {
+            const int b = args.block_order[bi];
+            for (int it = args.block_off[b]; it < args.block_off[b + 1]; ++it, ++li) {
+                const int a = li & 1;
+                const uint32_t par = (li >> 1) & 1;
+                const EvalItem item = args.items[it];
+                const bool far = item.nrows < 0;
+                const int nrows = item.nrows & 0x7fffffff;
+                // per source row: {c log2(e) / h^2, -(that) |y'|^2, w_0, 0}
+                const float4 *cp = (far ? args.Cs : args.Ct) + item.row0;
+                const float *wp = (far ? args.Ws : args.Wt) + (int64_t)item.row0 * args.r;
+                if (!mbar_wait(BAR_A_FULL(a), par, abort_flag, args.status)) goto epi_done;
+                if (!mbar_wait(BAR_T_FULL(a), par, abort_flag, args.status)) goto epi_done;
+                tc_fence_after();
+                float acc[RC];
+#pragma unroll
+                for (int z = 0; z < RC; ++z) acc[z] = 0.f;
+                if (q * 32 < item.cnt) {   // warp-uniform: skip quadrants with no target
+                    const float nt = a_norm[a * 128 + row];
+#pragma unroll 1
+                    for (int c = 0; c < 4 && c * 32 < nrows; ++c) {
+                        float g[32];
+                        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * 128 + c * 32), g);
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            const int j = c * 32 + jj;
+                            if (j < nrows) {   // uniform across the warp
+                                const float4 cv = __ldg(cp + j);
+                                const float g2 = fmaf(g[jj], 2.f, -nt);
+                                const float arg = fminf(fmaf(g2, cv.x, cv.y), 0.f);
+                                const float k = ex2_approx(arg);
+                                if constexpr (RC == 1) {
+                                    acc[0] = fmaf(k, cv.z, acc[0]);
+                                } else {
+#pragma unroll
+                                    for (int z = 0; z < RC; ++z)
+                                        if (z < args.r) acc[z] = fmaf(k, __ldg(wp + (int64_t)j * args.r + z), acc[z]);
+                                }
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(BAR_T_EMPTY(a));
+                if (row < item.cnt) {
+                    float *p = args.partial + (int64_t)(item.e0 + row) * args.r;
+#pragma unroll
+                    for (int z = 0; z < RC; ++z)
+                        if (z < args.r) p[z] = acc[z];
+                }
+            }
+        }
+    epi_done:;
+    } else if (lane == 0) {
+        // ------------------------------------------------- TMA + MMA issuer
+        constexpr int TX = 2 * NREG * REGION;      // hi + lo of one 128-row sub-block
+        int li = 0, lb = 0;
+        for (int64_t bi = blockIdx.x; bi < args.n_blocks && !*abort_flag; bi += gridDim.x, ++lb) {
+            const int b = args.block_order[bi];
+            const EvalItem first = args.items[args.block_off[b]];
+            const bool far = first.nrows < 0;
+            if (!mbar_wait(BAR_B_EMPTY, (lb & 1) ^ 1, abort_flag, args.status)) goto mma_done;
+            mbar_expect_tx(BAR_B_FULL, TX);
+            const CUtensorMap *mh = far ? &map_s_hi : &map_t_hi;
+            const CUtensorMap *ml = far ? &map_s_lo : &map_t_lo;
+#pragma unroll
+            for (int g = 0; g < NREG; ++g) {
+                const int x = g * (128 / EB);      // first element of swizzle region g
+                tma_load_2d(sbase + S::B_HI + g * REGION, mh, x, first.row0, BAR_B_FULL);
+                tma_load_2d(sbase + S::B_LO + g * REGION, ml, x, first.row0, BAR_B_FULL);
+            }
+            const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
+            for (int it = i0; it < i1; ++it, ++li) {
+                const int s = li & 1;
+                const uint32_t par = (li >> 1) & 1;
+                if (!mbar_wait(BAR_A_FULL(s), par, abort_flag, args.status)) goto mma_done;
+                if (it == i0 && !mbar_wait(BAR_B_FULL, lb & 1, abort_flag, args.status)) goto mma_done;
+                if (!mbar_wait(BAR_T_EMPTY(s), par ^ 1, abort_flag, args.status)) goto mma_done;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(s * 128);
+                const uint32_t a_hi = sbase + S::A0 + s * 2 * S::OPB, a_lo = a_hi + S::OPB;
+                const uint32_t b_hi = sbase + S::B_HI, b_lo = sbase + S::B_LO;
+#pragma unroll
+                for (int k = 0; k < KSTEPS; ++k) {
+                    // K step k: 32 bytes into swizzle region k / 4
+                    const uint32_t off = (uint32_t)((k >> 2) * REGION + (k & 3) * 32);
+                    tc_mma<P>(d_tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), IDESC, k > 0);
+                    tc_mma<P>(d_tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), IDESC, 1);
+                    tc_mma<P>(d_tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), IDESC, 1);
+                }
+                tc_commit(BAR_A_EMPTY(s));
+                tc_commit(BAR_T_FULL(s));
+                if (it == i1 - 1) tc_commit(BAR_B_EMPTY);
+            }
+        }
+    mma_done:;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 8) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// Tensor maps of the four source operand arrays for one precision.
+struct TcState {
+    CUtensorMap map[2][4];   // [precision: 0 tf32, 1 bf16][t_hi, t_lo, s_hi, s_lo]
+    bool ready[2] = {false, false};
+};
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+askit_status encode_map(EncodeTiledFn fn, CUtensorMap *m, void *base, int64_t rows, bool f32) {
+    const int eb = f32 ? 4 : 2;
+    cuuint64_t dims[2] = {(cuuint64_t)TC_K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)TC_K * eb};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / eb), (cuuint32_t)TILE_ROWS};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        askit_set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return ASKIT_ERR_CUDA;
+    }
+    return ASKIT_OK;
+}
+
+askit_status tc_state(askit_tree t, int pi, TcState **out) {
+    if (!t->tc) t->tc = new TcState();
+    TcState *st = (TcState *)t->tc;
+    if (!st->ready[pi]) {
+        void *fnp = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        ASK_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fnp, 12000, cudaEnableDefault, &q));
+        if (!fnp || q != cudaDriverEntryPointSuccess) {
+            askit_set_error("cuTensorMapEncodeTiled not available");
+            return ASKIT_ERR_CUDA;
+        }
+        EncodeTiledFn fn = (EncodeTiledFn)fnp;
+        bool f32 = pi == 0;
+        ASK_TRY(encode_map(fn, &st->map[pi][0], f32 ? (void *)t->Xt_hi : (void *)t->Xt_bhi, t->N_pad, f32));
+        ASK_TRY(encode_map(fn, &st->map[pi][1], f32 ? (void *)t->Xt_lo : (void *)t->Xt_blo, t->N_pad, f32));
+        ASK_TRY(encode_map(fn, &st->map[pi][2], f32 ? (void *)t->Xs_hi : (void *)t->Xs_bhi, t->srows, f32));
+        ASK_TRY(encode_map(fn, &st->map[pi][3], f32 ? (void *)t->Xs_lo : (void *)t->Xs_blo, t->srows, f32));
+        st->ready[pi] = true;
+    }
+    *out = st;
+    return ASKIT_OK;
+}
+
+template <int P, int RC>
+askit_status launch(askit_tree t, TcState *st, const TcArgs &a, cudaStream_t s) {
+    using S = Smem<P>;
+    const int pi = P == ASKIT_PREC_TF32X3 ? 0 : 1;
+    const size_t smem = S::BYTES + 1024;
+    static bool attr_set = false;
+    if (!attr_set) {
+        ASK_CUDA(cudaFuncSetAttribute(eval_tc_kernel<P, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    int dev = 0, sms = 0;
+    ASK_CUDA(cudaGetDevice(&dev));
+    ASK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned grid = (unsigned)std::min<int64_t>(a.n_blocks, sms);
+    eval_tc_kernel<P, RC><<<grid, TC_THREADS, smem, s>>>(st->map[pi][0], st->map[pi][1], st->map[pi][2],
+                                                         st->map[pi][3], a);
+    ASK_LAUNCH();
+    return ASKIT_OK;
+}
+
+}  // namespace
+
+askit_status eval_tc(askit_tree t, int precision, const float *Xq, int64_t ldq, const WorkLists &w,
+                     float *partial, cudaStream_t s) {
+    if (t->d > TC_K) {
+        askit_set_error("tensor-core evaluation covers d <= %d; use ASKIT_PREC_SIMT_FP32", TC_K);
+        return ASKIT_ERR_UNSUPPORTED;
+    }
+    if (t->r > Smem<ASKIT_PREC_TF32X3>::RC_MAX) {
+        askit_set_error("tensor-core evaluation covers r <= %d; use ASKIT_PREC_SIMT_FP32", Smem<ASKIT_PREC_TF32X3>::RC_MAX);
+        return ASKIT_ERR_UNSUPPORTED;
+    }
+    if (w.n_blocks == 0) return ASKIT_OK;
+    TcState *st = nullptr;
+    ASK_TRY(tc_state(t, precision == ASKIT_PREC_TF32X3 ? 0 : 1, &st));
+    TcArgs a;
+    a.items = w.items;
+    a.block_off = w.block_off;
+    a.block_order = w.block_order;
+    a.n_blocks = w.n_blocks;
+    a.tgt = w.tgt;
+    a.Xq = Xq;
+    a.ldq = ldq;
+    a.d_pad = t->d_pad;
+    a.cent = t->cent;
+    a.Ct = t->Ct;
+    a.Cs = t->Cs;
+    a.Wt = t->Wt;
+    a.Ws = t->Ws;
+    a.r = t->r;
+    a.partial = partial;
+    a.status = t->d_status;
+    if (precision == ASKIT_PREC_TF32X3) {
+        if (t->r == 1) return launch<ASKIT_PREC_TF32X3, 1>(t, st, a, s);
+        if (t->r <= 4) return launch<ASKIT_PREC_TF32X3, 4>(t, st, a, s);
+        return launch<ASKIT_PREC_TF32X3, 16>(t, st, a, s);
+    }
+    if (t->r == 1) return launch<ASKIT_PREC_BF16X3, 1>(t, st, a, s);
+    if (t->r <= 4) return launch<ASKIT_PREC_BF16X3, 4>(t, st, a, s);
+    return launch<ASKIT_PREC_BF16X3, 16>(t, st, a, s);
+}
+
+void eval_tc_free(askit_tree t) {
+    delete (TcState *)t->tc;
+    t->tc = nullptr;
+}

@@ -1,0 +1,469 @@
+// Tree build and nearest-neighbor search on the GPU (Section 2.2).
+//
+// Both the ASKIT tree and the random-projection (RP) trees of the kNN search
+// are built level by level: every node of a level computes its projection
+// key per point, the level's nodes are sorted segment-wise by (key, id), the
+// lower ceil(n/2) points form the left child, and each child is re-sorted by
+// id.  All leaves sit at one depth L, the least depth at which no node holds
+// more than the leaf size.  Distances and projections are FP64 sums in
+// ascending coordinate order with no fused multiply-add, so the trees and
+// neighbor lists are bit-exact functions of the input.
+#include <float.h>
+#include <limits.h>
+
+#include "askit_impl.cuh"
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ bool kv_less(double da, int ia, double db, int ib) {
+    return da < db || (da == db && ia < ib);
+}
+
+// Squared distance with an FP64 first operand (the node center).
+__device__ __forceinline__ double c_dist2_df(const double *x, const float *y, int d) {
+    double acc = 0.0;
+    for (int k = 0; k < d; ++k) {
+        double t = c_sub(x[k], (double)y[k]);
+        acc = c_add(acc, c_mul(t, t));
+    }
+    return acc;
+}
+
+// Segment (node) of each position at one tree level, by binary search over
+// the level's node starts.
+__global__ void seg_of_pos_kernel(const int32_t *lvl_start, int nseg, int64_t N, int32_t *seg) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= N) return;
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (lvl_start[mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    seg[q] = lo;
+}
+
+// Node centers: FP64 mean, points summed in the node's (ascending id) order.
+__global__ void center_kernel(const float *X, int d, const int32_t *order, const int32_t *lvl_start,
+                              const int32_t *lvl_size, double *xc) {
+    int node = blockIdx.x;
+    int k = blockIdx.y * blockDim.x + threadIdx.x;
+    if (k >= d) return;
+    int64_t b = lvl_start[node], n = lvl_size[node];
+    double acc = 0.0;
+    for (int64_t q = 0; q < n; ++q) acc = c_add(acc, (double)X[(int64_t)order[b + q] * d + k]);
+    xc[(int64_t)node * d + k] = c_div(acc, (double)n);
+}
+
+// Farthest point from a per-node reference: max D, ties to the smallest id.
+// Pass 1 raises best_bits to the largest D (non-negative doubles order like
+// their bit patterns); pass 2 lowers best_id among the points attaining it.
+template <bool FROM_CENTER>
+__global__ void far_pass1(const float *X, int d, const int32_t *order, const int32_t *seg, int64_t N,
+                          const double *xc, const int32_t *ref_id, double *Dq,
+                          unsigned long long *best_bits) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= N) return;
+    int node = seg[q];
+    const float *xj = X + (int64_t)order[q] * d;
+    double D = FROM_CENTER ? c_dist2_df(xc + (int64_t)node * d, xj, d)
+                           : c_dist2(X + (int64_t)ref_id[node] * d, xj, d);
+    Dq[q] = D;
+    atomicMax(best_bits + node, (unsigned long long)__double_as_longlong(D));
+}
+
+__global__ void far_pass2(const int32_t *order, const int32_t *seg, int64_t N, const double *Dq,
+                          const unsigned long long *best_bits, int32_t *best_id) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= N) return;
+    int node = seg[q];
+    if ((unsigned long long)__double_as_longlong(Dq[q]) == best_bits[node]) atomicMin(best_id + node, order[q]);
+}
+
+// Projection on the line (x_l, x_r) with origin x_l.
+__global__ void proj_line_kernel(const float *X, int d, const int32_t *order, const int32_t *seg,
+                                 int64_t N, const int32_t *xl, const int32_t *xr, double *p) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= N) return;
+    int node = seg[q];
+    const float *xj = X + (int64_t)order[q] * d;
+    const float *a = X + (int64_t)xl[node] * d;
+    const float *b = X + (int64_t)xr[node] * d;
+    double acc = 0.0;
+    for (int k = 0; k < d; ++k) {
+        double u = c_sub((double)xj[k], (double)a[k]);
+        double v = c_sub((double)b[k], (double)a[k]);
+        acc = c_add(acc, c_mul(u, v));
+    }
+    p[q] = acc;
+}
+
+// Projection on a Rademacher direction: bit k%64 of Philox word k/64 keyed
+// (seed, iter + 1) with counter (node, word/4) set means -1.
+__global__ void proj_rp_kernel(const float *X, int d, const int32_t *order, const int32_t *seg,
+                               int64_t N, int64_t node0, uint64_t seed, int iter, double *p) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= N) return;
+    int64_t node = node0 + seg[q];
+    const float *xj = X + (int64_t)order[q] * d;
+    double acc = 0.0;
+    uint64_t w = 0;
+    for (int k = 0; k < d; ++k) {
+        if ((k & 63) == 0) w = philox_word(seed, (uint64_t)iter + 1, (uint64_t)node, (uint64_t)(k >> 6));
+        double v = ((w >> (k & 63)) & 1) ? -1.0 : 1.0;
+        acc = c_add(acc, c_mul(v, (double)xj[k]));
+    }
+    p[q] = acc;
+}
+
+__global__ void iota_kernel(int32_t *a, int64_t n) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < n) a[q] = (int32_t)q;
+}
+
+template <class T>
+__global__ void fill_kernel(T *a, int64_t n, T v) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < n) a[q] = v;
+}
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// Warp-level best-32 list: lane l holds the l-th smallest (D, id) so far.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void warp_sort32(double &d, int &i, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            double od = __shfl_xor_sync(FULL, d, j);
+            int oi = __shfl_xor_sync(FULL, i, j);
+            bool keep_min = (((lane & j) == 0) == ((lane & k) == 0));
+            bool sw = keep_min ? kv_less(od, oi, d, i) : kv_less(d, i, od, oi);
+            if (sw) { d = od; i = oi; }
+        }
+    }
+}
+
+// Merge sorted candidates (cd, ci) into the sorted list (ld, li), keeping the
+// 32 smallest: half-cleaner against the reversed candidates, then a bitonic merge.
+__device__ __forceinline__ void warp_merge32(double &ld, int &li, double cd, int ci, int lane) {
+    double rd = __shfl_sync(FULL, cd, 31 - lane);
+    int ri = __shfl_sync(FULL, ci, 31 - lane);
+    if (kv_less(rd, ri, ld, li)) { ld = rd; li = ri; }
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) {
+        double od = __shfl_xor_sync(FULL, ld, j);
+        int oi = __shfl_xor_sync(FULL, li, j);
+        bool lower = (lane & j) == 0;
+        bool sw = lower ? kv_less(od, oi, ld, li) : kv_less(ld, li, od, oi);
+        if (sw) { ld = od; li = oi; }
+    }
+}
+
+// Offer one batch of candidates (one per lane) to the list.  `dedup` drops
+// candidates whose id is already listed (RP iterations revisit pairs).
+__device__ __forceinline__ void warp_offer(double &ld, int &li, double cd, int ci, int kappa,
+                                           bool dedup, int lane) {
+    double wd = __shfl_sync(FULL, ld, kappa - 1);
+    int wi = __shfl_sync(FULL, li, kappa - 1);
+    bool useful = kv_less(cd, ci, wd, wi);
+    if (!__ballot_sync(FULL, useful)) return;
+    if (dedup) {
+        bool dup = false;
+#pragma unroll 8
+        for (int l = 0; l < 32; ++l) dup |= (__shfl_sync(FULL, li, l) == ci);
+        if (dup) useful = false;
+    }
+    if (!useful) { cd = DBL_MAX; ci = INT_MAX; }
+    warp_sort32(cd, ci, lane);
+    warp_merge32(ld, li, cd, ci, lane);
+}
+
+// Exhaustive search of a candidate range for a set of queries; one warp per
+// query.  Candidates are rows cand[c0 .. c1) of X (ids), queries are ids
+// (self excluded) or rows of Y (qid < 0 marks out-of-sample).
+// The list of each query lives in (bd, bi)[q * 32 + lane].
+__global__ void knn_block_kernel(const float *X, int d, const int32_t *cand, const int32_t *cbeg,
+                                 const int32_t *cend, const int32_t *qids, const float *Y,
+                                 int64_t nq_total, const int32_t *qbeg, const int32_t *qend,
+                                 double *bd, int *bi, int kappa, bool dedup) {
+    extern __shared__ float sq[];   // one query row per warp
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int seg = blockIdx.x;
+    int64_t c0 = cbeg[seg], c1 = cend[seg];
+    float *myq = sq + (int64_t)warp * d;
+    for (int64_t q = qbeg[seg] + warp; q < qend[seg]; q += nw) {
+        int self = qids ? qids[q] : -1;
+        const float *xq = qids ? X + (int64_t)self * d : Y + q * d;
+        for (int k = lane; k < d; k += 32) myq[k] = xq[k];
+        __syncwarp();
+        int64_t slot = (qids ? (int64_t)self : q) * 32 + lane;
+        double ld = bd[slot];
+        int li = bi[slot];
+        for (int64_t cb = c0; cb < c1; cb += 32) {
+            double cd = DBL_MAX;
+            int ci = INT_MAX;
+            if (cb + lane < c1) {
+                int j = cand ? cand[cb + lane] : (int)(cb + lane);
+                if (j != self) {
+                    const float *xj = X + (int64_t)j * d;
+                    double acc = 0.0;
+                    for (int k = 0; k < d; ++k) {
+                        double t = c_sub((double)myq[k], (double)xj[k]);
+                        acc = c_add(acc, c_mul(t, t));
+                    }
+                    cd = acc;
+                    ci = j;
+                }
+            }
+            warp_offer(ld, li, cd, ci, kappa, dedup, lane);
+        }
+        bd[slot] = ld;
+        bi[slot] = li;
+        __syncwarp();
+    }
+}
+
+__global__ void knn_extract_kernel(const double *bd, const int *bi, int64_t Q, int kappa,
+                                   int32_t *ids, double *dist) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= Q * kappa) return;
+    int64_t q = t / kappa;
+    int z = (int)(t % kappa);
+    ids[t] = bi[q * 32 + z];
+    dist[t] = bd[q * 32 + z];
+}
+
+__global__ void knn_dist_kernel(const float *X, int64_t N, int d, int kappa, const int32_t *ids,
+                                double *dist) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= N * kappa) return;
+    int64_t i = t / kappa;
+    dist[t] = c_dist2(X + i * d, X + (int64_t)ids[t] * d, d);
+}
+
+// Scratch shared by one tree build.
+struct TreeScratch {
+    int32_t *seg = nullptr, *tmp_ids = nullptr, *bid = nullptr, *xl = nullptr;
+    double *keys = nullptr, *keys_out = nullptr, *xc = nullptr, *Dq = nullptr;
+    unsigned long long *bbits = nullptr;
+    int32_t *lvl_start = nullptr, *lvl_end = nullptr, *lvl_size = nullptr;
+    void *cub = nullptr;
+    size_t cub_bytes = 0;
+};
+
+void free_scratch(TreeScratch &s) {
+    cudaFree(s.seg); cudaFree(s.tmp_ids); cudaFree(s.bid); cudaFree(s.xl); cudaFree(s.keys);
+    cudaFree(s.keys_out); cudaFree(s.xc); cudaFree(s.Dq); cudaFree(s.bbits); cudaFree(s.lvl_start);
+    cudaFree(s.lvl_end); cudaFree(s.lvl_size); cudaFree(s.cub);
+}
+
+}  // namespace
+
+int tree_depth(int64_t N, int64_t leaf) {
+    int L = 0;
+    while (((N + ((int64_t)1 << L) - 1) >> L) > leaf) ++L;
+    return L;
+}
+
+void tree_ranges(int64_t N, int L, std::vector<int64_t> &start, std::vector<int64_t> &size) {
+    int64_t nn = (int64_t)2 << L;
+    start.assign(nn, 0);
+    size.assign(nn, 0);
+    size[1] = N;
+    for (int64_t a = 1; a < ((int64_t)1 << L); ++a) {
+        start[2 * a] = start[a];
+        size[2 * a] = (size[a] + 1) / 2;
+        start[2 * a + 1] = start[a] + (size[a] + 1) / 2;
+        size[2 * a + 1] = size[a] / 2;
+    }
+}
+
+// kind 0: ASKIT split (center, two farthest-point scans, line projection);
+// kind 1: RP split (Rademacher direction of (seed, iter, node)).
+askit_status build_tree_gpu(const float *X, int64_t N, int d, int L, int kind, uint64_t seed,
+                            int iter, int32_t *order, cudaStream_t s) {
+    std::vector<int64_t> st, sz;
+    tree_ranges(N, L, st, sz);
+    int64_t nn = (int64_t)2 << L;
+    std::vector<int32_t> hs(nn), he(nn), hz(nn);
+    for (int64_t a = 0; a < nn; ++a) {
+        hs[a] = (int32_t)st[a];
+        he[a] = (int32_t)(st[a] + sz[a]);
+        hz[a] = (int32_t)sz[a];
+    }
+    TreeScratch sc;
+    askit_status rc = ASKIT_OK;
+    auto fail = [&](cudaError_t e, const char *what) {
+        askit_set_error("tree build: %s: %s", what, cudaGetErrorString(e));
+        rc = e == cudaErrorMemoryAllocation ? ASKIT_ERR_OOM : ASKIT_ERR_CUDA;
+    };
+#define TCHK(x, what) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { fail(e_, what); goto done; } } while (0)
+    {
+        int64_t half = (int64_t)1 << (L > 0 ? L - 1 : 0);
+        TCHK(cudaMalloc(&sc.seg, sizeof(int32_t) * N), "alloc");
+        TCHK(cudaMalloc(&sc.tmp_ids, sizeof(int32_t) * N), "alloc");
+        TCHK(cudaMalloc(&sc.keys, sizeof(double) * N), "alloc");
+        TCHK(cudaMalloc(&sc.keys_out, sizeof(double) * N), "alloc");
+        TCHK(cudaMalloc(&sc.Dq, sizeof(double) * N), "alloc");
+        TCHK(cudaMalloc(&sc.bid, sizeof(int32_t) * half), "alloc");
+        TCHK(cudaMalloc(&sc.xl, sizeof(int32_t) * half), "alloc");
+        TCHK(cudaMalloc(&sc.bbits, sizeof(unsigned long long) * half), "alloc");
+        TCHK(cudaMalloc(&sc.xc, sizeof(double) * half * d), "alloc");
+        TCHK(cudaMalloc(&sc.lvl_start, sizeof(int32_t) * nn), "alloc");
+        TCHK(cudaMalloc(&sc.lvl_end, sizeof(int32_t) * nn), "alloc");
+        TCHK(cudaMalloc(&sc.lvl_size, sizeof(int32_t) * nn), "alloc");
+        TCHK(cudaMemcpyAsync(sc.lvl_start, hs.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice, s), "copy");
+        TCHK(cudaMemcpyAsync(sc.lvl_end, he.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice, s), "copy");
+        TCHK(cudaMemcpyAsync(sc.lvl_size, hz.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice, s), "copy");
+        // scratch for the largest segmented sort (all N keys, up to 2^L segments)
+        size_t b1 = 0, b2 = 0;
+        if ((rc = seg_sort_f64_i32(nullptr, nullptr, nullptr, nullptr, N, (int)half, nullptr, nullptr, nullptr, &b1, s)) != ASKIT_OK) goto done;
+        if ((rc = seg_sort_i32(nullptr, nullptr, N, (int)(2 * half), nullptr, nullptr, nullptr, &b2, s)) != ASKIT_OK) goto done;
+        sc.cub_bytes = b1 > b2 ? b1 : b2;
+        TCHK(cudaMalloc(&sc.cub, sc.cub_bytes), "alloc");
+
+        iota_kernel<<<nblk(N, 256), 256, 0, s>>>(order, N);
+        for (int t = 0; t < L; ++t) {
+            int64_t a0 = (int64_t)1 << t;
+            int nseg = (int)a0;
+            const int32_t *ls = sc.lvl_start + a0, *le = sc.lvl_end + a0, *lz = sc.lvl_size + a0;
+            seg_of_pos_kernel<<<nblk(N, 256), 256, 0, s>>>(ls, nseg, N, sc.seg);
+            if (kind == 0) {
+                center_kernel<<<dim3(nseg, (d + 63) / 64), 64, 0, s>>>(X, d, order, ls, lz, sc.xc);
+                // x_l: farthest from the center
+                fill_kernel<unsigned long long><<<nblk(nseg, 256), 256, 0, s>>>(sc.bbits, nseg, 0ull);
+                fill_kernel<int32_t><<<nblk(nseg, 256), 256, 0, s>>>(sc.bid, nseg, INT_MAX);
+                far_pass1<true><<<nblk(N, 256), 256, 0, s>>>(X, d, order, sc.seg, N, sc.xc, nullptr, sc.Dq, sc.bbits);
+                far_pass2<<<nblk(N, 256), 256, 0, s>>>(order, sc.seg, N, sc.Dq, sc.bbits, sc.bid);
+                TCHK(cudaMemcpyAsync(sc.xl, sc.bid, sizeof(int32_t) * nseg, cudaMemcpyDeviceToDevice, s), "copy");
+                // x_r: farthest from x_l
+                fill_kernel<unsigned long long><<<nblk(nseg, 256), 256, 0, s>>>(sc.bbits, nseg, 0ull);
+                fill_kernel<int32_t><<<nblk(nseg, 256), 256, 0, s>>>(sc.bid, nseg, INT_MAX);
+                far_pass1<false><<<nblk(N, 256), 256, 0, s>>>(X, d, order, sc.seg, N, nullptr, sc.xl, sc.Dq, sc.bbits);
+                far_pass2<<<nblk(N, 256), 256, 0, s>>>(order, sc.seg, N, sc.Dq, sc.bbits, sc.bid);
+                proj_line_kernel<<<nblk(N, 256), 256, 0, s>>>(X, d, order, sc.seg, N, sc.xl, sc.bid, sc.keys);
+            } else {
+                proj_rp_kernel<<<nblk(N, 256), 256, 0, s>>>(X, d, order, sc.seg, N, a0, seed, iter, sc.keys);
+            }
+            TCHK(cudaGetLastError(), "projection kernels");
+            // (key, id) order inside every node: stable sort of an id-ascending segment
+            if ((rc = seg_sort_f64_i32(sc.keys, sc.keys_out, order, sc.tmp_ids, N, nseg, ls, le, sc.cub, &sc.cub_bytes, s)) != ASKIT_OK) goto done;
+            // children back to ascending id
+            if ((rc = seg_sort_i32(sc.tmp_ids, order, N, 2 * nseg, sc.lvl_start + 2 * a0, sc.lvl_end + 2 * a0, sc.cub, &sc.cub_bytes, s)) != ASKIT_OK) goto done;
+        }
+        TCHK(cudaStreamSynchronize(s), "sync");
+    }
+done:
+#undef TCHK
+    cudaStreamSynchronize(s);
+    free_scratch(sc);
+    return rc;
+}
+
+namespace {
+askit_status knn_lists_init(int64_t Q, double **bd, int **bi, cudaStream_t s) {
+    ASK_CUDA(cudaMalloc(bd, sizeof(double) * Q * 32));
+    ASK_CUDA(cudaMalloc(bi, sizeof(int) * Q * 32));
+    fill_kernel<double><<<nblk(Q * 32, 256), 256, 0, s>>>(*bd, Q * 32, DBL_MAX);
+    fill_kernel<int><<<nblk(Q * 32, 256), 256, 0, s>>>(*bi, Q * 32, INT_MAX);
+    ASK_LAUNCH();
+    return ASKIT_OK;
+}
+}  // namespace
+
+// Exact kNN: every point (Y == nullptr, self excluded) or every row of Y
+// against all N points; the candidates are split in chunks so that many
+// blocks share the work of one query set.
+askit_status knn_exact_gpu(const float *X, int64_t N, int d, int kappa, const float *Y, int64_t Q,
+                           int32_t *ids, double *dist, cudaStream_t s) {
+    double *bd = nullptr;
+    int *bi = nullptr;
+    int32_t *qids = nullptr, *segs = nullptr;
+    askit_status rc = knn_lists_init(Q, &bd, &bi, s);
+    if (rc == ASKIT_OK) {
+        // one block per (query chunk of 64): candidates = all N
+        const int QC = 64;
+        int64_t nqb = (Q + QC - 1) / QC;
+        std::vector<int32_t> h(4 * nqb);
+        for (int64_t b = 0; b < nqb; ++b) {
+            h[b] = 0;
+            h[nqb + b] = (int32_t)N;
+            h[2 * nqb + b] = (int32_t)(b * QC);
+            h[3 * nqb + b] = (int32_t)std::min<int64_t>(Q, (b + 1) * QC);
+        }
+        cudaError_t e = cudaMalloc(&segs, sizeof(int32_t) * 4 * nqb);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(segs, h.data(), sizeof(int32_t) * 4 * nqb, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && !Y) {
+            e = cudaMalloc(&qids, sizeof(int32_t) * Q);
+            if (e == cudaSuccess) iota_kernel<<<nblk(Q, 256), 256, 0, s>>>(qids, Q);
+        }
+        if (e == cudaSuccess) {
+            knn_block_kernel<<<(unsigned)nqb, 256, 8 * d * sizeof(float), s>>>(
+                X, d, nullptr, segs, segs + nqb, qids, Y, Q, segs + 2 * nqb, segs + 3 * nqb, bd, bi, kappa, false);
+            knn_extract_kernel<<<nblk(Q * kappa, 256), 256, 0, s>>>(bd, bi, Q, kappa, ids, dist);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            askit_set_error("exact kNN: %s", cudaGetErrorString(e));
+            rc = ASKIT_ERR_CUDA;
+        }
+    }
+    cudaFree(bd); cudaFree(bi); cudaFree(qids); cudaFree(segs);
+    return rc;
+}
+
+// RP-tree kNN (Section 2.2): iters trees; in each, every point searches its
+// leaf exhaustively and the best kappa candidates are kept across trees.
+askit_status knn_rp_gpu(const float *X, int64_t N, int d, int kappa, int iters, int64_t rp_leaf,
+                        uint64_t seed, int32_t *ids, double *dist, cudaStream_t s) {
+    int L = tree_depth(N, rp_leaf);
+    std::vector<int64_t> st, sz;
+    tree_ranges(N, L, st, sz);
+    int64_t nleaf = (int64_t)1 << L;
+    std::vector<int32_t> h(2 * nleaf);
+    for (int64_t a = 0; a < nleaf; ++a) {
+        h[a] = (int32_t)st[nleaf + a];
+        h[nleaf + a] = (int32_t)(st[nleaf + a] + sz[nleaf + a]);
+    }
+    double *bd = nullptr;
+    int *bi = nullptr;
+    int32_t *order = nullptr, *segs = nullptr;
+    askit_status rc = knn_lists_init(N, &bd, &bi, s);
+    cudaError_t e = cudaSuccess;
+    if (rc == ASKIT_OK) {
+        e = cudaMalloc(&order, sizeof(int32_t) * N);
+        if (e == cudaSuccess) e = cudaMalloc(&segs, sizeof(int32_t) * 2 * nleaf);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(segs, h.data(), sizeof(int32_t) * 2 * nleaf, cudaMemcpyHostToDevice, s);
+    }
+    for (int it = 0; rc == ASKIT_OK && e == cudaSuccess && it < iters; ++it) {
+        rc = build_tree_gpu(X, N, d, L, 1, seed, it, order, s);
+        if (rc != ASKIT_OK) break;
+        // queries of leaf b = its own points (ids in `order`), candidates = the same range
+        knn_block_kernel<<<(unsigned)nleaf, 256, 8 * d * sizeof(float), s>>>(
+            X, d, order, segs, segs + nleaf, order, nullptr, N, segs, segs + nleaf, bd, bi, kappa, true);
+        e = cudaGetLastError();
+    }
+    if (rc == ASKIT_OK && e == cudaSuccess) {
+        knn_extract_kernel<<<nblk(N * kappa, 256), 256, 0, s>>>(bd, bi, N, kappa, ids, dist);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (rc == ASKIT_OK && e != cudaSuccess) {
+        askit_set_error("RP kNN: %s", cudaGetErrorString(e));
+        rc = ASKIT_ERR_CUDA;
+    }
+    cudaFree(bd); cudaFree(bi); cudaFree(order); cudaFree(segs);
+    return rc;
+}
+
+askit_status knn_dist_gpu(const float *X, int64_t N, int d, int kappa, const int32_t *ids,
+                          double *dist, cudaStream_t s) {
+    knn_dist_kernel<<<nblk(N * kappa, 256), 256, 0, s>>>(X, N, d, kappa, ids, dist);
+    ASK_LAUNCH();
+    return ASKIT_OK;
+}

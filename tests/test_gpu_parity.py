@@ -1,0 +1,191 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Neighbor lists, tree permutation, node neighbor lists, sampled targets,
+skeleton ids and the interpolation matrices must be bit-exact (ties broken
+by index, FP64 arithmetic in the same order on both sides).  Evaluated u must
+match the oracle's Evaluate on the same structure to relative L2 error 1e-5
+for the FP32 paths (plain FP32 and 3xTF32) and 1e-4 for the BF16x3 split.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_0260_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"simt_fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 1e-4}
+
+
+def _askit():
+    from paper_1410_0260_gb300 import askit
+    return askit
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def build_pair(X, cfg_kw, h=None):
+    askit = _askit()
+    ocfg = oracle.Config(**{k: v for k, v in cfg_kw.items() if k != "precision"})
+    otree = oracle.Tree(X, ocfg, hsrc=h)
+    gcfg = askit.Config(**{k: v for k, v in cfg_kw.items() if k in askit.Config.__dataclass_fields__})
+    Xd = torch.from_numpy(X).cuda()
+    hd = None if h is None else torch.from_numpy(np.asarray(h, np.float32)).cuda()
+    gtree = askit.Tree(Xd, gcfg, h=hd)
+    return otree, gtree
+
+
+def check_structures(otree, gtree):
+    askit = _askit()
+    N = otree.N
+    assert np.array_equal(gtree.structure(askit.STRUCT_PERM), otree.perm())
+    oid, odd = otree.knn()
+    assert np.array_equal(gtree.structure(askit.STRUCT_KNN), oid)
+    assert np.array_equal(gtree.structure(askit.STRUCT_KNN_DIST), odd)        # bitwise FP64
+    assert np.array_equal(gtree.structure(askit.STRUCT_HSRC), otree.hsrc())
+    c = otree.counts()
+    nn = otree.nnodes
+    g_s = gtree.structure(askit.STRUCT_SKEL_S)
+    g_nc = gtree.structure(askit.STRUCT_NCOL)
+    g_nlc = gtree.structure(askit.STRUCT_NL_CNT)
+    g_nl = gtree.structure(askit.STRUCT_NL_IDS)
+    g_tr = gtree.structure(askit.STRUCT_TROWS)
+    g_sk = gtree.structure(askit.STRUCT_SKEL_IDS)
+    g_P = gtree.structure(askit.STRUCT_P)
+    sk_off = 0
+    p_off = 0
+    for a in range(2, nn):
+        nd = otree.node(a)
+        assert g_nlc[a] == c["nl"][a], a
+        assert np.array_equal(g_nl[a, : c["nl"][a]], nd["nl_ids"]), a
+        assert np.array_equal(g_tr[a, : c["ell"][a]], nd["trows"]), a
+        assert g_nc[a] == c["ncol"][a] and g_s[a] == c["s"][a], a
+        s = int(c["s"][a])
+        assert np.array_equal(g_sk[sk_off: sk_off + s], nd["skel"]), a
+        npp = s * (int(c["ncol"][a]) - s)
+        assert np.array_equal(g_P[p_off: p_off + npp], nd["P"].ravel()), a   # bitwise FP64
+        sk_off += s
+        p_off += npp
+    assert sk_off == len(g_sk)
+
+
+def eval_both(otree, gtree, W, precision):
+    otree.set_weights(W.astype(np.float64))
+    gtree.set_precision(precision)
+    gtree.set_weights(torch.from_numpy(W).cuda())
+    U = gtree.evaluate()
+    torch.cuda.synchronize()
+    gtree.sync()
+    return U.cpu().numpy(), otree.evaluate()
+
+
+SMALL = dict(leaf_size=128, kappa=16, knn_mode=0, s_max=64, id_tol=1e-6, h=1.0, seed=1)
+
+
+@pytest.fixture(scope="module")
+def small_mixture():
+    w = wl.SMALL_MIXTURE
+    X = w.make_points()
+    W = w.make_weights()
+    otree, gtree = build_pair(X, SMALL)
+    return X, W, otree, gtree
+
+
+def test_small_mixture_structures_bit_exact(small_mixture):
+    X, W, otree, gtree = small_mixture
+    check_structures(otree, gtree)
+
+
+@pytest.mark.parametrize("precision", ["simt_fp32", "tf32x3", "bf16x3"])
+def test_small_mixture_u_matches_oracle(small_mixture, precision):
+    X, W, otree, gtree = small_mixture
+    Ug, Uo = eval_both(otree, gtree, W, precision)
+    assert rel(Ug, Uo) <= TOL[precision]
+
+
+def test_ragged_rp_knn_variable_bandwidth_multi_rhs():
+    """Ragged leaves (N not m 2^L), RP-tree kNN, h_j from the 4th neighbor, r = 3."""
+    X = wl.manifold(3001, 20, 4, 0.02, seed=9)
+    kw = dict(leaf_size=48, kappa=10, knn_mode=1, rp_iters=3, s_max=24, id_tol=1e-5, bw_mode=2, bw_k=4,
+              seed=5)
+    otree, gtree = build_pair(X, kw)
+    check_structures(otree, gtree)
+    W = np.random.default_rng(1).standard_normal((3001, 3)).astype(np.float32)
+    for prec in ("simt_fp32", "tf32x3"):
+        Ug, Uo = eval_both(otree, gtree, W, prec)
+        assert rel(Ug, Uo) <= TOL[prec]
+
+
+def test_manifold_d64_rp_knn():
+    """The 64-D manifold shape of the 1M-point workload at N = 16384."""
+    w = wl.MANIFOLD_1M_64.scaled(16384)
+    X, W = w.make_points(), w.make_weights()
+    kw = dict(leaf_size=512, kappa=32, knn_mode=1, rp_iters=2, s_max=256, id_tol=1e-4, h=0.35, seed=2)
+    otree, gtree = build_pair(X, kw)
+    check_structures(otree, gtree)
+    for prec in ("simt_fp32", "tf32x3", "bf16x3"):
+        Ug, Uo = eval_both(otree, gtree, W, prec)
+        assert rel(Ug, Uo) <= TOL[prec], prec
+
+
+def test_pruning_off_and_single_leaf_are_direct_sums():
+    X = wl.mixture(700, 6, 3, 4.0, seed=3)
+    W = np.random.default_rng(2).standard_normal((700, 1)).astype(np.float32)
+    ref = oracle.direct(X, W, 1.0, 0.5, targets=np.arange(700))
+    askit = _askit()
+    for kw in (dict(leaf_size=64, kappa=8, s_max=8, prune=0), dict(leaf_size=1024, kappa=8, s_max=8)):
+        t = askit.Tree(torch.from_numpy(X).cuda(), askit.Config(precision="simt_fp32", **kw))
+        t.set_weights(torch.from_numpy(W).cuda())
+        U = t.evaluate().cpu().numpy()
+        assert rel(U, ref) <= 1e-5
+
+
+def test_out_of_sample_targets():
+    w = wl.SMALL_MIXTURE.scaled(2048)
+    X, W = w.make_points(), w.make_weights()
+    rng = np.random.default_rng(4)
+    Y = (X[rng.integers(0, 2048, 333)] + 0.3 * rng.standard_normal((333, 8))).astype(np.float32)
+    kw = dict(leaf_size=64, kappa=16, s_max=32, id_tol=1e-6, h=1.0)
+    otree, gtree = build_pair(X, kw)
+    otree.set_weights(W.astype(np.float64))
+    Uo = otree.evaluate_oos(Y)
+    gtree.set_weights(torch.from_numpy(W).cuda())
+    for prec in ("simt_fp32", "tf32x3"):
+        gtree.set_precision(prec)
+        Ug = gtree.evaluate_targets(torch.from_numpy(Y).cuda()).cpu().numpy()
+        assert rel(Ug, Uo) <= TOL[prec]
+
+
+def test_evaluate_host_matches_device_path(small_mixture):
+    X, W, otree, gtree = small_mixture
+    gtree.set_precision("tf32x3")
+    Uh = gtree.evaluate_host(W)
+    gtree.set_weights(torch.from_numpy(W).cuda())
+    Ud = gtree.evaluate().cpu().numpy()
+    assert np.array_equal(Uh, Ud)
+
+
+def test_evaluation_is_deterministic(small_mixture):
+    X, W, otree, gtree = small_mixture
+    gtree.set_precision("tf32x3")
+    gtree.set_weights(torch.from_numpy(W).cuda())
+    a = gtree.evaluate().cpu().numpy()
+    b = gtree.evaluate().cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_invalid_arguments_are_errors_not_faults():
+    askit = _askit()
+    X = torch.zeros((10, 3), device="cuda")
+    with pytest.raises(askit.AskitError):
+        askit.Tree(X, askit.Config(kappa=20))          # kappa > N - 1
+    with pytest.raises(askit.AskitError):
+        askit.Tree(X, askit.Config(leaf_size=1, kappa=2))
+    t = askit.Tree(torch.randn((50, 3), device="cuda"), askit.Config(leaf_size=8, kappa=4, s_max=4))
+    with pytest.raises(askit.AskitError):
+        t.evaluate()                                  # weights not set
+    with pytest.raises(askit.AskitError):
+        t.set_weights(torch.zeros((50, 65), device="cuda"))   # r > 64
