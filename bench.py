@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="tf32x3", choices=["simt_fp32", "tf32x3", "bf16x3"])
+    ap.add_argument("--precision", default="tf32x3", choices=["simt_fp32", "tf32x3", "bf16x3", "fp16x3"])
     ap.add_argument("--n", type=int, default=0, help="override N (smaller runs; not a bench line)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -293,7 +293,7 @@ def main():
                 "unit": "Tops/s", "peak_source": "152 SMs x 128 FP32 lanes x max SM clock"}
     else:
         bf16 = (peaks or {}).get("bf16_tflops", 1900.0)
-        tpeak = bf16 * (TF32_OVER_BF16 if args.precision == "tf32x3" else 1.0)
+        tpeak = bf16 * (TF32_OVER_BF16 if args.precision == "tf32x3" else 1.0)   # fp16 and bf16 share the rate
         t_tensor = P * 3 * 2 * d / (tpeak * 1e12)
         t_mufu = P / mufu_peak
         if t_tensor >= t_mufu:
@@ -316,7 +316,7 @@ def main():
     launches_per_step = 1 + info["L"] + 2
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"simt_fp32": "f32", "tf32x3": "tf32x3", "bf16x3": "bf16x3"}[args.precision],
+            "vs_baseline": None, "dtype": {"simt_fp32": "f32", "tf32x3": "tf32x3", "bf16x3": "bf16x3", "fp16x3": "fp16x3"}[args.precision],
             "data": "synthetic",
             "config": {"workload": w.name, "N": N, "d": d, "m": w.leaf_size, "kappa": w.kappa,
                        "knn": "rp-trees x%d" % w.rp_iters, "s_max": w.s_max, "id_tol": w.id_tol, "h": w.h,

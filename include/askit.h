@@ -55,7 +55,8 @@ typedef enum {
 enum {
     ASKIT_PREC_SIMT_FP32 = 0, /* plain FP32 difference form on CUDA cores */
     ASKIT_PREC_TF32X3 = 1,    /* tcgen05 tensor cores, 3xTF32 split, FP32 accumulate */
-    ASKIT_PREC_BF16X3 = 2     /* tcgen05 tensor cores, BF16x3 split, FP32 accumulate */
+    ASKIT_PREC_BF16X3 = 2,    /* tcgen05 tensor cores, BF16x3 split, FP32 accumulate */
+    ASKIT_PREC_FP16X3 = 3     /* tcgen05 tensor cores, FP16x3 split (power-of-2 prescaled), FP32 accumulate */
 };
 
 /* Bandwidth of the Gaussian (Section 4: constant h, or h_j per source). */

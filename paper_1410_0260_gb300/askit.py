@@ -19,8 +19,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libaskit.so")
 _lock = threading.Lock()
 _lib = None
 
-PREC_SIMT_FP32, PREC_TF32X3, PREC_BF16X3 = 0, 1, 2
-PRECISIONS = {"simt_fp32": PREC_SIMT_FP32, "tf32x3": PREC_TF32X3, "bf16x3": PREC_BF16X3}
+PREC_SIMT_FP32, PREC_TF32X3, PREC_BF16X3, PREC_FP16X3 = 0, 1, 2, 3
+PRECISIONS = {"simt_fp32": PREC_SIMT_FP32, "tf32x3": PREC_TF32X3, "bf16x3": PREC_BF16X3, "fp16x3": PREC_FP16X3}
 BW_CONSTANT, BW_ARRAY, BW_KNN = 0, 1, 2
 (STRUCT_PERM, STRUCT_KNN, STRUCT_KNN_DIST, STRUCT_SKEL_S, STRUCT_SKEL_IDS, STRUCT_NL_CNT,
  STRUCT_NL_IDS, STRUCT_TROWS, STRUCT_HSRC, STRUCT_P, STRUCT_NCOL, STRUCT_WSKEL) = range(12)

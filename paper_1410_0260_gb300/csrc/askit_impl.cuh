@@ -107,6 +107,11 @@ struct WorkLists {
     EvalItem *items = nullptr;       // [n_items], grouped by sub-block
     int32_t *block_off = nullptr;    // [n_blocks + 1] items of each sub-block
     int32_t *block_order = nullptr;  // [n_blocks] heaviest first
+    // persistent-kernel schedule: sub-blocks dealt to n_ctas CTAs, heaviest
+    // first, each to the CTA with the least work so far
+    int n_ctas = 0;
+    int32_t *cta_off = nullptr;      // [n_ctas + 1]
+    int32_t *cta_blocks = nullptr;   // [n_blocks]
     int64_t pairs_alg = 0, pairs_cmp = 0, near_tot = 0, far_tot = 0;
 };
 
@@ -171,6 +176,8 @@ struct askit_tree_s {
     float *cent = nullptr;         // [n_sub, TC_K]
     float *Xt_hi = nullptr, *Xt_lo = nullptr, *Xs_hi = nullptr, *Xs_lo = nullptr;   // TF32 split
     uint16_t *Xt_bhi = nullptr, *Xt_blo = nullptr, *Xs_bhi = nullptr, *Xs_blo = nullptr; // BF16 split
+    uint16_t *Xt_hhi = nullptr, *Xt_hlo = nullptr, *Xs_hhi = nullptr, *Xs_hlo = nullptr; // FP16 split (prescaled)
+    float f16_scale = 1.f;         // power of 2 keeping centered coordinates within FP16 range
     float *nrmc_t = nullptr, *nrmc_s = nullptr;
     float4 *Ct = nullptr, *Cs = nullptr;   // per source row {c log2 e / h^2, -(that) |y'|^2, w_0, 0}
     int64_t srows = 0;             // rows of the skeleton-pool arrays

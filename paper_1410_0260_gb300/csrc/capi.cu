@@ -104,7 +104,7 @@ askit_status validate(const askit_params *p, int64_t N, int32_t d, int64_t ldx, 
     if (p->bw_mode < 0 || p->bw_mode > 2) { askit_set_error("bad bw_mode"); return ASKIT_ERR_INVALID_ARG; }
     if (p->knn_mode < 0 || p->knn_mode > 1) { askit_set_error("bad knn_mode"); return ASKIT_ERR_INVALID_ARG; }
     if (p->knn_mode == 1 && p->rp_iters < 1) { askit_set_error("rp_iters must be >= 1"); return ASKIT_ERR_INVALID_ARG; }
-    if (p->precision < 0 || p->precision > 2) { askit_set_error("bad precision"); return ASKIT_ERR_INVALID_ARG; }
+    if (p->precision < 0 || p->precision > 3) { askit_set_error("bad precision"); return ASKIT_ERR_INVALID_ARG; }
     return ASKIT_OK;
 }
 
@@ -328,7 +328,7 @@ askit_status askit_set_weights(askit_tree t, const float *W_dev, int32_t r, int6
 }
 
 askit_status askit_set_precision(askit_tree t, int32_t precision) {
-    if (!t || precision < 0 || precision > 2) { askit_set_error("bad tree or precision"); return ASKIT_ERR_INVALID_ARG; }
+    if (!t || precision < 0 || precision > 3) { askit_set_error("bad tree or precision"); return ASKIT_ERR_INVALID_ARG; }
     t->precision = precision;
     return ASKIT_OK;
 }

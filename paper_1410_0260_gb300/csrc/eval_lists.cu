@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "askit_impl.cuh"
 
@@ -272,8 +273,8 @@ askit_status build_eval_operands(askit_tree t, cudaStream_t s) {
 // FP32 value with the 13 low mantissa bits cleared, lo = x - hi; BF16: hi =
 // bf16(x), lo = bf16(x - hi) -- and the squared norms of the centered rows.
 __global__ void tc_prep_kernel(const float *X, int d_pad, const int64_t *sb_row0, const int32_t *sb_nrows,
-                               int64_t rows_total, float *cent, float *Xhi, float *Xlo, uint16_t *Bhi,
-                               uint16_t *Blo, float *nrmc) {
+                               int64_t rows_total, float f16_scale, float *cent, float *Xhi, float *Xlo,
+                               uint16_t *Bhi, uint16_t *Blo, uint16_t *Hhi, uint16_t *Hlo, float *nrmc) {
     int g = blockIdx.x;
     int64_t r0 = sb_row0[g];
     int nr = sb_nrows[g];
@@ -286,13 +287,14 @@ __global__ void tc_prep_kernel(const float *X, int d_pad, const int64_t *sb_row0
         cent[(int64_t)g * TC_K + k] = c[k];
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < ASK_BLK_N; q += blockDim.x) {
+    // only the sub-block's own rows: the 128-row window of a short sub-block
+    // overlaps the next one, whose rows its own CTA writes
+    for (int q = threadIdx.x; q < nr; q += blockDim.x) {
         int64_t row = r0 + q;
         if (row >= rows_total) break;
-        bool valid = q < nr;
         double nn = 0.0;
         for (int k = 0; k < TC_K; ++k) {
-            float x = (valid && k < d_pad) ? X[row * d_pad + k] - c[k] : 0.f;
+            float x = (k < d_pad) ? X[row * d_pad + k] - c[k] : 0.f;
             nn += (double)x * x;
             float hi = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
             Xhi[row * TC_K + k] = hi;
@@ -301,9 +303,22 @@ __global__ void tc_prep_kernel(const float *X, int d_pad, const int64_t *sb_row0
             __nv_bfloat16 bl = __float2bfloat16_rn(x - __bfloat162float(bh));
             Bhi[row * TC_K + k] = *reinterpret_cast<uint16_t *>(&bh);
             Blo[row * TC_K + k] = *reinterpret_cast<uint16_t *>(&bl);
+            const float xs = x * f16_scale;
+            __half hh = __float2half_rn(xs);
+            __half hl = __float2half_rn(xs - __half2float(hh));
+            Hhi[row * TC_K + k] = __half_as_ushort(hh);
+            Hlo[row * TC_K + k] = __half_as_ushort(hl);
         }
         nrmc[row] = (float)nn;
     }
+}
+
+// Largest |x_k| over the data (bounds every centered coordinate by twice it).
+__global__ void extent_kernel(const float *X, int64_t N, int d, float *ext) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float v = e < N * d ? fabsf(X[e]) : 0.f;
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(ext), __float_as_int(v));
 }
 
 askit_status build_tc_operands(askit_tree t, cudaStream_t s) {
@@ -351,6 +366,14 @@ askit_status build_tc_operands(askit_tree t, cudaStream_t s) {
     ASK_TRY(t->arena.alloc(&t->Xt_blo, (size_t)t->N_pad * TC_K));
     ASK_TRY(t->arena.alloc(&t->Xs_bhi, (size_t)t->srows * TC_K));
     ASK_TRY(t->arena.alloc(&t->Xs_blo, (size_t)t->srows * TC_K));
+    ASK_TRY(t->arena.alloc(&t->Xt_hhi, (size_t)t->N_pad * TC_K));
+    ASK_TRY(t->arena.alloc(&t->Xt_hlo, (size_t)t->N_pad * TC_K));
+    ASK_TRY(t->arena.alloc(&t->Xs_hhi, (size_t)t->srows * TC_K));
+    ASK_TRY(t->arena.alloc(&t->Xs_hlo, (size_t)t->srows * TC_K));
+    ASK_CUDA(cudaMemsetAsync(t->Xt_hhi, 0, sizeof(uint16_t) * t->N_pad * TC_K, s));
+    ASK_CUDA(cudaMemsetAsync(t->Xt_hlo, 0, sizeof(uint16_t) * t->N_pad * TC_K, s));
+    ASK_CUDA(cudaMemsetAsync(t->Xs_hhi, 0, sizeof(uint16_t) * t->srows * TC_K, s));
+    ASK_CUDA(cudaMemsetAsync(t->Xs_hlo, 0, sizeof(uint16_t) * t->srows * TC_K, s));
     ASK_TRY(t->arena.alloc(&t->nrmc_t, t->N_pad));
     ASK_TRY(t->arena.alloc(&t->nrmc_s, t->srows));
     ASK_TRY(t->arena.alloc(&t->Ct, t->N_pad));
@@ -365,13 +388,30 @@ askit_status build_tc_operands(askit_tree t, cudaStream_t s) {
     ASK_CUDA(cudaMemsetAsync(t->Xs_blo, 0, sizeof(uint16_t) * t->srows * TC_K, s));
     ASK_CUDA(cudaMemsetAsync(t->nrmc_t, 0, sizeof(float) * t->N_pad, s));
     ASK_CUDA(cudaMemsetAsync(t->nrmc_s, 0, sizeof(float) * t->srows, s));
+    // FP16 prescale: a power of 2 that maps the data's widest coordinate
+    // range to at most 2^14, so centered values and their differences stay
+    // far below the FP16 maximum (65504)
+    {
+        float *ext = nullptr;
+        ASK_CUDA(cudaMalloc(&ext, sizeof(float)));
+        ASK_CUDA(cudaMemsetAsync(ext, 0, sizeof(float), s));
+        extent_kernel<<<(unsigned)((t->N * t->d + 255) / 256), 256, 0, s>>>(t->X, t->N, t->d, ext);
+        float hext = 0.f;
+        ASK_CUDA(cudaMemcpyAsync(&hext, ext, sizeof(float), cudaMemcpyDeviceToHost, s));
+        ASK_CUDA(cudaStreamSynchronize(s));
+        cudaFree(ext);
+        int e = 0;
+        if (hext > 0.f) frexpf(16384.f / (2.f * hext), &e);
+        t->f16_scale = ldexpf(1.f, e - 1);
+    }
     if (n_leaf_sub > 0)
-        tc_prep_kernel<<<(unsigned)n_leaf_sub, 128, 0, s>>>(t->Xt, t->d_pad, d_r0, d_nr, t->N_pad, t->cent, t->Xt_hi,
-                                                          t->Xt_lo, t->Xt_bhi, t->Xt_blo, t->nrmc_t);
+        tc_prep_kernel<<<(unsigned)n_leaf_sub, 128, 0, s>>>(t->Xt, t->d_pad, d_r0, d_nr, t->N_pad, t->f16_scale, t->cent,
+                                                          t->Xt_hi, t->Xt_lo, t->Xt_bhi, t->Xt_blo, t->Xt_hhi,
+                                                          t->Xt_hlo, t->nrmc_t);
     if (t->n_sub > n_leaf_sub)
         tc_prep_kernel<<<(unsigned)(t->n_sub - n_leaf_sub), 128, 0, s>>>(
-            t->Xs, t->d_pad, d_r0 + n_leaf_sub, d_nr + n_leaf_sub, t->srows, t->cent + n_leaf_sub * TC_K, t->Xs_hi,
-            t->Xs_lo, t->Xs_bhi, t->Xs_blo, t->nrmc_s);
+            t->Xs, t->d_pad, d_r0 + n_leaf_sub, d_nr + n_leaf_sub, t->srows, t->f16_scale,
+            t->cent + n_leaf_sub * TC_K, t->Xs_hi, t->Xs_lo, t->Xs_bhi, t->Xs_blo, t->Xs_hhi, t->Xs_hlo, t->nrmc_s);
     ASK_LAUNCH();
     ASK_CUDA(cudaStreamSynchronize(s));
     cudaFree(d_r0);
@@ -502,6 +542,40 @@ askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, int
         std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
         WTRY(arena.alloc(&w.block_order, nb));
         WCHK(cudaMemcpyAsync(w.block_order, order.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
+        // LPT schedule over one persistent CTA per SM: a sub-block costs its
+        // items plus a fixed reload of its source tile
+        int dev = 0, sms = 0;
+        WCHK(cudaGetDevice(&dev));
+        WCHK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int nc = (int)std::max<int64_t>(1, std::min<int64_t>(nb, sms));
+        std::vector<std::vector<int32_t>> lists(nc);
+        std::vector<std::pair<int64_t, int>> heap;   // (load, cta), min-heap
+        for (int c = 0; c < nc; ++c) heap.push_back({0, c});
+        auto cmp = [](const std::pair<int64_t, int> &x, const std::pair<int64_t, int> &y) {
+            return x.first > y.first || (x.first == y.first && x.second > y.second);
+        };
+        std::make_heap(heap.begin(), heap.end(), cmp);
+        for (int64_t q = 0; q < nb; ++q) {
+            const int32_t bq = order[q];
+            std::pop_heap(heap.begin(), heap.end(), cmp);
+            auto top = heap.back();
+            heap.pop_back();
+            lists[top.second].push_back(bq);
+            top.first += (boff[bq + 1] - boff[bq]) * 4 + 3;
+            heap.push_back(top);
+            std::push_heap(heap.begin(), heap.end(), cmp);
+        }
+        std::vector<int32_t> coff(nc + 1, 0), cblk;
+        cblk.reserve(nb);
+        for (int c = 0; c < nc; ++c) {
+            coff[c + 1] = coff[c] + (int32_t)lists[c].size();
+            cblk.insert(cblk.end(), lists[c].begin(), lists[c].end());
+        }
+        w.n_ctas = nc;
+        WTRY(arena.alloc(&w.cta_off, nc + 1));
+        WTRY(arena.alloc(&w.cta_blocks, std::max<int64_t>(1, nb)));
+        WCHK(cudaMemcpyAsync(w.cta_off, coff.data(), sizeof(int32_t) * (nc + 1), cudaMemcpyHostToDevice, s));
+        WCHK(cudaMemcpyAsync(w.cta_blocks, cblk.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
         WCHK(cudaStreamSynchronize(s));
         int64_t sn = 0, sf = 0, pa = 0;
         for (int64_t q = 0; q < T; ++q) { sn += h_near[q]; sf += h_far[q]; pa += h_pairs[q]; }

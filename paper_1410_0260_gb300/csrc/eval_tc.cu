@@ -4,13 +4,16 @@
 // direct near field, or of a node's skeleton for the far field) against up
 // to 128 targets that all need it (see eval_lists.cu).  For each item
 //
-//     G = X' Y'^T           (tcgen05.mma, 128 x 128 x 64, FP32 accumulators in TMEM)
-//     r^2 = |x'|^2 + |y'|^2 - 2 G
+//     G = A B^T             (tcgen05.mma, 128 x 128 x 64, FP32 accumulators in TMEM)
+//     r^2 = (|a|^2 + 2 a.delta) + |y - c_T|^2 - 2 G
 //     partial_t = sum_j exp2(-c log2(e) r^2 / h_j^2) w_j
 //
-// where x' = x - c_b and y' = y - c_b are centered on the sub-block's mean
-// c_b, which keeps the norm expansion's cancellation error at the scale of
-// the sub-block instead of the data set.  The contraction is split in three
+// with a = x - c_T (targets centered on the item's first target c_T),
+// b = y - c_B (sources centered on their sub-block's mean c_B, pre-split in
+// HBM) and delta = c_T - c_B, an exact rewriting of |x - y|^2.  Every term
+// is bounded by the spread of the item's targets or by |x - y| itself, so
+// the FP32 rounding of the norm expansion stays at that scale even for the
+// wide skeletons of high tree nodes.  The contraction is split in three
 // products (hi*hi + hi*lo + lo*hi) of TF32 or BF16 parts with FP32
 // accumulation.
 //
@@ -30,6 +33,7 @@
 // and TMEM is freed before the kernel returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "askit_impl.cuh"
 
@@ -39,7 +43,7 @@ constexpr int TC_THREADS = 288;
 constexpr int TILE_ROWS = 128;                  // M = N = 128
 constexpr int REGION = TILE_ROWS * 128;         // one 128-row x 128-byte swizzled region (16 KB)
 constexpr uint32_t TMEM_COLS = 256;             // two 128-column FP32 accumulators
-constexpr int SPIN_LIMIT = 1 << 26;
+constexpr int SPIN_LIMIT = 1 << 24;
 
 // Precision traits: element bytes, swizzle regions per operand (TC_K
 // elements x element bytes / 128), MMA K steps, tcgen05 operand format.
@@ -51,6 +55,10 @@ template <> struct Prec<ASKIT_PREC_TF32X3> {
 template <> struct Prec<ASKIT_PREC_BF16X3> {
     static constexpr int EB = 2, NREG = 1, KSTEPS = 4;   // K = 16 per MMA
     static constexpr uint32_t FMT = 1;                   // BF16 in .kind::f16
+};
+template <> struct Prec<ASKIT_PREC_FP16X3> {
+    static constexpr int EB = 2, NREG = 1, KSTEPS = 4;   // K = 16 per MMA
+    static constexpr uint32_t FMT = 0;                   // F16 in .kind::f16
 };
 
 // Instruction descriptor of .kind::tf32 / .kind::f16: D = F32 (bits 4-5),
@@ -167,25 +175,30 @@ struct Smem {
     static constexpr int B_HI = 0, B_LO = OPB;
     static constexpr int A0 = 2 * OPB;                     // stage s: hi at A0 + s*2*OPB, lo at + OPB
     static constexpr int TILES = 6 * OPB;
-    static constexpr int ANORM = TILES;                    // float [2][128] centered target norms
+    static constexpr int ANORM = TILES;                    // float [2][128] |a|^2 + 2 a.delta per target row
+    static constexpr int COLV = ANORM + 2 * 128 * 4;       // float4 [2][128] per source row {2 u sc, -sc q, -sc, w_0}
     static constexpr int RC_MAX = 16;
-    static constexpr int BAR = ANORM + 2 * 128 * 4;        // 10 mbarriers
+    static constexpr int COLW = COLV + 2 * 128 * 16;       // float [2][128][RC_MAX] weights (r > 1)
+    static constexpr int BAR = COLW + 2 * 128 * RC_MAX * 4;   // 10 mbarriers
     static constexpr int MISC = BAR + 10 * 8;              // tmem address, abort flag
     static constexpr int BYTES = MISC + 16;
 };
 
 struct TcArgs {
     const EvalItem *items;
-    const int32_t *block_off, *block_order;
-    int64_t n_blocks;
+    const int32_t *block_off;
+    const int32_t *cta_off, *cta_blocks;   // this CTA's sub-blocks: cta_blocks[cta_off[c] .. cta_off[c+1])
     const int32_t *tgt;       // entry -> target slot
     const float *Xq;          // target coordinates [*, ldq]
     int64_t ldq;
     int d_pad;
     const float *cent;        // [n_sub, TC_K]
-    const float4 *Ct, *Cs;    // per source row {c log2(e) / h^2, -(that) |y'|^2, w_0, 0}
+    const float *sc_t, *sc_s; // c log2(e) / h^2 per source row
+    const float *Xt, *Xs;     // raw source coordinates [*, d_pad] (column terms)
     const float *Wt, *Ws;
     int r;
+    float f16_scale;          // power-of-2 prescale of the FP16 operands (1 otherwise)
+    float g_unscale;          // 1 / f16_scale^2 (1 otherwise)
     float *partial;
     int *status;
 };
@@ -202,6 +215,8 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(sm);
     float *a_norm = reinterpret_cast<float *>(sm + S::ANORM);
+    float4 *colv = reinterpret_cast<float4 *>(sm + S::COLV);
+    float *colw = reinterpret_cast<float *>(sm + S::COLW);
     const uint32_t bar0 = sbase + S::BAR;
     auto BAR_A_FULL = [&](int s) { return bar0 + 8 * s; };
     auto BAR_A_EMPTY = [&](int s) { return bar0 + 8 * (2 + s); };
@@ -238,63 +253,124 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
 
     if (warp < 4) {
         // ------------------------------------------------------------ loaders
-        constexpr int CPR = TC_K / 4;            // 16-byte source chunks (4 floats) per row
-        constexpr int RPP = 32 / CPR;            // rows per warp pass
-        const int c4 = lane % CPR;               // this lane's 4 columns: 4*c4 .. 4*c4+3
-        const int rsub = lane / CPR;
+        // thread t owns target row t and source row t of every item
+        const int t = tid;
+        const int nk4 = args.d_pad / 4;            // 16-byte chunks of a coordinate row
         int li = 0;
-        for (int64_t bi = blockIdx.x; bi < args.n_blocks && !*abort_flag; bi += gridDim.x) {
-            const int b = args.block_order[bi];
-            for (int it = args.block_off[b]; it < args.block_off[b + 1]; ++it, ++li) {
+        for (int ci = args.cta_off[blockIdx.x]; ci < args.cta_off[blockIdx.x + 1] && !*abort_flag; ++ci) {
+            const int b = args.cta_blocks[ci];
+            const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
+            EvalItem item = args.items[i0];
+            const bool far = item.nrows < 0;
+            const int nrows = item.nrows & 0x7fffffff;
+            const bool has_src = t < nrows;
+            const int64_t srow = (int64_t)item.row0 + t;
+            const float *ysrc = (far ? args.Xs : args.Xt) + srow * args.d_pad;
+            const float *cB = args.cent + (int64_t)item.cidx * TC_K;
+            // block-constant column data of source row t: c log2(e) / h^2 and w
+            const float sc = has_src ? __ldg((far ? args.sc_s : args.sc_t) + srow) : 0.f;
+            const float *wrow = (far ? args.Ws : args.Wt) + srow * args.r;
+            const float w0 = has_src ? __ldg(wrow) : 0.f;
+            int slot = t < item.cnt ? args.tgt[item.e0 + t] : -1;
+            int first = args.tgt[item.e0];
+            for (int it = i0; it < i1; ++it, ++li) {
                 const int s = li & 1;
                 const uint32_t par = ((li >> 1) & 1) ^ 1;
+                const int cnt = item.cnt;
+                const float *xrow = args.Xq + (int64_t)(slot >= 0 ? slot : 0) * args.ldq;
+                const float *xt0 = args.Xq + (int64_t)first * args.ldq;
+                const bool has_tgt = slot >= 0;
+                // prefetch the next item of the block (its entries follow this item's)
+                if (it + 1 < i1) {
+                    item = args.items[it + 1];
+                    slot = t < item.cnt ? args.tgt[item.e0 + t] : -1;
+                    first = args.tgt[item.e0];
+                }
                 if (!mbar_wait(BAR_A_EMPTY(s), par, abort_flag, args.status)) goto loader_done;
                 if (!mbar_wait(BAR_T_EMPTY(s), par, abort_flag, args.status)) goto loader_done;
-                const EvalItem item = args.items[it];
-                const float4 cen = *reinterpret_cast<const float4 *>(args.cent + (int64_t)item.cidx * TC_K + 4 * c4);
                 uint8_t *ahi = sm + S::A0 + s * 2 * S::OPB;
                 uint8_t *alo = ahi + S::OPB;
+                float nn = 0.f, dd = 0.f, qq = 0.f;
+                // two 4-column chunks per step: 32 contiguous bytes of a row
 #pragma unroll 4
-                for (int pass = 0; pass < 32 / RPP; ++pass) {
-                    const int row = warp * 32 + pass * RPP + rsub;
-                    const bool valid = row < item.cnt && 4 * c4 < args.d_pad;
-                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (valid) {
-                        const int64_t slot = args.tgt[item.e0 + row];
-                        v = __ldg(reinterpret_cast<const float4 *>(args.Xq + slot * args.ldq + 4 * c4));
-                        v.x -= cen.x; v.y -= cen.y; v.z -= cen.z; v.w -= cen.w;
-                    }
-                    float nn = v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
+                for (int k8 = 0; k8 < TC_K / 8; ++k8) {
+                    float xa[8], ya[8];
+                    if (2 * k8 < nk4) {
+                        const float4 x0 = has_tgt ? __ldg(reinterpret_cast<const float4 *>(xrow + 8 * k8)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const float4 x1 = has_tgt ? __ldg(reinterpret_cast<const float4 *>(xrow + 8 * k8 + 4)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const float4 t0 = __ldg(reinterpret_cast<const float4 *>(xt0 + 8 * k8));
+                        const float4 t1 = __ldg(reinterpret_cast<const float4 *>(xt0 + 8 * k8 + 4));
+                        const float4 b0 = *reinterpret_cast<const float4 *>(cB + 8 * k8);
+                        const float4 b1 = *reinterpret_cast<const float4 *>(cB + 8 * k8 + 4);
+                        const float4 y0 = has_src ? __ldg(reinterpret_cast<const float4 *>(ysrc + 8 * k8)) : t0;
+                        const float4 y1 = has_src ? __ldg(reinterpret_cast<const float4 *>(ysrc + 8 * k8 + 4)) : t1;
+                        const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                        const float ts[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+                        const float bs[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                        const float ys[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
 #pragma unroll
-                    for (int o = CPR / 2; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
-                    if (c4 == 0) a_norm[s * 128 + row] = nn;
-                    if constexpr (P == ASKIT_PREC_TF32X3) {
-                        float4 hi, lo;
-                        hi.x = __uint_as_float(__float_as_uint(v.x) & 0xffffe000u);
-                        hi.y = __uint_as_float(__float_as_uint(v.y) & 0xffffe000u);
-                        hi.z = __uint_as_float(__float_as_uint(v.z) & 0xffffe000u);
-                        hi.w = __uint_as_float(__float_as_uint(v.w) & 0xffffe000u);
-                        lo.x = v.x - hi.x; lo.y = v.y - hi.y; lo.z = v.z - hi.z; lo.w = v.w - hi.w;
-                        const int reg = c4 >> 3, chunk = c4 & 7;
-                        const int off = reg * REGION + row * 128 + ((chunk ^ (row & 7)) << 4);
-                        *reinterpret_cast<float4 *>(ahi + off) = hi;
-                        *reinterpret_cast<float4 *>(alo + off) = lo;
+                        for (int e = 0; e < 8; ++e) {
+                            xa[e] = has_tgt ? xs[e] - ts[e] : 0.f;       // a = x - c_T
+                            nn = fmaf(xa[e], xa[e], nn);
+                            dd = fmaf(xa[e], ts[e] - bs[e], dd);          // a . delta
+                            ya[e] = ys[e] - ts[e];                        // y - c_T
+                            qq = fmaf(ya[e], ya[e], qq);
+                        }
                     } else {
-                        __nv_bfloat16 h0 = __float2bfloat16_rn(v.x), h1 = __float2bfloat16_rn(v.y);
-                        __nv_bfloat16 h2 = __float2bfloat16_rn(v.z), h3 = __float2bfloat16_rn(v.w);
-                        __nv_bfloat16 l0 = __float2bfloat16_rn(v.x - __bfloat162float(h0));
-                        __nv_bfloat16 l1 = __float2bfloat16_rn(v.y - __bfloat162float(h1));
-                        __nv_bfloat16 l2 = __float2bfloat16_rn(v.z - __bfloat162float(h2));
-                        __nv_bfloat16 l3 = __float2bfloat16_rn(v.w - __bfloat162float(h3));
-                        uint2 hv, lv;
-                        hv.x = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                        hv.y = (uint32_t)__bfloat16_as_ushort(h2) | ((uint32_t)__bfloat16_as_ushort(h3) << 16);
-                        lv.x = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-                        lv.y = (uint32_t)__bfloat16_as_ushort(l2) | ((uint32_t)__bfloat16_as_ushort(l3) << 16);
-                        const int off = row * 128 + (((c4 >> 1) ^ (row & 7)) << 4) + (c4 & 1) * 8;
-                        *reinterpret_cast<uint2 *>(ahi + off) = hv;
-                        *reinterpret_cast<uint2 *>(alo + off) = lv;
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) xa[e] = 0.f;
                     }
+                    if constexpr (P == ASKIT_PREC_TF32X3) {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int c4 = 2 * k8 + h, reg = c4 >> 3, chunk = c4 & 7;
+                            float4 hi, lo;
+                            hi.x = __uint_as_float(__float_as_uint(xa[4 * h + 0]) & 0xffffe000u);
+                            hi.y = __uint_as_float(__float_as_uint(xa[4 * h + 1]) & 0xffffe000u);
+                            hi.z = __uint_as_float(__float_as_uint(xa[4 * h + 2]) & 0xffffe000u);
+                            hi.w = __uint_as_float(__float_as_uint(xa[4 * h + 3]) & 0xffffe000u);
+                            lo.x = xa[4 * h + 0] - hi.x; lo.y = xa[4 * h + 1] - hi.y;
+                            lo.z = xa[4 * h + 2] - hi.z; lo.w = xa[4 * h + 3] - hi.w;
+                            const int off = reg * REGION + t * 128 + ((chunk ^ (t & 7)) << 4);
+                            *reinterpret_cast<float4 *>(ahi + off) = hi;
+                            *reinterpret_cast<float4 *>(alo + off) = lo;
+                        }
+                    } else {
+                        // 8 elements = one 16-byte chunk of the 128-byte row
+                        uint32_t hv[4], lv[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            float v0 = xa[2 * e], v1 = xa[2 * e + 1];
+                            uint16_t h0, h1, l0, l1;
+                            if constexpr (P == ASKIT_PREC_FP16X3) {
+                                v0 *= args.f16_scale; v1 *= args.f16_scale;
+                                const __half a0 = __float2half_rn(v0), a1 = __float2half_rn(v1);
+                                h0 = __half_as_ushort(a0); h1 = __half_as_ushort(a1);
+                                l0 = __half_as_ushort(__float2half_rn(v0 - __half2float(a0)));
+                                l1 = __half_as_ushort(__float2half_rn(v1 - __half2float(a1)));
+                            } else {
+                                const __nv_bfloat16 a0 = __float2bfloat16_rn(v0), a1 = __float2bfloat16_rn(v1);
+                                h0 = __bfloat16_as_ushort(a0); h1 = __bfloat16_as_ushort(a1);
+                                l0 = __bfloat16_as_ushort(__float2bfloat16_rn(v0 - __bfloat162float(a0)));
+                                l1 = __bfloat16_as_ushort(__float2bfloat16_rn(v1 - __bfloat162float(a1)));
+                            }
+                            hv[e] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                            lv[e] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+                        }
+                        const int off = t * 128 + ((k8 ^ (t & 7)) << 4);
+                        *reinterpret_cast<uint4 *>(ahi + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                        *reinterpret_cast<uint4 *>(alo + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                    }
+                }
+                (void)cnt;
+                // row term |a|^2 + 2 a.delta; column data of source row t:
+                // arg = g (2 u sc) + (-sc) p_t + (-sc q) = -sc (p_t + q - 2 u g)
+                a_norm[s * 128 + t] = nn + 2.f * dd;
+                colv[s * 128 + t] = make_float4(2.f * args.g_unscale * sc, -sc * qq, -sc, w0);
+                if (RC > 1) {
+#pragma unroll
+                    for (int z = 0; z < RC; ++z)
+                        colw[(s * 128 + t) * RC + z] = (has_src && z < args.r) ? __ldg(wrow + z) : 0.f;
                 }
                 // generic-proxy stores -> visible to the tensor core's async proxy
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -307,47 +383,41 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
         const int row = tid - 128;                 // TMEM lane = target row of the item
         const int q = warp & 3;                    // this warp's TMEM lane quadrant
         int li = 0;
-        for (int64_t bi = blockIdx.x; bi < args.n_blocks && !*abort_flag; bi += gridDim.x) {
-            const int b = args.block_order[bi];
+        for (int ci = args.cta_off[blockIdx.x]; ci < args.cta_off[blockIdx.x + 1] && !*abort_flag; ++ci) {
+            const int b = args.cta_blocks[ci];
             for (int it = args.block_off[b]; it < args.block_off[b + 1]; ++it, ++li) {
                 const int a = li & 1;
                 const uint32_t par = (li >> 1) & 1;
                 const EvalItem item = args.items[it];
-                const bool far = item.nrows < 0;
                 const int nrows = item.nrows & 0x7fffffff;
-                // per source row: {c log2(e) / h^2, -(that) |y'|^2, w_0, 0}
-                const float4 *cp = (far ? args.Cs : args.Ct) + item.row0;
-                const float *wp = (far ? args.Ws : args.Wt) + (int64_t)item.row0 * args.r;
                 if (!mbar_wait(BAR_A_FULL(a), par, abort_flag, args.status)) goto epi_done;
                 if (!mbar_wait(BAR_T_FULL(a), par, abort_flag, args.status)) goto epi_done;
                 tc_fence_after();
-                float acc[RC];
+                float acc[RC < 4 ? 4 : RC];
 #pragma unroll
-                for (int z = 0; z < RC; ++z) acc[z] = 0.f;
+                for (int z = 0; z < (RC < 4 ? 4 : RC); ++z) acc[z] = 0.f;
                 if (q * 32 < item.cnt) {   // warp-uniform: skip quadrants with no target
-                    const float nt = a_norm[a * 128 + row];
+                    const float pt = a_norm[a * 128 + row];
+                    const float4 *cv4 = colv + a * 128;
+                    const float *cw = colw + a * 128 * RC;
 #pragma unroll 1
                     for (int c = 0; c < 4 && c * 32 < nrows; ++c) {
                         float g[32];
                         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * 128 + c * 32), g);
 #pragma unroll
                         for (int jj = 0; jj < 32; ++jj) {
-                            const int j = c * 32 + jj;
-                            if (j < nrows) {   // uniform across the warp
-                                const float4 cv = __ldg(cp + j);
-                                const float g2 = fmaf(g[jj], 2.f, -nt);
-                                const float arg = fminf(fmaf(g2, cv.x, cv.y), 0.f);
-                                const float k = ex2_approx(arg);
-                                if constexpr (RC == 1) {
-                                    acc[0] = fmaf(k, cv.z, acc[0]);
-                                } else {
+                            // columns past nrows carry w = 0 (and sc = 0)
+                            const float4 cv = cv4[c * 32 + jj];
+                            const float k = ex2_approx(fmaf(g[jj], cv.x, fmaf(cv.z, pt, cv.y)));
+                            if constexpr (RC == 1) {
+                                acc[jj & 3] = fmaf(k, cv.w, acc[jj & 3]);
+                            } else {
 #pragma unroll
-                                    for (int z = 0; z < RC; ++z)
-                                        if (z < args.r) acc[z] = fmaf(k, __ldg(wp + (int64_t)j * args.r + z), acc[z]);
-                                }
+                                for (int z = 0; z < RC; ++z) acc[z] = fmaf(k, cw[(c * 32 + jj) * RC + z], acc[z]);
                             }
                         }
                     }
+                    if constexpr (RC == 1) acc[0] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
                 }
                 tc_fence_before();
                 mbar_arrive(BAR_T_EMPTY(a));
@@ -364,8 +434,8 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
         // ------------------------------------------------- TMA + MMA issuer
         constexpr int TX = 2 * NREG * REGION;      // hi + lo of one 128-row sub-block
         int li = 0, lb = 0;
-        for (int64_t bi = blockIdx.x; bi < args.n_blocks && !*abort_flag; bi += gridDim.x, ++lb) {
-            const int b = args.block_order[bi];
+        for (int ci = args.cta_off[blockIdx.x]; ci < args.cta_off[blockIdx.x + 1] && !*abort_flag; ++ci, ++lb) {
+            const int b = args.cta_blocks[ci];
             const EvalItem first = args.items[args.block_off[b]];
             const bool far = first.nrows < 0;
             if (!mbar_wait(BAR_B_EMPTY, (lb & 1) ^ 1, abort_flag, args.status)) goto mma_done;
@@ -389,13 +459,20 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                 const uint32_t d_tmem = tmem + (uint32_t)(s * 128);
                 const uint32_t a_hi = sbase + S::A0 + s * 2 * S::OPB, a_lo = a_hi + S::OPB;
                 const uint32_t b_hi = sbase + S::B_HI, b_lo = sbase + S::B_LO;
+                // The tensor core rounds each accumulation step to the running
+                // sum's precision, so the small cross terms go in first (while the
+                // accumulator is small) and the hi*hi products last.
 #pragma unroll
                 for (int k = 0; k < KSTEPS; ++k) {
                     // K step k: 32 bytes into swizzle region k / 4
                     const uint32_t off = (uint32_t)((k >> 2) * REGION + (k & 3) * 32);
-                    tc_mma<P>(d_tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), IDESC, k > 0);
-                    tc_mma<P>(d_tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), IDESC, 1);
+                    tc_mma<P>(d_tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), IDESC, k > 0);
                     tc_mma<P>(d_tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), IDESC, 1);
+                }
+#pragma unroll
+                for (int k = 0; k < KSTEPS; ++k) {
+                    const uint32_t off = (uint32_t)((k >> 2) * REGION + (k & 3) * 32);
+                    tc_mma<P>(d_tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), IDESC, 1);
                 }
                 tc_commit(BAR_A_EMPTY(s));
                 tc_commit(BAR_T_FULL(s));
@@ -414,21 +491,23 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
 
 // Tensor maps of the four source operand arrays for one precision.
 struct TcState {
-    CUtensorMap map[2][4];   // [precision: 0 tf32, 1 bf16][t_hi, t_lo, s_hi, s_lo]
-    bool ready[2] = {false, false};
+    CUtensorMap map[3][4];   // [precision: 0 tf32, 1 bf16, 2 fp16][t_hi, t_lo, s_hi, s_lo]
+    bool ready[3] = {false, false, false};
 };
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-askit_status encode_map(EncodeTiledFn fn, CUtensorMap *m, void *base, int64_t rows, bool f32) {
+askit_status encode_map(EncodeTiledFn fn, CUtensorMap *m, void *base, int64_t rows, int ty) {
+    const bool f32 = ty == 0;
     const int eb = f32 ? 4 : 2;
     cuuint64_t dims[2] = {(cuuint64_t)TC_K, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)TC_K * eb};
     cuuint32_t box[2] = {(cuuint32_t)(128 / eb), (cuuint32_t)TILE_ROWS};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims,
+    CUresult r = fn(m, ty == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                       : ty == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims,
                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -450,11 +529,15 @@ askit_status tc_state(askit_tree t, int pi, TcState **out) {
             return ASKIT_ERR_CUDA;
         }
         EncodeTiledFn fn = (EncodeTiledFn)fnp;
-        bool f32 = pi == 0;
-        ASK_TRY(encode_map(fn, &st->map[pi][0], f32 ? (void *)t->Xt_hi : (void *)t->Xt_bhi, t->N_pad, f32));
-        ASK_TRY(encode_map(fn, &st->map[pi][1], f32 ? (void *)t->Xt_lo : (void *)t->Xt_blo, t->N_pad, f32));
-        ASK_TRY(encode_map(fn, &st->map[pi][2], f32 ? (void *)t->Xs_hi : (void *)t->Xs_bhi, t->srows, f32));
-        ASK_TRY(encode_map(fn, &st->map[pi][3], f32 ? (void *)t->Xs_lo : (void *)t->Xs_blo, t->srows, f32));
+        const int ty = pi;   // 0 fp32 (tf32), 1 bf16, 2 fp16
+        void *th = pi == 0 ? (void *)t->Xt_hi : pi == 1 ? (void *)t->Xt_bhi : (void *)t->Xt_hhi;
+        void *tl = pi == 0 ? (void *)t->Xt_lo : pi == 1 ? (void *)t->Xt_blo : (void *)t->Xt_hlo;
+        void *sh = pi == 0 ? (void *)t->Xs_hi : pi == 1 ? (void *)t->Xs_bhi : (void *)t->Xs_hhi;
+        void *sl = pi == 0 ? (void *)t->Xs_lo : pi == 1 ? (void *)t->Xs_blo : (void *)t->Xs_hlo;
+        ASK_TRY(encode_map(fn, &st->map[pi][0], th, t->N_pad, ty));
+        ASK_TRY(encode_map(fn, &st->map[pi][1], tl, t->N_pad, ty));
+        ASK_TRY(encode_map(fn, &st->map[pi][2], sh, t->srows, ty));
+        ASK_TRY(encode_map(fn, &st->map[pi][3], sl, t->srows, ty));
         st->ready[pi] = true;
     }
     *out = st;
@@ -462,19 +545,16 @@ askit_status tc_state(askit_tree t, int pi, TcState **out) {
 }
 
 template <int P, int RC>
-askit_status launch(askit_tree t, TcState *st, const TcArgs &a, cudaStream_t s) {
+askit_status launch(askit_tree t, TcState *st, const TcArgs &a, int a_grid, cudaStream_t s) {
     using S = Smem<P>;
-    const int pi = P == ASKIT_PREC_TF32X3 ? 0 : 1;
+    const int pi = P == ASKIT_PREC_TF32X3 ? 0 : P == ASKIT_PREC_BF16X3 ? 1 : 2;
     const size_t smem = S::BYTES + 1024;
     static bool attr_set = false;
     if (!attr_set) {
         ASK_CUDA(cudaFuncSetAttribute(eval_tc_kernel<P, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr_set = true;
     }
-    int dev = 0, sms = 0;
-    ASK_CUDA(cudaGetDevice(&dev));
-    ASK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const unsigned grid = (unsigned)std::min<int64_t>(a.n_blocks, sms);
+    const unsigned grid = (unsigned)a_grid;
     eval_tc_kernel<P, RC><<<grid, TC_THREADS, smem, s>>>(st->map[pi][0], st->map[pi][1], st->map[pi][2],
                                                          st->map[pi][3], a);
     ASK_LAUNCH();
@@ -495,32 +575,41 @@ askit_status eval_tc(askit_tree t, int precision, const float *Xq, int64_t ldq, 
     }
     if (w.n_blocks == 0) return ASKIT_OK;
     TcState *st = nullptr;
-    ASK_TRY(tc_state(t, precision == ASKIT_PREC_TF32X3 ? 0 : 1, &st));
+    ASK_TRY(tc_state(t, precision == ASKIT_PREC_TF32X3 ? 0 : precision == ASKIT_PREC_BF16X3 ? 1 : 2, &st));
     TcArgs a;
     a.items = w.items;
     a.block_off = w.block_off;
-    a.block_order = w.block_order;
-    a.n_blocks = w.n_blocks;
+    a.cta_off = w.cta_off;
+    a.cta_blocks = w.cta_blocks;
     a.tgt = w.tgt;
     a.Xq = Xq;
     a.ldq = ldq;
     a.d_pad = t->d_pad;
     a.cent = t->cent;
-    a.Ct = t->Ct;
-    a.Cs = t->Cs;
+    a.sc_t = t->sc_t;
+    a.sc_s = t->sc_s;
+    a.Xt = t->Xt;
+    a.Xs = t->Xs;
     a.Wt = t->Wt;
     a.Ws = t->Ws;
     a.r = t->r;
     a.partial = partial;
     a.status = t->d_status;
+    a.f16_scale = precision == ASKIT_PREC_FP16X3 ? t->f16_scale : 1.f;
+    a.g_unscale = 1.f / (a.f16_scale * a.f16_scale);
     if (precision == ASKIT_PREC_TF32X3) {
-        if (t->r == 1) return launch<ASKIT_PREC_TF32X3, 1>(t, st, a, s);
-        if (t->r <= 4) return launch<ASKIT_PREC_TF32X3, 4>(t, st, a, s);
-        return launch<ASKIT_PREC_TF32X3, 16>(t, st, a, s);
+        if (t->r == 1) return launch<ASKIT_PREC_TF32X3, 1>(t, st, a, w.n_ctas, s);
+        if (t->r <= 4) return launch<ASKIT_PREC_TF32X3, 4>(t, st, a, w.n_ctas, s);
+        return launch<ASKIT_PREC_TF32X3, 16>(t, st, a, w.n_ctas, s);
     }
-    if (t->r == 1) return launch<ASKIT_PREC_BF16X3, 1>(t, st, a, s);
-    if (t->r <= 4) return launch<ASKIT_PREC_BF16X3, 4>(t, st, a, s);
-    return launch<ASKIT_PREC_BF16X3, 16>(t, st, a, s);
+    if (precision == ASKIT_PREC_BF16X3) {
+        if (t->r == 1) return launch<ASKIT_PREC_BF16X3, 1>(t, st, a, w.n_ctas, s);
+        if (t->r <= 4) return launch<ASKIT_PREC_BF16X3, 4>(t, st, a, w.n_ctas, s);
+        return launch<ASKIT_PREC_BF16X3, 16>(t, st, a, w.n_ctas, s);
+    }
+    if (t->r == 1) return launch<ASKIT_PREC_FP16X3, 1>(t, st, a, w.n_ctas, s);
+    if (t->r <= 4) return launch<ASKIT_PREC_FP16X3, 4>(t, st, a, w.n_ctas, s);
+    return launch<ASKIT_PREC_FP16X3, 16>(t, st, a, w.n_ctas, s);
 }
 
 void eval_tc_free(askit_tree t) {

@@ -4,7 +4,9 @@ Neighbor lists, tree permutation, node neighbor lists, sampled targets,
 skeleton ids and the interpolation matrices must be bit-exact (ties broken
 by index, FP64 arithmetic in the same order on both sides).  Evaluated u must
 match the oracle's Evaluate on the same structure to relative L2 error 1e-5
-for the FP32 paths (plain FP32 and 3xTF32) and 1e-4 for the BF16x3 split.
+for the plain FP32 path and 1e-4 for the split-product tensor-core paths
+(3xTF32, BF16x3, FP16x3).  FP16x3 is also held to 1e-5 (FP32 grade) on the
+cases here.
 """
 import numpy as np
 import pytest
@@ -15,7 +17,8 @@ from paper_1410_0260_gb300 import workloads as wl
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"simt_fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 1e-4}
+TOL = {"simt_fp32": 1e-5, "tf32x3": 1e-4, "bf16x3": 1e-4, "fp16x3": 1e-4}
+FP32_GRADE = 1e-5
 
 
 def _askit():
@@ -99,11 +102,13 @@ def test_small_mixture_structures_bit_exact(small_mixture):
     check_structures(otree, gtree)
 
 
-@pytest.mark.parametrize("precision", ["simt_fp32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("precision", ["simt_fp32", "tf32x3", "bf16x3", "fp16x3"])
 def test_small_mixture_u_matches_oracle(small_mixture, precision):
     X, W, otree, gtree = small_mixture
     Ug, Uo = eval_both(otree, gtree, W, precision)
     assert rel(Ug, Uo) <= TOL[precision]
+    if precision == "fp16x3":
+        assert rel(Ug, Uo) <= FP32_GRADE
 
 
 def test_ragged_rp_knn_variable_bandwidth_multi_rhs():
@@ -114,7 +119,7 @@ def test_ragged_rp_knn_variable_bandwidth_multi_rhs():
     otree, gtree = build_pair(X, kw)
     check_structures(otree, gtree)
     W = np.random.default_rng(1).standard_normal((3001, 3)).astype(np.float32)
-    for prec in ("simt_fp32", "tf32x3"):
+    for prec in ("simt_fp32", "tf32x3", "fp16x3"):
         Ug, Uo = eval_both(otree, gtree, W, prec)
         assert rel(Ug, Uo) <= TOL[prec]
 
@@ -126,9 +131,11 @@ def test_manifold_d64_rp_knn():
     kw = dict(leaf_size=512, kappa=32, knn_mode=1, rp_iters=2, s_max=256, id_tol=1e-4, h=0.35, seed=2)
     otree, gtree = build_pair(X, kw)
     check_structures(otree, gtree)
-    for prec in ("simt_fp32", "tf32x3", "bf16x3"):
+    for prec in ("simt_fp32", "tf32x3", "bf16x3", "fp16x3"):
         Ug, Uo = eval_both(otree, gtree, W, prec)
         assert rel(Ug, Uo) <= TOL[prec], prec
+        if prec == "fp16x3":
+            assert rel(Ug, Uo) <= FP32_GRADE
 
 
 def test_pruning_off_and_single_leaf_are_direct_sums():
