@@ -17,14 +17,15 @@
 // products (hi*hi + hi*lo + lo*hi) of TF32 or BF16 parts with FP32
 // accumulation.
 //
-// One CTA per SM, warp-specialized, 288 threads:
-//   warps 0-3  loaders: gather the item's target rows (coalesced 16-byte
-//              loads), center and split them, and store them in the
-//              128-byte-swizzled K-major layout the tensor core reads (two
-//              shared-memory stages);
-//   warps 4-7  epilogue: tcgen05.ld of their 32 TMEM lanes (one row each),
+// One CTA per SM, warp-specialized, 416 threads:
+//   warps 0-7  loaders, two groups taking alternate items: thread t gathers
+//              the item's target row t, centers and splits it, and stores it
+//              in the 128-byte-swizzled K-major layout the tensor core reads
+//              (stage = group); it also forms the row term of target t and
+//              the column data of source row t;
+//   warps 8-11 epilogue: tcgen05.ld of their 32 TMEM lanes (one row each),
 //              exponent on MUFU.EX2, reduction against the weights;
-//   warp 8     one thread issues the TMA loads of the sub-block (centered,
+//   warp 12    one thread issues the TMA loads of the sub-block (centered,
 //              pre-split rows) and the tcgen05.mma instructions, and commits
 //              them to mbarriers.
 // Two TMEM accumulators (2 x 128 columns) let the MMAs of item i+1 run
@@ -39,7 +40,7 @@
 
 namespace {
 
-constexpr int TC_THREADS = 288;
+constexpr int TC_THREADS = 416;
 constexpr int TILE_ROWS = 128;                  // M = N = 128
 constexpr int REGION = TILE_ROWS * 128;         // one 128-row x 128-byte swizzled region (16 KB)
 constexpr uint32_t TMEM_COLS = 256;             // two 128-column FP32 accumulators
@@ -241,7 +242,7 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 8) {
+    if (warp == 12) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      ::"r"(smem_u32(tmem_slot)), "r"(TMEM_COLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -251,15 +252,18 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp < 4) {
+    if (warp < 8) {
         // ------------------------------------------------------------ loaders
-        // thread t owns target row t and source row t of every item
-        const int t = tid;
+        // two groups of four warps take alternate items (group g fills stage g);
+        // thread t of a group owns target row t and source row t of its items
+        const int grp = warp >> 2;
+        const int t = tid & 127;
         const int nk4 = args.d_pad / 4;            // 16-byte chunks of a coordinate row
         int li = 0;
         for (int ci = args.cta_off[blockIdx.x]; ci < args.cta_off[blockIdx.x + 1] && !*abort_flag; ++ci) {
             const int b = args.cta_blocks[ci];
             const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
+            const int li_block_end = li + (i1 - i0);
             EvalItem item = args.items[i0];
             const bool far = item.nrows < 0;
             const int nrows = item.nrows & 0x7fffffff;
@@ -271,18 +275,22 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
             const float sc = has_src ? __ldg((far ? args.sc_s : args.sc_t) + srow) : 0.f;
             const float *wrow = (far ? args.Ws : args.Wt) + srow * args.r;
             const float w0 = has_src ? __ldg(wrow) : 0.f;
-            int slot = t < item.cnt ? args.tgt[item.e0 + t] : -1;
-            int first = args.tgt[item.e0];
-            for (int it = i0; it < i1; ++it, ++li) {
+            // this group's first item of the block
+            int it = i0 + (((li & 1) ^ grp) & 1);
+            if (it < i1) item = args.items[it];
+            int slot = (it < i1 && t < item.cnt) ? args.tgt[item.e0 + t] : -1;
+            int first = it < i1 ? args.tgt[item.e0] : 0;
+            li += ((li & 1) ^ grp) & 1;
+            for (; it < i1; it += 2, li += 2) {
                 const int s = li & 1;
                 const uint32_t par = ((li >> 1) & 1) ^ 1;
                 const int cnt = item.cnt;
                 const float *xrow = args.Xq + (int64_t)(slot >= 0 ? slot : 0) * args.ldq;
                 const float *xt0 = args.Xq + (int64_t)first * args.ldq;
                 const bool has_tgt = slot >= 0;
-                // prefetch the next item of the block (its entries follow this item's)
-                if (it + 1 < i1) {
-                    item = args.items[it + 1];
+                // prefetch this group's next item of the block
+                if (it + 2 < i1) {
+                    item = args.items[it + 2];
                     slot = t < item.cnt ? args.tgt[item.e0 + t] : -1;
                     first = args.tgt[item.e0];
                 }
@@ -376,11 +384,13 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(BAR_A_FULL(s));
             }
+            // li now points past this block for this group; realign to the block end
+            li = li_block_end;
         }
     loader_done:;
-    } else if (warp < 8) {
+    } else if (warp < 12) {
         // ----------------------------------------------------------- epilogue
-        const int row = tid - 128;                 // TMEM lane = target row of the item
+        const int row = tid - 256;                 // TMEM lane = target row of the item
         const int q = warp & 3;                    // this warp's TMEM lane quadrant
         int li = 0;
         for (int ci = args.cta_off[blockIdx.x]; ci < args.cta_off[blockIdx.x + 1] && !*abort_flag; ++ci) {
@@ -483,7 +493,7 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 8) {
+    if (warp == 12) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
