@@ -199,6 +199,33 @@ askit_status askit_destroy(askit_tree t);
 const char *askit_status_string(askit_status s);
 const char *askit_last_error(void);
 
+/*
+ * Exact kNN without allocating device memory.  The paper has no counterpart:
+ * this is a library service for callers that cannot call cudaMalloc -- for
+ * instance a serving process that reserves its device memory once, up front,
+ * for the resident tree and its request buffers and must not grow afterwards,
+ * or a latency-critical caller that cannot afford cudaMalloc's implicit
+ * device synchronization.
+ *
+ * Same result as the exact kNN of askit_setup (knn_mode 0): for each query
+ * the kappa smallest (D, id) over the N points, D the FP64 squared distance
+ * summed in coordinate order, ties by the smaller id.
+ *   X_dev   [N, d] FP32 points, rows contiguous (stride d).
+ *   Y_dev   [Q, d] FP32 queries (stride d), or NULL: the queries are the N
+ *           points themselves (Q must equal N) and each excludes itself.
+ *   ids_dev [Q, kappa] int32 and dist_dev [Q, kappa] double receive the
+ *           neighbors, nearest first.  All buffers are caller-owned.
+ * Limits: Q <= 8192 per call (INVALID_ARG beyond), 1 <= kappa <= 32,
+ * d <= 1536.  Scratch: a fixed 3 MiB device array inside the library,
+ * resident on every GPU that loads it until the process exits.  The first
+ * call on a device looks up that array's device address (so make the first
+ * call before any stream capture); every call shares the array, so calls
+ * that overlap on the GPU race and must be serialized by the caller.
+ * Enqueues on `stream` and returns without waiting.
+ */
+askit_status askit_knn_noalloc(const float *X_dev, int64_t N, int32_t d, const float *Y_dev, int64_t Q,
+                               int32_t kappa, int32_t *ids_dev, double *dist_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

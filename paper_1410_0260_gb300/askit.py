@@ -28,7 +28,7 @@ BW_CONSTANT, BW_ARRAY, BW_KNN = 0, 1, 2
 EXPORTS = ["askit_default_params", "askit_setup", "askit_set_weights", "askit_evaluate",
            "askit_evaluate_targets", "askit_evaluate_host", "askit_set_precision", "askit_get_info",
            "askit_get_structure", "askit_sync", "askit_destroy", "askit_status_string",
-           "askit_last_error"]
+           "askit_last_error", "askit_knn_noalloc"]
 
 
 class AskitError(RuntimeError):
@@ -73,6 +73,7 @@ def load(path: str | None = None):
             L.askit_get_structure.argtypes = [V, I32, V, C.c_size_t]
             L.askit_sync.argtypes = [V, V]
             L.askit_destroy.argtypes = [V]
+            L.askit_knn_noalloc.argtypes = [V, I64, I32, V, I64, I32, V, V, V]
             L.askit_status_string.restype = C.c_char_p
             L.askit_status_string.argtypes = [C.c_int]
             L.askit_last_error.restype = C.c_char_p

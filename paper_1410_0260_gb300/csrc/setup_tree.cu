@@ -11,6 +11,8 @@
 #include <float.h>
 #include <limits.h>
 
+#include <mutex>
+
 #include "askit_impl.cuh"
 
 namespace {
@@ -464,6 +466,130 @@ askit_status knn_rp_gpu(const float *X, int64_t N, int d, int kappa, int iters, 
 askit_status knn_dist_gpu(const float *X, int64_t N, int d, int kappa, const int32_t *ids,
                           double *dist, cudaStream_t s) {
     knn_dist_kernel<<<nblk(N * kappa, 256), 256, 0, s>>>(X, N, d, kappa, ids, dist);
+    ASK_LAUNCH();
+    return ASKIT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free exact kNN (askit_knn_noalloc).
+//
+// The per-query best-32 lists live in this file-scope device array instead
+// of memory from cudaMalloc: KNN_NOALLOC_MAX_Q queries x 32 slots x (8-byte
+// distance + 4-byte id) = 3 MiB, held by every GPU that loads the library
+// until the process exits.  Every call reuses it, so each call first resets
+// the lists it uses, and calls that overlap on the GPU (on different
+// streams, or from different threads) race on it.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t KNN_NOALLOC_MAX_Q = 8192;
+constexpr int KNN_NOALLOC_QPB = 64;   // queries per block
+static __device__ __align__(256) unsigned char g_knn_scratch[KNN_NOALLOC_MAX_Q * 32 * (sizeof(double) + sizeof(int))];
+
+// Host-side address of g_knn_scratch on each device (the array's name is
+// only a host stand-in; kernels must be given the device address).
+std::mutex g_knn_scratch_mu;
+void *g_knn_scratch_dev[64] = {nullptr};
+
+askit_status knn_scratch_address(void **out) {
+    int dev = 0;
+    ASK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        askit_set_error("device ordinal %d out of range for the allocation-free kNN", dev);
+        return ASKIT_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_knn_scratch_mu);
+    if (!g_knn_scratch_dev[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_knn_scratch);
+        if (e != cudaSuccess || !p) {
+            askit_set_error("cudaGetSymbolAddress(knn scratch): %s", cudaGetErrorString(e));
+            return ASKIT_ERR_CUDA;
+        }
+        g_knn_scratch_dev[dev] = p;
+    }
+    *out = g_knn_scratch_dev[dev];
+    return ASKIT_OK;
+}
+
+// Exhaustive search of all N points for queries [64 b, 64 b + 64): one warp
+// per query; Y == nullptr means the queries are the points themselves (self
+// excluded).  Same FP64 distance and (D, id) order as the setup's kNN.
+__global__ void knn_noalloc_kernel(const float *X, int64_t N, int d, const float *Y, int64_t Q, double *bd,
+                                   int *bi, int kappa) {
+    extern __shared__ float sq[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t q0 = (int64_t)blockIdx.x * KNN_NOALLOC_QPB;
+    const int64_t q1 = q0 + KNN_NOALLOC_QPB < Q ? q0 + KNN_NOALLOC_QPB : Q;
+    float *myq = sq + (int64_t)warp * d;
+    for (int64_t q = q0 + warp; q < q1; q += nw) {
+        const int64_t self = Y ? -1 : q;
+        const float *xq = Y ? Y + q * d : X + q * d;
+        for (int k = lane; k < d; k += 32) myq[k] = xq[k];
+        __syncwarp();
+        double ld = bd[q * 32 + lane];
+        int li = bi[q * 32 + lane];
+        for (int64_t cb = 0; cb < N; cb += 32) {
+            double cd = DBL_MAX;
+            int ci = INT_MAX;
+            if (cb + lane < N && cb + lane != self) {
+                const float *xj = X + (cb + lane) * d;
+                double acc = 0.0;
+                for (int k = 0; k < d; ++k) {
+                    double t = c_sub((double)myq[k], (double)xj[k]);
+                    acc = c_add(acc, c_mul(t, t));
+                }
+                cd = acc;
+                ci = (int)(cb + lane);
+            }
+            warp_offer(ld, li, cd, ci, kappa, false, lane);
+        }
+        bd[q * 32 + lane] = ld;
+        bi[q * 32 + lane] = li;
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+extern "C" askit_status askit_knn_noalloc(const float *X_dev, int64_t N, int32_t d, const float *Y_dev, int64_t Q,
+                                          int32_t kappa, int32_t *ids_dev, double *dist_dev, void *stream) {
+    if (!X_dev || !ids_dev || !dist_dev) {
+        askit_set_error("X_dev, ids_dev and dist_dev must be non-NULL");
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    if (N < 1 || d < 1 || Q < 1 || kappa < 1 || kappa > 32) {
+        askit_set_error("need N >= 1, d >= 1, Q >= 1 and 1 <= kappa <= 32");
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    if (Q > KNN_NOALLOC_MAX_Q) {
+        askit_set_error("askit_knn_noalloc handles at most %lld queries per call (got %lld)",
+                        (long long)KNN_NOALLOC_MAX_Q, (long long)Q);
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    if (!Y_dev && Q != N) {
+        askit_set_error("with Y_dev == NULL the queries are the N points: Q must equal N");
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    if (kappa > (Y_dev ? N : N - 1)) {
+        askit_set_error("kappa exceeds the number of candidate neighbors");
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    if ((size_t)8 * d * sizeof(float) > 48 * 1024) {
+        askit_set_error("askit_knn_noalloc handles d <= %d", (int)(48 * 1024 / (8 * sizeof(float))));
+        return ASKIT_ERR_UNSUPPORTED;
+    }
+    void *scratch = nullptr;
+    ASK_TRY(knn_scratch_address(&scratch));
+    double *bd = static_cast<double *>(scratch);
+    int *bi = reinterpret_cast<int *>(bd + KNN_NOALLOC_MAX_Q * 32);
+    cudaStream_t s = (cudaStream_t)stream;
+    // the array keeps the previous call's lists: reset the ones used here
+    fill_kernel<double><<<nblk(Q * 32, 256), 256, 0, s>>>(bd, Q * 32, DBL_MAX);
+    fill_kernel<int><<<nblk(Q * 32, 256), 256, 0, s>>>(bi, Q * 32, INT_MAX);
+    knn_noalloc_kernel<<<(unsigned)((Q + KNN_NOALLOC_QPB - 1) / KNN_NOALLOC_QPB), 256, 8 * d * sizeof(float), s>>>(
+        X_dev, N, d, Y_dev, Q, bd, bi, kappa);
+    knn_extract_kernel<<<nblk(Q * kappa, 256), 256, 0, s>>>(bd, bi, Q, kappa, ids_dev, dist_dev);
     ASK_LAUNCH();
     return ASKIT_OK;
 }
