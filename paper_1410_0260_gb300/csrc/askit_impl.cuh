@@ -315,6 +315,6 @@ askit_status upward_weights(askit_tree t, const float *W, int r, int64_t ldw, cu
 // eval_simt.cu / eval_tc.cu: partial[e * r + z] for every entry e of w
 askit_status eval_simt(askit_tree t, const float *Xq, int64_t ldq, const WorkLists &w, float *partial,
                        cudaStream_t s);
-askit_status eval_tc(askit_tree t, int precision, const float *Xq, int64_t ldq, const WorkLists &w,
-                     float *partial, cudaStream_t s);
+askit_status eval_tc(askit_tree t, int precision, const float *Xq, int64_t ldq, int64_t q_rows,
+                     const WorkLists &w, float *partial, cudaStream_t s);
 void eval_tc_free(askit_tree t);

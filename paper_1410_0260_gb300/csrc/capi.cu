@@ -220,12 +220,13 @@ askit_status setup_impl(askit_tree t, const float *X_dev, int64_t ldx, const flo
 
 // Evaluate over one set of work lists: every (target, sub-block) entry's
 // partial sum, then each target's entries summed in their fixed order.
-askit_status run_eval(askit_tree t, int precision, const float *Xq, int64_t ldq, const WorkLists &w,
-                      float *partial, const int32_t *out_rows, float *U, int64_t ldu, cudaStream_t s) {
+askit_status run_eval(askit_tree t, int precision, const float *Xq, int64_t ldq, int64_t q_rows,
+                      const WorkLists &w, float *partial, const int32_t *out_rows, float *U, int64_t ldu,
+                      cudaStream_t s) {
     if (precision == ASKIT_PREC_SIMT_FP32)
         ASK_TRY(eval_simt(t, Xq, ldq, w, partial, s));
     else
-        ASK_TRY(eval_tc(t, precision, Xq, ldq, w, partial, s));
+        ASK_TRY(eval_tc(t, precision, Xq, ldq, q_rows, w, partial, s));
     return reduce_partials(w, partial, t->r, out_rows, U, ldu, s);
 }
 
@@ -337,7 +338,7 @@ askit_status askit_evaluate(askit_tree t, float *U_dev, int64_t ldu, void *strea
     if (!t || !U_dev) { askit_set_error("tree and U_dev must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
     if (!t->weights_ready) { askit_set_error("askit_set_weights has not been called"); return ASKIT_ERR_NOT_READY; }
     if (ldu < t->r) { askit_set_error("ldu < r"); return ASKIT_ERR_INVALID_ARG; }
-    return run_eval(t, t->precision, t->Xt, t->d_pad, t->wl, t->partial, t->perm, U_dev, ldu,
+    return run_eval(t, t->precision, t->Xt, t->d_pad, t->N_pad, t->wl, t->partial, t->perm, U_dev, ldu,
                     (cudaStream_t)stream);
 }
 
@@ -381,7 +382,7 @@ askit_status askit_evaluate_targets(askit_tree t, const float *Y_dev, int64_t T,
     OTRY(oos_prune_sets(t, ids_s, T, kappa, sets, s));
     OTRY(build_work_lists(t, sets, kappa, T, w, tmp, s));
     OTRY(tmp.alloc(&partial, (size_t)w.n_entries * t->r));
-    OTRY(run_eval(t, t->precision, Yt, t->d_pad, w, partial, order, U_dev, ldu, s));
+    OTRY(run_eval(t, t->precision, Yt, t->d_pad, T_pad, w, partial, order, U_dev, ldu, s));
     if (cudaStreamSynchronize(s) != cudaSuccess) { askit_set_error("out-of-sample evaluate: %s", cudaGetErrorString(cudaGetLastError())); rc = ASKIT_ERR_CUDA; }
 out:
 #undef OTRY

@@ -40,7 +40,7 @@
 
 namespace {
 
-constexpr int TC_THREADS = 416;
+constexpr int TC_THREADS = 448;
 constexpr int TILE_ROWS = 128;                  // M = N = 128
 constexpr int REGION = TILE_ROWS * 128;         // one 128-row x 128-byte swizzled region (16 KB)
 constexpr uint32_t TMEM_COLS = 256;             // two 128-column FP32 accumulators
@@ -122,6 +122,17 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// Four rows (r0..r3) of a 2D FP32 tensor, one box row each, into consecutive
+// box rows at dst (tile::gather4).
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap *map, int x, int r0, int r1, int r2,
+                                            int r3, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(bar)
+        : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
@@ -172,16 +183,22 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // Shared-memory plan (offsets from a 1024-byte aligned base).
 template <int P>
 struct Smem {
+    // the 16-bit splits have room to stage raw rows: targets are then gathered
+    // by TMA (tile::gather4) and the loaders work from shared memory only
+    static constexpr bool GATHER = P != ASKIT_PREC_TF32X3;
     static constexpr int OPB = Prec<P>::NREG * REGION;    // one operand (hi or lo) of one tile
     static constexpr int B_HI = 0, B_LO = OPB;
     static constexpr int A0 = 2 * OPB;                     // stage s: hi at A0 + s*2*OPB, lo at + OPB
     static constexpr int TILES = 6 * OPB;
-    static constexpr int ANORM = TILES;                    // float [2][128] |a|^2 + 2 a.delta per target row
+    static constexpr int RAWSTAGE = TILE_ROWS * TC_K * 4;  // one stage of gathered FP32 target rows
+    static constexpr int RAW = TILES;                      // [2] stages (GATHER)
+    static constexpr int RAWB = RAW + (GATHER ? 2 * RAWSTAGE : 0);        // raw FP32 source rows (GATHER)
+    static constexpr int ANORM = RAWB + (GATHER ? RAWSTAGE : 0);          // float [2][128] |a|^2 + 2 a.delta
     static constexpr int COLV = ANORM + 2 * 128 * 4;       // float4 [2][128] per source row {2 u sc, -sc q, -sc, w_0}
     static constexpr int RC_MAX = 16;
     static constexpr int COLW = COLV + 2 * 128 * 16;       // float [2][128][RC_MAX] weights (r > 1)
-    static constexpr int BAR = COLW + 2 * 128 * RC_MAX * 4;   // 10 mbarriers
-    static constexpr int MISC = BAR + 10 * 8;              // tmem address, abort flag
+    static constexpr int BAR = COLW + 2 * 128 * RC_MAX * 4;   // 14 mbarriers
+    static constexpr int MISC = BAR + 14 * 8;              // tmem address, abort flag
     static constexpr int BYTES = MISC + 16;
 };
 
@@ -208,7 +225,8 @@ template <int P, int RC>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_constant__ CUtensorMap map_t_lo,
                const __grid_constant__ CUtensorMap map_s_hi, const __grid_constant__ CUtensorMap map_s_lo,
-               const TcArgs args) {
+               const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_rt,
+               const __grid_constant__ CUtensorMap map_rs, const TcArgs args) {
     using S = Smem<P>;
     constexpr int EB = Prec<P>::EB, NREG = Prec<P>::NREG, KSTEPS = Prec<P>::KSTEPS;
     constexpr uint32_t IDESC = make_idesc(Prec<P>::FMT, TILE_ROWS, TILE_ROWS);
@@ -224,6 +242,8 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
     const uint32_t BAR_B_FULL = bar0 + 8 * 4, BAR_B_EMPTY = bar0 + 8 * 5;
     auto BAR_T_FULL = [&](int a) { return bar0 + 8 * (6 + a); };
     auto BAR_T_EMPTY = [&](int a) { return bar0 + 8 * (8 + a); };
+    auto BAR_R_FULL = [&](int a) { return bar0 + 8 * (10 + a); };    // gathered target rows landed
+    auto BAR_R_EMPTY = [&](int a) { return bar0 + 8 * (12 + a); };   // loader done with the raw stage
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + S::MISC);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + S::MISC + 4);
 
@@ -239,6 +259,10 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
         mbar_init(BAR_T_FULL(1), 1);
         mbar_init(BAR_T_EMPTY(0), 128);
         mbar_init(BAR_T_EMPTY(1), 128);
+        mbar_init(BAR_R_FULL(0), 1);
+        mbar_init(BAR_R_FULL(1), 1);
+        mbar_init(BAR_R_EMPTY(0), 128);
+        mbar_init(BAR_R_EMPTY(1), 128);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -259,7 +283,7 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
         const int grp = warp >> 2;
         const int t = tid & 127;
         const int nk4 = args.d_pad / 4;            // 16-byte chunks of a coordinate row
-        int li = 0;
+        int li = 0, lb = 0;
         for (int ci = args.cta_off[blockIdx.x]; ci < args.cta_off[blockIdx.x + 1] && !*abort_flag; ++ci) {
             const int b = args.cta_blocks[ci];
             const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
@@ -275,6 +299,7 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
             const float sc = has_src ? __ldg((far ? args.sc_s : args.sc_t) + srow) : 0.f;
             const float *wrow = (far ? args.Ws : args.Wt) + srow * args.r;
             const float w0 = has_src ? __ldg(wrow) : 0.f;
+            bool waited_b = false;   // B_FULL of this block waited (gather path)
             // this group's first item of the block
             int it = i0 + (((li & 1) ^ grp) & 1);
             if (it < i1) item = args.items[it];
@@ -299,6 +324,66 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                 uint8_t *ahi = sm + S::A0 + s * 2 * S::OPB;
                 uint8_t *alo = ahi + S::OPB;
                 float nn = 0.f, dd = 0.f, qq = 0.f;
+                if constexpr (S::GATHER) {
+                    // gathered target rows (stage s) and the sub-block's raw rows
+                    if (!mbar_wait(BAR_R_FULL(s), (li >> 1) & 1, abort_flag, args.status)) goto loader_done;
+                    if (!waited_b) {
+                        if (!mbar_wait(BAR_B_FULL, lb & 1, abort_flag, args.status)) goto loader_done;
+                        waited_b = true;
+                    }
+                    const float *raw = reinterpret_cast<const float *>(sm + S::RAW + s * S::RAWSTAGE);
+                    const float *rawb = reinterpret_cast<const float *>(sm + S::RAWB);
+                    const int dp = args.d_pad;
+#pragma unroll 4
+                    for (int j = 0; j < TC_K / 4; ++j) {
+                        // chunks in an order rotated by the row: conflict-free shared loads
+                        const int k4 = (j + t) & (nk4 - 1);
+                        float xa[4] = {0.f, 0.f, 0.f, 0.f};
+                        int kst = j;   // chunk to store (zeros past d_pad)
+                        if (j < nk4) {
+                            kst = k4;
+                            const float4 tt = *reinterpret_cast<const float4 *>(raw + 4 * k4);   // c_T = row 0
+                            const float4 bb = *reinterpret_cast<const float4 *>(cB + 4 * k4);
+                            const float4 xx = has_tgt ? *reinterpret_cast<const float4 *>(raw + t * dp + 4 * k4) : tt;
+                            const float4 yy = has_src ? *reinterpret_cast<const float4 *>(rawb + t * dp + 4 * k4) : tt;
+                            const float ts[4] = {tt.x, tt.y, tt.z, tt.w}, bs[4] = {bb.x, bb.y, bb.z, bb.w};
+                            const float xs[4] = {xx.x, xx.y, xx.z, xx.w}, ys[4] = {yy.x, yy.y, yy.z, yy.w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                xa[e] = xs[e] - ts[e];
+                                nn = fmaf(xa[e], xa[e], nn);
+                                dd = fmaf(xa[e], ts[e] - bs[e], dd);
+                                const float ya = ys[e] - ts[e];
+                                qq = fmaf(ya, ya, qq);
+                            }
+                        }
+                        // 4 elements = 8 bytes of the 128-byte row
+                        uint32_t hv[2], lv[2];
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            float v0 = xa[2 * e], v1 = xa[2 * e + 1];
+                            uint16_t h0, h1, l0, l1;
+                            if constexpr (P == ASKIT_PREC_FP16X3) {
+                                v0 *= args.f16_scale; v1 *= args.f16_scale;
+                                const __half a0 = __float2half_rn(v0), a1 = __float2half_rn(v1);
+                                h0 = __half_as_ushort(a0); h1 = __half_as_ushort(a1);
+                                l0 = __half_as_ushort(__float2half_rn(v0 - __half2float(a0)));
+                                l1 = __half_as_ushort(__float2half_rn(v1 - __half2float(a1)));
+                            } else {
+                                const __nv_bfloat16 a0 = __float2bfloat16_rn(v0), a1 = __float2bfloat16_rn(v1);
+                                h0 = __bfloat16_as_ushort(a0); h1 = __bfloat16_as_ushort(a1);
+                                l0 = __bfloat16_as_ushort(__float2bfloat16_rn(v0 - __bfloat162float(a0)));
+                                l1 = __bfloat16_as_ushort(__float2bfloat16_rn(v1 - __bfloat162float(a1)));
+                            }
+                            hv[e] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                            lv[e] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+                        }
+                        const int off = t * 128 + (((kst >> 1) ^ (t & 7)) << 4) + (kst & 1) * 8;
+                        *reinterpret_cast<uint2 *>(ahi + off) = make_uint2(hv[0], hv[1]);
+                        *reinterpret_cast<uint2 *>(alo + off) = make_uint2(lv[0], lv[1]);
+                    }
+                    if (!has_tgt) nn = dd = 0.f;
+                } else {
                 // two 4-column chunks per step: 32 contiguous bytes of a row
 #pragma unroll 4
                 for (int k8 = 0; k8 < TC_K / 8; ++k8) {
@@ -370,6 +455,7 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                         *reinterpret_cast<uint4 *>(alo + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
                     }
                 }
+                }
                 (void)cnt;
                 // row term |a|^2 + 2 a.delta; column data of source row t:
                 // arg = g (2 u sc) + (-sc) p_t + (-sc q) = -sc (p_t + q - 2 u g)
@@ -383,9 +469,11 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                 // generic-proxy stores -> visible to the tensor core's async proxy
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(BAR_A_FULL(s));
+                if constexpr (S::GATHER) mbar_arrive(BAR_R_EMPTY(s));
             }
             // li now points past this block for this group; realign to the block end
             li = li_block_end;
+            ++lb;
         }
     loader_done:;
     } else if (warp < 12) {
@@ -440,9 +528,36 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
             }
         }
     epi_done:;
-    } else if (lane == 0) {
+    } else if (warp == 13) {
+        // ---------------------------------------------- target-row gatherer (warp 13)
+        if constexpr (S::GATHER) {
+            const uint32_t bytes = (uint32_t)(TILE_ROWS * args.d_pad * 4);
+            int li = 0;
+            for (int ci = args.cta_off[blockIdx.x]; ci < args.cta_off[blockIdx.x + 1] && !*abort_flag; ++ci) {
+                const int b = args.cta_blocks[ci];
+                for (int it = args.block_off[b]; it < args.block_off[b + 1]; ++it, ++li) {
+                    const int s = li & 1;
+                    if (!mbar_wait(BAR_R_EMPTY(s), ((li >> 1) & 1) ^ 1, abort_flag, args.status)) goto gather_done;
+                    const EvalItem item = args.items[it];
+                    const int first = args.tgt[item.e0];
+                    int r[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int row = 4 * lane + i;   // rows past cnt repeat the first target
+                        r[i] = row < item.cnt ? args.tgt[item.e0 + row] : first;
+                    }
+                    if (lane == 0) mbar_expect_tx(BAR_R_FULL(s), bytes);
+                    __syncwarp();
+                    tma_gather4(sbase + S::RAW + s * S::RAWSTAGE + 4 * lane * args.d_pad * 4, &map_q, 0, r[0], r[1],
+                                r[2], r[3], BAR_R_FULL(s));
+                }
+            }
+        gather_done:;
+        }
+    } else if (warp == 12 && lane == 0) {
         // ------------------------------------------------- TMA + MMA issuer
-        constexpr int TX = 2 * NREG * REGION;      // hi + lo of one 128-row sub-block
+        // hi + lo of one 128-row sub-block, and its raw FP32 rows (gather path)
+        const uint32_t TX = 2 * NREG * REGION + (S::GATHER ? (uint32_t)(TILE_ROWS * args.d_pad * 4) : 0u);
         int li = 0, lb = 0;
         for (int ci = args.cta_off[blockIdx.x]; ci < args.cta_off[blockIdx.x + 1] && !*abort_flag; ++ci, ++lb) {
             const int b = args.cta_blocks[ci];
@@ -458,6 +573,8 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                 tma_load_2d(sbase + S::B_HI + g * REGION, mh, x, first.row0, BAR_B_FULL);
                 tma_load_2d(sbase + S::B_LO + g * REGION, ml, x, first.row0, BAR_B_FULL);
             }
+            if constexpr (S::GATHER)
+                tma_load_2d(sbase + S::RAWB, far ? &map_rs : &map_rt, 0, first.row0, BAR_B_FULL);
             const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
             for (int it = i0; it < i1; ++it, ++li) {
                 const int s = li & 1;
@@ -503,6 +620,9 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
 struct TcState {
     CUtensorMap map[3][4];   // [precision: 0 tf32, 1 bf16, 2 fp16][t_hi, t_lo, s_hi, s_lo]
     bool ready[3] = {false, false, false};
+    CUtensorMap raw_t, raw_s;   // raw FP32 source rows, 128-row boxes (gather path)
+    bool raw_ready = false;
+    void *encode = nullptr;     // cuTensorMapEncodeTiled
 };
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -527,10 +647,27 @@ askit_status encode_map(EncodeTiledFn fn, CUtensorMap *m, void *base, int64_t ro
     return ASKIT_OK;
 }
 
+// Unswizzled FP32 map over [rows, cols] with boxes of box_rows full rows
+// (box_rows = 1 for tile::gather4).
+askit_status encode_raw(EncodeTiledFn fn, CUtensorMap *m, const void *base, int64_t rows, int cols, int box_rows) {
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 4};
+    cuuint32_t box[2] = {(cuuint32_t)cols, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        askit_set_error("cuTensorMapEncodeTiled (raw rows) failed (%d)", (int)r);
+        return ASKIT_ERR_CUDA;
+    }
+    return ASKIT_OK;
+}
+
 askit_status tc_state(askit_tree t, int pi, TcState **out) {
     if (!t->tc) t->tc = new TcState();
     TcState *st = (TcState *)t->tc;
-    if (!st->ready[pi]) {
+    if (!st->encode) {
         void *fnp = nullptr;
         cudaDriverEntryPointQueryResult q;
         ASK_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fnp, 12000, cudaEnableDefault, &q));
@@ -538,7 +675,15 @@ askit_status tc_state(askit_tree t, int pi, TcState **out) {
             askit_set_error("cuTensorMapEncodeTiled not available");
             return ASKIT_ERR_CUDA;
         }
-        EncodeTiledFn fn = (EncodeTiledFn)fnp;
+        st->encode = fnp;
+    }
+    EncodeTiledFn fn = (EncodeTiledFn)st->encode;
+    if (!st->raw_ready) {
+        ASK_TRY(encode_raw(fn, &st->raw_t, t->Xt, t->N_pad, t->d_pad, TILE_ROWS));
+        ASK_TRY(encode_raw(fn, &st->raw_s, t->Xs, t->srows, t->d_pad, TILE_ROWS));
+        st->raw_ready = true;
+    }
+    if (!st->ready[pi]) {
         const int ty = pi;   // 0 fp32 (tf32), 1 bf16, 2 fp16
         void *th = pi == 0 ? (void *)t->Xt_hi : pi == 1 ? (void *)t->Xt_bhi : (void *)t->Xt_hhi;
         void *tl = pi == 0 ? (void *)t->Xt_lo : pi == 1 ? (void *)t->Xt_blo : (void *)t->Xt_hlo;
@@ -555,7 +700,8 @@ askit_status tc_state(askit_tree t, int pi, TcState **out) {
 }
 
 template <int P, int RC>
-askit_status launch(askit_tree t, TcState *st, const TcArgs &a, int a_grid, cudaStream_t s) {
+askit_status launch(askit_tree t, TcState *st, const CUtensorMap &map_q, const TcArgs &a, int a_grid,
+                    cudaStream_t s) {
     using S = Smem<P>;
     const int pi = P == ASKIT_PREC_TF32X3 ? 0 : P == ASKIT_PREC_BF16X3 ? 1 : 2;
     const size_t smem = S::BYTES + 1024;
@@ -566,15 +712,15 @@ askit_status launch(askit_tree t, TcState *st, const TcArgs &a, int a_grid, cuda
     }
     const unsigned grid = (unsigned)a_grid;
     eval_tc_kernel<P, RC><<<grid, TC_THREADS, smem, s>>>(st->map[pi][0], st->map[pi][1], st->map[pi][2],
-                                                         st->map[pi][3], a);
+                                                         st->map[pi][3], map_q, st->raw_t, st->raw_s, a);
     ASK_LAUNCH();
     return ASKIT_OK;
 }
 
 }  // namespace
 
-askit_status eval_tc(askit_tree t, int precision, const float *Xq, int64_t ldq, const WorkLists &w,
-                     float *partial, cudaStream_t s) {
+askit_status eval_tc(askit_tree t, int precision, const float *Xq, int64_t ldq, int64_t q_rows,
+                     const WorkLists &w, float *partial, cudaStream_t s) {
     if (t->d > TC_K) {
         askit_set_error("tensor-core evaluation covers d <= %d; use ASKIT_PREC_SIMT_FP32", TC_K);
         return ASKIT_ERR_UNSUPPORTED;
@@ -584,8 +730,15 @@ askit_status eval_tc(askit_tree t, int precision, const float *Xq, int64_t ldq, 
         return ASKIT_ERR_UNSUPPORTED;
     }
     if (w.n_blocks == 0) return ASKIT_OK;
+    if (ldq != t->d_pad) {
+        askit_set_error("target rows must have d_pad columns");
+        return ASKIT_ERR_INVALID_ARG;
+    }
     TcState *st = nullptr;
     ASK_TRY(tc_state(t, precision == ASKIT_PREC_TF32X3 ? 0 : precision == ASKIT_PREC_BF16X3 ? 1 : 2, &st));
+    // gather map over this call's target rows (one box row per gathered row)
+    CUtensorMap map_q;
+    ASK_TRY(encode_raw((EncodeTiledFn)st->encode, &map_q, Xq, q_rows, t->d_pad, 1));
     TcArgs a;
     a.items = w.items;
     a.block_off = w.block_off;
@@ -608,18 +761,18 @@ askit_status eval_tc(askit_tree t, int precision, const float *Xq, int64_t ldq, 
     a.f16_scale = precision == ASKIT_PREC_FP16X3 ? t->f16_scale : 1.f;
     a.g_unscale = 1.f / (a.f16_scale * a.f16_scale);
     if (precision == ASKIT_PREC_TF32X3) {
-        if (t->r == 1) return launch<ASKIT_PREC_TF32X3, 1>(t, st, a, w.n_ctas, s);
-        if (t->r <= 4) return launch<ASKIT_PREC_TF32X3, 4>(t, st, a, w.n_ctas, s);
-        return launch<ASKIT_PREC_TF32X3, 16>(t, st, a, w.n_ctas, s);
+        if (t->r == 1) return launch<ASKIT_PREC_TF32X3, 1>(t, st, map_q, a, w.n_ctas, s);
+        if (t->r <= 4) return launch<ASKIT_PREC_TF32X3, 4>(t, st, map_q, a, w.n_ctas, s);
+        return launch<ASKIT_PREC_TF32X3, 16>(t, st, map_q, a, w.n_ctas, s);
     }
     if (precision == ASKIT_PREC_BF16X3) {
-        if (t->r == 1) return launch<ASKIT_PREC_BF16X3, 1>(t, st, a, w.n_ctas, s);
-        if (t->r <= 4) return launch<ASKIT_PREC_BF16X3, 4>(t, st, a, w.n_ctas, s);
-        return launch<ASKIT_PREC_BF16X3, 16>(t, st, a, w.n_ctas, s);
+        if (t->r == 1) return launch<ASKIT_PREC_BF16X3, 1>(t, st, map_q, a, w.n_ctas, s);
+        if (t->r <= 4) return launch<ASKIT_PREC_BF16X3, 4>(t, st, map_q, a, w.n_ctas, s);
+        return launch<ASKIT_PREC_BF16X3, 16>(t, st, map_q, a, w.n_ctas, s);
     }
-    if (t->r == 1) return launch<ASKIT_PREC_FP16X3, 1>(t, st, a, w.n_ctas, s);
-    if (t->r <= 4) return launch<ASKIT_PREC_FP16X3, 4>(t, st, a, w.n_ctas, s);
-    return launch<ASKIT_PREC_FP16X3, 16>(t, st, a, w.n_ctas, s);
+    if (t->r == 1) return launch<ASKIT_PREC_FP16X3, 1>(t, st, map_q, a, w.n_ctas, s);
+    if (t->r <= 4) return launch<ASKIT_PREC_FP16X3, 4>(t, st, map_q, a, w.n_ctas, s);
+    return launch<ASKIT_PREC_FP16X3, 16>(t, st, map_q, a, w.n_ctas, s);
 }
 
 void eval_tc_free(askit_tree t) {
