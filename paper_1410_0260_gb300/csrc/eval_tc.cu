@@ -133,6 +133,13 @@ __device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// Plain bulk copy global -> shared (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
@@ -193,8 +200,9 @@ struct Smem {
     static constexpr int RAWSTAGE = TILE_ROWS * TC_K * 4;  // one stage of gathered FP32 target rows
     static constexpr int RAW = TILES;                      // [2] stages (GATHER)
     static constexpr int RAWB = RAW + (GATHER ? 2 * RAWSTAGE : 0);        // raw FP32 source rows (GATHER)
-    static constexpr int ANORM = RAWB + (GATHER ? RAWSTAGE : 0);          // float [2][128] |a|^2 + 2 a.delta
-    static constexpr int COLV = ANORM + 2 * 128 * 4;       // float4 [2][128] per source row {2 u sc, -sc q, -sc, w_0}
+    static constexpr int CENT = RAWB + (GATHER ? RAWSTAGE : 0);           // float [TC_K] c_B of the sub-block
+    static constexpr int ANORM = CENT + TC_K * 4;                         // float [2][128] |a|^2 + 2 a.delta
+    static constexpr int COLV = ANORM + 2 * 128 * 4;       // float4 [2][128]: per source pair {A, B}, {C, w} (see loader)
     static constexpr int RC_MAX = 16;
     static constexpr int COLW = COLV + 2 * 128 * 16;       // float [2][128][RC_MAX] weights (r > 1)
     static constexpr int BAR = COLW + 2 * 128 * RC_MAX * 4;   // 14 mbarriers
@@ -303,8 +311,8 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
             // this group's first item of the block
             int it = i0 + (((li & 1) ^ grp) & 1);
             if (it < i1) item = args.items[it];
-            int slot = (it < i1 && t < item.cnt) ? args.tgt[item.e0 + t] : -1;
-            int first = it < i1 ? args.tgt[item.e0] : 0;
+            int slot = (it < i1 && t < item.cnt) ? (S::GATHER ? 0 : args.tgt[item.e0 + t]) : -1;
+            int first = (it < i1 && !S::GATHER) ? args.tgt[item.e0] : 0;
             li += ((li & 1) ^ grp) & 1;
             for (; it < i1; it += 2, li += 2) {
                 const int s = li & 1;
@@ -313,11 +321,16 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                 const float *xrow = args.Xq + (int64_t)(slot >= 0 ? slot : 0) * args.ldq;
                 const float *xt0 = args.Xq + (int64_t)first * args.ldq;
                 const bool has_tgt = slot >= 0;
-                // prefetch this group's next item of the block
+                // prefetch this group's next item of the block (the gather path
+                // needs only its size: the gather warp fetches the rows)
                 if (it + 2 < i1) {
                     item = args.items[it + 2];
-                    slot = t < item.cnt ? args.tgt[item.e0 + t] : -1;
-                    first = args.tgt[item.e0];
+                    if constexpr (!S::GATHER) {
+                        slot = t < item.cnt ? args.tgt[item.e0 + t] : -1;
+                        first = args.tgt[item.e0];
+                    } else {
+                        slot = t < item.cnt ? 0 : -1;
+                    }
                 }
                 if (!mbar_wait(BAR_A_EMPTY(s), par, abort_flag, args.status)) goto loader_done;
                 if (!mbar_wait(BAR_T_EMPTY(s), par, abort_flag, args.status)) goto loader_done;
@@ -333,6 +346,7 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                     }
                     const float *raw = reinterpret_cast<const float *>(sm + S::RAW + s * S::RAWSTAGE);
                     const float *rawb = reinterpret_cast<const float *>(sm + S::RAWB);
+                    const float *cBs = reinterpret_cast<const float *>(sm + S::CENT);
                     const int dp = args.d_pad;
 #pragma unroll 4
                     for (int j = 0; j < TC_K / 4; ++j) {
@@ -343,7 +357,7 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                         if (j < nk4) {
                             kst = k4;
                             const float4 tt = *reinterpret_cast<const float4 *>(raw + 4 * k4);   // c_T = row 0
-                            const float4 bb = *reinterpret_cast<const float4 *>(cB + 4 * k4);
+                            const float4 bb = *reinterpret_cast<const float4 *>(cBs + 4 * k4);
                             const float4 xx = has_tgt ? *reinterpret_cast<const float4 *>(raw + t * dp + 4 * k4) : tt;
                             const float4 yy = has_src ? *reinterpret_cast<const float4 *>(rawb + t * dp + 4 * k4) : tt;
                             const float ts[4] = {tt.x, tt.y, tt.z, tt.w}, bs[4] = {bb.x, bb.y, bb.z, bb.w};
@@ -357,26 +371,25 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                                 qq = fmaf(ya, ya, qq);
                             }
                         }
-                        // 4 elements = 8 bytes of the 128-byte row
+                        // 4 elements = 8 bytes of the 128-byte row; packed 2-wide conversions
                         uint32_t hv[2], lv[2];
 #pragma unroll
                         for (int e = 0; e < 2; ++e) {
-                            float v0 = xa[2 * e], v1 = xa[2 * e + 1];
-                            uint16_t h0, h1, l0, l1;
                             if constexpr (P == ASKIT_PREC_FP16X3) {
-                                v0 *= args.f16_scale; v1 *= args.f16_scale;
-                                const __half a0 = __float2half_rn(v0), a1 = __float2half_rn(v1);
-                                h0 = __half_as_ushort(a0); h1 = __half_as_ushort(a1);
-                                l0 = __half_as_ushort(__float2half_rn(v0 - __half2float(a0)));
-                                l1 = __half_as_ushort(__float2half_rn(v1 - __half2float(a1)));
+                                const float v0 = xa[2 * e] * args.f16_scale, v1 = xa[2 * e + 1] * args.f16_scale;
+                                const __half2 h = __floats2half2_rn(v0, v1);
+                                const float2 hf = __half22float2(h);
+                                const __half2 l = __floats2half2_rn(v0 - hf.x, v1 - hf.y);
+                                hv[e] = *reinterpret_cast<const uint32_t *>(&h);
+                                lv[e] = *reinterpret_cast<const uint32_t *>(&l);
                             } else {
-                                const __nv_bfloat16 a0 = __float2bfloat16_rn(v0), a1 = __float2bfloat16_rn(v1);
-                                h0 = __bfloat16_as_ushort(a0); h1 = __bfloat16_as_ushort(a1);
-                                l0 = __bfloat16_as_ushort(__float2bfloat16_rn(v0 - __bfloat162float(a0)));
-                                l1 = __bfloat16_as_ushort(__float2bfloat16_rn(v1 - __bfloat162float(a1)));
+                                const float v0 = xa[2 * e], v1 = xa[2 * e + 1];
+                                const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                                const float2 hf = __bfloat1622float2(h);
+                                const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+                                hv[e] = *reinterpret_cast<const uint32_t *>(&h);
+                                lv[e] = *reinterpret_cast<const uint32_t *>(&l);
                             }
-                            hv[e] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-                            lv[e] = (uint32_t)l0 | ((uint32_t)l1 << 16);
                         }
                         const int off = t * 128 + (((kst >> 1) ^ (t & 7)) << 4) + (kst & 1) * 8;
                         *reinterpret_cast<uint2 *>(ahi + off) = make_uint2(hv[0], hv[1]);
@@ -460,7 +473,15 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                 // row term |a|^2 + 2 a.delta; column data of source row t:
                 // arg = g (2 u sc) + (-sc) p_t + (-sc q) = -sc (p_t + q - 2 u g)
                 a_norm[s * 128 + t] = nn + 2.f * dd;
-                colv[s * 128 + t] = make_float4(2.f * args.g_unscale * sc, -sc * qq, -sc, w0);
+                {
+                    // column pairs: [pair][0] = {A_j, A_j+1, B_j, B_j+1}, [pair][1] = {C_j, C_j+1, w_j, w_j+1}
+                    float *cp = reinterpret_cast<float *>(colv + s * 128 + 2 * (t >> 1));
+                    const int h = t & 1;
+                    cp[0 + h] = 2.f * args.g_unscale * sc;
+                    cp[2 + h] = -sc * qq;
+                    cp[4 + h] = -sc;
+                    cp[6 + h] = w0;
+                }
                 if (RC > 1) {
 #pragma unroll
                     for (int z = 0; z < RC; ++z)
@@ -491,31 +512,47 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                 if (!mbar_wait(BAR_A_FULL(a), par, abort_flag, args.status)) goto epi_done;
                 if (!mbar_wait(BAR_T_FULL(a), par, abort_flag, args.status)) goto epi_done;
                 tc_fence_after();
-                float acc[RC < 4 ? 4 : RC];
+                float acc[RC];
 #pragma unroll
-                for (int z = 0; z < (RC < 4 ? 4 : RC); ++z) acc[z] = 0.f;
+                for (int z = 0; z < RC; ++z) acc[z] = 0.f;
+                float2 acc2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};   // RC == 1
                 if (q * 32 < item.cnt) {   // warp-uniform: skip quadrants with no target
                     const float pt = a_norm[a * 128 + row];
+                    const float2 pt2 = make_float2(pt, pt);
                     const float4 *cv4 = colv + a * 128;
-                    const float *cw = colw + a * 128 * RC;
+                    const float *cwp = colw + a * 128 * RC;
 #pragma unroll 1
                     for (int c = 0; c < 4 && c * 32 < nrows; ++c) {
                         float g[32];
                         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * 128 + c * 32), g);
+                        if constexpr (RC == 1) {
+                            // two columns per step with packed FP32x2 FMAs:
+                            // arg = g A + (C p + B) = -sc (p + q - 2 u g); columns past
+                            // nrows carry w = 0
 #pragma unroll
-                        for (int jj = 0; jj < 32; ++jj) {
-                            // columns past nrows carry w = 0 (and sc = 0)
-                            const float4 cv = cv4[c * 32 + jj];
-                            const float k = ex2_approx(fmaf(g[jj], cv.x, fmaf(cv.z, pt, cv.y)));
-                            if constexpr (RC == 1) {
-                                acc[jj & 3] = fmaf(k, cv.w, acc[jj & 3]);
-                            } else {
+                            for (int jj = 0; jj < 32; jj += 2) {
+                                const float4 ab = cv4[c * 32 + jj];
+                                const float4 cw = cv4[c * 32 + jj + 1];
+                                const float2 inner = __ffma2_rn(make_float2(cw.x, cw.y), pt2, make_float2(ab.z, ab.w));
+                                const float2 arg = __ffma2_rn(make_float2(g[jj], g[jj + 1]), make_float2(ab.x, ab.y), inner);
+                                const float2 k = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+                                acc2[(jj >> 1) & 1] = __ffma2_rn(k, make_float2(cw.z, cw.w), acc2[(jj >> 1) & 1]);
+                            }
+                        } else {
 #pragma unroll
-                                for (int z = 0; z < RC; ++z) acc[z] = fmaf(k, cw[(c * 32 + jj) * RC + z], acc[z]);
+                            for (int jj = 0; jj < 32; ++jj) {
+                                const int j = c * 32 + jj;
+                                const float4 ab = cv4[j & ~1];
+                                const float4 cw = cv4[(j & ~1) + 1];
+                                const bool h = j & 1;
+                                const float A = h ? ab.y : ab.x, B = h ? ab.w : ab.z, Cc = h ? cw.y : cw.x;
+                                const float k = ex2_approx(fmaf(g[jj], A, fmaf(Cc, pt, B)));
+#pragma unroll
+                                for (int z = 0; z < RC; ++z) acc[z] = fmaf(k, cwp[j * RC + z], acc[z]);
                             }
                         }
                     }
-                    if constexpr (RC == 1) acc[0] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+                    if constexpr (RC == 1) acc[0] = (acc2[0].x + acc2[0].y) + (acc2[1].x + acc2[1].y);
                 }
                 tc_fence_before();
                 mbar_arrive(BAR_T_EMPTY(a));
@@ -557,7 +594,7 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
     } else if (warp == 12 && lane == 0) {
         // ------------------------------------------------- TMA + MMA issuer
         // hi + lo of one 128-row sub-block, and its raw FP32 rows (gather path)
-        const uint32_t TX = 2 * NREG * REGION + (S::GATHER ? (uint32_t)(TILE_ROWS * args.d_pad * 4) : 0u);
+        const uint32_t TX = 2 * NREG * REGION + (S::GATHER ? (uint32_t)(TILE_ROWS * args.d_pad * 4 + TC_K * 4) : 0u);
         int li = 0, lb = 0;
         for (int ci = args.cta_off[blockIdx.x]; ci < args.cta_off[blockIdx.x + 1] && !*abort_flag; ++ci, ++lb) {
             const int b = args.cta_blocks[ci];
@@ -573,8 +610,10 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                 tma_load_2d(sbase + S::B_HI + g * REGION, mh, x, first.row0, BAR_B_FULL);
                 tma_load_2d(sbase + S::B_LO + g * REGION, ml, x, first.row0, BAR_B_FULL);
             }
-            if constexpr (S::GATHER)
+            if constexpr (S::GATHER) {
                 tma_load_2d(sbase + S::RAWB, far ? &map_rs : &map_rt, 0, first.row0, BAR_B_FULL);
+                bulk_copy(sbase + S::CENT, args.cent + (int64_t)first.cidx * TC_K, TC_K * 4, BAR_B_FULL);
+            }
             const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
             for (int it = i0; it < i1; ++it, ++li) {
                 const int s = li & 1;
