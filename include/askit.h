@@ -147,6 +147,18 @@ askit_status askit_evaluate_targets(askit_tree t, const float *Y_dev, int64_t T,
 askit_status askit_evaluate_host(askit_tree t, const float *W_host, int32_t r, int64_t ldw,
                                  float *U_host, int64_t ldu, void *stream);
 
+/*
+ * Direct sum of eq. (1.1) at selected points, without approximation: for
+ * each target id, the sum over all N points of K(x_i, x_j) w_j with the
+ * tree's points, bandwidths and current weights (plain FP32, difference
+ * form).  The yardstick of ASKIT's error (Section 4 measures the relative
+ * error against direct evaluation on sampled points).
+ *   tgt_dev [T] int32 point ids (caller order); U_dev [T, r] (stride ldu).
+ * Cost O(T N d); requires askit_set_weights first.
+ */
+askit_status askit_direct(askit_tree t, const int32_t *tgt_dev, int64_t T, float *U_dev, int64_t ldu,
+                          void *stream);
+
 /* Precision of subsequent askit_evaluate calls (ASKIT_PREC_*). */
 askit_status askit_set_precision(askit_tree t, int32_t precision);
 

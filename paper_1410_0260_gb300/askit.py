@@ -28,7 +28,7 @@ BW_CONSTANT, BW_ARRAY, BW_KNN = 0, 1, 2
 EXPORTS = ["askit_default_params", "askit_setup", "askit_set_weights", "askit_evaluate",
            "askit_evaluate_targets", "askit_evaluate_host", "askit_set_precision", "askit_get_info",
            "askit_get_structure", "askit_sync", "askit_destroy", "askit_status_string",
-           "askit_last_error", "askit_knn_noalloc"]
+           "askit_last_error", "askit_knn_noalloc", "askit_direct"]
 
 
 class AskitError(RuntimeError):
@@ -74,6 +74,7 @@ def load(path: str | None = None):
             L.askit_sync.argtypes = [V, V]
             L.askit_destroy.argtypes = [V]
             L.askit_knn_noalloc.argtypes = [V, I64, I32, V, I64, I32, V, V, V]
+            L.askit_direct.argtypes = [V, V, I64, V, I64, V]
             L.askit_status_string.restype = C.c_char_p
             L.askit_status_string.argtypes = [C.c_int]
             L.askit_last_error.restype = C.c_char_p
@@ -209,6 +210,14 @@ class Tree:
         _check(load().askit_evaluate_host(self._t, C.c_void_p(W_ptr), r, r, C.c_void_p(U_ptr), r,
                                           _stream(stream)))
         self.r = r
+
+    def direct(self, targets, stream=None) -> torch.Tensor:
+        """Exact direct sum (eq. 1.1) at the given point ids, with the current weights."""
+        tg = torch.as_tensor(targets, dtype=torch.int32, device=self.device).contiguous()
+        out = torch.empty((tg.numel(), max(self.r, 1)), dtype=torch.float32, device=self.device)
+        _check(load().askit_direct(self._t, C.c_void_p(tg.data_ptr()), tg.numel(), C.c_void_p(out.data_ptr()),
+                                   out.stride(0), _stream(stream)))
+        return out
 
     def sync(self, stream=None):
         _check(load().askit_sync(self._t, _stream(stream)))

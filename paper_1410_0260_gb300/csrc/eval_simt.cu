@@ -111,3 +111,72 @@ askit_status eval_simt(askit_tree t, const float *Xq, int64_t ldq, const WorkLis
     ASK_LAUNCH();
     return ASKIT_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Direct sum of eq. (1.1) at selected points: every source point, no
+// approximation (the yardstick of ASKIT's error, Section 4).  One block per
+// target; threads stride over the sources in tree order and reduce in a
+// fixed order.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int DIRECT_THREADS = 256;
+template <int RMAX>
+__global__ void __launch_bounds__(DIRECT_THREADS) direct_kernel(const float *__restrict__ X, int d,
+                                                               const int32_t *__restrict__ tgt,
+                                                               const float *__restrict__ Xt, int d_pad, int64_t N,
+                                                               const float *__restrict__ sc_t,
+                                                               const float *__restrict__ Wt, int r, float *U,
+                                                               int64_t ldu) {
+    __shared__ float xs[1024];
+    __shared__ float red[DIRECT_THREADS / 32][RMAX];
+    const int q = blockIdx.x;
+    const int64_t i = tgt[q];
+    for (int k = threadIdx.x; k < d_pad; k += blockDim.x) xs[k] = k < d ? X[i * d + k] : 0.f;
+    __syncthreads();
+    float acc[RMAX];
+#pragma unroll
+    for (int z = 0; z < RMAX; ++z) acc[z] = 0.f;
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+        const float *y = Xt + j * d_pad;
+        float D = 0.f;
+        for (int k = 0; k < d_pad; k += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(y + k);
+            const float a = xs[k] - v.x, b = xs[k + 1] - v.y, c = xs[k + 2] - v.z, e = xs[k + 3] - v.w;
+            D = fmaf(a, a, D); D = fmaf(b, b, D); D = fmaf(c, c, D); D = fmaf(e, e, D);
+        }
+        const float kv = exp2f(-sc_t[j] * D);
+#pragma unroll
+        for (int z = 0; z < RMAX; ++z)
+            if (z < r) acc[z] = fmaf(kv, Wt[j * r + z], acc[z]);
+    }
+#pragma unroll
+    for (int z = 0; z < RMAX; ++z) {
+        float v = acc[z];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][z] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < RMAX && threadIdx.x < r) {
+        float v = 0.f;
+        for (int w = 0; w < DIRECT_THREADS / 32; ++w) v += red[w][threadIdx.x];
+        U[q * ldu + threadIdx.x] = v;
+    }
+}
+}  // namespace
+
+extern "C" askit_status askit_direct(askit_tree t, const int32_t *tgt_dev, int64_t T, float *U_dev, int64_t ldu,
+                                     void *stream) {
+    if (!t || !tgt_dev || !U_dev) { askit_set_error("tree, tgt_dev and U_dev must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
+    if (!t->weights_ready) { askit_set_error("askit_set_weights has not been called"); return ASKIT_ERR_NOT_READY; }
+    if (T < 1 || T > (1 << 30) || ldu < t->r) { askit_set_error("need 1 <= T and ldu >= r"); return ASKIT_ERR_INVALID_ARG; }
+    if (t->d_pad > 1024) { askit_set_error("askit_direct handles d <= 1024"); return ASKIT_ERR_UNSUPPORTED; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (t->r <= 1)
+        direct_kernel<1><<<(unsigned)T, DIRECT_THREADS, 0, s>>>(t->X, t->d, tgt_dev, t->Xt, t->d_pad, t->N, t->sc_t, t->Wt, t->r, U_dev, ldu);
+    else if (t->r <= 16)
+        direct_kernel<16><<<(unsigned)T, DIRECT_THREADS, 0, s>>>(t->X, t->d, tgt_dev, t->Xt, t->d_pad, t->N, t->sc_t, t->Wt, t->r, U_dev, ldu);
+    else
+        direct_kernel<64><<<(unsigned)T, DIRECT_THREADS, 0, s>>>(t->X, t->d, tgt_dev, t->Xt, t->d_pad, t->N, t->sc_t, t->Wt, t->r, U_dev, ldu);
+    ASK_LAUNCH();
+    return ASKIT_OK;
+}

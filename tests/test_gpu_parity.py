@@ -196,3 +196,44 @@ def test_invalid_arguments_are_errors_not_faults():
         t.evaluate()                                  # weights not set
     with pytest.raises(askit.AskitError):
         t.set_weights(torch.zeros((50, 65), device="cuda"))   # r > 64
+
+
+def test_direct_sum_matches_oracle():
+    askit = _askit()
+    X = wl.mixture(1500, 5, 3, 4.0, seed=13)
+    W = np.random.default_rng(3).standard_normal((1500, 2)).astype(np.float32)
+    t = askit.Tree(torch.from_numpy(X).cuda(), askit.Config(leaf_size=64, kappa=8, s_max=8, h=0.9,
+                                                           precision="simt_fp32"))
+    t.set_weights(torch.from_numpy(W).cuda())
+    tg = np.arange(0, 1500, 7)
+    Ug = t.direct(tg).cpu().numpy()
+    Uo = oracle.direct(X, W, np.float32(0.9), 0.5, targets=tg)
+    assert rel(Ug, Uo) <= 1e-5
+
+
+def test_multi_rhs_16_on_the_8m_recipe_shape():
+    """r = 16 weight vectors, m = 1024, s <= 512, h = 0.5: the 8M-point recipe at N = 16384."""
+    w = wl.MANIFOLD_8M_64_R16.scaled(16384)
+    X, W = w.make_points(), w.make_weights()
+    kw = dict(leaf_size=1024, kappa=32, knn_mode=1, rp_iters=2, s_max=512, id_tol=1e-4, h=0.5, seed=3)
+    otree, gtree = build_pair(X, kw)
+    check_structures(otree, gtree)
+    for prec in ("simt_fp32", "fp16x3", "bf16x3"):
+        Ug, Uo = eval_both(otree, gtree, W, prec)
+        assert rel(Ug, Uo) <= TOL[prec], prec
+
+
+def test_d1000_variable_bandwidth_on_the_1000d_recipe_shape():
+    """d = 1000, h_j = distance to the 16th neighbor, adaptive s in [32, 128]: the
+    1M x 1000 recipe at N = 2048 (plain FP32 path; the tensor-core path covers d <= 64)."""
+    w = wl.MANIFOLD_1M_1000_VARH.scaled(2048)
+    X, W = w.make_points(), w.make_weights()
+    kw = dict(leaf_size=256, kappa=16, knn_mode=0, s_max=128, s_min=32, id_tol=1e-3, bw_mode=2, bw_k=16, seed=4)
+    otree, gtree = build_pair(X, kw)
+    check_structures(otree, gtree)
+    Ug, Uo = eval_both(otree, gtree, W, "simt_fp32")
+    assert rel(Ug, Uo) <= TOL["simt_fp32"]
+    askit = _askit()
+    gtree.set_precision("fp16x3")
+    with pytest.raises(askit.AskitError):
+        gtree.evaluate()
