@@ -7,10 +7,19 @@ w ~ N(0, 1), Gaussian h = 0.35 (exp(-r^2 / 2h^2)), leaf size m = 512,
 kappa = 32 neighbors by random-projection trees, s <= 256, ID tolerance 1e-4.
 
 One step = one pass of the evaluation hot path over a new weight vector:
-weights into tree order and the upward pass of skeleton weights
-(askit_set_weights), then Evaluate at all N points (askit_evaluate).  The tree,
+weights into tree order and the upward pass of skeleton weights, then
+Evaluate at all N points, replayed as one captured CUDA graph
+(askit_graph_launch; the same kernels as askit_set_weights + askit_evaluate).  The tree,
 kNN, skeletons and work lists are built once (setup, reported separately).
 Metric: evaluated targets per second (whole job = all ranks).
+
+Serving (the "serving" key, 1 GPU): a 2,097,152-point 64-D tree (8-dim
+manifold, h = 0.4, m = 512, s <= 256) stays resident while a seeded stream of
+requests arrives as a Poisson process at 200 requests/s; each request is 1-64
+new weight vectors or an out-of-sample batch of 100-100,000 points from the
+same distribution.  The loop batches them continuously over two slots and
+admits batches by device footprint; p50/p99 latency and targets/s are
+reported for the split-precision path and for plain FP32 on the same stream.
 
 --impl reference times the CPU oracle (plain FP64 C) on the host cores on a
 bounded sample of the same workload and prints the same JSON line.
@@ -46,17 +55,24 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp16x3", choices=["simt_fp32", "tf32x3", "bf16x3", "fp16x3"])
+    ap.add_argument("--workload", default="manifold1m_d64", choices=list(WORKLOADS),
+                    help="which workload to time (the default is the bench line's)")
     ap.add_argument("--n", type=int, default=0, help="override N (smaller runs; not a bench line)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-n", type=int, default=65536)
     ap.add_argument("--cpu-targets", type=int, default=4096)
+    ap.add_argument("--serve-requests", type=int, default=32, help="requests per serving run (0: no serving run)")
     return ap.parse_args()
+
+
+WORKLOADS = {"manifold1m_d64": "MANIFOLD_1M_64", "manifold8m_d64_r16": "MANIFOLD_8M_64_R16",
+             "manifold1m_d1000": "MANIFOLD_1M_1000_VARH"}
 
 
 def workload(args):
     from paper_1410_0260_gb300 import workloads as wl
-    w = wl.MANIFOLD_1M_64
+    w = getattr(wl, WORKLOADS[args.workload])
     return w.scaled(args.n) if args.n else w
 
 
@@ -185,6 +201,50 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def serving(args, dev, precision):
+    """The serving workload, replayed once per precision on one resident tree."""
+    import torch
+    from paper_1410_0260_gb300 import askit, serve
+    from paper_1410_0260_gb300 import workloads as wl
+    w = wl.SERVING_2M_64.scaled(2 * args.n) if args.n else wl.SERVING_2M_64
+    t0 = time.perf_counter()
+    tree = askit.Tree(torch.from_numpy(w.make_points()).to(dev), askit_config(w, precision))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    Wres = torch.from_numpy(w.make_weights(1)).to(dev)
+    pool = torch.from_numpy(w.make_weights(128, seed_offset=7)).to(dev)
+    spec = wl.request_stream(args.serve_requests, 200.0, seed=w.seed)
+    rng = np.random.default_rng(w.seed + 17)
+    n_q = sum(size for _, kind, size in spec if kind == "targets")
+    Y = torch.from_numpy(wl.manifold_queries(max(n_q, 1), w.d, w.k_intr, w.noise, w.seed, w.seed + 99)).pin_memory()
+    stream, off = [], 0
+    for ta, kind, size in spec:
+        if kind == "weights":
+            c0 = int(rng.integers(0, 128 - size + 1))
+            stream.append((ta, kind, pool[:, c0:c0 + size]))
+        else:
+            stream.append((ta, kind, Y[off:off + size]))
+            off += size
+    out = {"workload": w.name, "arrivals_per_s": 200.0, "slots": 2, "setup_s": setup_s,
+           "targets_counted_as": "N r per weight request, T per target batch"}
+    for prec in (precision, "simt_fp32"):
+        tree.set_precision(prec)
+        srv = serve.Server(tree, Wres, n_slots=2)
+        serve.replay(srv, [(0.0, "weights", pool[:, :16]), (0.0, "targets", Y[:1000])])   # warm-up
+        srv.completed.clear()
+        srv.n_batches = 0
+        reqs = serve.replay(srv, stream)
+        st = serve.latency_stats(reqs, w.N)
+        st["peak_concurrent_batches"] = srv.peak_concurrency
+        st["batches"] = srv.n_batches
+        srv.close()
+        out[prec] = st
+    if precision != "simt_fp32":
+        out["split_over_fp32_targets_per_s"] = out[precision]["targets_per_s"] / out["simt_fp32"]["targets_per_s"]
+    tree.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -207,7 +267,8 @@ def main():
     N = w.N
     Xd = torch.from_numpy(X).to(dev)
     Wd = torch.from_numpy(W).to(dev)
-    U = torch.empty((N, 1), dtype=torch.float32, device=dev)
+    r = W.shape[1]
+    U = torch.empty((N, r), dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     tree = askit.Tree(Xd, askit_config(w, args.precision))
@@ -216,9 +277,13 @@ def main():
     info = tree.info()
     stream = torch.cuda.current_stream()
 
+    # the step is replayed from a captured CUDA graph (askit_graph_*): the
+    # upward pass and Evaluate, one graph launch per step
+    graph = tree.capture(Wd, U)
+    tree.set_weights(Wd)        # the tree's default weights, for the Evaluate-only timing
+
     def step():
-        tree.set_weights(Wd)
-        tree.evaluate(U)
+        graph.launch()
 
     for _ in range(args.warmup):
         step()
@@ -279,21 +344,21 @@ def main():
     e2e = None
     if not args.no_e2e:
         Wh = torch.from_numpy(W).pin_memory()
-        Uh = torch.empty((N, 1), dtype=torch.float32).pin_memory()
+        Uh = torch.empty((N, r), dtype=torch.float32).pin_memory()
         for _ in range(2):
-            tree.evaluate_host_ptr(Wh.data_ptr(), 1, Uh.data_ptr())
+            tree.evaluate_host_ptr(Wh.data_ptr(), r, Uh.data_ptr())
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            tree.evaluate_host_ptr(Wh.data_ptr(), 1, Uh.data_ptr())
+            tree.evaluate_host_ptr(Wh.data_ptr(), r, Uh.data_ptr())
         dt = time.perf_counter() - t0
         if world > 1:
             t = torch.tensor([dt], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t[0])
         e2e = {"value": world * N * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(W.nbytes),
-               "d2h_bytes_per_step": int(N * 4)}
+               "d2h_bytes_per_step": int(N * r * 4)}
 
     # roofline of the Evaluate kernel
     peaks = measured_peaks()
@@ -329,28 +394,32 @@ def main():
         cpu = cpu_baseline(args, w)
         cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
-    # a0 permute-in, one upward kernel per level, the two column-data packs,
-    # Evaluate, and the fixed-order reduction
-    launches_per_step = 1 + info["L"] + (2 if args.precision != "simt_fp32" else 0) + 2
+    # permute-in, one upward kernel per level, Evaluate, fixed-order reduction
+    launches_per_step = 1 + info["L"] + 2
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"simt_fp32": "f32", "tf32x3": "tf32x3", "bf16x3": "bf16x3", "fp16x3": "fp16x3"}[args.precision],
             "data": "synthetic",
             "config": {"workload": w.name, "N": N, "d": d, "m": w.leaf_size, "kappa": w.kappa,
-                       "knn": "rp-trees x%d" % w.rp_iters, "s_max": w.s_max, "id_tol": w.id_tol, "h": w.h,
-                       "r": 1, "precision": args.precision, "parallelism": f"replicas x{world}",
+                       "knn": "rp-trees x%d" % w.rp_iters, "s_max": w.s_max, "s_min": w.s_min, "id_tol": w.id_tol,
+                       "h": w.h if w.bw_mode == 0 else "distance to neighbor %d" % w.bw_k,
+                       "r": r, "precision": args.precision, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (coordinates %.0f MB)" % (N * info["d_pad"] * 4 / 1e6)},
             "rel_err_vs_fp32": rel_vs_fp32, "rel_err_ok": rel_vs_fp32 <= 1e-4, "eps2_vs_direct": eps2,
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk, "roofline": roof,
-            "cpu_baseline": cpu,
+            "cpu_baseline": cpu, "serving": None,
             "work": {"pairs_algorithmic": P, "pairs_computed": info["pairs_computed"],
                      "near_per_target": info["near_total"] / N, "far_per_target": info["far_total"] / N,
                      "items": info["n_items"], "blocks": info["n_blocks"], "entries": info["n_entries"], "L": info["L"],
                      "skeleton_rows": info["skel_total"], "setup_s": setup_s,
                      "device_gb": info["device_bytes"] / 1e9}}
+    graph.close()
+    tree.close()
+    del Xd, Wd, U
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        line["serving"] = serving(args, dev, args.precision)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    tree.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -159,6 +159,58 @@ askit_status askit_evaluate_host(askit_tree t, const float *W_host, int32_t r, i
 askit_status askit_direct(askit_tree t, const int32_t *tgt_dev, int64_t T, float *U_dev, int64_t ldu,
                           void *stream);
 
+/*
+ * Weight contexts.  askit_set_weights/askit_evaluate use the tree's default
+ * weights; a context holds its own weight vectors, skeleton weights (the
+ * upward pass of Section 2.1) and Evaluate scratch, so that several weight
+ * sets can be evaluated concurrently on different streams while the tree
+ * structures are shared read-only (a serving loop batching requests).  A
+ * context is tied to its tree and must be destroyed before it.  Calls on one
+ * context must not overlap on the GPU.
+ */
+typedef struct askit_weights_s *askit_weights;
+askit_status askit_weights_create(askit_tree t, askit_weights *out);
+/* upward pass for W_dev [N, r] (stride ldw, caller order), 1 <= r <= 64 */
+askit_status askit_weights_set(askit_weights w, const float *W_dev, int32_t r, int64_t ldw, void *stream);
+/* Evaluate at every point with the context's weights: U_dev [N, r] */
+askit_status askit_weights_evaluate(askit_weights w, float *U_dev, int64_t ldu, void *stream);
+/* Evaluate at out-of-sample targets Y_dev [T, d] with the context's weights */
+askit_status askit_weights_evaluate_targets(askit_weights w, const float *Y_dev, int64_t T, int64_t ldy,
+                                            float *U_dev, int64_t ldu, void *stream);
+askit_status askit_weights_destroy(askit_weights w);
+
+/*
+ * A captured evaluation step.  askit_graph_create records, as one CUDA graph,
+ * the upward pass of skeleton weights for W_dev (Section 2.1, Algorithm 3)
+ * followed by Evaluate at every point (Algorithm 4) into U_dev; each
+ * askit_graph_launch replays it with a single launch on `stream`.
+ *   W_dev [N, r] (stride ldw, caller order, 1 <= r <= 64) and U_dev [N, r]
+ *   (stride ldu) are caller-owned and bound at creation: every replay reads
+ *   the current contents of W_dev and overwrites U_dev.  Both must stay
+ *   allocated while the graph exists.
+ * The graph owns a weight context of its own (the tree's default weights are
+ * not touched) and uses the tree's precision at creation time.  Creation runs
+ * one step uncaptured on `stream` (allocations and operand preparation happen
+ * there), waits for it, then captures a second step on a private stream in
+ * thread-local capture mode; it must not be called while `stream` is itself
+ * being captured.
+ * Replays of one graph must not overlap on the GPU.  Destroy the graph before
+ * its tree.
+ */
+typedef struct askit_graph_s *askit_graph;
+askit_status askit_graph_create(askit_tree t, const float *W_dev, int32_t r, int64_t ldw, float *U_dev,
+                                int64_t ldu, void *stream, askit_graph *out);
+askit_status askit_graph_launch(askit_graph g, void *stream);
+askit_status askit_graph_destroy(askit_graph g);
+
+/*
+ * Device bytes a request needs, for admission by memory footprint.
+ *   kind 0: a weight context for r vectors (n ignored);
+ *   kind 1: an out-of-sample batch of n targets with r weight vectors
+ *           (work lists estimated from the in-sample entries per target, x2).
+ */
+askit_status askit_footprint(askit_tree t, int32_t kind, int64_t n, int32_t r, size_t *bytes);
+
 /* Precision of subsequent askit_evaluate calls (ASKIT_PREC_*). */
 askit_status askit_set_precision(askit_tree t, int32_t precision);
 

@@ -28,7 +28,10 @@ BW_CONSTANT, BW_ARRAY, BW_KNN = 0, 1, 2
 EXPORTS = ["askit_default_params", "askit_setup", "askit_set_weights", "askit_evaluate",
            "askit_evaluate_targets", "askit_evaluate_host", "askit_set_precision", "askit_get_info",
            "askit_get_structure", "askit_sync", "askit_destroy", "askit_status_string",
-           "askit_last_error", "askit_knn_noalloc", "askit_direct"]
+           "askit_last_error", "askit_knn_noalloc", "askit_direct", "askit_weights_create",
+           "askit_weights_set", "askit_weights_evaluate", "askit_weights_evaluate_targets",
+           "askit_weights_destroy", "askit_footprint", "askit_graph_create", "askit_graph_launch",
+           "askit_graph_destroy"]
 
 
 class AskitError(RuntimeError):
@@ -75,6 +78,15 @@ def load(path: str | None = None):
             L.askit_destroy.argtypes = [V]
             L.askit_knn_noalloc.argtypes = [V, I64, I32, V, I64, I32, V, V, V]
             L.askit_direct.argtypes = [V, V, I64, V, I64, V]
+            L.askit_weights_create.argtypes = [V, C.POINTER(V)]
+            L.askit_weights_set.argtypes = [V, V, I32, I64, V]
+            L.askit_weights_evaluate.argtypes = [V, V, I64, V]
+            L.askit_weights_evaluate_targets.argtypes = [V, V, I64, I64, V, I64, V]
+            L.askit_weights_destroy.argtypes = [V]
+            L.askit_footprint.argtypes = [V, I32, I64, I32, C.POINTER(C.c_size_t)]
+            L.askit_graph_create.argtypes = [V, V, I32, I64, V, I64, V, C.POINTER(V)]
+            L.askit_graph_launch.argtypes = [V, V]
+            L.askit_graph_destroy.argtypes = [V]
             L.askit_status_string.restype = C.c_char_p
             L.askit_status_string.argtypes = [C.c_int]
             L.askit_last_error.restype = C.c_char_p
@@ -222,6 +234,19 @@ class Tree:
     def sync(self, stream=None):
         _check(load().askit_sync(self._t, _stream(stream)))
 
+    def weights_context(self) -> "Weights":
+        return Weights(self)
+
+    def capture(self, W: torch.Tensor, U: torch.Tensor, stream=None) -> "Graph":
+        """A CUDA graph of set_weights(W) + evaluate(U); replays read W's
+        current contents and overwrite U."""
+        return Graph(self, W, U, stream)
+
+    def footprint(self, kind: int, n: int, r: int) -> int:
+        b = C.c_size_t()
+        _check(load().askit_footprint(self._t, kind, n, r, C.byref(b)))
+        return b.value
+
     def info(self) -> dict:
         inf = Info()
         _check(load().askit_get_info(self._t, C.byref(inf)))
@@ -246,3 +271,76 @@ class Tree:
         a = np.zeros(shape, dt)
         _check(load().askit_get_structure(self._t, which, a.ctypes.data_as(C.c_void_p), a.nbytes))
         return a
+
+
+class Weights:
+    """A weight context of a tree (independent of the tree's default weights)."""
+
+    def __init__(self, tree: Tree):
+        self.tree = tree
+        h = C.c_void_p()
+        _check(load().askit_weights_create(tree._t, C.byref(h)))
+        self._w = h
+        self.r = 0
+
+    def set(self, W: torch.Tensor, stream=None):
+        W = _dev_f32(W, "W")
+        _check(load().askit_weights_set(self._w, C.c_void_p(W.data_ptr()), W.shape[1], W.stride(0), _stream(stream)))
+        self._W = W
+        self.r = W.shape[1]
+
+    def evaluate(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.tree.N, max(self.r, 1)), dtype=torch.float32, device=self.tree.device)
+        _check(load().askit_weights_evaluate(self._w, C.c_void_p(out.data_ptr()), out.stride(0), _stream(stream)))
+        return out
+
+    def evaluate_targets(self, Y: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        Y = _dev_f32(Y, "Y")
+        if out is None:
+            out = torch.empty((Y.shape[0], max(self.r, 1)), dtype=torch.float32, device=self.tree.device)
+        _check(load().askit_weights_evaluate_targets(self._w, C.c_void_p(Y.data_ptr()), Y.shape[0], Y.stride(0),
+                                                     C.c_void_p(out.data_ptr()), out.stride(0), _stream(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "_w", None):
+            load().askit_weights_destroy(self._w)
+            self._w = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Graph:
+    """A captured weights + Evaluate step (askit_graph_*)."""
+
+    def __init__(self, tree: Tree, W: torch.Tensor, U: torch.Tensor, stream=None):
+        # the graph binds these buffers' addresses: no copies here
+        for name, a in (("W", W), ("U", U)):
+            if not (a.is_cuda and a.dtype == torch.float32 and a.dim() == 2 and a.stride(1) == 1):
+                raise AskitError(f"{name} must be a row-major 2-D FP32 CUDA tensor")
+        if W.shape[0] != tree.N or U.shape != W.shape:
+            raise AskitError("W and U must both be [N, r]")
+        self.tree, self.W, self.U = tree, W, U
+        h = C.c_void_p()
+        _check(load().askit_graph_create(tree._t, C.c_void_p(W.data_ptr()), W.shape[1], W.stride(0),
+                                         C.c_void_p(U.data_ptr()), U.stride(0), _stream(stream), C.byref(h)))
+        self._g = h
+
+    def launch(self, stream=None):
+        _check(load().askit_graph_launch(self._g, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_g", None):
+            load().askit_graph_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -58,12 +58,16 @@ constexpr int TC_K = 64;
 struct DevArena {
     std::vector<void *> ptrs;
     size_t bytes = 0;
+    // stream-ordered mode (per-call temporaries): cudaMallocAsync/cudaFreeAsync
+    // on `stream`, so freeing does not synchronize the device
+    bool async = false;
+    cudaStream_t stream = nullptr;
     template <class T>
     askit_status alloc(T **p, size_t count) {
         *p = nullptr;
         if (count == 0) count = 1;
         void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+        cudaError_t e = async ? cudaMallocAsync(&q, count * sizeof(T), stream) : cudaMalloc(&q, count * sizeof(T));
         if (e != cudaSuccess) {
             askit_set_error("cudaMalloc(%zu bytes): %s", count * sizeof(T), cudaGetErrorString(e));
             return e == cudaErrorMemoryAllocation ? ASKIT_ERR_OOM : ASKIT_ERR_CUDA;
@@ -79,7 +83,10 @@ struct DevArena {
     }
     void free_all() {
         for (void *q : ptrs)
-            if (q) cudaFree(q);
+            if (q) {
+                if (async) cudaFreeAsync(q, stream);
+                else cudaFree(q);
+            }
         ptrs.clear();
         bytes = 0;
     }
@@ -113,6 +120,33 @@ struct WorkLists {
     int32_t *cta_off = nullptr;      // [n_ctas + 1]
     int32_t *cta_blocks = nullptr;   // [n_blocks]
     int64_t pairs_alg = 0, pairs_cmp = 0, near_tot = 0, far_tot = 0;
+};
+
+// Weights of one evaluation context: W in tree order, the skeleton weights
+// of the upward pass, and the per-entry partial sums of Evaluate.  A tree
+// has a default context; askit_weights_create adds independent ones, so
+// several weight sets can be evaluated concurrently on different streams.
+struct WeightCtx {
+    int r = 0, r_cap = 0;
+    float *Wt = nullptr;       // [N_pad, r] weights in tree order
+    float *Ws = nullptr;       // [rows of the skeleton pool, r] skeleton weights
+    float *partial = nullptr;  // [in-sample entries, r_cap]
+    bool ready = false;
+    DevArena arena;
+};
+
+struct askit_tree_s;
+struct askit_weights_s {
+    askit_tree_s *t = nullptr;
+    WeightCtx ctx;
+};
+
+// A captured set_weights + evaluate step with its own weight context.
+struct askit_graph_s {
+    askit_tree_s *t = nullptr;
+    WeightCtx ctx;
+    cudaGraphExec_t exec = nullptr;
+    int64_t n_nodes = 0;
 };
 
 struct askit_tree_s {
@@ -157,15 +191,11 @@ struct askit_tree_s {
     float *Xs = nullptr;       // [spool_rows, d_pad] skeleton coordinate pool
     float *nrm_t = nullptr, *nrm_s = nullptr;   // squared norms
     float *sc_t = nullptr, *sc_s = nullptr;     // c * log2(e) / h_j^2 per source row
-    int r = 0;
-    float *Wt = nullptr;       // [N_pad, r] weights in tree order
-    float *Ws = nullptr;       // [spool_rows, r] skeleton weights
-    bool weights_ready = false;
+    WeightCtx dw;              // default weight context (askit_set_weights)
     int precision = ASKIT_PREC_TF32X3;
 
-    // in-sample work lists and the per-entry partial sums of Evaluate
+    // in-sample work lists
     WorkLists wl;
-    float *partial = nullptr;      // [wl.n_entries, r]
 
     // tensor-core operands: every source sub-block centered on its own mean,
     // split into hi + lo parts (TF32 and BF16), TC_K columns, and the squared
@@ -179,12 +209,13 @@ struct askit_tree_s {
     uint16_t *Xt_hhi = nullptr, *Xt_hlo = nullptr, *Xs_hhi = nullptr, *Xs_hlo = nullptr; // FP16 split (prescaled)
     float f16_scale = 1.f;         // power of 2 keeping centered coordinates within FP16 range
     float *nrmc_t = nullptr, *nrmc_s = nullptr;
-    float4 *Ct = nullptr, *Cs = nullptr;   // per source row {c log2 e / h^2, -(that) |y'|^2, w_0, 0}
     int64_t srows = 0;             // rows of the skeleton-pool arrays
 
     int *d_status = nullptr;       // sticky kernel status
     int *d_ticket = nullptr;       // persistent-kernel work counter
     void *tc = nullptr;            // tensor-core kernel state (tensor maps)
+    void *tcw = nullptr;           // the same for the wide (d > TC_K) kernel
+    int kw = TC_K;                 // row width of the pre-split operands and centers
 };
 
 // ---------------------------------------------------------------------------
@@ -310,11 +341,15 @@ askit_status oos_prune_sets(askit_tree t, const int32_t *knn, int64_t T, int str
                             cudaStream_t s);
 
 // weights.cu
-askit_status upward_weights(askit_tree t, const float *W, int r, int64_t ldw, cudaStream_t s);
+askit_status weights_reserve(askit_tree t, WeightCtx &c, int r, cudaStream_t s);
+askit_status upward_weights(askit_tree t, WeightCtx &c, const float *W, int r, int64_t ldw, cudaStream_t s);
 
 // eval_simt.cu / eval_tc.cu: partial[e * r + z] for every entry e of w
-askit_status eval_simt(askit_tree t, const float *Xq, int64_t ldq, const WorkLists &w, float *partial,
-                       cudaStream_t s);
-askit_status eval_tc(askit_tree t, int precision, const float *Xq, int64_t ldq, int64_t q_rows,
-                     const WorkLists &w, float *partial, cudaStream_t s);
+askit_status eval_simt(askit_tree t, const WeightCtx &c, const float *Xq, int64_t ldq, const WorkLists &w,
+                       float *partial, cudaStream_t s);
+askit_status eval_tc(askit_tree t, const WeightCtx &c, int precision, const float *Xq, int64_t ldq,
+                     int64_t q_rows, const WorkLists &w, float *partial, cudaStream_t s);
 void eval_tc_free(askit_tree t);
+askit_status eval_tc_wide(askit_tree t, const WeightCtx &c, int precision, const float *Xq, int64_t ldq,
+                          int64_t q_rows, const WorkLists &w, float *partial, cudaStream_t s);
+void eval_tc_wide_free(askit_tree t);

@@ -21,6 +21,9 @@ void askit_set_error(const char *fmt, ...) {
     g_err = buf;
 }
 
+askit_status evaluate_targets_ctx(askit_tree t, const WeightCtx &c, const float *Y_dev, int64_t T, int64_t ldy,
+                                  float *U_dev, int64_t ldu, cudaStream_t s);
+
 namespace {
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -220,14 +223,28 @@ askit_status setup_impl(askit_tree t, const float *X_dev, int64_t ldx, const flo
 
 // Evaluate over one set of work lists: every (target, sub-block) entry's
 // partial sum, then each target's entries summed in their fixed order.
-askit_status run_eval(askit_tree t, int precision, const float *Xq, int64_t ldq, int64_t q_rows,
-                      const WorkLists &w, float *partial, const int32_t *out_rows, float *U, int64_t ldu,
-                      cudaStream_t s) {
+askit_status run_eval(askit_tree t, const WeightCtx &c, int precision, const float *Xq, int64_t ldq,
+                      int64_t q_rows, const WorkLists &w, float *partial, const int32_t *out_rows, float *U,
+                      int64_t ldu, cudaStream_t s) {
     if (precision == ASKIT_PREC_SIMT_FP32)
-        ASK_TRY(eval_simt(t, Xq, ldq, w, partial, s));
+        ASK_TRY(eval_simt(t, c, Xq, ldq, w, partial, s));
     else
-        ASK_TRY(eval_tc(t, precision, Xq, ldq, q_rows, w, partial, s));
-    return reduce_partials(w, partial, t->r, out_rows, U, ldu, s);
+        ASK_TRY(eval_tc(t, c, precision, Xq, ldq, q_rows, w, partial, s));
+    return reduce_partials(w, partial, c.r, out_rows, U, ldu, s);
+}
+
+askit_status set_weights_ctx(askit_tree t, WeightCtx &c, const float *W_dev, int32_t r, int64_t ldw,
+                             cudaStream_t s) {
+    if (!W_dev) { askit_set_error("W_dev must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
+    if (r < 1 || r > 64 || ldw < r) { askit_set_error("need 1 <= r <= 64 and ldw >= r"); return ASKIT_ERR_INVALID_ARG; }
+    return upward_weights(t, c, W_dev, r, ldw, s);
+}
+
+askit_status evaluate_ctx(askit_tree t, const WeightCtx &c, float *U_dev, int64_t ldu, cudaStream_t s) {
+    if (!U_dev) { askit_set_error("U_dev must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
+    if (!c.ready) { askit_set_error("no weights set"); return ASKIT_ERR_NOT_READY; }
+    if (ldu < c.r) { askit_set_error("ldu < r"); return ASKIT_ERR_INVALID_ARG; }
+    return run_eval(t, c, t->precision, t->Xt, t->d_pad, t->N_pad, t->wl, c.partial, t->perm, U_dev, ldu, s);
 }
 
 }  // namespace
@@ -306,26 +323,8 @@ askit_status askit_setup(const float *X_dev, int64_t N, int32_t d, int64_t ldx, 
 }
 
 askit_status askit_set_weights(askit_tree t, const float *W_dev, int32_t r, int64_t ldw, void *stream) {
-    if (!t || !W_dev) { askit_set_error("tree and W_dev must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
-    if (r < 1 || r > 64 || ldw < r) { askit_set_error("need 1 <= r <= 64 and ldw >= r"); return ASKIT_ERR_INVALID_ARG; }
-    cudaStream_t s = (cudaStream_t)stream;
-    if (r != t->r) {
-        if (t->Wt) t->arena.release(t->Wt);
-        if (t->Ws) t->arena.release(t->Ws);
-        t->Wt = t->Ws = nullptr;
-        int64_t srows = std::max<int64_t>(t->spool_rows, 1) + 256;
-        if (t->partial) t->arena.release(t->partial);
-        t->partial = nullptr;
-        ASK_TRY(t->arena.alloc(&t->Wt, (size_t)t->N_pad * r));
-        ASK_TRY(t->arena.alloc(&t->Ws, (size_t)srows * r));
-        ASK_TRY(t->arena.alloc(&t->partial, (size_t)t->wl.n_entries * r));
-        ASK_CUDA(cudaMemsetAsync(t->Wt, 0, sizeof(float) * t->N_pad * r, s));
-        ASK_CUDA(cudaMemsetAsync(t->Ws, 0, sizeof(float) * srows * r, s));
-        t->r = r;
-    }
-    ASK_TRY(upward_weights(t, W_dev, r, ldw, s));
-    t->weights_ready = true;
-    return ASKIT_OK;
+    if (!t) { askit_set_error("tree is NULL"); return ASKIT_ERR_INVALID_ARG; }
+    return set_weights_ctx(t, t->dw, W_dev, r, ldw, (cudaStream_t)stream);
 }
 
 askit_status askit_set_precision(askit_tree t, int32_t precision) {
@@ -335,21 +334,29 @@ askit_status askit_set_precision(askit_tree t, int32_t precision) {
 }
 
 askit_status askit_evaluate(askit_tree t, float *U_dev, int64_t ldu, void *stream) {
-    if (!t || !U_dev) { askit_set_error("tree and U_dev must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
-    if (!t->weights_ready) { askit_set_error("askit_set_weights has not been called"); return ASKIT_ERR_NOT_READY; }
-    if (ldu < t->r) { askit_set_error("ldu < r"); return ASKIT_ERR_INVALID_ARG; }
-    return run_eval(t, t->precision, t->Xt, t->d_pad, t->N_pad, t->wl, t->partial, t->perm, U_dev, ldu,
-                    (cudaStream_t)stream);
+    if (!t) { askit_set_error("tree is NULL"); return ASKIT_ERR_INVALID_ARG; }
+    return evaluate_ctx(t, t->dw, U_dev, ldu, (cudaStream_t)stream);
 }
 
 askit_status askit_evaluate_targets(askit_tree t, const float *Y_dev, int64_t T, int64_t ldy, float *U_dev,
                                     int64_t ldu, void *stream) {
-    if (!t || !Y_dev || !U_dev) { askit_set_error("tree, Y_dev and U_dev must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
-    if (!t->weights_ready) { askit_set_error("askit_set_weights has not been called"); return ASKIT_ERR_NOT_READY; }
-    if (T < 1 || ldy < t->d || ldu < t->r) { askit_set_error("need T >= 1, ldy >= d, ldu >= r"); return ASKIT_ERR_INVALID_ARG; }
-    cudaStream_t s = (cudaStream_t)stream;
+    if (!t) { askit_set_error("tree is NULL"); return ASKIT_ERR_INVALID_ARG; }
+    return evaluate_targets_ctx(t, t->dw, Y_dev, T, ldy, U_dev, ldu, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+askit_status evaluate_targets_ctx(askit_tree t, const WeightCtx &c, const float *Y_dev, int64_t T, int64_t ldy,
+                                  float *U_dev, int64_t ldu, cudaStream_t s) {
+    if (!Y_dev || !U_dev) { askit_set_error("Y_dev and U_dev must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
+    if (!c.ready) { askit_set_error("no weights set"); return ASKIT_ERR_NOT_READY; }
+    if (T < 1 || ldy < t->d || ldu < c.r) { askit_set_error("need T >= 1, ldy >= d, ldu >= r"); return ASKIT_ERR_INVALID_ARG; }
     const int kappa = t->kappa, d = t->d;
+    // per-call temporaries are stream-ordered: releasing them does not
+    // synchronize the device, so concurrent calls on other streams overlap
     DevArena tmp;
+    tmp.async = true;
+    tmp.stream = s;
     float *Yc = nullptr, *Yt = nullptr, *nrm = nullptr;
     int32_t *ids = nullptr, *ids_s = nullptr, *order = nullptr, *vals = nullptr, *sets = nullptr;
     double *dist = nullptr;
@@ -381,15 +388,17 @@ askit_status askit_evaluate_targets(askit_tree t, const float *Y_dev, int64_t T,
     OTRY(tmp.alloc(&sets, (size_t)T * kappa));
     OTRY(oos_prune_sets(t, ids_s, T, kappa, sets, s));
     OTRY(build_work_lists(t, sets, kappa, T, w, tmp, s));
-    OTRY(tmp.alloc(&partial, (size_t)w.n_entries * t->r));
-    OTRY(run_eval(t, t->precision, Yt, t->d_pad, T_pad, w, partial, order, U_dev, ldu, s));
+    OTRY(tmp.alloc(&partial, (size_t)w.n_entries * c.r));
+    OTRY(run_eval(t, c, t->precision, Yt, t->d_pad, T_pad, w, partial, order, U_dev, ldu, s));
     if (cudaStreamSynchronize(s) != cudaSuccess) { askit_set_error("out-of-sample evaluate: %s", cudaGetErrorString(cudaGetLastError())); rc = ASKIT_ERR_CUDA; }
 out:
 #undef OTRY
-    cudaStreamSynchronize(s);
     tmp.free_all();
+    cudaStreamSynchronize(s);
     return rc;
 }
+
+extern "C" {
 
 askit_status askit_evaluate_host(askit_tree t, const float *W_host, int32_t r, int64_t ldw, float *U_host,
                                  int64_t ldu, void *stream) {
@@ -423,7 +432,7 @@ askit_status askit_get_info(askit_tree t, askit_info *info) {
     info->d_pad = t->d_pad;
     info->L = t->L;
     info->kappa = t->kappa;
-    info->r = t->r;
+    info->r = t->dw.r;
     info->n_nodes = t->n_nodes;
     info->skel_total = t->skel_total;
     info->skel_rows_padded = t->spool_rows;
@@ -469,14 +478,15 @@ askit_status askit_get_structure(askit_tree t, int32_t which, void *host, size_t
         case ASKIT_STRUCT_HSRC: src = t->hsrc; want = sizeof(float) * N; break;
         case ASKIT_STRUCT_P: src = t->P64; want = sizeof(double) * t->p_total; break;
         case ASKIT_STRUCT_WSKEL: {
-            if (!t->weights_ready) { askit_set_error("no weights set"); return ASKIT_ERR_NOT_READY; }
-            want = sizeof(float) * t->skel_total * t->r;
+            const WeightCtx &c = t->dw;
+            if (!c.ready) { askit_set_error("no weights set"); return ASKIT_ERR_NOT_READY; }
+            want = sizeof(float) * t->skel_total * c.r;
             if (bytes != want) break;
             float *h = (float *)host;
             for (int64_t a = 2; a < nn; ++a) {
                 if (!t->h_s[a]) continue;
-                ASK_CUDA(cudaMemcpy(h + t->h_skoff[a] * t->r, t->Ws + t->h_spool[a] * t->r,
-                                    sizeof(float) * t->h_s[a] * t->r, cudaMemcpyDeviceToHost));
+                ASK_CUDA(cudaMemcpy(h + t->h_skoff[a] * c.r, c.Ws + t->h_spool[a] * c.r,
+                                    sizeof(float) * t->h_s[a] * c.r, cudaMemcpyDeviceToHost));
             }
             return ASKIT_OK;
         }
@@ -504,8 +514,141 @@ askit_status askit_destroy(askit_tree t) {
     if (!t) return ASKIT_OK;
     cudaDeviceSynchronize();
     eval_tc_free(t);
+    t->dw.arena.free_all();
     t->arena.free_all();
     delete t;
+    return ASKIT_OK;
+}
+
+askit_status askit_weights_create(askit_tree t, askit_weights *out) {
+    if (!t || !out) { askit_set_error("tree and out must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
+    askit_weights w = new askit_weights_s();
+    w->t = t;
+    *out = w;
+    return ASKIT_OK;
+}
+
+askit_status askit_weights_set(askit_weights w, const float *W_dev, int32_t r, int64_t ldw, void *stream) {
+    if (!w) { askit_set_error("weights handle is NULL"); return ASKIT_ERR_INVALID_ARG; }
+    return set_weights_ctx(w->t, w->ctx, W_dev, r, ldw, (cudaStream_t)stream);
+}
+
+askit_status askit_weights_evaluate(askit_weights w, float *U_dev, int64_t ldu, void *stream) {
+    if (!w) { askit_set_error("weights handle is NULL"); return ASKIT_ERR_INVALID_ARG; }
+    return evaluate_ctx(w->t, w->ctx, U_dev, ldu, (cudaStream_t)stream);
+}
+
+askit_status askit_weights_evaluate_targets(askit_weights w, const float *Y_dev, int64_t T, int64_t ldy,
+                                            float *U_dev, int64_t ldu, void *stream) {
+    if (!w) { askit_set_error("weights handle is NULL"); return ASKIT_ERR_INVALID_ARG; }
+    return evaluate_targets_ctx(w->t, w->ctx, Y_dev, T, ldy, U_dev, ldu, (cudaStream_t)stream);
+}
+
+askit_status askit_weights_destroy(askit_weights w) {
+    if (!w) return ASKIT_OK;
+    cudaDeviceSynchronize();
+    w->ctx.arena.free_all();
+    delete w;
+    return ASKIT_OK;
+}
+
+askit_status askit_graph_create(askit_tree t, const float *W_dev, int32_t r, int64_t ldw, float *U_dev,
+                                int64_t ldu, void *stream, askit_graph *out) {
+    if (!t || !out || !U_dev) { askit_set_error("tree, U_dev and out must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (ldu < r) { askit_set_error("ldu < r"); return ASKIT_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    ASK_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) {
+        askit_set_error("askit_graph_create must not run inside a stream capture");
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    askit_graph g = new askit_graph_s();
+    g->t = t;
+    askit_status rc = ASKIT_OK;
+    cudaGraph_t graph = nullptr;
+    // uncaptured step: grows the context's buffers, builds operand state
+    rc = set_weights_ctx(t, g->ctx, W_dev, r, ldw, s);
+    if (rc == ASKIT_OK) rc = evaluate_ctx(t, g->ctx, U_dev, ldu, s);
+    if (rc == ASKIT_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+        askit_set_error("graph warm-up step: %s", cudaGetErrorString(cudaGetLastError()));
+        rc = ASKIT_ERR_CUDA;
+    }
+    // capture on a private stream: the caller's may be the legacy default
+    // stream, which cannot be captured
+    cudaStream_t cs = nullptr;
+    if (rc == ASKIT_OK && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        askit_set_error("capture stream: %s", cudaGetErrorString(cudaGetLastError()));
+        rc = ASKIT_ERR_CUDA;
+    }
+    if (rc == ASKIT_OK) {
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            askit_set_error("begin capture: %s", cudaGetErrorString(cudaGetLastError()));
+            rc = ASKIT_ERR_CUDA;
+        } else {
+            rc = set_weights_ctx(t, g->ctx, W_dev, r, ldw, cs);
+            if (rc == ASKIT_OK) rc = evaluate_ctx(t, g->ctx, U_dev, ldu, cs);
+            cudaError_t e = cudaStreamEndCapture(cs, &graph);      // always end the capture
+            if (rc == ASKIT_OK && e != cudaSuccess) {
+                askit_set_error("end capture: %s", cudaGetErrorString(e));
+                rc = ASKIT_ERR_CUDA;
+            }
+        }
+    }
+    if (cs) cudaStreamDestroy(cs);
+    if (rc == ASKIT_OK && cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) {
+        askit_set_error("graph instantiate: %s", cudaGetErrorString(cudaGetLastError()));
+        rc = ASKIT_ERR_CUDA;
+    }
+    if (graph) {
+        size_t nn = 0;
+        if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess) g->n_nodes = (int64_t)nn;
+        cudaGraphDestroy(graph);
+    }
+    if (rc != ASKIT_OK) {
+        cudaGetLastError();
+        askit_graph_destroy(g);
+        return rc;
+    }
+    *out = g;
+    return ASKIT_OK;
+}
+
+askit_status askit_graph_launch(askit_graph g, void *stream) {
+    if (!g || !g->exec) { askit_set_error("graph is NULL"); return ASKIT_ERR_INVALID_ARG; }
+    ASK_CUDA(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+    return ASKIT_OK;
+}
+
+askit_status askit_graph_destroy(askit_graph g) {
+    if (!g) return ASKIT_OK;
+    cudaDeviceSynchronize();
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    g->ctx.arena.free_all();
+    delete g;
+    return ASKIT_OK;
+}
+
+askit_status askit_footprint(askit_tree t, int32_t kind, int64_t n, int32_t r, size_t *bytes) {
+    if (!t || !bytes || r < 1 || n < 0 || (kind != 0 && kind != 1)) {
+        askit_set_error("need a tree, kind 0 or 1, n >= 0, r >= 1 and bytes");
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    const int64_t srows = std::max<int64_t>(t->spool_rows, 1) + 256;
+    const double per_target = (double)t->wl.n_entries / std::max<int64_t>(1, t->N);
+    size_t b = 0;
+    if (kind == 0) {
+        // a weight context: W in tree order, skeleton weights, partials
+        b = sizeof(float) * ((size_t)t->N_pad * r + (size_t)srows * r + (size_t)t->wl.n_entries * r);
+    } else {
+        // an out-of-sample batch of n targets: queries, kNN, prune sets and
+        // work lists (entries estimated from the in-sample rate, doubled)
+        const double ent = 2.0 * per_target * n + 1024;
+        b = (size_t)(n * ((size_t)t->d * 4 + (size_t)t->d_pad * 4 + (size_t)t->kappa * (4 + 8 + 4 + 4) + 64) +
+                     ent * (8 * 4 + 4 + 4 * r + 32 / 128.0) + (1 << 20));
+    }
+    *bytes = b;
     return ASKIT_OK;
 }
 

@@ -269,47 +269,54 @@ askit_status build_eval_operands(askit_tree t, cudaStream_t s) {
 }
 
 // One CTA per source sub-block: its center (FP64 mean of the valid rows,
-// rounded), the centered rows split for the tensor cores -- TF32: hi = the
-// FP32 value with the 13 low mantissa bits cleared, lo = x - hi; BF16: hi =
-// bf16(x), lo = bf16(x - hi) -- and the squared norms of the centered rows.
-__global__ void tc_prep_kernel(const float *X, int d_pad, const int64_t *sb_row0, const int32_t *sb_nrows,
+// rounded), the centered rows split for the tensor cores -- TF32 (narrow
+// rows only): hi = the FP32 value with the 13 low mantissa bits cleared,
+// lo = x - hi; BF16: hi = bf16(x), lo = bf16(x - hi); FP16 likewise on the
+// prescaled value -- and the squared norms of the centered rows.  Rows are
+// kw wide (zeros past d); one warp per row, lanes across the columns.
+__global__ void tc_prep_kernel(const float *X, int d_pad, int kw, const int64_t *sb_row0, const int32_t *sb_nrows,
                                int64_t rows_total, float f16_scale, float *cent, float *Xhi, float *Xlo,
                                uint16_t *Bhi, uint16_t *Blo, uint16_t *Hhi, uint16_t *Hlo, float *nrmc) {
-    int g = blockIdx.x;
-    int64_t r0 = sb_row0[g];
-    int nr = sb_nrows[g];
-    __shared__ float c[TC_K];
-    for (int k = threadIdx.x; k < TC_K; k += blockDim.x) {
+    extern __shared__ float c[];   // [kw]
+    const int g = blockIdx.x;
+    const int64_t r0 = sb_row0[g];
+    const int nr = sb_nrows[g];
+    for (int k = threadIdx.x; k < kw; k += blockDim.x) {
         double acc = 0.0;
         if (k < d_pad)
             for (int q = 0; q < nr; ++q) acc += (double)X[(r0 + q) * d_pad + k];
         c[k] = nr > 0 ? (float)(acc / nr) : 0.f;
-        cent[(int64_t)g * TC_K + k] = c[k];
+        cent[(int64_t)g * kw + k] = c[k];
     }
     __syncthreads();
     // only the sub-block's own rows: the 128-row window of a short sub-block
     // overlaps the next one, whose rows its own CTA writes
-    for (int q = threadIdx.x; q < nr; q += blockDim.x) {
-        int64_t row = r0 + q;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = warp; q < nr; q += nw) {
+        const int64_t row = r0 + q;
         if (row >= rows_total) break;
         double nn = 0.0;
-        for (int k = 0; k < TC_K; ++k) {
-            float x = (k < d_pad) ? X[row * d_pad + k] - c[k] : 0.f;
+        for (int k = lane; k < kw; k += 32) {
+            const float x = (k < d_pad) ? X[row * d_pad + k] - c[k] : 0.f;
             nn += (double)x * x;
-            float hi = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
-            Xhi[row * TC_K + k] = hi;
-            Xlo[row * TC_K + k] = x - hi;
-            __nv_bfloat16 bh = __float2bfloat16_rn(x);
-            __nv_bfloat16 bl = __float2bfloat16_rn(x - __bfloat162float(bh));
-            Bhi[row * TC_K + k] = *reinterpret_cast<uint16_t *>(&bh);
-            Blo[row * TC_K + k] = *reinterpret_cast<uint16_t *>(&bl);
+            const int64_t o = row * kw + k;
+            if (Xhi) {
+                const float hi = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+                Xhi[o] = hi;
+                Xlo[o] = x - hi;
+            }
+            const __nv_bfloat16 bh = __float2bfloat16_rn(x);
+            const __nv_bfloat16 bl = __float2bfloat16_rn(x - __bfloat162float(bh));
+            Bhi[o] = __bfloat16_as_ushort(bh);
+            Blo[o] = __bfloat16_as_ushort(bl);
             const float xs = x * f16_scale;
-            __half hh = __float2half_rn(xs);
-            __half hl = __float2half_rn(xs - __half2float(hh));
-            Hhi[row * TC_K + k] = __half_as_ushort(hh);
-            Hlo[row * TC_K + k] = __half_as_ushort(hl);
+            const __half hh = __float2half_rn(xs);
+            const __half hl = __float2half_rn(xs - __half2float(hh));
+            Hhi[o] = __half_as_ushort(hh);
+            Hlo[o] = __half_as_ushort(hl);
         }
-        nrmc[row] = (float)nn;
+        for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+        if (lane == 0) nrmc[row] = (float)nn;
     }
 }
 
@@ -349,7 +356,13 @@ askit_status build_tc_operands(askit_tree t, cudaStream_t s) {
     ASK_TRY(t->arena.alloc(&t->node_cbase, nn));
     ASK_CUDA(cudaMemcpyAsync(t->leaf_cbase, lcb.data(), sizeof(int32_t) * M, cudaMemcpyHostToDevice, s));
     ASK_CUDA(cudaMemcpyAsync(t->node_cbase, ncb.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice, s));
-    if (t->d > TC_K) return ASKIT_OK;   // the tensor-core operands cover d <= TC_K
+    // narrow rows (d <= TC_K) get TC_K columns and all three splits; wide
+    // rows are rounded up to a multiple of 64 columns and get the 16-bit
+    // splits only
+    const bool wide = t->d > TC_K;
+    const int kw = wide ? (t->d_pad + 63) / 64 * 64 : TC_K;
+    if (kw > 8192) return ASKIT_OK;     // no tensor-core operands (plain FP32 path only)
+    t->kw = kw;
     int64_t *d_r0 = nullptr;
     int32_t *d_nr = nullptr;
     ASK_CUDA(cudaMalloc(&d_r0, sizeof(int64_t) * std::max<int64_t>(1, t->n_sub)));
@@ -357,35 +370,26 @@ askit_status build_tc_operands(askit_tree t, cudaStream_t s) {
     ASK_CUDA(cudaMemcpyAsync(d_r0, r0.data(), sizeof(int64_t) * t->n_sub, cudaMemcpyHostToDevice, s));
     ASK_CUDA(cudaMemcpyAsync(d_nr, nr.data(), sizeof(int32_t) * t->n_sub, cudaMemcpyHostToDevice, s));
     t->srows = std::max<int64_t>(t->spool_rows, 1) + 256;
-    ASK_TRY(t->arena.alloc(&t->cent, (size_t)std::max<int64_t>(1, t->n_sub) * TC_K));
-    ASK_TRY(t->arena.alloc(&t->Xt_hi, (size_t)t->N_pad * TC_K));
-    ASK_TRY(t->arena.alloc(&t->Xt_lo, (size_t)t->N_pad * TC_K));
-    ASK_TRY(t->arena.alloc(&t->Xs_hi, (size_t)t->srows * TC_K));
-    ASK_TRY(t->arena.alloc(&t->Xs_lo, (size_t)t->srows * TC_K));
-    ASK_TRY(t->arena.alloc(&t->Xt_bhi, (size_t)t->N_pad * TC_K));
-    ASK_TRY(t->arena.alloc(&t->Xt_blo, (size_t)t->N_pad * TC_K));
-    ASK_TRY(t->arena.alloc(&t->Xs_bhi, (size_t)t->srows * TC_K));
-    ASK_TRY(t->arena.alloc(&t->Xs_blo, (size_t)t->srows * TC_K));
-    ASK_TRY(t->arena.alloc(&t->Xt_hhi, (size_t)t->N_pad * TC_K));
-    ASK_TRY(t->arena.alloc(&t->Xt_hlo, (size_t)t->N_pad * TC_K));
-    ASK_TRY(t->arena.alloc(&t->Xs_hhi, (size_t)t->srows * TC_K));
-    ASK_TRY(t->arena.alloc(&t->Xs_hlo, (size_t)t->srows * TC_K));
-    ASK_CUDA(cudaMemsetAsync(t->Xt_hhi, 0, sizeof(uint16_t) * t->N_pad * TC_K, s));
-    ASK_CUDA(cudaMemsetAsync(t->Xt_hlo, 0, sizeof(uint16_t) * t->N_pad * TC_K, s));
-    ASK_CUDA(cudaMemsetAsync(t->Xs_hhi, 0, sizeof(uint16_t) * t->srows * TC_K, s));
-    ASK_CUDA(cudaMemsetAsync(t->Xs_hlo, 0, sizeof(uint16_t) * t->srows * TC_K, s));
+    const size_t et = (size_t)t->N_pad * kw, es = (size_t)t->srows * kw;
+    ASK_TRY(t->arena.alloc(&t->cent, (size_t)std::max<int64_t>(1, t->n_sub) * kw));
+    if (!wide) {
+        ASK_TRY(t->arena.alloc(&t->Xt_hi, et));
+        ASK_TRY(t->arena.alloc(&t->Xt_lo, et));
+        ASK_TRY(t->arena.alloc(&t->Xs_hi, es));
+        ASK_TRY(t->arena.alloc(&t->Xs_lo, es));
+        ASK_CUDA(cudaMemsetAsync(t->Xt_hi, 0, sizeof(float) * et, s));
+        ASK_CUDA(cudaMemsetAsync(t->Xt_lo, 0, sizeof(float) * et, s));
+        ASK_CUDA(cudaMemsetAsync(t->Xs_hi, 0, sizeof(float) * es, s));
+        ASK_CUDA(cudaMemsetAsync(t->Xs_lo, 0, sizeof(float) * es, s));
+    }
+    uint16_t **h16[8] = {&t->Xt_bhi, &t->Xt_blo, &t->Xt_hhi, &t->Xt_hlo, &t->Xs_bhi, &t->Xs_blo, &t->Xs_hhi, &t->Xs_hlo};
+    for (int i = 0; i < 8; ++i) {
+        const size_t n = i < 4 ? et : es;
+        ASK_TRY(t->arena.alloc(h16[i], n));
+        ASK_CUDA(cudaMemsetAsync(*h16[i], 0, sizeof(uint16_t) * n, s));
+    }
     ASK_TRY(t->arena.alloc(&t->nrmc_t, t->N_pad));
     ASK_TRY(t->arena.alloc(&t->nrmc_s, t->srows));
-    ASK_TRY(t->arena.alloc(&t->Ct, t->N_pad));
-    ASK_TRY(t->arena.alloc(&t->Cs, t->srows));
-    ASK_CUDA(cudaMemsetAsync(t->Xt_hi, 0, sizeof(float) * t->N_pad * TC_K, s));
-    ASK_CUDA(cudaMemsetAsync(t->Xt_lo, 0, sizeof(float) * t->N_pad * TC_K, s));
-    ASK_CUDA(cudaMemsetAsync(t->Xs_hi, 0, sizeof(float) * t->srows * TC_K, s));
-    ASK_CUDA(cudaMemsetAsync(t->Xs_lo, 0, sizeof(float) * t->srows * TC_K, s));
-    ASK_CUDA(cudaMemsetAsync(t->Xt_bhi, 0, sizeof(uint16_t) * t->N_pad * TC_K, s));
-    ASK_CUDA(cudaMemsetAsync(t->Xt_blo, 0, sizeof(uint16_t) * t->N_pad * TC_K, s));
-    ASK_CUDA(cudaMemsetAsync(t->Xs_bhi, 0, sizeof(uint16_t) * t->srows * TC_K, s));
-    ASK_CUDA(cudaMemsetAsync(t->Xs_blo, 0, sizeof(uint16_t) * t->srows * TC_K, s));
     ASK_CUDA(cudaMemsetAsync(t->nrmc_t, 0, sizeof(float) * t->N_pad, s));
     ASK_CUDA(cudaMemsetAsync(t->nrmc_s, 0, sizeof(float) * t->srows, s));
     // FP16 prescale: a power of 2 that maps the data's widest coordinate
@@ -404,14 +408,15 @@ askit_status build_tc_operands(askit_tree t, cudaStream_t s) {
         if (hext > 0.f) frexpf(16384.f / (2.f * hext), &e);
         t->f16_scale = ldexpf(1.f, e - 1);
     }
+    const size_t csm = sizeof(float) * kw;
     if (n_leaf_sub > 0)
-        tc_prep_kernel<<<(unsigned)n_leaf_sub, 128, 0, s>>>(t->Xt, t->d_pad, d_r0, d_nr, t->N_pad, t->f16_scale, t->cent,
-                                                          t->Xt_hi, t->Xt_lo, t->Xt_bhi, t->Xt_blo, t->Xt_hhi,
-                                                          t->Xt_hlo, t->nrmc_t);
+        tc_prep_kernel<<<(unsigned)n_leaf_sub, 256, csm, s>>>(t->Xt, t->d_pad, kw, d_r0, d_nr, t->N_pad, t->f16_scale,
+                                                            t->cent, t->Xt_hi, t->Xt_lo, t->Xt_bhi, t->Xt_blo,
+                                                            t->Xt_hhi, t->Xt_hlo, t->nrmc_t);
     if (t->n_sub > n_leaf_sub)
-        tc_prep_kernel<<<(unsigned)(t->n_sub - n_leaf_sub), 128, 0, s>>>(
-            t->Xs, t->d_pad, d_r0 + n_leaf_sub, d_nr + n_leaf_sub, t->srows, t->f16_scale,
-            t->cent + n_leaf_sub * TC_K, t->Xs_hi, t->Xs_lo, t->Xs_bhi, t->Xs_blo, t->Xs_hhi, t->Xs_hlo, t->nrmc_s);
+        tc_prep_kernel<<<(unsigned)(t->n_sub - n_leaf_sub), 256, csm, s>>>(
+            t->Xs, t->d_pad, kw, d_r0 + n_leaf_sub, d_nr + n_leaf_sub, t->srows, t->f16_scale,
+            t->cent + n_leaf_sub * kw, t->Xs_hi, t->Xs_lo, t->Xs_bhi, t->Xs_blo, t->Xs_hhi, t->Xs_hlo, t->nrmc_s);
     ASK_LAUNCH();
     ASK_CUDA(cudaStreamSynchronize(s));
     cudaFree(d_r0);
@@ -460,42 +465,42 @@ askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, int
     w.T = T;
 #define WCHK(x) do { e = (x); if (e != cudaSuccess) goto fail; } while (0)
 #define WTRY(x) do { rc = (x); if (rc != ASKIT_OK) goto out; } while (0)
-    WCHK(cudaMalloc(&cnt, sizeof(int64_t) * (T + 1)));
-    WCHK(cudaMalloc(&nearc, sizeof(int64_t) * T));
-    WCHK(cudaMalloc(&farc, sizeof(int64_t) * T));
-    WCHK(cudaMalloc(&pairs, sizeof(int64_t) * T));
+    WCHK(cudaMallocAsync(&cnt, sizeof(int64_t) * (T + 1), s));
+    WCHK(cudaMallocAsync(&nearc, sizeof(int64_t) * T, s));
+    WCHK(cudaMallocAsync(&farc, sizeof(int64_t) * T, s));
+    WCHK(cudaMallocAsync(&pairs, sizeof(int64_t) * T, s));
     WTRY(arena.alloc(&w.off, T + 1));
     WCHK(cudaMemsetAsync(cnt + T, 0, sizeof(int64_t), s));
     count_kernel<<<nblk(T, 128), 128, 0, s>>>(sets, stride, T, t->L, t->nsize, t->d_s, cnt, nearc, farc, pairs);
     WCHK(cudaGetLastError());
     WTRY(scan_i64(nullptr, nullptr, T + 1, nullptr, &tb, s));
-    WCHK(cudaMalloc(&tmp, tb));
+    WCHK(cudaMallocAsync(&tmp, tb, s));
     WTRY(scan_i64(cnt, w.off, T + 1, tmp, &tb, s));
     WCHK(cudaMemcpyAsync(&total, w.off + T, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     WCHK(cudaMemcpyAsync(h_near.data(), nearc, sizeof(int64_t) * T, cudaMemcpyDeviceToHost, s));
     WCHK(cudaMemcpyAsync(h_far.data(), farc, sizeof(int64_t) * T, cudaMemcpyDeviceToHost, s));
     WCHK(cudaMemcpyAsync(h_pairs.data(), pairs, sizeof(int64_t) * T, cudaMemcpyDeviceToHost, s));
     WCHK(cudaStreamSynchronize(s));
-    cudaFree(tmp);
+    cudaFreeAsync(tmp, s);
     tmp = nullptr;
     w.n_entries = total;
-    WCHK(cudaMalloc(&keys, sizeof(uint64_t) * total));
-    WCHK(cudaMalloc(&keys_s, sizeof(uint64_t) * total));
-    WCHK(cudaMalloc(&vals, sizeof(int64_t) * total));
-    WCHK(cudaMalloc(&emit_of, sizeof(int64_t) * total));
+    WCHK(cudaMallocAsync(&keys, sizeof(uint64_t) * total, s));
+    WCHK(cudaMallocAsync(&keys_s, sizeof(uint64_t) * total, s));
+    WCHK(cudaMallocAsync(&vals, sizeof(int64_t) * total, s));
+    WCHK(cudaMallocAsync(&emit_of, sizeof(int64_t) * total, s));
     emit_kernel<<<nblk(T, 128), 128, 0, s>>>(sets, stride, T, t->L, t->nsize, t->d_s, w.off, keys, vals);
     WCHK(cudaGetLastError());
     WTRY(sort_u64_i64(nullptr, nullptr, nullptr, nullptr, total, nullptr, &tb, s));
     WTRY(scan_i64(nullptr, nullptr, total, nullptr, &tb2, s));
     tb = std::max(tb, tb2);
-    WCHK(cudaMalloc(&tmp, tb));
+    WCHK(cudaMallocAsync(&tmp, tb, s));
     WTRY(sort_u64_i64(keys, keys_s, vals, emit_of, total, tmp, &tb, s));
     WTRY(arena.alloc(&w.slot_of_emit, total));
     WTRY(arena.alloc(&w.tgt, total));
-    WCHK(cudaMalloc(&bflag, sizeof(int64_t) * total));
-    WCHK(cudaMalloc(&bidx, sizeof(int64_t) * total));
-    WCHK(cudaMalloc(&iflag, sizeof(int64_t) * total));
-    WCHK(cudaMalloc(&iidx, sizeof(int64_t) * total));
+    WCHK(cudaMallocAsync(&bflag, sizeof(int64_t) * total, s));
+    WCHK(cudaMallocAsync(&bidx, sizeof(int64_t) * total, s));
+    WCHK(cudaMallocAsync(&iflag, sizeof(int64_t) * total, s));
+    WCHK(cudaMallocAsync(&iidx, sizeof(int64_t) * total, s));
     scatter_kernel<<<nblk(total, 256), 256, 0, s>>>(keys_s, emit_of, total, w.slot_of_emit, w.tgt, bflag);
     WCHK(cudaGetLastError());
     WTRY(scan_i64(bflag, bidx, total, tmp, &tb, s));
@@ -506,7 +511,7 @@ askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, int
         WCHK(cudaStreamSynchronize(s));
         nb = lastb + lastf;
     }
-    WCHK(cudaMalloc(&bstart, sizeof(int64_t) * nb));
+    WCHK(cudaMallocAsync(&bstart, sizeof(int64_t) * nb, s));
     block_start_kernel<<<nblk(total, 256), 256, 0, s>>>(bflag, bidx, total, bstart);
     item_flag_kernel<<<nblk(total, 256), 256, 0, s>>>(bflag, bidx, bstart, total, iflag);
     WCHK(cudaGetLastError());
@@ -594,9 +599,9 @@ out:
 #undef WCHK
 #undef WTRY
     cudaStreamSynchronize(s);
-    cudaFree(cnt); cudaFree(nearc); cudaFree(farc); cudaFree(pairs); cudaFree(vals); cudaFree(emit_of);
-    cudaFree(bflag); cudaFree(bidx); cudaFree(bstart); cudaFree(iflag); cudaFree(iidx);
-    cudaFree(keys); cudaFree(keys_s); cudaFree(tmp);
+    for (void *q : {(void *)cnt, (void *)nearc, (void *)farc, (void *)pairs, (void *)vals, (void *)emit_of, (void *)bflag,
+                    (void *)bidx, (void *)bstart, (void *)iflag, (void *)iidx, (void *)keys, (void *)keys_s, tmp})
+        if (q) cudaFreeAsync(q, s);
     return rc;
 }
 

@@ -95,14 +95,14 @@ __global__ void __launch_bounds__(ASK_TILE_M) eval_simt_kernel(
 
 }  // namespace
 
-askit_status eval_simt(askit_tree t, const float *Xq, int64_t ldq, const WorkLists &w, float *partial,
-                       cudaStream_t s) {
+askit_status eval_simt(askit_tree t, const WeightCtx &c, const float *Xq, int64_t ldq, const WorkLists &w,
+                       float *partial, cudaStream_t s) {
     if (w.n_blocks == 0) return ASKIT_OK;
-    int r = t->r;
+    int r = c.r;
 #define LAUNCH(R)                                                                                   \
     eval_simt_kernel<R><<<(unsigned)w.n_blocks, ASK_TILE_M, 0, s>>>(                                \
         Xq, ldq, w.items, w.block_off, w.block_order, w.tgt, partial, t->Xt, t->Xs, t->sc_t,        \
-        t->sc_s, t->Wt, t->Ws, t->d_pad, r)
+        t->sc_s, c.Wt, c.Ws, t->d_pad, r)
     if (r <= 1) LAUNCH(1);
     else if (r <= 4) LAUNCH(4);
     else if (r <= 16) LAUNCH(16);
@@ -167,16 +167,17 @@ __global__ void __launch_bounds__(DIRECT_THREADS) direct_kernel(const float *__r
 extern "C" askit_status askit_direct(askit_tree t, const int32_t *tgt_dev, int64_t T, float *U_dev, int64_t ldu,
                                      void *stream) {
     if (!t || !tgt_dev || !U_dev) { askit_set_error("tree, tgt_dev and U_dev must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
-    if (!t->weights_ready) { askit_set_error("askit_set_weights has not been called"); return ASKIT_ERR_NOT_READY; }
-    if (T < 1 || T > (1 << 30) || ldu < t->r) { askit_set_error("need 1 <= T and ldu >= r"); return ASKIT_ERR_INVALID_ARG; }
+    if (!t->dw.ready) { askit_set_error("askit_set_weights has not been called"); return ASKIT_ERR_NOT_READY; }
+    if (T < 1 || T > (1 << 30) || ldu < t->dw.r) { askit_set_error("need 1 <= T and ldu >= r"); return ASKIT_ERR_INVALID_ARG; }
     if (t->d_pad > 1024) { askit_set_error("askit_direct handles d <= 1024"); return ASKIT_ERR_UNSUPPORTED; }
     cudaStream_t s = (cudaStream_t)stream;
-    if (t->r <= 1)
-        direct_kernel<1><<<(unsigned)T, DIRECT_THREADS, 0, s>>>(t->X, t->d, tgt_dev, t->Xt, t->d_pad, t->N, t->sc_t, t->Wt, t->r, U_dev, ldu);
-    else if (t->r <= 16)
-        direct_kernel<16><<<(unsigned)T, DIRECT_THREADS, 0, s>>>(t->X, t->d, tgt_dev, t->Xt, t->d_pad, t->N, t->sc_t, t->Wt, t->r, U_dev, ldu);
+    const WeightCtx &c = t->dw;
+    if (c.r <= 1)
+        direct_kernel<1><<<(unsigned)T, DIRECT_THREADS, 0, s>>>(t->X, t->d, tgt_dev, t->Xt, t->d_pad, t->N, t->sc_t, c.Wt, c.r, U_dev, ldu);
+    else if (c.r <= 16)
+        direct_kernel<16><<<(unsigned)T, DIRECT_THREADS, 0, s>>>(t->X, t->d, tgt_dev, t->Xt, t->d_pad, t->N, t->sc_t, c.Wt, c.r, U_dev, ldu);
     else
-        direct_kernel<64><<<(unsigned)T, DIRECT_THREADS, 0, s>>>(t->X, t->d, tgt_dev, t->Xt, t->d_pad, t->N, t->sc_t, t->Wt, t->r, U_dev, ldu);
+        direct_kernel<64><<<(unsigned)T, DIRECT_THREADS, 0, s>>>(t->X, t->d, tgt_dev, t->Xt, t->d_pad, t->N, t->sc_t, c.Wt, c.r, U_dev, ldu);
     ASK_LAUNCH();
     return ASKIT_OK;
 }

@@ -36,15 +36,19 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <mutex>
+
 #include "askit_impl.cuh"
+#include "tc_ptx.cuh"
 
 namespace {
+
+using namespace tcx;
 
 constexpr int TC_THREADS = 448;
 constexpr int TILE_ROWS = 128;                  // M = N = 128
 constexpr int REGION = TILE_ROWS * 128;         // one 128-row x 128-byte swizzled region (16 KB)
 constexpr uint32_t TMEM_COLS = 256;             // two 128-column FP32 accumulators
-constexpr int SPIN_LIMIT = 1 << 24;
 
 // Precision traits: element bytes, swizzle regions per operand (TC_K
 // elements x element bytes / 128), MMA K steps, tcgen05 operand format.
@@ -61,131 +65,6 @@ template <> struct Prec<ASKIT_PREC_FP16X3> {
     static constexpr int EB = 2, NREG = 1, KSTEPS = 4;   // K = 16 per MMA
     static constexpr uint32_t FMT = 0;                   // F16 in .kind::f16
 };
-
-// Instruction descriptor of .kind::tf32 / .kind::f16: D = F32 (bits 4-5),
-// A and B format (bits 7-9, 10-12), both K-major, N >> 3 (bits 17-22),
-// M >> 4 (bits 24-28).
-__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, int M, int N) {
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// Shared-memory matrix descriptor for a K-major operand in the 128-byte
-// swizzle: start address >> 4, leading-byte offset (unused for this layout,
-// 1), stride-byte offset 1024 B between 8-row core-matrix groups, the
-// descriptor version bit 46, swizzle mode 2 (128 B) in bits 61-63.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on the phase of the given parity.  Returns false when the
-// kernel is aborting (another role timed out) or this wait timed out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *status) {
-    for (int it = 0; it < SPIN_LIMIT; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 1023) == 1023 && *abort_flag) return false;
-    }
-    *abort_flag = 1;
-    atomicExch(status, ASK_DEV_TIMEOUT);
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
-// Four rows (r0..r3) of a 2D FP32 tensor, one box row each, into consecutive
-// box rows at dst (tile::gather4).
-__device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap *map, int x, int r0, int r1, int r2,
-                                            int r3, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
-        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(bar)
-        : "memory");
-}
-
-// Plain bulk copy global -> shared (16-byte aligned, size a multiple of 16).
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(dst), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-template <int P>
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
-    if constexpr (P == ASKIT_PREC_TF32X3) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-            ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accum)
-            : "memory");
-    } else {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-            ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accum)
-            : "memory");
-    }
-}
-
-// 32 consecutive FP32 columns of this warp's 32 TMEM lanes (one row per thread).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
-        : "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
 // Shared-memory plan (offsets from a 1024-byte aligned base).
 template <int P>
@@ -569,7 +448,7 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
         // ---------------------------------------------- target-row gatherer (warp 13)
         if constexpr (S::GATHER) {
             const uint32_t bytes = (uint32_t)(TILE_ROWS * args.d_pad * 4);
-            int li = 0;
+            int li = 0, issued = 0;
             for (int ci = args.cta_off[blockIdx.x]; ci < args.cta_off[blockIdx.x + 1] && !*abort_flag; ++ci) {
                 const int b = args.cta_blocks[ci];
                 for (int it = args.block_off[b]; it < args.block_off[b + 1]; ++it, ++li) {
@@ -583,24 +462,28 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                         const int row = 4 * lane + i;   // rows past cnt repeat the first target
                         r[i] = row < item.cnt ? args.tgt[item.e0 + row] : first;
                     }
+                    ++issued;
                     if (lane == 0) mbar_expect_tx(BAR_R_FULL(s), bytes);
                     __syncwarp();
                     tma_gather4(sbase + S::RAW + s * S::RAWSTAGE + 4 * lane * args.d_pad * 4, &map_q, 0, r[0], r[1],
                                 r[2], r[3], BAR_R_FULL(s));
                 }
             }
-        gather_done:;
+        gather_done:
+            // rows of the last two items may still be landing after an abort
+            for (int gg = issued > 2 ? issued - 2 : 0; gg < issued; ++gg) mbar_drain(BAR_R_FULL(gg & 1), (gg >> 1) & 1);
         }
     } else if (warp == 12 && lane == 0) {
         // ------------------------------------------------- TMA + MMA issuer
         // hi + lo of one 128-row sub-block, and its raw FP32 rows (gather path)
         const uint32_t TX = 2 * NREG * REGION + (S::GATHER ? (uint32_t)(TILE_ROWS * args.d_pad * 4 + TC_K * 4) : 0u);
-        int li = 0, lb = 0;
+        int li = 0, lb = 0, b_issued = 0;
         for (int ci = args.cta_off[blockIdx.x]; ci < args.cta_off[blockIdx.x + 1] && !*abort_flag; ++ci, ++lb) {
             const int b = args.cta_blocks[ci];
             const EvalItem first = args.items[args.block_off[b]];
             const bool far = first.nrows < 0;
             if (!mbar_wait(BAR_B_EMPTY, (lb & 1) ^ 1, abort_flag, args.status)) goto mma_done;
+            b_issued = lb + 1;
             mbar_expect_tx(BAR_B_FULL, TX);
             const CUtensorMap *mh = far ? &map_s_hi : &map_t_hi;
             const CUtensorMap *ml = far ? &map_s_lo : &map_t_lo;
@@ -645,7 +528,9 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                 if (it == i1 - 1) tc_commit(BAR_B_EMPTY);
             }
         }
-    mma_done:;
+    mma_done:
+        // the last sub-block's copies may still be landing after an abort
+        if (b_issued > 0) mbar_drain(BAR_B_FULL, (b_issued - 1) & 1);
     }
     tc_fence_before();
     __syncthreads();
@@ -663,10 +548,6 @@ struct TcState {
     bool raw_ready = false;
     void *encode = nullptr;     // cuTensorMapEncodeTiled
 };
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 askit_status encode_map(EncodeTiledFn fn, CUtensorMap *m, void *base, int64_t rows, int ty) {
     const bool f32 = ty == 0;
@@ -703,7 +584,10 @@ askit_status encode_raw(EncodeTiledFn fn, CUtensorMap *m, const void *base, int6
     return ASKIT_OK;
 }
 
+std::mutex g_tc_mu;   // tensor-map state and launch attributes are built once, under a lock
+
 askit_status tc_state(askit_tree t, int pi, TcState **out) {
+    std::lock_guard<std::mutex> lock(g_tc_mu);
     if (!t->tc) t->tc = new TcState();
     TcState *st = (TcState *)t->tc;
     if (!st->encode) {
@@ -745,9 +629,12 @@ askit_status launch(askit_tree t, TcState *st, const CUtensorMap &map_q, const T
     const int pi = P == ASKIT_PREC_TF32X3 ? 0 : P == ASKIT_PREC_BF16X3 ? 1 : 2;
     const size_t smem = S::BYTES + 1024;
     static bool attr_set = false;
-    if (!attr_set) {
-        ASK_CUDA(cudaFuncSetAttribute(eval_tc_kernel<P, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
+    {
+        std::lock_guard<std::mutex> lock(g_tc_mu);
+        if (!attr_set) {
+            ASK_CUDA(cudaFuncSetAttribute(eval_tc_kernel<P, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr_set = true;
+        }
     }
     const unsigned grid = (unsigned)a_grid;
     eval_tc_kernel<P, RC><<<grid, TC_THREADS, smem, s>>>(st->map[pi][0], st->map[pi][1], st->map[pi][2],
@@ -758,13 +645,10 @@ askit_status launch(askit_tree t, TcState *st, const CUtensorMap &map_q, const T
 
 }  // namespace
 
-askit_status eval_tc(askit_tree t, int precision, const float *Xq, int64_t ldq, int64_t q_rows,
-                     const WorkLists &w, float *partial, cudaStream_t s) {
-    if (t->d > TC_K) {
-        askit_set_error("tensor-core evaluation covers d <= %d; use ASKIT_PREC_SIMT_FP32", TC_K);
-        return ASKIT_ERR_UNSUPPORTED;
-    }
-    if (t->r > Smem<ASKIT_PREC_TF32X3>::RC_MAX) {
+askit_status eval_tc(askit_tree t, const WeightCtx &c, int precision, const float *Xq, int64_t ldq,
+                     int64_t q_rows, const WorkLists &w, float *partial, cudaStream_t s) {
+    if (t->d > TC_K) return eval_tc_wide(t, c, precision, Xq, ldq, q_rows, w, partial, s);
+    if (c.r > Smem<ASKIT_PREC_TF32X3>::RC_MAX) {
         askit_set_error("tensor-core evaluation covers r <= %d; use ASKIT_PREC_SIMT_FP32", Smem<ASKIT_PREC_TF32X3>::RC_MAX);
         return ASKIT_ERR_UNSUPPORTED;
     }
@@ -792,29 +676,30 @@ askit_status eval_tc(askit_tree t, int precision, const float *Xq, int64_t ldq, 
     a.sc_s = t->sc_s;
     a.Xt = t->Xt;
     a.Xs = t->Xs;
-    a.Wt = t->Wt;
-    a.Ws = t->Ws;
-    a.r = t->r;
+    a.Wt = c.Wt;
+    a.Ws = c.Ws;
+    a.r = c.r;
     a.partial = partial;
     a.status = t->d_status;
     a.f16_scale = precision == ASKIT_PREC_FP16X3 ? t->f16_scale : 1.f;
     a.g_unscale = 1.f / (a.f16_scale * a.f16_scale);
     if (precision == ASKIT_PREC_TF32X3) {
-        if (t->r == 1) return launch<ASKIT_PREC_TF32X3, 1>(t, st, map_q, a, w.n_ctas, s);
-        if (t->r <= 4) return launch<ASKIT_PREC_TF32X3, 4>(t, st, map_q, a, w.n_ctas, s);
+        if (c.r == 1) return launch<ASKIT_PREC_TF32X3, 1>(t, st, map_q, a, w.n_ctas, s);
+        if (c.r <= 4) return launch<ASKIT_PREC_TF32X3, 4>(t, st, map_q, a, w.n_ctas, s);
         return launch<ASKIT_PREC_TF32X3, 16>(t, st, map_q, a, w.n_ctas, s);
     }
     if (precision == ASKIT_PREC_BF16X3) {
-        if (t->r == 1) return launch<ASKIT_PREC_BF16X3, 1>(t, st, map_q, a, w.n_ctas, s);
-        if (t->r <= 4) return launch<ASKIT_PREC_BF16X3, 4>(t, st, map_q, a, w.n_ctas, s);
+        if (c.r == 1) return launch<ASKIT_PREC_BF16X3, 1>(t, st, map_q, a, w.n_ctas, s);
+        if (c.r <= 4) return launch<ASKIT_PREC_BF16X3, 4>(t, st, map_q, a, w.n_ctas, s);
         return launch<ASKIT_PREC_BF16X3, 16>(t, st, map_q, a, w.n_ctas, s);
     }
-    if (t->r == 1) return launch<ASKIT_PREC_FP16X3, 1>(t, st, map_q, a, w.n_ctas, s);
-    if (t->r <= 4) return launch<ASKIT_PREC_FP16X3, 4>(t, st, map_q, a, w.n_ctas, s);
+    if (c.r == 1) return launch<ASKIT_PREC_FP16X3, 1>(t, st, map_q, a, w.n_ctas, s);
+    if (c.r <= 4) return launch<ASKIT_PREC_FP16X3, 4>(t, st, map_q, a, w.n_ctas, s);
     return launch<ASKIT_PREC_FP16X3, 16>(t, st, map_q, a, w.n_ctas, s);
 }
 
 void eval_tc_free(askit_tree t) {
     delete (TcState *)t->tc;
     t->tc = nullptr;
+    eval_tc_wide_free(t);
 }

@@ -205,21 +205,42 @@ __global__ void knn_block_kernel(const float *X, int d, const int32_t *cand, con
         int64_t slot = (qids ? (int64_t)self : q) * 32 + lane;
         double ld = bd[slot];
         int li = bi[slot];
+        // FP32 pre-filter: the FP32 difference-form sum of d squares is within a
+        // factor (1 +- gam) of the exact value, gam = (d + 2) 2^-24 (plus slack),
+        // so a candidate whose FP32 distance exceeds the current kappa-th FP64
+        // distance by that factor cannot enter the list and needs no FP64 work.
+        const float gam = (float)(d + 2) * 5.9604645e-8f * 1.25f + 1e-6f;
         for (int64_t cb = c0; cb < c1; cb += 32) {
             double cd = DBL_MAX;
             int ci = INT_MAX;
+            int j = -1;
+            float d32 = 3.4e38f;
             if (cb + lane < c1) {
-                int j = cand ? cand[cb + lane] : (int)(cb + lane);
+                j = cand ? cand[cb + lane] : (int)(cb + lane);
                 if (j != self) {
                     const float *xj = X + (int64_t)j * d;
-                    double acc = 0.0;
+                    float a = 0.f;
                     for (int k = 0; k < d; ++k) {
-                        double t = c_sub((double)myq[k], (double)xj[k]);
-                        acc = c_add(acc, c_mul(t, t));
+                        const float t = myq[k] - xj[k];
+                        a = fmaf(t, t, a);
                     }
-                    cd = acc;
-                    ci = j;
+                    d32 = a;
+                } else {
+                    j = -1;
                 }
+            }
+            const double kth = __shfl_sync(FULL, ld, kappa - 1);
+            const bool need = j >= 0 && (!(d32 < 3.0e38f) || (double)d32 * (1.0 - (double)gam) <= kth);
+            if (!__ballot_sync(FULL, need)) continue;
+            if (need) {
+                const float *xj = X + (int64_t)j * d;
+                double acc = 0.0;
+                for (int k = 0; k < d; ++k) {
+                    double t = c_sub((double)myq[k], (double)xj[k]);
+                    acc = c_add(acc, c_mul(t, t));
+                }
+                cd = acc;
+                ci = j;
             }
             warp_offer(ld, li, cd, ci, kappa, dedup, lane);
         }
@@ -368,8 +389,8 @@ done:
 
 namespace {
 askit_status knn_lists_init(int64_t Q, double **bd, int **bi, cudaStream_t s) {
-    ASK_CUDA(cudaMalloc(bd, sizeof(double) * Q * 32));
-    ASK_CUDA(cudaMalloc(bi, sizeof(int) * Q * 32));
+    ASK_CUDA(cudaMallocAsync(bd, sizeof(double) * Q * 32, s));
+    ASK_CUDA(cudaMallocAsync(bi, sizeof(int) * Q * 32, s));
     fill_kernel<double><<<nblk(Q * 32, 256), 256, 0, s>>>(*bd, Q * 32, DBL_MAX);
     fill_kernel<int><<<nblk(Q * 32, 256), 256, 0, s>>>(*bi, Q * 32, INT_MAX);
     ASK_LAUNCH();
@@ -397,10 +418,10 @@ askit_status knn_exact_gpu(const float *X, int64_t N, int d, int kappa, const fl
             h[2 * nqb + b] = (int32_t)(b * QC);
             h[3 * nqb + b] = (int32_t)std::min<int64_t>(Q, (b + 1) * QC);
         }
-        cudaError_t e = cudaMalloc(&segs, sizeof(int32_t) * 4 * nqb);
+        cudaError_t e = cudaMallocAsync(&segs, sizeof(int32_t) * 4 * nqb, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(segs, h.data(), sizeof(int32_t) * 4 * nqb, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess && !Y) {
-            e = cudaMalloc(&qids, sizeof(int32_t) * Q);
+            e = cudaMallocAsync(&qids, sizeof(int32_t) * Q, s);
             if (e == cudaSuccess) iota_kernel<<<nblk(Q, 256), 256, 0, s>>>(qids, Q);
         }
         if (e == cudaSuccess) {
@@ -415,7 +436,8 @@ askit_status knn_exact_gpu(const float *X, int64_t N, int d, int kappa, const fl
             rc = ASKIT_ERR_CUDA;
         }
     }
-    cudaFree(bd); cudaFree(bi); cudaFree(qids); cudaFree(segs);
+    for (void *q : {(void *)bd, (void *)bi, (void *)qids, (void *)segs})
+        if (q) cudaFreeAsync(q, s);
     return rc;
 }
 
@@ -459,7 +481,7 @@ askit_status knn_rp_gpu(const float *X, int64_t N, int d, int kappa, int iters, 
         askit_set_error("RP kNN: %s", cudaGetErrorString(e));
         rc = ASKIT_ERR_CUDA;
     }
-    cudaFree(bd); cudaFree(bi); cudaFree(order); cudaFree(segs);
+    cudaFreeAsync(bd, s); cudaFreeAsync(bi, s); cudaFree(order); cudaFree(segs);
     return rc;
 }
 

@@ -63,36 +63,47 @@ __global__ void upward_kernel(int64_t a0, bool leaf_level, int r, const int32_t 
     }
 }
 
-// Packed per-source-row column data of the tensor-core epilogue.
-__global__ void pack_cols_kernel(const float *sc, const float *nrmc, const float *W, int r, int64_t rows,
-                                 float4 *C) {
-    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= rows) return;
-    const float s = sc[q];
-    C[q] = make_float4(s, -s * nrmc[q], W[q * r], 0.f);
-}
-
 }  // namespace
 
-askit_status upward_weights(askit_tree t, const float *W, int r, int64_t ldw, cudaStream_t s) {
+// Buffers of a weight context for r vectors (grow-only; the padding rows of
+// Wt and Ws stay zero).
+askit_status weights_reserve(askit_tree t, WeightCtx &c, int r, cudaStream_t s) {
+    if (r <= c.r_cap) {
+        c.r = r;
+        return ASKIT_OK;
+    }
+    c.arena.free_all();
+    c.Wt = c.Ws = c.partial = nullptr;
+    const int64_t srows = std::max<int64_t>(t->spool_rows, 1) + 256;
+    ASK_TRY(c.arena.alloc(&c.Wt, (size_t)t->N_pad * r));
+    ASK_TRY(c.arena.alloc(&c.Ws, (size_t)srows * r));
+    ASK_TRY(c.arena.alloc(&c.partial, (size_t)std::max<int64_t>(1, t->wl.n_entries) * r));
+    ASK_CUDA(cudaMemsetAsync(c.Wt, 0, sizeof(float) * t->N_pad * r, s));
+    ASK_CUDA(cudaMemsetAsync(c.Ws, 0, sizeof(float) * srows * r, s));
+    c.r_cap = r;
+    c.r = r;
+    c.ready = true;
+    return ASKIT_OK;
+}
+
+askit_status upward_weights(askit_tree t, WeightCtx &c, const float *W, int r, int64_t ldw, cudaStream_t s) {
+    ASK_TRY(weights_reserve(t, c, r, s));
     int64_t N = t->N;
-    permute_in_kernel<<<(unsigned)((N * r + 255) / 256), 256, 0, s>>>(W, ldw, r, t->perm, N, t->Wt);
+    // rows of Wt/Ws are r apart: with a smaller r than the capacity, rows past
+    // the first r columns are not used, so a fresh layout per call is fine
+    permute_in_kernel<<<(unsigned)((N * r + 255) / 256), 256, 0, s>>>(W, ldw, r, t->perm, N, c.Wt);
     ASK_LAUNCH();
     for (int depth = t->L; depth >= 1; --depth) {
         int64_t a0 = (int64_t)1 << depth;
         unsigned nb = (unsigned)a0;
         if (r == 1)
             upward_kernel<1><<<nb, 256, 0, s>>>(a0, depth == t->L, r, t->nstart, t->d_s, t->d_ncol, t->d_pivoff,
-                                               t->piv, t->d_poff, t->P32, t->d_spool, t->Wt, t->Ws);
+                                               t->piv, t->d_poff, t->P32, t->d_spool, c.Wt, c.Ws);
         else
             upward_kernel<8><<<nb, 256, 0, s>>>(a0, depth == t->L, r, t->nstart, t->d_s, t->d_ncol, t->d_pivoff,
-                                               t->piv, t->d_poff, t->P32, t->d_spool, t->Wt, t->Ws);
+                                               t->piv, t->d_poff, t->P32, t->d_spool, c.Wt, c.Ws);
         ASK_LAUNCH();
     }
-    if (t->Ct) {
-        pack_cols_kernel<<<(unsigned)((t->N_pad + 255) / 256), 256, 0, s>>>(t->sc_t, t->nrmc_t, t->Wt, r, t->N_pad, t->Ct);
-        pack_cols_kernel<<<(unsigned)((t->srows + 255) / 256), 256, 0, s>>>(t->sc_s, t->nrmc_s, t->Ws, r, t->srows, t->Cs);
-        ASK_LAUNCH();
-    }
+    c.ready = true;
     return ASKIT_OK;
 }

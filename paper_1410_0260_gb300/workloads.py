@@ -42,6 +42,34 @@ def manifold(N: int, d: int, k: int, noise: float, seed: int, chunk: int = 1 << 
     return X
 
 
+def manifold_queries(T: int, d: int, k: int, noise: float, seed: int, qseed: int) -> np.ndarray:
+    """Fresh points from the same embedding as ``manifold(..., seed)``: the
+    same matrix A (the first draw of that generator), new z and noise."""
+    A = np.random.default_rng(seed).standard_normal((d, k))
+    A, _ = np.linalg.qr(A)
+    rng = np.random.default_rng(qseed)
+    z = rng.standard_normal((T, k))
+    return (z @ A.T + noise * rng.standard_normal((T, d))).astype(np.float32)
+
+
+def request_stream(n: int, rate: float, seed: int, r_max: int = 64, t_min: int = 100,
+                   t_max: int = 100_000) -> list[tuple[float, str, int]]:
+    """Serving requests: Poisson arrivals at ``rate`` per second; each is,
+    with probability 1/2, a weight request of r ~ U{1..r_max} vectors or an
+    out-of-sample batch of T targets, log-uniform in [t_min, t_max].
+    Returns (arrival time in s, kind, size)."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    out = []
+    for i in range(n):
+        if rng.random() < 0.5:
+            out.append((float(t[i]), "weights", int(rng.integers(1, r_max + 1))))
+        else:
+            T = int(round(10 ** rng.uniform(np.log10(t_min), np.log10(t_max))))
+            out.append((float(t[i]), "targets", T))
+    return out
+
+
 def weights(N: int, r: int, law: str, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed + 1000)
     if law == "normal":

@@ -225,15 +225,34 @@ def test_multi_rhs_16_on_the_8m_recipe_shape():
 
 def test_d1000_variable_bandwidth_on_the_1000d_recipe_shape():
     """d = 1000, h_j = distance to the 16th neighbor, adaptive s in [32, 128]: the
-    1M x 1000 recipe at N = 2048 (plain FP32 path; the tensor-core path covers d <= 64)."""
+    1M x 1000 recipe at N = 2048, plain FP32 and the K-chunked tensor-core path."""
     w = wl.MANIFOLD_1M_1000_VARH.scaled(2048)
     X, W = w.make_points(), w.make_weights()
     kw = dict(leaf_size=256, kappa=16, knn_mode=0, s_max=128, s_min=32, id_tol=1e-3, bw_mode=2, bw_k=16, seed=4)
     otree, gtree = build_pair(X, kw)
     check_structures(otree, gtree)
-    Ug, Uo = eval_both(otree, gtree, W, "simt_fp32")
-    assert rel(Ug, Uo) <= TOL["simt_fp32"]
+    for prec in ("simt_fp32", "fp16x3", "bf16x3"):
+        Ug, Uo = eval_both(otree, gtree, W, prec)
+        assert rel(Ug, Uo) <= TOL[prec], prec
     askit = _askit()
-    gtree.set_precision("fp16x3")
+    gtree.set_precision("tf32x3")          # the wide kernel runs the 16-bit splits only
     with pytest.raises(askit.AskitError):
         gtree.evaluate()
+
+
+def test_wide_rows_with_a_ragged_last_chunk():
+    """d = 72 (rows padded to 96, K chunks of 64: the second chunk half outside
+    the rows), ragged leaves, r = 3, out-of-sample targets."""
+    X = wl.mixture(3001, 72, 5, 3.0, seed=21)
+    W = np.random.default_rng(6).standard_normal((3001, 3)).astype(np.float32)
+    kw = dict(leaf_size=100, kappa=12, knn_mode=0, s_max=48, id_tol=1e-5, h=4.0, seed=8)
+    otree, gtree = build_pair(X, kw)
+    for prec in ("fp16x3", "bf16x3"):
+        Ug, Uo = eval_both(otree, gtree, W, prec)
+        assert rel(Ug, Uo) <= TOL[prec], prec
+    Y = (X[:500] + 0.5 * np.random.default_rng(7).standard_normal((500, 72))).astype(np.float32)
+    otree.set_weights(W.astype(np.float64))
+    Uo = otree.evaluate_oos(Y)
+    gtree.set_precision("fp16x3")
+    Ug = gtree.evaluate_targets(torch.from_numpy(Y).cuda()).cpu().numpy()
+    assert rel(Ug, Uo) <= TOL["fp16x3"]
