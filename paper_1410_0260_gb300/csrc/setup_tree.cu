@@ -250,6 +250,138 @@ __global__ void knn_block_kernel(const float *X, int d, const int32_t *cand, con
     }
 }
 
+// Tiled exhaustive search: block (qb, sp) takes queries [64 qb, 64 qb + 64)
+// against the candidate split [c0, c1).  FP32 squared distances of 64 x 128
+// tiles (difference form, k ascending, one FMA per coordinate: the same
+// rounding bound as the per-warp search) go to shared memory; warp w then
+// filters the rows of its 8 queries against their current kappa-th FP64
+// distance and recomputes the survivors in canonical FP64.  Each split
+// writes its own best-32 lists; knn_merge_kernel merges the splits.
+constexpr int KT_Q = 64, KT_C = 128, KT_K = 32;
+
+__global__ void __launch_bounds__(256) knn_tiled_kernel(const float *X, int64_t N, int d, const float *Y,
+                                                         int64_t Q, int64_t split_len, int kappa, double *bd,
+                                                         int *bi) {
+    // the distance tile reuses the chunk buffers (the selection ends before
+    // the next tile's first chunk is loaded)
+    __shared__ float sbuf[KT_Q * (KT_C + 1)];
+    float (*qs)[KT_Q + 1] = reinterpret_cast<float (*)[KT_Q + 1]>(sbuf);
+    float (*cs)[KT_C + 1] = reinterpret_cast<float (*)[KT_C + 1]>(sbuf + KT_K * (KT_Q + 1));
+    float (*dt)[KT_C + 1] = reinterpret_cast<float (*)[KT_C + 1]>(sbuf);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int64_t q0 = (int64_t)blockIdx.x * KT_Q;
+    const int64_t c0 = (int64_t)blockIdx.y * split_len;
+    const int64_t c1 = c0 + split_len < N ? c0 + split_len : N;
+    const float gam = (float)(d + 2) * 5.9604645e-8f * 1.25f + 1e-6f;
+    double ld[8];
+    int li[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) { ld[u] = DBL_MAX; li[u] = INT_MAX; }
+    for (int64_t cb = c0; cb < c1; cb += KT_C) {
+        float acc[4][8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        for (int k0 = 0; k0 < d; k0 += KT_K) {
+            __syncthreads();
+            // query chunk [64 x 32] and candidate chunk [128 x 32], transposed, zeros outside
+            for (int e = tid; e < KT_Q * KT_K; e += 256) {
+                const int qq = e / KT_K, kk = e % KT_K;
+                const int64_t q = q0 + qq;
+                float v = 0.f;
+                if (q < Q && k0 + kk < d) v = Y ? Y[q * d + k0 + kk] : X[q * d + k0 + kk];
+                qs[kk][qq] = v;
+            }
+            for (int e = tid; e < KT_C * KT_K; e += 256) {
+                const int cc = e / KT_K, kk = e % KT_K;
+                const int64_t j = cb + cc;
+                cs[kk][cc] = (j < c1 && k0 + kk < d) ? X[j * d + k0 + kk] : 0.f;
+            }
+            __syncthreads();
+            const int kn = d - k0 < KT_K ? d - k0 : KT_K;
+            for (int kk = 0; kk < kn; ++kk) {
+                float qv[4], cv[8];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) qv[i] = qs[kk][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) cv[j] = cs[kk][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float t = qv[i] - cv[j];
+                        acc[i][j] = fmaf(t, t, acc[i][j]);
+                    }
+            }
+        }
+        __syncthreads();     // every thread is done with the chunk buffers
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) dt[ty + 16 * i][tx + 16 * j] = acc[i][j];
+        __syncthreads();
+        // selection: warp w owns queries 8w .. 8w+7 of the tile
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int qq = 8 * warp + u;
+            const int64_t q = q0 + qq;
+            if (q >= Q) continue;                         // warp-uniform
+            const float *xq = Y ? Y + q * d : X + q * d;
+            for (int rr = 0; rr < KT_C / 32; ++rr) {
+                const int64_t j = cb + rr * 32 + lane;
+                const bool valid = j < c1 && (Y || j != q);
+                const float d32 = dt[qq][rr * 32 + lane];
+                const double kth = __shfl_sync(FULL, ld[u], kappa - 1);
+                const bool need = valid && (double)d32 * (1.0 - (double)gam) <= kth;
+                if (!__ballot_sync(FULL, need)) continue;
+                double cd = DBL_MAX;
+                int ci = INT_MAX;
+                if (need) {
+                    const float *xj = X + j * d;
+                    double a = 0.0;
+                    for (int k = 0; k < d; ++k) {
+                        const double t = c_sub((double)xq[k], (double)xj[k]);
+                        a = c_add(a, c_mul(t, t));
+                    }
+                    cd = a;
+                    ci = (int)j;
+                }
+                warp_offer(ld[u], li[u], cd, ci, kappa, false, lane);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int64_t q = q0 + 8 * warp + u;
+        if (q < Q) {
+            const int64_t o = ((int64_t)blockIdx.y * Q + q) * 32 + lane;
+            bd[o] = ld[u];
+            bi[o] = li[u];
+        }
+    }
+}
+
+// Merge the splits' best-32 lists of each query (one warp per query) and
+// write the kappa nearest.
+__global__ void knn_merge_kernel(const double *bd, const int *bi, int64_t Q, int nsplit, int kappa,
+                                 int32_t *ids, double *dist) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (q >= Q) return;                                   // warp-uniform
+    double ld = DBL_MAX;
+    int li = INT_MAX;
+    for (int sp = 0; sp < nsplit; ++sp) {
+        const int64_t o = ((int64_t)sp * Q + q) * 32 + lane;
+        warp_offer(ld, li, bd[o], bi[o], kappa, false, lane);
+    }
+    if (lane < kappa) {
+        ids[q * kappa + lane] = li;
+        dist[q * kappa + lane] = ld;
+    }
+}
+
 __global__ void knn_extract_kernel(const double *bd, const int *bi, int64_t Q, int kappa,
                                    int32_t *ids, double *dist) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -399,45 +531,34 @@ askit_status knn_lists_init(int64_t Q, double **bd, int **bi, cudaStream_t s) {
 }  // namespace
 
 // Exact kNN: every point (Y == nullptr, self excluded) or every row of Y
-// against all N points; the candidates are split in chunks so that many
-// blocks share the work of one query set.
+// against all N points.  Query tiles of 64 x candidate splits, chosen so that
+// about four blocks per SM have work; the splits' lists are merged.
 askit_status knn_exact_gpu(const float *X, int64_t N, int d, int kappa, const float *Y, int64_t Q,
                            int32_t *ids, double *dist, cudaStream_t s) {
+    const int64_t nqb = (Q + KT_Q - 1) / KT_Q;
+    int64_t nsplit = (4 * 152 + nqb - 1) / nqb;
+    nsplit = std::max<int64_t>(1, std::min<int64_t>(nsplit, N / (4 * KT_C)));
+    nsplit = std::min<int64_t>(nsplit, 65535);
+    int64_t split_len = (N + nsplit - 1) / nsplit;
+    split_len = (split_len + KT_C - 1) / KT_C * KT_C;
+    nsplit = (N + split_len - 1) / split_len;
     double *bd = nullptr;
     int *bi = nullptr;
-    int32_t *qids = nullptr, *segs = nullptr;
-    askit_status rc = knn_lists_init(Q, &bd, &bi, s);
-    if (rc == ASKIT_OK) {
-        // one block per (query chunk of 64): candidates = all N
-        const int QC = 64;
-        int64_t nqb = (Q + QC - 1) / QC;
-        std::vector<int32_t> h(4 * nqb);
-        for (int64_t b = 0; b < nqb; ++b) {
-            h[b] = 0;
-            h[nqb + b] = (int32_t)N;
-            h[2 * nqb + b] = (int32_t)(b * QC);
-            h[3 * nqb + b] = (int32_t)std::min<int64_t>(Q, (b + 1) * QC);
-        }
-        cudaError_t e = cudaMallocAsync(&segs, sizeof(int32_t) * 4 * nqb, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(segs, h.data(), sizeof(int32_t) * 4 * nqb, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess && !Y) {
-            e = cudaMallocAsync(&qids, sizeof(int32_t) * Q, s);
-            if (e == cudaSuccess) iota_kernel<<<nblk(Q, 256), 256, 0, s>>>(qids, Q);
-        }
-        if (e == cudaSuccess) {
-            knn_block_kernel<<<(unsigned)nqb, 256, 8 * d * sizeof(float), s>>>(
-                X, d, nullptr, segs, segs + nqb, qids, Y, Q, segs + 2 * nqb, segs + 3 * nqb, bd, bi, kappa, false);
-            knn_extract_kernel<<<nblk(Q * kappa, 256), 256, 0, s>>>(bd, bi, Q, kappa, ids, dist);
-            e = cudaGetLastError();
-        }
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) {
-            askit_set_error("exact kNN: %s", cudaGetErrorString(e));
-            rc = ASKIT_ERR_CUDA;
-        }
+    cudaError_t e = cudaMallocAsync(&bd, sizeof(double) * nsplit * Q * 32, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&bi, sizeof(int) * nsplit * Q * 32, s);
+    if (e == cudaSuccess) {
+        knn_tiled_kernel<<<dim3((unsigned)nqb, (unsigned)nsplit), 256, 0, s>>>(X, N, d, Y, Q, split_len, kappa, bd, bi);
+        knn_merge_kernel<<<nblk(Q * 32, 256), 256, 0, s>>>(bd, bi, Q, (int)nsplit, kappa, ids, dist);
+        e = cudaGetLastError();
     }
-    for (void *q : {(void *)bd, (void *)bi, (void *)qids, (void *)segs})
-        if (q) cudaFreeAsync(q, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    askit_status rc = ASKIT_OK;
+    if (e != cudaSuccess) {
+        askit_set_error("exact kNN: %s", cudaGetErrorString(e));
+        rc = ASKIT_ERR_CUDA;
+    }
+    if (bd) cudaFreeAsync(bd, s);
+    if (bi) cudaFreeAsync(bi, s);
     return rc;
 }
 

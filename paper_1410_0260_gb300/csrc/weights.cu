@@ -18,49 +18,92 @@ __global__ void permute_in_kernel(const float *W, int64_t ldw, int r, const int3
     Wt[e] = W[(int64_t)perm[q] * ldw + z];
 }
 
-// One block per node of the level; warps take rows q of w~_a; lanes split
-// the unskeletonized columns u and reduce with shuffles.
+// One block per node of the level.  The rows v(R) the node's P multiplies
+// (gathered through its pivot order) are staged in shared memory once, in
+// chunks of UP_KU rows and RC columns; warps then take rows q of w~_a, lanes
+// split the columns u of P and reduce with shuffles.
+constexpr int UP_KU = 1024;
+
 template <int RC>
-__global__ void upward_kernel(int64_t a0, bool leaf_level, int r, const int32_t *nstart,
-                              const int32_t *s, const int32_t *ncol, const int64_t *pivoff,
-                              const int32_t *piv, const int64_t *poff, const float *P32,
-                              const int64_t *spool, const float *Wt, float *Ws) {
-    int64_t a = a0 + blockIdx.x;
-    int sa = s[a], c = ncol[a], nr = c - sa;
+__host__ __device__ constexpr int up_stride() { return RC == 1 ? 1 : RC + 4; }   // padded: conflict-free float4 reads
+
+template <int RC>
+__global__ void upward_kernel(int64_t a0, bool leaf_level, int r, const int32_t *nstart, const int32_t *s,
+                              const int32_t *ncol, const int64_t *pivoff, const int32_t *piv, const int64_t *poff,
+                              const float *P32, const int64_t *spool, const float *Wt, float *Ws) {
+    extern __shared__ float vs[];
+    constexpr int STR = up_stride<RC>();
+    const int64_t a = a0 + blockIdx.x;
+    const int sa = s[a], c = ncol[a], nr = c - sa;
     if (sa == 0) return;
     const int32_t *pv = piv + pivoff[a];
     const float *P = P32 + poff[a];
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int sl = leaf_level ? 0 : s[2 * a];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int sl = leaf_level ? 0 : s[2 * a];
     const float *vl = leaf_level ? Wt + (int64_t)nstart[a] * r : Ws + spool[2 * a] * r;
     const float *vr = leaf_level ? nullptr : Ws + spool[2 * a + 1] * r;
     auto vrow = [&](int col) -> const float * {
         return (leaf_level || col < sl) ? vl + (int64_t)col * r : vr + (int64_t)(col - sl) * r;
     };
     float *out = Ws + spool[a] * r;
-    for (int q = warp; q < sa; q += nw) {
-        for (int z0 = 0; z0 < r; z0 += RC) {
-            float acc[RC];
-#pragma unroll
-            for (int zz = 0; zz < RC; ++zz) acc[zz] = 0.f;
-            for (int u = lane; u < nr; u += 32) {
-                float p = P[(int64_t)q * nr + u];
-                const float *vu = vrow(pv[sa + u]);
-#pragma unroll
-                for (int zz = 0; zz < RC; ++zz)
-                    if (z0 + zz < r) acc[zz] = fmaf(p, vu[z0 + zz], acc[zz]);
+    for (int z0 = 0; z0 < r; z0 += RC) {
+        for (int u0 = 0; u0 < nr || u0 == 0; u0 += UP_KU) {
+            const int ku = nr - u0 < UP_KU ? nr - u0 : UP_KU;
+            __syncthreads();
+            for (int e = threadIdx.x; e < ku * RC; e += blockDim.x) {
+                const int uu = e / RC, z = e % RC;
+                vs[uu * STR + z] = (z0 + z < r) ? vrow(pv[sa + u0 + uu])[z0 + z] : 0.f;
             }
+            __syncthreads();
+            for (int q = warp; q < sa; q += nw) {
+                float acc[RC];
 #pragma unroll
-            for (int zz = 0; zz < RC; ++zz)
-                for (int o = 16; o > 0; o >>= 1) acc[zz] += __shfl_xor_sync(0xffffffffu, acc[zz], o);
-            if (lane == 0) {
-                const float *vs = vrow(pv[q]);
+                for (int z = 0; z < RC; ++z) acc[z] = 0.f;
+                for (int uu = lane; uu < ku; uu += 32) {
+                    const float p = P[(int64_t)q * nr + u0 + uu];
+                    if constexpr (RC == 1) {
+                        acc[0] = fmaf(p, vs[uu], acc[0]);
+                    } else {
 #pragma unroll
-                for (int zz = 0; zz < RC; ++zz)
-                    if (z0 + zz < r) out[(int64_t)q * r + z0 + zz] = vs[z0 + zz] + acc[zz];
+                        for (int z4 = 0; z4 < RC / 4; ++z4) {
+                            const float4 v = *reinterpret_cast<const float4 *>(vs + uu * STR + 4 * z4);
+                            acc[4 * z4 + 0] = fmaf(p, v.x, acc[4 * z4 + 0]);
+                            acc[4 * z4 + 1] = fmaf(p, v.y, acc[4 * z4 + 1]);
+                            acc[4 * z4 + 2] = fmaf(p, v.z, acc[4 * z4 + 2]);
+                            acc[4 * z4 + 3] = fmaf(p, v.w, acc[4 * z4 + 3]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int z = 0; z < RC; ++z)
+                    for (int o = 16; o > 0; o >>= 1) acc[z] += __shfl_xor_sync(0xffffffffu, acc[z], o);
+                if (lane == 0) {
+                    const float *vsk = vrow(pv[q]);
+#pragma unroll
+                    for (int z = 0; z < RC; ++z)
+                        if (z0 + z < r) {
+                            float *o = out + (int64_t)q * r + z0 + z;
+                            *o = (u0 == 0 ? vsk[z0 + z] : *o) + acc[z];
+                        }
+                }
             }
+            if (nr == 0) break;
         }
     }
+}
+
+template <int RC>
+askit_status launch_upward(askit_tree t, WeightCtx &c, int depth, int r, cudaStream_t s) {
+    const size_t smem = sizeof(float) * UP_KU * up_stride<RC>();
+    // set once per kernel instance (thread-safe static initialisation)
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(upward_kernel<RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    ASK_CUDA(attr);
+    const int64_t a0 = (int64_t)1 << depth;
+    upward_kernel<RC><<<(unsigned)a0, 256, smem, s>>>(a0, depth == t->L, r, t->nstart, t->d_s, t->d_ncol, t->d_pivoff,
+                                                      t->piv, t->d_poff, t->P32, t->d_spool, c.Wt, c.Ws);
+    ASK_LAUNCH();
+    return ASKIT_OK;
 }
 
 }  // namespace
@@ -94,15 +137,12 @@ askit_status upward_weights(askit_tree t, WeightCtx &c, const float *W, int r, i
     permute_in_kernel<<<(unsigned)((N * r + 255) / 256), 256, 0, s>>>(W, ldw, r, t->perm, N, c.Wt);
     ASK_LAUNCH();
     for (int depth = t->L; depth >= 1; --depth) {
-        int64_t a0 = (int64_t)1 << depth;
-        unsigned nb = (unsigned)a0;
         if (r == 1)
-            upward_kernel<1><<<nb, 256, 0, s>>>(a0, depth == t->L, r, t->nstart, t->d_s, t->d_ncol, t->d_pivoff,
-                                               t->piv, t->d_poff, t->P32, t->d_spool, c.Wt, c.Ws);
+            ASK_TRY(launch_upward<1>(t, c, depth, r, s));
+        else if (r <= 4)
+            ASK_TRY(launch_upward<4>(t, c, depth, r, s));
         else
-            upward_kernel<8><<<nb, 256, 0, s>>>(a0, depth == t->L, r, t->nstart, t->d_s, t->d_ncol, t->d_pivoff,
-                                               t->piv, t->d_poff, t->P32, t->d_spool, c.Wt, c.Ws);
-        ASK_LAUNCH();
+            ASK_TRY(launch_upward<16>(t, c, depth, r, s));
     }
     c.ready = true;
     return ASKIT_OK;
