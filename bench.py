@@ -386,7 +386,9 @@ def main():
                     "peak_source": "MUFU ex2: 152 SMs x 16/clk x max SM clock"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
-    roof["kernel"] = "eval_simt_kernel" if args.precision == "simt_fp32" else "eval_tc_kernel"
+    roof["kernel"] = ("eval_simt_kernel" if args.precision == "simt_fp32" else
+                      "eval_tcw_kernel" if d > 64 else
+                      "eval_tc16_kernel" if args.precision == "fp16x3" else "eval_tc_kernel")
     roof["ms_per_launch"] = ms_eval
 
     cpu = None
@@ -395,7 +397,8 @@ def main():
         cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
     # permute-in, one upward kernel per level, Evaluate, fixed-order reduction
-    launches_per_step = 1 + info["L"] + 2
+    # (+ the per-sub-block column data of the FP16x3 kernel)
+    launches_per_step = 1 + info["L"] + 2 + (1 if (args.precision == "fp16x3" and d <= 64) else 0)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"simt_fp32": "f32", "tf32x3": "tf32x3", "bf16x3": "bf16x3", "fp16x3": "fp16x3"}[args.precision],

@@ -131,6 +131,8 @@ struct WeightCtx {
     float *Wt = nullptr;       // [N_pad, r] weights in tree order
     float *Ws = nullptr;       // [rows of the skeleton pool, r] skeleton weights
     float *partial = nullptr;  // [in-sample entries, r_cap]
+    float4 *colv = nullptr;    // [n_sub, 128] per-sub-block column data (16-bit tensor-core path)
+    float *colw = nullptr;     // [n_sub, 128, 16] per-sub-block weights (r > 1)
     bool ready = false;
     DevArena arena;
 };
@@ -215,6 +217,10 @@ struct askit_tree_s {
     int *d_ticket = nullptr;       // persistent-kernel work counter
     void *tc = nullptr;            // tensor-core kernel state (tensor maps)
     void *tcw = nullptr;           // the same for the wide (d > TC_K) kernel
+    void *tc16 = nullptr;          // the same for the 16-bit narrow kernel
+    int64_t *sb_row0 = nullptr;    // [n_sub] first row of each sub-block (Xt rows, then Xs rows)
+    int32_t *sb_nr = nullptr;      // [n_sub] rows of each sub-block
+    int64_t n_leaf_sub = 0;        // sub-blocks of leaves (the rest are skeleton sub-blocks)
     int kw = TC_K;                 // row width of the pre-split operands and centers
 };
 
@@ -353,3 +359,6 @@ void eval_tc_free(askit_tree t);
 askit_status eval_tc_wide(askit_tree t, const WeightCtx &c, int precision, const float *Xq, int64_t ldq,
                           int64_t q_rows, const WorkLists &w, float *partial, cudaStream_t s);
 void eval_tc_wide_free(askit_tree t);
+askit_status eval_tc16(askit_tree t, const WeightCtx &c, int precision, const float *Xq, int64_t ldq, int64_t q_rows,
+                       const WorkLists &w, float *partial, cudaStream_t s);
+void eval_tc16_free(askit_tree t);

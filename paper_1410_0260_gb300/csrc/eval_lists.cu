@@ -363,12 +363,13 @@ askit_status build_tc_operands(askit_tree t, cudaStream_t s) {
     const int kw = wide ? (t->d_pad + 63) / 64 * 64 : TC_K;
     if (kw > 8192) return ASKIT_OK;     // no tensor-core operands (plain FP32 path only)
     t->kw = kw;
-    int64_t *d_r0 = nullptr;
-    int32_t *d_nr = nullptr;
-    ASK_CUDA(cudaMalloc(&d_r0, sizeof(int64_t) * std::max<int64_t>(1, t->n_sub)));
-    ASK_CUDA(cudaMalloc(&d_nr, sizeof(int32_t) * std::max<int64_t>(1, t->n_sub)));
-    ASK_CUDA(cudaMemcpyAsync(d_r0, r0.data(), sizeof(int64_t) * t->n_sub, cudaMemcpyHostToDevice, s));
-    ASK_CUDA(cudaMemcpyAsync(d_nr, nr.data(), sizeof(int32_t) * t->n_sub, cudaMemcpyHostToDevice, s));
+    ASK_TRY(t->arena.alloc(&t->sb_row0, std::max<int64_t>(1, t->n_sub)));
+    ASK_TRY(t->arena.alloc(&t->sb_nr, std::max<int64_t>(1, t->n_sub)));
+    ASK_CUDA(cudaMemcpyAsync(t->sb_row0, r0.data(), sizeof(int64_t) * t->n_sub, cudaMemcpyHostToDevice, s));
+    ASK_CUDA(cudaMemcpyAsync(t->sb_nr, nr.data(), sizeof(int32_t) * t->n_sub, cudaMemcpyHostToDevice, s));
+    t->n_leaf_sub = n_leaf_sub;
+    int64_t *d_r0 = t->sb_row0;
+    int32_t *d_nr = t->sb_nr;
     t->srows = std::max<int64_t>(t->spool_rows, 1) + 256;
     const size_t et = (size_t)t->N_pad * kw, es = (size_t)t->srows * kw;
     ASK_TRY(t->arena.alloc(&t->cent, (size_t)std::max<int64_t>(1, t->n_sub) * kw));
@@ -419,8 +420,6 @@ askit_status build_tc_operands(askit_tree t, cudaStream_t s) {
             t->cent + n_leaf_sub * kw, t->Xs_hi, t->Xs_lo, t->Xs_bhi, t->Xs_blo, t->Xs_hhi, t->Xs_hlo, t->nrmc_s);
     ASK_LAUNCH();
     ASK_CUDA(cudaStreamSynchronize(s));
-    cudaFree(d_r0);
-    cudaFree(d_nr);
     return ASKIT_OK;
 }
 

@@ -227,11 +227,15 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                     const float *rawb = reinterpret_cast<const float *>(sm + S::RAWB);
                     const float *cBs = reinterpret_cast<const float *>(sm + S::CENT);
                     const int dp = args.d_pad;
+                    // packed FP32x2 arithmetic: two coordinates per instruction
+                    const float2 m1 = make_float2(-1.f, -1.f), z2 = make_float2(0.f, 0.f);
+                    const float2 sc2 = make_float2(args.f16_scale, args.f16_scale);
+                    float2 nn2 = z2, dd2 = z2, qq2 = z2;
 #pragma unroll 4
                     for (int j = 0; j < TC_K / 4; ++j) {
                         // chunks in an order rotated by the row: conflict-free shared loads
                         const int k4 = (j + t) & (nk4 - 1);
-                        float xa[4] = {0.f, 0.f, 0.f, 0.f};
+                        float2 xa[2] = {z2, z2};
                         int kst = j;   // chunk to store (zeros past d_pad)
                         if (j < nk4) {
                             kst = k4;
@@ -239,15 +243,17 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                             const float4 bb = *reinterpret_cast<const float4 *>(cBs + 4 * k4);
                             const float4 xx = has_tgt ? *reinterpret_cast<const float4 *>(raw + t * dp + 4 * k4) : tt;
                             const float4 yy = has_src ? *reinterpret_cast<const float4 *>(rawb + t * dp + 4 * k4) : tt;
-                            const float ts[4] = {tt.x, tt.y, tt.z, tt.w}, bs[4] = {bb.x, bb.y, bb.z, bb.w};
-                            const float xs[4] = {xx.x, xx.y, xx.z, xx.w}, ys[4] = {yy.x, yy.y, yy.z, yy.w};
+                            const float2 tv[2] = {make_float2(tt.x, tt.y), make_float2(tt.z, tt.w)};
+                            const float2 bv[2] = {make_float2(bb.x, bb.y), make_float2(bb.z, bb.w)};
+                            const float2 xv[2] = {make_float2(xx.x, xx.y), make_float2(xx.z, xx.w)};
+                            const float2 yv[2] = {make_float2(yy.x, yy.y), make_float2(yy.z, yy.w)};
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                xa[e] = xs[e] - ts[e];
-                                nn = fmaf(xa[e], xa[e], nn);
-                                dd = fmaf(xa[e], ts[e] - bs[e], dd);
-                                const float ya = ys[e] - ts[e];
-                                qq = fmaf(ya, ya, qq);
+                            for (int e = 0; e < 2; ++e) {
+                                xa[e] = __ffma2_rn(tv[e], m1, xv[e]);                        // a = x - c_T
+                                nn2 = __ffma2_rn(xa[e], xa[e], nn2);
+                                dd2 = __ffma2_rn(xa[e], __ffma2_rn(bv[e], m1, tv[e]), dd2);   // a . delta
+                                const float2 ya = __ffma2_rn(tv[e], m1, yv[e]);              // y - c_T
+                                qq2 = __ffma2_rn(ya, ya, qq2);
                             }
                         }
                         // 4 elements = 8 bytes of the 128-byte row; packed 2-wide conversions
@@ -255,17 +261,15 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
 #pragma unroll
                         for (int e = 0; e < 2; ++e) {
                             if constexpr (P == ASKIT_PREC_FP16X3) {
-                                const float v0 = xa[2 * e] * args.f16_scale, v1 = xa[2 * e + 1] * args.f16_scale;
-                                const __half2 h = __floats2half2_rn(v0, v1);
-                                const float2 hf = __half22float2(h);
-                                const __half2 l = __floats2half2_rn(v0 - hf.x, v1 - hf.y);
+                                const float2 v = __ffma2_rn(xa[e], sc2, z2);
+                                const __half2 h = __float22half2_rn(v);
+                                const __half2 l = __float22half2_rn(__ffma2_rn(__half22float2(h), m1, v));
                                 hv[e] = *reinterpret_cast<const uint32_t *>(&h);
                                 lv[e] = *reinterpret_cast<const uint32_t *>(&l);
                             } else {
-                                const float v0 = xa[2 * e], v1 = xa[2 * e + 1];
-                                const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-                                const float2 hf = __bfloat1622float2(h);
-                                const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+                                const float2 v = xa[e];
+                                const __nv_bfloat162 h = __float22bfloat162_rn(v);
+                                const __nv_bfloat162 l = __float22bfloat162_rn(__ffma2_rn(__bfloat1622float2(h), m1, v));
                                 hv[e] = *reinterpret_cast<const uint32_t *>(&h);
                                 lv[e] = *reinterpret_cast<const uint32_t *>(&l);
                             }
@@ -274,6 +278,9 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                         *reinterpret_cast<uint2 *>(ahi + off) = make_uint2(hv[0], hv[1]);
                         *reinterpret_cast<uint2 *>(alo + off) = make_uint2(lv[0], lv[1]);
                     }
+                    nn = nn2.x + nn2.y;
+                    dd = dd2.x + dd2.y;
+                    qq = qq2.x + qq2.y;
                     if (!has_tgt) nn = dd = 0.f;
                 } else {
                 // two 4-column chunks per step: 32 contiguous bytes of a row
@@ -400,10 +407,11 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                     const float2 pt2 = make_float2(pt, pt);
                     const float4 *cv4 = colv + a * 128;
                     const float *cwp = colw + a * 128 * RC;
-#pragma unroll 1
-                    for (int c = 0; c < 4 && c * 32 < nrows; ++c) {
+                    // columns of 32 in pairs: both TMEM loads issued before one wait
+                    auto cols = [&](int c, const uint32_t (&gr)[32]) {
                         float g[32];
-                        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * 128 + c * 32), g);
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) g[jj] = __uint_as_float(gr[jj]);
                         if constexpr (RC == 1) {
                             // two columns per step with packed FP32x2 FMAs:
                             // arg = g A + (C p + B) = -sc (p + q - 2 u g); columns past
@@ -429,6 +437,20 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
 #pragma unroll
                                 for (int z = 0; z < RC; ++z) acc[z] = fmaf(k, cwp[j * RC + z], acc[z]);
                             }
+                        }
+                    };
+                    const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * 128);
+#pragma unroll 1
+                    for (int c = 0; c < 4 && c * 32 < nrows; c += 2) {
+                        uint32_t g0[32], g1[32];
+                        const bool two = (c + 1) * 32 < nrows;      // warp-uniform
+                        tmem_ld32_async(tbase + (uint32_t)(c * 32), g0);
+                        if (two) tmem_ld32_async(tbase + (uint32_t)((c + 1) * 32), g1);
+                        tmem_wait_pin(g0);
+                        cols(c, g0);
+                        if (two) {
+                            reg_pin(g1);
+                            cols(c + 1, g1);
                         }
                     }
                     if constexpr (RC == 1) acc[0] = (acc2[0].x + acc2[0].y) + (acc2[1].x + acc2[1].y);
@@ -648,6 +670,11 @@ askit_status launch(askit_tree t, TcState *st, const CUtensorMap &map_q, const T
 askit_status eval_tc(askit_tree t, const WeightCtx &c, int precision, const float *Xq, int64_t ldq,
                      int64_t q_rows, const WorkLists &w, float *partial, cudaStream_t s) {
     if (t->d > TC_K) return eval_tc_wide(t, c, precision, Xq, ldq, q_rows, w, partial, s);
+    // FP16x3 centers both sides on the sub-block mean (eval_tc16.cu); BF16x3
+    // keeps the per-item target centering below: its 8-bit significands leave
+    // a residual of about 2^-17 of |a| |b| per product, so the smaller |a| of
+    // the per-item center is what keeps it within the split-path tolerance
+    if (precision == ASKIT_PREC_FP16X3) return eval_tc16(t, c, precision, Xq, ldq, q_rows, w, partial, s);
     if (c.r > Smem<ASKIT_PREC_TF32X3>::RC_MAX) {
         askit_set_error("tensor-core evaluation covers r <= %d; use ASKIT_PREC_SIMT_FP32", Smem<ASKIT_PREC_TF32X3>::RC_MAX);
         return ASKIT_ERR_UNSUPPORTED;
@@ -693,13 +720,13 @@ askit_status eval_tc(askit_tree t, const WeightCtx &c, int precision, const floa
         if (c.r <= 4) return launch<ASKIT_PREC_BF16X3, 4>(t, st, map_q, a, w.n_ctas, s);
         return launch<ASKIT_PREC_BF16X3, 16>(t, st, map_q, a, w.n_ctas, s);
     }
-    if (c.r == 1) return launch<ASKIT_PREC_FP16X3, 1>(t, st, map_q, a, w.n_ctas, s);
-    if (c.r <= 4) return launch<ASKIT_PREC_FP16X3, 4>(t, st, map_q, a, w.n_ctas, s);
-    return launch<ASKIT_PREC_FP16X3, 16>(t, st, map_q, a, w.n_ctas, s);
+    askit_set_error("unknown tensor-core precision %d", precision);
+    return ASKIT_ERR_INVALID_ARG;
 }
 
 void eval_tc_free(askit_tree t) {
     delete (TcState *)t->tc;
     t->tc = nullptr;
     eval_tc_wide_free(t);
+    eval_tc16_free(t);
 }

@@ -1,0 +1,525 @@
+// Evaluate (Algorithm 4) on the tcgen05 tensor cores with FP16x3 split
+// operands, d <= 64 (the kernel is written for both 16-bit types; BF16x3 is
+// served by eval_tc.cu's per-item centering, see there).
+//
+// Work item = one source sub-block (<= 128 rows of a leaf's points for the
+// direct near field, or of a node's skeleton for the far field) against up
+// to 128 targets that all need it (eval_lists.cu).  Both sides are centered
+// on the sub-block's mean c_B:
+//
+//     a = x - c_B (targets, centered and split on chip)
+//     b = y - c_B (sources, pre-split in HBM)
+//     r^2 = |a|^2 + |b|^2 - 2 a.b,   G = a.b on the tensor cores
+//     partial_t = sum_j exp2(-c log2(e) r^2 / h_j^2) w_j
+//
+// The products are split in three (hi*hi + hi*lo + lo*hi) with FP32
+// accumulation, the small cross terms issued first.  A sub-block's column
+// data (c log2(e) / h_j^2, |b_j|^2, w_j) does not depend on the targets: it
+// is built once per Evaluate (tc16_cols_kernel) and bulk-copied with the
+// sub-block, so the loaders only center and split target rows.
+//
+// One CTA per SM, 448 threads:
+//   warps 0-7  two loader groups taking alternate items: thread t centers and
+//              splits target row t (gathered by warp 13) into the 128-byte
+//              swizzled K-major layout and forms |a|^2;
+//   warps 8-11 epilogue: tcgen05.ld of their 32 TMEM lanes (one row each),
+//              exponent on MUFU.EX2, reduction against the weights;
+//   warp 12    TMEM allocation; lane 0 loads each sub-block (TMA tiles of the
+//              pre-split rows, bulk copies of its center and column data)
+//              and issues the tcgen05.mma instructions;
+//   warp 13    TMA tile::gather4 of each item's target rows, three stages.
+// Four TMEM accumulators (4 x 128 columns) let the MMAs run up to three items
+// ahead of the epilogue.  Every mbarrier wait is bounded: on timeout the
+// kernel records ASK_DEV_TIMEOUT, all roles leave their loops, producers
+// wait for their copies in flight, and TMEM is freed before the kernel
+// returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <mutex>
+
+#include "askit_impl.cuh"
+#include "tc_ptx.cuh"
+
+namespace {
+
+using namespace tcx;
+
+constexpr int T16_THREADS = 448;
+constexpr int T16_ROWS = 128;
+constexpr int T16_REGION = T16_ROWS * 128;     // 128 rows x 128 bytes (64 16-bit elements), swizzled
+constexpr uint32_t T16_TMEM_COLS = 512;        // four 128-column FP32 accumulators
+constexpr int T16_NRAW = 3;                    // gathered target-row stages
+
+template <int RC>
+struct S16 {
+    static constexpr int B_HI = 0, B_LO = T16_REGION;
+    static constexpr int A0 = 2 * T16_REGION;                 // stage s: hi at A0 + 2s REGION, lo + REGION
+    static constexpr int RAW = A0 + 4 * T16_REGION;           // [3] stages of 128 rows x d_pad floats
+    static constexpr int RAWSTAGE = T16_ROWS * TC_K * 4;
+    static constexpr int BLK = RAW + T16_NRAW * RAWSTAGE;     // [2] per-sub-block slots
+    static constexpr int BLK_CENT = 0;                        // float [64] c_B
+    static constexpr int BLK_COLV = 256;                      // float4 [128] pair-interleaved column data
+    static constexpr int BLK_COLW = BLK_COLV + 128 * 16;      // float [128][RC] weights (RC > 1)
+    static constexpr int COLW_BYTES = RC > 1 ? 128 * RC * 4 : 0;
+    static constexpr int BLKSLOT = BLK_COLW + COLW_BYTES;
+    static constexpr int ANORM = BLK + 2 * BLKSLOT;           // float [4][128] |a|^2
+    static constexpr int BAR = ANORM + 4 * 128 * 4;           // 24 mbarriers
+    static constexpr int MISC = BAR + 24 * 8;                 // tmem address, abort flag
+    static constexpr int BYTES = MISC + 16;
+    static constexpr uint32_t BLK_TX = 256 + 128 * 16 + COLW_BYTES;
+};
+
+struct T16Args {
+    const EvalItem *items;
+    const int32_t *block_off;
+    const int32_t *cta_off, *cta_blocks;
+    const int32_t *tgt;       // entry -> target slot (row of Xq)
+    int d_pad;
+    const float *cent;        // [n_sub, TC_K]
+    const float4 *colv;       // [n_sub, 128] pair-interleaved {A_j, A_j+1, B_j, B_j+1}, {C_j, C_j+1, w_j, w_j+1}
+    const float *colw;        // [n_sub, 128, RC] (RC > 1)
+    int r;
+    float f16_scale;
+    float *partial;
+    int *status;
+};
+
+template <int P, int RC>
+__global__ void __launch_bounds__(T16_THREADS, 1)
+eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_constant__ CUtensorMap map_t_lo,
+                 const __grid_constant__ CUtensorMap map_s_hi, const __grid_constant__ CUtensorMap map_s_lo,
+                 const __grid_constant__ CUtensorMap map_q, const T16Args args) {
+    using S = S16<RC>;
+    constexpr uint32_t IDESC = make_idesc(P == ASKIT_PREC_BF16X3 ? 1u : 0u, T16_ROWS, T16_ROWS);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(sm);
+    float *a_norm = reinterpret_cast<float *>(sm + S::ANORM);
+    const uint32_t bar0 = sbase + S::BAR;
+    auto BAR_A_FULL = [&](int s) { return bar0 + 8 * s; };           // loader group stored A stage s (128)
+    auto BAR_A_EMPTY = [&](int s) { return bar0 + 8 * (2 + s); };    // MMAs reading A stage s done (commit)
+    auto BAR_R_FULL = [&](int s) { return bar0 + 8 * (4 + s); };     // target rows of raw stage s landed
+    auto BAR_R_EMPTY = [&](int s) { return bar0 + 8 * (7 + s); };    // loaders done with raw stage s (128)
+    const uint32_t BAR_B_FULL = bar0 + 8 * 10, BAR_B_EMPTY = bar0 + 8 * 11;
+    auto BAR_BLK_FULL = [&](int s) { return bar0 + 8 * (12 + s); };  // center + column data of slot s landed
+    auto BAR_BLK_EMPTY = [&](int s) { return bar0 + 8 * (14 + s); }; // epilogue done with slot s (128)
+    auto BAR_T_FULL = [&](int a) { return bar0 + 8 * (16 + a); };    // accumulator a complete (commit)
+    auto BAR_T_EMPTY = [&](int a) { return bar0 + 8 * (20 + a); };   // epilogue drained accumulator a (128)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + S::MISC);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + S::MISC + 4);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(BAR_A_FULL(s), 128);
+            mbar_init(BAR_A_EMPTY(s), 1);
+            mbar_init(BAR_BLK_FULL(s), 1);
+            mbar_init(BAR_BLK_EMPTY(s), 128);
+        }
+        for (int s = 0; s < T16_NRAW; ++s) {
+            mbar_init(BAR_R_FULL(s), 1);
+            mbar_init(BAR_R_EMPTY(s), 128);
+        }
+        mbar_init(BAR_B_FULL, 1);
+        mbar_init(BAR_B_EMPTY, 1);
+        for (int a = 0; a < 4; ++a) {
+            mbar_init(BAR_T_FULL(a), 1);
+            mbar_init(BAR_T_EMPTY(a), 128);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 12) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(T16_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int c_begin = args.cta_off[blockIdx.x], c_end = args.cta_off[blockIdx.x + 1];
+
+    if (warp < 8) {
+        // ------------------------------------------------------------ loaders
+        const int grp = warp >> 2, t = tid & 127;
+        const int dp = args.d_pad, nk4 = dp / 4;
+        const float2 m1 = make_float2(-1.f, -1.f), z2 = make_float2(0.f, 0.f);
+        const float2 sc2 = make_float2(args.f16_scale, args.f16_scale);
+        int li = 0, lb = 0;
+        for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci, ++lb) {
+            const int b = args.cta_blocks[ci];
+            const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
+            bool need_blk = true;
+            for (int it = i0; it < i1; ++it, ++li) {
+                if ((li & 1) != grp) continue;
+                const int cnt = args.items[it].cnt;
+                const bool has_tgt = t < cnt;
+                const int sa = li & 1, sr = li % T16_NRAW, a4 = li & 3;
+                if (!mbar_wait(BAR_A_EMPTY(sa), ((li >> 1) & 1) ^ 1, abort_flag, args.status)) goto loader_done;
+                if (!mbar_wait(BAR_T_EMPTY(a4), ((li >> 2) & 1) ^ 1, abort_flag, args.status)) goto loader_done;
+                if (!mbar_wait(BAR_R_FULL(sr), (li / T16_NRAW) & 1, abort_flag, args.status)) goto loader_done;
+                if (need_blk) {
+                    if (!mbar_wait(BAR_BLK_FULL(lb & 1), (lb >> 1) & 1, abort_flag, args.status)) goto loader_done;
+                    need_blk = false;
+                }
+                const float *rrow = reinterpret_cast<const float *>(sm + S::RAW + sr * S::RAWSTAGE) + t * dp;
+                const float *cen = reinterpret_cast<const float *>(sm + S::BLK + (lb & 1) * S::BLKSLOT + S::BLK_CENT);
+                uint8_t *ahi = sm + S::A0 + sa * 2 * T16_REGION;
+                uint8_t *alo = ahi + T16_REGION;
+                float2 nn2 = z2;
+#pragma unroll 4
+                for (int j = 0; j < TC_K / 4; ++j) {
+                    // 4-element chunks in an order rotated by the row: conflict-free shared loads
+                    const int k4 = (j + t) & (nk4 - 1);
+                    float2 xa[2] = {z2, z2};
+                    int kst = j;   // chunk to store (zeros past d_pad)
+                    if (j < nk4) {
+                        kst = k4;
+                        if (has_tgt) {
+                            const float4 xx = *reinterpret_cast<const float4 *>(rrow + 4 * k4);
+                            const float4 cc = *reinterpret_cast<const float4 *>(cen + 4 * k4);
+                            xa[0] = __ffma2_rn(make_float2(cc.x, cc.y), m1, make_float2(xx.x, xx.y));
+                            xa[1] = __ffma2_rn(make_float2(cc.z, cc.w), m1, make_float2(xx.z, xx.w));
+                            nn2 = __ffma2_rn(xa[0], xa[0], nn2);
+                            nn2 = __ffma2_rn(xa[1], xa[1], nn2);
+                        }
+                    }
+                    uint32_t hv[2], lv[2];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        if constexpr (P == ASKIT_PREC_FP16X3) {
+                            const float2 v = __ffma2_rn(xa[e], sc2, z2);
+                            const __half2 h = __float22half2_rn(v);
+                            const __half2 l = __float22half2_rn(__ffma2_rn(__half22float2(h), m1, v));
+                            hv[e] = *reinterpret_cast<const uint32_t *>(&h);
+                            lv[e] = *reinterpret_cast<const uint32_t *>(&l);
+                        } else {
+                            const __nv_bfloat162 h = __float22bfloat162_rn(xa[e]);
+                            const __nv_bfloat162 l = __float22bfloat162_rn(__ffma2_rn(__bfloat1622float2(h), m1, xa[e]));
+                            hv[e] = *reinterpret_cast<const uint32_t *>(&h);
+                            lv[e] = *reinterpret_cast<const uint32_t *>(&l);
+                        }
+                    }
+                    const int off = t * 128 + (((kst >> 1) ^ (t & 7)) << 4) + (kst & 1) * 8;
+                    *reinterpret_cast<uint2 *>(ahi + off) = make_uint2(hv[0], hv[1]);
+                    *reinterpret_cast<uint2 *>(alo + off) = make_uint2(lv[0], lv[1]);
+                }
+                a_norm[a4 * 128 + t] = nn2.x + nn2.y;
+                // generic-proxy stores -> visible to the tensor core's async proxy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(BAR_A_FULL(sa));
+                mbar_arrive(BAR_R_EMPTY(sr));
+            }
+        }
+    loader_done:;
+    } else if (warp < 12) {
+        // ----------------------------------------------------------- epilogue
+        const int row = tid - 256;                 // TMEM lane = target row of the item
+        const int q = warp & 3;                    // this warp's TMEM lane quadrant
+        int li = 0, lb = 0;
+        for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci, ++lb) {
+            const int b = args.cta_blocks[ci];
+            const int bs = lb & 1;
+            if (!mbar_wait(BAR_BLK_FULL(bs), (lb >> 1) & 1, abort_flag, args.status)) goto epi_done;
+            const float4 *cv4 = reinterpret_cast<const float4 *>(sm + S::BLK + bs * S::BLKSLOT + S::BLK_COLV);
+            const float *cwp = reinterpret_cast<const float *>(sm + S::BLK + bs * S::BLKSLOT + S::BLK_COLW);
+            for (int it = args.block_off[b]; it < args.block_off[b + 1]; ++it, ++li) {
+                const int a4 = li & 3;
+                const EvalItem item = args.items[it];
+                const int nrows = item.nrows & 0x7fffffff;
+                if (!mbar_wait(BAR_T_FULL(a4), (li >> 2) & 1, abort_flag, args.status)) goto epi_done;
+                tc_fence_after();
+                float acc[RC];
+#pragma unroll
+                for (int z = 0; z < RC; ++z) acc[z] = 0.f;
+                float2 acc2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};   // RC == 1
+                if (q * 32 < item.cnt) {   // warp-uniform: skip quadrants with no target
+                    const float pt = a_norm[a4 * 128 + row];
+                    const float2 pt2 = make_float2(pt, pt);
+                    // arg = g A + (C p + B) = -sc (p + q - 2 g / scale^2); columns past
+                    // nrows carry A = B = C = w = 0
+                    auto cols = [&](int c, const uint32_t (&gr)[32]) {
+                        if constexpr (RC == 1) {
+#pragma unroll
+                            for (int jj = 0; jj < 32; jj += 2) {
+                                const float4 ab = cv4[c * 32 + jj];
+                                const float4 cw = cv4[c * 32 + jj + 1];
+                                const float2 inner = __ffma2_rn(make_float2(cw.x, cw.y), pt2, make_float2(ab.z, ab.w));
+                                const float2 arg = __ffma2_rn(make_float2(__uint_as_float(gr[jj]), __uint_as_float(gr[jj + 1])),
+                                                              make_float2(ab.x, ab.y), inner);
+                                const float2 k = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+                                acc2[(jj >> 1) & 1] = __ffma2_rn(k, make_float2(cw.z, cw.w), acc2[(jj >> 1) & 1]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int jj = 0; jj < 32; ++jj) {
+                                const int j = c * 32 + jj;
+                                const float4 ab = cv4[j & ~1];
+                                const float4 cw = cv4[(j & ~1) + 1];
+                                const bool h = j & 1;
+                                const float A = h ? ab.y : ab.x, B = h ? ab.w : ab.z, Cc = h ? cw.y : cw.x;
+                                const float k = ex2_approx(fmaf(__uint_as_float(gr[jj]), A, fmaf(Cc, pt, B)));
+#pragma unroll
+                                for (int z = 0; z < RC; ++z) acc[z] = fmaf(k, cwp[j * RC + z], acc[z]);
+                            }
+                        }
+                    };
+                    const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a4 * 128);
+#pragma unroll 1
+                    for (int c = 0; c < 4 && c * 32 < nrows; c += 2) {
+                        // two 32-column loads per wait
+                        uint32_t g0[32], g1[32];
+                        const bool two = (c + 1) * 32 < nrows;      // warp-uniform
+                        tmem_ld32_async(tbase + (uint32_t)(c * 32), g0);
+                        if (two) tmem_ld32_async(tbase + (uint32_t)((c + 1) * 32), g1);
+                        tmem_wait_pin(g0);
+                        cols(c, g0);
+                        if (two) {
+                            reg_pin(g1);
+                            cols(c + 1, g1);
+                        }
+                    }
+                    if constexpr (RC == 1) acc[0] = (acc2[0].x + acc2[0].y) + (acc2[1].x + acc2[1].y);
+                }
+                tc_fence_before();
+                mbar_arrive(BAR_T_EMPTY(a4));
+                if (row < item.cnt) {
+                    float *p = args.partial + (int64_t)(item.e0 + row) * args.r;
+#pragma unroll
+                    for (int z = 0; z < RC; ++z)
+                        if (z < args.r) p[z] = acc[z];
+                }
+            }
+            mbar_arrive(BAR_BLK_EMPTY(bs));
+        }
+    epi_done:;
+    } else if (warp == 13) {
+        // ------------------------------------------------- target-row gatherer
+        const uint32_t bytes = (uint32_t)(T16_ROWS * args.d_pad * 4);
+        int li = 0, issued = 0;
+        for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci) {
+            const int b = args.cta_blocks[ci];
+            for (int it = args.block_off[b]; it < args.block_off[b + 1]; ++it, ++li) {
+                const int sr = li % T16_NRAW;
+                if (!mbar_wait(BAR_R_EMPTY(sr), ((li / T16_NRAW) & 1) ^ 1, abort_flag, args.status)) goto gather_done;
+                const EvalItem item = args.items[it];
+                const int first = args.tgt[item.e0];
+                int r[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int rw = 4 * lane + i;   // rows past cnt repeat the first target
+                    r[i] = rw < item.cnt ? args.tgt[item.e0 + rw] : first;
+                }
+                ++issued;
+                if (lane == 0) mbar_expect_tx(BAR_R_FULL(sr), bytes);
+                __syncwarp();
+                tma_gather4(sbase + S::RAW + sr * S::RAWSTAGE + 4 * lane * args.d_pad * 4, &map_q, 0, r[0], r[1], r[2],
+                            r[3], BAR_R_FULL(sr));
+            }
+        }
+    gather_done:
+        // rows of the last stages may still be landing after an abort
+        for (int gg = issued > T16_NRAW ? issued - T16_NRAW : 0; gg < issued; ++gg)
+            mbar_drain(BAR_R_FULL(gg % T16_NRAW), (gg / T16_NRAW) & 1);
+    } else if (warp == 12 && lane == 0) {
+        // ------------------------------------- sub-block loads + MMA issuer
+        int li = 0, lb = 0, b_issued = 0;
+        for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci, ++lb) {
+            const int b = args.cta_blocks[ci];
+            const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
+            const EvalItem first = args.items[i0];
+            const bool far = first.nrows < 0;
+            const int bs = lb & 1;
+            if (!mbar_wait(BAR_B_EMPTY, (lb & 1) ^ 1, abort_flag, args.status)) goto mma_done;
+            if (!mbar_wait(BAR_BLK_EMPTY(bs), ((lb >> 1) & 1) ^ 1, abort_flag, args.status)) goto mma_done;
+            b_issued = lb + 1;
+            mbar_expect_tx(BAR_B_FULL, 2 * T16_REGION);
+            tma_load_2d(sbase + S::B_HI, far ? &map_s_hi : &map_t_hi, 0, first.row0, BAR_B_FULL);
+            tma_load_2d(sbase + S::B_LO, far ? &map_s_lo : &map_t_lo, 0, first.row0, BAR_B_FULL);
+            const uint32_t slot = sbase + S::BLK + bs * S::BLKSLOT;
+            mbar_expect_tx(BAR_BLK_FULL(bs), S::BLK_TX);
+            bulk_copy(slot + S::BLK_CENT, args.cent + (int64_t)first.cidx * TC_K, TC_K * 4, BAR_BLK_FULL(bs));
+            bulk_copy(slot + S::BLK_COLV, args.colv + (int64_t)first.cidx * 128, 128 * 16, BAR_BLK_FULL(bs));
+            if constexpr (RC > 1)
+                bulk_copy(slot + S::BLK_COLW, args.colw + (int64_t)first.cidx * 128 * RC, S::COLW_BYTES, BAR_BLK_FULL(bs));
+            for (int it = i0; it < i1; ++it, ++li) {
+                const int sa = li & 1, a4 = li & 3;
+                if (!mbar_wait(BAR_A_FULL(sa), (li >> 1) & 1, abort_flag, args.status)) goto mma_done;
+                if (it == i0 && !mbar_wait(BAR_B_FULL, lb & 1, abort_flag, args.status)) goto mma_done;
+                if (!mbar_wait(BAR_T_EMPTY(a4), ((li >> 2) & 1) ^ 1, abort_flag, args.status)) goto mma_done;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(a4 * 128);
+                const uint32_t a_hi = sbase + S::A0 + sa * 2 * T16_REGION, a_lo = a_hi + T16_REGION;
+                const uint32_t b_hi = sbase + S::B_HI, b_lo = sbase + S::B_LO;
+                // the tensor core rounds each accumulation step to the running sum's
+                // precision: the small cross terms first, the hi*hi products last
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {   // K = 16 per MMA: 32 bytes into the 128-byte rows
+                    const uint32_t off = (uint32_t)(k * 32);
+                    tc_mma<P>(d_tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), IDESC, k > 0);
+                    tc_mma<P>(d_tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), IDESC, 1);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t off = (uint32_t)(k * 32);
+                    tc_mma<P>(d_tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), IDESC, 1);
+                }
+                tc_commit(BAR_A_EMPTY(sa));
+                tc_commit(BAR_T_FULL(a4));
+                if (it == i1 - 1) tc_commit(BAR_B_EMPTY);
+            }
+        }
+    mma_done:
+        // the last sub-block's copies may still be landing after an abort
+        if (b_issued > 0) {
+            mbar_drain(BAR_B_FULL, (b_issued - 1) & 1);
+            mbar_drain(BAR_BLK_FULL((b_issued - 1) & 1), ((b_issued - 1) >> 1) & 1);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 12) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(T16_TMEM_COLS) : "memory");
+    }
+}
+
+// Column data of every sub-block for one Evaluate: thread t of block b takes
+// source row t of sub-block b.  colv pairs rows (2p, 2p+1):
+// {A_2p, A_2p+1, B_2p, B_2p+1}, {C_2p, C_2p+1, w_2p, w_2p+1} with
+// A = 2 sc / scale^2, B = -sc |b|^2, C = -sc (zeros past the sub-block's rows).
+template <int RC>
+__global__ void tc16_cols_kernel(const int64_t *sb_row0, const int32_t *sb_nr, int64_t n_leaf_sub, const float *sc_t,
+                                 const float *sc_s, const float *nrm_t, const float *nrm_s, const float *Wt,
+                                 const float *Ws, int r, float g_unscale, float4 *colv, float *colw) {
+    const int64_t b = blockIdx.x;
+    const int t = threadIdx.x;
+    const bool far = b >= n_leaf_sub;
+    const int64_t row = sb_row0[b] + t;
+    const bool valid = t < sb_nr[b];
+    const float sc = valid ? (far ? sc_s : sc_t)[row] : 0.f;
+    const float nrm = valid ? (far ? nrm_s : nrm_t)[row] : 0.f;
+    const float *w = (far ? Ws : Wt) + row * r;
+    float *cp = reinterpret_cast<float *>(colv + b * 128 + 2 * (t >> 1));
+    const int o = t & 1;
+    cp[0 + o] = 2.f * g_unscale * sc;
+    cp[2 + o] = -sc * nrm;
+    cp[4 + o] = -sc;
+    cp[6 + o] = valid ? w[0] : 0.f;
+    if (RC > 1) {
+#pragma unroll
+        for (int z = 0; z < RC; ++z) colw[(b * 128 + t) * RC + z] = (valid && z < r) ? w[z] : 0.f;
+    }
+}
+
+// Tensor maps of the pre-split source arrays ([rows, 64] 16-bit; boxes of
+// 64 x 128, 128-byte swizzle) for BF16 (index 0) and FP16 (index 1).
+struct T16State {
+    CUtensorMap map[2][4];   // [t_hi, t_lo, s_hi, s_lo]
+    bool ready[2] = {false, false};
+    EncodeTiledFn encode = nullptr;
+};
+
+std::mutex g_t16_mu;
+
+askit_status t16_state(askit_tree t, int pi, T16State **out) {
+    std::lock_guard<std::mutex> lock(g_t16_mu);
+    if (!t->tc16) t->tc16 = new T16State();
+    T16State *st = (T16State *)t->tc16;
+    if (!st->encode) ASK_TRY(encode_fn(&st->encode));
+    if (!st->ready[pi]) {
+        const CUtensorMapDataType ty = pi == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+        const void *arr[4] = {pi == 0 ? (void *)t->Xt_bhi : (void *)t->Xt_hhi,
+                              pi == 0 ? (void *)t->Xt_blo : (void *)t->Xt_hlo,
+                              pi == 0 ? (void *)t->Xs_bhi : (void *)t->Xs_hhi,
+                              pi == 0 ? (void *)t->Xs_blo : (void *)t->Xs_hlo};
+        for (int i = 0; i < 4; ++i)
+            ASK_TRY(encode_2d(st->encode, &st->map[pi][i], ty, 2, arr[i], i < 2 ? t->N_pad : t->srows, TC_K, 64,
+                              T16_ROWS, CU_TENSOR_MAP_SWIZZLE_128B));
+        st->ready[pi] = true;
+    }
+    *out = st;
+    return ASKIT_OK;
+}
+
+template <int P, int RC>
+askit_status launch16(T16State *st, int pi, const CUtensorMap &map_q, const T16Args &a, int grid, cudaStream_t s) {
+    using S = S16<RC>;
+    const size_t smem = S::BYTES + 1024;
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(eval_tc16_kernel<P, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    ASK_CUDA(attr);
+    eval_tc16_kernel<P, RC><<<(unsigned)grid, T16_THREADS, smem, s>>>(st->map[pi][0], st->map[pi][1],
+                                                                     st->map[pi][2], st->map[pi][3], map_q, a);
+    ASK_LAUNCH();
+    return ASKIT_OK;
+}
+
+template <int P, int RC>
+askit_status run16(askit_tree t, const WeightCtx &c, T16State *st, int pi, const CUtensorMap &map_q, T16Args a,
+                   const WorkLists &w, cudaStream_t s) {
+    const float g_unscale = 1.f / (a.f16_scale * a.f16_scale);
+    tc16_cols_kernel<RC><<<(unsigned)t->n_sub, 128, 0, s>>>(t->sb_row0, t->sb_nr, t->n_leaf_sub, t->sc_t, t->sc_s,
+                                                            t->nrmc_t, t->nrmc_s, c.Wt, c.Ws, c.r, g_unscale, c.colv,
+                                                            c.colw);
+    ASK_LAUNCH();
+    a.colv = c.colv;
+    a.colw = c.colw;
+    return launch16<P, RC>(st, pi, map_q, a, w.n_ctas, s);
+}
+
+template <int P>
+askit_status dispatch16(askit_tree t, const WeightCtx &c, T16State *st, int pi, const CUtensorMap &map_q,
+                        const T16Args &a, const WorkLists &w, cudaStream_t s) {
+    if (c.r == 1) return run16<P, 1>(t, c, st, pi, map_q, a, w, s);
+    if (c.r <= 4) return run16<P, 4>(t, c, st, pi, map_q, a, w, s);
+    return run16<P, 16>(t, c, st, pi, map_q, a, w, s);
+}
+
+}  // namespace
+
+askit_status eval_tc16(askit_tree t, const WeightCtx &c, int precision, const float *Xq, int64_t ldq, int64_t q_rows,
+                       const WorkLists &w, float *partial, cudaStream_t s) {
+    if (c.r > 16) {
+        askit_set_error("tensor-core evaluation covers r <= 16; use ASKIT_PREC_SIMT_FP32");
+        return ASKIT_ERR_UNSUPPORTED;
+    }
+    if (w.n_blocks == 0) return ASKIT_OK;
+    if (ldq != t->d_pad || !c.colv || (c.r > 1 && !c.colw)) {
+        askit_set_error("target rows must have d_pad columns and the column buffers must exist");
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    const int pi = precision == ASKIT_PREC_BF16X3 ? 0 : 1;
+    T16State *st = nullptr;
+    ASK_TRY(t16_state(t, pi, &st));
+    CUtensorMap map_q;   // one box row per gathered target row
+    ASK_TRY(encode_2d(st->encode, &map_q, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, Xq, q_rows, t->d_pad, t->d_pad, 1,
+                      CU_TENSOR_MAP_SWIZZLE_NONE));
+    T16Args a;
+    a.items = w.items;
+    a.block_off = w.block_off;
+    a.cta_off = w.cta_off;
+    a.cta_blocks = w.cta_blocks;
+    a.tgt = w.tgt;
+    a.d_pad = t->d_pad;
+    a.cent = t->cent;
+    a.colv = nullptr;
+    a.colw = nullptr;
+    a.r = c.r;
+    a.f16_scale = precision == ASKIT_PREC_FP16X3 ? t->f16_scale : 1.f;
+    a.partial = partial;
+    a.status = t->d_status;
+    if (precision != ASKIT_PREC_FP16X3) {
+        askit_set_error("eval_tc16 runs FP16x3");
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    return dispatch16<ASKIT_PREC_FP16X3>(t, c, st, pi, map_q, a, w, s);
+}
+
+void eval_tc16_free(askit_tree t) {
+    delete (T16State *)t->tc16;
+    t->tc16 = nullptr;
+}
