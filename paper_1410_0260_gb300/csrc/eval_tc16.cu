@@ -153,9 +153,12 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
             const int b = args.cta_blocks[ci];
             const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
             bool need_blk = true;
+            // this group's first item of the block: li and it advance together
+            int cnt_next = (i0 + ((grp - li) & 1) < i1) ? args.items[i0 + ((grp - li) & 1)].cnt : 0;
             for (int it = i0; it < i1; ++it, ++li) {
                 if ((li & 1) != grp) continue;
-                const int cnt = args.items[it].cnt;
+                const int cnt = cnt_next;
+                if (it + 2 < i1) cnt_next = args.items[it + 2].cnt;   // in flight while this item waits
                 const bool has_tgt = t < cnt;
                 const int sa = li & 1, sr = li % T16_NRAW, a4 = li & 3;
                 if (!mbar_wait(BAR_A_EMPTY(sa), ((li >> 1) & 1) ^ 1, abort_flag, args.status)) goto loader_done;
@@ -226,9 +229,12 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
             if (!mbar_wait(BAR_BLK_FULL(bs), (lb >> 1) & 1, abort_flag, args.status)) goto epi_done;
             const float4 *cv4 = reinterpret_cast<const float4 *>(sm + S::BLK + bs * S::BLKSLOT + S::BLK_COLV);
             const float *cwp = reinterpret_cast<const float *>(sm + S::BLK + bs * S::BLKSLOT + S::BLK_COLW);
-            for (int it = args.block_off[b]; it < args.block_off[b + 1]; ++it, ++li) {
+            const int i1 = args.block_off[b + 1];
+            EvalItem nxt = args.items[args.block_off[b]];
+            for (int it = args.block_off[b]; it < i1; ++it, ++li) {
                 const int a4 = li & 3;
-                const EvalItem item = args.items[it];
+                const EvalItem item = nxt;
+                if (it + 1 < i1) nxt = args.items[it + 1];   // in flight while this item waits
                 const int nrows = item.nrows & 0x7fffffff;
                 if (!mbar_wait(BAR_T_FULL(a4), (li >> 2) & 1, abort_flag, args.status)) goto epi_done;
                 tc_fence_after();
@@ -298,27 +304,47 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
     epi_done:;
     } else if (warp == 13) {
         // ------------------------------------------------- target-row gatherer
+        // The next item's descriptor and target slots are loaded while this
+        // item waits for its stage, so the two dependent global loads are
+        // off the critical path.
         const uint32_t bytes = (uint32_t)(T16_ROWS * args.d_pad * 4);
-        int li = 0, issued = 0;
-        for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci) {
-            const int b = args.cta_blocks[ci];
-            for (int it = args.block_off[b]; it < args.block_off[b + 1]; ++it, ++li) {
-                const int sr = li % T16_NRAW;
-                if (!mbar_wait(BAR_R_EMPTY(sr), ((li / T16_NRAW) & 1) ^ 1, abort_flag, args.status)) goto gather_done;
-                const EvalItem item = args.items[it];
-                const int first = args.tgt[item.e0];
-                int r[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int rw = 4 * lane + i;   // rows past cnt repeat the first target
-                    r[i] = rw < item.cnt ? args.tgt[item.e0 + rw] : first;
-                }
-                ++issued;
-                if (lane == 0) mbar_expect_tx(BAR_R_FULL(sr), bytes);
-                __syncwarp();
-                tma_gather4(sbase + S::RAW + sr * S::RAWSTAGE + 4 * lane * args.d_pad * 4, &map_q, 0, r[0], r[1], r[2],
-                            r[3], BAR_R_FULL(sr));
+        int issued = 0;
+        int ci = c_begin, it = 0;
+        auto seek = [&](int &c, int &i) {   // first item at or after (c, i) in this CTA's order
+            while (c < c_end && i >= args.block_off[args.cta_blocks[c] + 1]) {
+                ++c;
+                if (c < c_end) i = args.block_off[args.cta_blocks[c]];
             }
+        };
+        auto rows = [&](int i, int (&r)[4]) {
+            const EvalItem item = args.items[i];
+            const int first = args.tgt[item.e0];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int rw = 4 * lane + k;   // rows past cnt repeat the first target
+                r[k] = rw < item.cnt ? args.tgt[item.e0 + rw] : first;
+            }
+        };
+        if (ci < c_end) it = args.block_off[args.cta_blocks[ci]];
+        seek(ci, it);
+        int r[4] = {0, 0, 0, 0};
+        if (ci < c_end) rows(it, r);
+        for (int li = 0; ci < c_end && !*abort_flag; ++li) {
+            int ci2 = ci, it2 = it + 1;
+            seek(ci2, it2);
+            int rn[4] = {0, 0, 0, 0};
+            if (ci2 < c_end) rows(it2, rn);
+            const int sr = li % T16_NRAW;
+            if (!mbar_wait(BAR_R_EMPTY(sr), ((li / T16_NRAW) & 1) ^ 1, abort_flag, args.status)) goto gather_done;
+            ++issued;
+            if (lane == 0) mbar_expect_tx(BAR_R_FULL(sr), bytes);
+            __syncwarp();
+            tma_gather4(sbase + S::RAW + sr * S::RAWSTAGE + 4 * lane * args.d_pad * 4, &map_q, 0, r[0], r[1], r[2], r[3],
+                        BAR_R_FULL(sr));
+            ci = ci2;
+            it = it2;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) r[k] = rn[k];
         }
     gather_done:
         // rows of the last stages may still be landing after an abort
