@@ -90,7 +90,8 @@ template <int P, int RC>
 __global__ void __launch_bounds__(T16_THREADS, 1)
 eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_constant__ CUtensorMap map_t_lo,
                  const __grid_constant__ CUtensorMap map_s_hi, const __grid_constant__ CUtensorMap map_s_lo,
-                 const __grid_constant__ CUtensorMap map_q, const T16Args args) {
+                 const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_q8,
+                 const T16Args args) {
     using S = S16<RC>;
     constexpr uint32_t IDESC = make_idesc(P == ASKIT_PREC_BF16X3 ? 1u : 0u, T16_ROWS, T16_ROWS);
     extern __shared__ uint8_t smem_raw[];
@@ -339,8 +340,21 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
             ++issued;
             if (lane == 0) mbar_expect_tx(BAR_R_FULL(sr), bytes);
             __syncwarp();
-            tma_gather4(sbase + S::RAW + sr * S::RAWSTAGE + 4 * lane * args.d_pad * 4, &map_q, 0, r[0], r[1], r[2], r[3],
-                        BAR_R_FULL(sr));
+            {
+                // rows 8m .. 8m+7 (lanes 2m, 2m+1) that are 8 consecutive target
+                // slots arrive in one tiled copy; the rest by tile::gather4
+                const bool mine4 = r[1] == r[0] + 1 && r[2] == r[0] + 2 && r[3] == r[0] + 3;
+                const int r0_hi = __shfl_down_sync(0xffffffffu, r[0], 1);
+                const bool both4 = __shfl_down_sync(0xffffffffu, (int)mine4, 1) != 0;
+                const bool run8_lo = (lane & 1) == 0 && mine4 && both4 && r0_hi == r[0] + 4;
+                const bool run8 = __shfl_sync(0xffffffffu, (int)run8_lo, lane & ~1) != 0;
+                const uint32_t dst = sbase + S::RAW + sr * S::RAWSTAGE + 4 * lane * args.d_pad * 4;
+                if (run8) {
+                    if ((lane & 1) == 0) tma_load_2d(dst, &map_q8, 0, r[0], BAR_R_FULL(sr));
+                } else {
+                    tma_gather4(dst, &map_q, 0, r[0], r[1], r[2], r[3], BAR_R_FULL(sr));
+                }
+            }
             ci = ci2;
             it = it2;
 #pragma unroll
@@ -472,20 +486,22 @@ askit_status t16_state(askit_tree t, int pi, T16State **out) {
 }
 
 template <int P, int RC>
-askit_status launch16(T16State *st, int pi, const CUtensorMap &map_q, const T16Args &a, int grid, cudaStream_t s) {
+askit_status launch16(T16State *st, int pi, const CUtensorMap &map_q, const CUtensorMap &map_q8, const T16Args &a,
+                      int grid, cudaStream_t s) {
     using S = S16<RC>;
     const size_t smem = S::BYTES + 1024;
     static const cudaError_t attr =
         cudaFuncSetAttribute(eval_tc16_kernel<P, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     ASK_CUDA(attr);
     eval_tc16_kernel<P, RC><<<(unsigned)grid, T16_THREADS, smem, s>>>(st->map[pi][0], st->map[pi][1],
-                                                                     st->map[pi][2], st->map[pi][3], map_q, a);
+                                                                     st->map[pi][2], st->map[pi][3], map_q, map_q8, a);
     ASK_LAUNCH();
     return ASKIT_OK;
 }
 
 template <int P, int RC>
-askit_status run16(askit_tree t, const WeightCtx &c, T16State *st, int pi, const CUtensorMap &map_q, T16Args a,
+askit_status run16(askit_tree t, const WeightCtx &c, T16State *st, int pi, const CUtensorMap &map_q,
+                   const CUtensorMap &map_q8, T16Args a,
                    const WorkLists &w, cudaStream_t s) {
     const float g_unscale = 1.f / (a.f16_scale * a.f16_scale);
     tc16_cols_kernel<RC><<<(unsigned)t->n_sub, 128, 0, s>>>(t->sb_row0, t->sb_nr, t->n_leaf_sub, t->sc_t, t->sc_s,
@@ -494,15 +510,15 @@ askit_status run16(askit_tree t, const WeightCtx &c, T16State *st, int pi, const
     ASK_LAUNCH();
     a.colv = c.colv;
     a.colw = c.colw;
-    return launch16<P, RC>(st, pi, map_q, a, w.n_ctas, s);
+    return launch16<P, RC>(st, pi, map_q, map_q8, a, w.n_ctas, s);
 }
 
 template <int P>
 askit_status dispatch16(askit_tree t, const WeightCtx &c, T16State *st, int pi, const CUtensorMap &map_q,
-                        const T16Args &a, const WorkLists &w, cudaStream_t s) {
-    if (c.r == 1) return run16<P, 1>(t, c, st, pi, map_q, a, w, s);
-    if (c.r <= 4) return run16<P, 4>(t, c, st, pi, map_q, a, w, s);
-    return run16<P, 16>(t, c, st, pi, map_q, a, w, s);
+                        const CUtensorMap &map_q8, const T16Args &a, const WorkLists &w, cudaStream_t s) {
+    if (c.r == 1) return run16<P, 1>(t, c, st, pi, map_q, map_q8, a, w, s);
+    if (c.r <= 4) return run16<P, 4>(t, c, st, pi, map_q, map_q8, a, w, s);
+    return run16<P, 16>(t, c, st, pi, map_q, map_q8, a, w, s);
 }
 
 }  // namespace
@@ -524,6 +540,9 @@ askit_status eval_tc16(askit_tree t, const WeightCtx &c, int precision, const fl
     CUtensorMap map_q;   // one box row per gathered target row
     ASK_TRY(encode_2d(st->encode, &map_q, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, Xq, q_rows, t->d_pad, t->d_pad, 1,
                       CU_TENSOR_MAP_SWIZZLE_NONE));
+    CUtensorMap map_q8;  // runs of 8 consecutive target rows: one tiled box
+    ASK_TRY(encode_2d(st->encode, &map_q8, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, Xq, q_rows, t->d_pad, t->d_pad, 8,
+                      CU_TENSOR_MAP_SWIZZLE_NONE));
     T16Args a;
     a.items = w.items;
     a.block_off = w.block_off;
@@ -542,7 +561,7 @@ askit_status eval_tc16(askit_tree t, const WeightCtx &c, int precision, const fl
         askit_set_error("eval_tc16 runs FP16x3");
         return ASKIT_ERR_INVALID_ARG;
     }
-    return dispatch16<ASKIT_PREC_FP16X3>(t, c, st, pi, map_q, a, w, s);
+    return dispatch16<ASKIT_PREC_FP16X3>(t, c, st, pi, map_q, map_q8, a, w, s);
 }
 
 void eval_tc16_free(askit_tree t) {
