@@ -212,6 +212,8 @@ def serving(args, dev, precision):
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     Wres = torch.from_numpy(w.make_weights(1)).to(dev)
+    tree.set_weights(Wres)
+    out_tune = tree.autotune(reps=2)
     pool = torch.from_numpy(w.make_weights(128, seed_offset=7)).to(dev)
     spec = wl.request_stream(args.serve_requests, 200.0, seed=w.seed)
     rng = np.random.default_rng(w.seed + 17)
@@ -226,6 +228,7 @@ def serving(args, dev, precision):
             stream.append((ta, kind, Y[off:off + size]))
             off += size
     out = {"workload": w.name, "arrivals_per_s": 200.0, "slots": 2, "setup_s": setup_s,
+           "autotune": next((c for c in out_tune if c["chosen"]), None),
            "targets_counted_as": "N r per weight request, T per target batch"}
     for prec in (precision, "simt_fp32"):
         tree.set_precision(prec)
@@ -277,6 +280,10 @@ def main():
     info = tree.info()
     stream = torch.cuda.current_stream()
 
+    # launch configuration of the Evaluate kernel picked by the autotuner
+    # (part of setup: it times candidates on this tree's own work lists)
+    tree.set_weights(Wd)
+    tune = tree.autotune(reps=3)
     # the step is replayed from a captured CUDA graph (askit_graph_*): the
     # upward pass and Evaluate, one graph launch per step
     graph = tree.capture(Wd, U)
@@ -411,6 +418,7 @@ def main():
             "rel_err_vs_fp32": rel_vs_fp32, "rel_err_ok": rel_vs_fp32 <= 1e-4, "eps2_vs_direct": eps2,
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk, "roofline": roof,
             "cpu_baseline": cpu, "serving": None,
+            "autotune": {"chosen": next((c for c in tune if c["chosen"]), None), "candidates": tune},
             "work": {"pairs_algorithmic": P, "pairs_computed": info["pairs_computed"],
                      "near_per_target": info["near_total"] / N, "far_per_target": info["far_total"] / N,
                      "items": info["n_items"], "blocks": info["n_blocks"], "entries": info["n_entries"], "L": info["L"],

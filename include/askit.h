@@ -204,6 +204,31 @@ askit_status askit_graph_launch(askit_graph g, void *stream);
 askit_status askit_graph_destroy(askit_graph g);
 
 /*
+ * Autotuner of the evaluation kernels' launch configuration.  Times every
+ * candidate configuration of the persistent Evaluate kernel for the tree's
+ * current precision on its own work lists and default weights (set them
+ * first), keeps the fastest for later evaluations of this tree, and reports
+ * each candidate.  Candidates:
+ *   schedule    0: sub-blocks dealt heaviest first to the least-loaded CTA;
+ *               1: sub-blocks in tree order, cut into contiguous equal-cost
+ *                  ranges (consecutive sub-blocks share targets: L2 reuse);
+ *   stages      gathered target-row stages of the FP16x3 kernel (2 or 3);
+ *   tiled_runs  1: runs of 8 consecutive target rows arrive in one tiled
+ *               copy (FP16x3 kernel), 0: every row by tile::gather4.
+ * Only the schedule varies for the other tensor-core kernels; the plain FP32
+ * kernel has one configuration.  Results do not depend on the configuration
+ * (every work item is computed the same way; partials are reduced in a fixed
+ * order).  `reps` timed evaluations per candidate after one warm-up; at most
+ * `max_out` entries are written to `out`, the count to `n_out`.  Blocks.
+ */
+typedef struct {
+    int32_t schedule, stages, tiled_runs, chosen;
+    double ms;   /* mean Evaluate time of the candidate */
+} askit_tune_entry;
+askit_status askit_autotune(askit_tree t, int32_t reps, void *stream, askit_tune_entry *out, int32_t max_out,
+                            int32_t *n_out);
+
+/*
  * Device bytes a request needs, for admission by memory footprint.
  *   kind 0: a weight context for r vectors (n ignored);
  *   kind 1: an out-of-sample batch of n targets with r weight vectors

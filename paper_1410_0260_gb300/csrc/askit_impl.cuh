@@ -117,8 +117,10 @@ struct WorkLists {
     // persistent-kernel schedule: sub-blocks dealt to n_ctas CTAs, heaviest
     // first, each to the CTA with the least work so far
     int n_ctas = 0;
-    int32_t *cta_off = nullptr;      // [n_ctas + 1]
+    int32_t *cta_off = nullptr;      // [n_ctas + 1] the schedule in use (one of the two below)
     int32_t *cta_blocks = nullptr;   // [n_blocks]
+    int32_t *sched_off[2] = {nullptr, nullptr};     // 0: longest first (LPT), 1: tree-order ranges
+    int32_t *sched_blocks[2] = {nullptr, nullptr};
     int64_t pairs_alg = 0, pairs_cmp = 0, near_tot = 0, far_tot = 0;
 };
 
@@ -221,6 +223,11 @@ struct askit_tree_s {
     int64_t *sb_row0 = nullptr;    // [n_sub] first row of each sub-block (Xt rows, then Xs rows)
     int32_t *sb_nr = nullptr;      // [n_sub] rows of each sub-block
     int64_t n_leaf_sub = 0;        // sub-blocks of leaves (the rest are skeleton sub-blocks)
+    std::vector<int64_t> h_sub_pos; // [n_sub] tree position of each sub-block's node (schedule order)
+    // launch configuration of the evaluation kernels (askit_autotune)
+    int tune_sched = 0;            // block-to-CTA schedule: 0 LPT, 1 tree-order ranges
+    int tune_stages = 3;           // gathered target-row stages of the FP16x3 kernel (2 or 3)
+    int tune_runs = 1;             // 8-row tiled loads for runs of consecutive targets
     int kw = TC_K;                 // row width of the pre-split operands and centers
 };
 

@@ -552,6 +552,65 @@ askit_status askit_weights_destroy(askit_weights w) {
     return ASKIT_OK;
 }
 
+askit_status askit_autotune(askit_tree t, int32_t reps, void *stream, askit_tune_entry *out, int32_t max_out,
+                            int32_t *n_out) {
+    if (!t || !n_out || (max_out > 0 && !out) || reps < 1) {
+        askit_set_error("need a tree, reps >= 1, n_out and room for the entries");
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    if (!t->dw.ready) { askit_set_error("set weights before autotuning"); return ASKIT_ERR_NOT_READY; }
+    cudaStream_t s = (cudaStream_t)stream;
+    struct Cand { int sched, stages, runs; double ms; };
+    std::vector<Cand> cand;
+    const bool tc = t->precision != ASKIT_PREC_SIMT_FP32;
+    const bool fp16 = t->precision == ASKIT_PREC_FP16X3 && t->d <= TC_K;
+    for (int sc = 0; sc < (tc ? 2 : 1); ++sc)
+        for (int st = (fp16 ? 2 : t->tune_stages); st <= (fp16 ? 3 : t->tune_stages); ++st)
+            for (int ru = (fp16 ? 0 : t->tune_runs); ru <= (fp16 ? 1 : t->tune_runs); ++ru)
+                cand.push_back({sc, st, ru, 0.0});
+    float *U = nullptr;
+    ASK_CUDA(cudaMallocAsync(&U, sizeof(float) * (size_t)t->N * std::max(1, t->dw.r), s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    askit_status rc = ASKIT_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        askit_set_error("events");
+        rc = ASKIT_ERR_CUDA;
+    }
+    auto apply = [&](const Cand &c) {
+        t->tune_sched = c.sched;
+        t->tune_stages = c.stages;
+        t->tune_runs = c.runs;
+        t->wl.cta_off = t->wl.sched_off[c.sched & 1];
+        t->wl.cta_blocks = t->wl.sched_blocks[c.sched & 1];
+    };
+    for (size_t k = 0; k < cand.size() && rc == ASKIT_OK; ++k) {
+        apply(cand[k]);
+        rc = evaluate_ctx(t, t->dw, U, std::max(1, t->dw.r), s);                 // warm-up
+        if (rc == ASKIT_OK && cudaEventRecord(e0, s) != cudaSuccess) rc = ASKIT_ERR_CUDA;
+        for (int q = 0; q < reps && rc == ASKIT_OK; ++q) rc = evaluate_ctx(t, t->dw, U, std::max(1, t->dw.r), s);
+        if (rc == ASKIT_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)) {
+            askit_set_error("autotune timing: %s", cudaGetErrorString(cudaGetLastError()));
+            rc = ASKIT_ERR_CUDA;
+        }
+        float ms = 0.f;
+        if (rc == ASKIT_OK) cudaEventElapsedTime(&ms, e0, e1);
+        cand[k].ms = ms / reps;
+    }
+    size_t best = 0;
+    for (size_t k = 1; k < cand.size(); ++k)
+        if (cand[k].ms < cand[best].ms) best = k;
+    if (!cand.empty()) apply(cand[best]);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(U, s);
+    cudaStreamSynchronize(s);
+    if (rc != ASKIT_OK) return rc;
+    *n_out = (int32_t)std::min<size_t>(cand.size(), (size_t)std::max(0, max_out));
+    for (int32_t k = 0; k < *n_out; ++k)
+        out[k] = {cand[k].sched, cand[k].stages, cand[k].runs, (int32_t)((size_t)k == best), cand[k].ms};
+    return ASKIT_OK;
+}
+
 askit_status askit_graph_create(askit_tree t, const float *W_dev, int32_t r, int64_t ldw, float *U_dev,
                                 int64_t ldu, void *stream, askit_graph *out) {
     if (!t || !out || !U_dev) { askit_set_error("tree, U_dev and out must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }

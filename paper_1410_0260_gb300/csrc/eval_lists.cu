@@ -352,6 +352,12 @@ askit_status build_tc_operands(askit_tree t, cudaStream_t s) {
     }
     for (int64_t a = 2; a < nn; ++a) ncb[a] += (int32_t)n_leaf_sub;
     t->n_sub = (int64_t)r0.size();
+    // schedule order of the sub-blocks: the tree position of their node's
+    // first point (leaf sub-blocks: their own first row), then their index
+    t->h_sub_pos.assign(t->n_sub, 0);
+    for (int64_t q = 0; q < n_leaf_sub; ++q) t->h_sub_pos[q] = r0[q];
+    for (int64_t a = 2; a < nn; ++a)
+        for (int64_t ch = 0; ch * ASK_BLK_N < t->h_s[a]; ++ch) t->h_sub_pos[ncb[a] + ch] = t->h_start[a];
     ASK_TRY(t->arena.alloc(&t->leaf_cbase, M));
     ASK_TRY(t->arena.alloc(&t->node_cbase, nn));
     ASK_CUDA(cudaMemcpyAsync(t->leaf_cbase, lcb.data(), sizeof(int32_t) * M, cudaMemcpyHostToDevice, s));
@@ -546,40 +552,73 @@ askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, int
         std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
         WTRY(arena.alloc(&w.block_order, nb));
         WCHK(cudaMemcpyAsync(w.block_order, order.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
-        // LPT schedule over one persistent CTA per SM: a sub-block costs its
-        // items plus a fixed reload of its source tile
+        // Two schedules over one persistent CTA per SM (a sub-block costs its
+        // items plus a fixed reload of its source tile); askit_autotune picks.
+        //  0: LPT -- heaviest first, each to the least-loaded CTA;
+        //  1: tree order -- sub-blocks sorted by their node's position, cut
+        //     into contiguous ranges of equal cost, so consecutive sub-blocks
+        //     of a CTA share most of their targets (L2 reuse of target rows).
         int dev = 0, sms = 0;
         WCHK(cudaGetDevice(&dev));
         WCHK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         const int nc = (int)std::max<int64_t>(1, std::min<int64_t>(nb, sms));
-        std::vector<std::vector<int32_t>> lists(nc);
-        std::vector<std::pair<int64_t, int>> heap;   // (load, cta), min-heap
-        for (int c = 0; c < nc; ++c) heap.push_back({0, c});
-        auto cmp = [](const std::pair<int64_t, int> &x, const std::pair<int64_t, int> &y) {
-            return x.first > y.first || (x.first == y.first && x.second > y.second);
-        };
-        std::make_heap(heap.begin(), heap.end(), cmp);
-        for (int64_t q = 0; q < nb; ++q) {
-            const int32_t bq = order[q];
-            std::pop_heap(heap.begin(), heap.end(), cmp);
-            auto top = heap.back();
-            heap.pop_back();
-            lists[top.second].push_back(bq);
-            top.first += (boff[bq + 1] - boff[bq]) * 4 + 3;
-            heap.push_back(top);
-            std::push_heap(heap.begin(), heap.end(), cmp);
+        auto bcost = [&](int32_t b) { return (int64_t)(boff[b + 1] - boff[b]) * 4 + 3; };
+        std::vector<int32_t> coff[2], cblk[2];
+        {
+            std::vector<std::vector<int32_t>> lists(nc);
+            std::vector<std::pair<int64_t, int>> heap;   // (load, cta), min-heap
+            for (int c = 0; c < nc; ++c) heap.push_back({0, c});
+            auto cmp = [](const std::pair<int64_t, int> &x, const std::pair<int64_t, int> &y) {
+                return x.first > y.first || (x.first == y.first && x.second > y.second);
+            };
+            std::make_heap(heap.begin(), heap.end(), cmp);
+            for (int64_t q = 0; q < nb; ++q) {
+                const int32_t bq = order[q];
+                std::pop_heap(heap.begin(), heap.end(), cmp);
+                auto top = heap.back();
+                heap.pop_back();
+                lists[top.second].push_back(bq);
+                top.first += bcost(bq);
+                heap.push_back(top);
+                std::push_heap(heap.begin(), heap.end(), cmp);
+            }
+            coff[0].assign(nc + 1, 0);
+            for (int c = 0; c < nc; ++c) {
+                coff[0][c + 1] = coff[0][c] + (int32_t)lists[c].size();
+                cblk[0].insert(cblk[0].end(), lists[c].begin(), lists[c].end());
+            }
         }
-        std::vector<int32_t> coff(nc + 1, 0), cblk;
-        cblk.reserve(nb);
-        for (int c = 0; c < nc; ++c) {
-            coff[c + 1] = coff[c] + (int32_t)lists[c].size();
-            cblk.insert(cblk.end(), lists[c].begin(), lists[c].end());
+        {
+            std::vector<int64_t> bpos(nb, 0);
+            for (int64_t b = 0; b < nb; ++b) {
+                const int32_t cx = hi[boff[b]].cidx;
+                bpos[b] = (cx >= 0 && cx < (int32_t)t->h_sub_pos.size()) ? t->h_sub_pos[cx] : 0;
+            }
+            std::vector<int32_t> tord(nb);
+            for (int64_t b = 0; b < nb; ++b) tord[b] = (int32_t)b;
+            std::stable_sort(tord.begin(), tord.end(), [&](int32_t x, int32_t y) { return bpos[x] < bpos[y]; });
+            int64_t total = 0;
+            for (int64_t b = 0; b < nb; ++b) total += bcost((int32_t)b);
+            coff[1].assign(nc + 1, 0);
+            int c = 0;
+            int64_t acc = 0;
+            for (int64_t q = 0; q < nb; ++q) {
+                cblk[1].push_back(tord[q]);
+                acc += bcost(tord[q]);
+                ++coff[1][c + 1];
+                if (c < nc - 1 && acc * nc >= (int64_t)(c + 1) * total) ++c;
+            }
+            for (int k = 0; k < nc; ++k) coff[1][k + 1] += coff[1][k];
         }
         w.n_ctas = nc;
-        WTRY(arena.alloc(&w.cta_off, nc + 1));
-        WTRY(arena.alloc(&w.cta_blocks, std::max<int64_t>(1, nb)));
-        WCHK(cudaMemcpyAsync(w.cta_off, coff.data(), sizeof(int32_t) * (nc + 1), cudaMemcpyHostToDevice, s));
-        WCHK(cudaMemcpyAsync(w.cta_blocks, cblk.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
+        for (int k = 0; k < 2; ++k) {
+            WTRY(arena.alloc(&w.sched_off[k], nc + 1));
+            WTRY(arena.alloc(&w.sched_blocks[k], std::max<int64_t>(1, nb)));
+            WCHK(cudaMemcpyAsync(w.sched_off[k], coff[k].data(), sizeof(int32_t) * (nc + 1), cudaMemcpyHostToDevice, s));
+            WCHK(cudaMemcpyAsync(w.sched_blocks[k], cblk[k].data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
+        }
+        w.cta_off = w.sched_off[t->tune_sched & 1];
+        w.cta_blocks = w.sched_blocks[t->tune_sched & 1];
         WCHK(cudaStreamSynchronize(s));
         int64_t sn = 0, sf = 0, pa = 0;
         for (int64_t q = 0; q < T; ++q) { sn += h_near[q]; sf += h_far[q]; pa += h_pairs[q]; }

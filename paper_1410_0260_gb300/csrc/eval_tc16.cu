@@ -27,7 +27,8 @@
 //   warp 12    TMEM allocation; lane 0 loads each sub-block (TMA tiles of the
 //              pre-split rows, bulk copies of its center and column data)
 //              and issues the tcgen05.mma instructions;
-//   warp 13    TMA tile::gather4 of each item's target rows, three stages.
+//   warp 13    TMA tile::gather4 of each item's target rows (8-row tiled boxes
+//              for runs of consecutive rows), two or three stages.
 // Four TMEM accumulators (4 x 128 columns) let the MMAs run up to three items
 // ahead of the epilogue.  Every mbarrier wait is bounded: on timeout the
 // kernel records ASK_DEV_TIMEOUT, all roles leave their loops, producers
@@ -50,15 +51,15 @@ constexpr int T16_THREADS = 448;
 constexpr int T16_ROWS = 128;
 constexpr int T16_REGION = T16_ROWS * 128;     // 128 rows x 128 bytes (64 16-bit elements), swizzled
 constexpr uint32_t T16_TMEM_COLS = 512;        // four 128-column FP32 accumulators
-constexpr int T16_NRAW = 3;                    // gathered target-row stages
 
-template <int RC>
+// NRAW: stages of gathered target rows (2 or 3, chosen by askit_autotune)
+template <int RC, int NRAW>
 struct S16 {
     static constexpr int B_HI = 0, B_LO = T16_REGION;
     static constexpr int A0 = 2 * T16_REGION;                 // stage s: hi at A0 + 2s REGION, lo + REGION
-    static constexpr int RAW = A0 + 4 * T16_REGION;           // [3] stages of 128 rows x d_pad floats
+    static constexpr int RAW = A0 + 4 * T16_REGION;           // [NRAW] stages of 128 rows x d_pad floats
     static constexpr int RAWSTAGE = T16_ROWS * TC_K * 4;
-    static constexpr int BLK = RAW + T16_NRAW * RAWSTAGE;     // [2] per-sub-block slots
+    static constexpr int BLK = RAW + NRAW * RAWSTAGE;         // [2] per-sub-block slots
     static constexpr int BLK_CENT = 0;                        // float [64] c_B
     static constexpr int BLK_COLV = 256;                      // float4 [128] pair-interleaved column data
     static constexpr int BLK_COLW = BLK_COLV + 128 * 16;      // float [128][RC] weights (RC > 1)
@@ -82,17 +83,18 @@ struct T16Args {
     const float *colw;        // [n_sub, 128, RC] (RC > 1)
     int r;
     float f16_scale;
+    int runs;                 // 8-row tiled loads for runs of consecutive target rows
     float *partial;
     int *status;
 };
 
-template <int P, int RC>
+template <int P, int RC, int NRAW>
 __global__ void __launch_bounds__(T16_THREADS, 1)
 eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_constant__ CUtensorMap map_t_lo,
                  const __grid_constant__ CUtensorMap map_s_hi, const __grid_constant__ CUtensorMap map_s_lo,
                  const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_q8,
                  const T16Args args) {
-    using S = S16<RC>;
+    using S = S16<RC, NRAW>;
     constexpr uint32_t IDESC = make_idesc(P == ASKIT_PREC_BF16X3 ? 1u : 0u, T16_ROWS, T16_ROWS);
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -119,7 +121,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
             mbar_init(BAR_BLK_FULL(s), 1);
             mbar_init(BAR_BLK_EMPTY(s), 128);
         }
-        for (int s = 0; s < T16_NRAW; ++s) {
+        for (int s = 0; s < NRAW; ++s) {
             mbar_init(BAR_R_FULL(s), 1);
             mbar_init(BAR_R_EMPTY(s), 128);
         }
@@ -161,10 +163,10 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                 const int cnt = cnt_next;
                 if (it + 2 < i1) cnt_next = args.items[it + 2].cnt;   // in flight while this item waits
                 const bool has_tgt = t < cnt;
-                const int sa = li & 1, sr = li % T16_NRAW, a4 = li & 3;
+                const int sa = li & 1, sr = li % NRAW, a4 = li & 3;
                 if (!mbar_wait(BAR_A_EMPTY(sa), ((li >> 1) & 1) ^ 1, abort_flag, args.status)) goto loader_done;
                 if (!mbar_wait(BAR_T_EMPTY(a4), ((li >> 2) & 1) ^ 1, abort_flag, args.status)) goto loader_done;
-                if (!mbar_wait(BAR_R_FULL(sr), (li / T16_NRAW) & 1, abort_flag, args.status)) goto loader_done;
+                if (!mbar_wait(BAR_R_FULL(sr), (li / NRAW) & 1, abort_flag, args.status)) goto loader_done;
                 if (need_blk) {
                     if (!mbar_wait(BAR_BLK_FULL(lb & 1), (lb >> 1) & 1, abort_flag, args.status)) goto loader_done;
                     need_blk = false;
@@ -335,8 +337,8 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
             seek(ci2, it2);
             int rn[4] = {0, 0, 0, 0};
             if (ci2 < c_end) rows(it2, rn);
-            const int sr = li % T16_NRAW;
-            if (!mbar_wait(BAR_R_EMPTY(sr), ((li / T16_NRAW) & 1) ^ 1, abort_flag, args.status)) goto gather_done;
+            const int sr = li % NRAW;
+            if (!mbar_wait(BAR_R_EMPTY(sr), ((li / NRAW) & 1) ^ 1, abort_flag, args.status)) goto gather_done;
             ++issued;
             if (lane == 0) mbar_expect_tx(BAR_R_FULL(sr), bytes);
             __syncwarp();
@@ -347,7 +349,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                 const int r0_hi = __shfl_down_sync(0xffffffffu, r[0], 1);
                 const bool both4 = __shfl_down_sync(0xffffffffu, (int)mine4, 1) != 0;
                 const bool run8_lo = (lane & 1) == 0 && mine4 && both4 && r0_hi == r[0] + 4;
-                const bool run8 = __shfl_sync(0xffffffffu, (int)run8_lo, lane & ~1) != 0;
+                const bool run8 = args.runs && __shfl_sync(0xffffffffu, (int)run8_lo, lane & ~1) != 0;
                 const uint32_t dst = sbase + S::RAW + sr * S::RAWSTAGE + 4 * lane * args.d_pad * 4;
                 if (run8) {
                     if ((lane & 1) == 0) tma_load_2d(dst, &map_q8, 0, r[0], BAR_R_FULL(sr));
@@ -362,8 +364,8 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
         }
     gather_done:
         // rows of the last stages may still be landing after an abort
-        for (int gg = issued > T16_NRAW ? issued - T16_NRAW : 0; gg < issued; ++gg)
-            mbar_drain(BAR_R_FULL(gg % T16_NRAW), (gg / T16_NRAW) & 1);
+        for (int gg = issued > NRAW ? issued - NRAW : 0; gg < issued; ++gg)
+            mbar_drain(BAR_R_FULL(gg % NRAW), (gg / NRAW) & 1);
     } else if (warp == 12 && lane == 0) {
         // ------------------------------------- sub-block loads + MMA issuer
         int li = 0, lb = 0, b_issued = 0;
@@ -485,15 +487,15 @@ askit_status t16_state(askit_tree t, int pi, T16State **out) {
     return ASKIT_OK;
 }
 
-template <int P, int RC>
+template <int P, int RC, int NRAW>
 askit_status launch16(T16State *st, int pi, const CUtensorMap &map_q, const CUtensorMap &map_q8, const T16Args &a,
                       int grid, cudaStream_t s) {
-    using S = S16<RC>;
+    using S = S16<RC, NRAW>;
     const size_t smem = S::BYTES + 1024;
     static const cudaError_t attr =
-        cudaFuncSetAttribute(eval_tc16_kernel<P, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(eval_tc16_kernel<P, RC, NRAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     ASK_CUDA(attr);
-    eval_tc16_kernel<P, RC><<<(unsigned)grid, T16_THREADS, smem, s>>>(st->map[pi][0], st->map[pi][1],
+    eval_tc16_kernel<P, RC, NRAW><<<(unsigned)grid, T16_THREADS, smem, s>>>(st->map[pi][0], st->map[pi][1],
                                                                      st->map[pi][2], st->map[pi][3], map_q, map_q8, a);
     ASK_LAUNCH();
     return ASKIT_OK;
@@ -510,7 +512,8 @@ askit_status run16(askit_tree t, const WeightCtx &c, T16State *st, int pi, const
     ASK_LAUNCH();
     a.colv = c.colv;
     a.colw = c.colw;
-    return launch16<P, RC>(st, pi, map_q, map_q8, a, w.n_ctas, s);
+    if (t->tune_stages == 2) return launch16<P, RC, 2>(st, pi, map_q, map_q8, a, w.n_ctas, s);
+    return launch16<P, RC, 3>(st, pi, map_q, map_q8, a, w.n_ctas, s);
 }
 
 template <int P>
@@ -555,6 +558,7 @@ askit_status eval_tc16(askit_tree t, const WeightCtx &c, int precision, const fl
     a.colw = nullptr;
     a.r = c.r;
     a.f16_scale = precision == ASKIT_PREC_FP16X3 ? t->f16_scale : 1.f;
+    a.runs = t->tune_runs;
     a.partial = partial;
     a.status = t->d_status;
     if (precision != ASKIT_PREC_FP16X3) {
