@@ -214,19 +214,27 @@ askit_status askit_graph_destroy(askit_graph g);
  *                  ranges (consecutive sub-blocks share targets: L2 reuse);
  *   stages      gathered target-row stages of the FP16x3 kernel (2 or 3);
  *   tiled_runs  1: runs of 8 consecutive target rows arrive in one tiled
- *               copy (FP16x3 kernel), 0: every row by tile::gather4.
+ *               copy (FP16x3 kernel), 0: every row by tile::gather4;
+ *   pairs       1: the FP16x3 kernel takes sub-blocks 2k and 2k+1 of a node
+ *               (same targets) in one 256-column item (schedule 2: the
+ *               leaders dealt longest first), r <= 4.
  * Only the schedule varies for the other tensor-core kernels; the plain FP32
- * kernel has one configuration.  Results do not depend on the configuration
- * (every work item is computed the same way; partials are reduced in a fixed
- * order).  `reps` timed evaluations per candidate after one warm-up; at most
+ * kernel has one configuration.  Schedules, stages and tiled runs change no
+ * result bit (every work item is computed the same way; partials are reduced
+ * in a fixed order); paired items sum both sub-blocks' columns in one
+ * accumulator, which changes the FP32 summation order only.  `reps` timed evaluations per candidate after one warm-up; at most
  * `max_out` entries are written to `out`, the count to `n_out`.  Blocks.
  */
 typedef struct {
-    int32_t schedule, stages, tiled_runs, chosen;
+    int32_t schedule, stages, tiled_runs, pairs, chosen;
     double ms;   /* mean Evaluate time of the candidate */
 } askit_tune_entry;
 askit_status askit_autotune(askit_tree t, int32_t reps, void *stream, askit_tune_entry *out, int32_t max_out,
                             int32_t *n_out);
+/* Set the launch configuration directly (schedule 0|1, stages 2|3,
+ * tiled_runs 0|1, pairs 0|1; pairs needs stages 2 and uses its own
+ * schedule).  Host call; applies to later evaluations of the tree. */
+askit_status askit_set_launch(askit_tree t, int32_t schedule, int32_t stages, int32_t tiled_runs, int32_t pairs);
 
 /*
  * Device bytes a request needs, for admission by memory footprint.

@@ -31,12 +31,12 @@ EXPORTS = ["askit_default_params", "askit_setup", "askit_set_weights", "askit_ev
            "askit_last_error", "askit_knn_noalloc", "askit_direct", "askit_weights_create",
            "askit_weights_set", "askit_weights_evaluate", "askit_weights_evaluate_targets",
            "askit_weights_destroy", "askit_footprint", "askit_graph_create", "askit_graph_launch",
-           "askit_graph_destroy", "askit_autotune"]
+           "askit_graph_destroy", "askit_autotune", "askit_set_launch"]
 
 
 class TuneEntry(C.Structure):
-    _fields_ = [("schedule", C.c_int32), ("stages", C.c_int32), ("tiled_runs", C.c_int32), ("chosen", C.c_int32),
-                ("ms", C.c_double)]
+    _fields_ = [("schedule", C.c_int32), ("stages", C.c_int32), ("tiled_runs", C.c_int32), ("pairs", C.c_int32),
+                ("chosen", C.c_int32), ("ms", C.c_double)]
 
 
 class AskitError(RuntimeError):
@@ -93,6 +93,7 @@ def load(path: str | None = None):
             L.askit_graph_launch.argtypes = [V, V]
             L.askit_graph_destroy.argtypes = [V]
             L.askit_autotune.argtypes = [V, I32, V, C.POINTER(TuneEntry), I32, C.POINTER(I32)]
+            L.askit_set_launch.argtypes = [V, I32, I32, I32, I32]
             L.askit_status_string.restype = C.c_char_p
             L.askit_status_string.argtypes = [C.c_int]
             L.askit_last_error.restype = C.c_char_p
@@ -249,8 +250,14 @@ class Tree:
         out = (TuneEntry * 16)()
         n = C.c_int32()
         _check(load().askit_autotune(self._t, reps, _stream(stream), out, 16, C.byref(n)))
-        return [{"schedule": ("lpt", "tree_order")[e.schedule], "stages": e.stages, "tiled_runs": bool(e.tiled_runs),
-                 "chosen": bool(e.chosen), "ms": e.ms} for e in out[:n.value]]
+        return [{"schedule": ("lpt", "tree_order", "lpt_pairs")[e.schedule], "stages": e.stages,
+                 "tiled_runs": bool(e.tiled_runs), "pairs": bool(e.pairs), "chosen": bool(e.chosen), "ms": e.ms}
+                for e in out[:n.value]]
+
+    def set_launch(self, schedule: str = "lpt", stages: int = 3, tiled_runs: bool = True, pairs: bool = False):
+        """Set the evaluation kernel's launch configuration (see autotune)."""
+        _check(load().askit_set_launch(self._t, {"lpt": 0, "tree_order": 1}[schedule], stages, int(tiled_runs),
+                                       int(pairs)))
 
     def capture(self, W: torch.Tensor, U: torch.Tensor, stream=None) -> "Graph":
         """A CUDA graph of set_weights(W) + evaluate(U); replays read W's

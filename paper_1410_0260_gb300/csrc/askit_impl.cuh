@@ -119,8 +119,13 @@ struct WorkLists {
     int n_ctas = 0;
     int32_t *cta_off = nullptr;      // [n_ctas + 1] the schedule in use (one of the two below)
     int32_t *cta_blocks = nullptr;   // [n_blocks]
-    int32_t *sched_off[2] = {nullptr, nullptr};     // 0: longest first (LPT), 1: tree-order ranges
-    int32_t *sched_blocks[2] = {nullptr, nullptr};
+    // 0: longest first (LPT), 1: tree-order ranges, 2: LPT over sub-block
+    // pairs (the leader of each pair; followers are processed with it)
+    int32_t *sched_off[3] = {nullptr, nullptr, nullptr};
+    int32_t *sched_blocks[3] = {nullptr, nullptr, nullptr};
+    int n_ctas_sched[3] = {0, 0, 0};
+    int32_t *partner = nullptr;      // [n_blocks] the paired follower of a leader block, else -1
+    int64_t n_pairs = 0;
     int64_t pairs_alg = 0, pairs_cmp = 0, near_tot = 0, far_tot = 0;
 };
 
@@ -224,10 +229,12 @@ struct askit_tree_s {
     int32_t *sb_nr = nullptr;      // [n_sub] rows of each sub-block
     int64_t n_leaf_sub = 0;        // sub-blocks of leaves (the rest are skeleton sub-blocks)
     std::vector<int64_t> h_sub_pos; // [n_sub] tree position of each sub-block's node (schedule order)
+    std::vector<int64_t> h_sub_node; // [n_sub] heap index of each sub-block's node
     // launch configuration of the evaluation kernels (askit_autotune)
     int tune_sched = 0;            // block-to-CTA schedule: 0 LPT, 1 tree-order ranges
     int tune_stages = 3;           // gathered target-row stages of the FP16x3 kernel (2 or 3)
     int tune_runs = 1;             // 8-row tiled loads for runs of consecutive targets
+    int tune_pairs = 0;            // FP16x3: items over two sub-blocks of a node (256 columns)
     int kw = TC_K;                 // row width of the pre-split operands and centers
 };
 

@@ -552,6 +552,25 @@ askit_status askit_weights_destroy(askit_weights w) {
     return ASKIT_OK;
 }
 
+askit_status askit_set_launch(askit_tree t, int32_t schedule, int32_t stages, int32_t tiled_runs, int32_t pairs) {
+    if (!t || schedule < 0 || schedule > 1 || stages < 2 || stages > 3 || tiled_runs < 0 || tiled_runs > 1 ||
+        pairs < 0 || pairs > 1) {
+        askit_set_error("need schedule 0|1, stages 2|3, tiled_runs 0|1, pairs 0|1");
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    if (pairs && stages != 2) {
+        askit_set_error("paired items run with two stages");
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    t->tune_sched = pairs ? 0 : schedule;
+    t->tune_stages = stages;
+    t->tune_runs = tiled_runs;
+    t->tune_pairs = pairs;
+    t->wl.cta_off = t->wl.sched_off[t->tune_sched];
+    t->wl.cta_blocks = t->wl.sched_blocks[t->tune_sched];
+    return ASKIT_OK;
+}
+
 askit_status askit_autotune(askit_tree t, int32_t reps, void *stream, askit_tune_entry *out, int32_t max_out,
                             int32_t *n_out) {
     if (!t || !n_out || (max_out > 0 && !out) || reps < 1) {
@@ -560,14 +579,17 @@ askit_status askit_autotune(askit_tree t, int32_t reps, void *stream, askit_tune
     }
     if (!t->dw.ready) { askit_set_error("set weights before autotuning"); return ASKIT_ERR_NOT_READY; }
     cudaStream_t s = (cudaStream_t)stream;
-    struct Cand { int sched, stages, runs; double ms; };
+    struct Cand { int sched, stages, runs, pairs; double ms; };
     std::vector<Cand> cand;
     const bool tc = t->precision != ASKIT_PREC_SIMT_FP32;
     const bool fp16 = t->precision == ASKIT_PREC_FP16X3 && t->d <= TC_K;
     for (int sc = 0; sc < (tc ? 2 : 1); ++sc)
         for (int st = (fp16 ? 2 : t->tune_stages); st <= (fp16 ? 3 : t->tune_stages); ++st)
             for (int ru = (fp16 ? 0 : t->tune_runs); ru <= (fp16 ? 1 : t->tune_runs); ++ru)
-                cand.push_back({sc, st, ru, 0.0});
+                cand.push_back({sc, st, ru, 0, 0.0});
+    // paired 256-column items (FP16x3, r <= 4): their own schedule, two stages
+    if (fp16 && t->dw.r <= 4 && t->wl.n_pairs > 0)
+        for (int ru = 0; ru <= 1; ++ru) cand.push_back({2, 2, ru, 1, 0.0});
     float *U = nullptr;
     ASK_CUDA(cudaMallocAsync(&U, sizeof(float) * (size_t)t->N * std::max(1, t->dw.r), s));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -577,11 +599,12 @@ askit_status askit_autotune(askit_tree t, int32_t reps, void *stream, askit_tune
         rc = ASKIT_ERR_CUDA;
     }
     auto apply = [&](const Cand &c) {
-        t->tune_sched = c.sched;
+        t->tune_sched = c.pairs ? 0 : c.sched;
         t->tune_stages = c.stages;
         t->tune_runs = c.runs;
-        t->wl.cta_off = t->wl.sched_off[c.sched & 1];
-        t->wl.cta_blocks = t->wl.sched_blocks[c.sched & 1];
+        t->tune_pairs = c.pairs;
+        t->wl.cta_off = t->wl.sched_off[t->tune_sched & 1];
+        t->wl.cta_blocks = t->wl.sched_blocks[t->tune_sched & 1];
     };
     for (size_t k = 0; k < cand.size() && rc == ASKIT_OK; ++k) {
         apply(cand[k]);
@@ -607,7 +630,7 @@ askit_status askit_autotune(askit_tree t, int32_t reps, void *stream, askit_tune
     if (rc != ASKIT_OK) return rc;
     *n_out = (int32_t)std::min<size_t>(cand.size(), (size_t)std::max(0, max_out));
     for (int32_t k = 0; k < *n_out; ++k)
-        out[k] = {cand[k].sched, cand[k].stages, cand[k].runs, (int32_t)((size_t)k == best), cand[k].ms};
+        out[k] = {cand[k].sched, cand[k].stages, cand[k].runs, cand[k].pairs, (int32_t)((size_t)k == best), cand[k].ms};
     return ASKIT_OK;
 }
 

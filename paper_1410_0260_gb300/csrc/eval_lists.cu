@@ -268,24 +268,29 @@ askit_status build_eval_operands(askit_tree t, cudaStream_t s) {
     return ASKIT_OK;
 }
 
-// One CTA per source sub-block: its center (FP64 mean of the valid rows,
-// rounded), the centered rows split for the tensor cores -- TF32 (narrow
+// One CTA per source sub-block: its center (FP64 mean of the rows of the
+// sub-block's node, rounded), the centered rows split for the tensor cores -- TF32 (narrow
 // rows only): hi = the FP32 value with the 13 low mantissa bits cleared,
 // lo = x - hi; BF16: hi = bf16(x), lo = bf16(x - hi); FP16 likewise on the
 // prescaled value -- and the squared norms of the centered rows.  Rows are
 // kw wide (zeros past d); one warp per row, lanes across the columns.
 __global__ void tc_prep_kernel(const float *X, int d_pad, int kw, const int64_t *sb_row0, const int32_t *sb_nrows,
-                               int64_t rows_total, float f16_scale, float *cent, float *Xhi, float *Xlo,
-                               uint16_t *Bhi, uint16_t *Blo, uint16_t *Hhi, uint16_t *Hlo, float *nrmc) {
+                               const int64_t *nd_row0, const int32_t *nd_nrows, int64_t rows_total, float f16_scale,
+                               float *cent, float *Xhi, float *Xlo, uint16_t *Bhi, uint16_t *Blo, uint16_t *Hhi,
+                               uint16_t *Hlo, float *nrmc) {
     extern __shared__ float c[];   // [kw]
     const int g = blockIdx.x;
     const int64_t r0 = sb_row0[g];
     const int nr = sb_nrows[g];
+    // the center is the mean of the whole node (leaf or skeleton) the
+    // sub-block belongs to, so that all sub-blocks of a node share it
+    const int64_t n0 = nd_row0[g];
+    const int nn = nd_nrows[g];
     for (int k = threadIdx.x; k < kw; k += blockDim.x) {
         double acc = 0.0;
         if (k < d_pad)
-            for (int q = 0; q < nr; ++q) acc += (double)X[(r0 + q) * d_pad + k];
-        c[k] = nr > 0 ? (float)(acc / nr) : 0.f;
+            for (int q = 0; q < nn; ++q) acc += (double)X[(n0 + q) * d_pad + k];
+        c[k] = nn > 0 ? (float)(acc / nn) : 0.f;
         cent[(int64_t)g * kw + k] = c[k];
     }
     __syncthreads();
@@ -333,12 +338,18 @@ askit_status build_tc_operands(askit_tree t, cudaStream_t s) {
     std::vector<int32_t> lcb(M), ncb(nn, 0);
     std::vector<int64_t> r0;
     std::vector<int32_t> nr;
+    std::vector<int64_t> node_r0;    // per sub-block: first row and rows of its node
+    std::vector<int32_t> node_nr;    //   (every sub-block of a node shares the node's center)
+    std::vector<int64_t> sub_node;   // per sub-block: heap index of its node
     for (int64_t l = 0; l < M; ++l) {
         lcb[l] = (int32_t)r0.size();
         int64_t a = M + l, sz = t->h_size[a];
         for (int64_t ch = 0; ch * ASK_BLK_N < sz; ++ch) {
             r0.push_back(t->h_start[a] + ch * ASK_BLK_N);
             nr.push_back((int32_t)std::min<int64_t>(ASK_BLK_N, sz - ch * ASK_BLK_N));
+            node_r0.push_back(t->h_start[a]);
+            node_nr.push_back((int32_t)sz);
+            sub_node.push_back(a);
         }
     }
     int64_t n_leaf_sub = (int64_t)r0.size();
@@ -348,12 +359,16 @@ askit_status build_tc_operands(askit_tree t, cudaStream_t s) {
         for (int64_t ch = 0; ch * ASK_BLK_N < sz; ++ch) {
             r0.push_back(t->h_spool[a] + ch * ASK_BLK_N);
             nr.push_back((int32_t)std::min<int64_t>(ASK_BLK_N, sz - ch * ASK_BLK_N));
+            node_r0.push_back(t->h_spool[a]);
+            node_nr.push_back((int32_t)sz);
+            sub_node.push_back(a);
         }
     }
     for (int64_t a = 2; a < nn; ++a) ncb[a] += (int32_t)n_leaf_sub;
     t->n_sub = (int64_t)r0.size();
     // schedule order of the sub-blocks: the tree position of their node's
     // first point (leaf sub-blocks: their own first row), then their index
+    t->h_sub_node = sub_node;
     t->h_sub_pos.assign(t->n_sub, 0);
     for (int64_t q = 0; q < n_leaf_sub; ++q) t->h_sub_pos[q] = r0[q];
     for (int64_t a = 2; a < nn; ++a)
@@ -376,6 +391,12 @@ askit_status build_tc_operands(askit_tree t, cudaStream_t s) {
     t->n_leaf_sub = n_leaf_sub;
     int64_t *d_r0 = t->sb_row0;
     int32_t *d_nr = t->sb_nr;
+    int64_t *d_nd0 = nullptr;
+    int32_t *d_ndn = nullptr;
+    ASK_CUDA(cudaMallocAsync(&d_nd0, sizeof(int64_t) * std::max<int64_t>(1, t->n_sub), s));
+    ASK_CUDA(cudaMallocAsync(&d_ndn, sizeof(int32_t) * std::max<int64_t>(1, t->n_sub), s));
+    ASK_CUDA(cudaMemcpyAsync(d_nd0, node_r0.data(), sizeof(int64_t) * t->n_sub, cudaMemcpyHostToDevice, s));
+    ASK_CUDA(cudaMemcpyAsync(d_ndn, node_nr.data(), sizeof(int32_t) * t->n_sub, cudaMemcpyHostToDevice, s));
     t->srows = std::max<int64_t>(t->spool_rows, 1) + 256;
     const size_t et = (size_t)t->N_pad * kw, es = (size_t)t->srows * kw;
     ASK_TRY(t->arena.alloc(&t->cent, (size_t)std::max<int64_t>(1, t->n_sub) * kw));
@@ -417,14 +438,17 @@ askit_status build_tc_operands(askit_tree t, cudaStream_t s) {
     }
     const size_t csm = sizeof(float) * kw;
     if (n_leaf_sub > 0)
-        tc_prep_kernel<<<(unsigned)n_leaf_sub, 256, csm, s>>>(t->Xt, t->d_pad, kw, d_r0, d_nr, t->N_pad, t->f16_scale,
-                                                            t->cent, t->Xt_hi, t->Xt_lo, t->Xt_bhi, t->Xt_blo,
-                                                            t->Xt_hhi, t->Xt_hlo, t->nrmc_t);
+        tc_prep_kernel<<<(unsigned)n_leaf_sub, 256, csm, s>>>(t->Xt, t->d_pad, kw, d_r0, d_nr, d_nd0, d_ndn, t->N_pad,
+                                                            t->f16_scale, t->cent, t->Xt_hi, t->Xt_lo, t->Xt_bhi,
+                                                            t->Xt_blo, t->Xt_hhi, t->Xt_hlo, t->nrmc_t);
     if (t->n_sub > n_leaf_sub)
         tc_prep_kernel<<<(unsigned)(t->n_sub - n_leaf_sub), 256, csm, s>>>(
-            t->Xs, t->d_pad, kw, d_r0 + n_leaf_sub, d_nr + n_leaf_sub, t->srows, t->f16_scale,
-            t->cent + n_leaf_sub * kw, t->Xs_hi, t->Xs_lo, t->Xs_bhi, t->Xs_blo, t->Xs_hhi, t->Xs_hlo, t->nrmc_s);
+            t->Xs, t->d_pad, kw, d_r0 + n_leaf_sub, d_nr + n_leaf_sub, d_nd0 + n_leaf_sub, d_ndn + n_leaf_sub,
+            t->srows, t->f16_scale, t->cent + n_leaf_sub * kw, t->Xs_hi, t->Xs_lo, t->Xs_bhi, t->Xs_blo, t->Xs_hhi,
+            t->Xs_hlo, t->nrmc_s);
     ASK_LAUNCH();
+    cudaFreeAsync(d_nd0, s);
+    cudaFreeAsync(d_ndn, s);
     ASK_CUDA(cudaStreamSynchronize(s));
     return ASKIT_OK;
 }
@@ -563,7 +587,7 @@ askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, int
         WCHK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         const int nc = (int)std::max<int64_t>(1, std::min<int64_t>(nb, sms));
         auto bcost = [&](int32_t b) { return (int64_t)(boff[b + 1] - boff[b]) * 4 + 3; };
-        std::vector<int32_t> coff[2], cblk[2];
+        std::vector<int32_t> coff[3], cblk[3];
         {
             std::vector<std::vector<int32_t>> lists(nc);
             std::vector<std::pair<int64_t, int>> heap;   // (load, cta), min-heap
@@ -610,13 +634,77 @@ askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, int
             }
             for (int k = 0; k < nc; ++k) coff[1][k + 1] += coff[1][k];
         }
+        // Pairs: sub-blocks 2k and 2k+1 of one node need the same targets (a
+        // target needing a node needs all its sub-blocks), so their items
+        // match one to one; the FP16x3 kernel can take both in one 256-column
+        // item.  The leader keeps its items, the follower's are skipped.
+        std::vector<int32_t> partner(nb, -1);
+        std::vector<char> follower(nb, 0);
+        if (!t->h_sub_node.empty()) {
+            std::vector<int32_t> blk_of_sub(t->h_sub_node.size(), -1);
+            for (int64_t b = 0; b < nb; ++b) {
+                const int32_t cx = hi[boff[b]].cidx;
+                if (cx >= 0 && cx < (int32_t)blk_of_sub.size()) blk_of_sub[cx] = (int32_t)b;
+            }
+            for (int64_t b = 0; b < nb; ++b) {
+                const int32_t cx = hi[boff[b]].cidx;
+                if (cx < 0 || cx + 1 >= (int32_t)t->h_sub_node.size()) continue;
+                const int64_t node = t->h_sub_node[cx];
+                if (t->h_sub_node[cx + 1] != node) continue;
+                int32_t first = cx;
+                while (first > 0 && t->h_sub_node[first - 1] == node) --first;
+                if ((cx - first) & 1) continue;           // odd position in its node
+                const int32_t b2 = blk_of_sub[cx + 1];
+                if (b2 < 0 || boff[b2 + 1] - boff[b2] != boff[b + 1] - boff[b]) continue;
+                // a leader is never the last sub-block of its node, so it is
+                // full and its follower's rows start 128 rows later
+                bool same = (hi[boff[b]].nrows & 0x7fffffff) == ASK_BLK_N;
+                for (int32_t k = 0; same && k < boff[b + 1] - boff[b]; ++k)
+                    same = hi[boff[b] + k].cnt == hi[boff[b2] + k].cnt;
+                if (!same) continue;
+                partner[b] = b2;
+                follower[b2] = 1;
+            }
+        }
+        {
+            std::vector<std::vector<int32_t>> lists(nc);
+            std::vector<std::pair<int64_t, int>> heap;
+            for (int c = 0; c < nc; ++c) heap.push_back({0, c});
+            auto cmp = [](const std::pair<int64_t, int> &x, const std::pair<int64_t, int> &y) {
+                return x.first > y.first || (x.first == y.first && x.second > y.second);
+            };
+            std::make_heap(heap.begin(), heap.end(), cmp);
+            int64_t np = 0;
+            for (int64_t q = 0; q < nb; ++q) {
+                const int32_t bq = order[q];
+                if (follower[bq]) continue;
+                np += partner[bq] >= 0;
+                std::pop_heap(heap.begin(), heap.end(), cmp);
+                auto top = heap.back();
+                heap.pop_back();
+                lists[top.second].push_back(bq);
+                top.first += bcost(bq) * (partner[bq] >= 0 ? 2 : 1);
+                heap.push_back(top);
+                std::push_heap(heap.begin(), heap.end(), cmp);
+            }
+            coff[2].assign(nc + 1, 0);
+            for (int c = 0; c < nc; ++c) {
+                coff[2][c + 1] = coff[2][c] + (int32_t)lists[c].size();
+                cblk[2].insert(cblk[2].end(), lists[c].begin(), lists[c].end());
+            }
+            w.n_pairs = np;
+        }
         w.n_ctas = nc;
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < 3; ++k) {
             WTRY(arena.alloc(&w.sched_off[k], nc + 1));
             WTRY(arena.alloc(&w.sched_blocks[k], std::max<int64_t>(1, nb)));
             WCHK(cudaMemcpyAsync(w.sched_off[k], coff[k].data(), sizeof(int32_t) * (nc + 1), cudaMemcpyHostToDevice, s));
-            WCHK(cudaMemcpyAsync(w.sched_blocks[k], cblk[k].data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
+            WCHK(cudaMemcpyAsync(w.sched_blocks[k], cblk[k].data(), sizeof(int32_t) * cblk[k].size(),
+                                 cudaMemcpyHostToDevice, s));
+            w.n_ctas_sched[k] = nc;
         }
+        WTRY(arena.alloc(&w.partner, std::max<int64_t>(1, nb)));
+        WCHK(cudaMemcpyAsync(w.partner, partner.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
         w.cta_off = w.sched_off[t->tune_sched & 1];
         w.cta_blocks = w.sched_blocks[t->tune_sched & 1];
         WCHK(cudaStreamSynchronize(s));

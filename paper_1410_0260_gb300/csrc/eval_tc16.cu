@@ -52,24 +52,26 @@ constexpr int T16_ROWS = 128;
 constexpr int T16_REGION = T16_ROWS * 128;     // 128 rows x 128 bytes (64 16-bit elements), swizzled
 constexpr uint32_t T16_TMEM_COLS = 512;        // four 128-column FP32 accumulators
 
-// NRAW: stages of gathered target rows (2 or 3, chosen by askit_autotune)
-template <int RC, int NRAW>
+// NRAW: stages of gathered target rows (2 or 3); NB: sub-blocks per item
+// (1, or 2 for the paired 256-column items of one node); NACC = 4 / NB
+// TMEM accumulators of 128 NB columns.  Chosen by askit_autotune.
+template <int RC, int NRAW, int NB>
 struct S16 {
-    static constexpr int B_HI = 0, B_LO = T16_REGION;
-    static constexpr int A0 = 2 * T16_REGION;                 // stage s: hi at A0 + 2s REGION, lo + REGION
+    static constexpr int NACC = 4 / NB;
+    static constexpr int B_HI = 0, B_LO = NB * T16_REGION;    // NB x 128 rows each, contiguous
+    static constexpr int A0 = 2 * NB * T16_REGION;            // stage s: hi at A0 + 2s REGION, lo + REGION
     static constexpr int RAW = A0 + 4 * T16_REGION;           // [NRAW] stages of 128 rows x d_pad floats
     static constexpr int RAWSTAGE = T16_ROWS * TC_K * 4;
-    static constexpr int BLK = RAW + NRAW * RAWSTAGE;         // [2] per-sub-block slots
+    static constexpr int BLK = RAW + NRAW * RAWSTAGE;         // [2] per-item-block slots
     static constexpr int BLK_CENT = 0;                        // float [64] c_B
-    static constexpr int BLK_COLV = 256;                      // float4 [128] pair-interleaved column data
-    static constexpr int BLK_COLW = BLK_COLV + 128 * 16;      // float [128][RC] weights (RC > 1)
-    static constexpr int COLW_BYTES = RC > 1 ? 128 * RC * 4 : 0;
+    static constexpr int BLK_COLV = 256;                      // float4 [128 NB] pair-interleaved column data
+    static constexpr int BLK_COLW = BLK_COLV + NB * 128 * 16; // float [128 NB][RC] weights (RC > 1)
+    static constexpr int COLW_BYTES = RC > 1 ? NB * 128 * RC * 4 : 0;
     static constexpr int BLKSLOT = BLK_COLW + COLW_BYTES;
-    static constexpr int ANORM = BLK + 2 * BLKSLOT;           // float [4][128] |a|^2
+    static constexpr int ANORM = BLK + 2 * BLKSLOT;           // float [NACC][128] |a|^2
     static constexpr int BAR = ANORM + 4 * 128 * 4;           // 24 mbarriers
     static constexpr int MISC = BAR + 24 * 8;                 // tmem address, abort flag
     static constexpr int BYTES = MISC + 16;
-    static constexpr uint32_t BLK_TX = 256 + 128 * 16 + COLW_BYTES;
 };
 
 struct T16Args {
@@ -84,18 +86,20 @@ struct T16Args {
     int r;
     float f16_scale;
     int runs;                 // 8-row tiled loads for runs of consecutive target rows
+    const int32_t *partner;   // [n_blocks] paired follower block, or -1 (NB == 2)
     float *partial;
     int *status;
 };
 
-template <int P, int RC, int NRAW>
+template <int P, int RC, int NRAW, int NB>
 __global__ void __launch_bounds__(T16_THREADS, 1)
 eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_constant__ CUtensorMap map_t_lo,
                  const __grid_constant__ CUtensorMap map_s_hi, const __grid_constant__ CUtensorMap map_s_lo,
                  const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_q8,
                  const T16Args args) {
-    using S = S16<RC, NRAW>;
-    constexpr uint32_t IDESC = make_idesc(P == ASKIT_PREC_BF16X3 ? 1u : 0u, T16_ROWS, T16_ROWS);
+    using S = S16<RC, NRAW, NB>;
+    constexpr int NACC = S::NACC;
+    constexpr uint32_t FMT = P == ASKIT_PREC_BF16X3 ? 1u : 0u;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(sm);
@@ -127,7 +131,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
         }
         mbar_init(BAR_B_FULL, 1);
         mbar_init(BAR_B_EMPTY, 1);
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < NACC; ++a) {
             mbar_init(BAR_T_FULL(a), 1);
             mbar_init(BAR_T_EMPTY(a), 128);
         }
@@ -163,9 +167,9 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                 const int cnt = cnt_next;
                 if (it + 2 < i1) cnt_next = args.items[it + 2].cnt;   // in flight while this item waits
                 const bool has_tgt = t < cnt;
-                const int sa = li & 1, sr = li % NRAW, a4 = li & 3;
+                const int sa = li & 1, sr = li % NRAW, a4 = li % NACC;
                 if (!mbar_wait(BAR_A_EMPTY(sa), ((li >> 1) & 1) ^ 1, abort_flag, args.status)) goto loader_done;
-                if (!mbar_wait(BAR_T_EMPTY(a4), ((li >> 2) & 1) ^ 1, abort_flag, args.status)) goto loader_done;
+                if (!mbar_wait(BAR_T_EMPTY(a4), ((li / NACC) & 1) ^ 1, abort_flag, args.status)) goto loader_done;
                 if (!mbar_wait(BAR_R_FULL(sr), (li / NRAW) & 1, abort_flag, args.status)) goto loader_done;
                 if (need_blk) {
                     if (!mbar_wait(BAR_BLK_FULL(lb & 1), (lb >> 1) & 1, abort_flag, args.status)) goto loader_done;
@@ -232,21 +236,26 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
             if (!mbar_wait(BAR_BLK_FULL(bs), (lb >> 1) & 1, abort_flag, args.status)) goto epi_done;
             const float4 *cv4 = reinterpret_cast<const float4 *>(sm + S::BLK + bs * S::BLKSLOT + S::BLK_COLV);
             const float *cwp = reinterpret_cast<const float *>(sm + S::BLK + bs * S::BLKSLOT + S::BLK_COLW);
-            const int i1 = args.block_off[b + 1];
-            EvalItem nxt = args.items[args.block_off[b]];
-            for (int it = args.block_off[b]; it < i1; ++it, ++li) {
-                const int a4 = li & 3;
+            const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
+            // a paired follower's columns follow the leader's 128
+            const int pb = NB == 2 ? args.partner[b] : -1;
+            const int f0 = pb >= 0 ? args.block_off[pb] : 0;
+            const int ncols_f = pb >= 0 ? (args.items[f0].nrows & 0x7fffffff) : 0;
+            EvalItem nxt = args.items[i0];
+            for (int it = i0; it < i1; ++it, ++li) {
+                const int a4 = li % NACC;
                 const EvalItem item = nxt;
                 if (it + 1 < i1) nxt = args.items[it + 1];   // in flight while this item waits
-                const int nrows = item.nrows & 0x7fffffff;
-                if (!mbar_wait(BAR_T_FULL(a4), (li >> 2) & 1, abort_flag, args.status)) goto epi_done;
+                const int nrows = (item.nrows & 0x7fffffff) + ncols_f;
+                const int e0f = pb >= 0 ? args.items[f0 + (it - i0)].e0 : 0;
+                if (!mbar_wait(BAR_T_FULL(a4), (li / NACC) & 1, abort_flag, args.status)) goto epi_done;
                 tc_fence_after();
                 float acc[RC];
 #pragma unroll
                 for (int z = 0; z < RC; ++z) acc[z] = 0.f;
                 float2 acc2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};   // RC == 1
                 if (q * 32 < item.cnt) {   // warp-uniform: skip quadrants with no target
-                    const float pt = a_norm[a4 * 128 + row];
+                    const float pt = a_norm[a4 * 128 + row];   // NACC <= 4 slots
                     const float2 pt2 = make_float2(pt, pt);
                     // arg = g A + (C p + B) = -sc (p + q - 2 g / scale^2); columns past
                     // nrows carry A = B = C = w = 0
@@ -276,19 +285,23 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                             }
                         }
                     };
-                    const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a4 * 128);
+                    const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a4 * 128 * NB);
+                    // 32-column chunks; the TMEM load of chunk c + 1 is in flight
+                    // while chunk c is computed (two register buffers)
+                    const int nch = (nrows + 31) >> 5;
+                    uint32_t ga[32], gb[32];
+                    tmem_ld32_async(tbase, ga);
+                    tmem_wait_pin(ga);
 #pragma unroll 1
-                    for (int c = 0; c < 4 && c * 32 < nrows; c += 2) {
-                        // two 32-column loads per wait
-                        uint32_t g0[32], g1[32];
-                        const bool two = (c + 1) * 32 < nrows;      // warp-uniform
-                        tmem_ld32_async(tbase + (uint32_t)(c * 32), g0);
-                        if (two) tmem_ld32_async(tbase + (uint32_t)((c + 1) * 32), g1);
-                        tmem_wait_pin(g0);
-                        cols(c, g0);
-                        if (two) {
-                            reg_pin(g1);
-                            cols(c + 1, g1);
+                    for (int c = 0; c < nch; c += 2) {
+                        const bool h1 = c + 1 < nch, h2 = c + 2 < nch;   // warp-uniform
+                        if (h1) tmem_ld32_async(tbase + (uint32_t)((c + 1) * 32), gb);
+                        cols(c, ga);
+                        if (h1) {
+                            tmem_wait_pin(gb);
+                            if (h2) tmem_ld32_async(tbase + (uint32_t)((c + 2) * 32), ga);
+                            cols(c + 1, gb);
+                            if (h2) tmem_wait_pin(ga);
                         }
                     }
                     if constexpr (RC == 1) acc[0] = (acc2[0].x + acc2[0].y) + (acc2[1].x + acc2[1].y);
@@ -300,6 +313,12 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
 #pragma unroll
                     for (int z = 0; z < RC; ++z)
                         if (z < args.r) p[z] = acc[z];
+                    if (pb >= 0) {   // the follower's entry: its share is in the leader's sum
+                        float *pf = args.partial + (int64_t)(e0f + row) * args.r;
+#pragma unroll
+                        for (int z = 0; z < RC; ++z)
+                            if (z < args.r) pf[z] = 0.f;
+                    }
                 }
             }
             mbar_arrive(BAR_BLK_EMPTY(bs));
@@ -375,25 +394,36 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
             const EvalItem first = args.items[i0];
             const bool far = first.nrows < 0;
             const int bs = lb & 1;
+            // a paired follower (NB == 2) is the next sub-block of the same
+            // node: its rows, column data and weights follow the leader's
+            const int pb = NB == 2 ? args.partner[b] : -1;
+            const int nsb = pb >= 0 ? 2 : 1;
+            const int ncols = (first.nrows & 0x7fffffff) + (pb >= 0 ? (args.items[args.block_off[pb]].nrows & 0x7fffffff) : 0);
+            const uint32_t idesc = make_idesc(FMT, T16_ROWS, (ncols + 15) & ~15);
             if (!mbar_wait(BAR_B_EMPTY, (lb & 1) ^ 1, abort_flag, args.status)) goto mma_done;
             if (!mbar_wait(BAR_BLK_EMPTY(bs), ((lb >> 1) & 1) ^ 1, abort_flag, args.status)) goto mma_done;
             b_issued = lb + 1;
-            mbar_expect_tx(BAR_B_FULL, 2 * T16_REGION);
-            tma_load_2d(sbase + S::B_HI, far ? &map_s_hi : &map_t_hi, 0, first.row0, BAR_B_FULL);
-            tma_load_2d(sbase + S::B_LO, far ? &map_s_lo : &map_t_lo, 0, first.row0, BAR_B_FULL);
+            mbar_expect_tx(BAR_B_FULL, (uint32_t)(2 * nsb * T16_REGION));
+            for (int h = 0; h < nsb; ++h) {
+                tma_load_2d(sbase + S::B_HI + h * T16_REGION, far ? &map_s_hi : &map_t_hi, 0, first.row0 + 128 * h,
+                            BAR_B_FULL);
+                tma_load_2d(sbase + S::B_LO + h * T16_REGION, far ? &map_s_lo : &map_t_lo, 0, first.row0 + 128 * h,
+                            BAR_B_FULL);
+            }
             const uint32_t slot = sbase + S::BLK + bs * S::BLKSLOT;
-            mbar_expect_tx(BAR_BLK_FULL(bs), S::BLK_TX);
+            const uint32_t colw_bytes = RC > 1 ? (uint32_t)(nsb * 128 * RC * 4) : 0u;
+            mbar_expect_tx(BAR_BLK_FULL(bs), (uint32_t)(256 + nsb * 128 * 16) + colw_bytes);
             bulk_copy(slot + S::BLK_CENT, args.cent + (int64_t)first.cidx * TC_K, TC_K * 4, BAR_BLK_FULL(bs));
-            bulk_copy(slot + S::BLK_COLV, args.colv + (int64_t)first.cidx * 128, 128 * 16, BAR_BLK_FULL(bs));
+            bulk_copy(slot + S::BLK_COLV, args.colv + (int64_t)first.cidx * 128, nsb * 128 * 16, BAR_BLK_FULL(bs));
             if constexpr (RC > 1)
-                bulk_copy(slot + S::BLK_COLW, args.colw + (int64_t)first.cidx * 128 * RC, S::COLW_BYTES, BAR_BLK_FULL(bs));
+                bulk_copy(slot + S::BLK_COLW, args.colw + (int64_t)first.cidx * 128 * RC, colw_bytes, BAR_BLK_FULL(bs));
             for (int it = i0; it < i1; ++it, ++li) {
-                const int sa = li & 1, a4 = li & 3;
+                const int sa = li & 1, a4 = li % NACC;
                 if (!mbar_wait(BAR_A_FULL(sa), (li >> 1) & 1, abort_flag, args.status)) goto mma_done;
                 if (it == i0 && !mbar_wait(BAR_B_FULL, lb & 1, abort_flag, args.status)) goto mma_done;
-                if (!mbar_wait(BAR_T_EMPTY(a4), ((li >> 2) & 1) ^ 1, abort_flag, args.status)) goto mma_done;
+                if (!mbar_wait(BAR_T_EMPTY(a4), ((li / NACC) & 1) ^ 1, abort_flag, args.status)) goto mma_done;
                 tc_fence_after();
-                const uint32_t d_tmem = tmem + (uint32_t)(a4 * 128);
+                const uint32_t d_tmem = tmem + (uint32_t)(a4 * 128 * NB);
                 const uint32_t a_hi = sbase + S::A0 + sa * 2 * T16_REGION, a_lo = a_hi + T16_REGION;
                 const uint32_t b_hi = sbase + S::B_HI, b_lo = sbase + S::B_LO;
                 // the tensor core rounds each accumulation step to the running sum's
@@ -401,13 +431,13 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {   // K = 16 per MMA: 32 bytes into the 128-byte rows
                     const uint32_t off = (uint32_t)(k * 32);
-                    tc_mma<P>(d_tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), IDESC, k > 0);
-                    tc_mma<P>(d_tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), IDESC, 1);
+                    tc_mma<P>(d_tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, k > 0);
+                    tc_mma<P>(d_tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1);
                 }
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const uint32_t off = (uint32_t)(k * 32);
-                    tc_mma<P>(d_tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), IDESC, 1);
+                    tc_mma<P>(d_tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, 1);
                 }
                 tc_commit(BAR_A_EMPTY(sa));
                 tc_commit(BAR_T_FULL(a4));
@@ -487,24 +517,24 @@ askit_status t16_state(askit_tree t, int pi, T16State **out) {
     return ASKIT_OK;
 }
 
-template <int P, int RC, int NRAW>
+template <int P, int RC, int NRAW, int NB>
 askit_status launch16(T16State *st, int pi, const CUtensorMap &map_q, const CUtensorMap &map_q8, const T16Args &a,
                       int grid, cudaStream_t s) {
-    using S = S16<RC, NRAW>;
+    using S = S16<RC, NRAW, NB>;
     const size_t smem = S::BYTES + 1024;
-    static const cudaError_t attr =
-        cudaFuncSetAttribute(eval_tc16_kernel<P, RC, NRAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static_assert(S::BYTES + 1024 <= 232448, "shared-memory plan exceeds 227 KB");
+    static const cudaError_t attr = cudaFuncSetAttribute(eval_tc16_kernel<P, RC, NRAW, NB>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     ASK_CUDA(attr);
-    eval_tc16_kernel<P, RC, NRAW><<<(unsigned)grid, T16_THREADS, smem, s>>>(st->map[pi][0], st->map[pi][1],
-                                                                     st->map[pi][2], st->map[pi][3], map_q, map_q8, a);
+    eval_tc16_kernel<P, RC, NRAW, NB><<<(unsigned)grid, T16_THREADS, smem, s>>>(
+        st->map[pi][0], st->map[pi][1], st->map[pi][2], st->map[pi][3], map_q, map_q8, a);
     ASK_LAUNCH();
     return ASKIT_OK;
 }
 
 template <int P, int RC>
 askit_status run16(askit_tree t, const WeightCtx &c, T16State *st, int pi, const CUtensorMap &map_q,
-                   const CUtensorMap &map_q8, T16Args a,
-                   const WorkLists &w, cudaStream_t s) {
+                   const CUtensorMap &map_q8, T16Args a, const WorkLists &w, cudaStream_t s) {
     const float g_unscale = 1.f / (a.f16_scale * a.f16_scale);
     tc16_cols_kernel<RC><<<(unsigned)t->n_sub, 128, 0, s>>>(t->sb_row0, t->sb_nr, t->n_leaf_sub, t->sc_t, t->sc_s,
                                                             t->nrmc_t, t->nrmc_s, c.Wt, c.Ws, c.r, g_unscale, c.colv,
@@ -512,8 +542,17 @@ askit_status run16(askit_tree t, const WeightCtx &c, T16State *st, int pi, const
     ASK_LAUNCH();
     a.colv = c.colv;
     a.colw = c.colw;
-    if (t->tune_stages == 2) return launch16<P, RC, 2>(st, pi, map_q, map_q8, a, w.n_ctas, s);
-    return launch16<P, RC, 3>(st, pi, map_q, map_q8, a, w.n_ctas, s);
+    if constexpr (RC <= 4) {
+        // paired 256-column items: two stages fit next to the 64 KB source tile
+        if (t->tune_pairs && w.sched_off[2]) {
+            a.cta_off = w.sched_off[2];
+            a.cta_blocks = w.sched_blocks[2];
+            a.partner = w.partner;
+            return launch16<P, RC, 2, 2>(st, pi, map_q, map_q8, a, w.n_ctas, s);
+        }
+    }
+    if (t->tune_stages == 2) return launch16<P, RC, 2, 1>(st, pi, map_q, map_q8, a, w.n_ctas, s);
+    return launch16<P, RC, 3, 1>(st, pi, map_q, map_q8, a, w.n_ctas, s);
 }
 
 template <int P>
@@ -559,6 +598,7 @@ askit_status eval_tc16(askit_tree t, const WeightCtx &c, int precision, const fl
     a.r = c.r;
     a.f16_scale = precision == ASKIT_PREC_FP16X3 ? t->f16_scale : 1.f;
     a.runs = t->tune_runs;
+    a.partner = nullptr;
     a.partial = partial;
     a.status = t->d_status;
     if (precision != ASKIT_PREC_FP16X3) {
