@@ -86,12 +86,16 @@ struct T16Args {
     int r;
     float f16_scale;
     int runs;                 // 8-row tiled loads for runs of consecutive target rows
+    float uni_a, uni_c;       // UNI: A = 2 sc / scale^2 and C = -sc
     const int32_t *partner;   // [n_blocks] paired follower block, or -1 (NB == 2)
     float *partial;
     int *status;
 };
 
-template <int P, int RC, int NRAW, int NB>
+// UNI: one bandwidth for all sources (c log2(e) / h^2 = sc for every j): the
+// column data is then {B_j, B_j+1, w_j, w_j+1} per pair (8 bytes a column),
+// half of the general layout, and A = 2 sc / scale^2, C = -sc are scalars.
+template <int P, int RC, int NRAW, int NB, int UNI>
 __global__ void __launch_bounds__(T16_THREADS, 1)
 eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_constant__ CUtensorMap map_t_lo,
                  const __grid_constant__ CUtensorMap map_s_hi, const __grid_constant__ CUtensorMap map_s_lo,
@@ -99,6 +103,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                  const T16Args args) {
     using S = S16<RC, NRAW, NB>;
     constexpr int NACC = S::NACC;
+    static_assert(!UNI || RC == 1, "the uniform-bandwidth layout serves r = 1");
     constexpr uint32_t FMT = P == ASKIT_PREC_BF16X3 ? 1u : 0u;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -260,7 +265,19 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                     // arg = g A + (C p + B) = -sc (p + q - 2 g / scale^2); columns past
                     // nrows carry A = B = C = w = 0
                     auto cols = [&](int c, const uint32_t (&gr)[32]) {
-                        if constexpr (RC == 1) {
+                        if constexpr (RC == 1 && UNI) {
+                            const float2 a2 = make_float2(args.uni_a, args.uni_a);
+                            const float2 c2 = make_float2(args.uni_c, args.uni_c);
+#pragma unroll
+                            for (int jj = 0; jj < 32; jj += 2) {
+                                const float4 bw = cv4[(c * 32 + jj) >> 1];   // {B_j, B_j+1, w_j, w_j+1}
+                                const float2 inner = __ffma2_rn(c2, pt2, make_float2(bw.x, bw.y));
+                                const float2 arg = __ffma2_rn(make_float2(__uint_as_float(gr[jj]), __uint_as_float(gr[jj + 1])),
+                                                              a2, inner);
+                                const float2 k = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+                                acc2[(jj >> 1) & 1] = __ffma2_rn(k, make_float2(bw.z, bw.w), acc2[(jj >> 1) & 1]);
+                            }
+                        } else if constexpr (RC == 1) {
 #pragma unroll
                             for (int jj = 0; jj < 32; jj += 2) {
                                 const float4 ab = cv4[c * 32 + jj];
@@ -399,7 +416,9 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
             const int pb = NB == 2 ? args.partner[b] : -1;
             const int nsb = pb >= 0 ? 2 : 1;
             const int ncols = (first.nrows & 0x7fffffff) + (pb >= 0 ? (args.items[args.block_off[pb]].nrows & 0x7fffffff) : 0);
-            const uint32_t idesc = make_idesc(FMT, T16_ROWS, (ncols + 15) & ~15);
+            // N covers every 32-column chunk the epilogue reads, so no column it
+            // reads holds a stale accumulator
+            const uint32_t idesc = make_idesc(FMT, T16_ROWS, (ncols + 31) & ~31);
             if (!mbar_wait(BAR_B_EMPTY, (lb & 1) ^ 1, abort_flag, args.status)) goto mma_done;
             if (!mbar_wait(BAR_BLK_EMPTY(bs), ((lb >> 1) & 1) ^ 1, abort_flag, args.status)) goto mma_done;
             b_issued = lb + 1;
@@ -412,9 +431,10 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
             }
             const uint32_t slot = sbase + S::BLK + bs * S::BLKSLOT;
             const uint32_t colw_bytes = RC > 1 ? (uint32_t)(nsb * 128 * RC * 4) : 0u;
-            mbar_expect_tx(BAR_BLK_FULL(bs), (uint32_t)(256 + nsb * 128 * 16) + colw_bytes);
+            constexpr int CV = UNI ? 64 : 128;   // float4 of column data per sub-block
+            mbar_expect_tx(BAR_BLK_FULL(bs), (uint32_t)(256 + nsb * CV * 16) + colw_bytes);
             bulk_copy(slot + S::BLK_CENT, args.cent + (int64_t)first.cidx * TC_K, TC_K * 4, BAR_BLK_FULL(bs));
-            bulk_copy(slot + S::BLK_COLV, args.colv + (int64_t)first.cidx * 128, nsb * 128 * 16, BAR_BLK_FULL(bs));
+            bulk_copy(slot + S::BLK_COLV, args.colv + (int64_t)first.cidx * CV, nsb * CV * 16, BAR_BLK_FULL(bs));
             if constexpr (RC > 1)
                 bulk_copy(slot + S::BLK_COLW, args.colw + (int64_t)first.cidx * 128 * RC, colw_bytes, BAR_BLK_FULL(bs));
             for (int it = i0; it < i1; ++it, ++li) {
@@ -463,7 +483,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
 // source row t of sub-block b.  colv pairs rows (2p, 2p+1):
 // {A_2p, A_2p+1, B_2p, B_2p+1}, {C_2p, C_2p+1, w_2p, w_2p+1} with
 // A = 2 sc / scale^2, B = -sc |b|^2, C = -sc (zeros past the sub-block's rows).
-template <int RC>
+template <int RC, int UNI>
 __global__ void tc16_cols_kernel(const int64_t *sb_row0, const int32_t *sb_nr, int64_t n_leaf_sub, const float *sc_t,
                                  const float *sc_s, const float *nrm_t, const float *nrm_s, const float *Wt,
                                  const float *Ws, int r, float g_unscale, float4 *colv, float *colw) {
@@ -475,8 +495,14 @@ __global__ void tc16_cols_kernel(const int64_t *sb_row0, const int32_t *sb_nr, i
     const float sc = valid ? (far ? sc_s : sc_t)[row] : 0.f;
     const float nrm = valid ? (far ? nrm_s : nrm_t)[row] : 0.f;
     const float *w = (far ? Ws : Wt) + row * r;
-    float *cp = reinterpret_cast<float *>(colv + b * 128 + 2 * (t >> 1));
     const int o = t & 1;
+    if (UNI) {   // {B_j, B_j+1, w_j, w_j+1}; B = -inf past the rows: exp2 gives 0 there
+        float *cp = reinterpret_cast<float *>(colv + b * 64 + (t >> 1));
+        cp[0 + o] = valid ? -sc * nrm : -INFINITY;
+        cp[2 + o] = valid ? w[0] : 0.f;
+        return;
+    }
+    float *cp = reinterpret_cast<float *>(colv + b * 128 + 2 * (t >> 1));
     cp[0 + o] = 2.f * g_unscale * sc;
     cp[2 + o] = -sc * nrm;
     cp[4 + o] = -sc;
@@ -517,16 +543,16 @@ askit_status t16_state(askit_tree t, int pi, T16State **out) {
     return ASKIT_OK;
 }
 
-template <int P, int RC, int NRAW, int NB>
+template <int P, int RC, int NRAW, int NB, int UNI>
 askit_status launch16(T16State *st, int pi, const CUtensorMap &map_q, const CUtensorMap &map_q8, const T16Args &a,
                       int grid, cudaStream_t s) {
     using S = S16<RC, NRAW, NB>;
     const size_t smem = S::BYTES + 1024;
     static_assert(S::BYTES + 1024 <= 232448, "shared-memory plan exceeds 227 KB");
-    static const cudaError_t attr = cudaFuncSetAttribute(eval_tc16_kernel<P, RC, NRAW, NB>,
+    static const cudaError_t attr = cudaFuncSetAttribute(eval_tc16_kernel<P, RC, NRAW, NB, UNI>,
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     ASK_CUDA(attr);
-    eval_tc16_kernel<P, RC, NRAW, NB><<<(unsigned)grid, T16_THREADS, smem, s>>>(
+    eval_tc16_kernel<P, RC, NRAW, NB, UNI><<<(unsigned)grid, T16_THREADS, smem, s>>>(
         st->map[pi][0], st->map[pi][1], st->map[pi][2], st->map[pi][3], map_q, map_q8, a);
     ASK_LAUNCH();
     return ASKIT_OK;
@@ -536,23 +562,48 @@ template <int P, int RC>
 askit_status run16(askit_tree t, const WeightCtx &c, T16State *st, int pi, const CUtensorMap &map_q,
                    const CUtensorMap &map_q8, T16Args a, const WorkLists &w, cudaStream_t s) {
     const float g_unscale = 1.f / (a.f16_scale * a.f16_scale);
-    tc16_cols_kernel<RC><<<(unsigned)t->n_sub, 128, 0, s>>>(t->sb_row0, t->sb_nr, t->n_leaf_sub, t->sc_t, t->sc_s,
-                                                            t->nrmc_t, t->nrmc_s, c.Wt, c.Ws, c.r, g_unscale, c.colv,
-                                                            c.colw);
+    // one bandwidth for every source: compact column data (r = 1)
+    const bool uni = RC == 1 && t->prm.bw_mode == ASKIT_BW_CONSTANT;
+    if (uni) {
+        // the same rounding as the per-row values (h held in FP32)
+        const double hf = (double)(float)t->prm.h;
+        const float sc = (float)(t->prm.kernel_scale * 1.4426950408889634 / (hf * hf));
+        a.uni_a = 2.f * g_unscale * sc;
+        a.uni_c = -sc;
+        tc16_cols_kernel<RC, 1><<<(unsigned)t->n_sub, 128, 0, s>>>(t->sb_row0, t->sb_nr, t->n_leaf_sub, t->sc_t,
+                                                                   t->sc_s, t->nrmc_t, t->nrmc_s, c.Wt, c.Ws, c.r,
+                                                                   g_unscale, c.colv, c.colw);
+    } else {
+        tc16_cols_kernel<RC, 0><<<(unsigned)t->n_sub, 128, 0, s>>>(t->sb_row0, t->sb_nr, t->n_leaf_sub, t->sc_t,
+                                                                   t->sc_s, t->nrmc_t, t->nrmc_s, c.Wt, c.Ws, c.r,
+                                                                   g_unscale, c.colv, c.colw);
+    }
     ASK_LAUNCH();
     a.colv = c.colv;
     a.colw = c.colw;
+    if constexpr (RC == 1) {
+        if (uni) {
+            if (t->tune_pairs && w.sched_off[2]) {
+                a.cta_off = w.sched_off[2];
+                a.cta_blocks = w.sched_blocks[2];
+                a.partner = w.partner;
+                return launch16<P, RC, 2, 2, 1>(st, pi, map_q, map_q8, a, w.n_ctas, s);
+            }
+            if (t->tune_stages == 2) return launch16<P, RC, 2, 1, 1>(st, pi, map_q, map_q8, a, w.n_ctas, s);
+            return launch16<P, RC, 3, 1, 1>(st, pi, map_q, map_q8, a, w.n_ctas, s);
+        }
+    }
     if constexpr (RC <= 4) {
         // paired 256-column items: two stages fit next to the 64 KB source tile
         if (t->tune_pairs && w.sched_off[2]) {
             a.cta_off = w.sched_off[2];
             a.cta_blocks = w.sched_blocks[2];
             a.partner = w.partner;
-            return launch16<P, RC, 2, 2>(st, pi, map_q, map_q8, a, w.n_ctas, s);
+            return launch16<P, RC, 2, 2, 0>(st, pi, map_q, map_q8, a, w.n_ctas, s);
         }
     }
-    if (t->tune_stages == 2) return launch16<P, RC, 2, 1>(st, pi, map_q, map_q8, a, w.n_ctas, s);
-    return launch16<P, RC, 3, 1>(st, pi, map_q, map_q8, a, w.n_ctas, s);
+    if (t->tune_stages == 2) return launch16<P, RC, 2, 1, 0>(st, pi, map_q, map_q8, a, w.n_ctas, s);
+    return launch16<P, RC, 3, 1, 0>(st, pi, map_q, map_q8, a, w.n_ctas, s);
 }
 
 template <int P>
@@ -599,6 +650,7 @@ askit_status eval_tc16(askit_tree t, const WeightCtx &c, int precision, const fl
     a.f16_scale = precision == ASKIT_PREC_FP16X3 ? t->f16_scale : 1.f;
     a.runs = t->tune_runs;
     a.partner = nullptr;
+    a.uni_a = a.uni_c = 0.f;
     a.partial = partial;
     a.status = t->d_status;
     if (precision != ASKIT_PREC_FP16X3) {
