@@ -73,3 +73,27 @@ def test_autotune_needs_weights():
     with pytest.raises(askit.AskitError):
         t.autotune()
     t.close()
+
+
+def test_wide_kernel_schedules_match_the_oracle():
+    """d = 100 (rows padded to 128: two K chunks of 64, the second partly
+    outside the rows): both schedules, r = 1 and 3, against the oracle."""
+    import oracle
+    from paper_1410_0260_gb300 import askit, workloads
+    X = workloads.mixture(3000, 100, 4, 3.0, seed=31)
+    kw = dict(leaf_size=256, kappa=12, knn_mode=0, s_max=160, id_tol=1e-5, h=5.0, seed=9)
+    ot = oracle.Tree(X, oracle.Config(**kw))
+    gt = askit.Tree(torch.from_numpy(X).cuda(), askit.Config(precision="fp16x3", **kw))
+    for r in (1, 3):
+        W = np.random.default_rng(10 + r).standard_normal((3000, r)).astype(np.float32)
+        ot.set_weights(W.astype(np.float64))
+        Uo = ot.evaluate()
+        gt.set_weights(torch.from_numpy(W).cuda())
+        outs = []
+        for sched in ("lpt", "tree_order"):
+            gt.set_launch(sched, 3, True, False)
+            U = gt.evaluate().cpu().numpy()
+            assert np.linalg.norm(U - Uo) / np.linalg.norm(Uo) <= 1e-4, sched
+            outs.append(U)
+        assert np.array_equal(outs[0], outs[1])
+    gt.close()
