@@ -83,6 +83,23 @@ def askit_config(w, precision):
                         bw_k=w.bw_k, seed=w.seed, precision=precision)
 
 
+def measured_traffic(kernel, workload_name):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu
+    capture (profiles/traffic.json), while the kernel source is the one that
+    was measured; otherwise None."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))).get(kernel)
+        if not rec or rec.get("workload") != workload_name:
+            return None
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+            return None
+        return rec["bytes_per_launch"]
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -397,6 +414,7 @@ def main():
                       "eval_tcw_kernel" if d > 64 else
                       "eval_tc16_kernel" if args.precision == "fp16x3" else "eval_tc_kernel")
     roof["ms_per_launch"] = ms_eval
+    roof["traffic"] = measured_traffic(roof["kernel"], w.name)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
