@@ -148,6 +148,22 @@ askit_status askit_evaluate_host(askit_tree t, const float *W_host, int32_t r, i
                                  float *U_host, int64_t ldu, void *stream);
 
 /*
+ * Exact kNN of new points against the tree's points (the prune set of an
+ * out-of-sample target, Algorithm 4 with N_y in place of N_i): for each row
+ * of Y_dev [T, d] (stride ldy), the kappa (<= 32, the tree's kappa) nearest
+ * points by (squared distance, id), ties by id, distances in canonical FP64
+ * from the FP32 coordinates -- the same lists the exhaustive search gives.
+ *   ids_dev  [T, kappa] int32 point ids (caller order); dist_dev [T, kappa]
+ *   double squared distances.  Blocks until done.
+ * For d <= 64 a tensor-core FP16x3 shortlist (every point within a bound of
+ * each query's k-th distance, with a margin five times the arithmetic's error)
+ * is re-ranked in FP64; queries whose shortlist overflows take the exhaustive
+ * search.
+ */
+askit_status askit_knn_targets(askit_tree t, const float *Y_dev, int64_t T, int64_t ldy, int32_t *ids_dev,
+                               double *dist_dev, void *stream);
+
+/*
  * Direct sum of eq. (1.1) at selected points, without approximation: for
  * each target id, the sum over all N points of K(x_i, x_j) w_j with the
  * tree's points, bandwidths and current weights (plain FP32, difference

@@ -31,7 +31,7 @@ EXPORTS = ["askit_default_params", "askit_setup", "askit_set_weights", "askit_ev
            "askit_last_error", "askit_knn_noalloc", "askit_direct", "askit_weights_create",
            "askit_weights_set", "askit_weights_evaluate", "askit_weights_evaluate_targets",
            "askit_weights_destroy", "askit_footprint", "askit_graph_create", "askit_graph_launch",
-           "askit_graph_destroy", "askit_autotune", "askit_set_launch"]
+           "askit_graph_destroy", "askit_autotune", "askit_set_launch", "askit_knn_targets"]
 
 
 class TuneEntry(C.Structure):
@@ -94,6 +94,7 @@ def load(path: str | None = None):
             L.askit_graph_destroy.argtypes = [V]
             L.askit_autotune.argtypes = [V, I32, V, C.POINTER(TuneEntry), I32, C.POINTER(I32)]
             L.askit_set_launch.argtypes = [V, I32, I32, I32, I32]
+            L.askit_knn_targets.argtypes = [V, V, I64, I64, V, V, V]
             L.askit_status_string.restype = C.c_char_p
             L.askit_status_string.argtypes = [C.c_int]
             L.askit_last_error.restype = C.c_char_p
@@ -229,6 +230,16 @@ class Tree:
         _check(load().askit_evaluate_host(self._t, C.c_void_p(W_ptr), r, r, C.c_void_p(U_ptr), r,
                                           _stream(stream)))
         self.r = r
+
+    def knn_targets(self, Y: torch.Tensor, stream=None) -> tuple[torch.Tensor, torch.Tensor]:
+        """Exact kappa nearest tree points of each row of Y: (ids, squared distances)."""
+        Y = _dev_f32(Y, "Y")
+        kappa = self.info()["kappa"]
+        ids = torch.empty((Y.shape[0], kappa), dtype=torch.int32, device=self.device)
+        dist = torch.empty((Y.shape[0], kappa), dtype=torch.float64, device=self.device)
+        _check(load().askit_knn_targets(self._t, C.c_void_p(Y.data_ptr()), Y.shape[0], Y.stride(0),
+                                        C.c_void_p(ids.data_ptr()), C.c_void_p(dist.data_ptr()), _stream(stream)))
+        return ids, dist
 
     def direct(self, targets, stream=None) -> torch.Tensor:
         """Exact direct sum (eq. 1.1) at the given point ids, with the current weights."""

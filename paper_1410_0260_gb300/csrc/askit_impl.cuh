@@ -376,3 +376,9 @@ void eval_tc_wide_free(askit_tree t);
 askit_status eval_tc16(askit_tree t, const WeightCtx &c, int precision, const float *Xq, int64_t ldq, int64_t q_rows,
                        const WorkLists &w, float *partial, cudaStream_t s);
 void eval_tc16_free(askit_tree t);
+askit_status knn_shortlist_tc16(askit_tree t, const float *Yp, int64_t T, const float *U, int *cnt, int32_t *cand,
+                                int cap, float eta, cudaStream_t s);
+// exact kNN of out-of-sample points Y [T, d] against the tree's points:
+// tensor-core shortlist + canonical FP64 re-rank where the operands exist,
+// else the tiled exhaustive search; ids / dist [T, kappa] as knn_exact_gpu
+askit_status knn_oos(askit_tree t, const float *Y, int64_t T, int kappa, int32_t *ids, double *dist, cudaStream_t s);

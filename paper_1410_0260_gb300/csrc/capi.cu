@@ -373,7 +373,7 @@ askit_status evaluate_targets_ctx(askit_tree t, const WeightCtx &c, const float 
                           cudaMemcpyDeviceToDevice, s) != cudaSuccess) { askit_set_error("copy Y"); rc = ASKIT_ERR_CUDA; goto out; }
     OTRY(tmp.alloc(&ids, (size_t)T * kappa));
     OTRY(tmp.alloc(&dist, (size_t)T * kappa));
-    OTRY(knn_exact_gpu(t->X, t->N, d, kappa, Yc, T, ids, dist, s));
+    OTRY(knn_oos(t, Yc, T, kappa, ids, dist, s));
     OTRY(tmp.alloc(&keys, T)); OTRY(tmp.alloc(&keys_s, T));
     OTRY(tmp.alloc(&vals, T)); OTRY(tmp.alloc(&order, T));
     oos_keys_kernel<<<nblk(T, 256), 256, 0, s>>>(ids, kappa, t->pos, T, keys, vals);
@@ -552,6 +552,28 @@ askit_status askit_weights_destroy(askit_weights w) {
     return ASKIT_OK;
 }
 
+askit_status askit_knn_targets(askit_tree t, const float *Y_dev, int64_t T, int64_t ldy, int32_t *ids_dev,
+                               double *dist_dev, void *stream) {
+    if (!t || !Y_dev || !ids_dev || !dist_dev || T < 1 || ldy < t->d) {
+        askit_set_error("need a tree, T >= 1, ldy >= d and the three buffers");
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int d = t->d;
+    float *Yc = nullptr;
+    ASK_CUDA(cudaMallocAsync(&Yc, sizeof(float) * (size_t)T * d, s));
+    askit_status rc = ASKIT_OK;
+    if (cudaMemcpy2DAsync(Yc, sizeof(float) * d, Y_dev, sizeof(float) * ldy, sizeof(float) * d, T,
+                          cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+        askit_set_error("copy Y");
+        rc = ASKIT_ERR_CUDA;
+    }
+    if (rc == ASKIT_OK) rc = knn_oos(t, Yc, T, t->kappa, ids_dev, dist_dev, s);
+    cudaFreeAsync(Yc, s);
+    cudaStreamSynchronize(s);
+    return rc;
+}
+
 askit_status askit_set_launch(askit_tree t, int32_t schedule, int32_t stages, int32_t tiled_runs, int32_t pairs) {
     if (!t || schedule < 0 || schedule > 1 || stages < 2 || stages > 3 || tiled_runs < 0 || tiled_runs > 1 ||
         pairs < 0 || pairs > 1) {
@@ -727,8 +749,12 @@ askit_status askit_footprint(askit_tree t, int32_t kind, int64_t n, int32_t r, s
         // an out-of-sample batch of n targets: queries, kNN, prune sets and
         // work lists (entries estimated from the in-sample rate, doubled)
         const double ent = 2.0 * per_target * n + 1024;
+        // kNN shortlist: candidates (1024 a query), seed lists, padded rows, and
+        // the dense work items (every leaf sub-block against each 128 queries)
+        const double knn = (double)n * (1024 * 4 + 32 * 12 + (size_t)t->d_pad * 4 + 32) +
+                           (double)t->n_leaf_sub * ((n + 127) / 128) * sizeof(EvalItem);
         b = (size_t)(n * ((size_t)t->d * 4 + (size_t)t->d_pad * 4 + (size_t)t->kappa * (4 + 8 + 4 + 4) + 64) +
-                     ent * (8 * 4 + 4 + 4 * r + 32 / 128.0) + (1 << 20));
+                     ent * (8 * 4 + 4 + 4 * r + 32 / 128.0) + knn + (1 << 20));
     }
     *bytes = b;
     return ASKIT_OK;

@@ -87,14 +87,23 @@ struct T16Args {
     float f16_scale;
     int runs;                 // 8-row tiled loads for runs of consecutive target rows
     float uni_a, uni_c;       // UNI: A = 2 sc / scale^2 and C = -sc
+    // UNI == 2 (kNN shortlist): emit every source with D <= U_q (1 + eta) + eta (|a|^2 + |b|^2)
+    const float *knn_u;       // [queries] upper bound of each query's kappa-th distance
+    int *knn_cnt;             // [queries] candidates emitted
+    int32_t *knn_cand;        // [queries, knn_cap] tree positions of the candidates
+    int knn_cap;
+    float knn_eta, knn_m2u;   // margin, and -2 / scale^2
     const int32_t *partner;   // [n_blocks] paired follower block, or -1 (NB == 2)
     float *partial;
     int *status;
 };
 
-// UNI: one bandwidth for all sources (c log2(e) / h^2 = sc for every j): the
-// column data is then {B_j, B_j+1, w_j, w_j+1} per pair (8 bytes a column),
-// half of the general layout, and A = 2 sc / scale^2, C = -sc are scalars.
+// UNI == 1: one bandwidth for all sources (c log2(e) / h^2 = sc for every j):
+// the column data is then {B_j, B_j+1, w_j, w_j+1} per pair (8 bytes a
+// column), half of the general layout, and A = 2 sc / scale^2, C = -sc are
+// scalars.  UNI == 2: the kernel is the exact kNN's tensor-core shortlist
+// (queries against every source): the column data is {|b_j|^2 (1 - eta),
+// the same for j+1, position_j, position_j+1}; no kernel sum is formed.
 template <int P, int RC, int NRAW, int NB, int UNI>
 __global__ void __launch_bounds__(T16_THREADS, 1)
 eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_constant__ CUtensorMap map_t_lo,
@@ -103,7 +112,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                  const T16Args args) {
     using S = S16<RC, NRAW, NB>;
     constexpr int NACC = S::NACC;
-    static_assert(!UNI || RC == 1, "the uniform-bandwidth layout serves r = 1");
+    static_assert(!UNI || RC == 1, "the uniform-bandwidth and kNN layouts serve r = 1");
     constexpr uint32_t FMT = P == ASKIT_PREC_BF16X3 ? 1u : 0u;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -259,13 +268,32 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
 #pragma unroll
                 for (int z = 0; z < RC; ++z) acc[z] = 0.f;
                 float2 acc2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};   // RC == 1
+                // kNN shortlist: this row's query and its bound (loaded before the wait)
+                const int qs = UNI == 2 && row < item.cnt ? args.tgt[item.e0 + row] : -1;
+                const float qu = qs >= 0 ? args.knn_u[qs] : 0.f;
                 if (q * 32 < item.cnt) {   // warp-uniform: skip quadrants with no target
                     const float pt = a_norm[a4 * 128 + row];   // NACC <= 4 slots
                     const float2 pt2 = make_float2(pt, pt);
                     // arg = g A + (C p + B) = -sc (p + q - 2 g / scale^2); columns past
                     // nrows carry A = B = C = w = 0
+                    const float rth = qs >= 0 ? qu * (1.f + args.knn_eta) + args.knn_eta * pt : -INFINITY;
+                    const float2 m2u2 = make_float2(args.knn_m2u, args.knn_m2u);
+                    auto emit = [&](uint32_t pos) {
+                        const int k = atomicAdd(args.knn_cnt + qs, 1);
+                        if (k < args.knn_cap) args.knn_cand[(int64_t)qs * args.knn_cap + k] = (int32_t)pos;
+                    };
                     auto cols = [&](int c, const uint32_t (&gr)[32]) {
-                        if constexpr (RC == 1 && UNI) {
+                        if constexpr (UNI == 2) {
+#pragma unroll
+                            for (int jj = 0; jj < 32; jj += 2) {
+                                const float4 bp = cv4[(c * 32 + jj) >> 1];   // {B'_j, B'_j+1, pos_j, pos_j+1}
+                                const float2 inner = __fadd2_rn(pt2, make_float2(bp.x, bp.y));
+                                const float2 dd = __ffma2_rn(make_float2(__uint_as_float(gr[jj]), __uint_as_float(gr[jj + 1])),
+                                                             m2u2, inner);
+                                if (dd.x <= rth) emit(__float_as_uint(bp.z));
+                                if (dd.y <= rth) emit(__float_as_uint(bp.w));
+                            }
+                        } else if constexpr (RC == 1 && UNI == 1) {
                             const float2 a2 = make_float2(args.uni_a, args.uni_a);
                             const float2 c2 = make_float2(args.uni_c, args.uni_c);
 #pragma unroll
@@ -325,7 +353,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                 }
                 tc_fence_before();
                 mbar_arrive(BAR_T_EMPTY(a4));
-                if (row < item.cnt) {
+                if (UNI != 2 && row < item.cnt) {
                     float *p = args.partial + (int64_t)(item.e0 + row) * args.r;
 #pragma unroll
                     for (int z = 0; z < RC; ++z)
@@ -431,7 +459,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
             }
             const uint32_t slot = sbase + S::BLK + bs * S::BLKSLOT;
             const uint32_t colw_bytes = RC > 1 ? (uint32_t)(nsb * 128 * RC * 4) : 0u;
-            constexpr int CV = UNI ? 64 : 128;   // float4 of column data per sub-block
+            constexpr int CV = UNI ? 64 : 128;   // float4 of column data per sub-block (UNI 1, 2: compact)
             mbar_expect_tx(BAR_BLK_FULL(bs), (uint32_t)(256 + nsb * CV * 16) + colw_bytes);
             bulk_copy(slot + S::BLK_CENT, args.cent + (int64_t)first.cidx * TC_K, TC_K * 4, BAR_BLK_FULL(bs));
             bulk_copy(slot + S::BLK_COLV, args.colv + (int64_t)first.cidx * CV, nsb * CV * 16, BAR_BLK_FULL(bs));
@@ -513,7 +541,44 @@ __global__ void tc16_cols_kernel(const int64_t *sb_row0, const int32_t *sb_nr, i
     }
 }
 
-// Tensor maps of the pre-split source arrays ([rows, 64] 16-bit; boxes of
+// Column data of the kNN shortlist (leaf sub-blocks only): {|b_j|^2 (1 - eta)
+// or +inf past the rows, the same for j+1, tree position of row j, of j+1}.
+__global__ void tc16_knn_cols_kernel(const int64_t *sb_row0, const int32_t *sb_nr, const float *nrm_t, float eta,
+                                     float4 *colv) {
+    const int64_t b = blockIdx.x;
+    const int t = threadIdx.x;
+    const int64_t row = sb_row0[b] + t;
+    const bool valid = t < sb_nr[b];
+    float *cp = reinterpret_cast<float *>(colv + b * 64 + (t >> 1));
+    const int o = t & 1;
+    cp[0 + o] = valid ? nrm_t[row] * (1.f - eta) : INFINITY;
+    cp[2 + o] = __int_as_float(valid ? (int)row : 0);
+}
+
+// Dense work lists of the shortlist: every leaf sub-block b against every
+// tile of 128 queries k (item b * n_qt + k); the queries are the identity.
+__global__ void knn_items_kernel(const int64_t *sb_row0, const int32_t *sb_nr, int64_t n_sub, int n_qt, int64_t T,
+                                 EvalItem *items, int32_t *block_off) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e <= n_sub) block_off[e] = (int32_t)(e * n_qt);
+    if (e >= n_sub * n_qt) return;
+    const int64_t b = e / n_qt, k = e % n_qt;
+    EvalItem it;
+    it.row0 = (int32_t)sb_row0[b];
+    it.nrows = sb_nr[b];
+    it.e0 = (int32_t)(k * 128);
+    it.cnt = (int32_t)(T - k * 128 < 128 ? T - k * 128 : 128);
+    it.cidx = (int32_t)b;
+    it.pad_[0] = it.pad_[1] = it.pad_[2] = 0;
+    items[e] = it;
+}
+
+__global__ void iota32_kernel(int32_t *a, int64_t n) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < n) a[e] = (int32_t)e;
+}
+
+
 // 64 x 128, 128-byte swizzle) for BF16 (index 0) and FP16 (index 1).
 struct T16State {
     CUtensorMap map[2][4];   // [t_hi, t_lo, s_hi, s_lo]
@@ -651,6 +716,11 @@ askit_status eval_tc16(askit_tree t, const WeightCtx &c, int precision, const fl
     a.runs = t->tune_runs;
     a.partner = nullptr;
     a.uni_a = a.uni_c = 0.f;
+    a.knn_u = nullptr;
+    a.knn_cnt = nullptr;
+    a.knn_cand = nullptr;
+    a.knn_cap = 0;
+    a.knn_eta = a.knn_m2u = 0.f;
     a.partial = partial;
     a.status = t->d_status;
     if (precision != ASKIT_PREC_FP16X3) {
@@ -658,6 +728,114 @@ askit_status eval_tc16(askit_tree t, const WeightCtx &c, int precision, const fl
         return ASKIT_ERR_INVALID_ARG;
     }
     return dispatch16<ASKIT_PREC_FP16X3>(t, c, st, pi, map_q, map_q8, a, w, s);
+}
+
+// The exact kNN's tensor-core shortlist for T queries Yp [T, d_pad] (FP32):
+// every tree position whose FP16x3 distance to query q is at most
+// U[q] (1 + eta) + eta (|a|^2 + |b|^2) goes to cand[q, 0 .. cap) (cnt[q]
+// counts them, also past cap).  Leaf sub-blocks only (every point once).
+askit_status knn_shortlist_tc16(askit_tree t, const float *Yp, int64_t T, const float *U, int *cnt, int32_t *cand,
+                                int cap, float eta, cudaStream_t s) {
+    if (!t->Xt_hhi || t->d > TC_K || t->n_leaf_sub == 0) {
+        askit_set_error("the tensor-core shortlist needs the FP16 operands (d <= %d)", TC_K);
+        return ASKIT_ERR_UNSUPPORTED;
+    }
+    const int64_t nsub = t->n_leaf_sub;
+    const int n_qt = (int)((T + 127) / 128);
+    // pairs: sub-blocks 2k and 2k+1 of one leaf; the schedule deals leaders and
+    // singles to the CTAs in tree order, contiguous ranges of equal cost
+    std::vector<int32_t> partner(nsub, -1), blocks;
+    std::vector<int64_t> cost;
+    for (int64_t b = 0; b < nsub; ++b) {
+        const int64_t node = t->h_sub_node[b];
+        int64_t first = b;
+        while (first > 0 && t->h_sub_node[first - 1] == node) --first;
+        if ((b - first) & 1) continue;                            // a follower
+        if (b + 1 < nsub && t->h_sub_node[b + 1] == node) partner[b] = (int32_t)(b + 1);
+        blocks.push_back((int32_t)b);
+        cost.push_back(partner[b] >= 0 ? 2 : 1);
+    }
+    int dev = 0, sms = 0;
+    ASK_CUDA(cudaGetDevice(&dev));
+    ASK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int nc = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)blocks.size(), sms));
+    int64_t total = 0;
+    for (int64_t c : cost) total += c;
+    std::vector<int32_t> coff(nc + 1, 0);
+    {
+        int c = 0;
+        int64_t acc = 0;
+        for (size_t q = 0; q < blocks.size(); ++q) {
+            acc += cost[q];
+            ++coff[c + 1];
+            if (c < nc - 1 && acc * nc >= (int64_t)(c + 1) * total) ++c;
+        }
+        for (int k = 0; k < nc; ++k) coff[k + 1] += coff[k];
+    }
+    DevArena tmp;
+    tmp.async = true;
+    tmp.stream = s;
+    EvalItem *items = nullptr;
+    int32_t *boff = nullptr, *tgt = nullptr, *d_coff = nullptr, *d_blk = nullptr, *d_part = nullptr;
+    float4 *colv = nullptr;
+    askit_status rc = ASKIT_OK;
+#define KTRY(x) do { rc = (x); if (rc != ASKIT_OK) goto out; } while (0)
+    KTRY(tmp.alloc(&items, (size_t)nsub * n_qt));
+    KTRY(tmp.alloc(&boff, nsub + 1));
+    KTRY(tmp.alloc(&tgt, T));
+    KTRY(tmp.alloc(&d_coff, nc + 1));
+    KTRY(tmp.alloc(&d_blk, blocks.size()));
+    KTRY(tmp.alloc(&d_part, nsub));
+    KTRY(tmp.alloc(&colv, (size_t)nsub * 64));
+    {
+        const int64_t ne = std::max<int64_t>(nsub * n_qt, nsub + 1);
+        knn_items_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(t->sb_row0, t->sb_nr, nsub, n_qt, T, items, boff);
+        iota32_kernel<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(tgt, T);
+        tc16_knn_cols_kernel<<<(unsigned)nsub, 128, 0, s>>>(t->sb_row0, t->sb_nr, t->nrmc_t, eta, colv);
+        if (cudaGetLastError() != cudaSuccess) { askit_set_error("shortlist set-up launch"); rc = ASKIT_ERR_CUDA; goto out; }
+        if (cudaMemcpyAsync(d_coff, coff.data(), sizeof(int32_t) * (nc + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(d_blk, blocks.data(), sizeof(int32_t) * blocks.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(d_part, partner.data(), sizeof(int32_t) * nsub, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            askit_set_error("shortlist schedule copy");
+            rc = ASKIT_ERR_CUDA;
+            goto out;
+        }
+        T16State *st = nullptr;
+        KTRY(t16_state(t, 1, &st));
+        CUtensorMap map_q, map_q8;
+        KTRY(encode_2d(st->encode, &map_q, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, Yp, T, t->d_pad, t->d_pad, 1,
+                       CU_TENSOR_MAP_SWIZZLE_NONE));
+        KTRY(encode_2d(st->encode, &map_q8, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, Yp, T, t->d_pad, t->d_pad, 8,
+                       CU_TENSOR_MAP_SWIZZLE_NONE));
+        T16Args a;
+        a.items = items;
+        a.block_off = boff;
+        a.cta_off = d_coff;
+        a.cta_blocks = d_blk;
+        a.tgt = tgt;
+        a.d_pad = t->d_pad;
+        a.cent = t->cent;
+        a.colv = colv;
+        a.colw = nullptr;
+        a.r = 1;
+        a.f16_scale = t->f16_scale;
+        a.runs = 1;
+        a.partner = d_part;
+        a.uni_a = a.uni_c = 0.f;
+        a.knn_u = U;
+        a.knn_cnt = cnt;
+        a.knn_cand = cand;
+        a.knn_cap = cap;
+        a.knn_eta = eta;
+        a.knn_m2u = -2.f / (t->f16_scale * t->f16_scale);
+        a.partial = nullptr;
+        a.status = t->d_status;
+        KTRY((launch16<ASKIT_PREC_FP16X3, 1, 2, 2, 2>(st, 1, map_q, map_q8, a, nc, s)));
+    }
+out:
+#undef KTRY
+    tmp.free_all();
+    return rc;
 }
 
 void eval_tc16_free(askit_tree t) {

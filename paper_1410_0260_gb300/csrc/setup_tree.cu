@@ -562,6 +562,202 @@ askit_status knn_exact_gpu(const float *X, int64_t N, int d, int kappa, const fl
     return rc;
 }
 
+namespace {
+
+// Out-of-sample kNN, step 1: the two leaves whose centers are nearest to each
+// query (FP32; they only seed the search).  One warp per query, lanes over
+// the leaves.
+__global__ void knn_home_kernel(const float *Yp, int64_t T, int d_pad, const float *cent, const int32_t *leaf_cbase,
+                                int64_t M, int32_t *home) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (q >= T) return;                                  // warp-uniform
+    const float *y = Yp + q * d_pad;
+    float b0 = 3.4e38f, b1 = 3.4e38f;
+    int i0 = 0, i1 = 0;
+    for (int64_t l = lane; l < M; l += 32) {
+        const float *c = cent + (int64_t)leaf_cbase[l] * TC_K;
+        float acc = 0.f;
+        for (int k = 0; k < d_pad; ++k) {
+            const float t = y[k] - c[k];
+            acc = fmaf(t, t, acc);
+        }
+        if (acc < b0) { b1 = b0; i1 = i0; b0 = acc; i0 = (int)l; }
+        else if (acc < b1) { b1 = acc; i1 = (int)l; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {                   // merge the lanes' best two
+        const float ob0 = __shfl_xor_sync(FULL, b0, o), ob1 = __shfl_xor_sync(FULL, b1, o);
+        const int oi0 = __shfl_xor_sync(FULL, i0, o), oi1 = __shfl_xor_sync(FULL, i1, o);
+        float n0, n1;
+        int m0, m1;
+        if (ob0 < b0) { n0 = ob0; m0 = oi0; n1 = b0 < ob1 ? b0 : ob1; m1 = b0 < ob1 ? i0 : oi1; }
+        else { n0 = b0; m0 = i0; n1 = ob0 < b1 ? ob0 : b1; m1 = ob0 < b1 ? oi0 : i1; }
+        b0 = n0; i0 = m0; b1 = n1; i1 = m1;
+    }
+    if (lane == 0) {
+        home[2 * q] = i0;
+        home[2 * q + 1] = M > 1 ? i1 : i0;
+    }
+}
+
+// Step 2: the exact best-32 list of each query over the points of its two
+// home leaves (canonical FP64), and U = its kappa-th distance rounded up to
+// FP32: an upper bound of the query's true kappa-th distance.
+__global__ void knn_seed_kernel(const float *X, int d, const float *Y, int64_t T, const int32_t *home, int64_t M,
+                                const int32_t *nstart, const int32_t *nsize, const int32_t *perm, int kappa,
+                                double *bd, int *bi, float *U) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (q >= T) return;                                  // warp-uniform
+    const float *y = Y + q * d;
+    double ld = DBL_MAX;
+    int li = INT_MAX;
+    for (int h = 0; h < 2; ++h) {
+        const int l = home[2 * q + h];
+        if (h == 1 && l == home[2 * q]) break;
+        const int64_t a = M + l;
+        const int p0 = nstart[a], np = nsize[a];
+        for (int b = 0; b < np; b += 32) {
+            double cd = DBL_MAX;
+            int ci = INT_MAX;
+            if (b + lane < np) {
+                ci = perm[p0 + b + lane];
+                cd = c_dist2(y, X + (int64_t)ci * d, d);
+            }
+            warp_offer(ld, li, cd, ci, kappa, false, lane);
+        }
+    }
+    bd[q * 32 + lane] = ld;
+    bi[q * 32 + lane] = li;
+    const double kth = __shfl_sync(FULL, ld, kappa - 1);
+    if (lane == 0) U[q] = kth < 3.0e38 ? __double2float_ru(kth) : 3.4e38f;
+}
+
+// Step 4: re-rank each query's shortlist (tree positions) in canonical FP64
+// on top of its seed list; a query whose shortlist overflowed is queued for
+// the exhaustive search.
+__global__ void knn_rerank_kernel(const float *X, int d, const float *Y, int64_t T, const int32_t *perm,
+                                  const int *cnt, const int32_t *cand, int cap, int kappa, double *bd, int *bi,
+                                  int32_t *ids, double *dist, int *n_ovf, int32_t *ovf) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (q >= T) return;                                  // warp-uniform
+    const int n = cnt[q];
+    if (n > cap) {
+        if (lane == 0) ovf[atomicAdd(n_ovf, 1)] = (int32_t)q;
+        return;
+    }
+    const float *y = Y + q * d;
+    double ld = bd[q * 32 + lane];
+    int li = bi[q * 32 + lane];
+    for (int b = 0; b < n; b += 32) {
+        double cd = DBL_MAX;
+        int ci = INT_MAX;
+        if (b + lane < n) {
+            ci = perm[cand[q * cap + b + lane]];
+            cd = c_dist2(y, X + (int64_t)ci * d, d);
+        }
+        warp_offer(ld, li, cd, ci, kappa, true, lane);
+    }
+    if (lane < kappa) {
+        ids[q * kappa + lane] = li;
+        dist[q * kappa + lane] = ld;
+    }
+}
+
+__global__ void knn_pad_rows_kernel(const float *Y, int64_t T, int d, int d_pad, float *Yp) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= T * d_pad) return;
+    const int64_t q = e / d_pad;
+    const int k = (int)(e % d_pad);
+    Yp[e] = k < d ? Y[q * d + k] : 0.f;
+}
+
+__global__ void knn_gather_rows_kernel(const float *Y, int d, const int32_t *rows, int64_t n, float *out) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * d) return;
+    out[e] = Y[(int64_t)rows[e / d] * d + e % d];
+}
+
+__global__ void knn_scatter_kernel(const int32_t *ids_s, const double *dist_s, const int32_t *rows, int64_t n,
+                                   int kappa, int32_t *ids, double *dist) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * kappa) return;
+    const int64_t q = rows[e / kappa];
+    ids[q * kappa + e % kappa] = ids_s[e];
+    dist[q * kappa + e % kappa] = dist_s[e];
+}
+
+}  // namespace
+
+askit_status knn_oos(askit_tree t, const float *Y, int64_t T, int kappa, int32_t *ids, double *dist, cudaStream_t s) {
+    if (!t->Xt_hhi || t->d > TC_K || t->n_leaf_sub == 0 || kappa > 32)
+        return knn_exact_gpu(t->X, t->N, t->d, kappa, Y, T, ids, dist, s);
+    const int cap = 1024;
+    const float eta = 1.52587890625e-05f;   // 2^-16: five times the FP16x3 distance error bound
+    const int64_t M = (int64_t)1 << t->L;
+    DevArena tmp;
+    tmp.async = true;
+    tmp.stream = s;
+    float *Yp = nullptr, *U = nullptr;
+    int32_t *home = nullptr, *cand = nullptr, *ovf = nullptr;
+    int *cnt = nullptr, *bi = nullptr, *n_ovf = nullptr;
+    double *bd = nullptr;
+    int h_ovf = 0;
+    askit_status rc = ASKIT_OK;
+#define QTRY(x) do { rc = (x); if (rc != ASKIT_OK) goto out; } while (0)
+    QTRY(tmp.alloc(&Yp, (size_t)T * t->d_pad));
+    QTRY(tmp.alloc(&home, (size_t)T * 2));
+    QTRY(tmp.alloc(&U, T));
+    QTRY(tmp.alloc(&bd, (size_t)T * 32));
+    QTRY(tmp.alloc(&bi, (size_t)T * 32));
+    QTRY(tmp.alloc(&cnt, T));
+    QTRY(tmp.alloc(&cand, (size_t)T * cap));
+    QTRY(tmp.alloc(&ovf, T));
+    QTRY(tmp.alloc(&n_ovf, 1));
+    if (cudaMemsetAsync(cnt, 0, sizeof(int) * T, s) != cudaSuccess || cudaMemsetAsync(n_ovf, 0, sizeof(int), s) != cudaSuccess) {
+        askit_set_error("kNN: memset");
+        rc = ASKIT_ERR_CUDA;
+        goto out;
+    }
+    knn_pad_rows_kernel<<<nblk(T * t->d_pad, 256), 256, 0, s>>>(Y, T, t->d, t->d_pad, Yp);
+    knn_home_kernel<<<nblk(T * 32, 256), 256, 0, s>>>(Yp, T, t->d_pad, t->cent, t->leaf_cbase, M, home);
+    knn_seed_kernel<<<nblk(T * 32, 256), 256, 0, s>>>(t->X, t->d, Y, T, home, M, t->nstart, t->nsize, t->perm, kappa,
+                                                      bd, bi, U);
+    if (cudaGetLastError() != cudaSuccess) { askit_set_error("kNN: seed launch"); rc = ASKIT_ERR_CUDA; goto out; }
+    QTRY(knn_shortlist_tc16(t, Yp, T, U, cnt, cand, cap, eta, s));
+    knn_rerank_kernel<<<nblk(T * 32, 256), 256, 0, s>>>(t->X, t->d, Y, T, t->perm, cnt, cand, cap, kappa, bd, bi, ids,
+                                                        dist, n_ovf, ovf);
+    if (cudaGetLastError() != cudaSuccess) { askit_set_error("kNN: re-rank launch"); rc = ASKIT_ERR_CUDA; goto out; }
+    if (cudaMemcpyAsync(&h_ovf, n_ovf, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        askit_set_error("kNN: %s", cudaGetErrorString(cudaGetLastError()));
+        rc = ASKIT_ERR_CUDA;
+        goto out;
+    }
+    if (h_ovf > 0) {
+        // queries whose shortlist overflowed: the exhaustive search
+        float *Ys = nullptr;
+        int32_t *ids_s = nullptr;
+        double *dist_s = nullptr;
+        QTRY(tmp.alloc(&Ys, (size_t)h_ovf * t->d));
+        QTRY(tmp.alloc(&ids_s, (size_t)h_ovf * kappa));
+        QTRY(tmp.alloc(&dist_s, (size_t)h_ovf * kappa));
+        knn_gather_rows_kernel<<<nblk((int64_t)h_ovf * t->d, 256), 256, 0, s>>>(Y, t->d, ovf, h_ovf, Ys);
+        QTRY(knn_exact_gpu(t->X, t->N, t->d, kappa, Ys, h_ovf, ids_s, dist_s, s));
+        knn_scatter_kernel<<<nblk((int64_t)h_ovf * kappa, 256), 256, 0, s>>>(ids_s, dist_s, ovf, h_ovf, kappa, ids, dist);
+        if (cudaGetLastError() != cudaSuccess) { askit_set_error("kNN: overflow launch"); rc = ASKIT_ERR_CUDA; goto out; }
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        askit_set_error("kNN: %s", cudaGetErrorString(cudaGetLastError()));
+        rc = ASKIT_ERR_CUDA;
+    }
+out:
+#undef QTRY
+    tmp.free_all();
+    return rc;
+}
+
 // RP-tree kNN (Section 2.2): iters trees; in each, every point searches its
 // leaf exhaustively and the best kappa candidates are kept across trees.
 askit_status knn_rp_gpu(const float *X, int64_t N, int d, int kappa, int iters, int64_t rp_leaf,
