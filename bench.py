@@ -338,6 +338,13 @@ def main():
     e3.record(stream)
     torch.cuda.synchronize()
     ms_eval = e2.elapsed_time(e3) / args.steps
+    # the Evaluate kernel by itself: CUDA events around each of its launches
+    # on the stream it runs on (one launch per target batch)
+    tree.kernel_timing(True)
+    for _ in range(args.steps):
+        tree.evaluate(U)
+    k_ms, k_launches = tree.kernel_timing(False)
+    ms_kernel = k_ms / args.steps
     clk = clocks.stop()
     tree.sync()
     # accuracy of this precision against plain FP32 on the full workload
@@ -357,9 +364,9 @@ def main():
     Udir = tree.direct(tg.to(dev))
     eps2 = float(torch.linalg.vector_norm((U[tg.to(dev)] - Udir).double()) / torch.linalg.vector_norm(Udir.double()))
     if world > 1:
-        t = torch.tensor([ms, ms_eval], device=dev)
+        t = torch.tensor([ms, ms_eval, ms_kernel], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_eval = float(t[0]), float(t[1])
+        ms, ms_eval, ms_kernel = float(t[0]), float(t[1]), float(t[2])
     ms_step = ms / args.steps
     value = world * N / (ms_step / 1e3)
 
@@ -388,7 +395,7 @@ def main():
     peaks = measured_peaks()
     P = info["pairs_algorithmic"]
     d = w.d
-    sec = ms_eval / 1e3
+    sec = ms_kernel / 1e3
     smax = (clk or {}).get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0
     mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * smax * 1e6
     if args.precision == "simt_fp32":
@@ -401,7 +408,16 @@ def main():
         tpeak = bf16 * (TF32_OVER_BF16 if args.precision == "tf32x3" else 1.0)   # fp16 and bf16 share the rate
         t_tensor = P * 3 * 2 * d / (tpeak * 1e12)
         t_mufu = P / mufu_peak
-        if t_tensor >= t_mufu:
+        # FP32 lane FMAs per pair in the epilogue: the exponent's argument (2)
+        # and one per weight vector
+        fma_per_pair = r + 2
+        fma_peak = SM_COUNT * FP32_LANES_PER_SM * smax * 1e6
+        t_fma = P * fma_per_pair / fma_peak
+        if t_fma > max(t_tensor, t_mufu):
+            roof = {"bound": "alu", "achieved": P * fma_per_pair / sec / 1e12, "peak": fma_peak / 1e12,
+                    "unit": "Tfma/s", "peak_source": "FP32 FMA: 152 SMs x 128 lanes x max SM clock; "
+                    "%d FMAs per pair (r = %d weight sums + 2 for the exponent's argument)" % (fma_per_pair, r)}
+        elif t_tensor >= t_mufu:
             roof = {"bound": "tensor", "achieved": P * 3 * 2 * d / sec / 1e12, "peak": tpeak, "unit": "TFLOP/s",
                     "peak_source": ("measured bf16 burst x 1.1/2.25 (TF32)" if args.precision == "tf32x3"
                                     else "measured bf16 burst") + (" of measured" if peaks else " of fallback")}
@@ -413,7 +429,9 @@ def main():
     roof["kernel"] = ("eval_simt_kernel" if args.precision == "simt_fp32" else
                       "eval_tcw_kernel" if d > 64 else
                       "eval_tc16_kernel" if args.precision == "fp16x3" else "eval_tc_kernel")
-    roof["ms_per_launch"] = ms_eval
+    roof["ms_per_launch"] = k_ms / max(1, k_launches)
+    roof["launches_per_evaluate"] = k_launches // args.steps
+    roof["evaluate_ms"] = ms_eval
     roof["traffic"] = measured_traffic(roof["kernel"], w.name)
 
     cpu = None
@@ -421,9 +439,11 @@ def main():
         cpu = cpu_baseline(args, w)
         cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
-    # permute-in, one upward kernel per level, Evaluate, fixed-order reduction
-    # (+ the per-sub-block column data of the FP16x3 kernel)
-    launches_per_step = 1 + info["L"] + 2 + (1 if (args.precision == "fp16x3" and d <= 64) else 0)
+    # permute-in, one upward kernel per level, then per target batch Evaluate
+    # and the fixed-order reduction (+ the per-sub-block column data of the
+    # FP16x3 kernel)
+    per_batch = 2 + (1 if (args.precision == "fp16x3" and d <= 64) else 0)
+    launches_per_step = 1 + info["L"] + info["n_batches"] * per_batch
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"simt_fp32": "f32", "tf32x3": "tf32x3", "bf16x3": "bf16x3", "fp16x3": "fp16x3"}[args.precision],
@@ -440,6 +460,7 @@ def main():
             "work": {"pairs_algorithmic": P, "pairs_computed": info["pairs_computed"],
                      "near_per_target": info["near_total"] / N, "far_per_target": info["far_total"] / N,
                      "items": info["n_items"], "blocks": info["n_blocks"], "entries": info["n_entries"], "L": info["L"],
+                     "target_batches": info["n_batches"],
                      "skeleton_rows": info["skel_total"], "setup_s": setup_s,
                      "device_gb": info["device_bytes"] / 1e9}}
     graph.close()

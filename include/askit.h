@@ -83,11 +83,16 @@ typedef struct {
     double kernel_scale; /* c in exp(-c r^2 / h^2) */
     double h;            /* constant bandwidth (ASKIT_BW_CONSTANT) */
     uint64_t seed;       /* Philox key for RP directions and row sampling */
+    int64_t batch_entries; /* in-sample work lists are built and evaluated in
+                              batches of consecutive targets (tree order) of at
+                              most this many (target, sub-block) entries, which
+                              bounds the build's sort buffers and the partial
+                              sums; 0 = 2^28, at most 2^30 */
 } askit_params;
 
 /* Fill `p` with defaults (m = 128, kappa = 16, exact kNN, s_max = 64,
  * ell_extra = 20, prune = 1, constant h = 1, c = 1/2, id_tol = 1e-6,
- * TF32x3 evaluation, seed = 1). */
+ * TF32x3 evaluation, seed = 1, batch_entries = 0). */
 void askit_default_params(askit_params *p);
 
 /*
@@ -253,6 +258,19 @@ askit_status askit_autotune(askit_tree t, int32_t reps, void *stream, askit_tune
 askit_status askit_set_launch(askit_tree t, int32_t schedule, int32_t stages, int32_t tiled_runs, int32_t pairs);
 
 /*
+ * Device time of the evaluation kernel itself (Algorithm 4's work: the
+ * persistent kernel of the tree's precision, without the per-Evaluate column
+ * setup and the partial-sum reduction).  enable = 1 starts a timing session:
+ * every later launch of that kernel for this tree (askit_evaluate,
+ * askit_evaluate_targets, the weight-context calls; one launch per target
+ * batch) is bracketed by CUDA events on its own stream; launches captured
+ * into a graph are not timed.  enable = 0 ends the session, waits for the
+ * recorded events and returns the summed kernel time in `ms` and the number
+ * of timed launches in `launches` (both required then).  Host call.
+ */
+askit_status askit_kernel_timing(askit_tree t, int32_t enable, double *ms, int64_t *launches);
+
+/*
  * Device bytes a request needs, for admission by memory footprint.
  *   kind 0: a weight context for r vectors (n ignored);
  *   kind 1: an out-of-sample batch of n targets with r weight vectors
@@ -277,6 +295,7 @@ typedef struct {
     int64_t pairs_computed;   /* 128 x 128 target-source slots the items cover */
     int64_t near_total, far_total; /* sum over targets of |Near(i)| and |Far(i)| */
     int64_t device_bytes;     /* library-owned device memory */
+    int64_t n_batches;        /* in-sample target batches (askit_params.batch_entries) */
 } askit_info;
 askit_status askit_get_info(askit_tree t, askit_info *info);
 

@@ -31,7 +31,8 @@ EXPORTS = ["askit_default_params", "askit_setup", "askit_set_weights", "askit_ev
            "askit_last_error", "askit_knn_noalloc", "askit_direct", "askit_weights_create",
            "askit_weights_set", "askit_weights_evaluate", "askit_weights_evaluate_targets",
            "askit_weights_destroy", "askit_footprint", "askit_graph_create", "askit_graph_launch",
-           "askit_graph_destroy", "askit_autotune", "askit_set_launch", "askit_knn_targets"]
+           "askit_graph_destroy", "askit_autotune", "askit_set_launch", "askit_knn_targets",
+           "askit_kernel_timing"]
 
 
 class TuneEntry(C.Structure):
@@ -49,7 +50,7 @@ class Params(C.Structure):
                 ("s_min", C.c_int32), ("ell_extra", C.c_int32), ("prune", C.c_int32),
                 ("bw_mode", C.c_int32), ("bw_k", C.c_int32), ("precision", C.c_int32),
                 ("id_tol", C.c_double), ("kernel_scale", C.c_double), ("h", C.c_double),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("batch_entries", C.c_int64)]
 
 
 class Info(C.Structure):
@@ -57,7 +58,8 @@ class Info(C.Structure):
                 ("kappa", C.c_int32), ("r", C.c_int32), ("n_nodes", C.c_int64),
                 ("skel_total", C.c_int64), ("skel_rows_padded", C.c_int64), ("n_blocks", C.c_int64),
                 ("n_items", C.c_int64), ("n_entries", C.c_int64), ("pairs_algorithmic", C.c_int64), ("pairs_computed", C.c_int64),
-                ("near_total", C.c_int64), ("far_total", C.c_int64), ("device_bytes", C.c_int64)]
+                ("near_total", C.c_int64), ("far_total", C.c_int64), ("device_bytes", C.c_int64),
+                ("n_batches", C.c_int64)]
 
 
 def load(path: str | None = None):
@@ -95,6 +97,7 @@ def load(path: str | None = None):
             L.askit_autotune.argtypes = [V, I32, V, C.POINTER(TuneEntry), I32, C.POINTER(I32)]
             L.askit_set_launch.argtypes = [V, I32, I32, I32, I32]
             L.askit_knn_targets.argtypes = [V, V, I64, I64, V, V, V]
+            L.askit_kernel_timing.argtypes = [V, I32, C.POINTER(D), C.POINTER(I64)]
             L.askit_status_string.restype = C.c_char_p
             L.askit_status_string.argtypes = [C.c_int]
             L.askit_last_error.restype = C.c_char_p
@@ -145,11 +148,13 @@ class Config:
     kernel_scale: float = 0.5
     h: float = 1.0
     seed: int = 1
+    batch_entries: int = 0      # entries per in-sample work-list batch (0 = 2^28)
 
     def to_c(self) -> Params:
         return Params(self.leaf_size, self.kappa, self.knn_mode, self.rp_iters, self.rp_leaf, self.s_max,
                       self.s_min, self.ell_extra, self.prune, self.bw_mode, self.bw_k,
-                      PRECISIONS[self.precision], self.id_tol, self.kernel_scale, self.h, self.seed)
+                      PRECISIONS[self.precision], self.id_tol, self.kernel_scale, self.h, self.seed,
+                      self.batch_entries)
 
 
 class Tree:
@@ -269,6 +274,13 @@ class Tree:
         """Set the evaluation kernel's launch configuration (see autotune)."""
         _check(load().askit_set_launch(self._t, {"lpt": 0, "tree_order": 1}[schedule], stages, int(tiled_runs),
                                        int(pairs)))
+
+    def kernel_timing(self, enable: bool):
+        """Start (True) or end (False) timing the evaluation kernel's own
+        launches with CUDA events; ending returns (total ms, launches)."""
+        ms, n = C.c_double(), C.c_int64()
+        _check(load().askit_kernel_timing(self._t, int(enable), C.byref(ms), C.byref(n)))
+        return None if enable else (ms.value, n.value)
 
     def capture(self, W: torch.Tensor, U: torch.Tensor, stream=None) -> "Graph":
         """A CUDA graph of set_weights(W) + evaluate(U); replays read W's

@@ -50,6 +50,10 @@ constexpr int ASK_TILE_M = 128;
 constexpr int ASK_BLK_N = 128;
 // Columns of the tensor-core operand arrays (d <= TC_K).
 constexpr int TC_K = 64;
+// Default and largest entries of one in-sample work-list batch (entry
+// offsets inside a batch are int32).
+constexpr int64_t ASK_BATCH_ENTRIES = (int64_t)1 << 28;
+constexpr int64_t ASK_BATCH_ENTRIES_MAX = (int64_t)1 << 30;
 
 // ---------------------------------------------------------------------------
 // Device memory owned by a tree: every allocation is recorded and freed by
@@ -203,8 +207,11 @@ struct askit_tree_s {
     WeightCtx dw;              // default weight context (askit_set_weights)
     int precision = ASKIT_PREC_TF32X3;
 
-    // in-sample work lists
-    WorkLists wl;
+    // in-sample work lists, one per batch of consecutive target slots
+    // [wl_t0[b], wl_t0[b + 1]); the partial sums are sized for the largest
+    std::vector<WorkLists> wl;
+    std::vector<int64_t> wl_t0;
+    int64_t wl_entries = 0, wl_entries_max = 0;
 
     // tensor-core operands: every source sub-block centered on its own mean,
     // split into hi + lo parts (TF32 and BF16), TC_K columns, and the squared
@@ -236,7 +243,19 @@ struct askit_tree_s {
     int tune_runs = 1;             // 8-row tiled loads for runs of consecutive targets
     int tune_pairs = 0;            // FP16x3: items over two sub-blocks of a node (256 columns)
     int kw = TC_K;                 // row width of the pre-split operands and centers
+    // CUDA events around each launch of the evaluation kernel while timing
+    // is on (askit_kernel_timing): begin/end pairs, reused across sessions
+    struct KTimer {
+        bool on = false;
+        std::vector<cudaEvent_t> ev;
+        size_t used = 0;
+    } kt;
 };
+
+// Records the begin (end = false) or end event of one evaluation-kernel
+// launch on stream s while the tree's kernel timer is on; a no-op otherwise
+// and while s is being captured into a graph.
+askit_status ktimer_mark(askit_tree t, cudaStream_t s, bool end);
 
 // ---------------------------------------------------------------------------
 // Canonical FP64 arithmetic (device).  Every operation is an explicitly
@@ -352,6 +371,8 @@ askit_status skeletonize(askit_tree t, cudaStream_t s);
 // eval_lists.cu
 askit_status build_eval_operands(askit_tree t, cudaStream_t s);
 askit_status build_tc_operands(askit_tree t, cudaStream_t s);
+askit_status build_insample_lists(askit_tree t, const int32_t *sets, int stride, cudaStream_t s);
+void use_schedule(askit_tree t);
 askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, int64_t T, WorkLists &w,
                               DevArena &arena, cudaStream_t s);
 askit_status reduce_partials(const WorkLists &w, const float *partial, int r, const int32_t *out_rows,

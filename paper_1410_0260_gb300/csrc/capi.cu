@@ -6,6 +6,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 
 #include "askit_impl.cuh"
@@ -90,6 +91,8 @@ __global__ void gather_y_kernel(const float *Y, int64_t ldy, int d, int d_pad, c
     }
 }
 
+std::mutex g_kt_mu;
+
 askit_status validate(const askit_params *p, int64_t N, int32_t d, int64_t ldx, const float *h_dev) {
     if (!p) { askit_set_error("params is NULL"); return ASKIT_ERR_INVALID_ARG; }
     if (N < 1 || d < 1 || ldx < d) { askit_set_error("need N >= 1, d >= 1, ldx >= d"); return ASKIT_ERR_INVALID_ARG; }
@@ -108,6 +111,10 @@ askit_status validate(const askit_params *p, int64_t N, int32_t d, int64_t ldx, 
     if (p->knn_mode < 0 || p->knn_mode > 1) { askit_set_error("bad knn_mode"); return ASKIT_ERR_INVALID_ARG; }
     if (p->knn_mode == 1 && p->rp_iters < 1) { askit_set_error("rp_iters must be >= 1"); return ASKIT_ERR_INVALID_ARG; }
     if (p->precision < 0 || p->precision > 3) { askit_set_error("bad precision"); return ASKIT_ERR_INVALID_ARG; }
+    if (p->batch_entries != 0 && (p->batch_entries < 4096 || p->batch_entries > ASK_BATCH_ENTRIES_MAX)) {
+        askit_set_error("batch_entries must be 0 or in 4096..2^30");
+        return ASKIT_ERR_INVALID_ARG;
+    }
     return ASKIT_OK;
 }
 
@@ -208,8 +215,7 @@ askit_status setup_impl(askit_tree t, const float *X_dev, int64_t ldx, const flo
         int32_t *sets = nullptr;
         ASK_CUDA(cudaMalloc(&sets, sizeof(int32_t) * N * stride));
         askit_status rc = insample_prune_sets(t, sets, s);
-        if (rc == ASKIT_OK)
-            rc = build_work_lists(t, sets, stride, N, t->wl, t->arena, s);
+        if (rc == ASKIT_OK) rc = build_insample_lists(t, sets, stride, s);
         cudaFree(sets);
         ASK_TRY(rc);
     }
@@ -220,6 +226,30 @@ askit_status setup_impl(askit_tree t, const float *X_dev, int64_t ldx, const flo
     ASK_CUDA(cudaStreamSynchronize(s));
     return ASKIT_OK;
 }
+
+}  // namespace
+
+askit_status ktimer_mark(askit_tree t, cudaStream_t s, bool end) {
+    std::lock_guard<std::mutex> lock(g_kt_mu);
+    if (!t->kt.on) return ASKIT_OK;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    ASK_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return ASKIT_OK;
+    if (!end) {
+        while (t->kt.ev.size() < t->kt.used + 2) {
+            cudaEvent_t e = nullptr;
+            ASK_CUDA(cudaEventCreate(&e));
+            t->kt.ev.push_back(e);
+        }
+        ASK_CUDA(cudaEventRecord(t->kt.ev[t->kt.used], s));
+    } else {
+        ASK_CUDA(cudaEventRecord(t->kt.ev[t->kt.used + 1], s));
+        t->kt.used += 2;
+    }
+    return ASKIT_OK;
+}
+
+namespace {
 
 // Evaluate over one set of work lists: every (target, sub-block) entry's
 // partial sum, then each target's entries summed in their fixed order.
@@ -244,7 +274,14 @@ askit_status evaluate_ctx(askit_tree t, const WeightCtx &c, float *U_dev, int64_
     if (!U_dev) { askit_set_error("U_dev must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
     if (!c.ready) { askit_set_error("no weights set"); return ASKIT_ERR_NOT_READY; }
     if (ldu < c.r) { askit_set_error("ldu < r"); return ASKIT_ERR_INVALID_ARG; }
-    return run_eval(t, c, t->precision, t->Xt, t->d_pad, t->N_pad, t->wl, c.partial, t->perm, U_dev, ldu, s);
+    // batch b covers target slots [t0, t1): its target rows start at row t0
+    // of Xt and its results go to the points perm[t0 .. t1)
+    for (size_t b = 0; b < t->wl.size(); ++b) {
+        const int64_t t0 = t->wl_t0[b];
+        ASK_TRY(run_eval(t, c, t->precision, t->Xt + t0 * t->d_pad, t->d_pad, t->N_pad - t0, t->wl[b], c.partial,
+                         t->perm + t0, U_dev, ldu, s));
+    }
+    return ASKIT_OK;
 }
 
 }  // namespace
@@ -269,6 +306,7 @@ void askit_default_params(askit_params *p) {
     p->kernel_scale = 0.5;
     p->h = 1.0;
     p->seed = 1;
+    p->batch_entries = 0;
 }
 
 const char *askit_status_string(askit_status s) {
@@ -436,14 +474,19 @@ askit_status askit_get_info(askit_tree t, askit_info *info) {
     info->n_nodes = t->n_nodes;
     info->skel_total = t->skel_total;
     info->skel_rows_padded = t->spool_rows;
-    info->n_blocks = t->wl.n_blocks;
-    info->n_items = t->wl.n_items;
-    info->n_entries = t->wl.n_entries;
-    info->pairs_algorithmic = t->wl.pairs_alg;
-    info->pairs_computed = t->wl.pairs_cmp;
-    info->near_total = t->wl.near_tot;
-    info->far_total = t->wl.far_tot;
+    info->n_blocks = info->n_items = info->n_entries = 0;
+    info->pairs_algorithmic = info->pairs_computed = info->near_total = info->far_total = 0;
+    for (const WorkLists &w : t->wl) {
+        info->n_blocks += w.n_blocks;
+        info->n_items += w.n_items;
+        info->n_entries += w.n_entries;
+        info->pairs_algorithmic += w.pairs_alg;
+        info->pairs_computed += w.pairs_cmp;
+        info->near_total += w.near_tot;
+        info->far_total += w.far_tot;
+    }
     info->device_bytes = (int64_t)t->arena.bytes;
+    info->n_batches = (int64_t)t->wl.size();
     return ASKIT_OK;
 }
 
@@ -510,9 +553,35 @@ askit_status askit_sync(askit_tree t, void *stream) {
     return ASKIT_OK;
 }
 
+askit_status askit_kernel_timing(askit_tree t, int32_t enable, double *ms, int64_t *launches) {
+    if (!t || (!enable && (!ms || !launches))) {
+        askit_set_error("need a tree, and ms and launches to stop timing");
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_kt_mu);
+    if (enable) {
+        t->kt.on = true;
+        t->kt.used = 0;
+        return ASKIT_OK;
+    }
+    t->kt.on = false;
+    double tot = 0.0;
+    for (size_t k = 0; k + 1 < t->kt.used; k += 2) {
+        ASK_CUDA(cudaEventSynchronize(t->kt.ev[k + 1]));
+        float x = 0.f;
+        ASK_CUDA(cudaEventElapsedTime(&x, t->kt.ev[k], t->kt.ev[k + 1]));
+        tot += x;
+    }
+    *ms = tot;
+    *launches = (int64_t)(t->kt.used / 2);
+    t->kt.used = 0;
+    return ASKIT_OK;
+}
+
 askit_status askit_destroy(askit_tree t) {
     if (!t) return ASKIT_OK;
     cudaDeviceSynchronize();
+    for (cudaEvent_t e : t->kt.ev) cudaEventDestroy(e);
     eval_tc_free(t);
     t->dw.arena.free_all();
     t->arena.free_all();
@@ -588,8 +657,7 @@ askit_status askit_set_launch(askit_tree t, int32_t schedule, int32_t stages, in
     t->tune_stages = stages;
     t->tune_runs = tiled_runs;
     t->tune_pairs = pairs;
-    t->wl.cta_off = t->wl.sched_off[t->tune_sched];
-    t->wl.cta_blocks = t->wl.sched_blocks[t->tune_sched];
+    use_schedule(t);
     return ASKIT_OK;
 }
 
@@ -610,7 +678,9 @@ askit_status askit_autotune(askit_tree t, int32_t reps, void *stream, askit_tune
             for (int ru = (fp16 ? 0 : t->tune_runs); ru <= (fp16 ? 1 : t->tune_runs); ++ru)
                 cand.push_back({sc, st, ru, 0, 0.0});
     // paired 256-column items (FP16x3, r <= 4): their own schedule, two stages
-    if (fp16 && t->dw.r <= 4 && t->wl.n_pairs > 0)
+    int64_t n_pairs = 0;
+    for (const WorkLists &w : t->wl) n_pairs += w.n_pairs;
+    if (fp16 && t->dw.r <= 4 && n_pairs > 0)
         for (int ru = 0; ru <= 1; ++ru) cand.push_back({2, 2, ru, 1, 0.0});
     float *U = nullptr;
     ASK_CUDA(cudaMallocAsync(&U, sizeof(float) * (size_t)t->N * std::max(1, t->dw.r), s));
@@ -625,8 +695,7 @@ askit_status askit_autotune(askit_tree t, int32_t reps, void *stream, askit_tune
         t->tune_stages = c.stages;
         t->tune_runs = c.runs;
         t->tune_pairs = c.pairs;
-        t->wl.cta_off = t->wl.sched_off[t->tune_sched & 1];
-        t->wl.cta_blocks = t->wl.sched_blocks[t->tune_sched & 1];
+        use_schedule(t);
     };
     for (size_t k = 0; k < cand.size() && rc == ASKIT_OK; ++k) {
         apply(cand[k]);
@@ -740,11 +809,11 @@ askit_status askit_footprint(askit_tree t, int32_t kind, int64_t n, int32_t r, s
         return ASKIT_ERR_INVALID_ARG;
     }
     const int64_t srows = std::max<int64_t>(t->spool_rows, 1) + 256;
-    const double per_target = (double)t->wl.n_entries / std::max<int64_t>(1, t->N);
+    const double per_target = (double)t->wl_entries / std::max<int64_t>(1, t->N);
     size_t b = 0;
     if (kind == 0) {
         // a weight context: W in tree order, skeleton weights, partials
-        b = sizeof(float) * ((size_t)t->N_pad * r + (size_t)srows * r + (size_t)t->wl.n_entries * r);
+        b = sizeof(float) * ((size_t)t->N_pad * r + (size_t)srows * r + (size_t)t->wl_entries_max * r);
     } else {
         // an out-of-sample batch of n targets: queries, kNN, prune sets and
         // work lists (entries estimated from the in-sample rate, doubled)

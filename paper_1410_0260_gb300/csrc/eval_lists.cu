@@ -731,6 +731,62 @@ out:
     return rc;
 }
 
+// The in-sample work lists in batches of consecutive target slots: a count
+// pass over all N targets, then cuts wherever the next target would take the
+// running batch past the entry budget.  A sub-block's items and a pair's
+// matching lists never straddle a cut (both are lists of targets), and every
+// entry's partial sum is computed the same way in whichever batch holds it.
+askit_status build_insample_lists(askit_tree t, const int32_t *sets, int stride, cudaStream_t s) {
+    const int64_t N = t->N;
+    const int64_t budget = t->prm.batch_entries > 0 ? t->prm.batch_entries : ASK_BATCH_ENTRIES;
+    std::vector<int64_t> h_cnt(N);
+    {
+        int64_t *buf = nullptr;
+        ASK_CUDA(cudaMallocAsync(&buf, sizeof(int64_t) * 4 * N, s));
+        count_kernel<<<nblk(N, 128), 128, 0, s>>>(sets, stride, N, t->L, t->nsize, t->d_s, buf, buf + N, buf + 2 * N,
+                                                  buf + 3 * N);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt.data(), buf, sizeof(int64_t) * N, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFreeAsync(buf, s);
+        ASK_CUDA(e);
+    }
+    t->wl.clear();
+    t->wl_t0.assign(1, 0);
+    int64_t acc = 0;
+    for (int64_t q = 0; q < N; ++q) {
+        if (acc > 0 && acc + h_cnt[q] > budget) {
+            t->wl_t0.push_back(q);
+            acc = 0;
+        }
+        acc += h_cnt[q];
+    }
+    t->wl_t0.push_back(N);
+    const size_t nb = t->wl_t0.size() - 1;
+    t->wl.resize(nb);
+    t->wl_entries = t->wl_entries_max = 0;
+    for (size_t b = 0; b < nb; ++b) {
+        const int64_t t0 = t->wl_t0[b], T = t->wl_t0[b + 1] - t0;
+        ASK_TRY(build_work_lists(t, sets + t0 * stride, stride, T, t->wl[b], t->arena, s));
+        if (t->wl[b].n_entries >= ((int64_t)1 << 31)) {
+            askit_set_error("a single target has more than 2^31 work entries");
+            return ASKIT_ERR_UNSUPPORTED;
+        }
+        t->wl_entries += t->wl[b].n_entries;
+        t->wl_entries_max = std::max(t->wl_entries_max, t->wl[b].n_entries);
+    }
+    return ASKIT_OK;
+}
+
+// The CTA schedule the kernels use: LPT or tree order (askit_set_launch);
+// the paired schedule is taken by the FP16x3 kernel itself.
+void use_schedule(askit_tree t) {
+    for (WorkLists &w : t->wl) {
+        w.cta_off = w.sched_off[t->tune_sched & 1];
+        w.cta_blocks = w.sched_blocks[t->tune_sched & 1];
+    }
+}
+
 askit_status reduce_partials(const WorkLists &w, const float *partial, int r, const int32_t *out_rows, float *U,
                              int64_t ldu, cudaStream_t s) {
     if (w.T == 0) return ASKIT_OK;

@@ -99,6 +99,7 @@ askit_status eval_simt(askit_tree t, const WeightCtx &c, const float *Xq, int64_
                        float *partial, cudaStream_t s) {
     if (w.n_blocks == 0) return ASKIT_OK;
     int r = c.r;
+    ASK_TRY(ktimer_mark(t, s, false));
 #define LAUNCH(R)                                                                                   \
     eval_simt_kernel<R><<<(unsigned)w.n_blocks, ASK_TILE_M, 0, s>>>(                                \
         Xq, ldq, w.items, w.block_off, w.block_order, w.tgt, partial, t->Xt, t->Xs, t->sc_t,        \
@@ -109,7 +110,7 @@ askit_status eval_simt(askit_tree t, const WeightCtx &c, const float *Xq, int64_
     else LAUNCH(64);
 #undef LAUNCH
     ASK_LAUNCH();
-    return ASKIT_OK;
+    return ktimer_mark(t, s, true);
 }
 
 // ---------------------------------------------------------------------------

@@ -659,10 +659,11 @@ askit_status launch(askit_tree t, TcState *st, const CUtensorMap &map_q, const T
         }
     }
     const unsigned grid = (unsigned)a_grid;
+    ASK_TRY(ktimer_mark(t, s, false));
     eval_tc_kernel<P, RC><<<grid, TC_THREADS, smem, s>>>(st->map[pi][0], st->map[pi][1], st->map[pi][2],
                                                          st->map[pi][3], map_q, st->raw_t, st->raw_s, a);
     ASK_LAUNCH();
-    return ASKIT_OK;
+    return ktimer_mark(t, s, true);
 }
 
 }  // namespace

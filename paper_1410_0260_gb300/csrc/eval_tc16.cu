@@ -19,9 +19,10 @@
 // sub-block, so the loaders only center and split target rows.
 //
 // One CTA per SM, 448 threads:
-//   warps 0-7  two loader groups taking alternate items: thread t centers and
-//              splits target row t (gathered by warp 13) into the 128-byte
-//              swizzled K-major layout and forms |a|^2;
+//   warps 0-7  two loader groups taking alternate items: each warp centers
+//              and splits 32 target rows (gathered by warp 13), two rows at a
+//              time, into the 128-byte swizzled K-major layout and forms
+//              |a|^2 in a fixed order;
 //   warps 8-11 epilogue: tcgen05.ld of their 32 TMEM lanes (one row each),
 //              exponent on MUFU.EX2, reduction against the weights;
 //   warp 12    TMEM allocation; lane 0 loads each sub-block (TMA tiles of the
@@ -165,8 +166,16 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
 
     if (warp < 8) {
         // ------------------------------------------------------------ loaders
-        const int grp = warp >> 2, t = tid & 127;
+        // A warp converts its 32 rows two at a time: lane (h, k) takes
+        // 4-coordinate chunk k of row 2i + h, so each half-warp reads one
+        // row's contiguous bytes (no bank conflicts) and writes the row's
+        // whole 128-byte swizzled line.  |a|^2 is summed over the chunks by a
+        // butterfly across the 16 lanes in a fixed order, so a row's value
+        // does not depend on its position in the item.
+        const int grp = warp >> 2, wl = warp & 3;
+        const int hh = lane >> 4, kc = lane & 15;
         const int dp = args.d_pad, nk4 = dp / 4;
+        const bool kin = kc < nk4;
         const float2 m1 = make_float2(-1.f, -1.f), z2 = make_float2(0.f, 0.f);
         const float2 sc2 = make_float2(args.f16_scale, args.f16_scale);
         int li = 0, lb = 0;
@@ -174,13 +183,13 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
             const int b = args.cta_blocks[ci];
             const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
             bool need_blk = true;
+            float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);   // this lane's chunk of c_B
             // this group's first item of the block: li and it advance together
             int cnt_next = (i0 + ((grp - li) & 1) < i1) ? args.items[i0 + ((grp - li) & 1)].cnt : 0;
             for (int it = i0; it < i1; ++it, ++li) {
                 if ((li & 1) != grp) continue;
                 const int cnt = cnt_next;
                 if (it + 2 < i1) cnt_next = args.items[it + 2].cnt;   // in flight while this item waits
-                const bool has_tgt = t < cnt;
                 const int sa = li & 1, sr = li % NRAW, a4 = li % NACC;
                 if (!mbar_wait(BAR_A_EMPTY(sa), ((li >> 1) & 1) ^ 1, abort_flag, args.status)) goto loader_done;
                 if (!mbar_wait(BAR_T_EMPTY(a4), ((li / NACC) & 1) ^ 1, abort_flag, args.status)) goto loader_done;
@@ -188,29 +197,25 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                 if (need_blk) {
                     if (!mbar_wait(BAR_BLK_FULL(lb & 1), (lb >> 1) & 1, abort_flag, args.status)) goto loader_done;
                     need_blk = false;
+                    if (kin)
+                        cc = *reinterpret_cast<const float4 *>(sm + S::BLK + (lb & 1) * S::BLKSLOT + S::BLK_CENT +
+                                                               16 * kc);
                 }
-                const float *rrow = reinterpret_cast<const float *>(sm + S::RAW + sr * S::RAWSTAGE) + t * dp;
-                const float *cen = reinterpret_cast<const float *>(sm + S::BLK + (lb & 1) * S::BLKSLOT + S::BLK_CENT);
+                const float *raw = reinterpret_cast<const float *>(sm + S::RAW + sr * S::RAWSTAGE);
                 uint8_t *ahi = sm + S::A0 + sa * 2 * T16_REGION;
                 uint8_t *alo = ahi + T16_REGION;
-                float2 nn2 = z2;
-#pragma unroll 4
-                for (int j = 0; j < TC_K / 4; ++j) {
-                    // 4-element chunks in an order rotated by the row: conflict-free shared loads
-                    const int k4 = (j + t) & (nk4 - 1);
+                float part[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int row = 32 * wl + 2 * i + hh;
                     float2 xa[2] = {z2, z2};
-                    int kst = j;   // chunk to store (zeros past d_pad)
-                    if (j < nk4) {
-                        kst = k4;
-                        if (has_tgt) {
-                            const float4 xx = *reinterpret_cast<const float4 *>(rrow + 4 * k4);
-                            const float4 cc = *reinterpret_cast<const float4 *>(cen + 4 * k4);
-                            xa[0] = __ffma2_rn(make_float2(cc.x, cc.y), m1, make_float2(xx.x, xx.y));
-                            xa[1] = __ffma2_rn(make_float2(cc.z, cc.w), m1, make_float2(xx.z, xx.w));
-                            nn2 = __ffma2_rn(xa[0], xa[0], nn2);
-                            nn2 = __ffma2_rn(xa[1], xa[1], nn2);
-                        }
+                    if (kin && row < cnt) {
+                        const float4 xx = *reinterpret_cast<const float4 *>(raw + row * dp + 4 * kc);
+                        xa[0] = __ffma2_rn(make_float2(cc.x, cc.y), m1, make_float2(xx.x, xx.y));
+                        xa[1] = __ffma2_rn(make_float2(cc.z, cc.w), m1, make_float2(xx.z, xx.w));
                     }
+                    const float2 sq = __ffma2_rn(xa[1], xa[1], __fmul2_rn(xa[0], xa[0]));
+                    part[i] = sq.x + sq.y;
                     uint32_t hv[2], lv[2];
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
@@ -227,11 +232,24 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                             lv[e] = *reinterpret_cast<const uint32_t *>(&l);
                         }
                     }
-                    const int off = t * 128 + (((kst >> 1) ^ (t & 7)) << 4) + (kst & 1) * 8;
+                    const int off = row * 128 + (((kc >> 1) ^ (row & 7)) << 4) + (kc & 1) * 8;
                     *reinterpret_cast<uint2 *>(ahi + off) = make_uint2(hv[0], hv[1]);
                     *reinterpret_cast<uint2 *>(alo + off) = make_uint2(lv[0], lv[1]);
                 }
-                a_norm[a4 * 128 + t] = nn2.x + nn2.y;
+                // butterfly over the 16 chunk lanes: after the step with mask m
+                // a lane keeps the rows whose index bit m matches its own, so
+                // lane k ends with row 2k + h, each sum paired the same way
+#pragma unroll
+                for (int m = 8; m >= 1; m >>= 1) {
+                    const bool up = kc & m;
+#pragma unroll
+                    for (int q = 0; q < m; ++q) {
+                        const float send = up ? part[q] : part[q + m];
+                        const float keep = up ? part[q + m] : part[q];
+                        part[q] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+                    }
+                }
+                a_norm[a4 * 128 + 32 * wl + 2 * kc + hh] = part[0];
                 // generic-proxy stores -> visible to the tensor core's async proxy
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(BAR_A_FULL(sa));
@@ -268,6 +286,9 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
 #pragma unroll
                 for (int z = 0; z < RC; ++z) acc[z] = 0.f;
                 float2 acc2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};   // RC == 1
+                float2 accw[RC > 1 ? RC / 2 : 1];                                    // RC > 1
+#pragma unroll
+                for (int z = 0; z < (RC > 1 ? RC / 2 : 1); ++z) accw[z] = make_float2(0.f, 0.f);
                 // kNN shortlist: this row's query and its bound (loaded before the wait)
                 const int qs = UNI == 2 && row < item.cnt ? args.tgt[item.e0 + row] : -1;
                 const float qu = qs >= 0 ? args.knn_u[qs] : 0.f;
@@ -325,8 +346,16 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                                 const bool h = j & 1;
                                 const float A = h ? ab.y : ab.x, B = h ? ab.w : ab.z, Cc = h ? cw.y : cw.x;
                                 const float k = ex2_approx(fmaf(__uint_as_float(gr[jj]), A, fmaf(Cc, pt, B)));
+                                // the r weight sums as packed pairs: the same fused
+                                // products in the same order, half the instructions
+                                const float2 k2 = make_float2(k, k);
+                                const float4 *w4 = reinterpret_cast<const float4 *>(cwp + j * RC);
 #pragma unroll
-                                for (int z = 0; z < RC; ++z) acc[z] = fmaf(k, cwp[j * RC + z], acc[z]);
+                                for (int z = 0; z < RC / 4; ++z) {
+                                    const float4 wv = w4[z];
+                                    accw[2 * z] = __ffma2_rn(k2, make_float2(wv.x, wv.y), accw[2 * z]);
+                                    accw[2 * z + 1] = __ffma2_rn(k2, make_float2(wv.z, wv.w), accw[2 * z + 1]);
+                                }
                             }
                         }
                     };
@@ -349,7 +378,15 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                             if (h2) tmem_wait_pin(ga);
                         }
                     }
-                    if constexpr (RC == 1) acc[0] = (acc2[0].x + acc2[0].y) + (acc2[1].x + acc2[1].y);
+                    if constexpr (RC == 1) {
+                        acc[0] = (acc2[0].x + acc2[0].y) + (acc2[1].x + acc2[1].y);
+                    } else {
+#pragma unroll
+                        for (int z = 0; z < RC / 2; ++z) {
+                            acc[2 * z] = accw[z].x;
+                            acc[2 * z + 1] = accw[z].y;
+                        }
+                    }
                 }
                 tc_fence_before();
                 mbar_arrive(BAR_T_EMPTY(a4));
@@ -646,29 +683,34 @@ askit_status run16(askit_tree t, const WeightCtx &c, T16State *st, int pi, const
     ASK_LAUNCH();
     a.colv = c.colv;
     a.colw = c.colw;
-    if constexpr (RC == 1) {
-        if (uni) {
+    auto go = [&]() -> askit_status {
+        if constexpr (RC == 1) {
+            if (uni) {
+                if (t->tune_pairs && w.sched_off[2]) {
+                    a.cta_off = w.sched_off[2];
+                    a.cta_blocks = w.sched_blocks[2];
+                    a.partner = w.partner;
+                    return launch16<P, RC, 2, 2, 1>(st, pi, map_q, map_q8, a, w.n_ctas, s);
+                }
+                if (t->tune_stages == 2) return launch16<P, RC, 2, 1, 1>(st, pi, map_q, map_q8, a, w.n_ctas, s);
+                return launch16<P, RC, 3, 1, 1>(st, pi, map_q, map_q8, a, w.n_ctas, s);
+            }
+        }
+        if constexpr (RC <= 4) {
+            // paired 256-column items: two stages fit next to the 64 KB source tile
             if (t->tune_pairs && w.sched_off[2]) {
                 a.cta_off = w.sched_off[2];
                 a.cta_blocks = w.sched_blocks[2];
                 a.partner = w.partner;
-                return launch16<P, RC, 2, 2, 1>(st, pi, map_q, map_q8, a, w.n_ctas, s);
+                return launch16<P, RC, 2, 2, 0>(st, pi, map_q, map_q8, a, w.n_ctas, s);
             }
-            if (t->tune_stages == 2) return launch16<P, RC, 2, 1, 1>(st, pi, map_q, map_q8, a, w.n_ctas, s);
-            return launch16<P, RC, 3, 1, 1>(st, pi, map_q, map_q8, a, w.n_ctas, s);
         }
-    }
-    if constexpr (RC <= 4) {
-        // paired 256-column items: two stages fit next to the 64 KB source tile
-        if (t->tune_pairs && w.sched_off[2]) {
-            a.cta_off = w.sched_off[2];
-            a.cta_blocks = w.sched_blocks[2];
-            a.partner = w.partner;
-            return launch16<P, RC, 2, 2, 0>(st, pi, map_q, map_q8, a, w.n_ctas, s);
-        }
-    }
-    if (t->tune_stages == 2) return launch16<P, RC, 2, 1, 0>(st, pi, map_q, map_q8, a, w.n_ctas, s);
-    return launch16<P, RC, 3, 1, 0>(st, pi, map_q, map_q8, a, w.n_ctas, s);
+        if (t->tune_stages == 2) return launch16<P, RC, 2, 1, 0>(st, pi, map_q, map_q8, a, w.n_ctas, s);
+        return launch16<P, RC, 3, 1, 0>(st, pi, map_q, map_q8, a, w.n_ctas, s);
+    };
+    ASK_TRY(ktimer_mark(t, s, false));
+    ASK_TRY(go());
+    return ktimer_mark(t, s, true);
 }
 
 template <int P>

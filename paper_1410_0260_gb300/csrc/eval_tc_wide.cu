@@ -412,7 +412,7 @@ askit_status tcw_state(askit_tree t, int pi, TcwState **out) {
 }
 
 template <int P, int RC>
-askit_status launch_w(TcwState *st, int pi, const CUtensorMap &map_q, const TcwArgs &a, int grid, cudaStream_t s) {
+askit_status launch_w(askit_tree t, TcwState *st, int pi, const CUtensorMap &map_q, const TcwArgs &a, int grid, cudaStream_t s) {
     using S = WSmem<RC>;
     const size_t smem = S::BYTES + 1024;
     static bool attr_set = false;
@@ -424,10 +424,11 @@ askit_status launch_w(TcwState *st, int pi, const CUtensorMap &map_q, const TcwA
             attr_set = true;
         }
     }
+    ASK_TRY(ktimer_mark(t, s, false));
     eval_tcw_kernel<P, RC><<<(unsigned)grid, W_THREADS, smem, s>>>(st->map[pi][0], st->map[pi][1], st->map[pi][2],
                                                                    st->map[pi][3], map_q, a);
     ASK_LAUNCH();
-    return ASKIT_OK;
+    return ktimer_mark(t, s, true);
 }
 
 }  // namespace
@@ -474,13 +475,13 @@ askit_status eval_tc_wide(askit_tree t, const WeightCtx &c, int precision, const
     a.partial = partial;
     a.status = t->d_status;
     if (precision == ASKIT_PREC_BF16X3) {
-        if (c.r == 1) return launch_w<ASKIT_PREC_BF16X3, 1>(st, pi, map_q, a, w.n_ctas, s);
-        if (c.r <= 4) return launch_w<ASKIT_PREC_BF16X3, 4>(st, pi, map_q, a, w.n_ctas, s);
-        return launch_w<ASKIT_PREC_BF16X3, 16>(st, pi, map_q, a, w.n_ctas, s);
+        if (c.r == 1) return launch_w<ASKIT_PREC_BF16X3, 1>(t, st, pi, map_q, a, w.n_ctas, s);
+        if (c.r <= 4) return launch_w<ASKIT_PREC_BF16X3, 4>(t, st, pi, map_q, a, w.n_ctas, s);
+        return launch_w<ASKIT_PREC_BF16X3, 16>(t, st, pi, map_q, a, w.n_ctas, s);
     }
-    if (c.r == 1) return launch_w<ASKIT_PREC_FP16X3, 1>(st, pi, map_q, a, w.n_ctas, s);
-    if (c.r <= 4) return launch_w<ASKIT_PREC_FP16X3, 4>(st, pi, map_q, a, w.n_ctas, s);
-    return launch_w<ASKIT_PREC_FP16X3, 16>(st, pi, map_q, a, w.n_ctas, s);
+    if (c.r == 1) return launch_w<ASKIT_PREC_FP16X3, 1>(t, st, pi, map_q, a, w.n_ctas, s);
+    if (c.r <= 4) return launch_w<ASKIT_PREC_FP16X3, 4>(t, st, pi, map_q, a, w.n_ctas, s);
+    return launch_w<ASKIT_PREC_FP16X3, 16>(t, st, pi, map_q, a, w.n_ctas, s);
 }
 
 void eval_tc_wide_free(askit_tree t) {

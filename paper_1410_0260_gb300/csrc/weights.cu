@@ -122,7 +122,7 @@ askit_status weights_reserve(askit_tree t, WeightCtx &c, int r, cudaStream_t s) 
     const int64_t srows = std::max<int64_t>(t->spool_rows, 1) + 256;
     ASK_TRY(c.arena.alloc(&c.Wt, (size_t)t->N_pad * r));
     ASK_TRY(c.arena.alloc(&c.Ws, (size_t)srows * r));
-    ASK_TRY(c.arena.alloc(&c.partial, (size_t)std::max<int64_t>(1, t->wl.n_entries) * r));
+    ASK_TRY(c.arena.alloc(&c.partial, (size_t)std::max<int64_t>(1, t->wl_entries_max) * r));
     // per-sub-block column data of the 16-bit tensor-core kernel
     if (t->n_sub > 0 && t->d <= TC_K) {
         ASK_TRY(c.arena.alloc(&c.colv, (size_t)t->n_sub * 128));

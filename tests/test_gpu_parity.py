@@ -256,3 +256,51 @@ def test_wide_rows_with_a_ragged_last_chunk():
     gtree.set_precision("fp16x3")
     Ug = gtree.evaluate_targets(torch.from_numpy(Y).cuda()).cpu().numpy()
     assert rel(Ug, Uo) <= TOL["fp16x3"]
+
+
+def test_target_batches_match_one_batch():
+    """In-sample work lists cut into batches of consecutive targets (a small
+    entry budget) give the same u as one batch: bit-identical for plain FP32
+    and FP16x3 (every entry's partial sum is computed the same way in any batch
+    and at any position of its item; also with paired items and graph replay),
+    and within the oracle tolerance for every precision (3xTF32 and BF16x3
+    centre each item on its first target, which the cut changes)."""
+    askit = _askit()
+    w = wl.MANIFOLD_1M_64.scaled(16384)
+    X, W = w.make_points(), w.make_weights()
+    kw = dict(leaf_size=512, kappa=32, knn_mode=1, rp_iters=2, s_max=256, id_tol=1e-4, h=0.35, seed=2)
+    otree, g1 = build_pair(X, kw)
+    g2 = askit.Tree(torch.from_numpy(X).cuda(), askit.Config(batch_entries=40_000, **kw))
+    i1, i2 = g1.info(), g2.info()
+    assert i1["n_batches"] == 1 and i2["n_batches"] >= 8
+    for k in ("n_entries", "pairs_algorithmic", "near_total", "far_total"):
+        assert i1[k] == i2[k], k
+    check_structures(otree, g2)
+    for prec in ("simt_fp32", "tf32x3", "bf16x3", "fp16x3"):
+        U1, Uo = eval_both(otree, g1, W, prec)
+        U2, _ = eval_both(otree, g2, W, prec)
+        assert rel(U2, Uo) <= TOL[prec], prec
+        if prec in ("simt_fp32", "fp16x3"):
+            assert np.array_equal(U1, U2), prec
+    for g in (g1, g2):
+        g.set_launch("lpt", 2, True, pairs=True)
+    U1, Uo = eval_both(otree, g1, W, "fp16x3")
+    U2, _ = eval_both(otree, g2, W, "fp16x3")
+    assert rel(U2, Uo) <= TOL["fp16x3"]
+    assert np.array_equal(U1, U2)
+    Wd = torch.from_numpy(W).cuda()
+    Ud = torch.empty((X.shape[0], 1), device="cuda")
+    graph = g2.capture(Wd, Ud)
+    graph.launch()
+    torch.cuda.synchronize()
+    assert np.array_equal(Ud.cpu().numpy(), U2)
+    # the kernel timer: one timed launch per batch and evaluation; graph
+    # replays are not timed
+    g2.kernel_timing(True)
+    g2.evaluate()
+    g2.evaluate()
+    graph.launch()
+    ms, n = g2.kernel_timing(False)
+    assert n == 2 * i2["n_batches"] and ms > 0.0
+    with pytest.raises(askit.AskitError):
+        askit.Tree(torch.from_numpy(X).cuda(), askit.Config(batch_entries=100, **kw))
