@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--cpu-n", type=int, default=65536)
     ap.add_argument("--cpu-targets", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=32, help="requests per serving run (0: no serving run)")
+    ap.add_argument("--lists", default="target", choices=["target", "leaf"],
+                    help="interaction lists: per target (eq. 2.5, the bench line's) or leaf-grouped")
     return ap.parse_args()
 
 
@@ -76,11 +78,11 @@ def workload(args):
     return w.scaled(args.n) if args.n else w
 
 
-def askit_config(w, precision):
+def askit_config(w, precision, lists="target"):
     from paper_1410_0260_gb300 import askit
     return askit.Config(leaf_size=w.leaf_size, kappa=w.kappa, knn_mode=w.knn_mode, rp_iters=w.rp_iters,
                         s_max=w.s_max, s_min=w.s_min, id_tol=w.id_tol, h=w.h, bw_mode=w.bw_mode,
-                        bw_k=w.bw_k, seed=w.seed, precision=precision)
+                        bw_k=w.bw_k, seed=w.seed, precision=precision, prune=2 if lists == "leaf" else 1)
 
 
 def measured_traffic(kernel, workload_name):
@@ -291,7 +293,7 @@ def main():
     U = torch.empty((N, r), dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    tree = askit.Tree(Xd, askit_config(w, args.precision))
+    tree = askit.Tree(Xd, askit_config(w, args.precision, args.lists))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     info = tree.info()
@@ -452,6 +454,7 @@ def main():
                        "knn": "rp-trees x%d" % w.rp_iters, "s_max": w.s_max, "s_min": w.s_min, "id_tol": w.id_tol,
                        "h": w.h if w.bw_mode == 0 else "distance to neighbor %d" % w.bw_k,
                        "r": r, "precision": args.precision, "parallelism": f"replicas x{world}",
+                       "lists": {"target": "per target (eq. 2.5)", "leaf": "leaf-grouped"}[args.lists],
                        "l2": "inputs larger than L2 (coordinates %.0f MB)" % (N * info["d_pad"] * 4 / 1e6)},
             "rel_err_vs_fp32": rel_vs_fp32, "rel_err_ok": rel_vs_fp32 <= 1e-4, "eps2_vs_direct": eps2,
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk, "roofline": roof,

@@ -75,7 +75,12 @@ typedef struct {
     int32_t s_max;       /* largest skeleton (Section 3, s) */
     int32_t s_min;       /* smallest skeleton (adaptive rank floor) */
     int32_t ell_extra;   /* sampled rows ell = s_max + ell_extra (paper: 20) */
-    int32_t prune;       /* 1: neighbor pruning eq. (2.5); 0: every leaf direct */
+    int32_t prune;       /* 1: neighbor pruning eq. (2.5) per target; 0: every leaf
+                            direct; 2: leaf-grouped lists -- every target of a leaf
+                            is pruned with the union of {p} U N_p over the leaf's
+                            points p, so the targets of a leaf share one Near and
+                            one Far list (the overlap Section 3 notes for the
+                            targets of one leaf; out-of-sample targets keep N_y) */
     int32_t bw_mode;     /* ASKIT_BW_* */
     int32_t bw_k;        /* neighbor rank for ASKIT_BW_KNN (1..kappa) */
     int32_t precision;   /* ASKIT_PREC_* used by askit_evaluate */

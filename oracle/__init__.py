@@ -196,7 +196,7 @@ class Config:
     s_max: int = 64
     s_min: int = 1
     ell_extra: int = 20
-    prune: int = 1
+    prune: int = 1              # 0 none, 1 eq. (2.5) per target, 2 leaf-grouped lists
     bw_mode: int = 0
     bw_k: int = 16
     id_tol: float = 1e-6

@@ -747,7 +747,11 @@ static void evaluate_rec(const orc_tree *t, const float *x, const int64_t *pset,
 }
 
 /* In-sample targets: rows tgt[0..T) (point ids); U [T,r].  The prune set */
-/* of target i is {i} U N_i.                                              */
+/* of target i is {i} U N_i (eq. (2.5)).  With prune == 2 (leaf-grouped   */
+/* lists) it is the union of {p} U N_p over the points p of i's leaf, so  */
+/* every target of a leaf shares one Near and one Far list -- the grouping */
+/* Section 3 points to when it notes that the direct nodes of the targets */
+/* of one leaf overlap heavily.                                           */
 void orc_evaluate(const orc_tree *t, const int64_t *tgt, int64_t T, double *U,
                   int64_t *near, int64_t *far)
 {
@@ -755,13 +759,25 @@ void orc_evaluate(const orc_tree *t, const int64_t *tgt, int64_t T, double *U,
     #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t q = 0; q < T; ++q) {
         int64_t i = tgt[q];
-        int64_t *pset = (int64_t *)malloc(sizeof(int64_t) * (kappa + 1));
-        pset[0] = t->leafof[i];
-        for (int z = 0; z < kappa; ++z) pset[z + 1] = t->leafof[t->knn[(size_t)i * kappa + z]];
+        int64_t np = 0;
+        int64_t *pset;
+        if (t->prm.prune == 2) {
+            int64_t a = t->leafof[i];
+            pset = (int64_t *)malloc(sizeof(int64_t) * t->size[a] * (kappa + 1));
+            for (int64_t v = 0; v < t->size[a]; ++v) {
+                int64_t p = t->perm[t->start[a] + v];
+                pset[np++] = t->leafof[p];
+                for (int z = 0; z < kappa; ++z) pset[np++] = t->leafof[t->knn[(size_t)p * kappa + z]];
+            }
+        } else {
+            pset = (int64_t *)malloc(sizeof(int64_t) * (kappa + 1));
+            pset[np++] = t->leafof[i];
+            for (int z = 0; z < kappa; ++z) pset[np++] = t->leafof[t->knn[(size_t)i * kappa + z]];
+        }
         double *u = U + (size_t)q * t->r;
         for (int z = 0; z < t->r; ++z) u[z] = 0.0;
         int64_t nn = 0, nf = 0;
-        evaluate_rec(t, t->X + (size_t)i * t->d, pset, kappa + 1, 1, 0, u, &nn, &nf);
+        evaluate_rec(t, t->X + (size_t)i * t->d, pset, (int)np, 1, 0, u, &nn, &nf);
         if (near) near[q] = nn;
         if (far) far[q] = nf;
         free(pset);
@@ -770,7 +786,8 @@ void orc_evaluate(const orc_tree *t, const int64_t *tgt, int64_t T, double *U,
 
 /* Out-of-sample targets y (the paper takes sources = targets; reading    */
 /* taken): the prune set of y is its exact kappa nearest sources N_y (no  */
-/* self term); then Algorithm 4 unchanged.                                */
+/* self term); then Algorithm 4 unchanged.  y belongs to no leaf, so the  */
+/* leaf-grouped mode (prune == 2) uses the same per-target set here.      */
 void orc_evaluate_oos(const orc_tree *t, const float *Y, int64_t T, double *U,
                       int32_t *knn_out, int64_t *near, int64_t *far)
 {

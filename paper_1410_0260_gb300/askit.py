@@ -140,7 +140,7 @@ class Config:
     s_max: int = 64
     s_min: int = 1
     ell_extra: int = 20
-    prune: int = 1
+    prune: int = 1              # 1 eq. (2.5) per target, 0 none, 2 leaf-grouped lists
     bw_mode: int = BW_CONSTANT
     bw_k: int = 16
     precision: str = "tf32x3"

@@ -371,13 +371,22 @@ askit_status skeletonize(askit_tree t, cudaStream_t s);
 // eval_lists.cu
 askit_status build_eval_operands(askit_tree t, cudaStream_t s);
 askit_status build_tc_operands(askit_tree t, cudaStream_t s);
-askit_status build_insample_lists(askit_tree t, const int32_t *sets, int stride, cudaStream_t s);
+// Prune sets of a set of targets: rows of `stride` sorted leaf indices
+// padded with INT_MAX; target q uses row set_row[q] (leaf-grouped lists, one
+// row per leaf) or, with set_row == nullptr, row q.  cudaMalloc'd.
+struct PruneSets {
+    int32_t *sets = nullptr;
+    int stride = 0;
+    int32_t *set_row = nullptr;
+};
+void free_prune_sets(PruneSets &ps);
+askit_status build_insample_lists(askit_tree t, const PruneSets &ps, cudaStream_t s);
 void use_schedule(askit_tree t);
-askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, int64_t T, WorkLists &w,
-                              DevArena &arena, cudaStream_t s);
+askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, const int32_t *set_row, int64_t T,
+                              WorkLists &w, DevArena &arena, cudaStream_t s);
 askit_status reduce_partials(const WorkLists &w, const float *partial, int r, const int32_t *out_rows,
                              float *U, int64_t ldu, cudaStream_t s);
-askit_status insample_prune_sets(askit_tree t, int32_t *sets, cudaStream_t s);
+askit_status insample_prune_sets(askit_tree t, PruneSets &ps, cudaStream_t s);
 askit_status oos_prune_sets(askit_tree t, const int32_t *knn, int64_t T, int stride, int32_t *sets,
                             cudaStream_t s);
 

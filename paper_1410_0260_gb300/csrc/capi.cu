@@ -111,6 +111,7 @@ askit_status validate(const askit_params *p, int64_t N, int32_t d, int64_t ldx, 
     if (p->knn_mode < 0 || p->knn_mode > 1) { askit_set_error("bad knn_mode"); return ASKIT_ERR_INVALID_ARG; }
     if (p->knn_mode == 1 && p->rp_iters < 1) { askit_set_error("rp_iters must be >= 1"); return ASKIT_ERR_INVALID_ARG; }
     if (p->precision < 0 || p->precision > 3) { askit_set_error("bad precision"); return ASKIT_ERR_INVALID_ARG; }
+    if (p->prune < 0 || p->prune > 2) { askit_set_error("prune must be 0, 1 or 2"); return ASKIT_ERR_INVALID_ARG; }
     if (p->batch_entries != 0 && (p->batch_entries < 4096 || p->batch_entries > ASK_BATCH_ENTRIES_MAX)) {
         askit_set_error("batch_entries must be 0 or in 4096..2^30");
         return ASKIT_ERR_INVALID_ARG;
@@ -210,13 +211,10 @@ askit_status setup_impl(askit_tree t, const float *X_dev, int64_t ldx, const flo
     ASK_TRY(build_eval_operands(t, s));
     ASK_TRY(build_tc_operands(t, s));
     {
-        // prune sets: {i} U N_i as leaves; with pruning off, every leaf
-        int stride = t->prm.prune ? kappa + 1 : (int)((int64_t)1 << t->L);
-        int32_t *sets = nullptr;
-        ASK_CUDA(cudaMalloc(&sets, sizeof(int32_t) * N * stride));
-        askit_status rc = insample_prune_sets(t, sets, s);
-        if (rc == ASKIT_OK) rc = build_insample_lists(t, sets, stride, s);
-        cudaFree(sets);
+        PruneSets ps;
+        askit_status rc = insample_prune_sets(t, ps, s);
+        if (rc == ASKIT_OK) rc = build_insample_lists(t, ps, s);
+        free_prune_sets(ps);
         ASK_TRY(rc);
     }
     ASK_TRY(t->arena.alloc(&t->d_status, 4));
@@ -425,7 +423,7 @@ askit_status evaluate_targets_ctx(askit_tree t, const WeightCtx &c, const float 
     gather_y_kernel<<<(unsigned)T_pad, 128, 0, s>>>(Yc, d, d, t->d_pad, order, T, T_pad, Yt, nrm);
     OTRY(tmp.alloc(&sets, (size_t)T * kappa));
     OTRY(oos_prune_sets(t, ids_s, T, kappa, sets, s));
-    OTRY(build_work_lists(t, sets, kappa, T, w, tmp, s));
+    OTRY(build_work_lists(t, sets, kappa, nullptr, T, w, tmp, s));
     OTRY(tmp.alloc(&partial, (size_t)w.n_entries * c.r));
     OTRY(run_eval(t, c, t->precision, Yt, t->d_pad, T_pad, w, partial, order, U_dev, ldu, s));
     if (cudaStreamSynchronize(s) != cudaSuccess) { askit_set_error("out-of-sample evaluate: %s", cudaGetErrorString(cudaGetLastError())); rc = ASKIT_ERR_CUDA; }

@@ -89,6 +89,49 @@ __global__ void all_leaves_sets_kernel(int64_t N, int L, int32_t *sets) {
     sets[e] = (int32_t)(M + e % M);
 }
 
+// Leaf-grouped prune sets, step 1: for the point at tree position q, its
+// own leaf and its neighbors' leaves, at q (kappa + 1) .. (q + 1)(kappa + 1);
+// a leaf's points are consecutive positions, so each leaf owns one segment.
+__global__ void leaf_keys_kernel(const int32_t *perm, const int32_t *leafof, const int32_t *knn, int64_t N,
+                                 int kappa, int32_t *keys) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= N) return;
+    const int32_t i = perm[q];
+    int32_t *o = keys + q * (kappa + 1);
+    o[0] = leafof[i];
+    for (int z = 0; z < kappa; ++z) o[z + 1] = leafof[knn[(int64_t)i * kappa + z]];
+}
+
+// Step 2 (a warp per leaf, its segment sorted): count the distinct leaves
+// (stride == 0), or write them to the leaf's row of `stride` entries padded
+// with INT_MAX.
+__global__ void leaf_unique_kernel(const int32_t *keys, const int32_t *beg, const int32_t *end, int stride,
+                                   int32_t *rows, int32_t *cnt) {
+    const int a = blockIdx.x, lane = threadIdx.x;
+    const int32_t b0 = beg[a], b1 = end[a];
+    int n = 0;
+    for (int32_t base = b0; base < b1; base += 32) {
+        const int32_t e = base + lane;
+        const bool in = e < b1;
+        const int32_t v = in ? keys[e] : 0;
+        const bool first = in && (e == b0 || keys[e - 1] != v);
+        const unsigned m = __ballot_sync(0xffffffffu, first);
+        if (stride > 0 && first) rows[(int64_t)a * stride + n + __popc(m & ((1u << lane) - 1u))] = v;
+        n += __popc(m);
+    }
+    if (stride > 0)
+        for (int u = n + lane; u < stride; u += 32) rows[(int64_t)a * stride + u] = INT_MAX;
+    else if (lane == 0)
+        cnt[a] = n;
+}
+
+// Step 3: each target's row is its leaf's.
+__global__ void leaf_row_kernel(const int32_t *perm, const int32_t *leafof, int64_t N, int32_t M, int32_t *row) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= N) return;
+    row[q] = leafof[perm[q]] - M;
+}
+
 // Out-of-sample prune sets: distinct leaves of N_y (no self term).
 __global__ void oos_sets_kernel(const int32_t *leafof, const int32_t *knn, int64_t T, int kappa,
                                 int stride, int32_t *sets) {
@@ -124,8 +167,15 @@ __device__ __forceinline__ void walk_lists(const int32_t *set, int stride, int L
             int32_t b = set[u] >> sh;
             if (u > 0 && (set[u - 1] >> sh) == b) continue;   // ancestor already handled
             int32_t sib = b ^ 1;
-            bool inU = false;
-            for (int w = 0; w < n && !inU; ++w) inU = ((set[w] >> sh) == sib);
+            // the set is sorted, so the leaves under sib form one run: find
+            // the first leaf >= sib's first leaf
+            const int32_t lo = sib << sh;
+            int a = 0, z = n;
+            while (a < z) {
+                const int mid = (a + z) >> 1;
+                if (set[mid] < lo) a = mid + 1; else z = mid;
+            }
+            const bool inU = a < n && (set[a] >> sh) == sib;
             if (!inU) emit(sib, true);
         }
     }
@@ -142,12 +192,18 @@ __device__ __forceinline__ uint32_t sub_key(int32_t node, int chunk, bool far) {
     return ((uint32_t)node << 5) | ((uint32_t)chunk << 1) | (far ? 1u : 0u);
 }
 
-__global__ void count_kernel(const int32_t *sets, int stride, int64_t T, int L, const int32_t *nsize,
-                             const int32_t *s, int64_t *cnt, int64_t *nearc, int64_t *farc, int64_t *pairs) {
+// Prune-set row of target q: its own row, or a shared one (leaf-grouped).
+__device__ __forceinline__ const int32_t *set_of(const int32_t *sets, int stride, const int32_t *set_row, int64_t q) {
+    return sets + (set_row ? (int64_t)set_row[q] : q) * stride;
+}
+
+__global__ void count_kernel(const int32_t *sets, int stride, const int32_t *set_row, int64_t T, int L,
+                             const int32_t *nsize, const int32_t *s, int64_t *cnt, int64_t *nearc, int64_t *farc,
+                             int64_t *pairs) {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= T) return;
     int64_t c = 0, nf = 0, nn = 0, pr = 0;
-    walk_lists(sets + q * stride, stride, L, [&](int32_t node, bool far) {
+    walk_lists(set_of(sets, stride, set_row, q), stride, L, [&](int32_t node, bool far) {
         int rows = block_rows(node, far, nsize, s);
         c += (rows + ASK_BLK_N - 1) / ASK_BLK_N;
         pr += rows;
@@ -159,12 +215,13 @@ __global__ void count_kernel(const int32_t *sets, int stride, int64_t T, int L, 
     pairs[q] = pr;
 }
 
-__global__ void emit_kernel(const int32_t *sets, int stride, int64_t T, int L, const int32_t *nsize,
-                            const int32_t *s, const int64_t *off, uint64_t *keys, int64_t *vals) {
+__global__ void emit_kernel(const int32_t *sets, int stride, const int32_t *set_row, int64_t T, int L,
+                            const int32_t *nsize, const int32_t *s, const int64_t *off, uint64_t *keys,
+                            int64_t *vals) {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= T) return;
     int64_t o = off[q];
-    walk_lists(sets + q * stride, stride, L, [&](int32_t node, bool far) {
+    walk_lists(set_of(sets, stride, set_row, q), stride, L, [&](int32_t node, bool far) {
         int rows = block_rows(node, far, nsize, s);
         for (int ch = 0; ch * ASK_BLK_N < rows; ++ch) {
             keys[o] = ((uint64_t)sub_key(node, ch, far) << 32) | (uint64_t)q;
@@ -453,14 +510,76 @@ askit_status build_tc_operands(askit_tree t, cudaStream_t s) {
     return ASKIT_OK;
 }
 
-askit_status insample_prune_sets(askit_tree t, int32_t *sets, cudaStream_t s) {
+void free_prune_sets(PruneSets &ps) {
+    if (ps.sets) cudaFree(ps.sets);
+    if (ps.set_row) cudaFree(ps.set_row);
+    ps = PruneSets();
+}
+
+// Leaf-grouped prune sets: the sorted distinct leaves of {p} U N_p over the
+// points p of each leaf (one row per leaf), and every target's row index.
+askit_status leaf_prune_sets(askit_tree t, PruneSets &ps, cudaStream_t s) {
+    const int64_t N = t->N, M = (int64_t)1 << t->L, k1 = t->kappa + 1;
+    if (N * k1 >= ((int64_t)1 << 31)) {
+        askit_set_error("leaf-grouped lists need N (kappa + 1) < 2^31");
+        return ASKIT_ERR_UNSUPPORTED;
+    }
+    int32_t *keys = nullptr, *keys_s = nullptr, *beg = nullptr, *cnt = nullptr;
+    void *tmp = nullptr;
+    size_t tb = 0;
+    askit_status rc = ASKIT_OK;
+    std::vector<int32_t> hb(2 * M), hc(M);
+    for (int64_t a = 0; a < M; ++a) {
+        hb[a] = (int32_t)(t->h_start[M + a] * k1);
+        hb[M + a] = (int32_t)((t->h_start[M + a] + t->h_size[M + a]) * k1);
+    }
+    int mx = 0;
+#define PCHK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { askit_set_error("leaf prune sets: %s", cudaGetErrorString(e_)); rc = e_ == cudaErrorMemoryAllocation ? ASKIT_ERR_OOM : ASKIT_ERR_CUDA; goto out; } } while (0)
+#define PTRY(x) do { rc = (x); if (rc != ASKIT_OK) goto out; } while (0)
+    PCHK(cudaMalloc(&keys, sizeof(int32_t) * N * k1));
+    PCHK(cudaMalloc(&keys_s, sizeof(int32_t) * N * k1));
+    PCHK(cudaMalloc(&beg, sizeof(int32_t) * 2 * M));
+    PCHK(cudaMalloc(&cnt, sizeof(int32_t) * M));
+    PCHK(cudaMemcpyAsync(beg, hb.data(), sizeof(int32_t) * 2 * M, cudaMemcpyHostToDevice, s));
+    leaf_keys_kernel<<<nblk(N, 128), 128, 0, s>>>(t->perm, t->leafof, t->knn, N, t->kappa, keys);
+    PCHK(cudaGetLastError());
+    PTRY(seg_sort_i32(nullptr, nullptr, N * k1, (int)M, beg, beg + M, nullptr, &tb, s));
+    PCHK(cudaMalloc(&tmp, tb));
+    PTRY(seg_sort_i32(keys, keys_s, N * k1, (int)M, beg, beg + M, tmp, &tb, s));
+    leaf_unique_kernel<<<(unsigned)M, 32, 0, s>>>(keys_s, beg, beg + M, 0, nullptr, cnt);
+    PCHK(cudaGetLastError());
+    PCHK(cudaMemcpyAsync(hc.data(), cnt, sizeof(int32_t) * M, cudaMemcpyDeviceToHost, s));
+    PCHK(cudaStreamSynchronize(s));
+    for (int64_t a = 0; a < M; ++a) mx = std::max(mx, hc[a]);
+    ps.stride = std::max(mx, 1);
+    PCHK(cudaMalloc(&ps.sets, sizeof(int32_t) * M * ps.stride));
+    PCHK(cudaMalloc(&ps.set_row, sizeof(int32_t) * N));
+    leaf_unique_kernel<<<(unsigned)M, 32, 0, s>>>(keys_s, beg, beg + M, ps.stride, ps.sets, cnt);
+    leaf_row_kernel<<<nblk(N, 256), 256, 0, s>>>(t->perm, t->leafof, N, (int32_t)M, ps.set_row);
+    PCHK(cudaGetLastError());
+    PCHK(cudaStreamSynchronize(s));
+out:
+#undef PCHK
+#undef PTRY
+    for (void *q : {(void *)keys, (void *)keys_s, (void *)beg, (void *)cnt, tmp})
+        if (q) cudaFree(q);
+    if (rc != ASKIT_OK) free_prune_sets(ps);
+    return rc;
+}
+
+askit_status insample_prune_sets(askit_tree t, PruneSets &ps, cudaStream_t s) {
+    if (t->prm.prune == 2) return leaf_prune_sets(t, ps, s);
+    // {i} U N_i as leaves; with pruning off, every leaf
+    ps.stride = t->prm.prune ? t->kappa + 1 : (int)((int64_t)1 << t->L);
+    ps.set_row = nullptr;
+    ASK_CUDA(cudaMalloc(&ps.sets, sizeof(int32_t) * t->N * ps.stride));
     if (!t->prm.prune) {
         int64_t n = t->N << t->L;
-        all_leaves_sets_kernel<<<nblk(n, 256), 256, 0, s>>>(t->N, t->L, sets);
+        all_leaves_sets_kernel<<<nblk(n, 256), 256, 0, s>>>(t->N, t->L, ps.sets);
         ASK_LAUNCH();
         return ASKIT_OK;
     }
-    insample_sets_kernel<<<nblk(t->N, 128), 128, 0, s>>>(t->perm, t->leafof, t->knn, t->N, t->kappa, sets);
+    insample_sets_kernel<<<nblk(t->N, 128), 128, 0, s>>>(t->perm, t->leafof, t->knn, t->N, t->kappa, ps.sets);
     ASK_LAUNCH();
     return ASKIT_OK;
 }
@@ -479,8 +598,8 @@ askit_status oos_prune_sets(askit_tree t, const int32_t *knn, int64_t T, int str
 // the entry's target; reduce() then sums each target's entries in emission
 // order (Near leaves ascending, then Far nodes from the deepest level up),
 // which is fixed, so the result does not depend on scheduling.
-askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, int64_t T, WorkLists &wlst,
-                              DevArena &arena, cudaStream_t s) {
+askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, const int32_t *set_row, int64_t T,
+                              WorkLists &wlst, DevArena &arena, cudaStream_t s) {
     int64_t *cnt = nullptr, *nearc = nullptr, *farc = nullptr, *pairs = nullptr, *vals = nullptr, *emit_of = nullptr;
     int64_t *bflag = nullptr, *bidx = nullptr, *bstart = nullptr, *iflag = nullptr, *iidx = nullptr;
     uint64_t *keys = nullptr, *keys_s = nullptr;
@@ -500,7 +619,8 @@ askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, int
     WCHK(cudaMallocAsync(&pairs, sizeof(int64_t) * T, s));
     WTRY(arena.alloc(&w.off, T + 1));
     WCHK(cudaMemsetAsync(cnt + T, 0, sizeof(int64_t), s));
-    count_kernel<<<nblk(T, 128), 128, 0, s>>>(sets, stride, T, t->L, t->nsize, t->d_s, cnt, nearc, farc, pairs);
+    count_kernel<<<nblk(T, 128), 128, 0, s>>>(sets, stride, set_row, T, t->L, t->nsize, t->d_s, cnt, nearc, farc,
+                                              pairs);
     WCHK(cudaGetLastError());
     WTRY(scan_i64(nullptr, nullptr, T + 1, nullptr, &tb, s));
     WCHK(cudaMallocAsync(&tmp, tb, s));
@@ -517,7 +637,7 @@ askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, int
     WCHK(cudaMallocAsync(&keys_s, sizeof(uint64_t) * total, s));
     WCHK(cudaMallocAsync(&vals, sizeof(int64_t) * total, s));
     WCHK(cudaMallocAsync(&emit_of, sizeof(int64_t) * total, s));
-    emit_kernel<<<nblk(T, 128), 128, 0, s>>>(sets, stride, T, t->L, t->nsize, t->d_s, w.off, keys, vals);
+    emit_kernel<<<nblk(T, 128), 128, 0, s>>>(sets, stride, set_row, T, t->L, t->nsize, t->d_s, w.off, keys, vals);
     WCHK(cudaGetLastError());
     WTRY(sort_u64_i64(nullptr, nullptr, nullptr, nullptr, total, nullptr, &tb, s));
     WTRY(scan_i64(nullptr, nullptr, total, nullptr, &tb2, s));
@@ -736,15 +856,17 @@ out:
 // running batch past the entry budget.  A sub-block's items and a pair's
 // matching lists never straddle a cut (both are lists of targets), and every
 // entry's partial sum is computed the same way in whichever batch holds it.
-askit_status build_insample_lists(askit_tree t, const int32_t *sets, int stride, cudaStream_t s) {
+askit_status build_insample_lists(askit_tree t, const PruneSets &ps, cudaStream_t s) {
     const int64_t N = t->N;
+    const int32_t *sets = ps.sets, *set_row = ps.set_row;
+    const int stride = ps.stride;
     const int64_t budget = t->prm.batch_entries > 0 ? t->prm.batch_entries : ASK_BATCH_ENTRIES;
     std::vector<int64_t> h_cnt(N);
     {
         int64_t *buf = nullptr;
         ASK_CUDA(cudaMallocAsync(&buf, sizeof(int64_t) * 4 * N, s));
-        count_kernel<<<nblk(N, 128), 128, 0, s>>>(sets, stride, N, t->L, t->nsize, t->d_s, buf, buf + N, buf + 2 * N,
-                                                  buf + 3 * N);
+        count_kernel<<<nblk(N, 128), 128, 0, s>>>(sets, stride, set_row, N, t->L, t->nsize, t->d_s, buf, buf + N,
+                                                  buf + 2 * N, buf + 3 * N);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt.data(), buf, sizeof(int64_t) * N, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -767,7 +889,11 @@ askit_status build_insample_lists(askit_tree t, const int32_t *sets, int stride,
     t->wl_entries = t->wl_entries_max = 0;
     for (size_t b = 0; b < nb; ++b) {
         const int64_t t0 = t->wl_t0[b], T = t->wl_t0[b + 1] - t0;
-        ASK_TRY(build_work_lists(t, sets + t0 * stride, stride, T, t->wl[b], t->arena, s));
+        // a batch's targets start at t0: shift the shared-row index, or the rows
+        if (set_row)
+            ASK_TRY(build_work_lists(t, sets, stride, set_row + t0, T, t->wl[b], t->arena, s));
+        else
+            ASK_TRY(build_work_lists(t, sets + t0 * stride, stride, nullptr, T, t->wl[b], t->arena, s));
         if (t->wl[b].n_entries >= ((int64_t)1 << 31)) {
             askit_set_error("a single target has more than 2^31 work entries");
             return ASKIT_ERR_UNSUPPORTED;

@@ -363,19 +363,31 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                     // 32-column chunks; the TMEM load of chunk c + 1 is in flight
                     // while chunk c is computed (two register buffers)
                     const int nch = (nrows + 31) >> 5;
-                    uint32_t ga[32], gb[32];
-                    tmem_ld32_async(tbase, ga);
-                    tmem_wait_pin(ga);
+                    if constexpr (RC >= 16) {
+                        // r = 16: the weight sums give each chunk enough work to
+                        // cover the load; one buffer leaves registers to them
+                        uint32_t ga[32];
 #pragma unroll 1
-                    for (int c = 0; c < nch; c += 2) {
-                        const bool h1 = c + 1 < nch, h2 = c + 2 < nch;   // warp-uniform
-                        if (h1) tmem_ld32_async(tbase + (uint32_t)((c + 1) * 32), gb);
-                        cols(c, ga);
-                        if (h1) {
-                            tmem_wait_pin(gb);
-                            if (h2) tmem_ld32_async(tbase + (uint32_t)((c + 2) * 32), ga);
-                            cols(c + 1, gb);
-                            if (h2) tmem_wait_pin(ga);
+                        for (int c = 0; c < nch; ++c) {
+                            tmem_ld32_async(tbase + (uint32_t)(c * 32), ga);
+                            tmem_wait_pin(ga);
+                            cols(c, ga);
+                        }
+                    } else {
+                        uint32_t ga[32], gb[32];
+                        tmem_ld32_async(tbase, ga);
+                        tmem_wait_pin(ga);
+#pragma unroll 1
+                        for (int c = 0; c < nch; c += 2) {
+                            const bool h1 = c + 1 < nch, h2 = c + 2 < nch;   // warp-uniform
+                            if (h1) tmem_ld32_async(tbase + (uint32_t)((c + 1) * 32), gb);
+                            cols(c, ga);
+                            if (h1) {
+                                tmem_wait_pin(gb);
+                                if (h2) tmem_ld32_async(tbase + (uint32_t)((c + 2) * 32), ga);
+                                cols(c + 1, gb);
+                                if (h2) tmem_wait_pin(ga);
+                            }
                         }
                     }
                     if constexpr (RC == 1) {

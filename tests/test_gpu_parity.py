@@ -304,3 +304,31 @@ def test_target_batches_match_one_batch():
     assert n == 2 * i2["n_batches"] and ms > 0.0
     with pytest.raises(askit.AskitError):
         askit.Tree(torch.from_numpy(X).cuda(), askit.Config(batch_entries=100, **kw))
+
+
+def test_leaf_grouped_lists_match_oracle():
+    """Leaf-grouped interaction lists (prune = 2): the list counts equal the
+    oracle's exactly, u matches the oracle's Evaluate in every precision, and
+    target batches change no bit of the plain FP32 and FP16x3 results."""
+    askit = _askit()
+    w = wl.MANIFOLD_1M_64.scaled(8192)
+    X, W = w.make_points(), w.make_weights()
+    kw = dict(leaf_size=256, kappa=16, knn_mode=1, rp_iters=2, s_max=64, id_tol=1e-4, h=0.35, seed=2, prune=2)
+    otree, gtree = build_pair(X, kw)
+    check_structures(otree, gtree)
+    otree.set_weights(W.astype(np.float64))
+    _, near, far = otree.evaluate(counts=True)
+    info = gtree.info()
+    assert info["near_total"] == int(near.sum()) and info["far_total"] == int(far.sum())
+    perm = otree.perm()
+    leaf_of_slot = np.arange(X.shape[0]) // 256           # N = 2^k m: every leaf holds m points
+    nt = near[perm]
+    assert all(len(set(nt[leaf_of_slot == a])) == 1 for a in range(X.shape[0] // 256))
+    gb = askit.Tree(torch.from_numpy(X).cuda(), askit.Config(batch_entries=20_000, **kw))
+    assert gb.info()["n_batches"] >= 4
+    for prec in ("simt_fp32", "tf32x3", "bf16x3", "fp16x3"):
+        Ug, Uo = eval_both(otree, gtree, W, prec)
+        assert rel(Ug, Uo) <= TOL[prec], prec
+        if prec in ("simt_fp32", "fp16x3"):
+            Ub, _ = eval_both(otree, gb, W, prec)
+            assert np.array_equal(Ug, Ub), prec
