@@ -70,8 +70,8 @@ struct S16 {
     static constexpr int COLW_BYTES = RC > 1 ? NB * 128 * RC * 4 : 0;
     static constexpr int BLKSLOT = BLK_COLW + COLW_BYTES;
     static constexpr int ANORM = BLK + 2 * BLKSLOT;           // float [NACC][128] |a|^2
-    static constexpr int BAR = ANORM + 4 * 128 * 4;           // 24 mbarriers
-    static constexpr int MISC = BAR + 24 * 8;                 // tmem address, abort flag
+    static constexpr int BAR = ANORM + 4 * 128 * 4;           // 28 mbarriers
+    static constexpr int MISC = BAR + 28 * 8;                 // tmem address, abort flag
     static constexpr int BYTES = MISC + 16;
 };
 
@@ -129,6 +129,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
     auto BAR_BLK_EMPTY = [&](int s) { return bar0 + 8 * (14 + s); }; // epilogue done with slot s (128)
     auto BAR_T_FULL = [&](int a) { return bar0 + 8 * (16 + a); };    // accumulator a complete (commit)
     auto BAR_T_EMPTY = [&](int a) { return bar0 + 8 * (20 + a); };   // epilogue drained accumulator a (128)
+    auto BAR_N_EMPTY = [&](int a) { return bar0 + 8 * (24 + a); };   // epilogue read |a|^2 slot a (128)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + S::MISC);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + S::MISC + 4);
 
@@ -149,6 +150,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
         for (int a = 0; a < NACC; ++a) {
             mbar_init(BAR_T_FULL(a), 1);
             mbar_init(BAR_T_EMPTY(a), 128);
+            mbar_init(BAR_N_EMPTY(a), 128);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -192,7 +194,9 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                 if (it + 2 < i1) cnt_next = args.items[it + 2].cnt;   // in flight while this item waits
                 const int sa = li & 1, sr = li % NRAW, a4 = li % NACC;
                 if (!mbar_wait(BAR_A_EMPTY(sa), ((li >> 1) & 1) ^ 1, abort_flag, args.status)) goto loader_done;
-                if (!mbar_wait(BAR_T_EMPTY(a4), ((li / NACC) & 1) ^ 1, abort_flag, args.status)) goto loader_done;
+                // the |a|^2 slot of this item's accumulator: free once the
+                // epilogue of the item NACC back has read it (at its start)
+                if (!mbar_wait(BAR_N_EMPTY(a4), ((li / NACC) & 1) ^ 1, abort_flag, args.status)) goto loader_done;
                 if (!mbar_wait(BAR_R_FULL(sr), (li / NRAW) & 1, abort_flag, args.status)) goto loader_done;
                 if (need_blk) {
                     if (!mbar_wait(BAR_BLK_FULL(lb & 1), (lb >> 1) & 1, abort_flag, args.status)) goto loader_done;
@@ -282,6 +286,8 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                 const int e0f = pb >= 0 ? args.items[f0 + (it - i0)].e0 : 0;
                 if (!mbar_wait(BAR_T_FULL(a4), (li / NACC) & 1, abort_flag, args.status)) goto epi_done;
                 tc_fence_after();
+                const float pt = a_norm[a4 * 128 + row];   // NACC <= 4 slots
+                mbar_arrive(BAR_N_EMPTY(a4));
                 float acc[RC];
 #pragma unroll
                 for (int z = 0; z < RC; ++z) acc[z] = 0.f;
@@ -293,7 +299,6 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                 const int qs = UNI == 2 && row < item.cnt ? args.tgt[item.e0 + row] : -1;
                 const float qu = qs >= 0 ? args.knn_u[qs] : 0.f;
                 if (q * 32 < item.cnt) {   // warp-uniform: skip quadrants with no target
-                    const float pt = a_norm[a4 * 128 + row];   // NACC <= 4 slots
                     const float2 pt2 = make_float2(pt, pt);
                     // arg = g A + (C p + B) = -sc (p + q - 2 g / scale^2); columns past
                     // nrows carry A = B = C = w = 0
