@@ -18,13 +18,16 @@
 // is built once per Evaluate (tc16_cols_kernel) and bulk-copied with the
 // sub-block, so the loaders only center and split target rows.
 //
-// One CTA per SM, 448 threads:
-//   warps 0-7  two loader groups taking alternate items: each warp centers
-//              and splits 32 target rows (gathered by warp 13), two rows at a
-//              time, into the 128-byte swizzled K-major layout and forms
-//              |a|^2 in a fixed order;
-//   warps 8-11 epilogue: tcgen05.ld of their 32 TMEM lanes (one row each),
-//              exponent on MUFU.EX2, reduction against the weights;
+// One CTA per SM, 448 threads (r <= 4; r = 16 in brackets):
+//   warps 0-3  loaders [0-7: two groups taking alternate items]: each warp
+//              centers and splits 32 target rows (gathered by warp 13), two
+//              rows at a time, into the 128-byte swizzled K-major layout and
+//              forms |a|^2 in a fixed order;
+//   warps 4-11 two epilogue groups, each taking one half of every item's
+//              columns [8-11: one group, all columns]: tcgen05.ld of their
+//              32 TMEM lanes (one row each), exponent on MUFU.EX2, reduction
+//              against the weights; the second half's sums reach the first
+//              group through shared memory and are added last;
 //   warp 12    TMEM allocation; lane 0 loads each sub-block (TMA tiles of the
 //              pre-split rows, bulk copies of its center and column data)
 //              and issues the tcgen05.mma instructions;
@@ -70,8 +73,10 @@ struct S16 {
     static constexpr int COLW_BYTES = RC > 1 ? NB * 128 * RC * 4 : 0;
     static constexpr int BLKSLOT = BLK_COLW + COLW_BYTES;
     static constexpr int ANORM = BLK + 2 * BLKSLOT;           // float [NACC][128] |a|^2
-    static constexpr int BAR = ANORM + 4 * 128 * 4;           // 28 mbarriers
-    static constexpr int MISC = BAR + 28 * 8;                 // tmem address, abort flag
+    static constexpr bool EPI2 = RC <= 4;                     // two epilogue groups (column halves)
+    static constexpr int XBUF = ANORM + 4 * 128 * 4;          // float [NACC][128][RC]: second half's sums
+    static constexpr int BAR = XBUF + (EPI2 ? 4 * 128 * RC * 4 : 0);   // 32 mbarriers
+    static constexpr int MISC = BAR + 32 * 8;                 // tmem address, abort flag
     static constexpr int BYTES = MISC + 16;
 };
 
@@ -113,6 +118,15 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                  const T16Args args) {
     using S = S16<RC, NRAW, NB>;
     constexpr int NACC = S::NACC;
+    // r <= 4: one loader group (warps 0-3) and two epilogue groups (warps
+    // 4-7 and 8-11) that take the two halves of each item's columns, so two
+    // warps per SM sub-partition share the exponentials; r = 16: two loader
+    // groups taking alternate items and one epilogue group (its weight sums
+    // leave no room for the exchange buffer)
+    constexpr bool EPI2 = S::EPI2;
+    constexpr int NLG = EPI2 ? 1 : 2;
+    constexpr int EPI_W0 = 4 * NLG;
+    constexpr int NEPI = (12 - EPI_W0) * 32;
     static_assert(!UNI || RC == 1, "the uniform-bandwidth and kNN layouts serve r = 1");
     constexpr uint32_t FMT = P == ASKIT_PREC_BF16X3 ? 1u : 0u;
     extern __shared__ uint8_t smem_raw[];
@@ -129,7 +143,8 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
     auto BAR_BLK_EMPTY = [&](int s) { return bar0 + 8 * (14 + s); }; // epilogue done with slot s (128)
     auto BAR_T_FULL = [&](int a) { return bar0 + 8 * (16 + a); };    // accumulator a complete (commit)
     auto BAR_T_EMPTY = [&](int a) { return bar0 + 8 * (20 + a); };   // epilogue drained accumulator a (128)
-    auto BAR_N_EMPTY = [&](int a) { return bar0 + 8 * (24 + a); };   // epilogue read |a|^2 slot a (128)
+    auto BAR_N_EMPTY = [&](int a) { return bar0 + 8 * (24 + a); };   // epilogue read |a|^2 slot a (NEPI)
+    auto BAR_X_FULL = [&](int a) { return bar0 + 8 * (28 + a); };    // second epilogue half's sums of a (128)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + S::MISC);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + S::MISC + 4);
 
@@ -139,7 +154,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
             mbar_init(BAR_A_FULL(s), 128);
             mbar_init(BAR_A_EMPTY(s), 1);
             mbar_init(BAR_BLK_FULL(s), 1);
-            mbar_init(BAR_BLK_EMPTY(s), 128);
+            mbar_init(BAR_BLK_EMPTY(s), NEPI);
         }
         for (int s = 0; s < NRAW; ++s) {
             mbar_init(BAR_R_FULL(s), 1);
@@ -149,8 +164,9 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
         mbar_init(BAR_B_EMPTY, 1);
         for (int a = 0; a < NACC; ++a) {
             mbar_init(BAR_T_FULL(a), 1);
-            mbar_init(BAR_T_EMPTY(a), 128);
-            mbar_init(BAR_N_EMPTY(a), 128);
+            mbar_init(BAR_T_EMPTY(a), NEPI);
+            mbar_init(BAR_N_EMPTY(a), NEPI);
+            mbar_init(BAR_X_FULL(a), 128);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -166,7 +182,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
     const uint32_t tmem = *tmem_slot;
     const int c_begin = args.cta_off[blockIdx.x], c_end = args.cta_off[blockIdx.x + 1];
 
-    if (warp < 8) {
+    if (warp < EPI_W0) {
         // ------------------------------------------------------------ loaders
         // A warp converts its 32 rows two at a time: lane (h, k) takes
         // 4-coordinate chunk k of row 2i + h, so each half-warp reads one
@@ -187,11 +203,12 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
             bool need_blk = true;
             float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);   // this lane's chunk of c_B
             // this group's first item of the block: li and it advance together
-            int cnt_next = (i0 + ((grp - li) & 1) < i1) ? args.items[i0 + ((grp - li) & 1)].cnt : 0;
+            const int first = i0 + (NLG == 2 ? ((grp - li) & 1) : 0);
+            int cnt_next = first < i1 ? args.items[first].cnt : 0;
             for (int it = i0; it < i1; ++it, ++li) {
-                if ((li & 1) != grp) continue;
+                if (NLG == 2 && (li & 1) != grp) continue;
                 const int cnt = cnt_next;
-                if (it + 2 < i1) cnt_next = args.items[it + 2].cnt;   // in flight while this item waits
+                if (it + NLG < i1) cnt_next = args.items[it + NLG].cnt;   // in flight while this item waits
                 const int sa = li & 1, sr = li % NRAW, a4 = li % NACC;
                 if (!mbar_wait(BAR_A_EMPTY(sa), ((li >> 1) & 1) ^ 1, abort_flag, args.status)) goto loader_done;
                 // the |a|^2 slot of this item's accumulator: free once the
@@ -263,8 +280,9 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
     loader_done:;
     } else if (warp < 12) {
         // ----------------------------------------------------------- epilogue
-        const int row = tid - 256;                 // TMEM lane = target row of the item
         const int q = warp & 3;                    // this warp's TMEM lane quadrant
+        const int row = q * 32 + lane;             // TMEM lane = target row of the item
+        const int eg = EPI2 ? (warp - 4) >> 2 : 0; // column half of this group
         int li = 0, lb = 0;
         for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci, ++lb) {
             const int b = args.cta_blocks[ci];
@@ -366,25 +384,48 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                     };
                     const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a4 * 128 * NB);
                     // 32-column chunks; the TMEM load of chunk c + 1 is in flight
-                    // while chunk c is computed (two register buffers)
+                    // while chunk c is computed (two register buffers).  With two
+                    // groups, group g takes chunks [c_lo, c_hi) of its half.
                     const int nch = (nrows + 31) >> 5;
+                    const int hch = EPI2 ? (nch + 1) >> 1 : nch;
+                    const int c_lo = eg * hch, c_hi = min(nch, c_lo + hch);
                     if constexpr (RC >= 16) {
                         // r = 16: the weight sums give each chunk enough work to
-                        // cover the load; one buffer leaves registers to them
+                        // cover the load; one buffer leaves registers to them.  The
+                        // two column halves are summed apart and then added, the
+                        // order the two-group epilogue of r <= 4 uses, so a weight
+                        // vector's result does not depend on how many others share
+                        // its evaluation
+                        const int hsplit = (nch + 1) >> 1;
+                        float2 h0[RC / 2];
                         uint32_t ga[32];
 #pragma unroll 1
                         for (int c = 0; c < nch; ++c) {
+                            if (c == hsplit) {
+#pragma unroll
+                                for (int z = 0; z < RC / 2; ++z) {
+                                    h0[z] = accw[z];
+                                    accw[z] = make_float2(0.f, 0.f);
+                                }
+                            }
                             tmem_ld32_async(tbase + (uint32_t)(c * 32), ga);
                             tmem_wait_pin(ga);
                             cols(c, ga);
                         }
-                    } else {
+                        if (nch > hsplit) {
+#pragma unroll
+                            for (int z = 0; z < RC / 2; ++z) accw[z] = __fadd2_rn(h0[z], accw[z]);
+                        } else {
+#pragma unroll
+                            for (int z = 0; z < RC / 2; ++z) accw[z] = __fadd2_rn(accw[z], make_float2(0.f, 0.f));
+                        }
+                    } else if (c_lo < c_hi) {
                         uint32_t ga[32], gb[32];
-                        tmem_ld32_async(tbase, ga);
+                        tmem_ld32_async(tbase + (uint32_t)(c_lo * 32), ga);
                         tmem_wait_pin(ga);
 #pragma unroll 1
-                        for (int c = 0; c < nch; c += 2) {
-                            const bool h1 = c + 1 < nch, h2 = c + 2 < nch;   // warp-uniform
+                        for (int c = c_lo; c < c_hi; c += 2) {
+                            const bool h1 = c + 1 < c_hi, h2 = c + 2 < c_hi;   // warp-uniform
                             if (h1) tmem_ld32_async(tbase + (uint32_t)((c + 1) * 32), gb);
                             cols(c, ga);
                             if (h1) {
@@ -406,6 +447,22 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                     }
                 }
                 tc_fence_before();
+                if constexpr (EPI2) {
+                    // the second half's sums go to the first group through shared
+                    // memory; the first group releases the accumulator only after
+                    // reading them, so the buffer is free when the slot is reused
+                    float *xb = reinterpret_cast<float *>(sm + S::XBUF) + (a4 * 128 + row) * RC;
+                    if (eg == 1) {
+#pragma unroll
+                        for (int z = 0; z < RC; ++z) xb[z] = acc[z];
+                        mbar_arrive(BAR_X_FULL(a4));
+                        mbar_arrive(BAR_T_EMPTY(a4));
+                        continue;
+                    }
+                    if (!mbar_wait(BAR_X_FULL(a4), (li / NACC) & 1, abort_flag, args.status)) goto epi_done;
+#pragma unroll
+                    for (int z = 0; z < RC; ++z) acc[z] += xb[z];
+                }
                 mbar_arrive(BAR_T_EMPTY(a4));
                 if (UNI != 2 && row < item.cnt) {
                     float *p = args.partial + (int64_t)(item.e0 + row) * args.r;
