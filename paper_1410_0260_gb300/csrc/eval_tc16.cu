@@ -18,21 +18,21 @@
 // is built once per Evaluate (tc16_cols_kernel) and bulk-copied with the
 // sub-block, so the loaders only center and split target rows.
 //
-// One CTA per SM, 448 threads (r <= 4; r = 16 in brackets):
-//   warps 0-3  loaders [0-7: two groups taking alternate items]: each warp
-//              centers and splits 32 target rows (gathered by warp 13), two
-//              rows at a time, into the 128-byte swizzled K-major layout and
-//              forms |a|^2 in a fixed order;
-//   warps 4-11 two epilogue groups, each taking one half of every item's
-//              columns [8-11: one group, all columns]: tcgen05.ld of their
-//              32 TMEM lanes (one row each), exponent on MUFU.EX2, reduction
-//              against the weights; the second half's sums reach the first
-//              group through shared memory and are added last;
-//   warp 12    TMEM allocation; lane 0 loads each sub-block (TMA tiles of the
-//              pre-split rows, bulk copies of its center and column data)
-//              and issues the tcgen05.mma instructions;
-//   warp 13    TMA tile::gather4 of each item's target rows (8-row tiled boxes
-//              for runs of consecutive rows), two or three stages.
+// One CTA per SM; r <= 4: 576 threads (r = 16: 448, numbers in brackets):
+//   warps 0-7   two loader groups taking alternate items: each warp centers
+//               and splits 32 target rows (gathered by the last warp), two
+//               rows at a time, into the 128-byte swizzled K-major layout and
+//               forms |a|^2 in a fixed order;
+//   warps 8-15  two epilogue groups, each taking one half of every item's
+//               columns [8-11: one group, all columns]: tcgen05.ld of their
+//               32 TMEM lanes (one row each), exponent on MUFU.EX2, reduction
+//               against the weights; the second half's sums reach the first
+//               group through shared memory and are added last;
+//   warp 16 [12] TMEM allocation; lane 0 loads each sub-block (TMA tiles of
+//               the pre-split rows, bulk copies of its center and column
+//               data) and issues the tcgen05.mma instructions;
+//   warp 17 [13] TMA tile::gather4 of each item's target rows (8-row tiled
+//               boxes for runs of consecutive rows), two or three stages.
 // Four TMEM accumulators (4 x 128 columns) let the MMAs run up to three items
 // ahead of the epilogue.  Every mbarrier wait is bounded: on timeout the
 // kernel records ASK_DEV_TIMEOUT, all roles leave their loops, producers
@@ -51,7 +51,6 @@ namespace {
 
 using namespace tcx;
 
-constexpr int T16_THREADS = 448;
 constexpr int T16_ROWS = 128;
 constexpr int T16_REGION = T16_ROWS * 128;     // 128 rows x 128 bytes (64 16-bit elements), swizzled
 constexpr uint32_t T16_TMEM_COLS = 512;        // four 128-column FP32 accumulators
@@ -74,6 +73,7 @@ struct S16 {
     static constexpr int BLKSLOT = BLK_COLW + COLW_BYTES;
     static constexpr int ANORM = BLK + 2 * BLKSLOT;           // float [NACC][128] |a|^2
     static constexpr bool EPI2 = RC <= 4;                     // two epilogue groups (column halves)
+    static constexpr int THREADS = EPI2 ? 576 : 448;          // 2 loader groups, 1 or 2 epilogue groups, 2 warps
     static constexpr int XBUF = ANORM + 4 * 128 * 4;          // float [NACC][128][RC]: second half's sums
     static constexpr int BAR = XBUF + (EPI2 ? 4 * 128 * RC * 4 : 0);   // 32 mbarriers
     static constexpr int MISC = BAR + 32 * 8;                 // tmem address, abort flag
@@ -111,22 +111,23 @@ struct T16Args {
 // (queries against every source): the column data is {|b_j|^2 (1 - eta),
 // the same for j+1, position_j, position_j+1}; no kernel sum is formed.
 template <int P, int RC, int NRAW, int NB, int UNI>
-__global__ void __launch_bounds__(T16_THREADS, 1)
+__global__ void __launch_bounds__(S16<RC, NRAW, NB>::THREADS, 1)
 eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_constant__ CUtensorMap map_t_lo,
                  const __grid_constant__ CUtensorMap map_s_hi, const __grid_constant__ CUtensorMap map_s_lo,
                  const __grid_constant__ CUtensorMap map_q, const __grid_constant__ CUtensorMap map_q8,
                  const T16Args args) {
     using S = S16<RC, NRAW, NB>;
     constexpr int NACC = S::NACC;
-    // r <= 4: one loader group (warps 0-3) and two epilogue groups (warps
-    // 4-7 and 8-11) that take the two halves of each item's columns, so two
-    // warps per SM sub-partition share the exponentials; r = 16: two loader
-    // groups taking alternate items and one epilogue group (its weight sums
-    // leave no room for the exchange buffer)
+    // r <= 4: two epilogue groups (warps 8-11 and 12-15) take the two
+    // halves of each item's columns, so two warps per SM sub-partition share
+    // the exponentials; r = 16: one epilogue group (its weight sums leave no
+    // room for the exchange buffer)
     constexpr bool EPI2 = S::EPI2;
-    constexpr int NLG = EPI2 ? 1 : 2;
+    constexpr int NLG = 2;
     constexpr int EPI_W0 = 4 * NLG;
-    constexpr int NEPI = (12 - EPI_W0) * 32;
+    constexpr int EPI_END = EPI2 ? 16 : 12;
+    constexpr int W_MMA = EPI_END, W_GAT = EPI_END + 1;
+    constexpr int NEPI = (EPI_END - EPI_W0) * 32;
     static_assert(!UNI || RC == 1, "the uniform-bandwidth and kNN layouts serve r = 1");
     constexpr uint32_t FMT = P == ASKIT_PREC_BF16X3 ? 1u : 0u;
     extern __shared__ uint8_t smem_raw[];
@@ -171,7 +172,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 12) {
+    if (warp == W_MMA) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      ::"r"(smem_u32(tmem_slot)), "r"(T16_TMEM_COLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -196,6 +197,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
         const bool kin = kc < nk4;
         const float2 m1 = make_float2(-1.f, -1.f), z2 = make_float2(0.f, 0.f);
         const float2 sc2 = make_float2(args.f16_scale, args.f16_scale);
+        const float inv_sc2 = 1.f / (args.f16_scale * args.f16_scale);   // a power of 2
         int li = 0, lb = 0;
         for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci, ++lb) {
             const int b = args.cta_blocks[ci];
@@ -221,6 +223,12 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                     if (kin)
                         cc = *reinterpret_cast<const float4 *>(sm + S::BLK + (lb & 1) * S::BLKSLOT + S::BLK_CENT +
                                                                16 * kc);
+                    if constexpr (P == ASKIT_PREC_FP16X3) {
+                        // -c_B * scale, exact (the scale is a power of 2): one fused
+                        // operation then gives (x - c_B) * scale with a single rounding
+                        cc = make_float4(-cc.x * args.f16_scale, -cc.y * args.f16_scale, -cc.z * args.f16_scale,
+                                         -cc.w * args.f16_scale);
+                    }
                 }
                 const float *raw = reinterpret_cast<const float *>(sm + S::RAW + sr * S::RAWSTAGE);
                 uint8_t *ahi = sm + S::A0 + sa * 2 * T16_REGION;
@@ -232,8 +240,13 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                     float2 xa[2] = {z2, z2};
                     if (kin && row < cnt) {
                         const float4 xx = *reinterpret_cast<const float4 *>(raw + row * dp + 4 * kc);
-                        xa[0] = __ffma2_rn(make_float2(cc.x, cc.y), m1, make_float2(xx.x, xx.y));
-                        xa[1] = __ffma2_rn(make_float2(cc.z, cc.w), m1, make_float2(xx.z, xx.w));
+                        if constexpr (P == ASKIT_PREC_FP16X3) {   // scaled: v = (x - c_B) * scale
+                            xa[0] = __ffma2_rn(make_float2(xx.x, xx.y), sc2, make_float2(cc.x, cc.y));
+                            xa[1] = __ffma2_rn(make_float2(xx.z, xx.w), sc2, make_float2(cc.z, cc.w));
+                        } else {
+                            xa[0] = __ffma2_rn(make_float2(cc.x, cc.y), m1, make_float2(xx.x, xx.y));
+                            xa[1] = __ffma2_rn(make_float2(cc.z, cc.w), m1, make_float2(xx.z, xx.w));
+                        }
                     }
                     const float2 sq = __ffma2_rn(xa[1], xa[1], __fmul2_rn(xa[0], xa[0]));
                     part[i] = sq.x + sq.y;
@@ -241,7 +254,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
                         if constexpr (P == ASKIT_PREC_FP16X3) {
-                            const float2 v = __ffma2_rn(xa[e], sc2, z2);
+                            const float2 v = xa[e];
                             const __half2 h = __float22half2_rn(v);
                             const __half2 l = __float22half2_rn(__ffma2_rn(__half22float2(h), m1, v));
                             hv[e] = *reinterpret_cast<const uint32_t *>(&h);
@@ -270,7 +283,8 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                         part[q] = keep + __shfl_xor_sync(0xffffffffu, send, m);
                     }
                 }
-                a_norm[a4 * 128 + 32 * wl + 2 * kc + hh] = part[0];
+                // FP16x3: the sums of the scaled rows, scaled back exactly
+                a_norm[a4 * 128 + 32 * wl + 2 * kc + hh] = P == ASKIT_PREC_FP16X3 ? part[0] * inv_sc2 : part[0];
                 // generic-proxy stores -> visible to the tensor core's async proxy
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(BAR_A_FULL(sa));
@@ -278,11 +292,11 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
             }
         }
     loader_done:;
-    } else if (warp < 12) {
+    } else if (warp < EPI_END) {
         // ----------------------------------------------------------- epilogue
         const int q = warp & 3;                    // this warp's TMEM lane quadrant
         const int row = q * 32 + lane;             // TMEM lane = target row of the item
-        const int eg = EPI2 ? (warp - 4) >> 2 : 0; // column half of this group
+        const int eg = EPI2 ? (warp - EPI_W0) >> 2 : 0; // column half of this group
         int li = 0, lb = 0;
         for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci, ++lb) {
             const int b = args.cta_blocks[ci];
@@ -419,6 +433,16 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
 #pragma unroll
                             for (int z = 0; z < RC / 2; ++z) accw[z] = __fadd2_rn(accw[z], make_float2(0.f, 0.f));
                         }
+                    } else if (EPI2) {
+                        // two warps per sub-partition: one buffer each, the other
+                        // warp's work covers the load
+                        uint32_t ga[32];
+#pragma unroll 1
+                        for (int c = c_lo; c < c_hi; ++c) {
+                            tmem_ld32_async(tbase + (uint32_t)(c * 32), ga);
+                            tmem_wait_pin(ga);
+                            cols(c, ga);
+                        }
                     } else if (c_lo < c_hi) {
                         uint32_t ga[32], gb[32];
                         tmem_ld32_async(tbase + (uint32_t)(c_lo * 32), ga);
@@ -480,7 +504,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
             mbar_arrive(BAR_BLK_EMPTY(bs));
         }
     epi_done:;
-    } else if (warp == 13) {
+    } else if (warp == W_GAT) {
         // ------------------------------------------------- target-row gatherer
         // The next item's descriptor and target slots are loaded while this
         // item waits for its stage, so the two dependent global loads are
@@ -541,7 +565,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
         // rows of the last stages may still be landing after an abort
         for (int gg = issued > NRAW ? issued - NRAW : 0; gg < issued; ++gg)
             mbar_drain(BAR_R_FULL(gg % NRAW), (gg / NRAW) & 1);
-    } else if (warp == 12 && lane == 0) {
+    } else if (warp == W_MMA && lane == 0) {
         // ------------------------------------- sub-block loads + MMA issuer
         int li = 0, lb = 0, b_issued = 0;
         for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci, ++lb) {
@@ -612,7 +636,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 12) {
+    if (warp == W_MMA) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(T16_TMEM_COLS) : "memory");
     }
@@ -728,7 +752,7 @@ askit_status launch16(T16State *st, int pi, const CUtensorMap &map_q, const CUte
     static const cudaError_t attr = cudaFuncSetAttribute(eval_tc16_kernel<P, RC, NRAW, NB, UNI>,
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     ASK_CUDA(attr);
-    eval_tc16_kernel<P, RC, NRAW, NB, UNI><<<(unsigned)grid, T16_THREADS, smem, s>>>(
+    eval_tc16_kernel<P, RC, NRAW, NB, UNI><<<(unsigned)grid, S::THREADS, smem, s>>>(
         st->map[pi][0], st->map[pi][1], st->map[pi][2], st->map[pi][3], map_q, map_q8, a);
     ASK_LAUNCH();
     return ASKIT_OK;
