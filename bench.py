@@ -465,6 +465,7 @@ def main():
                      "items": info["n_items"], "blocks": info["n_blocks"], "entries": info["n_entries"], "L": info["L"],
                      "target_batches": info["n_batches"],
                      "skeleton_rows": info["skel_total"], "setup_s": setup_s,
+                     "setup_stage_s": {k: round(v / 1e3, 3) for k, v in info["setup_ms"].items()},
                      "device_gb": info["device_bytes"] / 1e9}}
     graph.close()
     tree.close()

@@ -301,6 +301,10 @@ typedef struct {
     int64_t near_total, far_total; /* sum over targets of |Near(i)| and |Far(i)| */
     int64_t device_bytes;     /* library-owned device memory */
     int64_t n_batches;        /* in-sample target batches (askit_params.batch_entries) */
+    double setup_ms[7];       /* askit_setup's wall time by stage: kNN, tree, node lists
+                                 (Algorithm 2), sampled rows (eq. 2.4), skeletons and
+                                 interpolation matrices (Algorithm 3), evaluation
+                                 operands, work lists */
 } askit_info;
 askit_status askit_get_info(askit_tree t, askit_info *info);
 

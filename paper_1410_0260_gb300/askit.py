@@ -59,7 +59,7 @@ class Info(C.Structure):
                 ("skel_total", C.c_int64), ("skel_rows_padded", C.c_int64), ("n_blocks", C.c_int64),
                 ("n_items", C.c_int64), ("n_entries", C.c_int64), ("pairs_algorithmic", C.c_int64), ("pairs_computed", C.c_int64),
                 ("near_total", C.c_int64), ("far_total", C.c_int64), ("device_bytes", C.c_int64),
-                ("n_batches", C.c_int64)]
+                ("n_batches", C.c_int64), ("setup_ms", C.c_double * 7)]
 
 
 def load(path: str | None = None):
@@ -295,7 +295,10 @@ class Tree:
     def info(self) -> dict:
         inf = Info()
         _check(load().askit_get_info(self._t, C.byref(inf)))
-        return {k: getattr(inf, k) for k, _ in Info._fields_}
+        out = {k: getattr(inf, k) for k, _ in Info._fields_}
+        out["setup_ms"] = dict(zip(("knn", "tree", "node_lists", "sampling", "skeletons", "operands", "work_lists"),
+                                   list(inf.setup_ms)))
+        return out
 
     def structure(self, which: int) -> np.ndarray:
         inf = self.info()

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <chrono>
 #include <string>
 #include <vector>
 
@@ -243,6 +244,9 @@ struct askit_tree_s {
     int tune_runs = 1;             // 8-row tiled loads for runs of consecutive targets
     int tune_pairs = 0;            // FP16x3: items over two sub-blocks of a node (256 columns)
     int kw = TC_K;                 // row width of the pre-split operands and centers
+    // wall time of the setup stages (askit_info.setup_ms)
+    double setup_ms[7] = {0, 0, 0, 0, 0, 0, 0};
+    std::chrono::steady_clock::time_point stage_t0;
     // CUDA events around each launch of the evaluation kernel while timing
     // is on (askit_kernel_timing): begin/end pairs, reused across sessions
     struct KTimer {

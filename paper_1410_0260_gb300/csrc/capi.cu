@@ -6,6 +6,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <chrono>
 #include <mutex>
 #include <string>
 
@@ -119,8 +120,18 @@ askit_status validate(const askit_params *p, int64_t N, int32_t d, int64_t ldx, 
     return ASKIT_OK;
 }
 
+// Wall time of setup stage k (host clock, the stream drained at each mark).
+askit_status stage_mark(askit_tree t, int k, cudaStream_t s) {
+    ASK_CUDA(cudaStreamSynchronize(s));
+    const auto now = std::chrono::steady_clock::now();
+    t->setup_ms[k] = std::chrono::duration<double, std::milli>(now - t->stage_t0).count();
+    t->stage_t0 = now;
+    return ASKIT_OK;
+}
+
 askit_status setup_impl(askit_tree t, const float *X_dev, int64_t ldx, const float *h_dev,
                         const int32_t *knn_dev, cudaStream_t s) {
+    t->stage_t0 = std::chrono::steady_clock::now();
     const int64_t N = t->N;
     const int d = t->d, kappa = t->kappa;
     ASK_TRY(t->arena.alloc(&t->X, (size_t)N * d));
@@ -146,6 +157,7 @@ askit_status setup_impl(askit_tree t, const float *X_dev, int64_t ldx, const flo
     } else {
         ASK_TRY(knn_rp_gpu(t->X, N, d, kappa, t->prm.rp_iters, t->rp_leaf, t->prm.seed, t->knn, t->knnd, s));
     }
+    ASK_TRY(stage_mark(t, 0, s));
     // bandwidth of every source point (Section 4)
     ASK_TRY(t->arena.alloc(&t->hsrc, N));
     if (t->prm.bw_mode == ASKIT_BW_CONSTANT) {
@@ -177,6 +189,7 @@ askit_status setup_impl(askit_tree t, const float *X_dev, int64_t ldx, const flo
         ASK_LAUNCH();
         ASK_CUDA(cudaStreamSynchronize(s));
     }
+    ASK_TRY(stage_mark(t, 1, s));
     // node neighbor lists, sampled targets, skeletons (Algorithms 2, 3)
     const int64_t nn = t->n_nodes;
     t->ell_max = t->prm.s_max + t->prm.ell_extra;
@@ -191,8 +204,11 @@ askit_status setup_impl(askit_tree t, const float *X_dev, int64_t ldx, const flo
     ASK_CUDA(cudaMemsetAsync(t->trows, 0xff, sizeof(int32_t) * nn * t->ell_max, s));
     ASK_CUDA(cudaMemsetAsync(t->d_ncol, 0, sizeof(int32_t) * nn, s));
     ASK_TRY(build_node_lists(t, s));
+    ASK_TRY(stage_mark(t, 2, s));
     ASK_TRY(build_samples(t, s));
+    ASK_TRY(stage_mark(t, 3, s));
     ASK_TRY(skeletonize(t, s));
+    ASK_TRY(stage_mark(t, 4, s));
     if (t->L == 0) {
         // a single leaf: no skeletons, empty pools
         t->h_skoff.assign(nn + 1, 0); t->h_pivoff.assign(nn + 1, 0);
@@ -210,6 +226,7 @@ askit_status setup_impl(askit_tree t, const float *X_dev, int64_t ldx, const flo
     // evaluation operands and the in-sample work lists (eq. (2.5), Algorithm 4)
     ASK_TRY(build_eval_operands(t, s));
     ASK_TRY(build_tc_operands(t, s));
+    ASK_TRY(stage_mark(t, 5, s));
     {
         PruneSets ps;
         askit_status rc = insample_prune_sets(t, ps, s);
@@ -217,6 +234,7 @@ askit_status setup_impl(askit_tree t, const float *X_dev, int64_t ldx, const flo
         free_prune_sets(ps);
         ASK_TRY(rc);
     }
+    ASK_TRY(stage_mark(t, 6, s));
     ASK_TRY(t->arena.alloc(&t->d_status, 4));
     ASK_TRY(t->arena.alloc(&t->d_ticket, 4));
     ASK_CUDA(cudaMemsetAsync(t->d_status, 0, sizeof(int) * 4, s));
@@ -485,6 +503,7 @@ askit_status askit_get_info(askit_tree t, askit_info *info) {
     }
     info->device_bytes = (int64_t)t->arena.bytes;
     info->n_batches = (int64_t)t->wl.size();
+    for (int k = 0; k < 7; ++k) info->setup_ms[k] = t->setup_ms[k];
     return ASKIT_OK;
 }
 

@@ -34,7 +34,6 @@
 // and TMEM is freed before the kernel returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
-#include <cuda_fp16.h>
 
 #include <mutex>
 
@@ -60,10 +59,6 @@ template <> struct Prec<ASKIT_PREC_TF32X3> {
 template <> struct Prec<ASKIT_PREC_BF16X3> {
     static constexpr int EB = 2, NREG = 1, KSTEPS = 4;   // K = 16 per MMA
     static constexpr uint32_t FMT = 1;                   // BF16 in .kind::f16
-};
-template <> struct Prec<ASKIT_PREC_FP16X3> {
-    static constexpr int EB = 2, NREG = 1, KSTEPS = 4;   // K = 16 per MMA
-    static constexpr uint32_t FMT = 0;                   // F16 in .kind::f16
 };
 
 // Shared-memory plan (offsets from a 1024-byte aligned base).
@@ -102,8 +97,8 @@ struct TcArgs {
     const float *Xt, *Xs;     // raw source coordinates [*, d_pad] (column terms)
     const float *Wt, *Ws;
     int r;
-    float f16_scale;          // power-of-2 prescale of the FP16 operands (1 otherwise)
-    float g_unscale;          // 1 / f16_scale^2 (1 otherwise)
+    float f16_scale;          // prescale of the 16-bit operands (1: BF16 and TF32 are not prescaled)
+    float g_unscale;          // 1 / f16_scale^2
     float *partial;
     int *status;
 };
@@ -260,19 +255,11 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                         uint32_t hv[2], lv[2];
 #pragma unroll
                         for (int e = 0; e < 2; ++e) {
-                            if constexpr (P == ASKIT_PREC_FP16X3) {
-                                const float2 v = __ffma2_rn(xa[e], sc2, z2);
-                                const __half2 h = __float22half2_rn(v);
-                                const __half2 l = __float22half2_rn(__ffma2_rn(__half22float2(h), m1, v));
-                                hv[e] = *reinterpret_cast<const uint32_t *>(&h);
-                                lv[e] = *reinterpret_cast<const uint32_t *>(&l);
-                            } else {
-                                const float2 v = xa[e];
-                                const __nv_bfloat162 h = __float22bfloat162_rn(v);
-                                const __nv_bfloat162 l = __float22bfloat162_rn(__ffma2_rn(__bfloat1622float2(h), m1, v));
-                                hv[e] = *reinterpret_cast<const uint32_t *>(&h);
-                                lv[e] = *reinterpret_cast<const uint32_t *>(&l);
-                            }
+                            const float2 v = xa[e];
+                            const __nv_bfloat162 h = __float22bfloat162_rn(v);
+                            const __nv_bfloat162 l = __float22bfloat162_rn(__ffma2_rn(__bfloat1622float2(h), m1, v));
+                            hv[e] = *reinterpret_cast<const uint32_t *>(&h);
+                            lv[e] = *reinterpret_cast<const uint32_t *>(&l);
                         }
                         const int off = t * 128 + (((kst >> 1) ^ (t & 7)) << 4) + (kst & 1) * 8;
                         *reinterpret_cast<uint2 *>(ahi + off) = make_uint2(hv[0], hv[1]);
@@ -334,18 +321,10 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
                         for (int e = 0; e < 4; ++e) {
                             float v0 = xa[2 * e], v1 = xa[2 * e + 1];
                             uint16_t h0, h1, l0, l1;
-                            if constexpr (P == ASKIT_PREC_FP16X3) {
-                                v0 *= args.f16_scale; v1 *= args.f16_scale;
-                                const __half a0 = __float2half_rn(v0), a1 = __float2half_rn(v1);
-                                h0 = __half_as_ushort(a0); h1 = __half_as_ushort(a1);
-                                l0 = __half_as_ushort(__float2half_rn(v0 - __half2float(a0)));
-                                l1 = __half_as_ushort(__float2half_rn(v1 - __half2float(a1)));
-                            } else {
-                                const __nv_bfloat16 a0 = __float2bfloat16_rn(v0), a1 = __float2bfloat16_rn(v1);
-                                h0 = __bfloat16_as_ushort(a0); h1 = __bfloat16_as_ushort(a1);
-                                l0 = __bfloat16_as_ushort(__float2bfloat16_rn(v0 - __bfloat162float(a0)));
-                                l1 = __bfloat16_as_ushort(__float2bfloat16_rn(v1 - __bfloat162float(a1)));
-                            }
+                            const __nv_bfloat16 a0 = __float2bfloat16_rn(v0), a1 = __float2bfloat16_rn(v1);
+                            h0 = __bfloat16_as_ushort(a0); h1 = __bfloat16_as_ushort(a1);
+                            l0 = __bfloat16_as_ushort(__float2bfloat16_rn(v0 - __bfloat162float(a0)));
+                            l1 = __bfloat16_as_ushort(__float2bfloat16_rn(v1 - __bfloat162float(a1)));
                             hv[e] = (uint32_t)h0 | ((uint32_t)h1 << 16);
                             lv[e] = (uint32_t)l0 | ((uint32_t)l1 << 16);
                         }
@@ -564,8 +543,8 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_consta
 
 // Tensor maps of the four source operand arrays for one precision.
 struct TcState {
-    CUtensorMap map[3][4];   // [precision: 0 tf32, 1 bf16, 2 fp16][t_hi, t_lo, s_hi, s_lo]
-    bool ready[3] = {false, false, false};
+    CUtensorMap map[2][4];   // [precision: 0 tf32, 1 bf16][t_hi, t_lo, s_hi, s_lo]
+    bool ready[2] = {false, false};
     CUtensorMap raw_t, raw_s;   // raw FP32 source rows, 128-row boxes (gather path)
     bool raw_ready = false;
     void *encode = nullptr;     // cuTensorMapEncodeTiled
@@ -629,11 +608,11 @@ askit_status tc_state(askit_tree t, int pi, TcState **out) {
         st->raw_ready = true;
     }
     if (!st->ready[pi]) {
-        const int ty = pi;   // 0 fp32 (tf32), 1 bf16, 2 fp16
-        void *th = pi == 0 ? (void *)t->Xt_hi : pi == 1 ? (void *)t->Xt_bhi : (void *)t->Xt_hhi;
-        void *tl = pi == 0 ? (void *)t->Xt_lo : pi == 1 ? (void *)t->Xt_blo : (void *)t->Xt_hlo;
-        void *sh = pi == 0 ? (void *)t->Xs_hi : pi == 1 ? (void *)t->Xs_bhi : (void *)t->Xs_hhi;
-        void *sl = pi == 0 ? (void *)t->Xs_lo : pi == 1 ? (void *)t->Xs_blo : (void *)t->Xs_hlo;
+        const int ty = pi;   // 0 fp32 (tf32), 1 bf16
+        void *th = pi == 0 ? (void *)t->Xt_hi : (void *)t->Xt_bhi;
+        void *tl = pi == 0 ? (void *)t->Xt_lo : (void *)t->Xt_blo;
+        void *sh = pi == 0 ? (void *)t->Xs_hi : (void *)t->Xs_bhi;
+        void *sl = pi == 0 ? (void *)t->Xs_lo : (void *)t->Xs_blo;
         ASK_TRY(encode_map(fn, &st->map[pi][0], th, t->N_pad, ty));
         ASK_TRY(encode_map(fn, &st->map[pi][1], tl, t->N_pad, ty));
         ASK_TRY(encode_map(fn, &st->map[pi][2], sh, t->srows, ty));
@@ -648,7 +627,7 @@ template <int P, int RC>
 askit_status launch(askit_tree t, TcState *st, const CUtensorMap &map_q, const TcArgs &a, int a_grid,
                     cudaStream_t s) {
     using S = Smem<P>;
-    const int pi = P == ASKIT_PREC_TF32X3 ? 0 : P == ASKIT_PREC_BF16X3 ? 1 : 2;
+    const int pi = P == ASKIT_PREC_TF32X3 ? 0 : 1;
     const size_t smem = S::BYTES + 1024;
     static bool attr_set = false;
     {
@@ -676,6 +655,10 @@ askit_status eval_tc(askit_tree t, const WeightCtx &c, int precision, const floa
     // a residual of about 2^-17 of |a| |b| per product, so the smaller |a| of
     // the per-item center is what keeps it within the split-path tolerance
     if (precision == ASKIT_PREC_FP16X3) return eval_tc16(t, c, precision, Xq, ldq, q_rows, w, partial, s);
+    if (precision != ASKIT_PREC_TF32X3 && precision != ASKIT_PREC_BF16X3) {
+        askit_set_error("unknown tensor-core precision %d", precision);
+        return ASKIT_ERR_INVALID_ARG;
+    }
     if (c.r > Smem<ASKIT_PREC_TF32X3>::RC_MAX) {
         askit_set_error("tensor-core evaluation covers r <= %d; use ASKIT_PREC_SIMT_FP32", Smem<ASKIT_PREC_TF32X3>::RC_MAX);
         return ASKIT_ERR_UNSUPPORTED;
@@ -686,7 +669,7 @@ askit_status eval_tc(askit_tree t, const WeightCtx &c, int precision, const floa
         return ASKIT_ERR_INVALID_ARG;
     }
     TcState *st = nullptr;
-    ASK_TRY(tc_state(t, precision == ASKIT_PREC_TF32X3 ? 0 : precision == ASKIT_PREC_BF16X3 ? 1 : 2, &st));
+    ASK_TRY(tc_state(t, precision == ASKIT_PREC_TF32X3 ? 0 : 1, &st));
     // gather map over this call's target rows (one box row per gathered row)
     CUtensorMap map_q;
     ASK_TRY(encode_raw((EncodeTiledFn)st->encode, &map_q, Xq, q_rows, t->d_pad, 1));
@@ -709,7 +692,7 @@ askit_status eval_tc(askit_tree t, const WeightCtx &c, int precision, const floa
     a.r = c.r;
     a.partial = partial;
     a.status = t->d_status;
-    a.f16_scale = precision == ASKIT_PREC_FP16X3 ? t->f16_scale : 1.f;
+    a.f16_scale = 1.f;
     a.g_unscale = 1.f / (a.f16_scale * a.f16_scale);
     if (precision == ASKIT_PREC_TF32X3) {
         if (c.r == 1) return launch<ASKIT_PREC_TF32X3, 1>(t, st, map_q, a, w.n_ctas, s);
