@@ -85,6 +85,42 @@ def askit_config(w, precision, lists="target"):
                         bw_k=w.bw_k, seed=w.seed, precision=precision, prune=2 if lists == "leaf" else 1)
 
 
+def roofline(P, d, r, precision, sec, peaks, smax_mhz):
+    """Roofline of the Evaluate kernel for P algorithmic pairs in `sec`
+    seconds: the binding unit among the tensor cores (three split products
+    of length d per pair), MUFU (one ex2 per pair) and the FP32 FMA pipe
+    (r + 2 FMAs per pair in the epilogue); plain FP32 is bound by its 2d lane
+    operations per pair."""
+    mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * smax_mhz * 1e6
+    lane_peak = SM_COUNT * FP32_LANES_PER_SM * smax_mhz * 1e6
+    if precision == "simt_fp32":
+        # two FP32 lane operations per pair and coordinate (subtract, fused multiply-add)
+        roof = {"bound": "alu", "achieved": P * 2 * d / sec / 1e12, "peak": lane_peak / 1e12,
+                "unit": "Tops/s", "peak_source": "152 SMs x 128 FP32 lanes x max SM clock"}
+    else:
+        bf16 = (peaks or {}).get("bf16_tflops", 1900.0)
+        tpeak = bf16 * (TF32_OVER_BF16 if precision == "tf32x3" else 1.0)   # fp16 and bf16 share the rate
+        t_tensor = P * 3 * 2 * d / (tpeak * 1e12)
+        t_mufu = P / mufu_peak
+        # FP32 lane FMAs per pair in the epilogue: the exponent's argument (2)
+        # and one per weight vector
+        fma_per_pair = r + 2
+        t_fma = P * fma_per_pair / lane_peak
+        if t_fma > max(t_tensor, t_mufu):
+            roof = {"bound": "alu", "achieved": P * fma_per_pair / sec / 1e12, "peak": lane_peak / 1e12,
+                    "unit": "Tfma/s", "peak_source": "FP32 FMA: 152 SMs x 128 lanes x max SM clock; "
+                    "%d FMAs per pair (r = %d weight sums + 2 for the exponent's argument)" % (fma_per_pair, r)}
+        elif t_tensor >= t_mufu:
+            roof = {"bound": "tensor", "achieved": P * 3 * 2 * d / sec / 1e12, "peak": tpeak, "unit": "TFLOP/s",
+                    "peak_source": ("measured bf16 burst x 1.1/2.25 (TF32)" if precision == "tf32x3"
+                                    else "measured bf16 burst") + (" of measured" if peaks else " of fallback")}
+        else:
+            roof = {"bound": "alu", "achieved": P / sec / 1e12, "peak": mufu_peak / 1e12, "unit": "Tex2/s",
+                    "peak_source": "MUFU ex2: 152 SMs x 16/clk x max SM clock"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    return roof
+
+
 def measured_traffic(kernel, workload_name):
     """DRAM bytes per launch of the dominant kernel from a committed ncu
     capture (profiles/traffic.json), while the kernel source is the one that
@@ -399,34 +435,7 @@ def main():
     d = w.d
     sec = ms_kernel / 1e3
     smax = (clk or {}).get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0
-    mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * smax * 1e6
-    if args.precision == "simt_fp32":
-        # two FP32 lane operations per pair and coordinate (subtract, fused multiply-add)
-        alu_peak = SM_COUNT * FP32_LANES_PER_SM * smax * 1e6
-        roof = {"bound": "alu", "achieved": P * 2 * d / sec / 1e12, "peak": alu_peak / 1e12,
-                "unit": "Tops/s", "peak_source": "152 SMs x 128 FP32 lanes x max SM clock"}
-    else:
-        bf16 = (peaks or {}).get("bf16_tflops", 1900.0)
-        tpeak = bf16 * (TF32_OVER_BF16 if args.precision == "tf32x3" else 1.0)   # fp16 and bf16 share the rate
-        t_tensor = P * 3 * 2 * d / (tpeak * 1e12)
-        t_mufu = P / mufu_peak
-        # FP32 lane FMAs per pair in the epilogue: the exponent's argument (2)
-        # and one per weight vector
-        fma_per_pair = r + 2
-        fma_peak = SM_COUNT * FP32_LANES_PER_SM * smax * 1e6
-        t_fma = P * fma_per_pair / fma_peak
-        if t_fma > max(t_tensor, t_mufu):
-            roof = {"bound": "alu", "achieved": P * fma_per_pair / sec / 1e12, "peak": fma_peak / 1e12,
-                    "unit": "Tfma/s", "peak_source": "FP32 FMA: 152 SMs x 128 lanes x max SM clock; "
-                    "%d FMAs per pair (r = %d weight sums + 2 for the exponent's argument)" % (fma_per_pair, r)}
-        elif t_tensor >= t_mufu:
-            roof = {"bound": "tensor", "achieved": P * 3 * 2 * d / sec / 1e12, "peak": tpeak, "unit": "TFLOP/s",
-                    "peak_source": ("measured bf16 burst x 1.1/2.25 (TF32)" if args.precision == "tf32x3"
-                                    else "measured bf16 burst") + (" of measured" if peaks else " of fallback")}
-        else:
-            roof = {"bound": "alu", "achieved": P / sec / 1e12, "peak": mufu_peak / 1e12, "unit": "Tex2/s",
-                    "peak_source": "MUFU ex2: 152 SMs x 16/clk x max SM clock"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof = roofline(P, d, r, args.precision, sec, peaks, smax)
     roof["traffic"] = None
     roof["kernel"] = ("eval_simt_kernel" if args.precision == "simt_fp32" else
                       "eval_tcw_kernel" if d > 64 else

@@ -44,14 +44,11 @@ def test_host_only_calls(lib):
     assert lib.askit_status_string(0) == b"ok"
     assert lib.askit_status_string(4) == b"device wait timed out"
 
-    class P(ctypes.Structure):
-        _fields_ = [(f, ctypes.c_int32) for f in ["m", "k", "km", "ri", "rl", "smax", "smin", "ee", "pr",
-                                                  "bw", "bwk", "prec"]] + \
-                   [("tol", ctypes.c_double), ("c", ctypes.c_double), ("h", ctypes.c_double),
-                    ("seed", ctypes.c_uint64)]
-    p = P()
+    from paper_1410_0260_gb300.askit import Params   # layout checked in test_abi_layout.py
+    p = Params()
     lib.askit_default_params(ctypes.byref(p))
-    assert p.m == 128 and p.k == 16 and p.ee == 20 and p.c == 0.5
+    assert p.leaf_size == 128 and p.kappa == 16 and p.ell_extra == 20 and p.kernel_scale == 0.5
+    assert p.batch_entries == 0 and p.prune == 1
     # invalid arguments are rejected before any device work
     out = ctypes.c_void_p()
     lib.askit_setup.restype = ctypes.c_int

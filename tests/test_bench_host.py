@@ -1,0 +1,54 @@
+"""bench.py's host-side arithmetic (CPU only): the roofline's binding unit
+and fraction, and the DRAM-traffic record keyed by the kernel source's hash."""
+import hashlib
+import json
+import os
+
+import pytest
+
+import bench
+
+PEAKS = {"bf16_tflops": 1908.7}
+
+
+def test_tensor_bound_for_one_weight_vector():
+    # 1M x 64 workload: 12.5e9 pairs, the kernel in 6.12 ms
+    P, sec = 12.499349438e9, 6.12e-3
+    roof = bench.roofline(P, 64, 1, "fp16x3", sec, PEAKS, 2070.0)
+    assert roof["bound"] == "tensor" and roof["unit"] == "TFLOP/s"
+    assert roof["achieved"] == pytest.approx(P * 3 * 2 * 64 / sec / 1e12)
+    assert roof["frac"] == pytest.approx(roof["achieved"] / 1908.7)
+    assert "of measured" in roof["peak_source"]
+
+
+def test_fma_bound_for_sixteen_weight_vectors():
+    # r = 16: 18 FMAs a pair outweigh 384 tensor flops and one ex2
+    P, sec = 4.392e11, 1.166
+    roof = bench.roofline(P, 64, 16, "fp16x3", sec, PEAKS, 2070.0)
+    assert roof["bound"] == "alu" and roof["unit"] == "Tfma/s"
+    assert roof["peak"] == pytest.approx(152 * 128 * 2070e6 / 1e12)
+    assert roof["achieved"] == pytest.approx(P * 18 / sec / 1e12)
+
+
+def test_mufu_bound_when_the_contraction_is_short():
+    # d = 8: three split products of length 8 take less than one ex2
+    roof = bench.roofline(1e9, 8, 1, "fp16x3", 1e-3, PEAKS, 2070.0)
+    assert roof["bound"] == "alu" and roof["unit"] == "Tex2/s"
+    assert roof["peak"] == pytest.approx(152 * 16 * 2070e6 / 1e12)
+
+
+def test_tf32_peak_and_plain_fp32():
+    roof = bench.roofline(1e10, 64, 1, "tf32x3", 1e-2, PEAKS, 2070.0)
+    assert roof["peak"] == pytest.approx(1908.7 * 1.1 / 2.25)
+    roof = bench.roofline(1e10, 64, 1, "simt_fp32", 1e-1, None, 2070.0)
+    assert roof["bound"] == "alu" and roof["achieved"] == pytest.approx(1e10 * 128 / 1e-1 / 1e12)
+
+
+def test_traffic_record_follows_the_kernel_source():
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
+    for kernel, r in rec.items():
+        src = open(os.path.join(bench.ROOT, r["source"]), "rb").read()
+        current = hashlib.sha256(src).hexdigest() == r["source_sha256"]
+        got = bench.measured_traffic(kernel, r["workload"])
+        assert got == (r["bytes_per_launch"] if current else None)
+        assert bench.measured_traffic(kernel, r["workload"] + " (another size)") is None

@@ -37,6 +37,9 @@ MUTATIONS = [
      "if (Y || j != tgt[t]) U[(size_t)t * r + q] = U[(size_t)t * r + q] + k * W[(size_t)j * r + q];"),
     ("exp reduction tail sign", "double r = (a - n * LN2_HEAD) - n * LN2_TAIL;", "double r = (a - n * LN2_HEAD) + n * LN2_TAIL;"),
     ("exp polynomial term", "0x1.5555555555555p-3,", "0x1.5555555555555p-2,"),
+    ("leaf-grouped set takes the target's neighbors",
+     "for (int z = 0; z < kappa; ++z) pset[np++] = t->leafof[t->knn[(size_t)p * kappa + z]];",
+     "for (int z = 0; z < kappa; ++z) pset[np++] = t->leafof[t->knn[(size_t)i * kappa + z]];"),
 ]
 
 
