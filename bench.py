@@ -85,6 +85,24 @@ def askit_config(w, precision, lists="target"):
                         bw_k=w.bw_k, seed=w.seed, precision=precision, prune=2 if lists == "leaf" else 1)
 
 
+def max_over_ranks(values, device):
+    """Each value's maximum over the ranks (replicas do the same work, so
+    the job takes as long as its slowest rank); unchanged on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_throughput(world, n_per_rank, ms_per_step):
+    """Targets per second of the whole job: every rank evaluates its own n
+    targets per step (replicas, weak scaling)."""
+    return world * n_per_rank / (ms_per_step / 1e3)
+
+
 def roofline(P, d, r, precision, sec, peaks, smax_mhz):
     """Roofline of the Evaluate kernel for P algorithmic pairs in `sec`
     seconds: the binding unit among the tensor cores (three split products
@@ -401,12 +419,9 @@ def main():
     tg = torch.from_numpy(np.random.default_rng(11).choice(N, size=min(1000, N), replace=False).astype(np.int64))
     Udir = tree.direct(tg.to(dev))
     eps2 = float(torch.linalg.vector_norm((U[tg.to(dev)] - Udir).double()) / torch.linalg.vector_norm(Udir.double()))
-    if world > 1:
-        t = torch.tensor([ms, ms_eval, ms_kernel], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_eval, ms_kernel = float(t[0]), float(t[1]), float(t[2])
+    ms, ms_eval, ms_kernel = max_over_ranks([ms, ms_eval, ms_kernel], dev)
     ms_step = ms / args.steps
-    value = world * N / (ms_step / 1e3)
+    value = job_throughput(world, N, ms_step)
 
     # end to end through the public host-buffer call: H2D of w, set_weights,
     # Evaluate, D2H of u, every step
@@ -422,11 +437,8 @@ def main():
         for _ in range(args.steps):
             tree.evaluate_host_ptr(Wh.data_ptr(), r, Uh.data_ptr())
         dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t[0])
-        e2e = {"value": world * N * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(W.nbytes),
+        (dt,) = max_over_ranks([dt], dev)
+        e2e = {"value": job_throughput(world, N, dt * 1e3 / args.steps), "unit": UNIT, "h2d_bytes_per_step": int(W.nbytes),
                "d2h_bytes_per_step": int(N * r * 4)}
 
     # roofline of the Evaluate kernel
@@ -465,6 +477,7 @@ def main():
                        "r": r, "precision": args.precision, "parallelism": f"replicas x{world}",
                        "lists": {"target": "per target (eq. 2.5)", "leaf": "leaf-grouped"}[args.lists],
                        "l2": "inputs larger than L2 (coordinates %.0f MB)" % (N * info["d_pad"] * 4 / 1e6)},
+            "targets_x_rhs_per_s": value * r,
             "rel_err_vs_fp32": rel_vs_fp32, "rel_err_ok": rel_vs_fp32 <= 1e-4, "eps2_vs_direct": eps2,
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk, "roofline": roof,
             "cpu_baseline": cpu, "serving": None,
