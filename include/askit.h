@@ -134,7 +134,9 @@ askit_status askit_set_weights(askit_tree t, const float *W_dev, int32_t r, int6
  * Evaluate (Algorithm 4) at every point: U_dev [N, r] FP32 (row stride
  * ldu >= r) receives u_i in the caller's point order.  Near-field leaves
  * are summed directly, pruned nodes through their skeletons; the work runs
- * as one persistent launch over all (target tile, source block) items.
+ * as one persistent launch over all (target tile, source block) items of
+ * each target batch (askit_params.batch_entries; one batch unless the
+ * entries exceed it), then a fixed-order reduction of the partial sums.
  * Requires askit_set_weights first (NOT_READY otherwise).
  */
 askit_status askit_evaluate(askit_tree t, float *U_dev, int64_t ldu, void *stream);
