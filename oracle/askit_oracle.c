@@ -12,7 +12,7 @@
  * Floating point: inputs are FP32, every computation is FP64, compiled with
  * -ffp-contract=off (no fused multiply-add), sums run in the order written.
  * Where the paper leaves a choice open, the reading taken is stated at the
- * function and collected in the design doc.
+ * function.
  *
  * Pinning (tests/test_oracle_*.py): each stage is checked against something
  * other than itself -- numpy's Philox for the RNG, libm/mpmath for exp,
