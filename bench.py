@@ -451,7 +451,8 @@ def main():
     roof["traffic"] = None
     roof["kernel"] = ("eval_simt_kernel" if args.precision == "simt_fp32" else
                       "eval_tcw_kernel" if d > 64 else
-                      "eval_tc16_kernel" if args.precision == "fp16x3" else "eval_tc_kernel")
+                      ("eval_g16_kernel" if info["fp16_centering"] == 2 else "eval_tc16_kernel")
+                      if args.precision == "fp16x3" else "eval_tc_kernel")
     roof["ms_per_launch"] = k_ms / max(1, k_launches)
     roof["launches_per_evaluate"] = k_launches // args.steps
     roof["evaluate_ms"] = ms_eval
@@ -475,6 +476,9 @@ def main():
                        "knn": "rp-trees x%d" % w.rp_iters, "s_max": w.s_max, "s_min": w.s_min, "id_tol": w.id_tol,
                        "h": w.h if w.bw_mode == 0 else "distance to neighbor %d" % w.bw_k,
                        "r": r, "precision": args.precision, "parallelism": f"replicas x{world}",
+                       "fp16_centering": ({1: "per source sub-block", 2: "global (data mean), pre-split"}
+                                          [info["fp16_centering"]] if args.precision == "fp16x3" and d <= 64 else None),
+                       "fp16_rho": info["fp16_rho"],
                        "lists": {"target": "per target (eq. 2.5)", "leaf": "leaf-grouped"}[args.lists],
                        "l2": "inputs larger than L2 (coordinates %.0f MB)" % (N * info["d_pad"] * 4 / 1e6)},
             "targets_x_rhs_per_s": value * r,

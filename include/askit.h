@@ -114,7 +114,9 @@ void askit_default_params(askit_params *p);
  *   out     receives the tree handle (library-owned; askit_destroy frees it).
  * Errors: INVALID_ARG for N < 1, d < 1, m < 2, kappa outside 1..min(32, N-1),
  * s_max < 1, non-positive h or id_tol < 0; OOM when device memory runs out;
- * UNSUPPORTED for N >= 2^31.  Blocks until the setup is complete.
+ * UNSUPPORTED for N >= 2^31, leaf_size or s_max above 2048 (16 sub-blocks
+ * of 128 rows) or a tree deeper than 25 levels.  Blocks until the setup is
+ * complete.
  */
 askit_status askit_setup(const float *X_dev, int64_t N, int32_t d, int64_t ldx,
                          const float *h_dev, const int32_t *knn_dev,
@@ -240,9 +242,12 @@ askit_status askit_graph_destroy(askit_graph g);
  *   schedule    0: sub-blocks dealt heaviest first to the least-loaded CTA;
  *               1: sub-blocks in tree order, cut into contiguous equal-cost
  *                  ranges (consecutive sub-blocks share targets: L2 reuse);
- *   stages      gathered target-row stages of the FP16x3 kernel (2 or 3);
+ *   stages      target-row stages of the FP16x3 kernels (per sub-block
+ *               centering: 2 or 3, 2 with paired items; global centering:
+ *               3 or 4);
  *   tiled_runs  1: runs of 8 consecutive target rows arrive in one tiled
- *               copy (FP16x3 kernel), 0: every row by tile::gather4;
+ *               copy (per-sub-block FP16x3 kernel), 0: every row by
+ *               tile::gather4;
  *   pairs       1: the FP16x3 kernel takes sub-blocks 2k and 2k+1 of a node
  *               (same targets) in one 256-column item (schedule 2: the
  *               leaders dealt longest first), r <= 4.
@@ -259,9 +264,10 @@ typedef struct {
 } askit_tune_entry;
 askit_status askit_autotune(askit_tree t, int32_t reps, void *stream, askit_tune_entry *out, int32_t max_out,
                             int32_t *n_out);
-/* Set the launch configuration directly (schedule 0|1, stages 2|3,
- * tiled_runs 0|1, pairs 0|1; pairs needs stages 2 and uses its own
- * schedule).  Host call; applies to later evaluations of the tree. */
+/* Set the launch configuration directly (schedule 0|1, stages 2..4,
+ * tiled_runs 0|1, pairs 0|1; pairs uses its own schedule; each kernel takes
+ * the nearest stage count it has).  Host call; applies to later evaluations
+ * of the tree. */
 askit_status askit_set_launch(askit_tree t, int32_t schedule, int32_t stages, int32_t tiled_runs, int32_t pairs);
 
 /*
@@ -288,6 +294,22 @@ askit_status askit_footprint(askit_tree t, int32_t kind, int64_t n, int32_t r, s
 /* Precision of subsequent askit_evaluate calls (ASKIT_PREC_*). */
 askit_status askit_set_precision(askit_tree t, int32_t precision);
 
+/*
+ * Target centering of the FP16x3 kernels for d <= 64 (an implementation
+ * choice below the paper's level; the result changes only within rounding):
+ *   0 automatic (default): mode 2 while askit_info.fp16_rho <= 512, else 1;
+ *   1 every item's target rows are centered on the source sub-block's mean
+ *     and split on the chip (the smallest rounding error);
+ *   2 every point is centered once on the data mean and pre-split in HBM, so
+ *     target rows reach the tensor cores without conversion (the fastest;
+ *     relative error of u about 1e-5 against about 1e-6 for mode 1, both
+ *     within the split-product tolerance 1e-4).
+ * Out-of-sample batches with a target outside the FP16-safe range of mode 2
+ * (beyond about 7 times the data's extent from its mean) take mode 1.
+ * Host call; applies to later evaluations.
+ */
+askit_status askit_set_fp16_centering(askit_tree t, int32_t mode);
+
 /* Sizes and work counts (host call). */
 typedef struct {
     int64_t N;
@@ -307,6 +329,13 @@ typedef struct {
                                  (Algorithm 2), sampled rows (eq. 2.4), skeletons and
                                  interpolation matrices (Algorithm 3), evaluation
                                  operands, work lists */
+    int32_t fp16_centering;   /* FP16x3 kernel askit_evaluate takes (d <= 64): 1 targets
+                                 centered per source sub-block on the chip, 2 all points
+                                 pre-split around the data mean (askit_set_fp16_centering) */
+    int32_t pad_;
+    double fp16_rho;          /* max_j sc_j * max_i |x_i - mean|^2, sc = c log2(e) / h_j^2:
+                                 the global form's exponent error is a few 2^-24 rho; the
+                                 automatic choice takes it while rho <= 512 */
 } askit_info;
 askit_status askit_get_info(askit_tree t, askit_info *info);
 
@@ -333,8 +362,23 @@ enum {
 };
 askit_status askit_get_structure(askit_tree t, int32_t which, void *host, size_t bytes);
 
-/* Waits for the tree's work on `stream` and reports sticky kernel errors. */
+/* Waits for the tree's work on `stream` and reports sticky kernel errors
+ * (TIMEOUT: a kernel gave up a bounded wait and its results are invalid).  A
+ * reported status is cleared, so the tree serves later calls. */
 askit_status askit_sync(askit_tree t, void *stream);
+
+/*
+ * Poll limit of the bounded mbarrier waits in the FP16x3 evaluation kernel
+ * (every wait of a producer/consumer role; each poll is one try_wait, which
+ * suspends the thread for a short time before giving up).  0 restores the
+ * default of 2^24 polls, far beyond any legitimate wait.  A small limit makes
+ * the waits give up: the kernel then records a sticky timeout (askit_sync
+ * returns TIMEOUT), every role leaves its loop, the copies and MMAs in
+ * flight are waited for, TMEM is freed and the kernel returns, so the
+ * context stays usable.  A debugging and test aid (no counterpart in the
+ * paper).  Host call; applies to later evaluations of the tree.
+ */
+askit_status askit_set_wait_limit(askit_tree t, int32_t polls);
 
 /* Frees the tree and everything it owns (waits for its work first). */
 askit_status askit_destroy(askit_tree t);
@@ -359,7 +403,7 @@ const char *askit_last_error(void);
  *   ids_dev [Q, kappa] int32 and dist_dev [Q, kappa] double receive the
  *           neighbors, nearest first.  All buffers are caller-owned.
  * Limits: Q <= 8192 per call (INVALID_ARG beyond), 1 <= kappa <= 32,
- * d <= 1536.  Scratch: a fixed 3 MiB device array inside the library,
+ * d <= 1536, N < 2^31 - 1024 (ids are int32; UNSUPPORTED beyond).  Scratch: a fixed 3 MiB device array inside the library,
  * resident on every GPU that loads it until the process exits.  The first
  * call on a device looks up that array's device address (so make the first
  * call before any stream capture); every call shares the array, so calls

@@ -32,7 +32,7 @@ EXPORTS = ["askit_default_params", "askit_setup", "askit_set_weights", "askit_ev
            "askit_weights_set", "askit_weights_evaluate", "askit_weights_evaluate_targets",
            "askit_weights_destroy", "askit_footprint", "askit_graph_create", "askit_graph_launch",
            "askit_graph_destroy", "askit_autotune", "askit_set_launch", "askit_knn_targets",
-           "askit_kernel_timing"]
+           "askit_kernel_timing", "askit_set_wait_limit", "askit_set_fp16_centering"]
 
 
 class TuneEntry(C.Structure):
@@ -59,7 +59,8 @@ class Info(C.Structure):
                 ("skel_total", C.c_int64), ("skel_rows_padded", C.c_int64), ("n_blocks", C.c_int64),
                 ("n_items", C.c_int64), ("n_entries", C.c_int64), ("pairs_algorithmic", C.c_int64), ("pairs_computed", C.c_int64),
                 ("near_total", C.c_int64), ("far_total", C.c_int64), ("device_bytes", C.c_int64),
-                ("n_batches", C.c_int64), ("setup_ms", C.c_double * 7)]
+                ("n_batches", C.c_int64), ("setup_ms", C.c_double * 7), ("fp16_centering", C.c_int32),
+                ("pad_", C.c_int32), ("fp16_rho", C.c_double)]
 
 
 def load(path: str | None = None):
@@ -96,6 +97,8 @@ def load(path: str | None = None):
             L.askit_graph_destroy.argtypes = [V]
             L.askit_autotune.argtypes = [V, I32, V, C.POINTER(TuneEntry), I32, C.POINTER(I32)]
             L.askit_set_launch.argtypes = [V, I32, I32, I32, I32]
+            L.askit_set_wait_limit.argtypes = [V, I32]
+            L.askit_set_fp16_centering.argtypes = [V, I32]
             L.askit_knn_targets.argtypes = [V, V, I64, I64, V, V, V]
             L.askit_kernel_timing.argtypes = [V, I32, C.POINTER(D), C.POINTER(I64)]
             L.askit_status_string.restype = C.c_char_p
@@ -263,9 +266,9 @@ class Tree:
     def autotune(self, reps: int = 3, stream=None) -> list[dict]:
         """Time the evaluation kernel's launch configurations on this tree
         (weights must be set) and keep the fastest; returns every candidate."""
-        out = (TuneEntry * 16)()
+        out = (TuneEntry * 32)()
         n = C.c_int32()
-        _check(load().askit_autotune(self._t, reps, _stream(stream), out, 16, C.byref(n)))
+        _check(load().askit_autotune(self._t, reps, _stream(stream), out, 32, C.byref(n)))
         return [{"schedule": ("lpt", "tree_order", "lpt_pairs")[e.schedule], "stages": e.stages,
                  "tiled_runs": bool(e.tiled_runs), "pairs": bool(e.pairs), "chosen": bool(e.chosen), "ms": e.ms}
                 for e in out[:n.value]]
@@ -274,6 +277,16 @@ class Tree:
         """Set the evaluation kernel's launch configuration (see autotune)."""
         _check(load().askit_set_launch(self._t, {"lpt": 0, "tree_order": 1}[schedule], stages, int(tiled_runs),
                                        int(pairs)))
+
+    def set_fp16_centering(self, mode: str = "auto"):
+        """FP16x3 target centering: "auto", "block" (per source sub-block, on
+        the chip) or "global" (pre-split around the data mean)."""
+        _check(load().askit_set_fp16_centering(self._t, {"auto": 0, "block": 1, "global": 2}[mode]))
+
+    def set_wait_limit(self, polls: int):
+        """Poll limit of the FP16x3 kernel's bounded waits (0: the default);
+        a debugging and test aid -- a tiny limit makes the waits give up."""
+        _check(load().askit_set_wait_limit(self._t, int(polls)))
 
     def kernel_timing(self, enable: bool):
         """Start (True) or end (False) timing the evaluation kernel's own

@@ -14,7 +14,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libaskit.so")
 
 SOURCES = ["capi.cu", "setup_sort.cu", "setup_tree.cu", "setup_skel.cu", "eval_lists.cu",
-           "weights.cu", "eval_simt.cu", "eval_tc.cu", "eval_tc_wide.cu", "eval_tc16.cu"]
+           "weights.cu", "eval_simt.cu", "eval_tc.cu", "eval_tc_wide.cu", "eval_tc16.cu", "eval_g16.cu"]
 # setup stages are bit-exact FP64: no contraction into fused multiply-adds anywhere
 NO_FMAD = {"setup_tree.cu", "setup_skel.cu"}
 
@@ -38,7 +38,9 @@ def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    deps = [src, os.path.join(CSRC, "askit_impl.cuh"), os.path.join(ROOT, "include", "askit.h"), __file__]
+    # every header of csrc/ (askit_impl.cuh, tc_ptx.cuh, ...) and the public header
+    deps = [src, os.path.join(ROOT, "include", "askit.h"), __file__]
+    deps += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -110,6 +110,14 @@ struct __align__(16) EvalItem {
     int32_t pad_[3];
 };
 
+// Target rows of one evaluation in the global-centered FP16x3 form: hi / lo
+// [rows, TC_K] FP16 of (x - xbar) g_scale and n [rows] = |x - xbar|^2.
+struct QuerySplit {
+    const uint16_t *hi = nullptr, *lo = nullptr;
+    const float *n = nullptr;
+    int64_t rows = 0;
+};
+
 // Work lists of one set of targets (in-sample, or one out-of-sample batch).
 struct WorkLists {
     int64_t T = 0, n_entries = 0, n_items = 0, n_blocks = 0;
@@ -228,6 +236,19 @@ struct askit_tree_s {
     float *nrmc_t = nullptr, *nrmc_s = nullptr;
     int64_t srows = 0;             // rows of the skeleton-pool arrays
 
+    // global-centered FP16x3 operands (d <= TC_K, eval_g16.cu): every point
+    // centered on the data mean g_xbar, prescaled by g_scale and split into
+    // FP16 hi + lo; n = |x - xbar|^2.  g_rho = max_j sc_j * max_i n_i decides
+    // whether they hold FP32-grade accuracy (g_ok)
+    uint16_t *Xg_hi = nullptr, *Xg_lo = nullptr, *Sg_hi = nullptr, *Sg_lo = nullptr;
+    float *ng_t = nullptr, *ng_s = nullptr;
+    float *g_xbar = nullptr;       // [TC_K] device
+    float g_scale = 1.f;
+    double g_rho = 0.0;
+    bool g_ok = false;
+    int fp16_centering = 0;        // 0 automatic (global when g_ok), 1 per sub-block, 2 global
+    void *g16 = nullptr;           // tensor maps of the global-centered kernel
+
     int *d_status = nullptr;       // sticky kernel status
     int *d_ticket = nullptr;       // persistent-kernel work counter
     void *tc = nullptr;            // tensor-core kernel state (tensor maps)
@@ -243,6 +264,7 @@ struct askit_tree_s {
     int tune_stages = 3;           // gathered target-row stages of the FP16x3 kernel (2 or 3)
     int tune_runs = 1;             // 8-row tiled loads for runs of consecutive targets
     int tune_pairs = 0;            // FP16x3: items over two sub-blocks of a node (256 columns)
+    int spin_limit = 0;            // polls of the FP16x3 kernel's bounded waits (0: default)
     int kw = TC_K;                 // row width of the pre-split operands and centers
     // wall time of the setup stages (askit_info.setup_ms)
     double setup_ms[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -402,7 +424,7 @@ askit_status upward_weights(askit_tree t, WeightCtx &c, const float *W, int r, i
 askit_status eval_simt(askit_tree t, const WeightCtx &c, const float *Xq, int64_t ldq, const WorkLists &w,
                        float *partial, cudaStream_t s);
 askit_status eval_tc(askit_tree t, const WeightCtx &c, int precision, const float *Xq, int64_t ldq,
-                     int64_t q_rows, const WorkLists &w, float *partial, cudaStream_t s);
+                     int64_t q_rows, const QuerySplit *qs, const WorkLists &w, float *partial, cudaStream_t s);
 void eval_tc_free(askit_tree t);
 askit_status eval_tc_wide(askit_tree t, const WeightCtx &c, int precision, const float *Xq, int64_t ldq,
                           int64_t q_rows, const WorkLists &w, float *partial, cudaStream_t s);
@@ -410,6 +432,17 @@ void eval_tc_wide_free(askit_tree t);
 askit_status eval_tc16(askit_tree t, const WeightCtx &c, int precision, const float *Xq, int64_t ldq, int64_t q_rows,
                        const WorkLists &w, float *partial, cudaStream_t s);
 void eval_tc16_free(askit_tree t);
+// eval_g16.cu: the global-centered FP16x3 kernel (targets pre-split in q)
+askit_status eval_g16(askit_tree t, const WeightCtx &c, const QuerySplit &q, const WorkLists &w, float *partial,
+                      cudaStream_t s);
+void eval_g16_free(askit_tree t);
+askit_status build_g16_operands(askit_tree t, cudaStream_t s);
+askit_status g16_split_rows(const float *X, int64_t ldx, int d, int64_t rows, const float *xbar, float scale,
+                            uint16_t *hi, uint16_t *lo, float *n, int *overflow, cudaStream_t s);
+// whether FP16x3 evaluations of this tree take the global-centered kernel
+inline bool use_g16(const askit_tree_s *t) {
+    return t->Xg_hi && (t->fp16_centering == 2 || (t->fp16_centering == 0 && t->g_ok));
+}
 askit_status knn_shortlist_tc16(askit_tree t, const float *Yp, int64_t T, const float *U, int *cnt, int32_t *cand,
                                 int cap, float eta, cudaStream_t s);
 // exact kNN of out-of-sample points Y [T, d] against the tree's points:

@@ -104,6 +104,17 @@ askit_status validate(const askit_params *p, int64_t N, int32_t d, int64_t ldx, 
         return ASKIT_ERR_INVALID_ARG;
     }
     if (p->s_max < 1 || p->s_min < 0 || p->ell_extra < 0) { askit_set_error("need s_max >= 1, s_min >= 0, ell_extra >= 0"); return ASKIT_ERR_INVALID_ARG; }
+    // a source block (a leaf's points or a skeleton) is cut into at most 16
+    // sub-blocks of ASK_BLK_N rows (the work lists keep the sub-block index in
+    // 4 bits), and a node's heap index must fit the lists' 27-bit node field
+    if (p->leaf_size > 16 * ASK_BLK_N || p->s_max > 16 * ASK_BLK_N) {
+        askit_set_error("leaf_size and s_max must be at most %d", 16 * ASK_BLK_N);
+        return ASKIT_ERR_UNSUPPORTED;
+    }
+    if (tree_depth(N, p->leaf_size) > 25) {
+        askit_set_error("the tree would have more than 2^25 leaves; raise leaf_size");
+        return ASKIT_ERR_UNSUPPORTED;
+    }
     if (!(p->id_tol >= 0.0) || !(p->kernel_scale > 0.0)) { askit_set_error("need id_tol >= 0 and kernel_scale > 0"); return ASKIT_ERR_INVALID_ARG; }
     if (p->bw_mode == ASKIT_BW_CONSTANT && !(p->h > 0.0)) { askit_set_error("h must be > 0"); return ASKIT_ERR_INVALID_ARG; }
     if (p->bw_mode == ASKIT_BW_ARRAY && !h_dev) { askit_set_error("ASKIT_BW_ARRAY needs h_dev"); return ASKIT_ERR_INVALID_ARG; }
@@ -270,12 +281,12 @@ namespace {
 // Evaluate over one set of work lists: every (target, sub-block) entry's
 // partial sum, then each target's entries summed in their fixed order.
 askit_status run_eval(askit_tree t, const WeightCtx &c, int precision, const float *Xq, int64_t ldq,
-                      int64_t q_rows, const WorkLists &w, float *partial, const int32_t *out_rows, float *U,
-                      int64_t ldu, cudaStream_t s) {
+                      int64_t q_rows, const QuerySplit *qs, const WorkLists &w, float *partial,
+                      const int32_t *out_rows, float *U, int64_t ldu, cudaStream_t s) {
     if (precision == ASKIT_PREC_SIMT_FP32)
         ASK_TRY(eval_simt(t, c, Xq, ldq, w, partial, s));
     else
-        ASK_TRY(eval_tc(t, c, precision, Xq, ldq, q_rows, w, partial, s));
+        ASK_TRY(eval_tc(t, c, precision, Xq, ldq, q_rows, qs, w, partial, s));
     return reduce_partials(w, partial, c.r, out_rows, U, ldu, s);
 }
 
@@ -294,8 +305,15 @@ askit_status evaluate_ctx(askit_tree t, const WeightCtx &c, float *U_dev, int64_
     // of Xt and its results go to the points perm[t0 .. t1)
     for (size_t b = 0; b < t->wl.size(); ++b) {
         const int64_t t0 = t->wl_t0[b];
-        ASK_TRY(run_eval(t, c, t->precision, t->Xt + t0 * t->d_pad, t->d_pad, t->N_pad - t0, t->wl[b], c.partial,
-                         t->perm + t0, U_dev, ldu, s));
+        QuerySplit q;   // the same target rows in the global-centered FP16x3 form
+        if (t->Xg_hi) {
+            q.hi = t->Xg_hi + t0 * TC_K;
+            q.lo = t->Xg_lo + t0 * TC_K;
+            q.n = t->ng_t + t0;
+            q.rows = t->N_pad - t0;
+        }
+        ASK_TRY(run_eval(t, c, t->precision, t->Xt + t0 * t->d_pad, t->d_pad, t->N_pad - t0, t->Xg_hi ? &q : nullptr,
+                         t->wl[b], c.partial, t->perm + t0, U_dev, ldu, s));
     }
     return ASKIT_OK;
 }
@@ -419,6 +437,10 @@ askit_status evaluate_targets_ctx(askit_tree t, const WeightCtx &c, const float 
     size_t cb = 0;
     WorkLists w;
     float *partial = nullptr;
+    uint16_t *yg_hi = nullptr, *yg_lo = nullptr;
+    float *yg_n = nullptr;
+    int *yg_flag = nullptr;
+    QuerySplit qs;
     int64_t T_pad = (T + ASK_TILE_M - 1) / ASK_TILE_M * ASK_TILE_M;
     askit_status rc = ASKIT_OK;
 #define OTRY(x) do { rc = (x); if (rc != ASKIT_OK) goto out; } while (0)
@@ -443,7 +465,27 @@ askit_status evaluate_targets_ctx(askit_tree t, const WeightCtx &c, const float 
     OTRY(oos_prune_sets(t, ids_s, T, kappa, sets, s));
     OTRY(build_work_lists(t, sets, kappa, nullptr, T, w, tmp, s));
     OTRY(tmp.alloc(&partial, (size_t)w.n_entries * c.r));
-    OTRY(run_eval(t, c, t->precision, Yt, t->d_pad, T_pad, w, partial, order, U_dev, ldu, s));
+    if (t->precision == ASKIT_PREC_FP16X3 && t->d <= TC_K && use_g16(t)) {
+        // the targets in the global-centered FP16x3 form; a batch reaching
+        // outside the FP16-safe range (far from the data) takes the
+        // per-sub-block centered kernel instead
+        OTRY(tmp.alloc(&yg_hi, (size_t)T_pad * TC_K));
+        OTRY(tmp.alloc(&yg_lo, (size_t)T_pad * TC_K));
+        OTRY(tmp.alloc(&yg_n, T_pad));
+        OTRY(tmp.alloc(&yg_flag, 1));
+        if (cudaMemsetAsync(yg_flag, 0, sizeof(int), s) != cudaSuccess) { askit_set_error("flag"); rc = ASKIT_ERR_CUDA; goto out; }
+        OTRY(g16_split_rows(Yt, t->d_pad, d, T_pad, t->g_xbar, t->g_scale, yg_hi, yg_lo, yg_n, yg_flag, s));
+        int flag = 0;
+        if (cudaMemcpyAsync(&flag, yg_flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) { askit_set_error("range flag"); rc = ASKIT_ERR_CUDA; goto out; }
+        if (!flag) {
+            qs.hi = yg_hi;
+            qs.lo = yg_lo;
+            qs.n = yg_n;
+            qs.rows = T_pad;
+        }
+    }
+    OTRY(run_eval(t, c, t->precision, Yt, t->d_pad, T_pad, qs.hi ? &qs : nullptr, w, partial, order, U_dev, ldu, s));
     if (cudaStreamSynchronize(s) != cudaSuccess) { askit_set_error("out-of-sample evaluate: %s", cudaGetErrorString(cudaGetLastError())); rc = ASKIT_ERR_CUDA; }
 out:
 #undef OTRY
@@ -503,6 +545,9 @@ askit_status askit_get_info(askit_tree t, askit_info *info) {
     }
     info->device_bytes = (int64_t)t->arena.bytes;
     info->n_batches = (int64_t)t->wl.size();
+    info->fp16_centering = use_g16(t) ? 2 : 1;
+    info->pad_ = 0;
+    info->fp16_rho = t->g_rho;
     for (int k = 0; k < 7; ++k) info->setup_ms[k] = t->setup_ms[k];
     return ASKIT_OK;
 }
@@ -565,9 +610,12 @@ askit_status askit_sync(askit_tree t, void *stream) {
     ASK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     int st = 0;
     ASK_CUDA(cudaMemcpy(&st, t->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st == ASK_DEV_OK) return ASKIT_OK;
+    // reported once: cleared so that the tree serves later calls
+    ASK_CUDA(cudaMemset(t->d_status, 0, sizeof(int)));
     if (st == ASK_DEV_TIMEOUT) { askit_set_error("a kernel gave up a bounded wait"); return ASKIT_ERR_TIMEOUT; }
-    if (st != ASK_DEV_OK) { askit_set_error("kernel status %d", st); return ASKIT_ERR_CUDA; }
-    return ASKIT_OK;
+    askit_set_error("kernel status %d", st);
+    return ASKIT_ERR_CUDA;
 }
 
 askit_status askit_kernel_timing(askit_tree t, int32_t enable, double *ms, int64_t *launches) {
@@ -661,13 +709,9 @@ askit_status askit_knn_targets(askit_tree t, const float *Y_dev, int64_t T, int6
 }
 
 askit_status askit_set_launch(askit_tree t, int32_t schedule, int32_t stages, int32_t tiled_runs, int32_t pairs) {
-    if (!t || schedule < 0 || schedule > 1 || stages < 2 || stages > 3 || tiled_runs < 0 || tiled_runs > 1 ||
+    if (!t || schedule < 0 || schedule > 1 || stages < 2 || stages > 4 || tiled_runs < 0 || tiled_runs > 1 ||
         pairs < 0 || pairs > 1) {
-        askit_set_error("need schedule 0|1, stages 2|3, tiled_runs 0|1, pairs 0|1");
-        return ASKIT_ERR_INVALID_ARG;
-    }
-    if (pairs && stages != 2) {
-        askit_set_error("paired items run with two stages");
+        askit_set_error("need schedule 0|1, stages 2..4, tiled_runs 0|1, pairs 0|1");
         return ASKIT_ERR_INVALID_ARG;
     }
     t->tune_sched = pairs ? 0 : schedule;
@@ -675,6 +719,18 @@ askit_status askit_set_launch(askit_tree t, int32_t schedule, int32_t stages, in
     t->tune_runs = tiled_runs;
     t->tune_pairs = pairs;
     use_schedule(t);
+    return ASKIT_OK;
+}
+
+askit_status askit_set_fp16_centering(askit_tree t, int32_t mode) {
+    if (!t || mode < 0 || mode > 2) { askit_set_error("need a tree and mode 0, 1 or 2"); return ASKIT_ERR_INVALID_ARG; }
+    t->fp16_centering = mode;
+    return ASKIT_OK;
+}
+
+askit_status askit_set_wait_limit(askit_tree t, int32_t polls) {
+    if (!t || polls < 0) { askit_set_error("need a tree and polls >= 0"); return ASKIT_ERR_INVALID_ARG; }
+    t->spin_limit = polls;
     return ASKIT_OK;
 }
 
@@ -690,15 +746,23 @@ askit_status askit_autotune(askit_tree t, int32_t reps, void *stream, askit_tune
     std::vector<Cand> cand;
     const bool tc = t->precision != ASKIT_PREC_SIMT_FP32;
     const bool fp16 = t->precision == ASKIT_PREC_FP16X3 && t->d <= TC_K;
+    // the global-centered kernel has 3 or 4 target-row stages and copies its
+    // rows without TMA (no tiled runs); the per-sub-block kernel 2 or 3 stages
+    // (two with paired items) and tiled runs on or off
+    const bool g16 = fp16 && use_g16(t);
+    const int st_lo = fp16 ? (g16 ? 3 : 2) : t->tune_stages;
+    const int st_hi = fp16 ? (g16 ? 4 : 3) : t->tune_stages;
+    const int ru_lo = fp16 && !g16 ? 0 : t->tune_runs, ru_hi = fp16 && !g16 ? 1 : t->tune_runs;
     for (int sc = 0; sc < (tc ? 2 : 1); ++sc)
-        for (int st = (fp16 ? 2 : t->tune_stages); st <= (fp16 ? 3 : t->tune_stages); ++st)
-            for (int ru = (fp16 ? 0 : t->tune_runs); ru <= (fp16 ? 1 : t->tune_runs); ++ru)
+        for (int st = st_lo; st <= st_hi; ++st)
+            for (int ru = ru_lo; ru <= ru_hi; ++ru)
                 cand.push_back({sc, st, ru, 0, 0.0});
-    // paired 256-column items (FP16x3, r <= 4): their own schedule, two stages
+    // paired 256-column items (FP16x3, r <= 4): their own schedule
     int64_t n_pairs = 0;
     for (const WorkLists &w : t->wl) n_pairs += w.n_pairs;
     if (fp16 && t->dw.r <= 4 && n_pairs > 0)
-        for (int ru = 0; ru <= 1; ++ru) cand.push_back({2, 2, ru, 1, 0.0});
+        for (int st = g16 ? st_lo : 2; st <= (g16 ? st_hi : 2); ++st)
+            for (int ru = ru_lo; ru <= ru_hi; ++ru) cand.push_back({2, st, ru, 1, 0.0});
     float *U = nullptr;
     ASK_CUDA(cudaMallocAsync(&U, sizeof(float) * (size_t)t->N * std::max(1, t->dw.r), s));
     cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -507,6 +507,7 @@ askit_status build_tc_operands(askit_tree t, cudaStream_t s) {
     cudaFreeAsync(d_nd0, s);
     cudaFreeAsync(d_ndn, s);
     ASK_CUDA(cudaStreamSynchronize(s));
+    if (!wide) ASK_TRY(build_g16_operands(t, s));
     return ASKIT_OK;
 }
 

@@ -648,8 +648,11 @@ askit_status launch(askit_tree t, TcState *st, const CUtensorMap &map_q, const T
 }  // namespace
 
 askit_status eval_tc(askit_tree t, const WeightCtx &c, int precision, const float *Xq, int64_t ldq,
-                     int64_t q_rows, const WorkLists &w, float *partial, cudaStream_t s) {
+                     int64_t q_rows, const QuerySplit *qs, const WorkLists &w, float *partial, cudaStream_t s) {
     if (t->d > TC_K) return eval_tc_wide(t, c, precision, Xq, ldq, q_rows, w, partial, s);
+    // FP16x3 with pre-split, globally centered targets where that keeps FP32
+    // grade (eval_g16.cu)
+    if (precision == ASKIT_PREC_FP16X3 && qs && use_g16(t)) return eval_g16(t, c, *qs, w, partial, s);
     // FP16x3 centers both sides on the sub-block mean (eval_tc16.cu); BF16x3
     // keeps the per-item target centering below: its 8-bit significands leave
     // a residual of about 2^-17 of |a| |b| per product, so the smaller |a| of
@@ -713,4 +716,5 @@ void eval_tc_free(askit_tree t) {
     t->tc = nullptr;
     eval_tc_wide_free(t);
     eval_tc16_free(t);
+    eval_g16_free(t);
 }

@@ -102,6 +102,7 @@ struct T16Args {
     const int32_t *partner;   // [n_blocks] paired follower block, or -1 (NB == 2)
     float *partial;
     int *status;
+    int spin;                 // polls of a bounded mbarrier wait before it gives up
 };
 
 // UNI == 1: one bandwidth for all sources (c log2(e) / h^2 = sc for every j):
@@ -212,13 +213,13 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                 const int cnt = cnt_next;
                 if (it + NLG < i1) cnt_next = args.items[it + NLG].cnt;   // in flight while this item waits
                 const int sa = li & 1, sr = li % NRAW, a4 = li % NACC;
-                if (!mbar_wait(BAR_A_EMPTY(sa), ((li >> 1) & 1) ^ 1, abort_flag, args.status)) goto loader_done;
+                if (!mbar_wait(BAR_A_EMPTY(sa), ((li >> 1) & 1) ^ 1, abort_flag, args.status, args.spin)) goto loader_done;
                 // the |a|^2 slot of this item's accumulator: free once the
                 // epilogue of the item NACC back has read it (at its start)
-                if (!mbar_wait(BAR_N_EMPTY(a4), ((li / NACC) & 1) ^ 1, abort_flag, args.status)) goto loader_done;
-                if (!mbar_wait(BAR_R_FULL(sr), (li / NRAW) & 1, abort_flag, args.status)) goto loader_done;
+                if (!mbar_wait(BAR_N_EMPTY(a4), ((li / NACC) & 1) ^ 1, abort_flag, args.status, args.spin)) goto loader_done;
+                if (!mbar_wait(BAR_R_FULL(sr), (li / NRAW) & 1, abort_flag, args.status, args.spin)) goto loader_done;
                 if (need_blk) {
-                    if (!mbar_wait(BAR_BLK_FULL(lb & 1), (lb >> 1) & 1, abort_flag, args.status)) goto loader_done;
+                    if (!mbar_wait(BAR_BLK_FULL(lb & 1), (lb >> 1) & 1, abort_flag, args.status, args.spin)) goto loader_done;
                     need_blk = false;
                     if (kin)
                         cc = *reinterpret_cast<const float4 *>(sm + S::BLK + (lb & 1) * S::BLKSLOT + S::BLK_CENT +
@@ -301,7 +302,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
         for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci, ++lb) {
             const int b = args.cta_blocks[ci];
             const int bs = lb & 1;
-            if (!mbar_wait(BAR_BLK_FULL(bs), (lb >> 1) & 1, abort_flag, args.status)) goto epi_done;
+            if (!mbar_wait(BAR_BLK_FULL(bs), (lb >> 1) & 1, abort_flag, args.status, args.spin)) goto epi_done;
             const float4 *cv4 = reinterpret_cast<const float4 *>(sm + S::BLK + bs * S::BLKSLOT + S::BLK_COLV);
             const float *cwp = reinterpret_cast<const float *>(sm + S::BLK + bs * S::BLKSLOT + S::BLK_COLW);
             const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
@@ -316,7 +317,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                 if (it + 1 < i1) nxt = args.items[it + 1];   // in flight while this item waits
                 const int nrows = (item.nrows & 0x7fffffff) + ncols_f;
                 const int e0f = pb >= 0 ? args.items[f0 + (it - i0)].e0 : 0;
-                if (!mbar_wait(BAR_T_FULL(a4), (li / NACC) & 1, abort_flag, args.status)) goto epi_done;
+                if (!mbar_wait(BAR_T_FULL(a4), (li / NACC) & 1, abort_flag, args.status, args.spin)) goto epi_done;
                 tc_fence_after();
                 const float pt = a_norm[a4 * 128 + row];   // NACC <= 4 slots
                 mbar_arrive(BAR_N_EMPTY(a4));
@@ -483,7 +484,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                         mbar_arrive(BAR_T_EMPTY(a4));
                         continue;
                     }
-                    if (!mbar_wait(BAR_X_FULL(a4), (li / NACC) & 1, abort_flag, args.status)) goto epi_done;
+                    if (!mbar_wait(BAR_X_FULL(a4), (li / NACC) & 1, abort_flag, args.status, args.spin)) goto epi_done;
 #pragma unroll
                     for (int z = 0; z < RC; ++z) acc[z] += xb[z];
                 }
@@ -537,7 +538,7 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
             int rn[4] = {0, 0, 0, 0};
             if (ci2 < c_end) rows(it2, rn);
             const int sr = li % NRAW;
-            if (!mbar_wait(BAR_R_EMPTY(sr), ((li / NRAW) & 1) ^ 1, abort_flag, args.status)) goto gather_done;
+            if (!mbar_wait(BAR_R_EMPTY(sr), ((li / NRAW) & 1) ^ 1, abort_flag, args.status, args.spin)) goto gather_done;
             ++issued;
             if (lane == 0) mbar_expect_tx(BAR_R_FULL(sr), bytes);
             __syncwarp();
@@ -568,6 +569,8 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
     } else if (warp == W_MMA && lane == 0) {
         // ------------------------------------- sub-block loads + MMA issuer
         int li = 0, lb = 0, b_issued = 0;
+        int blk_last[2] = {-1, -1};   // last block whose column data went to slot 0 / 1
+        int li_done = -1;             // last item whose MMAs were committed
         for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci, ++lb) {
             const int b = args.cta_blocks[ci];
             const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
@@ -582,9 +585,10 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
             // N covers every 32-column chunk the epilogue reads, so no column it
             // reads holds a stale accumulator
             const uint32_t idesc = make_idesc(FMT, T16_ROWS, (ncols + 31) & ~31);
-            if (!mbar_wait(BAR_B_EMPTY, (lb & 1) ^ 1, abort_flag, args.status)) goto mma_done;
-            if (!mbar_wait(BAR_BLK_EMPTY(bs), ((lb >> 1) & 1) ^ 1, abort_flag, args.status)) goto mma_done;
+            if (!mbar_wait(BAR_B_EMPTY, (lb & 1) ^ 1, abort_flag, args.status, args.spin)) goto mma_done;
+            if (!mbar_wait(BAR_BLK_EMPTY(bs), ((lb >> 1) & 1) ^ 1, abort_flag, args.status, args.spin)) goto mma_done;
             b_issued = lb + 1;
+            blk_last[bs] = lb;
             mbar_expect_tx(BAR_B_FULL, (uint32_t)(2 * nsb * T16_REGION));
             for (int h = 0; h < nsb; ++h) {
                 tma_load_2d(sbase + S::B_HI + h * T16_REGION, far ? &map_s_hi : &map_t_hi, 0, first.row0 + 128 * h,
@@ -602,9 +606,9 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                 bulk_copy(slot + S::BLK_COLW, args.colw + (int64_t)first.cidx * 128 * RC, colw_bytes, BAR_BLK_FULL(bs));
             for (int it = i0; it < i1; ++it, ++li) {
                 const int sa = li & 1, a4 = li % NACC;
-                if (!mbar_wait(BAR_A_FULL(sa), (li >> 1) & 1, abort_flag, args.status)) goto mma_done;
-                if (it == i0 && !mbar_wait(BAR_B_FULL, lb & 1, abort_flag, args.status)) goto mma_done;
-                if (!mbar_wait(BAR_T_EMPTY(a4), ((li / NACC) & 1) ^ 1, abort_flag, args.status)) goto mma_done;
+                if (!mbar_wait(BAR_A_FULL(sa), (li >> 1) & 1, abort_flag, args.status, args.spin)) goto mma_done;
+                if (it == i0 && !mbar_wait(BAR_B_FULL, lb & 1, abort_flag, args.status, args.spin)) goto mma_done;
+                if (!mbar_wait(BAR_T_EMPTY(a4), ((li / NACC) & 1) ^ 1, abort_flag, args.status, args.spin)) goto mma_done;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)(a4 * 128 * NB);
                 const uint32_t a_hi = sbase + S::A0 + sa * 2 * T16_REGION, a_lo = a_hi + T16_REGION;
@@ -625,14 +629,19 @@ eval_tc16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_cons
                 tc_commit(BAR_A_EMPTY(sa));
                 tc_commit(BAR_T_FULL(a4));
                 if (it == i1 - 1) tc_commit(BAR_B_EMPTY);
+                li_done = li;
             }
         }
     mma_done:
-        // the last sub-block's copies may still be landing after an abort
-        if (b_issued > 0) {
-            mbar_drain(BAR_B_FULL, (b_issued - 1) & 1);
-            mbar_drain(BAR_BLK_FULL((b_issued - 1) & 1), ((b_issued - 1) >> 1) & 1);
-        }
+        // after an abort: the last sub-block's tiles and the latest column
+        // data of each slot may still be landing (earlier copies were
+        // consumed before the slot was refilled), and MMAs may still be
+        // writing TMEM -- wait for all of them before TMEM is freed and the
+        // CTA exits (no-ops on the normal path, where all are complete)
+        if (b_issued > 0) mbar_drain(BAR_B_FULL, (b_issued - 1) & 1);
+        for (int k = 0; k < 2; ++k)
+            if (blk_last[k] >= 0) mbar_drain(BAR_BLK_FULL(k), (blk_last[k] >> 1) & 1);
+        if (li_done >= 0) mbar_drain(BAR_T_FULL(li_done % NACC), (li_done / NACC) & 1);
     }
     tc_fence_before();
     __syncthreads();
@@ -863,6 +872,7 @@ askit_status eval_tc16(askit_tree t, const WeightCtx &c, int precision, const fl
     a.knn_eta = a.knn_m2u = 0.f;
     a.partial = partial;
     a.status = t->d_status;
+    a.spin = t->spin_limit > 0 ? t->spin_limit : SPIN_LIMIT;
     if (precision != ASKIT_PREC_FP16X3) {
         askit_set_error("eval_tc16 runs FP16x3");
         return ASKIT_ERR_INVALID_ARG;
@@ -970,6 +980,7 @@ askit_status knn_shortlist_tc16(askit_tree t, const float *Yp, int64_t T, const 
         a.knn_m2u = -2.f / (t->f16_scale * t->f16_scale);
         a.partial = nullptr;
         a.status = t->d_status;
+        a.spin = SPIN_LIMIT;
         KTRY((launch16<ASKIT_PREC_FP16X3, 1, 2, 2, 2>(st, 1, map_q, map_q8, a, nc, s)));
     }
 out:

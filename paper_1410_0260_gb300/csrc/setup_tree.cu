@@ -901,6 +901,10 @@ extern "C" askit_status askit_knn_noalloc(const float *X_dev, int64_t N, int32_t
         askit_set_error("need N >= 1, d >= 1, Q >= 1 and 1 <= kappa <= 32");
         return ASKIT_ERR_INVALID_ARG;
     }
+    if (N >= ((int64_t)1 << 31) - 1024) {   // ids are int32 (the setup's bound)
+        askit_set_error("askit_knn_noalloc handles N below 2^31 - 1024");
+        return ASKIT_ERR_UNSUPPORTED;
+    }
     if (Q > KNN_NOALLOC_MAX_Q) {
         askit_set_error("askit_knn_noalloc handles at most %lld queries per call (got %lld)",
                         (long long)KNN_NOALLOC_MAX_Q, (long long)Q);

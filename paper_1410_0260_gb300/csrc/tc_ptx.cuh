@@ -52,12 +52,34 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait on the phase of the given parity.  Returns false when the
-// kernel is aborting (another role timed out) or this wait timed out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *status) {
-    for (int it = 0; it < SPIN_LIMIT; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 1023) == 1023 && *abort_flag) return false;
+// Non-blocking test of the phase of the given parity.
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on the phase of the given parity: at most `limit` polls (each
+// try_wait suspends the thread for a while before it gives up).  Returns false
+// when the kernel is aborting (another role timed out) or this wait timed out.
+// A limit below 1024 (a test of the timeout path) polls with the
+// non-blocking test_wait, so a phase not complete at once makes it give up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *status,
+                                          int limit = SPIN_LIMIT) {
+    if (limit < 1024) {
+        for (int it = 0; it < limit; ++it)
+            if (mbar_test_wait(bar, parity)) return true;
+    } else {
+        for (int it = 0; it < limit; ++it) {
+            if (mbar_try_wait(bar, parity)) return true;
+            if ((it & 1023) == 1023 && *abort_flag) return false;
+        }
     }
     *abort_flag = 1;
     atomicExch(status, ASK_DEV_TIMEOUT);
@@ -103,6 +125,17 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_
                  ::"r"(dst), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
                  : "memory");
 }
+
+// 16-byte asynchronous copy global -> shared through L2 only (cp.async.cg),
+// completion tracked per thread by commit groups.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+// generic-proxy writes of this thread -> visible to the async proxy (tensor core)
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }

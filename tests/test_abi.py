@@ -55,6 +55,21 @@ def test_host_only_calls(lib):
     rc = lib.askit_setup(ctypes.c_void_p(16), ctypes.c_int64(0), 3, ctypes.c_int64(3), None, None,
                          ctypes.byref(p), None, ctypes.byref(out))
     assert rc == 1 and not out.value
+    # a leaf or skeleton longer than 16 sub-blocks of 128 rows cannot be
+    # indexed by the work lists: refused (UNSUPPORTED) before any device work
+    for field, val in (("leaf_size", 4096), ("s_max", 2049)):
+        q = Params()
+        lib.askit_default_params(ctypes.byref(q))
+        setattr(q, field, val)
+        rc = lib.askit_setup(ctypes.c_void_p(16), ctypes.c_int64(3000), 3, ctypes.c_int64(3), None, None,
+                             ctypes.byref(q), None, ctypes.byref(out))
+        assert rc == 6 and not out.value, field
+    q = Params()
+    lib.askit_default_params(ctypes.byref(q))
+    q.leaf_size, q.kappa = 2, 1                      # 2^30 points in leaves of 2: depth 29 > 25
+    rc = lib.askit_setup(ctypes.c_void_p(16), ctypes.c_int64(1 << 30), 3, ctypes.c_int64(3), None, None,
+                         ctypes.byref(q), None, ctypes.byref(out))
+    assert rc == 6 and not out.value
 
 
 def test_oracle_and_product_share_no_code():

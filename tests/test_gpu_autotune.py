@@ -9,14 +9,21 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision,r,n_cand", [("fp16x3", 1, 10), ("fp16x3", 3, 10), ("fp16x3", 6, 8),
-                                                ("bf16x3", 1, 2), ("simt_fp32", 1, 1)])
-def test_autotune_keeps_results_and_picks_one(precision, r, n_cand):
+# candidates: FP16x3 with global centering (the automatic choice here) has
+# two schedules x stages 3, 4 + paired items at stages 3, 4 (none past
+# r = 4); per sub-block centering two schedules x stages 2, 3 x tiled runs
+# on/off + paired items with tiled runs on/off
+@pytest.mark.parametrize("precision,centering,r,n_cand",
+                         [("fp16x3", "auto", 1, 6), ("fp16x3", "auto", 3, 6), ("fp16x3", "auto", 6, 4),
+                          ("fp16x3", "block", 1, 10), ("fp16x3", "block", 3, 10), ("fp16x3", "block", 6, 8),
+                          ("bf16x3", "auto", 1, 2), ("simt_fp32", "auto", 1, 1)])
+def test_autotune_keeps_results_and_picks_one(precision, centering, r, n_cand):
     from paper_1410_0260_gb300 import askit, workloads
     w = workloads.MANIFOLD_1M_64.scaled(16384)
     X = torch.from_numpy(w.make_points()).cuda()
     t = askit.Tree(X, askit.Config(leaf_size=512, kappa=16, knn_mode=1, rp_iters=2, s_max=128, id_tol=1e-4,
                                    h=0.35, precision=precision))
+    t.set_fp16_centering(centering)
     W = torch.from_numpy(np.random.default_rng(2).standard_normal((16384, r)).astype(np.float32)).cuda()
     t.set_weights(W)
     before = t.evaluate().clone()
@@ -44,26 +51,30 @@ def test_every_launch_configuration_matches_the_oracle():
     kw = dict(leaf_size=512, kappa=16, knn_mode=1, rp_iters=2, s_max=200, id_tol=1e-4, h=0.35, seed=3)
     ot = oracle.Tree(X, oracle.Config(**kw))
     gt = askit.Tree(torch.from_numpy(X).cuda(), askit.Config(precision="fp16x3", **kw))
-    for r in (1, 3):
+    for r, centering in ((1, "auto"), (3, "auto"), (1, "block"), (3, "block")):
+        gt.set_fp16_centering(centering)
+        # the split-path tolerance for the global centering, FP32 grade per block
+        tol = 1e-4 if centering == "auto" else 1e-5
         W = np.random.default_rng(r).standard_normal((8192, r)).astype(np.float32)
         ot.set_weights(W.astype(np.float64))
         Uo = ot.evaluate()
         gt.set_weights(torch.from_numpy(W).cuda())
         ref = None
         for sched in ("lpt", "tree_order"):
-            for stages in (2, 3):
+            for stages in (2, 3, 4):
                 for runs in (False, True):
                     gt.set_launch(sched, stages, runs, False)
                     U = gt.evaluate().cpu().numpy()
-                    assert np.linalg.norm(U - Uo) / np.linalg.norm(Uo) <= 1e-5
+                    assert np.linalg.norm(U - Uo) / np.linalg.norm(Uo) <= tol
                     if ref is None:
                         ref = U
                     assert np.array_equal(U, ref)
-        for runs in (False, True):
-            gt.set_launch("lpt", 2, runs, True)
-            U = gt.evaluate().cpu().numpy()
-            assert np.linalg.norm(U - Uo) / np.linalg.norm(Uo) <= 1e-5
-            assert np.linalg.norm(U - ref) / np.linalg.norm(ref) <= 1e-6
+        for stages in (2, 3, 4):
+            for runs in (False, True):
+                gt.set_launch("lpt", stages, runs, True)
+                U = gt.evaluate().cpu().numpy()
+                assert np.linalg.norm(U - Uo) / np.linalg.norm(Uo) <= tol
+                assert np.linalg.norm(U - ref) / np.linalg.norm(ref) <= 1e-6
     gt.close()
 
 

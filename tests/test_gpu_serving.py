@@ -53,7 +53,7 @@ def test_results_alone_equal_results_in_the_mix(precision):
     alone = []
     for r in reqs:
         q = srv.submit(Request(r.kind, r.data))
-        q.done.wait(60)
+        assert q.done.wait(60), "request not answered"
         assert q.error is None, q.error
         alone.append(q.result.clone())
     srv.close()
@@ -61,11 +61,16 @@ def test_results_alone_equal_results_in_the_mix(precision):
     srv = Server(tree, Wres, n_slots=2)
     mixed = [srv.submit(Request(r.kind, r.data)) for r in reqs]
     for q in mixed:
-        q.done.wait(120)
+        assert q.done.wait(120), "request not answered"
         assert q.error is None, q.error
-    batched = len(srv.completed) == len(mixed)
+    completed = len(srv.completed)
+    n_batches, peak = srv.n_batches, srv.peak_concurrency
     srv.close()
-    assert batched
+    assert completed == len(mixed)
+    # continuous batching, not a queue: requests were merged into fewer
+    # batches than requests, and two batches were on the device at once
+    assert n_batches < len(mixed), n_batches
+    assert peak == 2, peak
     for a, q in zip(alone, mixed):
         b = q.result
         assert a.shape == b.shape
