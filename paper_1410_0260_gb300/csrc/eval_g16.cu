@@ -29,11 +29,10 @@
 // Work item = one source sub-block (or two sub-blocks of one node: a paired
 // 256-column item) against up to 128 targets needing it (eval_lists.cu).
 // One CTA per SM, 352 threads:
-//   warps 0-7  two epilogue groups, one per half of every item's columns:
-//              tcgen05.ld of their 32 TMEM lanes (two buffers), ex2 on MUFU,
-//              weight sums; the second half's sums reach the first group
-//              through shared memory and are added last (the order of
-//              eval_tc16.cu);
+//   warps 0-7  two epilogue groups, each summing whole sub-blocks (alternate
+//              items, or the two sub-blocks of a paired item): tcgen05.ld of
+//              their 32 TMEM lanes (two buffers), ex2 on MUFU, weight sums,
+//              one partial sum per (target, sub-block) entry;
 //   warp 8     TMEM allocation; lane 0 loads each sub-block (TMA tiles of its
 //              pre-split rows, bulk copies of its column data) and issues the
 //              tcgen05.mma instructions;
@@ -70,8 +69,7 @@ struct SG {
     static constexpr int COLW_BYTES = RC > 1 ? NB * 128 * RC * 4 : 0;
     static constexpr int BLKSLOT = BLK_COLW + COLW_BYTES;
     static constexpr int PT = BLK + 2 * BLKSLOT;            // float [NA][128] n_i of each stage's targets
-    static constexpr int XBUF = PT + NA * 128 * 4;          // float [NACC][128][RC] second half's sums
-    static constexpr int BAR = XBUF + NACC * 128 * RC * 4;  // 48 mbarriers
+    static constexpr int BAR = PT + NA * 128 * 4;           // 48 mbarriers
     static constexpr int MISC = BAR + 48 * 8;               // tmem address, abort flag
     static constexpr int BYTES = MISC + 16;
     static constexpr int THREADS = 352;
@@ -102,6 +100,9 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
     using S = SG<RC, NA, NB>;
     constexpr int NACC = S::NACC;
     constexpr int NEPI = 256;                    // epilogue threads (two groups of 128)
+    // readers of an item's n_i and drainers of its accumulator: one group
+    // (alternate items) or both (paired items)
+    constexpr int NITEM = NB == 2 ? 256 : 128;
     constexpr int W_MMA = 8, W_CP0 = 9;          // MMA warp, first of the two copier warps
     static_assert(NA >= 3 && NA <= 4, "the copiers keep NA - 2 items in flight");
     static_assert(!UNI || RC == 1, "the uniform-bandwidth layout serves r = 1");
@@ -113,13 +114,12 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
     auto BAR_A_FULL = [&](int s) { return bar0 + 8 * s; };            // target rows of stage s landed (64)
     auto BAR_A_EMPTY = [&](int s) { return bar0 + 8 * (4 + s); };     // MMAs reading stage s done (commit)
     auto BAR_P_FULL = [&](int s) { return bar0 + 8 * (8 + s); };      // n_i of stage s's item stored (64)
-    auto BAR_P_EMPTY = [&](int s) { return bar0 + 8 * (12 + s); };    // epilogue read them (NEPI)
+    auto BAR_P_EMPTY = [&](int s) { return bar0 + 8 * (12 + s); };    // epilogue read them (NITEM)
     const uint32_t BAR_B_FULL = bar0 + 8 * 16, BAR_B_EMPTY = bar0 + 8 * 17;
     auto BAR_BLK_FULL = [&](int s) { return bar0 + 8 * (18 + s); };   // column data of slot s landed
     auto BAR_BLK_EMPTY = [&](int s) { return bar0 + 8 * (20 + s); };  // epilogue done with slot s (NEPI)
     auto BAR_T_FULL = [&](int a) { return bar0 + 8 * (24 + a); };     // accumulator a complete (commit)
-    auto BAR_T_EMPTY = [&](int a) { return bar0 + 8 * (28 + a); };    // epilogue drained accumulator a (NEPI)
-    auto BAR_X_FULL = [&](int a) { return bar0 + 8 * (32 + a); };     // second half's sums of a (128)
+    auto BAR_T_EMPTY = [&](int a) { return bar0 + 8 * (28 + a); };    // epilogue drained accumulator a (NITEM)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + S::MISC);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + S::MISC + 4);
 
@@ -129,7 +129,7 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
             mbar_init(BAR_A_FULL(s), 64);
             mbar_init(BAR_A_EMPTY(s), 1);
             mbar_init(BAR_P_FULL(s), 64);
-            mbar_init(BAR_P_EMPTY(s), NEPI);
+            mbar_init(BAR_P_EMPTY(s), NITEM);
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(BAR_BLK_FULL(s), 1);
@@ -139,8 +139,7 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
         mbar_init(BAR_B_EMPTY, 1);
         for (int a = 0; a < NACC; ++a) {
             mbar_init(BAR_T_FULL(a), 1);
-            mbar_init(BAR_T_EMPTY(a), NEPI);
-            mbar_init(BAR_X_FULL(a), 128);
+            mbar_init(BAR_T_EMPTY(a), NITEM);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -158,9 +157,16 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
 
     if (warp < W_MMA) {
         // ----------------------------------------------------------- epilogue
+        // Each group sums whole sub-blocks: with single sub-blocks (NB == 1)
+        // the two groups take alternate items; with paired items (NB == 2)
+        // group 0 takes the leader's 128 columns and group 1 the follower's,
+        // and each writes its own entry's partial sum -- so every entry's
+        // partial is formed the same way in both layouts, and the groups
+        // never wait for each other.  A paired-layout item without a follower
+        // is summed by group 0 alone.
         const int q = warp & 3;                    // this warp's TMEM lane quadrant
         const int row = q * 32 + lane;             // TMEM lane = target row of the item
-        const int eg = warp >> 2;                  // column half of this group
+        const int eg = warp >> 2;                  // group
         int li = 0, lb = 0;
         for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci, ++lb) {
             const int b = args.cta_blocks[ci];
@@ -173,13 +179,18 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
             const int pb = NB == 2 ? args.partner[b] : -1;
             const int f0 = pb >= 0 ? args.block_off[pb] : 0;
             const int ncols_f = pb >= 0 ? (args.items[f0].nrows & 0x7fffffff) : 0;
-            EvalItem nxt = args.items[i0];
+            // this group's columns of every item of the block
+            const int nrows_l = args.items[i0].nrows & 0x7fffffff;
+            int c_lo = 0, c_hi = (nrows_l + 31) >> 5;
+            if (NB == 2 && eg == 1) {
+                c_lo = 4;
+                c_hi = pb >= 0 ? 4 + ((ncols_f + 31) >> 5) : 4;
+            }
             for (int it = i0; it < i1; ++it, ++li) {
+                if (NB == 1 && (li & 1) != eg) continue;   // the other group's item
                 const int a4 = li % NACC, sp = li % NA;
-                const EvalItem item = nxt;
-                if (it + 1 < i1) nxt = args.items[it + 1];   // in flight while this item waits
-                const int nrows = (item.nrows & 0x7fffffff) + ncols_f;
-                const int e0f = pb >= 0 ? args.items[f0 + (it - i0)].e0 : 0;
+                const EvalItem item = args.items[it];
+                const int e_out = (NB == 2 && eg == 1) ? (pb >= 0 ? args.items[f0 + (it - i0)].e0 : 0) : item.e0;
                 if (!mbar_wait(BAR_P_FULL(sp), (li / NA) & 1, abort_flag, args.status, args.spin)) goto epi_done;
                 const float pt = ptbuf[sp * 128 + row];
                 mbar_arrive(BAR_P_EMPTY(sp));
@@ -192,9 +203,9 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                 float2 accw[RC > 1 ? RC / 2 : 1];                                    // RC > 1
 #pragma unroll
                 for (int z = 0; z < (RC > 1 ? RC / 2 : 1); ++z) accw[z] = make_float2(0.f, 0.f);
-                if (q * 32 < item.cnt) {   // warp-uniform: skip quadrants with no target
+                if (q * 32 < item.cnt && c_lo < c_hi) {   // warp-uniform
                     const float2 pt2 = make_float2(pt, pt);
-                    // arg = G A + (C n_i + B); columns past nrows carry B = -inf
+                    // arg = G A + (C n_i + B); columns past the rows carry B = -inf
                     // (UNI) or A = B = C = w = 0
                     auto cols = [&](int c, const uint32_t (&gr)[32]) {
                         if constexpr (RC == 1 && UNI) {
@@ -241,27 +252,21 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                         }
                     };
                     const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a4 * 128 * NB);
-                    // 32-column chunks; group g takes chunks [c_lo, c_hi) of its
-                    // half.  Two register buffers: the TMEM load of chunk c + 1
-                    // is in flight while chunk c is computed
-                    const int nch = (nrows + 31) >> 5;
-                    const int hch = (nch + 1) >> 1;
-                    const int c_lo = eg * hch, c_hi = min(nch, c_lo + hch);
-                    if (c_lo < c_hi) {
-                        uint32_t ga[32], gb[32];
-                        tmem_ld32_async(tbase + (uint32_t)(c_lo * 32), ga);
-                        tmem_wait_pin(ga);
+                    // 32-column chunks with two register buffers: the TMEM load
+                    // of chunk c + 1 is in flight while chunk c is computed
+                    uint32_t ga[32], gb[32];
+                    tmem_ld32_async(tbase + (uint32_t)(c_lo * 32), ga);
+                    tmem_wait_pin(ga);
 #pragma unroll 1
-                        for (int c = c_lo; c < c_hi; c += 2) {
-                            const bool h1 = c + 1 < c_hi, h2 = c + 2 < c_hi;   // warp-uniform
-                            if (h1) tmem_ld32_async(tbase + (uint32_t)((c + 1) * 32), gb);
-                            cols(c, ga);
-                            if (h1) {
-                                tmem_wait_pin(gb);
-                                if (h2) tmem_ld32_async(tbase + (uint32_t)((c + 2) * 32), ga);
-                                cols(c + 1, gb);
-                                if (h2) tmem_wait_pin(ga);
-                            }
+                    for (int c = c_lo; c < c_hi; c += 2) {
+                        const bool h1 = c + 1 < c_hi, h2 = c + 2 < c_hi;   // warp-uniform
+                        if (h1) tmem_ld32_async(tbase + (uint32_t)((c + 1) * 32), gb);
+                        cols(c, ga);
+                        if (h1) {
+                            tmem_wait_pin(gb);
+                            if (h2) tmem_ld32_async(tbase + (uint32_t)((c + 2) * 32), ga);
+                            cols(c + 1, gb);
+                            if (h2) tmem_wait_pin(ga);
                         }
                     }
                     if constexpr (RC == 1) {
@@ -275,34 +280,12 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                     }
                 }
                 tc_fence_before();
-                {
-                    // the second half's sums go to the first group through shared
-                    // memory; the first group releases the accumulator only after
-                    // reading them, so the buffer is free when the slot is reused
-                    float *xb = reinterpret_cast<float *>(sm + S::XBUF) + (a4 * 128 + row) * RC;
-                    if (eg == 1) {
-#pragma unroll
-                        for (int z = 0; z < RC; ++z) xb[z] = acc[z];
-                        mbar_arrive(BAR_X_FULL(a4));
-                        mbar_arrive(BAR_T_EMPTY(a4));
-                        continue;
-                    }
-                    if (!mbar_wait(BAR_X_FULL(a4), (li / NACC) & 1, abort_flag, args.status, args.spin)) goto epi_done;
-#pragma unroll
-                    for (int z = 0; z < RC; ++z) acc[z] += xb[z];
-                }
                 mbar_arrive(BAR_T_EMPTY(a4));
-                if (row < item.cnt) {
-                    float *p = args.partial + (int64_t)(item.e0 + row) * args.r;
+                if (row < item.cnt && c_lo < c_hi) {
+                    float *p = args.partial + (int64_t)(e_out + row) * args.r;
 #pragma unroll
                     for (int z = 0; z < RC; ++z)
                         if (z < args.r) p[z] = acc[z];
-                    if (pb >= 0) {   // the follower's entry: its share is in the leader's sum
-                        float *pf = args.partial + (int64_t)(e0f + row) * args.r;
-#pragma unroll
-                        for (int z = 0; z < RC; ++z)
-                            if (z < args.r) pf[z] = 0.f;
-                    }
                 }
             }
             mbar_arrive(BAR_BLK_EMPTY(bs));
