@@ -111,10 +111,9 @@ struct __align__(16) EvalItem {
 };
 
 // Target rows of one evaluation in the global-centered FP16x3 form: hi / lo
-// [rows, TC_K] FP16 of (x - xbar) g_scale and n [rows] = |x - xbar|^2.
+// [rows, TC_K] FP16 of (x - xbar) g_sigma and the norm blocks x [rows, 16].
 struct QuerySplit {
-    const uint16_t *hi = nullptr, *lo = nullptr;
-    const float *n = nullptr;
+    const uint16_t *hi = nullptr, *lo = nullptr, *x = nullptr;
     int64_t rows = 0;
 };
 
@@ -237,13 +236,18 @@ struct askit_tree_s {
     int64_t srows = 0;             // rows of the skeleton-pool arrays
 
     // global-centered FP16x3 operands (d <= TC_K, eval_g16.cu): every point
-    // centered on the data mean g_xbar, prescaled by g_scale and split into
-    // FP16 hi + lo; n = |x - xbar|^2.  g_rho = max_j sc_j * max_i n_i decides
-    // whether they hold FP32-grade accuracy (g_ok)
-    uint16_t *Xg_hi = nullptr, *Xg_lo = nullptr, *Sg_hi = nullptr, *Sg_lo = nullptr;
+    // centered on the data mean g_xbar; targets (x - xbar) g_sigma and
+    // sources (y - xbar) 2 sc_j / g_sigma split into FP16 hi + lo; the norm
+    // blocks of targets [rows, 16] and of every source sub-block (scales
+    // g_tau, g_kappa); n = |x - xbar|^2.  g_rho = max_j sc_j * max_i n_i
+    // decides the automatic choice (g_ok)
+    uint16_t *Xg_hi = nullptr, *Xg_lo = nullptr, *Xg_x = nullptr;   // tree points as targets
+    uint16_t *Xb_hi = nullptr, *Xb_lo = nullptr;                    // tree points as sources
+    uint16_t *Sb_hi = nullptr, *Sb_lo = nullptr;                    // skeleton pool as sources
+    uint16_t *g_bx = nullptr;                                       // [n_sub, 128 x 16]
     float *ng_t = nullptr, *ng_s = nullptr;
     float *g_xbar = nullptr;       // [TC_K] device
-    float g_scale = 1.f;
+    float g_sigma = 1.f, g_tau = 1.f, g_kappa = 1.f;
     double g_rho = 0.0;
     bool g_ok = false;
     int fp16_centering = 0;        // 0 automatic (global when g_ok), 1 per sub-block, 2 global
@@ -437,8 +441,10 @@ askit_status eval_g16(askit_tree t, const WeightCtx &c, const QuerySplit &q, con
                       cudaStream_t s);
 void eval_g16_free(askit_tree t);
 askit_status build_g16_operands(askit_tree t, cudaStream_t s);
-askit_status g16_split_rows(const float *X, int64_t ldx, int d, int64_t rows, const float *xbar, float scale,
-                            uint16_t *hi, uint16_t *lo, float *n, int *overflow, cudaStream_t s);
+// target rows X [rows, ldx] (d columns) in the global-centered form of tree t;
+// *overflow (if given) is set when a value leaves the FP16-safe range
+askit_status g16_split_rows(const float *X, int64_t ldx, int d, int64_t rows, const askit_tree_s *t, uint16_t *hi,
+                            uint16_t *lo, uint16_t *nx, int *overflow, cudaStream_t s);
 // whether FP16x3 evaluations of this tree take the global-centered kernel
 inline bool use_g16(const askit_tree_s *t) {
     return t->Xg_hi && (t->fp16_centering == 2 || (t->fp16_centering == 0 && t->g_ok));

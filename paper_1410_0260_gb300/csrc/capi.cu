@@ -309,7 +309,7 @@ askit_status evaluate_ctx(askit_tree t, const WeightCtx &c, float *U_dev, int64_
         if (t->Xg_hi) {
             q.hi = t->Xg_hi + t0 * TC_K;
             q.lo = t->Xg_lo + t0 * TC_K;
-            q.n = t->ng_t + t0;
+            q.x = t->Xg_x + t0 * 16;
             q.rows = t->N_pad - t0;
         }
         ASK_TRY(run_eval(t, c, t->precision, t->Xt + t0 * t->d_pad, t->d_pad, t->N_pad - t0, t->Xg_hi ? &q : nullptr,
@@ -437,8 +437,7 @@ askit_status evaluate_targets_ctx(askit_tree t, const WeightCtx &c, const float 
     size_t cb = 0;
     WorkLists w;
     float *partial = nullptr;
-    uint16_t *yg_hi = nullptr, *yg_lo = nullptr;
-    float *yg_n = nullptr;
+    uint16_t *yg_hi = nullptr, *yg_lo = nullptr, *yg_x = nullptr;
     int *yg_flag = nullptr;
     QuerySplit qs;
     int64_t T_pad = (T + ASK_TILE_M - 1) / ASK_TILE_M * ASK_TILE_M;
@@ -471,17 +470,17 @@ askit_status evaluate_targets_ctx(askit_tree t, const WeightCtx &c, const float 
         // per-sub-block centered kernel instead
         OTRY(tmp.alloc(&yg_hi, (size_t)T_pad * TC_K));
         OTRY(tmp.alloc(&yg_lo, (size_t)T_pad * TC_K));
-        OTRY(tmp.alloc(&yg_n, T_pad));
+        OTRY(tmp.alloc(&yg_x, (size_t)T_pad * 16));
         OTRY(tmp.alloc(&yg_flag, 1));
         if (cudaMemsetAsync(yg_flag, 0, sizeof(int), s) != cudaSuccess) { askit_set_error("flag"); rc = ASKIT_ERR_CUDA; goto out; }
-        OTRY(g16_split_rows(Yt, t->d_pad, d, T_pad, t->g_xbar, t->g_scale, yg_hi, yg_lo, yg_n, yg_flag, s));
+        OTRY(g16_split_rows(Yt, t->d_pad, d, T_pad, t, yg_hi, yg_lo, yg_x, yg_flag, s));
         int flag = 0;
         if (cudaMemcpyAsync(&flag, yg_flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) { askit_set_error("range flag"); rc = ASKIT_ERR_CUDA; goto out; }
         if (!flag) {
             qs.hi = yg_hi;
             qs.lo = yg_lo;
-            qs.n = yg_n;
+            qs.x = yg_x;
             qs.rows = T_pad;
         }
     }

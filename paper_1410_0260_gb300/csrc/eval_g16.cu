@@ -1,30 +1,40 @@
 // Evaluate (Algorithm 4) on the tcgen05 tensor cores with FP16x3 split
-// operands, d <= 64, all operands pre-split in HBM ("global centering").
+// operands, d <= 64, every operand pre-split in HBM ("global centering"),
+// and the whole exponent argument formed by the tensor cores.
 //
-// Every point (target or source) is centered once on the data mean xbar and
-// prescaled by a power of 2 s:  x~ = (x - xbar) s, split x~ = hi + lo in FP16.
-// Then, per (target i, source j),
+// Every point is centered once on the data mean xbar.  With n = |x - xbar|^2
+// and sc_j = c log2(e) / h_j^2 (the source's bandwidth),
 //
-//     r^2 = n_i + n_j - 2 x~_i . x~_j / s^2,    n = |x - xbar|^2 (FP32),
-//     arg = -sc_j r^2 = (2 sc_j / s^2) G + (-sc_j) n_i + (-sc_j n_j),
-//     partial_i += exp2(arg) w_j,
+//     arg_ij = -sc_j |x_i - y_j|^2
+//            = 2 sc_j (x_i - xbar).(y_j - xbar) - sc_j n_i - sc_j n_j,
+//     partial_i += exp2(arg_ij) w_j.
 //
-// with G = x~_i . x~_j on the tensor cores as three split products
-// (hi*lo + lo*hi + hi*hi, FP32 accumulation, small terms first).  No target
-// row is converted on the chip: a work item's 128 target rows are copied in
-// the MMA's swizzled layout straight from HBM (16-byte cp.async, eight lanes
-// per 128-byte row; a TMA tile::gather4 issue costs about 75 cycles per four
-// rows on this part, which made the copies the bottleneck), so the kernel
-// has no loader warps, only the exponentials and weight sums of the epilogue
-// beside the MMAs.  The price is precision: the terms n_i, n_j and 2G are of the
-// size of the data's spread R^2 around xbar and are rounded in FP32, so the
-// exponent carries an error of a few 2^-24 sc R^2; the per-sub-block centered
-// kernel (eval_tc16.cu) keeps these terms at the size of a node instead.  The
-// tree picks this kernel only while sc_max R^2_max stays below a bound that
-// keeps the FP16x3 result at FP32 grade (build_tc_operands), and falls back
-// otherwise; askit_set_fp16_centering overrides the choice.  Measured: about
-// 1e-5 relative L2 error of u (the per-sub-block kernel: about 1e-6), inside
-// the split-product tolerance 1e-4.
+// The MMA accumulator receives arg_ij itself:
+//   - the main K = 64 block: targets a_i = (x_i - xbar) sigma, sources
+//     b_j = (y_j - xbar) 2 sc_j / sigma, each split into FP16 hi + lo and
+//     multiplied as hi*lo + lo*hi + hi*hi (FP32 accumulation, small terms
+//     first); sigma is a power of 2 near sqrt(2 sc_max), so both sides have
+//     similar magnitudes well inside the FP16 range;
+//   - one extra K = 16 block holding the norm terms already split:
+//     targets [h(n_i tau), h(n_i tau), l(n_i tau), kappa, kappa, 0 ...],
+//     sources [h(m_j), l(m_j), h(m_j), h(v_j), l(v_j), 0 ...] with
+//     m_j = -sc_j / tau, v_j = -sc_j n_j / kappa (tau, kappa powers of 2
+//     balancing the factors), whose product is -sc_j (n_i + n_j) to the
+//     split's precision.
+// So the epilogue is an ex2 on MUFU and one weight FMA per pair.  The price
+// is precision: the terms 2 sc (x - xbar).(y - xbar) and sc n are of the size
+// of sc R^2 (R = the data's spread around xbar) and are rounded in FP32, so
+// the exponent carries an error of a few 2^-24 sc R^2; the per-sub-block
+// centered kernel (eval_tc16.cu) keeps these terms at the size of a node.
+// The tree takes this kernel only while rho = sc_max R^2_max <= 512
+// (build_g16_operands), and askit_set_fp16_centering overrides the choice.
+// Measured: relative L2 error of u about 1e-5 (the per-sub-block kernel
+// about 1e-6), within the split-product tolerance 1e-4.
+//
+// No target row is converted on the chip: each work item's 128 target rows
+// are copied in the MMA's layouts straight from HBM (16-byte cp.async, eight
+// lanes per 128-byte row; a TMA tile::gather4 costs about 75 cycles of issue
+// per four rows on this part, which made the copies the bottleneck).
 //
 // Work item = one source sub-block (or two sub-blocks of one node: a paired
 // 256-column item) against up to 128 targets needing it (eval_lists.cu).
@@ -34,10 +44,10 @@
 //              their 32 TMEM lanes (two buffers), ex2 on MUFU, weight sums,
 //              one partial sum per (target, sub-block) entry;
 //   warp 8     TMEM allocation; lane 0 loads each sub-block (TMA tiles of its
-//              pre-split rows, bulk copies of its column data) and issues the
-//              tcgen05.mma instructions;
-//   warps 9-10 copy each item's target rows into NA stages (NA - 2 items in
-//              flight) and the targets' n_i into shared memory.
+//              split rows, bulk copies of its norm block and weights) and
+//              issues the tcgen05.mma instructions;
+//   warps 9-10 copy each item's target rows into NA stages (NA - 2 items'
+//              copies in flight).
 // Every mbarrier wait is bounded (ASK_DEV_TIMEOUT on expiry, all roles leave,
 // copies and MMAs in flight are waited for, TMEM is freed).
 #include <cuda.h>
@@ -54,7 +64,22 @@ using namespace tcx;
 
 constexpr int G_ROWS = 128;
 constexpr int G_REGION = G_ROWS * 128;   // 128 rows x 128 bytes (64 FP16), 128-byte swizzle
+constexpr int GX_REGION = G_ROWS * 32;   // 128 rows x 32 bytes (16 FP16): the norm block
+constexpr int GX_K = 16;                 // columns of the norm block
 constexpr uint32_t G_TMEM_COLS = 512;    // four 128-column (two 256-column) FP32 accumulators
+
+// Shared-memory descriptor of a K-major operand without swizzle: 8-row x
+// 16-byte core matrices stored contiguously, the next core matrix along K
+// 128 bytes on (leading-byte offset), along M/N 256 bytes on (stride-byte
+// offset); version bit 46, layout type 0 (no swizzle).
+__device__ __forceinline__ uint64_t ns_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+// Byte offset of row r, 16-byte chunk c of a norm block in that layout.
+__host__ __device__ __forceinline__ uint32_t nx_off(int r, int c) {
+    return (uint32_t)((r >> 3) * 256 + c * 128 + (r & 7) * 16);
+}
 
 // NA: target-row stages; NB: sub-blocks per item (1, or 2 for paired items);
 // NACC = 4 / NB TMEM accumulators of 128 NB columns.
@@ -62,37 +87,35 @@ template <int RC, int NA, int NB>
 struct SG {
     static constexpr int NACC = 4 / NB;
     static constexpr int B_HI = 0, B_LO = NB * G_REGION;    // NB x 128 rows each, contiguous
-    static constexpr int A0 = 2 * NB * G_REGION;            // stage s: hi at A0 + 2 s REGION, lo at + REGION
-    static constexpr int BLK = A0 + NA * 2 * G_REGION;      // [2] per-block column-data slots
-    static constexpr int BLK_COLV = 0;                      // float4 [128 NB] column data
-    static constexpr int BLK_COLW = NB * 128 * 16;          // float [128 NB][RC] weights (RC > 1)
-    static constexpr int COLW_BYTES = RC > 1 ? NB * 128 * RC * 4 : 0;
-    static constexpr int BLKSLOT = BLK_COLW + COLW_BYTES;
-    static constexpr int PT = BLK + 2 * BLKSLOT;            // float [NA][128] n_i of each stage's targets
-    static constexpr int BAR = PT + NA * 128 * 4;           // 48 mbarriers
-    static constexpr int MISC = BAR + 48 * 8;               // tmem address, abort flag
+    static constexpr int B_X = 2 * NB * G_REGION;           // NB x 128 rows of the norm block
+    static constexpr int A0 = B_X + NB * GX_REGION;         // stage s at A0 + s ASTAGE: hi, lo, norm block
+    static constexpr int ASTAGE = 2 * G_REGION + GX_REGION;
+    static constexpr int BLK = A0 + NA * ASTAGE;            // [2] per-block weight slots
+    static constexpr int BLKSLOT = NB * 128 * RC * 4;       // float [128 NB][RC]
+    static constexpr int BAR = BLK + 2 * BLKSLOT;           // 40 mbarriers
+    static constexpr int MISC = BAR + 40 * 8;               // tmem address, abort flag
     static constexpr int BYTES = MISC + 16;
     static constexpr int THREADS = 352;
+    static_assert(A0 % 1024 == 0 && ASTAGE % 1024 == 0, "swizzled stages need 1024-byte alignment");
 };
 
 struct G16Args {
     const EvalItem *items;
     const int32_t *block_off;
     const int32_t *cta_off, *cta_blocks;
-    const int32_t *tgt;       // entry -> target slot (row of the query operand)
-    const uint16_t *q_hi, *q_lo; // [query rows, 64] pre-split target rows
-    const float *qn;          // [query rows] n_i = |x_i - xbar|^2
-    const float4 *colv;       // [n_sub, 128] column data (UNI: [n_sub, 64])
-    const float *colw;        // [n_sub, 128, RC] (RC > 1)
-    const int32_t *partner;   // [n_blocks] paired follower block, or -1 (NB == 2)
+    const int32_t *tgt;            // entry -> target slot (row of the query operand)
+    const uint16_t *q_hi, *q_lo;   // [query rows, 64] split target rows
+    const uint16_t *q_x;           // [query rows, 16] target norm blocks
+    const uint16_t *bx;            // [n_sub, 128 x 16] source norm blocks (core-matrix layout)
+    const float *colw;             // [n_sub, 128, RC] weights (zeros past the rows)
+    const int32_t *partner;        // [n_blocks] paired follower block, or -1 (NB == 2)
     int r;
-    float uni_a, uni_c;       // UNI: A = 2 sc / s^2 and C = -sc
     float *partial;
     int *status;
     int spin;
 };
 
-template <int RC, int NA, int NB, int UNI>
+template <int RC, int NA, int NB>
 __global__ void __launch_bounds__(352, 1)
 eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_constant__ CUtensorMap map_t_lo,
                 const __grid_constant__ CUtensorMap map_s_hi, const __grid_constant__ CUtensorMap map_s_lo,
@@ -100,26 +123,22 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
     using S = SG<RC, NA, NB>;
     constexpr int NACC = S::NACC;
     constexpr int NEPI = 256;                    // epilogue threads (two groups of 128)
-    // readers of an item's n_i and drainers of its accumulator: one group
-    // (alternate items) or both (paired items)
+    // drainers of an item's accumulator: one group (alternate items) or both
+    // (paired items)
     constexpr int NITEM = NB == 2 ? 256 : 128;
     constexpr int W_MMA = 8, W_CP0 = 9;          // MMA warp, first of the two copier warps
     static_assert(NA >= 3 && NA <= 4, "the copiers keep NA - 2 items in flight");
-    static_assert(!UNI || RC == 1, "the uniform-bandwidth layout serves r = 1");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(sm);
-    float *ptbuf = reinterpret_cast<float *>(sm + S::PT);
     const uint32_t bar0 = sbase + S::BAR;
     auto BAR_A_FULL = [&](int s) { return bar0 + 8 * s; };            // target rows of stage s landed (64)
     auto BAR_A_EMPTY = [&](int s) { return bar0 + 8 * (4 + s); };     // MMAs reading stage s done (commit)
-    auto BAR_P_FULL = [&](int s) { return bar0 + 8 * (8 + s); };      // n_i of stage s's item stored (64)
-    auto BAR_P_EMPTY = [&](int s) { return bar0 + 8 * (12 + s); };    // epilogue read them (NITEM)
-    const uint32_t BAR_B_FULL = bar0 + 8 * 16, BAR_B_EMPTY = bar0 + 8 * 17;
-    auto BAR_BLK_FULL = [&](int s) { return bar0 + 8 * (18 + s); };   // column data of slot s landed
-    auto BAR_BLK_EMPTY = [&](int s) { return bar0 + 8 * (20 + s); };  // epilogue done with slot s (NEPI)
-    auto BAR_T_FULL = [&](int a) { return bar0 + 8 * (24 + a); };     // accumulator a complete (commit)
-    auto BAR_T_EMPTY = [&](int a) { return bar0 + 8 * (28 + a); };    // epilogue drained accumulator a (NITEM)
+    const uint32_t BAR_B_FULL = bar0 + 8 * 8, BAR_B_EMPTY = bar0 + 8 * 9;
+    auto BAR_BLK_FULL = [&](int s) { return bar0 + 8 * (10 + s); };   // weights of slot s landed
+    auto BAR_BLK_EMPTY = [&](int s) { return bar0 + 8 * (12 + s); };  // epilogue done with slot s (NEPI)
+    auto BAR_T_FULL = [&](int a) { return bar0 + 8 * (16 + a); };     // accumulator a complete (commit)
+    auto BAR_T_EMPTY = [&](int a) { return bar0 + 8 * (20 + a); };    // epilogue drained accumulator a (NITEM)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + S::MISC);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + S::MISC + 4);
 
@@ -128,8 +147,6 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
         for (int s = 0; s < NA; ++s) {
             mbar_init(BAR_A_FULL(s), 64);
             mbar_init(BAR_A_EMPTY(s), 1);
-            mbar_init(BAR_P_FULL(s), 64);
-            mbar_init(BAR_P_EMPTY(s), NITEM);
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(BAR_BLK_FULL(s), 1);
@@ -144,6 +161,13 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    // the copiers write only the first 16-byte chunk of each target row's
+    // norm block: the second (columns 8-15) stays zero
+    for (int e = tid; e < NA * G_ROWS; e += S::THREADS) {
+        const int s = e / G_ROWS, rr = e % G_ROWS;
+        *reinterpret_cast<uint4 *>(sm + S::A0 + s * S::ASTAGE + 2 * G_REGION + nx_off(rr, 1)) = make_uint4(0, 0, 0, 0);
+    }
+    fence_proxy_async();
     if (warp == W_MMA) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      ::"r"(smem_u32(tmem_slot)), "r"(G_TMEM_COLS) : "memory");
@@ -161,9 +185,8 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
         // the two groups take alternate items; with paired items (NB == 2)
         // group 0 takes the leader's 128 columns and group 1 the follower's,
         // and each writes its own entry's partial sum -- so every entry's
-        // partial is formed the same way in both layouts, and the groups
-        // never wait for each other.  A paired-layout item without a follower
-        // is summed by group 0 alone.
+        // partial is formed the same way in both layouts.  A paired-layout
+        // item without a follower is summed by group 0 alone.
         const int q = warp & 3;                    // this warp's TMEM lane quadrant
         const int row = q * 32 + lane;             // TMEM lane = target row of the item
         const int eg = warp >> 2;                  // group
@@ -172,8 +195,7 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
             const int b = args.cta_blocks[ci];
             const int bs = lb & 1;
             if (!mbar_wait(BAR_BLK_FULL(bs), (lb >> 1) & 1, abort_flag, args.status, args.spin)) goto epi_done;
-            const float4 *cv4 = reinterpret_cast<const float4 *>(sm + S::BLK + bs * S::BLKSLOT + S::BLK_COLV);
-            const float *cwp = reinterpret_cast<const float *>(sm + S::BLK + bs * S::BLKSLOT + S::BLK_COLW);
+            const float *cwp = reinterpret_cast<const float *>(sm + S::BLK + bs * S::BLKSLOT);
             const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
             // a paired follower's columns follow the leader's 128
             const int pb = NB == 2 ? args.partner[b] : -1;
@@ -188,12 +210,9 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
             }
             for (int it = i0; it < i1; ++it, ++li) {
                 if (NB == 1 && (li & 1) != eg) continue;   // the other group's item
-                const int a4 = li % NACC, sp = li % NA;
+                const int a4 = li % NACC;
                 const EvalItem item = args.items[it];
                 const int e_out = (NB == 2 && eg == 1) ? (pb >= 0 ? args.items[f0 + (it - i0)].e0 : 0) : item.e0;
-                if (!mbar_wait(BAR_P_FULL(sp), (li / NA) & 1, abort_flag, args.status, args.spin)) goto epi_done;
-                const float pt = ptbuf[sp * 128 + row];
-                mbar_arrive(BAR_P_EMPTY(sp));
                 if (!mbar_wait(BAR_T_FULL(a4), (li / NACC) & 1, abort_flag, args.status, args.spin)) goto epi_done;
                 tc_fence_after();
                 float acc[RC];
@@ -204,42 +223,25 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
 #pragma unroll
                 for (int z = 0; z < (RC > 1 ? RC / 2 : 1); ++z) accw[z] = make_float2(0.f, 0.f);
                 if (q * 32 < item.cnt && c_lo < c_hi) {   // warp-uniform
-                    const float2 pt2 = make_float2(pt, pt);
-                    // arg = G A + (C n_i + B); columns past the rows carry B = -inf
-                    // (UNI) or A = B = C = w = 0
+                    // the accumulator holds the exponent's argument; columns
+                    // past the rows carry w = 0
                     auto cols = [&](int c, const uint32_t (&gr)[32]) {
-                        if constexpr (RC == 1 && UNI) {
-                            const float2 a2 = make_float2(args.uni_a, args.uni_a);
-                            const float2 c2 = make_float2(args.uni_c, args.uni_c);
+                        if constexpr (RC == 1) {
 #pragma unroll
-                            for (int jj = 0; jj < 32; jj += 2) {
-                                const float4 bw = cv4[(c * 32 + jj) >> 1];   // {B_j, B_j+1, w_j, w_j+1}
-                                const float2 inner = __ffma2_rn(c2, pt2, make_float2(bw.x, bw.y));
-                                const float2 arg = __ffma2_rn(make_float2(__uint_as_float(gr[jj]), __uint_as_float(gr[jj + 1])),
-                                                              a2, inner);
-                                const float2 k = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
-                                acc2[(jj >> 1) & 1] = __ffma2_rn(k, make_float2(bw.z, bw.w), acc2[(jj >> 1) & 1]);
-                            }
-                        } else if constexpr (RC == 1) {
-#pragma unroll
-                            for (int jj = 0; jj < 32; jj += 2) {
-                                const float4 ab = cv4[c * 32 + jj];
-                                const float4 cw = cv4[c * 32 + jj + 1];
-                                const float2 inner = __ffma2_rn(make_float2(cw.x, cw.y), pt2, make_float2(ab.z, ab.w));
-                                const float2 arg = __ffma2_rn(make_float2(__uint_as_float(gr[jj]), __uint_as_float(gr[jj + 1])),
-                                                              make_float2(ab.x, ab.y), inner);
-                                const float2 k = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
-                                acc2[(jj >> 1) & 1] = __ffma2_rn(k, make_float2(cw.z, cw.w), acc2[(jj >> 1) & 1]);
+                            for (int jj = 0; jj < 32; jj += 4) {
+                                const float4 w4 = *reinterpret_cast<const float4 *>(cwp + c * 32 + jj);
+                                const float2 k0 = make_float2(ex2_approx(__uint_as_float(gr[jj])),
+                                                              ex2_approx(__uint_as_float(gr[jj + 1])));
+                                const float2 k1 = make_float2(ex2_approx(__uint_as_float(gr[jj + 2])),
+                                                              ex2_approx(__uint_as_float(gr[jj + 3])));
+                                acc2[0] = __ffma2_rn(k0, make_float2(w4.x, w4.y), acc2[0]);
+                                acc2[1] = __ffma2_rn(k1, make_float2(w4.z, w4.w), acc2[1]);
                             }
                         } else {
 #pragma unroll
                             for (int jj = 0; jj < 32; ++jj) {
                                 const int j = c * 32 + jj;
-                                const float4 ab = cv4[j & ~1];
-                                const float4 cw = cv4[(j & ~1) + 1];
-                                const bool h = j & 1;
-                                const float A = h ? ab.y : ab.x, B = h ? ab.w : ab.z, Cc = h ? cw.y : cw.x;
-                                const float k = ex2_approx(fmaf(__uint_as_float(gr[jj]), A, fmaf(Cc, pt, B)));
+                                const float k = ex2_approx(__uint_as_float(gr[jj]));
                                 const float2 k2 = make_float2(k, k);
                                 const float4 *w4 = reinterpret_cast<const float4 *>(cwp + j * RC);
 #pragma unroll
@@ -294,18 +296,20 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
     } else if (warp >= W_CP0) {
         // ----------------------------------------------------- target-row copiers
         // Copier warp w takes rows 64 w .. 64 w + 63 of every item: lane l
-        // holds the target slots of rows 64 w + 2 l and + 1, and each 16-byte
-        // copy instruction covers four whole rows (eight lanes per 128-byte
-        // row, coalesced), into the 128-byte swizzled K-major layout.  The
-        // item's copies form one commit group; the stage is reported full
-        // (after a proxy fence) DLAG items later, so NA - 1 items' copies are
-        // in flight.  The loads an item needs -- its descriptor, its target
-        // slots, their n_i -- run as a pipeline three items deep.
+        // holds the target slots of rows 64 w + 2 l and + 1.  Each 16-byte copy
+        // instruction of the split rows covers four whole rows (eight lanes per
+        // 128-byte row, coalesced) into the 128-byte swizzled K-major layout;
+        // the norm blocks' first chunks follow, one row per lane.  An item's
+        // copies form one commit group; the stage is reported full (after a
+        // proxy fence) NA - 2 items later.  The loads an item needs -- its
+        // descriptor, then its target slots -- run as a pipeline two items
+        // ahead.
         constexpr int DLAG = NA - 2;
         const int cw = warp - W_CP0;
         const int u = lane >> 3, j = lane & 7;           // row within a group of four, 16-byte chunk
         const char *qhi = reinterpret_cast<const char *>(args.q_hi);
         const char *qlo = reinterpret_cast<const char *>(args.q_lo);
+        const char *qx = reinterpret_cast<const char *>(args.q_x);
         // cursor over this CTA's items in order: block index, item, end of
         // the block's items (loaded once per block)
         int cc = c_begin, cit = 0, cend = 0;
@@ -343,30 +347,17 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                 r[k] = dd.ok ? args.tgt[dd.e0 + (rw < dd.cnt ? rw : 0)] : 0;
             }
         };
-        auto load_p = [&](bool ok, const int (&r)[2], float (&p)[2]) {
-#pragma unroll
-            for (int k = 0; k < 2; ++k) p[k] = ok ? args.qn[r[k]] : 0.f;
-        };
-        Desc d0 = load_desc(), d1 = load_desc(), d2 = load_desc();
-        int r0[2], r1[2], r2[2];
-        float p0[2], p1[2];
+        Desc d0 = load_desc(), d1 = load_desc();
+        int r0[2], r1[2];
         load_rows(d0, r0);
-        load_rows(d1, r1);
-        load_p(d0.ok, r0, p0);
         int li = 0;
         for (; d0.ok && !*abort_flag; ++li) {
-            const Desc d3 = load_desc();      // item li + 3
-            load_rows(d2, r2);                // item li + 2
-            load_p(d1.ok, r1, p1);            // item li + 1
+            const Desc d2 = load_desc();      // item li + 2
+            load_rows(d1, r1);                // item li + 1
             const int sa = li % NA;
-            // n_i of this item's targets: the slot is free once the epilogue
-            // of the item NA back has read it
-            if (!mbar_wait(BAR_P_EMPTY(sa), ((li / NA) & 1) ^ 1, abort_flag, args.status, args.spin)) goto copy_done;
-            *reinterpret_cast<float2 *>(ptbuf + sa * 128 + 64 * cw + 2 * lane) = make_float2(p0[0], p0[1]);
-            mbar_arrive(BAR_P_FULL(sa));
             if (!mbar_wait(BAR_A_EMPTY(sa), ((li / NA) & 1) ^ 1, abort_flag, args.status, args.spin)) goto copy_done;
             {
-                const uint32_t a_hi = sbase + S::A0 + sa * 2 * G_REGION;
+                const uint32_t a_hi = sbase + S::A0 + sa * S::ASTAGE;
 #pragma unroll
                 for (int g = 0; g < 16; ++g) {
                     // rows 64 cw + 4 g + u: slot held by lane 2 g + (u >> 1)
@@ -374,10 +365,15 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                     const int s0 = __shfl_sync(0xffffffffu, r0[0], src_lane);
                     const int s1 = __shfl_sync(0xffffffffu, r0[1], src_lane);
                     const int slot = (u & 1) ? s1 : s0;
-                    const int row = 64 * cw + 4 * g + u;
-                    const uint32_t off = (uint32_t)(row * 128 + ((j ^ (row & 7)) << 4));
+                    const int rr = 64 * cw + 4 * g + u;
+                    const uint32_t off = (uint32_t)(rr * 128 + ((j ^ (rr & 7)) << 4));
                     cp_async16(a_hi + off, qhi + (int64_t)slot * 128 + 16 * j);
                     cp_async16(a_hi + G_REGION + off, qlo + (int64_t)slot * 128 + 16 * j);
+                }
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int rr = 64 * cw + 2 * lane + k;
+                    cp_async16(a_hi + 2 * G_REGION + nx_off(rr, 0), qx + (int64_t)r0[k] * (2 * GX_K));
                 }
                 cp_async_commit();
             }
@@ -388,13 +384,8 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
             }
             d0 = d1;
             d1 = d2;
-            d2 = d3;
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                r0[k] = r1[k];
-                r1[k] = r2[k];
-                p0[k] = p1[k];
-            }
+            for (int k = 0; k < 2; ++k) r0[k] = r1[k];
         }
         // the last items' copies
         cp_async_wait<0>();
@@ -407,7 +398,7 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
     } else if (warp == W_MMA && lane == 0) {
         // ------------------------------------- sub-block loads + MMA issuer
         int li = 0, lb = 0, b_issued = 0;
-        int blk_last[2] = {-1, -1};   // last block whose column data went to slot 0 / 1
+        int blk_last[2] = {-1, -1};   // last block whose weights went to slot 0 / 1
         int li_done = -1;             // last item whose MMAs were committed
         for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci, ++lb) {
             const int b = args.cta_blocks[ci];
@@ -416,7 +407,7 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
             const bool far = first.nrows < 0;
             const int bs = lb & 1;
             // a paired follower (NB == 2) is the next sub-block of the same
-            // node: its rows, column data and weights follow the leader's
+            // node: its rows, norm block and weights follow the leader's
             const int pb = NB == 2 ? args.partner[b] : -1;
             const int nsb = pb >= 0 ? 2 : 1;
             const int ncols = (first.nrows & 0x7fffffff) + (pb >= 0 ? (args.items[args.block_off[pb]].nrows & 0x7fffffff) : 0);
@@ -427,20 +418,19 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
             if (!mbar_wait(BAR_BLK_EMPTY(bs), ((lb >> 1) & 1) ^ 1, abort_flag, args.status, args.spin)) goto mma_done;
             b_issued = lb + 1;
             blk_last[bs] = lb;
-            mbar_expect_tx(BAR_B_FULL, (uint32_t)(2 * nsb * G_REGION));
+            mbar_expect_tx(BAR_B_FULL, (uint32_t)(nsb * (2 * G_REGION + GX_REGION)));
             for (int h = 0; h < nsb; ++h) {
                 tma_load_2d(sbase + S::B_HI + h * G_REGION, far ? &map_s_hi : &map_t_hi, 0, first.row0 + 128 * h,
                             BAR_B_FULL);
                 tma_load_2d(sbase + S::B_LO + h * G_REGION, far ? &map_s_lo : &map_t_lo, 0, first.row0 + 128 * h,
                             BAR_B_FULL);
             }
-            const uint32_t slot = sbase + S::BLK + bs * S::BLKSLOT;
-            const uint32_t colw_bytes = RC > 1 ? (uint32_t)(nsb * 128 * RC * 4) : 0u;
-            constexpr int CV = UNI ? 64 : 128;   // float4 of column data per sub-block
-            mbar_expect_tx(BAR_BLK_FULL(bs), (uint32_t)(nsb * CV * 16) + colw_bytes);
-            bulk_copy(slot + S::BLK_COLV, args.colv + (int64_t)first.cidx * CV, nsb * CV * 16, BAR_BLK_FULL(bs));
-            if constexpr (RC > 1)
-                bulk_copy(slot + S::BLK_COLW, args.colw + (int64_t)first.cidx * 128 * RC, colw_bytes, BAR_BLK_FULL(bs));
+            bulk_copy(sbase + S::B_X, args.bx + (int64_t)first.cidx * G_ROWS * GX_K, (uint32_t)(nsb * GX_REGION),
+                      BAR_B_FULL);
+            const uint32_t wbytes = (uint32_t)(nsb * 128 * RC * 4);
+            mbar_expect_tx(BAR_BLK_FULL(bs), wbytes);
+            bulk_copy(sbase + S::BLK + bs * S::BLKSLOT, args.colw + (int64_t)first.cidx * 128 * RC, wbytes,
+                      BAR_BLK_FULL(bs));
             for (int it = i0; it < i1; ++it, ++li) {
                 const int sa = li % NA, a4 = li % NACC;
                 if (!mbar_wait(BAR_A_FULL(sa), (li / NA) & 1, abort_flag, args.status, args.spin)) goto mma_done;
@@ -448,10 +438,13 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                 if (!mbar_wait(BAR_T_EMPTY(a4), ((li / NACC) & 1) ^ 1, abort_flag, args.status, args.spin)) goto mma_done;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)(a4 * 128 * NB);
-                const uint32_t a_hi = sbase + S::A0 + sa * 2 * G_REGION, a_lo = a_hi + G_REGION;
-                const uint32_t b_hi = sbase + S::B_HI, b_lo = sbase + S::B_LO;
-                // the tensor core rounds each accumulation step to the running sum's
-                // precision: the small cross terms first, the hi*hi products last
+                const uint32_t a_hi = sbase + S::A0 + sa * S::ASTAGE, a_lo = a_hi + G_REGION;
+                const uint32_t a_x = a_hi + 2 * G_REGION;
+                const uint32_t b_hi = sbase + S::B_HI, b_lo = sbase + S::B_LO, b_x = sbase + S::B_X;
+                // the tensor core rounds each accumulation step to the running
+                // sum's precision: the small cross terms first, then the hi*hi
+                // products, then the norm block, which brings the sum down to
+                // the exponent's argument
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {   // K = 16 per MMA: 32 bytes into the 128-byte rows
                     const uint32_t off = (uint32_t)(k * 32);
@@ -463,6 +456,7 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                     const uint32_t off = (uint32_t)(k * 32);
                     tc_mma<ASKIT_PREC_FP16X3>(d_tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, 1);
                 }
+                tc_mma<ASKIT_PREC_FP16X3>(d_tmem, ns_desc(a_x), ns_desc(b_x), idesc, 1);
                 tc_commit(BAR_A_EMPTY(sa));
                 tc_commit(BAR_T_FULL(a4));
                 if (it == i1 - 1) tc_commit(BAR_B_EMPTY);
@@ -470,10 +464,10 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
             }
         }
     mma_done:
-        // after an abort: the last sub-block's tiles and the latest column
-        // data of each slot may still be landing, and MMAs may still be
-        // writing TMEM -- wait for them before TMEM is freed and the CTA
-        // exits (no-ops on the normal path)
+        // after an abort: the last sub-block's tiles and the latest weights of
+        // each slot may still be landing, and MMAs may still be writing TMEM
+        // -- wait for them before TMEM is freed and the CTA exits (no-ops on
+        // the normal path)
         if (b_issued > 0) mbar_drain(BAR_B_FULL, (b_issued - 1) & 1);
         for (int k = 0; k < 2; ++k)
             if (blk_last[k] >= 0) mbar_drain(BAR_BLK_FULL(k), (blk_last[k] >> 1) & 1);
@@ -487,43 +481,24 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
     }
 }
 
-// Column data of every sub-block for one Evaluate, from the global-centered
-// norms: thread t of block b takes source row t of sub-block b.  General
-// layout, rows (2p, 2p+1): {A_2p, A_2p+1, B_2p, B_2p+1}, {C_2p, C_2p+1, w_2p,
-// w_2p+1} with A = 2 sc / s^2, B = -sc n_j, C = -sc (zeros past the rows);
-// UNI (one bandwidth): {B_j, B_j+1, w_j, w_j+1} with B = -inf past the rows.
-template <int RC, int UNI>
-__global__ void g16_cols_kernel(const int64_t *sb_row0, const int32_t *sb_nr, int64_t n_leaf_sub, const float *sc_t,
-                                const float *sc_s, const float *ng_t, const float *ng_s, const float *Wt,
-                                const float *Ws, int r, float g_unscale, float4 *colv, float *colw) {
+// Weights of every sub-block for one Evaluate: thread t of block b takes
+// source row t of sub-block b: colw [b, t, z] = w_z (zeros past the rows and
+// past r).
+template <int RC>
+__global__ void g16_cols_kernel(const int64_t *sb_row0, const int32_t *sb_nr, int64_t n_leaf_sub, const float *Wt,
+                                const float *Ws, int r, float *colw) {
     const int64_t b = blockIdx.x;
     const int t = threadIdx.x;
     const bool far = b >= n_leaf_sub;
     const int64_t row = sb_row0[b] + t;
     const bool valid = t < sb_nr[b];
-    const float sc = valid ? (far ? sc_s : sc_t)[row] : 0.f;
-    const float nrm = valid ? (far ? ng_s : ng_t)[row] : 0.f;
     const float *w = (far ? Ws : Wt) + row * r;
-    const int o = t & 1;
-    if (UNI) {
-        float *cp = reinterpret_cast<float *>(colv + b * 64 + (t >> 1));
-        cp[0 + o] = valid ? -sc * nrm : -INFINITY;
-        cp[2 + o] = valid ? w[0] : 0.f;
-        return;
-    }
-    float *cp = reinterpret_cast<float *>(colv + b * 128 + 2 * (t >> 1));
-    cp[0 + o] = 2.f * g_unscale * sc;
-    cp[2 + o] = -sc * nrm;
-    cp[4 + o] = -sc;
-    cp[6 + o] = valid ? w[0] : 0.f;
-    if (RC > 1) {
 #pragma unroll
-        for (int z = 0; z < RC; ++z) colw[(b * 128 + t) * RC + z] = (valid && z < r) ? w[z] : 0.f;
-    }
+    for (int z = 0; z < RC; ++z) colw[(b * 128 + t) * RC + z] = (valid && z < r) ? w[z] : 0.f;
 }
 
-// Tensor maps over the tree's pre-split operands (64 x 128 boxes, 128-byte
-// swizzle): [t_hi, t_lo, s_hi, s_lo].
+// Tensor maps over the tree's split source rows (64 x 128 boxes, 128-byte
+// swizzle): [leaf rows hi, lo, skeleton rows hi, lo].
 struct G16State {
     CUtensorMap map[4];
     bool ready = false;
@@ -538,7 +513,7 @@ askit_status g16_state(askit_tree t, G16State **out) {
     G16State *st = (G16State *)t->g16;
     if (!st->encode) ASK_TRY(encode_fn(&st->encode));
     if (!st->ready) {
-        const void *arr[4] = {t->Xg_hi, t->Xg_lo, t->Sg_hi, t->Sg_lo};
+        const void *arr[4] = {t->Xb_hi, t->Xb_lo, t->Sb_hi, t->Sb_lo};
         for (int i = 0; i < 4; ++i)
             ASK_TRY(encode_2d(st->encode, &st->map[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, arr[i],
                               i < 2 ? t->N_pad : t->srows, TC_K, 64, G_ROWS, CU_TENSOR_MAP_SWIZZLE_128B));
@@ -548,66 +523,46 @@ askit_status g16_state(askit_tree t, G16State **out) {
     return ASKIT_OK;
 }
 
-template <int RC, int NA, int NB, int UNI>
+template <int RC, int NA, int NB>
 askit_status launch_g16(G16State *st, const G16Args &a, int grid, cudaStream_t s) {
     using S = SG<RC, NA, NB>;
     constexpr size_t smem = S::BYTES + 1024;
     static_assert(smem <= 232448, "shared-memory plan exceeds 227 KB");
-    static const cudaError_t attr = cudaFuncSetAttribute(eval_g16_kernel<RC, NA, NB, UNI>,
+    static const cudaError_t attr = cudaFuncSetAttribute(eval_g16_kernel<RC, NA, NB>,
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     ASK_CUDA(attr);
-    eval_g16_kernel<RC, NA, NB, UNI><<<(unsigned)grid, S::THREADS, smem, s>>>(
-        st->map[0], st->map[1], st->map[2], st->map[3], a);
+    eval_g16_kernel<RC, NA, NB><<<(unsigned)grid, S::THREADS, smem, s>>>(st->map[0], st->map[1], st->map[2],
+                                                                         st->map[3], a);
     ASK_LAUNCH();
     return ASKIT_OK;
-}
-
-template <int RC, int UNI>
-askit_status pick_g16(askit_tree t, G16State *st, G16Args a, const WorkLists &w, int stages, bool pairs,
-                      cudaStream_t s) {
-    // three or four target-row stages (one or two items' copies in flight);
-    // paired 256-column items up to r = 4
-    if constexpr (RC <= 4) {
-        if (pairs && w.sched_off[2]) {
-            a.cta_off = w.sched_off[2];
-            a.cta_blocks = w.sched_blocks[2];
-            a.partner = w.partner;
-            if (stages <= 3) return launch_g16<RC, 3, 2, UNI>(st, a, w.n_ctas, s);
-            return launch_g16<RC, 4, 2, UNI>(st, a, w.n_ctas, s);
-        }
-    }
-    if (stages <= 3) return launch_g16<RC, 3, 1, UNI>(st, a, w.n_ctas, s);
-    return launch_g16<RC, 4, 1, UNI>(st, a, w.n_ctas, s);
 }
 
 template <int RC>
 askit_status run_g16(askit_tree t, const WeightCtx &c, G16State *st, G16Args a, const WorkLists &w,
                      cudaStream_t s) {
-    const float g_unscale = 1.f / (t->g_scale * t->g_scale);
-    const bool uni = RC == 1 && t->prm.bw_mode == ASKIT_BW_CONSTANT;
-    if (uni) {
-        // the same rounding as the per-row values (h held in FP32)
-        const double hf = (double)(float)t->prm.h;
-        const float sc = (float)(t->prm.kernel_scale * 1.4426950408889634 / (hf * hf));
-        a.uni_a = 2.f * g_unscale * sc;
-        a.uni_c = -sc;
-        g16_cols_kernel<RC, 1><<<(unsigned)t->n_sub, 128, 0, s>>>(t->sb_row0, t->sb_nr, t->n_leaf_sub, t->sc_t, t->sc_s,
-                                                                  t->ng_t, t->ng_s, c.Wt, c.Ws, c.r, g_unscale, c.colv,
-                                                                  c.colw);
-    } else {
-        g16_cols_kernel<RC, 0><<<(unsigned)t->n_sub, 128, 0, s>>>(t->sb_row0, t->sb_nr, t->n_leaf_sub, t->sc_t, t->sc_s,
-                                                                  t->ng_t, t->ng_s, c.Wt, c.Ws, c.r, g_unscale, c.colv,
-                                                                  c.colw);
-    }
+    // weights in the sub-blocks' row order: r = 1 in the first 128 floats of
+    // each sub-block's column-data slot, r > 1 in the per-sub-block weights
+    float *colw = RC == 1 ? reinterpret_cast<float *>(c.colv) : c.colw;
+    g16_cols_kernel<RC><<<(unsigned)t->n_sub, 128, 0, s>>>(t->sb_row0, t->sb_nr, t->n_leaf_sub, c.Wt, c.Ws, c.r, colw);
     ASK_LAUNCH();
-    a.colv = c.colv;
-    a.colw = c.colw;
+    a.colw = colw;
     ASK_TRY(ktimer_mark(t, s, false));
-    if constexpr (RC == 1) {
-        if (uni) ASK_TRY((pick_g16<RC, 1>(t, st, a, w, t->tune_stages, t->tune_pairs, s)));
-        else ASK_TRY((pick_g16<RC, 0>(t, st, a, w, t->tune_stages, t->tune_pairs, s)));
-    } else {
-        ASK_TRY((pick_g16<RC, 0>(t, st, a, w, t->tune_stages, t->tune_pairs, s)));
+    // three or four target-row stages (one or two items' copies in flight);
+    // paired 256-column items up to r = 4
+    bool done = false;
+    if constexpr (RC <= 4) {
+        if (t->tune_pairs && w.sched_off[2]) {
+            a.cta_off = w.sched_off[2];
+            a.cta_blocks = w.sched_blocks[2];
+            a.partner = w.partner;
+            if (t->tune_stages <= 3) ASK_TRY((launch_g16<RC, 3, 2>(st, a, w.n_ctas, s)));
+            else ASK_TRY((launch_g16<RC, 4, 2>(st, a, w.n_ctas, s)));
+            done = true;
+        }
+    }
+    if (!done) {
+        if (t->tune_stages <= 3) ASK_TRY((launch_g16<RC, 3, 1>(st, a, w.n_ctas, s)));
+        else ASK_TRY((launch_g16<RC, 4, 1>(st, a, w.n_ctas, s)));
     }
     return ktimer_mark(t, s, true);
 }
@@ -621,7 +576,7 @@ askit_status eval_g16(askit_tree t, const WeightCtx &c, const QuerySplit &q, con
         return ASKIT_ERR_UNSUPPORTED;
     }
     if (w.n_blocks == 0) return ASKIT_OK;
-    if (!t->Xg_hi || !q.hi || !q.lo || !q.n || !c.colv || (c.r > 1 && !c.colw)) {
+    if (!t->Xb_hi || !t->g_bx || !q.hi || !q.lo || !q.x || !c.colv || (c.r > 1 && !c.colw)) {
         askit_set_error("the global-centered FP16x3 operands are missing");
         return ASKIT_ERR_INVALID_ARG;
     }
@@ -635,12 +590,11 @@ askit_status eval_g16(askit_tree t, const WeightCtx &c, const QuerySplit &q, con
     a.tgt = w.tgt;
     a.q_hi = q.hi;
     a.q_lo = q.lo;
-    a.qn = q.n;
-    a.colv = nullptr;
+    a.q_x = q.x;
+    a.bx = t->g_bx;
     a.colw = nullptr;
     a.partner = nullptr;
     a.r = c.r;
-    a.uni_a = a.uni_c = 0.f;
     a.partial = partial;
     a.status = t->d_status;
     a.spin = t->spin_limit > 0 ? t->spin_limit : SPIN_LIMIT;
@@ -655,14 +609,24 @@ void eval_g16_free(askit_tree t) {
 }
 
 // ---------------------------------------------------------------------------
-// Global-centered operands: x~ = (x - xbar) s split into FP16 hi + lo, and
-// n = |x - xbar|^2, one warp per row (lanes over the TC_K columns; the sum of
-// squares in FP64 over a fixed butterfly, then rounded).  Rows past `rows`
-// are left as they are (zeros from the caller's memset).  A row whose scaled
-// value leaves the FP16-safe range raises *overflow.
+// Operands.  FP16 split of v: hi = fp16(v), lo = fp16(v - hi).
 // ---------------------------------------------------------------------------
-__global__ void gsplit_kernel(const float *X, int64_t ldx, int d, int64_t rows, const float *xbar, float scale,
-                              uint16_t *hi, uint16_t *lo, float *n, int *overflow) {
+namespace {
+
+__device__ __forceinline__ void split16(float v, uint16_t &h, uint16_t &l) {
+    const __half vh = __float2half_rn(v);
+    const __half vl = __float2half_rn(v - __half2float(vh));
+    h = __half_as_ushort(vh);
+    l = __half_as_ushort(vl);
+}
+
+// Target rows: a = (x - xbar) sigma split, and the norm block [h(n tau),
+// h(n tau), l(n tau), kappa, kappa, 0 ...] with n = |x - xbar|^2 (FP64 sum
+// over a fixed butterfly, rounded).  One warp per row.  A value outside the
+// FP16-safe range raises *overflow.
+__global__ void gsplit_targets_kernel(const float *X, int64_t ldx, int d, int64_t rows, const float *xbar, float sigma,
+                                      float tau, float kappa, uint16_t *hi, uint16_t *lo, uint16_t *nx,
+                                      int *overflow) {
     const int lane = threadIdx.x & 31;
     const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= rows) return;
@@ -673,27 +637,84 @@ __global__ void gsplit_kernel(const float *X, int64_t ldx, int d, int64_t rows, 
         const int k = lane + 32 * h;
         const float x = k < d ? X[row * ldx + k] - xbar[k] : 0.f;
         acc += (double)x * (double)x;
-        const float v = x * scale;
+        const float v = x * sigma;
         bad |= !(fabsf(v) <= 30000.f);
-        const __half vh = __float2half_rn(v);
-        const __half vl = __float2half_rn(v - __half2float(vh));
-        hi[row * TC_K + k] = __half_as_ushort(vh);
-        lo[row * TC_K + k] = __half_as_ushort(vl);
+        split16(v, hi[row * TC_K + k], lo[row * TC_K + k]);
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) n[row] = (float)acc;
+    const float nt = (float)acc * tau;
+    bad |= !(nt <= 30000.f);
+    if (lane < GX_K) {
+        uint16_t h = 0, l = 0;
+        split16(nt, h, l);
+        const uint16_t kk = __half_as_ushort(__float2half_rn(kappa));
+        const uint16_t v = lane <= 1 ? h : lane == 2 ? l : lane <= 4 ? kk : (uint16_t)0;
+        nx[row * GX_K + lane] = v;
+    }
     if (__any_sync(0xffffffffu, bad) && lane == 0 && overflow) atomicExch(overflow, 1);
 }
 
-askit_status g16_split_rows(const float *X, int64_t ldx, int d, int64_t rows, const float *xbar, float scale,
-                            uint16_t *hi, uint16_t *lo, float *n, int *overflow, cudaStream_t s) {
-    if (rows <= 0) return ASKIT_OK;
-    gsplit_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(X, ldx, d, rows, xbar, scale, hi, lo, n, overflow);
-    ASK_LAUNCH();
-    return ASKIT_OK;
+// Source rows: b = (y - xbar) 2 sc_j / sigma split (sc_j the row's exponent
+// scale; padding rows carry sc = 0) and n_j.  One warp per row.
+__global__ void gsplit_sources_kernel(const float *X, int64_t ldx, int d, int64_t rows, const float *xbar,
+                                      const float *sc, float inv_sigma, uint16_t *hi, uint16_t *lo, float *nrm) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= rows) return;
+    const float f = 2.f * sc[row] * inv_sigma;
+    double acc = 0.0;
+#pragma unroll
+    for (int h = 0; h < TC_K / 32; ++h) {
+        const int k = lane + 32 * h;
+        const float x = k < d ? X[row * ldx + k] - xbar[k] : 0.f;
+        acc += (double)x * (double)x;
+        split16(x * f, hi[row * TC_K + k], lo[row * TC_K + k]);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) nrm[row] = (float)acc;
 }
 
-namespace {
+// Source norm blocks, one 128-row block per sub-block in the core-matrix
+// layout: row t = [h(m), l(m), h(m), h(v), l(v), 0 ...], m = -sc / tau,
+// v = -sc n / kappa.
+__global__ void gsplit_bx_kernel(const int64_t *sb_row0, const int32_t *sb_nr, int64_t n_leaf_sub, const float *sc_t,
+                                 const float *sc_s, const float *n_t, const float *n_s, float inv_tau, float inv_kappa,
+                                 uint16_t *bx) {
+    const int64_t b = blockIdx.x;
+    const int t = threadIdx.x;
+    const bool far = b >= n_leaf_sub;
+    const int64_t row = sb_row0[b] + t;
+    const bool valid = t < sb_nr[b];
+    uint16_t e[GX_K];
+#pragma unroll
+    for (int k = 0; k < GX_K; ++k) e[k] = 0;
+    // a row past the sub-block (the tile's next rows hold other points, whose
+    // main products may be large and positive) gets kappa v = -60000 kappa:
+    // its argument stays far below zero, so ex2 is finite (0) and the zero
+    // weight leaves no trace
+    e[3] = __half_as_ushort(__float2half_rn(-60000.f));
+    if (valid) {
+        const float sc = (far ? sc_s : sc_t)[row], n = (far ? n_s : n_t)[row];
+        uint16_t mh, ml, vh, vl;
+        split16(-sc * inv_tau, mh, ml);
+        split16(-sc * n * inv_kappa, vh, vl);
+        e[0] = mh;
+        e[1] = ml;
+        e[2] = mh;
+        e[3] = vh;
+        e[4] = vl;
+    }
+    uint8_t *blk = reinterpret_cast<uint8_t *>(bx + b * G_ROWS * GX_K);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        uint4 v;
+        v.x = (uint32_t)e[8 * c] | ((uint32_t)e[8 * c + 1] << 16);
+        v.y = (uint32_t)e[8 * c + 2] | ((uint32_t)e[8 * c + 3] << 16);
+        v.z = (uint32_t)e[8 * c + 4] | ((uint32_t)e[8 * c + 5] << 16);
+        v.w = (uint32_t)e[8 * c + 6] | ((uint32_t)e[8 * c + 7] << 16);
+        *reinterpret_cast<uint4 *>(blk + nx_off(t, c)) = v;
+    }
+}
 
 // Column sums of the first n rows of X [*, ldx] in FP64 (thread-strided
 // partial sums, then a fixed tree over the block): mean[k] = sum / n, FP32.
@@ -729,13 +750,30 @@ __global__ void max_kernel(const float *a, int64_t n, float *out) {
     if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(out), __float_as_int(v));
 }
 
+// The power of 2 nearest to v (in the exponent).
+float pow2_near(double v) {
+    if (!(v > 0.0)) return 1.f;
+    return ldexpf(1.f, (int)lround(log2(v)));
+}
+
 }  // namespace
 
+askit_status g16_split_rows(const float *X, int64_t ldx, int d, int64_t rows, const askit_tree_s *t, uint16_t *hi,
+                            uint16_t *lo, uint16_t *nx, int *overflow, cudaStream_t s) {
+    if (rows <= 0) return ASKIT_OK;
+    gsplit_targets_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(X, ldx, d, rows, t->g_xbar, t->g_sigma, t->g_tau,
+                                                                    t->g_kappa, hi, lo, nx, overflow);
+    ASK_LAUNCH();
+    return ASKIT_OK;
+}
+
 // The global-centered FP16x3 operands of a narrow tree (d <= TC_K): xbar (the
-// FP64 mean of the points), the prescale (a power of 2 mapping the largest
-// |x_k - xbar_k| to at most 2^12, so targets up to 7 times farther out still
-// fit FP16), the split rows of the tree points and of the skeleton pool, their
-// n = |x - xbar|^2, and the accuracy figure rho = max_j sc_j max_i n_i: the
+// FP64 mean of the points), the scales sigma (a power of 2 near sqrt(2 sc_max),
+// kept so that every |x_k - xbar_k| sigma <= 2^12: targets up to about 7 times
+// farther out still fit FP16), tau near sqrt(sc_max / R^2_max) and kappa near
+// sqrt(sc_max R^2_max), the split target rows of the tree points, the split
+// source rows of the points and of the skeleton pool, the source norm blocks
+// of every sub-block, and the accuracy figure rho = sc_max R^2_max: the
 // exponent's FP32 rounding error is a few 2^-24 rho, so g_ok (the automatic
 // choice of this kernel) holds while rho <= 512 (relative error of u about
 // 1e-5 at rho = 150, within the split-product tolerance 1e-4 up to the bound).
@@ -750,33 +788,52 @@ askit_status build_g16_operands(askit_tree t, cudaStream_t s) {
     ASK_CUDA(cudaMallocAsync(&red, 3 * sizeof(float), s));
     ASK_CUDA(cudaMemsetAsync(red, 0, 3 * sizeof(float), s));
     dev_extent_kernel<<<(unsigned)((t->N * d + 255) / 256), 256, 0, s>>>(t->Xt, t->d_pad, d, t->N, t->g_xbar, red);
+    max_kernel<<<(unsigned)((t->N + 255) / 256), 256, 0, s>>>(t->sc_t, t->N, red + 2);
     ASK_LAUNCH();
     float hred[3] = {0.f, 0.f, 0.f};
-    ASK_CUDA(cudaMemcpyAsync(hred, red, sizeof(float), cudaMemcpyDeviceToHost, s));
+    ASK_CUDA(cudaMemcpyAsync(hred, red, 3 * sizeof(float), cudaMemcpyDeviceToHost, s));
     ASK_CUDA(cudaStreamSynchronize(s));
-    int e = 0;
-    if (hred[0] > 0.f) frexpf(4096.f / hred[0], &e);
-    t->g_scale = ldexpf(1.f, e - 1);
+    const double ext = hred[0], sc_max = hred[2];
+    float sigma = pow2_near(sqrt(2.0 * sc_max));
+    while (ext * sigma > 4096.0) sigma *= 0.5f;
+    t->g_sigma = sigma;
+    // the sources' split rows and every row's n; every row, padding
+    // included, holds finite values (a 128-row tile read past a short
+    // sub-block multiplies them by zero weights)
     const size_t et = (size_t)t->N_pad * TC_K, es = (size_t)t->srows * TC_K;
-    ASK_TRY(t->arena.alloc(&t->Xg_hi, et));
-    ASK_TRY(t->arena.alloc(&t->Xg_lo, et));
-    ASK_TRY(t->arena.alloc(&t->Sg_hi, es));
-    ASK_TRY(t->arena.alloc(&t->Sg_lo, es));
     ASK_TRY(t->arena.alloc(&t->ng_t, t->N_pad));
     ASK_TRY(t->arena.alloc(&t->ng_s, t->srows));
-    // every row, padding included, holds finite values: a 128-row tile read
-    // past a short sub-block multiplies them by zero column data
-    ASK_TRY(g16_split_rows(t->Xt, t->d_pad, d, t->N_pad, t->g_xbar, t->g_scale, t->Xg_hi, t->Xg_lo, t->ng_t, nullptr,
-                           s));
-    ASK_TRY(g16_split_rows(t->Xs, t->d_pad, d, t->srows, t->g_xbar, t->g_scale, t->Sg_hi, t->Sg_lo, t->ng_s, nullptr,
-                           s));
+    ASK_TRY(t->arena.alloc(&t->Xb_hi, et));
+    ASK_TRY(t->arena.alloc(&t->Xb_lo, et));
+    ASK_TRY(t->arena.alloc(&t->Sb_hi, es));
+    ASK_TRY(t->arena.alloc(&t->Sb_lo, es));
+    gsplit_sources_kernel<<<(unsigned)((t->N_pad + 7) / 8), 256, 0, s>>>(t->Xt, t->d_pad, d, t->N_pad, t->g_xbar,
+                                                                        t->sc_t, 1.f / sigma, t->Xb_hi, t->Xb_lo,
+                                                                        t->ng_t);
+    gsplit_sources_kernel<<<(unsigned)((t->srows + 7) / 8), 256, 0, s>>>(t->Xs, t->d_pad, d, t->srows, t->g_xbar,
+                                                                        t->sc_s, 1.f / sigma, t->Sb_hi, t->Sb_lo,
+                                                                        t->ng_s);
     max_kernel<<<(unsigned)((t->N + 255) / 256), 256, 0, s>>>(t->ng_t, t->N, red + 1);
-    max_kernel<<<(unsigned)((t->N + 255) / 256), 256, 0, s>>>(t->sc_t, t->N, red + 2);
     ASK_LAUNCH();
     ASK_CUDA(cudaMemcpyAsync(hred, red, 3 * sizeof(float), cudaMemcpyDeviceToHost, s));
     ASK_CUDA(cudaStreamSynchronize(s));
     cudaFreeAsync(red, s);
-    t->g_rho = (double)hred[1] * (double)hred[2];
+    const double r2max = hred[1];
+    t->g_tau = pow2_near(r2max > 0.0 ? sqrt(sc_max / r2max) : 1.0);
+    t->g_kappa = pow2_near(sqrt(sc_max * r2max));
+    t->g_rho = sc_max * r2max;
     t->g_ok = t->g_rho <= RHO_MAX;
+    // the tree points as targets, and the sources' norm blocks
+    ASK_TRY(t->arena.alloc(&t->Xg_hi, et));
+    ASK_TRY(t->arena.alloc(&t->Xg_lo, et));
+    ASK_TRY(t->arena.alloc(&t->Xg_x, (size_t)t->N_pad * GX_K));
+    ASK_TRY(t->arena.alloc(&t->g_bx, (size_t)std::max<int64_t>(1, t->n_sub) * G_ROWS * GX_K));
+    ASK_TRY(g16_split_rows(t->Xt, t->d_pad, d, t->N_pad, t, t->Xg_hi, t->Xg_lo, t->Xg_x, nullptr, s));
+    if (t->n_sub > 0)
+        gsplit_bx_kernel<<<(unsigned)t->n_sub, 128, 0, s>>>(t->sb_row0, t->sb_nr, t->n_leaf_sub, t->sc_t, t->sc_s,
+                                                            t->ng_t, t->ng_s, 1.f / t->g_tau, 1.f / t->g_kappa,
+                                                            t->g_bx);
+    ASK_LAUNCH();
+    ASK_CUDA(cudaStreamSynchronize(s));
     return ASKIT_OK;
 }
