@@ -178,6 +178,27 @@ askit_status askit_knn_targets(askit_tree t, const float *Y_dev, int64_t T, int6
                                double *dist_dev, void *stream);
 
 /*
+ * Exact kNN of some of the tree's own points (Section 4 measures the hit rate
+ * hr of approximate neighbor lists against an exhaustive search): for each id
+ * in ids_dev [Q] (caller order, 0 .. N-1), the tree's kappa nearest other
+ * points by (squared distance, id) in canonical FP64 from the FP32
+ * coordinates, self excluded -- the lists of the setup's exact kNN
+ * (knn_mode 0) for those points.  nbr_dev [Q, kappa] int32, dist_dev
+ * [Q, kappa] double.  INVALID_ARG for an id out of range.  Blocks until done.
+ */
+askit_status askit_knn_points(askit_tree t, const int32_t *ids_dev, int64_t Q, int32_t *nbr_dev,
+                              double *dist_dev, void *stream);
+
+/*
+ * Evaluate with one part of Algorithm 4 only: part 1 the near field (the
+ * direct sums over the leaves of Near(i)), part 2 the far field (the
+ * skeleton sums over Far(i)), part 0 both (askit_evaluate).  The near field
+ * alone gives the error eps_kappa the paper reports beside eps (Table 4).
+ * U_dev [N, r] as askit_evaluate; uses the tree's default weights.
+ */
+askit_status askit_evaluate_part(askit_tree t, int32_t part, float *U_dev, int64_t ldu, void *stream);
+
+/*
  * Direct sum of eq. (1.1) at selected points, without approximation: for
  * each target id, the sum over all N points of K(x_i, x_j) w_j with the
  * tree's points, bandwidths and current weights (plain FP32, difference
@@ -290,6 +311,24 @@ askit_status askit_kernel_timing(askit_tree t, int32_t enable, double *ms, int64
  *           (work lists estimated from the in-sample entries per target, x2).
  */
 askit_status askit_footprint(askit_tree t, int32_t kind, int64_t n, int32_t r, size_t *bytes);
+
+/*
+ * Refinements of the pruning that Section 3 proposes against the error's
+ * growth with the node size (after eq. (3.5)); both rebuild the tree's
+ * in-sample work lists:
+ *   far_height >= 0: level restriction -- skeletons are used only for nodes
+ *     at most far_height levels above the leaves; a higher node that eq. (2.5)
+ *     prunes is replaced by its descendants at that height (-1: off).
+ *   kappa_cut > 0: adaptive kappa_i -- the prune set of point i keeps its
+ *     neighbors up to the last rank z whose kernel value exceeds e^-kappa_cut,
+ *     kappa_i = 1 + max{z : c D(i, N_i[z]) / h^2 < kappa_cut} (0 if none),
+ *     decided in FP64; out-of-sample targets likewise (0: all kappa).
+ * Blocks until the lists are rebuilt (waits for the device first).  The
+ * weights of the tree and of every weight context must be set again before
+ * they are evaluated (NOT_READY otherwise when the lists grew), and graphs
+ * captured before must be destroyed.
+ */
+askit_status askit_set_pruning(askit_tree t, int32_t far_height, double kappa_cut, void *stream);
 
 /* Precision of subsequent askit_evaluate calls (ASKIT_PREC_*). */
 askit_status askit_set_precision(askit_tree t, int32_t precision);

@@ -80,6 +80,9 @@ def _declare(L):
     L.orc_build.restype = P
     L.orc_set_weights.argtypes = [P, P, i32]
     L.orc_evaluate.argtypes = [P, P, i64, P, P, P]
+    L.orc_evaluate_part.argtypes = [P, P, i64, i32, P, P, P]
+    L.orc_evaluate_ext.argtypes = [P, P, i64, i32, i32, C.c_double, P, P, P]
+    L.orc_evaluate_oos_ext.argtypes = [P, P, i64, i32, C.c_double, P, P, P, P]
     L.orc_evaluate_oos.argtypes = [P, P, i64, P, P, P, P]
     L.orc_info.argtypes = [P, P]
     L.orc_get_perm.argtypes = [P, P]
@@ -89,6 +92,7 @@ def _declare(L):
     L.orc_get_node.argtypes = [P, i64, P, P, P, P, P, P, P, P]
     L.orc_free.argtypes = [P]
     L.orc_num_threads.restype = i32
+    L.orc_set_threads.argtypes = [i32]
 
 
 def _p(a):
@@ -105,6 +109,11 @@ def _f64(a):
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops (results do not depend on it)."""
+    lib().orc_set_threads(int(n))
 
 
 def philox4x64_10(ctr, key):
@@ -161,6 +170,14 @@ def knn_rp(X, kappa, iters, rp_leaf, seed):
     dd = np.zeros((N, kappa), np.float64)
     lib().orc_knn_rp(_p(X), N, d, kappa, iters, rp_leaf, seed, _p(ids), _p(dd))
     return ids, dd
+
+
+def hit_rate(ids, ids_exact):
+    """hr of Section 4: the mean fraction of the exact kappa nearest
+    neighbors found in each approximate list (rows compared as sets)."""
+    ids, ids_exact = np.asarray(ids), np.asarray(ids_exact)
+    hits = [len(set(a.tolist()) & set(b.tolist())) for a, b in zip(ids, ids_exact)]
+    return float(np.mean(hits)) / ids.shape[1]
 
 
 def tree_depth(N, leaf):
@@ -286,6 +303,35 @@ class Tree:
         far = np.zeros(T, np.int64)
         lib().orc_evaluate(self._t, _p(tg), T, _p(U), _p(near), _p(far))
         return (U, near, far) if counts else U
+
+    def evaluate_part(self, part, targets=None):
+        """Algorithm 4 with only the near field ("near": direct leaf sums) or
+        only the far field ("far": skeleton sums); near + far = evaluate()."""
+        tg = np.arange(self.N, dtype=np.int64) if targets is None else np.ascontiguousarray(targets, np.int64)
+        U = np.zeros((tg.shape[0], self.r), np.float64)
+        lib().orc_evaluate_part(self._t, _p(tg), tg.shape[0], {"near": 1, "far": 2}[part], _p(U), None, None)
+        return U
+
+    def evaluate_ext(self, far_height=-1, kappa_cut=0.0, targets=None, counts=False, part="all"):
+        """Algorithm 4 with the paper's proposed refinements (Section 3):
+        far_height >= 0 uses skeletons only for nodes at most that many
+        levels above the leaves; kappa_cut > 0 keeps in each prune set the
+        neighbors up to the last one whose kernel value exceeds e^-kappa_cut."""
+        tg = np.arange(self.N, dtype=np.int64) if targets is None else np.ascontiguousarray(targets, np.int64)
+        T = tg.shape[0]
+        U = np.zeros((T, self.r), np.float64)
+        near = np.zeros(T, np.int64)
+        far = np.zeros(T, np.int64)
+        lib().orc_evaluate_ext(self._t, _p(tg), T, {"near": 1, "far": 2, "all": 3}[part], int(far_height),
+                               float(kappa_cut), _p(U), _p(near), _p(far))
+        return (U, near, far) if counts else U
+
+    def evaluate_oos_ext(self, Y, far_height=-1, kappa_cut=0.0):
+        Y = _f32(Y)
+        T = Y.shape[0]
+        U = np.zeros((T, self.r), np.float64)
+        lib().orc_evaluate_oos_ext(self._t, _p(Y), T, int(far_height), float(kappa_cut), _p(U), None, None, None)
+        return U
 
     def evaluate_oos(self, Y, counts=False):
         Y = _f32(Y)

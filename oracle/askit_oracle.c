@@ -713,8 +713,17 @@ void orc_set_weights(orc_tree *t, const double *W, int r)
 /* `pset` is the prune set as leaf indices (np entries).                  */
 /* near/far count the leaves evaluated directly and the skeletons used.   */
 /* ------------------------------------------------------------------------ */
+/* `part` selects which terms enter u: 1 the near field (direct leaf sums), */
+/* 2 the far field (skeleton sums), 3 both (Algorithm 4 itself).  The paper */
+/* reports eps_kappa, the error of the near field alone (Table 4).           */
+/* `far_height` (>= 0) restricts the far field to nodes at most that many  */
+/* levels above the leaves (Section 3: "restrict the level(alpha) by       */
+/* starting the evaluation phase at a level which is a fixed distance from */
+/* the leaves"): a higher node that would be pruned is descended instead,  */
+/* down to that height.  -1: no restriction (Algorithm 4 as printed).      */
 static void evaluate_rec(const orc_tree *t, const float *x, const int64_t *pset, int np,
-                         int64_t a, int depth, double *u, int64_t *near, int64_t *far)
+                         int64_t a, int depth, double *u, int64_t *near, int64_t *far, int part,
+                         int far_height)
 {
     int r = t->r, d = t->d;
     int pruned = t->prm.prune;
@@ -722,8 +731,9 @@ static void evaluate_rec(const orc_tree *t, const float *x, const int64_t *pset,
         for (int q = 0; q < np && pruned; ++q)
             if ((pset[q] >> (t->L - depth)) == a) pruned = 0;
     if (depth == 0) pruned = 0;
+    if (far_height >= 0 && t->L - depth > far_height) pruned = 0;
     if (pruned) {
-        for (int64_t q = 0; q < t->sk_s[a]; ++q) {
+        for (int64_t q = 0; q < t->sk_s[a] && (part & 2); ++q) {
             int64_t j = t->skel[a][q];
             double h = (double)t->hsrc[j];
             double k = exp(-(t->prm.kscale * dist2_ff(x, t->X + (size_t)j * d, d)) / (h * h));
@@ -733,7 +743,7 @@ static void evaluate_rec(const orc_tree *t, const float *x, const int64_t *pset,
         return;
     }
     if (depth == t->L) {
-        for (int64_t q = 0; q < t->size[a]; ++q) {
+        for (int64_t q = 0; q < t->size[a] && (part & 1); ++q) {
             int64_t j = t->perm[t->start[a] + q];
             double h = (double)t->hsrc[j];
             double k = exp(-(t->prm.kscale * dist2_ff(x, t->X + (size_t)j * d, d)) / (h * h));
@@ -742,8 +752,29 @@ static void evaluate_rec(const orc_tree *t, const float *x, const int64_t *pset,
         ++*near;
         return;
     }
-    evaluate_rec(t, x, pset, np, 2 * a + 1, depth + 1, u, near, far);
-    evaluate_rec(t, x, pset, np, 2 * a, depth + 1, u, near, far);
+    evaluate_rec(t, x, pset, np, 2 * a + 1, depth + 1, u, near, far, part, far_height);
+    evaluate_rec(t, x, pset, np, 2 * a, depth + 1, u, near, far, part, far_height);
+}
+
+/* Adaptive kappa_i (Section 3: the distance to the (kappa+1)-st neighbor  */
+/* "can be used to derive an adaptive (per point) selection of kappa_i").   */
+/* Reading taken: with a kernel cut a > 0, the prune set keeps the         */
+/* neighbors up to the last rank whose kernel value exceeds e^-a, i.e.     */
+/* kappa_i = 1 + max{ z : c D(i, N_i[z]) / h^2 < a } (0 if none), with h   */
+/* the neighbor's bandwidth and D the stored FP64 squared distance; a <= 0 */
+/* keeps all kappa.  Neighbors past kappa_i may then be approximated in   */
+/* pruned nodes, where their kernel values are small.                      */
+static int kappa_of(const orc_tree *t, const double *dist, const int32_t *ids, double cut)
+{
+    int kappa = t->prm.kappa;
+    if (!(cut > 0.0)) return kappa;
+    int ki = 0;
+    for (int z = 0; z < kappa; ++z) {
+        double h = (double)t->hsrc[ids[z]];
+        double arg = (t->prm.kscale * dist[z]) / (h * h);
+        if (arg < cut) ki = z + 1;
+    }
+    return ki;
 }
 
 /* In-sample targets: rows tgt[0..T) (point ids); U [T,r].  The prune set */
@@ -752,8 +783,8 @@ static void evaluate_rec(const orc_tree *t, const float *x, const int64_t *pset,
 /* every target of a leaf shares one Near and one Far list -- the grouping */
 /* Section 3 points to when it notes that the direct nodes of the targets */
 /* of one leaf overlap heavily.                                           */
-void orc_evaluate(const orc_tree *t, const int64_t *tgt, int64_t T, double *U,
-                  int64_t *near, int64_t *far)
+void orc_evaluate_ext(const orc_tree *t, const int64_t *tgt, int64_t T, int part, int far_height,
+                      double kappa_cut, double *U, int64_t *near, int64_t *far)
 {
     int kappa = t->prm.kappa;
     #pragma omp parallel for schedule(dynamic, 4)
@@ -766,30 +797,44 @@ void orc_evaluate(const orc_tree *t, const int64_t *tgt, int64_t T, double *U,
             pset = (int64_t *)malloc(sizeof(int64_t) * t->size[a] * (kappa + 1));
             for (int64_t v = 0; v < t->size[a]; ++v) {
                 int64_t p = t->perm[t->start[a] + v];
+                int kp = kappa_of(t, t->knnd + (size_t)p * kappa, t->knn + (size_t)p * kappa, kappa_cut);
                 pset[np++] = t->leafof[p];
-                for (int z = 0; z < kappa; ++z) pset[np++] = t->leafof[t->knn[(size_t)p * kappa + z]];
+                for (int z = 0; z < kp; ++z) pset[np++] = t->leafof[t->knn[(size_t)p * kappa + z]];
             }
         } else {
+            int ki = kappa_of(t, t->knnd + (size_t)i * kappa, t->knn + (size_t)i * kappa, kappa_cut);
             pset = (int64_t *)malloc(sizeof(int64_t) * (kappa + 1));
             pset[np++] = t->leafof[i];
-            for (int z = 0; z < kappa; ++z) pset[np++] = t->leafof[t->knn[(size_t)i * kappa + z]];
+            for (int z = 0; z < ki; ++z) pset[np++] = t->leafof[t->knn[(size_t)i * kappa + z]];
         }
         double *u = U + (size_t)q * t->r;
         for (int z = 0; z < t->r; ++z) u[z] = 0.0;
         int64_t nn = 0, nf = 0;
-        evaluate_rec(t, t->X + (size_t)i * t->d, pset, (int)np, 1, 0, u, &nn, &nf);
+        evaluate_rec(t, t->X + (size_t)i * t->d, pset, (int)np, 1, 0, u, &nn, &nf, part, far_height);
         if (near) near[q] = nn;
         if (far) far[q] = nf;
         free(pset);
     }
 }
 
+void orc_evaluate_part(const orc_tree *t, const int64_t *tgt, int64_t T, int part, double *U,
+                       int64_t *near, int64_t *far)
+{
+    orc_evaluate_ext(t, tgt, T, part, -1, 0.0, U, near, far);
+}
+
+void orc_evaluate(const orc_tree *t, const int64_t *tgt, int64_t T, double *U,
+                  int64_t *near, int64_t *far)
+{
+    orc_evaluate_ext(t, tgt, T, 3, -1, 0.0, U, near, far);
+}
+
 /* Out-of-sample targets y (the paper takes sources = targets; reading    */
 /* taken): the prune set of y is its exact kappa nearest sources N_y (no  */
 /* self term); then Algorithm 4 unchanged.  y belongs to no leaf, so the  */
 /* leaf-grouped mode (prune == 2) uses the same per-target set here.      */
-void orc_evaluate_oos(const orc_tree *t, const float *Y, int64_t T, double *U,
-                      int32_t *knn_out, int64_t *near, int64_t *far)
+void orc_evaluate_oos_ext(const orc_tree *t, const float *Y, int64_t T, int far_height, double kappa_cut,
+                          double *U, int32_t *knn_out, int64_t *near, int64_t *far)
 {
     int kappa = t->prm.kappa, d = t->d;
     int32_t *ids = (int32_t *)malloc(sizeof(int32_t) * T * kappa);
@@ -797,18 +842,25 @@ void orc_evaluate_oos(const orc_tree *t, const float *Y, int64_t T, double *U,
     orc_knn_exact(t->X, t->N, d, kappa, Y, NULL, T, ids, dd);
     #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t q = 0; q < T; ++q) {
+        int ky = kappa_of(t, dd + (size_t)q * kappa, ids + (size_t)q * kappa, kappa_cut);
         int64_t *pset = (int64_t *)malloc(sizeof(int64_t) * (kappa + 1));
-        for (int z = 0; z < kappa; ++z) pset[z] = t->leafof[ids[(size_t)q * kappa + z]];
+        for (int z = 0; z < ky; ++z) pset[z] = t->leafof[ids[(size_t)q * kappa + z]];
         double *u = U + (size_t)q * t->r;
         for (int z = 0; z < t->r; ++z) u[z] = 0.0;
         int64_t nn = 0, nf = 0;
-        evaluate_rec(t, Y + (size_t)q * d, pset, kappa, 1, 0, u, &nn, &nf);
+        evaluate_rec(t, Y + (size_t)q * d, pset, ky, 1, 0, u, &nn, &nf, 3, far_height);
         if (near) near[q] = nn;
         if (far) far[q] = nf;
         free(pset);
     }
     if (knn_out) memcpy(knn_out, ids, sizeof(int32_t) * T * kappa);
     free(ids); free(dd);
+}
+
+void orc_evaluate_oos(const orc_tree *t, const float *Y, int64_t T, double *U,
+                      int32_t *knn_out, int64_t *near, int64_t *far)
+{
+    orc_evaluate_oos_ext(t, Y, T, -1, 0.0, U, knn_out, near, far);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -864,6 +916,17 @@ void orc_free(orc_tree *t)
     free(t->ncol); free(t->cols); free(t->sk_s); free(t->piv); free(t->P); free(t->skel);
     free(t->wsk); free(t->W); free(t->knn); free(t->knnd); free(t->hsrc); free(t->perm);
     free(t->leafof); free(t->start); free(t->size); free(t);
+}
+
+/* OpenMP threads of the oracle's parallel loops (independent targets,   */
+/* points or nodes only; results do not depend on it).                     */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }
 
 int orc_num_threads(void)

@@ -32,7 +32,8 @@ EXPORTS = ["askit_default_params", "askit_setup", "askit_set_weights", "askit_ev
            "askit_weights_set", "askit_weights_evaluate", "askit_weights_evaluate_targets",
            "askit_weights_destroy", "askit_footprint", "askit_graph_create", "askit_graph_launch",
            "askit_graph_destroy", "askit_autotune", "askit_set_launch", "askit_knn_targets",
-           "askit_kernel_timing", "askit_set_wait_limit", "askit_set_fp16_centering"]
+           "askit_kernel_timing", "askit_set_wait_limit", "askit_set_fp16_centering", "askit_knn_points",
+           "askit_evaluate_part", "askit_set_pruning"]
 
 
 class TuneEntry(C.Structure):
@@ -99,6 +100,9 @@ def load(path: str | None = None):
             L.askit_set_launch.argtypes = [V, I32, I32, I32, I32]
             L.askit_set_wait_limit.argtypes = [V, I32]
             L.askit_set_fp16_centering.argtypes = [V, I32]
+            L.askit_knn_points.argtypes = [V, V, I64, V, V, V]
+            L.askit_evaluate_part.argtypes = [V, I32, V, I64, V]
+            L.askit_set_pruning.argtypes = [V, I32, D, V]
             L.askit_knn_targets.argtypes = [V, V, I64, I64, V, V, V]
             L.askit_kernel_timing.argtypes = [V, I32, C.POINTER(D), C.POINTER(I64)]
             L.askit_status_string.restype = C.c_char_p
@@ -185,6 +189,7 @@ class Tree:
                                  C.byref(p), _stream(stream), C.byref(out)))
         self._t = out
         self.r = 0
+        self.kappa = cfg.kappa
 
     def close(self):
         if getattr(self, "_t", None):
@@ -257,6 +262,24 @@ class Tree:
                                    out.stride(0), _stream(stream)))
         return out
 
+    def knn_points(self, ids, stream=None):
+        """Exact kappa nearest neighbors of the tree's points `ids` (self
+        excluded): (ids [Q, kappa] int32, squared distances [Q, kappa] FP64)."""
+        q = torch.as_tensor(ids, dtype=torch.int32, device=self.device).contiguous()
+        nb = torch.empty((q.numel(), self.kappa), dtype=torch.int32, device=self.device)
+        dd = torch.empty((q.numel(), self.kappa), dtype=torch.float64, device=self.device)
+        _check(load().askit_knn_points(self._t, C.c_void_p(q.data_ptr()), q.numel(), C.c_void_p(nb.data_ptr()),
+                                       C.c_void_p(dd.data_ptr()), _stream(stream)))
+        return nb, dd
+
+    def evaluate_part(self, part: str, U: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Evaluate with the near field only ("near") or the far field only ("far")."""
+        if U is None:
+            U = torch.empty((self.N, max(self.r, 1)), dtype=torch.float32, device=self.device)
+        _check(load().askit_evaluate_part(self._t, {"all": 0, "near": 1, "far": 2}[part], C.c_void_p(U.data_ptr()),
+                                          U.stride(0), _stream(stream)))
+        return U
+
     def sync(self, stream=None):
         _check(load().askit_sync(self._t, _stream(stream)))
 
@@ -277,6 +300,11 @@ class Tree:
         """Set the evaluation kernel's launch configuration (see autotune)."""
         _check(load().askit_set_launch(self._t, {"lpt": 0, "tree_order": 1}[schedule], stages, int(tiled_runs),
                                        int(pairs)))
+
+    def set_pruning(self, far_height: int = -1, kappa_cut: float = 0.0, stream=None):
+        """Level-restricted far field (far_height >= 0) and adaptive kappa_i
+        (kappa_cut > 0); rebuilds the work lists -- set the weights again."""
+        _check(load().askit_set_pruning(self._t, int(far_height), float(kappa_cut), _stream(stream)))
 
     def set_fp16_centering(self, mode: str = "auto"):
         """FP16x3 target centering: "auto", "block" (per source sub-block, on

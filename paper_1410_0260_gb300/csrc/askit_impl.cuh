@@ -152,6 +152,7 @@ struct WeightCtx {
     float *partial = nullptr;  // [in-sample entries, r_cap]
     float4 *colv = nullptr;    // [n_sub, 128] per-sub-block column data (16-bit tensor-core path)
     float *colw = nullptr;     // [n_sub, 128, 16] per-sub-block weights (r > 1)
+    int64_t ent_cap = 0;       // entries the partial sums hold
     bool ready = false;
     DevArena arena;
 };
@@ -269,6 +270,11 @@ struct askit_tree_s {
     int tune_runs = 1;             // 8-row tiled loads for runs of consecutive targets
     int tune_pairs = 0;            // FP16x3: items over two sub-blocks of a node (256 columns)
     int spin_limit = 0;            // polls of the FP16x3 kernel's bounded waits (0: default)
+    // refinements of the pruning (askit_set_pruning): skeletons only for nodes
+    // at most far_height levels above the leaves (-1: all), and the kernel cut
+    // of the adaptive kappa_i (0: all kappa neighbors)
+    int far_height = -1;
+    double kappa_cut = 0.0;
     int kw = TC_K;                 // row width of the pre-split operands and centers
     // wall time of the setup stages (askit_info.setup_ms)
     double setup_ms[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -386,8 +392,9 @@ int tree_depth(int64_t N, int64_t leaf);
 void tree_ranges(int64_t N, int L, std::vector<int64_t> &start, std::vector<int64_t> &size);
 askit_status build_tree_gpu(const float *X, int64_t N, int d, int L, int kind, uint64_t seed,
                             int iter, int32_t *order, cudaStream_t s);
+// self (optional, [Q]): the point id each query Y row is, excluded from its list
 askit_status knn_exact_gpu(const float *X, int64_t N, int d, int kappa, const float *Y, int64_t Q,
-                           int32_t *ids, double *dist, cudaStream_t s);
+                           int32_t *ids, double *dist, cudaStream_t s, const int32_t *self = nullptr);
 askit_status knn_rp_gpu(const float *X, int64_t N, int d, int kappa, int iters, int64_t rp_leaf,
                         uint64_t seed, int32_t *ids, double *dist, cudaStream_t s);
 askit_status knn_dist_gpu(const float *X, int64_t N, int d, int kappa, const int32_t *ids,
@@ -417,8 +424,10 @@ askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, con
 askit_status reduce_partials(const WorkLists &w, const float *partial, int r, const int32_t *out_rows,
                              float *U, int64_t ldu, cudaStream_t s);
 askit_status insample_prune_sets(askit_tree t, PruneSets &ps, cudaStream_t s);
-askit_status oos_prune_sets(askit_tree t, const int32_t *knn, int64_t T, int stride, int32_t *sets,
-                            cudaStream_t s);
+askit_status oos_prune_sets(askit_tree t, const int32_t *knn, const double *dist, int64_t T, int stride,
+                            int32_t *sets, cudaStream_t s);
+// every array of w back to the arena
+void free_work_lists(WorkLists &w, DevArena &arena);
 
 // weights.cu
 askit_status weights_reserve(askit_tree t, WeightCtx &c, int r, cudaStream_t s);

@@ -69,8 +69,8 @@ __global__ void oos_keys_kernel(const int32_t *knn, int kappa, const int32_t *po
     vals[q] = (int32_t)q;
 }
 
-__global__ void gather_knn_kernel(const int32_t *knn, int kappa, const int32_t *order, int64_t T,
-                                  int32_t *out) {
+template <class V>
+__global__ void gather_knn_kernel(const V *knn, int kappa, const int32_t *order, int64_t T, V *out) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= T * kappa) return;
     int64_t q = e / kappa;
@@ -90,6 +90,19 @@ __global__ void gather_y_kernel(const float *Y, int64_t ldy, int d, int d_pad, c
             for (int k = 0; k < d; ++k) acc += (double)Y[q * ldy + k] * Y[q * ldy + k];
         nrm[row] = (float)acc;
     }
+}
+
+// Rows X[ids[q]] of the caller-order points; an id out of range sets *bad
+// and gives a zero row.
+__global__ void gather_points_kernel(const float *X, int64_t N, int d, const int32_t *ids, int64_t Q, float *Y,
+                                     int32_t *bad) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= Q * d) return;
+    const int64_t q = e / d;
+    const int32_t i = ids[q];
+    const bool ok = i >= 0 && i < N;
+    if (!ok && e % d == 0) *bad = 1;
+    Y[e] = ok ? X[(int64_t)i * d + e % d] : 0.f;
 }
 
 std::mutex g_kt_mu;
@@ -280,13 +293,26 @@ namespace {
 
 // Evaluate over one set of work lists: every (target, sub-block) entry's
 // partial sum, then each target's entries summed in their fixed order.
+// Partial sums of the items of the excluded field set to zero: part 1 keeps
+// the near field (leaf blocks), part 2 the far field (skeleton blocks).
+__global__ void keep_part_kernel(const EvalItem *items, int part, int r, float *partial) {
+    const EvalItem it = items[blockIdx.x];
+    const bool far = it.nrows < 0;
+    if ((part == 1) != far) return;                      // kept
+    for (int e = threadIdx.x; e < it.cnt * r; e += blockDim.x) partial[(int64_t)it.e0 * r + e] = 0.f;
+}
+
 askit_status run_eval(askit_tree t, const WeightCtx &c, int precision, const float *Xq, int64_t ldq,
                       int64_t q_rows, const QuerySplit *qs, const WorkLists &w, float *partial,
-                      const int32_t *out_rows, float *U, int64_t ldu, cudaStream_t s) {
+                      const int32_t *out_rows, float *U, int64_t ldu, cudaStream_t s, int part = 0) {
     if (precision == ASKIT_PREC_SIMT_FP32)
         ASK_TRY(eval_simt(t, c, Xq, ldq, w, partial, s));
     else
         ASK_TRY(eval_tc(t, c, precision, Xq, ldq, q_rows, qs, w, partial, s));
+    if (part != 0 && w.n_items > 0) {
+        keep_part_kernel<<<(unsigned)w.n_items, 128, 0, s>>>(w.items, part, c.r, partial);
+        ASK_LAUNCH();
+    }
     return reduce_partials(w, partial, c.r, out_rows, U, ldu, s);
 }
 
@@ -297,10 +323,15 @@ askit_status set_weights_ctx(askit_tree t, WeightCtx &c, const float *W_dev, int
     return upward_weights(t, c, W_dev, r, ldw, s);
 }
 
-askit_status evaluate_ctx(askit_tree t, const WeightCtx &c, float *U_dev, int64_t ldu, cudaStream_t s) {
+askit_status evaluate_ctx(askit_tree t, const WeightCtx &c, float *U_dev, int64_t ldu, cudaStream_t s,
+                          int part = 0) {
     if (!U_dev) { askit_set_error("U_dev must be non-NULL"); return ASKIT_ERR_INVALID_ARG; }
     if (!c.ready) { askit_set_error("no weights set"); return ASKIT_ERR_NOT_READY; }
     if (ldu < c.r) { askit_set_error("ldu < r"); return ASKIT_ERR_INVALID_ARG; }
+    if (c.ent_cap < t->wl_entries_max) {
+        askit_set_error("the work lists grew (askit_set_pruning): set this context's weights again");
+        return ASKIT_ERR_NOT_READY;
+    }
     // batch b covers target slots [t0, t1): its target rows start at row t0
     // of Xt and its results go to the points perm[t0 .. t1)
     for (size_t b = 0; b < t->wl.size(); ++b) {
@@ -313,7 +344,7 @@ askit_status evaluate_ctx(askit_tree t, const WeightCtx &c, float *U_dev, int64_
             q.rows = t->N_pad - t0;
         }
         ASK_TRY(run_eval(t, c, t->precision, t->Xt + t0 * t->d_pad, t->d_pad, t->N_pad - t0, t->Xg_hi ? &q : nullptr,
-                         t->wl[b], c.partial, t->perm + t0, U_dev, ldu, s));
+                         t->wl[b], c.partial, t->perm + t0, U_dev, ldu, s, part));
     }
     return ASKIT_OK;
 }
@@ -431,7 +462,7 @@ askit_status evaluate_targets_ctx(askit_tree t, const WeightCtx &c, const float 
     tmp.stream = s;
     float *Yc = nullptr, *Yt = nullptr, *nrm = nullptr;
     int32_t *ids = nullptr, *ids_s = nullptr, *order = nullptr, *vals = nullptr, *sets = nullptr;
-    double *dist = nullptr;
+    double *dist = nullptr, *dist_s = nullptr;
     uint64_t *keys = nullptr, *keys_s = nullptr;
     void *cub = nullptr;
     size_t cb = 0;
@@ -456,12 +487,14 @@ askit_status evaluate_targets_ctx(askit_tree t, const WeightCtx &c, const float 
     OTRY(tmp.alloc((char **)&cub, cb));
     OTRY(sort_u64_i32(keys, keys_s, vals, order, T, cub, &cb, s));
     OTRY(tmp.alloc(&ids_s, (size_t)T * kappa));
+    OTRY(tmp.alloc(&dist_s, (size_t)T * kappa));
     gather_knn_kernel<<<nblk(T * kappa, 256), 256, 0, s>>>(ids, kappa, order, T, ids_s);
+    gather_knn_kernel<<<nblk(T * kappa, 256), 256, 0, s>>>(dist, kappa, order, T, dist_s);
     OTRY(tmp.alloc(&Yt, (size_t)T_pad * t->d_pad));
     OTRY(tmp.alloc(&nrm, T_pad));
     gather_y_kernel<<<(unsigned)T_pad, 128, 0, s>>>(Yc, d, d, t->d_pad, order, T, T_pad, Yt, nrm);
     OTRY(tmp.alloc(&sets, (size_t)T * kappa));
-    OTRY(oos_prune_sets(t, ids_s, T, kappa, sets, s));
+    OTRY(oos_prune_sets(t, ids_s, dist_s, T, kappa, sets, s));
     OTRY(build_work_lists(t, sets, kappa, nullptr, T, w, tmp, s));
     OTRY(tmp.alloc(&partial, (size_t)w.n_entries * c.r));
     if (t->precision == ASKIT_PREC_FP16X3 && t->d <= TC_K && use_g16(t)) {
@@ -707,6 +740,47 @@ askit_status askit_knn_targets(askit_tree t, const float *Y_dev, int64_t T, int6
     return rc;
 }
 
+askit_status askit_knn_points(askit_tree t, const int32_t *ids_dev, int64_t Q, int32_t *nbr_dev, double *dist_dev,
+                              void *stream) {
+    if (!t || !ids_dev || !nbr_dev || !dist_dev || Q < 1) {
+        askit_set_error("need a tree, Q >= 1 and the three buffers");
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int d = t->d;
+    float *Y = nullptr;
+    int32_t *bad = nullptr;
+    ASK_CUDA(cudaMallocAsync(&Y, sizeof(float) * (size_t)Q * d, s));
+    askit_status rc = ASKIT_OK;
+    if (cudaMallocAsync(&bad, sizeof(int32_t), s) != cudaSuccess || cudaMemsetAsync(bad, 0, sizeof(int32_t), s) != cudaSuccess) {
+        askit_set_error("allocation");
+        rc = ASKIT_ERR_OOM;
+    }
+    if (rc == ASKIT_OK) {
+        gather_points_kernel<<<nblk(Q * d, 256), 256, 0, s>>>(t->X, t->N, d, ids_dev, Q, Y, bad);
+        int hbad = 0;
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            askit_set_error("gather points");
+            rc = ASKIT_ERR_CUDA;
+        } else if (hbad) {
+            askit_set_error("a point id is outside 0 .. N-1");
+            rc = ASKIT_ERR_INVALID_ARG;
+        }
+    }
+    if (rc == ASKIT_OK) rc = knn_exact_gpu(t->X, t->N, d, t->kappa, Y, Q, nbr_dev, dist_dev, s, ids_dev);
+    cudaFreeAsync(Y, s);
+    if (bad) cudaFreeAsync(bad, s);
+    cudaStreamSynchronize(s);
+    return rc;
+}
+
+askit_status askit_evaluate_part(askit_tree t, int32_t part, float *U_dev, int64_t ldu, void *stream) {
+    if (!t || part < 0 || part > 2) { askit_set_error("need a tree and part 0, 1 or 2"); return ASKIT_ERR_INVALID_ARG; }
+    return evaluate_ctx(t, t->dw, U_dev, ldu, (cudaStream_t)stream, part);
+}
+
 askit_status askit_set_launch(askit_tree t, int32_t schedule, int32_t stages, int32_t tiled_runs, int32_t pairs) {
     if (!t || schedule < 0 || schedule > 1 || stages < 2 || stages > 4 || tiled_runs < 0 || tiled_runs > 1 ||
         pairs < 0 || pairs > 1) {
@@ -718,6 +792,27 @@ askit_status askit_set_launch(askit_tree t, int32_t schedule, int32_t stages, in
     t->tune_runs = tiled_runs;
     t->tune_pairs = pairs;
     use_schedule(t);
+    return ASKIT_OK;
+}
+
+askit_status askit_set_pruning(askit_tree t, int32_t far_height, double kappa_cut, void *stream) {
+    if (!t || far_height < -1 || !(kappa_cut >= 0.0) || kappa_cut > 1e300) {
+        askit_set_error("need a tree, far_height >= -1 and a finite kappa_cut >= 0");
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    ASK_CUDA(cudaStreamSynchronize(s));
+    ASK_CUDA(cudaDeviceSynchronize());       // no evaluation may still read the old lists
+    for (WorkLists &w : t->wl) free_work_lists(w, t->arena);
+    t->far_height = far_height;
+    t->kappa_cut = kappa_cut;
+    PruneSets ps;
+    askit_status rc = insample_prune_sets(t, ps, s);
+    if (rc == ASKIT_OK) rc = build_insample_lists(t, ps, s);
+    free_prune_sets(ps);
+    ASK_TRY(rc);
+    use_schedule(t);
+    ASK_CUDA(cudaStreamSynchronize(s));
     return ASKIT_OK;
 }
 

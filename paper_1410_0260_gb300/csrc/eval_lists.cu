@@ -59,16 +59,36 @@ __global__ void spool_ids_kernel(int64_t n_nodes, const int64_t *spool, const in
     }
 }
 
+// Adaptive kappa_i (the per-point selection Section 3 proposes from the
+// distance to the neighbors): with a kernel cut a > 0, the neighbors kept in
+// the prune set run up to the last rank whose kernel value exceeds e^-a,
+// kappa_i = 1 + max{ z : c D_z / h_z^2 < a } (0 if none), h_z the
+// neighbor's bandwidth, decided in canonical FP64 like the oracle; a <= 0
+// keeps all kappa.
+__device__ __forceinline__ int kappa_of(const double *dist, const int32_t *ids, int kappa, const float *hsrc,
+                                        double kscale, double cut) {
+    if (!(cut > 0.0)) return kappa;
+    int ki = 0;
+    for (int z = 0; z < kappa; ++z) {
+        const double h = (double)hsrc[ids[z]];
+        if (c_div(c_mul(kscale, dist[z]), c_mul(h, h)) < cut) ki = z + 1;
+    }
+    return ki;
+}
+
 // Prune set of each in-sample target (tree position q): the sorted distinct
-// leaves of {i} U N_i, padded with INT_MAX to kappa + 1 entries.
+// leaves of {i} U N_i (the first kappa_i neighbors), padded with INT_MAX to
+// kappa + 1 entries.
 __global__ void insample_sets_kernel(const int32_t *perm, const int32_t *leafof, const int32_t *knn,
+                                     const double *knnd, const float *hsrc, double kscale, double cut,
                                      int64_t N, int kappa, int32_t *sets) {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= N) return;
     int32_t i = perm[q];
     int32_t *o = sets + q * (kappa + 1);
     int n = 0;
-    for (int z = -1; z < kappa; ++z) {
+    const int ki = kappa_of(knnd + (int64_t)i * kappa, knn + (int64_t)i * kappa, kappa, hsrc, kscale, cut);
+    for (int z = -1; z < ki; ++z) {
         int32_t lf = leafof[z < 0 ? i : knn[(int64_t)i * kappa + z]];
         int p = n;
         bool dup = false;
@@ -92,14 +112,16 @@ __global__ void all_leaves_sets_kernel(int64_t N, int L, int32_t *sets) {
 // Leaf-grouped prune sets, step 1: for the point at tree position q, its
 // own leaf and its neighbors' leaves, at q (kappa + 1) .. (q + 1)(kappa + 1);
 // a leaf's points are consecutive positions, so each leaf owns one segment.
-__global__ void leaf_keys_kernel(const int32_t *perm, const int32_t *leafof, const int32_t *knn, int64_t N,
-                                 int kappa, int32_t *keys) {
+__global__ void leaf_keys_kernel(const int32_t *perm, const int32_t *leafof, const int32_t *knn, const double *knnd,
+                                 const float *hsrc, double kscale, double cut, int64_t N, int kappa, int32_t *keys) {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= N) return;
     const int32_t i = perm[q];
     int32_t *o = keys + q * (kappa + 1);
     o[0] = leafof[i];
-    for (int z = 0; z < kappa; ++z) o[z + 1] = leafof[knn[(int64_t)i * kappa + z]];
+    // neighbors past kappa_i repeat the own leaf (removed with the duplicates)
+    const int ki = kappa_of(knnd + (int64_t)i * kappa, knn + (int64_t)i * kappa, kappa, hsrc, kscale, cut);
+    for (int z = 0; z < kappa; ++z) o[z + 1] = z < ki ? leafof[knn[(int64_t)i * kappa + z]] : o[0];
 }
 
 // Step 2 (a warp per leaf, its segment sorted): count the distinct leaves
@@ -132,14 +154,16 @@ __global__ void leaf_row_kernel(const int32_t *perm, const int32_t *leafof, int6
     row[q] = leafof[perm[q]] - M;
 }
 
-// Out-of-sample prune sets: distinct leaves of N_y (no self term).
-__global__ void oos_sets_kernel(const int32_t *leafof, const int32_t *knn, int64_t T, int kappa,
-                                int stride, int32_t *sets) {
+// Out-of-sample prune sets: distinct leaves of N_y (its first kappa_y
+// neighbors; no self term).
+__global__ void oos_sets_kernel(const int32_t *leafof, const int32_t *knn, const double *dist, const float *hsrc,
+                                double kscale, double cut, int64_t T, int kappa, int stride, int32_t *sets) {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= T) return;
     int32_t *o = sets + q * stride;
     int n = 0;
-    for (int z = 0; z < kappa; ++z) {
+    const int ky = kappa_of(dist + q * kappa, knn + q * kappa, kappa, hsrc, kscale, cut);
+    for (int z = 0; z < ky; ++z) {
         int32_t lf = leafof[knn[q * kappa + z]];
         int p = n;
         bool dup = false;
@@ -155,9 +179,12 @@ __global__ void oos_sets_kernel(const int32_t *leafof, const int32_t *knn, int64
 // Near and Far sets of one target from its sorted prune leaves.  Near =
 // the leaves; Far = for each depth, the sibling of every distinct ancestor
 // at that depth when the sibling is not itself an ancestor of a near leaf.
-// emit(node, far) is called once per node of Near(i) and Far(i).
+// With a height limit fh >= 0 (skeletons only for nodes at most fh levels
+// above the leaves, Section 3's level restriction), a higher Far node is
+// replaced by its descendants fh levels above the leaves (none holds a near
+// leaf).  emit(node, far) is called once per node of Near(i) and Far(i).
 template <class F>
-__device__ __forceinline__ void walk_lists(const int32_t *set, int stride, int L, F emit) {
+__device__ __forceinline__ void walk_lists(const int32_t *set, int stride, int L, int fh, F emit) {
     int n = 0;
     while (n < stride && set[n] != INT_MAX) ++n;
     for (int u = 0; u < n; ++u) emit(set[u], false);
@@ -176,7 +203,13 @@ __device__ __forceinline__ void walk_lists(const int32_t *set, int stride, int L
                 if (set[mid] < lo) a = mid + 1; else z = mid;
             }
             const bool inU = a < n && (set[a] >> sh) == sib;
-            if (!inU) emit(sib, true);
+            if (inU) continue;
+            if (fh >= 0 && sh > fh) {
+                const int down = sh - fh;
+                for (int32_t k = 0; k < ((int32_t)1 << down); ++k) emit((sib << down) + k, true);
+            } else {
+                emit(sib, true);
+            }
         }
     }
 }
@@ -197,13 +230,13 @@ __device__ __forceinline__ const int32_t *set_of(const int32_t *sets, int stride
     return sets + (set_row ? (int64_t)set_row[q] : q) * stride;
 }
 
-__global__ void count_kernel(const int32_t *sets, int stride, const int32_t *set_row, int64_t T, int L,
+__global__ void count_kernel(const int32_t *sets, int stride, const int32_t *set_row, int64_t T, int L, int fh,
                              const int32_t *nsize, const int32_t *s, int64_t *cnt, int64_t *nearc, int64_t *farc,
                              int64_t *pairs) {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= T) return;
     int64_t c = 0, nf = 0, nn = 0, pr = 0;
-    walk_lists(set_of(sets, stride, set_row, q), stride, L, [&](int32_t node, bool far) {
+    walk_lists(set_of(sets, stride, set_row, q), stride, L, fh, [&](int32_t node, bool far) {
         int rows = block_rows(node, far, nsize, s);
         c += (rows + ASK_BLK_N - 1) / ASK_BLK_N;
         pr += rows;
@@ -215,13 +248,13 @@ __global__ void count_kernel(const int32_t *sets, int stride, const int32_t *set
     pairs[q] = pr;
 }
 
-__global__ void emit_kernel(const int32_t *sets, int stride, const int32_t *set_row, int64_t T, int L,
+__global__ void emit_kernel(const int32_t *sets, int stride, const int32_t *set_row, int64_t T, int L, int fh,
                             const int32_t *nsize, const int32_t *s, const int64_t *off, uint64_t *keys,
                             int64_t *vals) {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= T) return;
     int64_t o = off[q];
-    walk_lists(set_of(sets, stride, set_row, q), stride, L, [&](int32_t node, bool far) {
+    walk_lists(set_of(sets, stride, set_row, q), stride, L, fh, [&](int32_t node, bool far) {
         int rows = block_rows(node, far, nsize, s);
         for (int ch = 0; ch * ASK_BLK_N < rows; ++ch) {
             keys[o] = ((uint64_t)sub_key(node, ch, far) << 32) | (uint64_t)q;
@@ -542,7 +575,8 @@ askit_status leaf_prune_sets(askit_tree t, PruneSets &ps, cudaStream_t s) {
     PCHK(cudaMalloc(&beg, sizeof(int32_t) * 2 * M));
     PCHK(cudaMalloc(&cnt, sizeof(int32_t) * M));
     PCHK(cudaMemcpyAsync(beg, hb.data(), sizeof(int32_t) * 2 * M, cudaMemcpyHostToDevice, s));
-    leaf_keys_kernel<<<nblk(N, 128), 128, 0, s>>>(t->perm, t->leafof, t->knn, N, t->kappa, keys);
+    leaf_keys_kernel<<<nblk(N, 128), 128, 0, s>>>(t->perm, t->leafof, t->knn, t->knnd, t->hsrc, t->prm.kernel_scale,
+                                                  t->kappa_cut, N, t->kappa, keys);
     PCHK(cudaGetLastError());
     PTRY(seg_sort_i32(nullptr, nullptr, N * k1, (int)M, beg, beg + M, nullptr, &tb, s));
     PCHK(cudaMalloc(&tmp, tb));
@@ -580,14 +614,16 @@ askit_status insample_prune_sets(askit_tree t, PruneSets &ps, cudaStream_t s) {
         ASK_LAUNCH();
         return ASKIT_OK;
     }
-    insample_sets_kernel<<<nblk(t->N, 128), 128, 0, s>>>(t->perm, t->leafof, t->knn, t->N, t->kappa, ps.sets);
+    insample_sets_kernel<<<nblk(t->N, 128), 128, 0, s>>>(t->perm, t->leafof, t->knn, t->knnd, t->hsrc,
+                                                         t->prm.kernel_scale, t->kappa_cut, t->N, t->kappa, ps.sets);
     ASK_LAUNCH();
     return ASKIT_OK;
 }
 
-askit_status oos_prune_sets(askit_tree t, const int32_t *knn, int64_t T, int stride, int32_t *sets,
-                            cudaStream_t s) {
-    oos_sets_kernel<<<nblk(T, 128), 128, 0, s>>>(t->leafof, knn, T, t->kappa, stride, sets);
+askit_status oos_prune_sets(askit_tree t, const int32_t *knn, const double *dist, int64_t T, int stride,
+                            int32_t *sets, cudaStream_t s) {
+    oos_sets_kernel<<<nblk(T, 128), 128, 0, s>>>(t->leafof, knn, dist, t->hsrc, t->prm.kernel_scale, t->kappa_cut, T,
+                                                 t->kappa, stride, sets);
     ASK_LAUNCH();
     return ASKIT_OK;
 }
@@ -620,7 +656,8 @@ askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, con
     WCHK(cudaMallocAsync(&pairs, sizeof(int64_t) * T, s));
     WTRY(arena.alloc(&w.off, T + 1));
     WCHK(cudaMemsetAsync(cnt + T, 0, sizeof(int64_t), s));
-    count_kernel<<<nblk(T, 128), 128, 0, s>>>(sets, stride, set_row, T, t->L, t->nsize, t->d_s, cnt, nearc, farc,
+    count_kernel<<<nblk(T, 128), 128, 0, s>>>(sets, stride, set_row, T, t->L, t->far_height, t->nsize, t->d_s, cnt,
+                                              nearc, farc,
                                               pairs);
     WCHK(cudaGetLastError());
     WTRY(scan_i64(nullptr, nullptr, T + 1, nullptr, &tb, s));
@@ -638,7 +675,8 @@ askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, con
     WCHK(cudaMallocAsync(&keys_s, sizeof(uint64_t) * total, s));
     WCHK(cudaMallocAsync(&vals, sizeof(int64_t) * total, s));
     WCHK(cudaMallocAsync(&emit_of, sizeof(int64_t) * total, s));
-    emit_kernel<<<nblk(T, 128), 128, 0, s>>>(sets, stride, set_row, T, t->L, t->nsize, t->d_s, w.off, keys, vals);
+    emit_kernel<<<nblk(T, 128), 128, 0, s>>>(sets, stride, set_row, T, t->L, t->far_height, t->nsize, t->d_s, w.off,
+                                             keys, vals);
     WCHK(cudaGetLastError());
     WTRY(sort_u64_i64(nullptr, nullptr, nullptr, nullptr, total, nullptr, &tb, s));
     WTRY(scan_i64(nullptr, nullptr, total, nullptr, &tb2, s));
@@ -866,8 +904,8 @@ askit_status build_insample_lists(askit_tree t, const PruneSets &ps, cudaStream_
     {
         int64_t *buf = nullptr;
         ASK_CUDA(cudaMallocAsync(&buf, sizeof(int64_t) * 4 * N, s));
-        count_kernel<<<nblk(N, 128), 128, 0, s>>>(sets, stride, set_row, N, t->L, t->nsize, t->d_s, buf, buf + N,
-                                                  buf + 2 * N, buf + 3 * N);
+        count_kernel<<<nblk(N, 128), 128, 0, s>>>(sets, stride, set_row, N, t->L, t->far_height, t->nsize, t->d_s, buf,
+                                                  buf + N, buf + 2 * N, buf + 3 * N);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt.data(), buf, sizeof(int64_t) * N, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -903,6 +941,15 @@ askit_status build_insample_lists(askit_tree t, const PruneSets &ps, cudaStream_
         t->wl_entries_max = std::max(t->wl_entries_max, t->wl[b].n_entries);
     }
     return ASKIT_OK;
+}
+
+void free_work_lists(WorkLists &w, DevArena &arena) {
+    void *ptrs[] = {w.off, w.slot_of_emit, w.tgt, w.items, w.block_off, w.block_order, w.sched_off[0],
+                    w.sched_off[1], w.sched_off[2], w.sched_blocks[0], w.sched_blocks[1], w.sched_blocks[2],
+                    w.partner};
+    for (void *p : ptrs)
+        if (p) arena.release(p);
+    w = WorkLists();
 }
 
 // The CTA schedule the kernels use: LPT or tree order (askit_set_launch);

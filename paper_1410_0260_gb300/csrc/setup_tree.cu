@@ -261,7 +261,7 @@ constexpr int KT_Q = 64, KT_C = 128, KT_K = 32;
 
 __global__ void __launch_bounds__(256) knn_tiled_kernel(const float *X, int64_t N, int d, const float *Y,
                                                          int64_t Q, int64_t split_len, int kappa, double *bd,
-                                                         int *bi) {
+                                                         int *bi, const int32_t *self) {
     // the distance tile reuses the chunk buffers (the selection ends before
     // the next tile's first chunk is loaded)
     __shared__ float sbuf[KT_Q * (KT_C + 1)];
@@ -331,7 +331,9 @@ __global__ void __launch_bounds__(256) knn_tiled_kernel(const float *X, int64_t 
             const float *xq = Y ? Y + q * d : X + q * d;
             for (int rr = 0; rr < KT_C / 32; ++rr) {
                 const int64_t j = cb + rr * 32 + lane;
-                const bool valid = j < c1 && (Y || j != q);
+                // queries Y exclude no point unless `self` names the point each
+                // query is (the tree's own points as queries)
+                const bool valid = j < c1 && (self ? j != self[q] : (Y || j != q));
                 const float d32 = dt[qq][rr * 32 + lane];
                 const double kth = __shfl_sync(FULL, ld[u], kappa - 1);
                 const bool need = valid && (double)d32 * (1.0 - (double)gam) <= kth;
@@ -534,7 +536,7 @@ askit_status knn_lists_init(int64_t Q, double **bd, int **bi, cudaStream_t s) {
 // against all N points.  Query tiles of 64 x candidate splits, chosen so that
 // about four blocks per SM have work; the splits' lists are merged.
 askit_status knn_exact_gpu(const float *X, int64_t N, int d, int kappa, const float *Y, int64_t Q,
-                           int32_t *ids, double *dist, cudaStream_t s) {
+                           int32_t *ids, double *dist, cudaStream_t s, const int32_t *self) {
     const int64_t nqb = (Q + KT_Q - 1) / KT_Q;
     int64_t nsplit = (4 * 152 + nqb - 1) / nqb;
     nsplit = std::max<int64_t>(1, std::min<int64_t>(nsplit, N / (4 * KT_C)));
@@ -547,7 +549,8 @@ askit_status knn_exact_gpu(const float *X, int64_t N, int d, int kappa, const fl
     cudaError_t e = cudaMallocAsync(&bd, sizeof(double) * nsplit * Q * 32, s);
     if (e == cudaSuccess) e = cudaMallocAsync(&bi, sizeof(int) * nsplit * Q * 32, s);
     if (e == cudaSuccess) {
-        knn_tiled_kernel<<<dim3((unsigned)nqb, (unsigned)nsplit), 256, 0, s>>>(X, N, d, Y, Q, split_len, kappa, bd, bi);
+        knn_tiled_kernel<<<dim3((unsigned)nqb, (unsigned)nsplit), 256, 0, s>>>(X, N, d, Y, Q, split_len, kappa, bd, bi,
+                                                                               self);
         knn_merge_kernel<<<nblk(Q * 32, 256), 256, 0, s>>>(bd, bi, Q, (int)nsplit, kappa, ids, dist);
         e = cudaGetLastError();
     }

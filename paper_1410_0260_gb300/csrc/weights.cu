@@ -18,11 +18,14 @@ __global__ void permute_in_kernel(const float *W, int64_t ldw, int r, const int3
     Wt[e] = W[(int64_t)perm[q] * ldw + z];
 }
 
-// One block per node of the level.  The rows v(R) the node's P multiplies
-// (gathered through its pivot order) are staged in shared memory once, in
-// chunks of UP_KU rows and RC columns; warps then take rows q of w~_a, lanes
-// split the columns u of P and reduce with shuffles.
+// Block (a, y) takes rows [32 y, 32 y + 32) of node a's w~_a (the levels
+// near the root have few nodes, so a node's rows are spread over blocks).
+// The rows v(R) the node's P multiplies (gathered through its pivot order)
+// are staged in shared memory, in chunks of UP_KU rows and RC columns; warps
+// then take rows q of w~_a, lanes split the columns u of P and reduce with
+// shuffles (the same order for every split of the rows).
 constexpr int UP_KU = 1024;
+constexpr int UP_ROWS = 32;
 
 template <int RC>
 __host__ __device__ constexpr int up_stride() { return RC == 1 ? 1 : RC + 4; }   // padded: conflict-free float4 reads
@@ -35,7 +38,8 @@ __global__ void upward_kernel(int64_t a0, bool leaf_level, int r, const int32_t 
     constexpr int STR = up_stride<RC>();
     const int64_t a = a0 + blockIdx.x;
     const int sa = s[a], c = ncol[a], nr = c - sa;
-    if (sa == 0) return;
+    const int q0 = UP_ROWS * blockIdx.y, q1 = min(sa, q0 + UP_ROWS);
+    if (q0 >= sa) return;                                 // block-uniform
     const int32_t *pv = piv + pivoff[a];
     const float *P = P32 + poff[a];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -55,7 +59,7 @@ __global__ void upward_kernel(int64_t a0, bool leaf_level, int r, const int32_t 
                 vs[uu * STR + z] = (z0 + z < r) ? vrow(pv[sa + u0 + uu])[z0 + z] : 0.f;
             }
             __syncthreads();
-            for (int q = warp; q < sa; q += nw) {
+            for (int q = q0 + warp; q < q1; q += nw) {
                 float acc[RC];
 #pragma unroll
                 for (int z = 0; z < RC; ++z) acc[z] = 0.f;
@@ -100,21 +104,25 @@ askit_status launch_upward(askit_tree t, WeightCtx &c, int depth, int r, cudaStr
         cudaFuncSetAttribute(upward_kernel<RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     ASK_CUDA(attr);
     const int64_t a0 = (int64_t)1 << depth;
-    upward_kernel<RC><<<(unsigned)a0, 256, smem, s>>>(a0, depth == t->L, r, t->nstart, t->d_s, t->d_ncol, t->d_pivoff,
-                                                      t->piv, t->d_poff, t->P32, t->d_spool, c.Wt, c.Ws);
+    const unsigned ny = (unsigned)((std::max(1, t->prm.s_max) + UP_ROWS - 1) / UP_ROWS);
+    upward_kernel<RC><<<dim3((unsigned)a0, ny), 256, smem, s>>>(a0, depth == t->L, r, t->nstart, t->d_s, t->d_ncol,
+                                                                t->d_pivoff, t->piv, t->d_poff, t->P32, t->d_spool,
+                                                                c.Wt, c.Ws);
     ASK_LAUNCH();
     return ASKIT_OK;
 }
 
 }  // namespace
 
-// Buffers of a weight context for r vectors (grow-only; the padding rows of
-// Wt and Ws stay zero).
+// Buffers of a weight context for r vectors (grow-only in r and in the work
+// lists' entries; the padding rows of Wt and Ws stay zero).
 askit_status weights_reserve(askit_tree t, WeightCtx &c, int r, cudaStream_t s) {
-    if (r <= c.r_cap) {
+    if (r <= c.r_cap && t->wl_entries_max <= c.ent_cap) {
         c.r = r;
         return ASKIT_OK;
     }
+    const int r_req = r;
+    r = std::max(r, c.r_cap);      // the capacity never shrinks
     c.arena.free_all();
     c.Wt = c.Ws = c.partial = nullptr;
     c.colv = nullptr;
@@ -123,6 +131,7 @@ askit_status weights_reserve(askit_tree t, WeightCtx &c, int r, cudaStream_t s) 
     ASK_TRY(c.arena.alloc(&c.Wt, (size_t)t->N_pad * r));
     ASK_TRY(c.arena.alloc(&c.Ws, (size_t)srows * r));
     ASK_TRY(c.arena.alloc(&c.partial, (size_t)std::max<int64_t>(1, t->wl_entries_max) * r));
+    c.ent_cap = t->wl_entries_max;
     // per-sub-block column data of the 16-bit tensor-core kernel
     if (t->n_sub > 0 && t->d <= TC_K) {
         ASK_TRY(c.arena.alloc(&c.colv, (size_t)t->n_sub * 128));
@@ -131,7 +140,7 @@ askit_status weights_reserve(askit_tree t, WeightCtx &c, int r, cudaStream_t s) 
     ASK_CUDA(cudaMemsetAsync(c.Wt, 0, sizeof(float) * t->N_pad * r, s));
     ASK_CUDA(cudaMemsetAsync(c.Ws, 0, sizeof(float) * srows * r, s));
     c.r_cap = r;
-    c.r = r;
+    c.r = r_req;
     c.ready = true;
     return ASKIT_OK;
 }

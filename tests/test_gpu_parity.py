@@ -395,3 +395,85 @@ def test_leaf_grouped_lists_match_oracle():
         if prec in ("simt_fp32", "fp16x3", "fp16x3_block"):
             Ub, _ = eval_both(otree, gb, W, prec)
             assert np.array_equal(Ug, Ub), prec
+
+
+def test_knn_of_own_points_matches_the_oracle_and_gives_hit_rate():
+    """askit_knn_points: the exact kNN of some of the tree's own points (self
+    excluded), bit-exact with the oracle's exhaustive search; with it the
+    hit rate hr of the random-projection lists (Section 4) equals the
+    oracle's hr on the same structure."""
+    w = wl.MANIFOLD_1M_64.scaled(16384)
+    X, W = w.make_points(), w.make_weights()
+    kw = dict(leaf_size=512, kappa=32, knn_mode=1, rp_iters=2, s_max=256, id_tol=1e-4, h=0.35, seed=2)
+    otree, gtree = build_pair(X, kw)
+    ids = np.random.default_rng(3).choice(X.shape[0], size=700, replace=False).astype(np.int32)
+    ids[:3] = [0, X.shape[0] - 1, ids[5]]          # both ends and a repeat
+    nb, dd = gtree.knn_points(torch.from_numpy(ids).cuda())
+    ref_ids, ref_d = oracle.knn_exact(X, 32, rows=ids.astype(np.int64))
+    assert np.array_equal(nb.cpu().numpy(), ref_ids)
+    assert np.array_equal(dd.cpu().numpy(), ref_d)
+    o_ids, _ = otree.knn()
+    hr_gpu = oracle.hit_rate(gtree.structure(_askit().STRUCT_KNN)[ids], nb.cpu().numpy())
+    hr_orc = oracle.hit_rate(o_ids[ids], ref_ids)
+    assert hr_gpu == hr_orc and 0.0 < hr_orc <= 1.0
+    askit = _askit()
+    with pytest.raises(askit.AskitError):
+        gtree.knn_points(torch.tensor([X.shape[0]], dtype=torch.int32).cuda())
+
+
+def test_near_and_far_fields_match_the_oracle():
+    """askit_evaluate_part: the near field alone (whose error is the paper's
+    eps_kappa) and the far field alone match the oracle's parts, and the two
+    add up to the whole evaluation."""
+    w = wl.MANIFOLD_1M_64.scaled(16384)
+    X, W = w.make_points(), w.make_weights()
+    kw = dict(leaf_size=512, kappa=32, knn_mode=1, rp_iters=2, s_max=256, id_tol=1e-4, h=0.35, seed=2)
+    otree, gtree = build_pair(X, kw)
+    otree.set_weights(W.astype(np.float64))
+    gtree.set_weights(torch.from_numpy(W).cuda())
+    on, of = otree.evaluate_part("near"), otree.evaluate_part("far")
+    assert np.allclose(on + of, otree.evaluate(), rtol=0, atol=1e-12 * np.abs(on).max())
+    for prec in ALL:
+        set_prec(gtree, prec)
+        gn = gtree.evaluate_part("near").cpu().numpy()
+        gf = gtree.evaluate_part("far").cpu().numpy()
+        ga = gtree.evaluate().cpu().numpy()
+        assert_u(gn, on, TOL[prec], (prec, "near"))
+        # the far field is the smaller part: its tolerance is set against the whole u
+        assert np.linalg.norm(gf - of) <= TOL[prec] * np.linalg.norm(on + of), (prec, "far")
+        assert np.linalg.norm(gn + gf - ga) <= 1e-6 * np.linalg.norm(ga), prec
+
+
+def test_level_restriction_and_adaptive_kappa_match_the_oracle():
+    """askit_set_pruning: the level-restricted far field and the adaptive
+    kappa_i of Section 3 rebuild the work lists; the Near/Far counts equal the
+    oracle's and u matches the oracle's refined Evaluate in every precision,
+    in sample and out of sample."""
+    askit = _askit()
+    w = wl.MANIFOLD_1M_64.scaled(16384)
+    X, W = w.make_points(), w.make_weights()
+    kw = dict(leaf_size=512, kappa=32, knn_mode=1, rp_iters=2, s_max=256, id_tol=1e-4, h=0.35, seed=2)
+    otree, gtree = build_pair(X, kw)
+    otree.set_weights(W.astype(np.float64))
+    Wd = torch.from_numpy(W).cuda()
+    gtree.set_weights(Wd)
+    Y = (X[np.random.default_rng(8).integers(0, X.shape[0], 400)] +
+         0.02 * np.random.default_rng(9).standard_normal((400, 64))).astype(np.float32)
+    for fh, cut in ((0, 0.0), (3, 0.0), (-1, 3.0), (2, 4.0)):
+        gtree.set_pruning(fh, cut)
+        with pytest.raises(askit.AskitError):
+            gtree.evaluate()                             # the lists changed: weights first
+        gtree.set_weights(Wd)
+        Uo, near, far = otree.evaluate_ext(fh, cut, counts=True)
+        info = gtree.info()
+        assert info["near_total"] == int(near.sum()) and info["far_total"] == int(far.sum()), (fh, cut)
+        Uoy = otree.evaluate_oos_ext(Y, fh, cut)
+        for prec in ALL:
+            Ug, _ = eval_both(otree, gtree, W, prec)
+            assert_u(Ug, otree.evaluate_ext(fh, cut), TOL[prec], (fh, cut, prec))
+            Ugy = gtree.evaluate_targets(torch.from_numpy(Y).cuda()).cpu().numpy()
+            assert_u(Ugy, Uoy, TOL[prec], (fh, cut, prec, "out of sample"))
+    gtree.set_pruning(-1, 0.0)
+    gtree.set_weights(Wd)
+    Ug, Uo = eval_both(otree, gtree, W, "fp16x3")
+    assert_u(Ug, Uo, TOL["fp16x3"], "back to eq. (2.5)")

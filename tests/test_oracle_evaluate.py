@@ -228,3 +228,50 @@ def test_variable_bandwidth_kth_neighbor():
     assert np.array_equal(T.hsrc(), h)
     T.set_weights(W)
     assert rel(T.evaluate(), oracle.direct(X, W, h, 0.5, targets=np.arange(256))) < 1e-13
+
+
+def test_near_and_far_parts():
+    """The near field alone (direct leaf sums, whose error is the paper's
+    eps_kappa) and the far field alone (skeleton sums) add up to Evaluate;
+    with pruning off the far field vanishes and the near field is the direct
+    sum; the near field alone equals a brute-force sum over each target's
+    near leaves (from the definition of U_i)."""
+    X, W = _data(seed=4)
+    T = oracle.Tree(X, oracle.Config(leaf_size=32, kappa=6, s_max=8, id_tol=0.0, h=1.0))
+    T.set_weights(W)
+    near, far, tot = T.evaluate_part("near"), T.evaluate_part("far"), T.evaluate()
+    assert np.abs(near + far - tot).max() <= 1e-12 * np.abs(tot).max()
+    assert np.abs(far).max() > 0 and np.abs(near).max() > 0
+    perm = T.perm()
+    c = T.counts()
+    leaf_of = np.empty(len(X), np.int64)
+    M = 1 << T.L
+    for lf in range(M):
+        a = M + lf
+        leaf_of[perm[c["start"][a]: c["start"][a] + c["size"][a]]] = lf
+    ids, _ = T.knn()
+    for i in (0, 17, 300):
+        leaves = {leaf_of[i]} | {leaf_of[j] for j in ids[i]}
+        pts = np.concatenate([perm[c["start"][M + lf]: c["start"][M + lf] + c["size"][M + lf]] for lf in sorted(leaves)])
+        D = ((X[i].astype(np.float64) - X[pts].astype(np.float64)) ** 2).sum(1)
+        ref = (np.exp(-0.5 * D) * W[pts, 0]).sum()
+        assert abs(near[i, 0] - ref) <= 1e-12 * (np.abs(W).sum())
+    T0 = oracle.Tree(X, oracle.Config(leaf_size=32, kappa=6, s_max=8, id_tol=0.0, h=1.0, prune=0))
+    T0.set_weights(W)
+    assert np.abs(T0.evaluate_part("far")).max() == 0.0
+    assert rel(T0.evaluate_part("near"), oracle.direct(X, W, 1.0, 0.5, targets=np.arange(len(X)))) < 1e-13
+
+
+def test_hit_rate():
+    """hr (Section 4): the mean fraction of the exact neighbors found."""
+    a = np.array([[1, 2, 3, 4], [5, 6, 7, 8]])
+    assert oracle.hit_rate(a, a) == 1.0
+    assert oracle.hit_rate(a, a + 100) == 0.0
+    b = np.array([[4, 3, 9, 1], [8, 0, 0, 0]])       # 3 of 4, then 1 of 4
+    assert oracle.hit_rate(b, a) == (3 + 1) / 8
+    X, _ = _data(N=400, seed=5)
+    ex, _ = oracle.knn_exact(X, 8)
+    rp, _ = oracle.knn_rp(X, 8, 1, 64, 3)
+    rp_all, _ = oracle.knn_rp(X, 8, 1, 400, 3)        # one leaf holds every point: exact
+    assert oracle.hit_rate(rp_all, ex) == 1.0
+    assert 0.0 < oracle.hit_rate(rp, ex) < 1.0
