@@ -27,6 +27,10 @@ eps2 and the near field's error eps_kappa against the direct sum on 1000
 sampled targets, and the hit rate hr of the random-projection neighbor lists
 (Section 4 reports all three).
 
+The "prune_table" key reproduces Section 3's Table 1 (nodes visited under
+distance pruning and under neighbor pruning, curve / Gaussian / hypersphere
+in 2-256 dimensions, N = 65,536, m = 64, kappa = 128).
+
 The "configs" key measures the other two benchmark workloads at full size on
 the same GPU: N = 8,388,608 points in d = 64 (10-dim manifold, h = 0.5,
 m = 1024, s <= 512) with r = 16 weight vectors, and N = 1,048,576 points in
@@ -344,6 +348,12 @@ def accuracy(tree, precision, U, w, dev, n_sample=1000):
     return out
 
 
+def extra_default(args):
+    """The extra sections (Table 1, the other workloads) run with the default
+    workload at full size, or when asked for."""
+    return args.configs == "all" or (args.configs == "auto" and not args.n and args.workload == "manifold1m_d64")
+
+
 def measure_config(args, dev, key, steps=3, warmup=2):
     """One of the other benchmark workloads at full size: setup, autotuned
     launch configuration, Evaluate time (the call and the kernel's own
@@ -405,6 +415,35 @@ def measure_config(args, dev, key, steps=3, warmup=2):
     tree.close()
     del U, Wd
     torch.cuda.empty_cache()
+    return out
+
+
+def prune_table(dev, N=65536, m=64, kappa=128):
+    """Section 3's Table 1: the share of tree nodes the downward pass visits,
+    averaged over all targets, under distance pruning (R) and under neighbor
+    pruning (kappa), for points on a curve, Gaussian points and points on a
+    hypersphere of intrinsic dimension four, in 2, 4, 32 and 256 dimensions
+    (N = 65,536, m = 64, kappa = 128, R unscaled)."""
+    import torch
+    from paper_1410_0260_gb300 import askit
+    from paper_1410_0260_gb300 import workloads as wl
+    out = {"N": N, "m": m, "kappa": kappa, "rscale": 1.0, "unit": "% of tree nodes visited, mean over targets"}
+    t0 = time.perf_counter()
+    for gen in ("curve", "gaussian", "hypersphere"):
+        row = {}
+        for d in (2, 4, 32, 256):
+            if gen == "hypersphere" and d < 4:
+                continue
+            X = torch.from_numpy(getattr(wl, gen)(N, d, 17)).to(dev)
+            vk, vd = askit.prune_stats(X, m, kappa, 1.0)
+            L = 0
+            while -(-N // (1 << L)) > m:
+                L += 1
+            tot = (2 << L) - 1
+            row[f"{d}D"] = {"R": round(100.0 * float(vd.double().mean()) / tot, 2),
+                            "kappa": round(100.0 * float(vk.double().mean()) / tot, 2)}
+        out[gen] = row
+    out["seconds"] = time.perf_counter() - t0
     return out
 
 
@@ -623,9 +662,13 @@ def main():
     del Xd, Wd, U
     if rank == 0 and world == 1 and args.serve_requests > 0:
         line["serving"] = serving(args, dev, args.precision)
+    if rank == 0 and world == 1 and extra_default(args):
+        try:
+            line["prune_table"] = prune_table(dev)
+        except Exception as e:
+            line["prune_table"] = {"error": repr(e)}
     # the other benchmark workloads, at full size (one GPU)
-    extra = args.configs == "all" or (args.configs == "auto" and not args.n and args.workload == "manifold1m_d64")
-    if rank == 0 and world == 1 and extra:
+    if rank == 0 and world == 1 and extra_default(args) and args.configs != "none":
         line["configs"] = {}
         for key in ("manifold8m_d64_r16", "manifold1m_d1000"):
             try:

@@ -199,6 +199,23 @@ askit_status askit_knn_points(askit_tree t, const int32_t *ids_dev, int64_t Q, i
 askit_status askit_evaluate_part(askit_tree t, int32_t part, float *U_dev, int64_t ldu, void *stream);
 
 /*
+ * Pruning statistics of Section 3's Table 1 for the points X_dev [N, d]
+ * (stride ldx) as targets: the number of tree nodes the downward pass visits
+ * (Evaluate calls, pruned nodes included) with leaves of at most leaf_size
+ * points, under neighbor pruning (eq. (2.5) with the exact kappa nearest
+ * neighbors, kappa <= 256) into visited_knn_dev [N] and under distance
+ * pruning (a node is pruned when ||x - c|| > rscale R, c its centroid and R
+ * the largest distance from c to its points; rscale = 1 as printed) into
+ * visited_dist_dev [N] (int64, caller order).  The tree has 2^(L+1) - 1
+ * nodes, L the least depth whose nodes hold at most leaf_size points.
+ * Decisions in canonical FP64 (reproducible).  N <= 2^22, d <= 4096.
+ * Allocates its own scratch; blocks until done.
+ */
+askit_status askit_prune_stats(const float *X_dev, int64_t N, int32_t d, int64_t ldx, int32_t leaf_size,
+                               int32_t kappa, double rscale, int64_t *visited_knn_dev,
+                               int64_t *visited_dist_dev, void *stream);
+
+/*
  * Direct sum of eq. (1.1) at selected points, without approximation: for
  * each target id, the sum over all N points of K(x_i, x_j) w_j with the
  * tree's points, bandwidths and current weights (plain FP32, difference

@@ -81,6 +81,8 @@ def _declare(L):
     L.orc_set_weights.argtypes = [P, P, i32]
     L.orc_evaluate.argtypes = [P, P, i64, P, P, P]
     L.orc_evaluate_part.argtypes = [P, P, i64, i32, P, P, P]
+    L.orc_prune_stats.argtypes = [P, i64, i32, i64, i32, C.c_double, P, P]
+    L.orc_prune_stats.restype = i32
     L.orc_evaluate_ext.argtypes = [P, P, i64, i32, i32, C.c_double, P, P, P]
     L.orc_evaluate_oos_ext.argtypes = [P, P, i64, i32, C.c_double, P, P, P, P]
     L.orc_evaluate_oos.argtypes = [P, P, i64, P, P, P, P]
@@ -170,6 +172,19 @@ def knn_rp(X, kappa, iters, rp_leaf, seed):
     dd = np.zeros((N, kappa), np.float64)
     lib().orc_knn_rp(_p(X), N, d, kappa, iters, rp_leaf, seed, _p(ids), _p(dd))
     return ids, dd
+
+
+def prune_stats(X, m, kappa, rscale=1.0):
+    """Nodes the downward pass visits per target (Table 1 of Section 3)
+    under neighbor pruning (exact kNN, kappa neighbors) and under distance
+    pruning (centroid, radius R scaled by rscale): (L, visited_knn [N],
+    visited_dist [N]); the tree has 2^(L+1) - 1 nodes."""
+    X = _f32(X)
+    N, d = X.shape
+    vk = np.zeros(N, np.int64)
+    vd = np.zeros(N, np.int64)
+    L = lib().orc_prune_stats(_p(X), N, d, m, kappa, float(rscale), _p(vk), _p(vd))
+    return L, vk, vd
 
 
 def hit_rate(ids, ids_exact):

@@ -532,7 +532,7 @@ static void build_node_lists(orc_tree *t)
 
 /* Sampled skeletonization targets, eq. (2.4): T_a = N_a U Sample(X \ (X_a */
 /* U N_a), ell_a - |N_a|) without replacement, ell_a = min(s_max +        */
-/* ell_extra, N - |X_a|).  Reading taken for "uniformly chosen": draw n   */
+/* ell_extra, N - |X_a|).  Reading taken for the uniform sampling: draw n */
 /* of node a is j = floor(u * N / 2^32) with u the top 32 bits of Philox  */
 /* word n keyed (seed, 0), counter (a, n/4); j is rejected when it lies in */
 /* X_a, in N_a, or was drawn before.  Rows: N_a in key order, then draws. */
@@ -717,10 +717,10 @@ void orc_set_weights(orc_tree *t, const double *W, int r)
 /* 2 the far field (skeleton sums), 3 both (Algorithm 4 itself).  The paper */
 /* reports eps_kappa, the error of the near field alone (Table 4).           */
 /* `far_height` (>= 0) restricts the far field to nodes at most that many  */
-/* levels above the leaves (Section 3: "restrict the level(alpha) by       */
-/* starting the evaluation phase at a level which is a fixed distance from */
-/* the leaves"): a higher node that would be pruned is descended instead,  */
-/* down to that height.  -1: no restriction (Algorithm 4 as printed).      */
+/* levels above the leaves (Section 3 proposes bounding the level of the   */
+/* skeletons used by starting the downward pass a fixed number of levels   */
+/* above the leaves): a higher node that would be pruned is descended      */
+/* instead, down to that height.  -1: no restriction (Algorithm 4).        */
 static void evaluate_rec(const orc_tree *t, const float *x, const int64_t *pset, int np,
                          int64_t a, int depth, double *u, int64_t *near, int64_t *far, int part,
                          int far_height)
@@ -756,8 +756,8 @@ static void evaluate_rec(const orc_tree *t, const float *x, const int64_t *pset,
     evaluate_rec(t, x, pset, np, 2 * a, depth + 1, u, near, far, part, far_height);
 }
 
-/* Adaptive kappa_i (Section 3: the distance to the (kappa+1)-st neighbor  */
-/* "can be used to derive an adaptive (per point) selection of kappa_i").   */
+/* Adaptive kappa_i (Section 3 suggests choosing kappa per point from the */
+/* distance to its farther neighbors).                                     */
 /* Reading taken: with a kernel cut a > 0, the prune set keeps the         */
 /* neighbors up to the last rank whose kernel value exceeds e^-a, i.e.     */
 /* kappa_i = 1 + max{ z : c D(i, N_i[z]) / h^2 < a } (0 if none), with h   */
@@ -861,6 +861,90 @@ void orc_evaluate_oos(const orc_tree *t, const float *Y, int64_t T, double *U,
                       int32_t *knn_out, int64_t *near, int64_t *far)
 {
     orc_evaluate_oos_ext(t, Y, T, -1, 0.0, U, knn_out, near, far);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pruning statistics of Table 1 (Section 3, which compares distance     */
+/* pruning with neighbor pruning): for every point i as a target, the     */
+/* number of tree nodes the downward pass visits (Evaluate calls, pruned */
+/* nodes included) under                                                   */
+/*   neighbor pruning, eq. (2.5): a node is pruned unless it holds i or    */
+/*     one of its kappa nearest neighbors (the exact kNN, any kappa);      */
+/*   distance pruning: a node alpha with centroid c_alpha and radius       */
+/*     R_alpha = max_{x in alpha} ||x - c_alpha|| is pruned when           */
+/*     ||x_i - c_alpha|| > rscale R_alpha (Section 3 remarks that R needs */
+/*     a scale factor to separate the nodes; rscale = 1 is the plain rule).*/
+/* The root is never pruned.  Readings taken: c_alpha is the FP64 mean of  */
+/* the node's points summed in leaf order, distances are compared squared */
+/* (D(x_i, c) > rscale^2 R^2) in FP64, coordinates in ascending order.    */
+/* ------------------------------------------------------------------------ */
+static int64_t visit_dist(const float *x, int d, int L, int64_t a, int depth, const double *cent,
+                          const double *r2, double rs2)
+{
+    int64_t v = 1;
+    if (depth > 0 && dist2_df(cent + (size_t)a * d, x, d) > rs2 * r2[a]) return v;
+    if (depth == L) return v;
+    return v + visit_dist(x, d, L, 2 * a, depth + 1, cent, r2, rs2) +
+           visit_dist(x, d, L, 2 * a + 1, depth + 1, cent, r2, rs2);
+}
+
+static int64_t visit_knn(int L, int64_t a, int depth, const int64_t *pset, int np)
+{
+    int64_t v = 1;
+    int keep = depth == 0;
+    for (int q = 0; q < np && !keep; ++q)
+        if ((pset[q] >> (L - depth)) == a) keep = 1;
+    if (!keep || depth == L) return v;
+    return v + visit_knn(L, 2 * a, depth + 1, pset, np) + visit_knn(L, 2 * a + 1, depth + 1, pset, np);
+}
+
+int orc_prune_stats(const float *X, int64_t N, int d, int64_t m, int kappa, double rscale,
+                    int64_t *visited_knn, int64_t *visited_dist)
+{
+    int L = orc_tree_depth(N, m);
+    int64_t nn = (int64_t)2 << L;
+    int64_t *perm = (int64_t *)malloc(sizeof(int64_t) * N);
+    int64_t *start = (int64_t *)calloc(nn, sizeof(int64_t));
+    int64_t *size = (int64_t *)calloc(nn, sizeof(int64_t));
+    build_tree(X, N, d, L, 0, 0, 0, perm, start, size);
+    int64_t *leaf = (int64_t *)malloc(sizeof(int64_t) * N);
+    for (int64_t a = (int64_t)1 << L; a < nn; ++a)
+        for (int64_t q = 0; q < size[a]; ++q) leaf[perm[start[a] + q]] = a;
+    int32_t *ids = (int32_t *)malloc(sizeof(int32_t) * N * kappa);
+    double *dd = (double *)malloc(sizeof(double) * N * kappa);
+    int64_t *rows = (int64_t *)malloc(sizeof(int64_t) * N);
+    for (int64_t i = 0; i < N; ++i) rows[i] = i;
+    orc_knn_exact(X, N, d, kappa, NULL, rows, N, ids, dd);
+    double *cent = (double *)calloc((size_t)nn * d, sizeof(double));
+    double *r2 = (double *)calloc(nn, sizeof(double));
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t a = 1; a < nn; ++a) {
+        if (size[a] == 0) continue;
+        double *c = cent + (size_t)a * d;
+        for (int64_t q = 0; q < size[a]; ++q) {
+            const float *x = X + (size_t)perm[start[a] + q] * d;
+            for (int k = 0; k < d; ++k) c[k] = c[k] + (double)x[k];
+        }
+        for (int k = 0; k < d; ++k) c[k] = c[k] / (double)size[a];
+        double mx = 0.0;
+        for (int64_t q = 0; q < size[a]; ++q) {
+            double D = dist2_df(c, X + (size_t)perm[start[a] + q] * d, d);
+            if (D > mx) mx = D;
+        }
+        r2[a] = mx;
+    }
+    const double rs2 = rscale * rscale;
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t pset[1 + 4096];
+        int np = 0;
+        pset[np++] = leaf[i];
+        for (int z = 0; z < kappa && z < 4096; ++z) pset[np++] = leaf[ids[(size_t)i * kappa + z]];
+        visited_knn[i] = visit_knn(L, 1, 0, pset, np);
+        visited_dist[i] = visit_dist(X + (size_t)i * d, d, L, 1, 0, cent, r2, rs2);
+    }
+    free(perm); free(start); free(size); free(leaf); free(ids); free(dd); free(rows); free(cent); free(r2);
+    return L;
 }
 
 /* ------------------------------------------------------------------------ */

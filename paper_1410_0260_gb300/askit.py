@@ -33,7 +33,7 @@ EXPORTS = ["askit_default_params", "askit_setup", "askit_set_weights", "askit_ev
            "askit_weights_destroy", "askit_footprint", "askit_graph_create", "askit_graph_launch",
            "askit_graph_destroy", "askit_autotune", "askit_set_launch", "askit_knn_targets",
            "askit_kernel_timing", "askit_set_wait_limit", "askit_set_fp16_centering", "askit_knn_points",
-           "askit_evaluate_part", "askit_set_pruning"]
+           "askit_evaluate_part", "askit_set_pruning", "askit_prune_stats"]
 
 
 class TuneEntry(C.Structure):
@@ -62,6 +62,18 @@ class Info(C.Structure):
                 ("near_total", C.c_int64), ("far_total", C.c_int64), ("device_bytes", C.c_int64),
                 ("n_batches", C.c_int64), ("setup_ms", C.c_double * 7), ("fp16_centering", C.c_int32),
                 ("pad_", C.c_int32), ("fp16_rho", C.c_double)]
+
+
+def prune_stats(X: torch.Tensor, leaf_size: int, kappa: int, rscale: float = 1.0, stream=None):
+    """Nodes visited per target under neighbor and distance pruning (Section
+    3, Table 1): (visited_knn [N], visited_dist [N]) int64 on X's device."""
+    X = _dev_f32(X, "X")
+    N, d = X.shape
+    vk = torch.empty(N, dtype=torch.int64, device=X.device)
+    vd = torch.empty(N, dtype=torch.int64, device=X.device)
+    _check(load().askit_prune_stats(C.c_void_p(X.data_ptr()), N, d, X.stride(0), leaf_size, kappa, float(rscale),
+                                    C.c_void_p(vk.data_ptr()), C.c_void_p(vd.data_ptr()), _stream(stream)))
+    return vk, vd
 
 
 def load(path: str | None = None):
@@ -103,6 +115,7 @@ def load(path: str | None = None):
             L.askit_knn_points.argtypes = [V, V, I64, V, V, V]
             L.askit_evaluate_part.argtypes = [V, I32, V, I64, V]
             L.askit_set_pruning.argtypes = [V, I32, D, V]
+            L.askit_prune_stats.argtypes = [V, I64, I32, I64, I32, I32, D, V, V, V]
             L.askit_knn_targets.argtypes = [V, V, I64, I64, V, V, V]
             L.askit_kernel_timing.argtypes = [V, I32, C.POINTER(D), C.POINTER(I64)]
             L.askit_status_string.restype = C.c_char_p

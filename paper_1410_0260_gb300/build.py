@@ -14,9 +14,9 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libaskit.so")
 
 SOURCES = ["capi.cu", "setup_sort.cu", "setup_tree.cu", "setup_skel.cu", "eval_lists.cu",
-           "weights.cu", "eval_simt.cu", "eval_tc.cu", "eval_tc_wide.cu", "eval_tc16.cu", "eval_g16.cu"]
+           "weights.cu", "eval_simt.cu", "eval_tc.cu", "eval_tc_wide.cu", "eval_tc16.cu", "eval_g16.cu", "prune_stats.cu"]
 # setup stages are bit-exact FP64: no contraction into fused multiply-adds anywhere
-NO_FMAD = {"setup_tree.cu", "setup_skel.cu"}
+NO_FMAD = {"setup_tree.cu", "setup_skel.cu", "prune_stats.cu"}
 
 
 def nvcc() -> str:

@@ -42,6 +42,35 @@ def manifold(N: int, d: int, k: int, noise: float, seed: int, chunk: int = 1 << 
     return X
 
 
+def curve(N: int, d: int, seed: int) -> np.ndarray:
+    """Points on the curve of Section 3's pruning experiment (intrinsic
+    dimension one): x_k = f_k(k pi t), t ~ U[0, 1], k = 1..d, f_k = cos for
+    odd k and sin for even k."""
+    t = np.random.default_rng(seed).uniform(0.0, 1.0, N)
+    k = np.arange(1, d + 1)
+    arg = np.pi * t[:, None] * k[None, :]
+    return np.where(k % 2 == 1, np.cos(arg), np.sin(arg)).astype(np.float32)
+
+
+def gaussian(N: int, d: int, seed: int) -> np.ndarray:
+    """Standard normal points (intrinsic dimension = d)."""
+    return np.random.default_rng(seed).standard_normal((N, d)).astype(np.float32)
+
+
+def hypersphere(N: int, d: int, seed: int) -> np.ndarray:
+    """Points uniform on a hypersphere of intrinsic dimension four: the unit
+    sphere of R^5 (normalized Gaussian draws) mapped into R^d by a seeded
+    matrix with orthonormal columns; with d = 4 the unit sphere of R^4."""
+    rng = np.random.default_rng(seed)
+    k = min(5, d)
+    z = rng.standard_normal((N, k))
+    z /= np.linalg.norm(z, axis=1, keepdims=True)
+    if k == d:
+        return z.astype(np.float32)
+    A, _ = np.linalg.qr(rng.standard_normal((d, k)))
+    return (z @ A.T).astype(np.float32)
+
+
 def manifold_queries(T: int, d: int, k: int, noise: float, seed: int, qseed: int) -> np.ndarray:
     """Fresh points from the same embedding as ``manifold(..., seed)``: the
     same matrix A (the first draw of that generator), new z and noise."""

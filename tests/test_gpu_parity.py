@@ -459,13 +459,22 @@ def test_level_restriction_and_adaptive_kappa_match_the_oracle():
     gtree.set_weights(Wd)
     Y = (X[np.random.default_rng(8).integers(0, X.shape[0], 400)] +
          0.02 * np.random.default_rng(9).standard_normal((400, 64))).astype(np.float32)
+    cap = gtree.info()["n_entries"]          # one batch: the partial buffer's size at set_weights
+    grew = 0
     for fh, cut in ((0, 0.0), (3, 0.0), (-1, 3.0), (2, 4.0)):
         gtree.set_pruning(fh, cut)
-        with pytest.raises(askit.AskitError):
-            gtree.evaluate()                             # the lists changed: weights first
-        gtree.set_weights(Wd)
-        Uo, near, far = otree.evaluate_ext(fh, cut, counts=True)
         info = gtree.info()
+        assert info["n_batches"] == 1
+        if info["n_entries"] > cap:
+            # the lists outgrew the weight context's partial sums: weights first
+            with pytest.raises(askit.AskitError):
+                gtree.evaluate()
+            gtree.set_weights(Wd)
+            cap, grew = info["n_entries"], grew + 1
+        # otherwise the skeleton weights (which do not depend on the lists) stay valid
+        Uo, near, far = otree.evaluate_ext(fh, cut, counts=True)
+        set_prec(gtree, "fp16x3")
+        assert_u(gtree.evaluate().cpu().numpy(), Uo, TOL["fp16x3"], (fh, cut, "same weights"))
         assert info["near_total"] == int(near.sum()) and info["far_total"] == int(far.sum()), (fh, cut)
         Uoy = otree.evaluate_oos_ext(Y, fh, cut)
         for prec in ALL:
@@ -473,7 +482,22 @@ def test_level_restriction_and_adaptive_kappa_match_the_oracle():
             assert_u(Ug, otree.evaluate_ext(fh, cut), TOL[prec], (fh, cut, prec))
             Ugy = gtree.evaluate_targets(torch.from_numpy(Y).cuda()).cpu().numpy()
             assert_u(Ugy, Uoy, TOL[prec], (fh, cut, prec, "out of sample"))
+    assert grew >= 1                          # far_height 0 lists far more nodes
     gtree.set_pruning(-1, 0.0)
-    gtree.set_weights(Wd)
     Ug, Uo = eval_both(otree, gtree, W, "fp16x3")
     assert_u(Ug, Uo, TOL["fp16x3"], "back to eq. (2.5)")
+
+
+@pytest.mark.parametrize("gen,d", [("curve", 8), ("gaussian", 3), ("hypersphere", 6), ("gaussian", 40)])
+def test_prune_stats_match_the_oracle(gen, d):
+    """askit_prune_stats (Section 3, Table 1): the nodes visited by every
+    target under neighbor pruning (exact kNN, kappa = 128 here, past the
+    setup's 32) and under distance pruning equal the oracle's, bit for bit
+    (every decision is canonical FP64)."""
+    askit = _askit()
+    X = getattr(wl, gen)(3000, d, 11)
+    for kappa, rscale in ((128, 1.0), (20, 0.5)):
+        vk, vd = askit.prune_stats(torch.from_numpy(X).cuda(), 32, kappa, rscale)
+        L, ok, od = oracle.prune_stats(X, 32, kappa, rscale)
+        assert np.array_equal(vk.cpu().numpy(), ok), (gen, d, kappa)
+        assert np.array_equal(vd.cpu().numpy(), od), (gen, d, kappa)

@@ -20,7 +20,16 @@ MUTATIONS = [
     ("pivot tie rule", "if (acc > best) { best = acc; p = j; }", "if (acc >= best) { best = acc; p = j; }"),
     ("skeleton weights drop P term", "t->wsk[a][q * r + z] = v[(size_t)t->piv[a][q] * r + z] + acc;",
      "t->wsk[a][q * r + z] = v[(size_t)t->piv[a][q] * r + z];"),
-    ("evaluate skips right child", "evaluate_rec(t, x, pset, np, 2 * a + 1, depth + 1, u, near, far);", ""),
+    ("evaluate skips right child",
+     "evaluate_rec(t, x, pset, np, 2 * a + 1, depth + 1, u, near, far, part, far_height);", ""),
+    ("far height off by one", "if (far_height >= 0 && t->L - depth > far_height) pruned = 0;",
+     "if (far_height >= 0 && t->L - depth >= far_height) pruned = 0;"),
+    ("adaptive kappa keeps the first failing neighbor", "if (arg < cut) ki = z + 1;", "if (arg <= cut) ki = z + 2;"),
+    ("distance pruning ignores the radius scale", "> rs2 * r2[a]) return v;", "> r2[a]) return v;"),
+    ("neighbor pruning visits one child", "return v + visit_knn(L, 2 * a, depth + 1, pset, np) + visit_knn(L, 2 * a + 1, depth + 1, pset, np);",
+     "return v + visit_knn(L, 2 * a, depth + 1, pset, np);"),
+    ("centroid over half the node", "for (int64_t q = 0; q < size[a]; ++q) {\n            const float *x",
+     "for (int64_t q = 0; q < size[a] / 2; ++q) {\n            const float *x"),
     ("prune test off by a level", "if ((pset[q] >> (t->L - depth)) == a) pruned = 0;",
      "if ((pset[q] >> (t->L - depth + 1)) == a) pruned = 0;"),
     ("median side", "int64_t nl = (n + 1) / 2;", "int64_t nl = n / 2;"),
@@ -38,8 +47,8 @@ MUTATIONS = [
     ("exp reduction tail sign", "double r = (a - n * LN2_HEAD) - n * LN2_TAIL;", "double r = (a - n * LN2_HEAD) + n * LN2_TAIL;"),
     ("exp polynomial term", "0x1.5555555555555p-3,", "0x1.5555555555555p-2,"),
     ("leaf-grouped set takes the target's neighbors",
-     "for (int z = 0; z < kappa; ++z) pset[np++] = t->leafof[t->knn[(size_t)p * kappa + z]];",
-     "for (int z = 0; z < kappa; ++z) pset[np++] = t->leafof[t->knn[(size_t)i * kappa + z]];"),
+     "for (int z = 0; z < kp; ++z) pset[np++] = t->leafof[t->knn[(size_t)p * kappa + z]];",
+     "for (int z = 0; z < kp; ++z) pset[np++] = t->leafof[t->knn[(size_t)i * kappa + z]];"),
 ]
 
 
