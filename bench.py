@@ -59,7 +59,10 @@ sys.path.insert(0, ROOT)
 METRIC = "ASKIT eval targets/s at rel.err <=1e-4 vs plain FP32 on 1 GB300"
 UNIT = "targets/s"
 SM_COUNT = 152
-MUFU_PER_SM_CLK = 16          # ex2 per SM per clock (4 SM sub-partitions x 4)
+# ex2 per SM per clock: one warp instruction per clock on the XU pipe of this
+# part (ncu's XU peak; an FP16x3 Evaluate capture issues 0.436 ex2 warp
+# instructions per active SM cycle and ncu reports 43.2 % of the XU peak)
+MUFU_PER_SM_CLK = 32
 FP32_LANES_PER_SM = 128
 TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense tensor-rate ratio
 
@@ -76,13 +79,19 @@ def parse():
     ap.add_argument("--n", type=int, default=0, help="override N (smaller runs; not a bench line)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-n", type=int, default=65536)
+    ap.add_argument("--cpu-n", type=int, default=0,
+                    help="points of the oracle's instance (0: the workload's own N)")
     ap.add_argument("--cpu-targets", type=int, default=10000)
     ap.add_argument("--cpu-targets-1core", type=int, default=1500)
     ap.add_argument("--configs", default="auto", choices=["auto", "all", "none"],
                     help="also measure the 8M x 64 (r = 16) and 1M x 1000 (variable h) workloads at full size "
                          "(auto: with the default workload and N)")
-    ap.add_argument("--serve-requests", type=int, default=32, help="requests per serving run (0: no serving run)")
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests per serving run of the split path (0: no serving run)")
+    ap.add_argument("--serve-requests-fp32", type=int, default=48,
+                    help="requests of the saturated plain-FP32 comparator run")
+    ap.add_argument("--serve-load", type=float, default=0.6,
+                    help="offered load of the sustained serving run, as a fraction of the measured capacity")
     ap.add_argument("--lists", default="target", choices=["target", "leaf"],
                     help="interaction lists: per target (eq. 2.5, the bench line's) or leaf-grouped")
     return ap.parse_args()
@@ -123,12 +132,14 @@ def job_throughput(world, n_per_rank, ms_per_step):
     return world * n_per_rank / (ms_per_step / 1e3)
 
 
-def roofline(P, d, r, precision, sec, peaks, smax_mhz):
+def roofline(P, d, r, precision, sec, peaks, smax_mhz, arg_on_tensor=False, weights_on_tensor=False):
     """Roofline of the Evaluate kernel for P algorithmic pairs in `sec`
     seconds: the binding unit among the tensor cores (three split products
-    of length d per pair), MUFU (one ex2 per pair) and the FP32 FMA pipe
-    (r + 2 FMAs per pair in the epilogue); plain FP32 is bound by its 2d lane
-    operations per pair."""
+    of length d per pair, and of length r when the weight sums run there
+    too), MUFU (one ex2 per pair) and the FP32 FMA pipe (r FMAs per pair in
+    the epilogue unless the tensor cores take the weight sums, plus 2 for the
+    exponent's argument unless the tensor cores form it); plain FP32 is bound
+    by its 2d lane operations per pair."""
     mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * smax_mhz * 1e6
     lane_peak = SM_COUNT * FP32_LANES_PER_SM * smax_mhz * 1e6
     if precision == "simt_fp32":
@@ -138,23 +149,25 @@ def roofline(P, d, r, precision, sec, peaks, smax_mhz):
     else:
         bf16 = (peaks or {}).get("bf16_tflops", 1900.0)
         tpeak = bf16 * (TF32_OVER_BF16 if precision == "tf32x3" else 1.0)   # fp16 and bf16 share the rate
-        t_tensor = P * 3 * 2 * d / (tpeak * 1e12)
+        k_tensor = d + (r if weights_on_tensor else 0)     # contraction length per pair
+        t_tensor = P * 3 * 2 * k_tensor / (tpeak * 1e12)
         t_mufu = P / mufu_peak
         # FP32 lane FMAs per pair in the epilogue: the exponent's argument (2)
         # and one per weight vector
-        fma_per_pair = r + 2
+        fma_per_pair = (0 if weights_on_tensor else r) + (0 if arg_on_tensor else 2)
         t_fma = P * fma_per_pair / lane_peak
         if t_fma > max(t_tensor, t_mufu):
             roof = {"bound": "alu", "achieved": P * fma_per_pair / sec / 1e12, "peak": lane_peak / 1e12,
                     "unit": "Tfma/s", "peak_source": "FP32 FMA: 152 SMs x 128 lanes x max SM clock; "
-                    "%d FMAs per pair (r = %d weight sums + 2 for the exponent's argument)" % (fma_per_pair, r)}
+                    "%d FMAs per pair (r = %d weight sums%s)" %
+                    (fma_per_pair, r, "" if arg_on_tensor else " + 2 for the exponent's argument")}
         elif t_tensor >= t_mufu:
-            roof = {"bound": "tensor", "achieved": P * 3 * 2 * d / sec / 1e12, "peak": tpeak, "unit": "TFLOP/s",
+            roof = {"bound": "tensor", "achieved": P * 3 * 2 * k_tensor / sec / 1e12, "peak": tpeak, "unit": "TFLOP/s",
                     "peak_source": ("measured bf16 burst x 1.1/2.25 (TF32)" if precision == "tf32x3"
                                     else "measured bf16 burst") + (" of measured" if peaks else " of fallback")}
         else:
             roof = {"bound": "alu", "achieved": P / sec / 1e12, "peak": mufu_peak / 1e12, "unit": "Tex2/s",
-                    "peak_source": "MUFU ex2: 152 SMs x 16/clk x max SM clock"}
+                    "peak_source": "MUFU ex2: 152 SMs x 32/clk x max SM clock"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     return roof
 
@@ -237,14 +250,16 @@ class ClockSampler:
 
 
 class OracleSample:
-    """The oracle as it stands, on the host cores: ASKIT setup on a bounded
-    instance of the same recipe (N = cpu_n points), then Evaluate (Algorithm 4)
-    timed on a fixed sample of its targets."""
+    """The oracle as it stands, on the host cores: ASKIT setup on the
+    workload itself (or, with --cpu-n, on an instance of the same recipe with
+    that many points), then Evaluate (Algorithm 4) timed on a fixed sample of
+    its targets."""
 
     def __init__(self, args, w):
         import oracle
         self.oracle = oracle
-        ws = w.scaled(args.cpu_n)
+        n_pts = args.cpu_n or w.N
+        ws = w if n_pts == w.N else w.scaled(n_pts)
         X, W = ws.make_points(), ws.make_weights()
         cfg = oracle.Config(leaf_size=ws.leaf_size, kappa=ws.kappa, knn_mode=ws.knn_mode,
                             rp_iters=ws.rp_iters, s_max=ws.s_max, s_min=ws.s_min, id_tol=ws.id_tol, h=ws.h,
@@ -253,11 +268,11 @@ class OracleSample:
         self.tree = oracle.Tree(X, cfg)
         self.tree.set_weights(W.astype(np.float64))
         self.setup_s = time.perf_counter() - t0
-        n = min(args.cpu_targets, args.cpu_n)
-        self.tg = np.random.default_rng(7).choice(args.cpu_n, size=n, replace=False)
-        self.sample = (f"oracle Evaluate (Algorithm 4, FP64 C, OpenMP over targets) on {n} targets of a "
-                       f"N={args.cpu_n} instance of the same manifold recipe (d={ws.d}, m={ws.leaf_size}, "
-                       f"kappa={ws.kappa}, s<={ws.s_max}); oracle setup {self.setup_s:.1f}s not timed")
+        n = min(args.cpu_targets, n_pts)
+        self.tg = np.random.default_rng(7).choice(n_pts, size=n, replace=False)
+        self.sample = (f"oracle Evaluate (Algorithm 4, FP64 C, OpenMP over targets) on {n} sampled targets of "
+                       f"'{ws.name}' (N={n_pts}, d={ws.d}, m={ws.leaf_size}, kappa={ws.kappa}, s<={ws.s_max}); "
+                       f"oracle setup {self.setup_s:.1f}s not timed")
 
     def step(self, tg=None) -> float:
         t0 = time.perf_counter()
@@ -325,9 +340,12 @@ def accuracy(tree, precision, U, w, dev, n_sample=1000):
     if precision != "simt_fp32":
         tree.set_precision("simt_fp32")
         Uref = torch.empty_like(U)
+        tree.kernel_timing(True)
         tree.evaluate(Uref)
+        k_ms, _ = tree.kernel_timing(False)
         torch.cuda.synchronize()
         tree.set_precision(precision)
+        out["fp32_kernel_ms"] = k_ms
         out["rel_err_vs_fp32"] = float(torch.linalg.vector_norm((U - Uref).double()) /
                                        torch.linalg.vector_norm(Uref.double()))
         del Uref
@@ -395,8 +413,9 @@ def measure_config(args, dev, key, steps=3, warmup=2):
     tree.sync()
     acc = accuracy(tree, args.precision, U, w, dev)
     peaks = measured_peaks()
+    g16 = args.precision == "fp16x3" and w.d <= 64 and info["fp16_centering"] == 2
     roof = roofline(info["pairs_algorithmic"], w.d, r, args.precision, k_ms / steps / 1e3, peaks,
-                    (peaks or {}).get("sm_max_mhz") or 2070.0)
+                    (peaks or {}).get("sm_max_mhz") or 2070.0, arg_on_tensor=g16, weights_on_tensor=g16 and r > 4)
     roof["kernel"] = ("eval_tcw_kernel" if w.d > 64 else
                       "eval_g16_kernel" if info["fp16_centering"] == 2 else "eval_tc16_kernel")
     roof["ms_per_launch"] = k_ms / max(1, k_launches)
@@ -447,10 +466,70 @@ def prune_table(dev, N=65536, m=64, kappa=128):
     return out
 
 
-def serving(args, dev, precision):
-    """The serving workload, replayed once per precision on one resident tree."""
+SERVE_RATE = 200.0      # arrivals per second of the serving recipe
+
+
+def _mean_request_targets(N, r_max=64, t_min=100, t_max=100_000):
+    """Expected evaluated targets of one request of workloads.request_stream:
+    half weight requests (N r, r ~ U{1..r_max}), half target batches
+    (log-uniform T in [t_min, t_max])."""
+    return 0.5 * N * (r_max + 1) / 2 + 0.5 * (t_max - t_min) / np.log(t_max / t_min)
+
+
+def _serve_stream(w, n, rate, seed, pool, dev):
+    """n requests of the serving recipe at `rate` per second: weight requests
+    take column slices of a resident pool of 128 vectors, target batches rows
+    of pinned host queries (copied in by the server)."""
     import torch
-    from paper_1410_0260_gb300 import askit, serve
+    from paper_1410_0260_gb300 import workloads as wl
+    spec = wl.request_stream(n, rate, seed=seed)
+    rng = np.random.default_rng(seed + 17)
+    n_q = sum(size for _, kind, size in spec if kind == "targets")
+    Y = torch.from_numpy(wl.manifold_queries(max(n_q, 1), w.d, w.k_intr, w.noise, w.seed, seed + 99)).pin_memory()
+    stream, off = [], 0
+    for ta, kind, size in spec:
+        if kind == "weights":
+            c0 = int(rng.integers(0, 128 - size + 1))
+            stream.append((ta, kind, pool[:, c0:c0 + size]))
+        else:
+            stream.append((ta, kind, Y[off:off + size]))
+            off += size
+    return stream, Y
+
+
+def _serve_run(tree, Wres, stream, N, warm):
+    """One replay on a fresh two-slot server: latency and throughput, the
+    offered load next to the achieved one, and whether the queue grew
+    (offered above what was served: the latencies then measure queueing and
+    grow with the run's length)."""
+    from paper_1410_0260_gb300 import serve
+    srv = serve.Server(tree, Wres, n_slots=2)
+    serve.replay(srv, warm)
+    srv.completed.clear()
+    srv.n_batches = 0
+    reqs = serve.replay(srv, stream)
+    st = serve.latency_stats(reqs, N)
+    st["peak_concurrent_batches"] = srv.peak_concurrency
+    st["batches"] = srv.n_batches
+    srv.close()
+    span = max(ta for ta, _, _ in stream) - min(ta for ta, _, _ in stream)
+    offered = sum(N * d.shape[1] if k == "weights" else d.shape[0] for _, k, d in stream)
+    st["offered_requests_per_s"] = (len(stream) - 1) / span if span > 0 else float("inf")
+    st["offered_targets_per_s"] = offered / span if span > 0 else float("inf")
+    st["completed_requests_per_s"] = st["completed"] / st["wall_s"]
+    st["overloaded"] = bool(st["offered_targets_per_s"] > 1.1 * st["targets_per_s"])
+    return st
+
+
+def serving(args, dev, precision):
+    """The serving workload on one resident tree: the specified stream
+    (Poisson arrivals at 200/s, far above one GPU's capacity: a saturated
+    run that measures capacity, its latencies are queueing), the same recipe
+    at a sustainable rate (60 % of the measured capacity: the latencies of a
+    stable queue), and plain FP32 saturated by the specified stream (its
+    capacity, the comparator)."""
+    import torch
+    from paper_1410_0260_gb300 import askit
     from paper_1410_0260_gb300 import workloads as wl
     w = wl.SERVING_2M_64.scaled(2 * args.n) if args.n else wl.SERVING_2M_64
     t0 = time.perf_counter()
@@ -461,35 +540,26 @@ def serving(args, dev, precision):
     tree.set_weights(Wres)
     out_tune = tree.autotune(reps=2)
     pool = torch.from_numpy(w.make_weights(128, seed_offset=7)).to(dev)
-    spec = wl.request_stream(args.serve_requests, 200.0, seed=w.seed)
-    rng = np.random.default_rng(w.seed + 17)
-    n_q = sum(size for _, kind, size in spec if kind == "targets")
-    Y = torch.from_numpy(wl.manifold_queries(max(n_q, 1), w.d, w.k_intr, w.noise, w.seed, w.seed + 99)).pin_memory()
-    stream, off = [], 0
-    for ta, kind, size in spec:
-        if kind == "weights":
-            c0 = int(rng.integers(0, 128 - size + 1))
-            stream.append((ta, kind, pool[:, c0:c0 + size]))
-        else:
-            stream.append((ta, kind, Y[off:off + size]))
-            off += size
-    out = {"workload": w.name, "arrivals_per_s": 200.0, "slots": 2, "setup_s": setup_s,
+    mean_t = _mean_request_targets(w.N)
+    out = {"workload": w.name, "slots": 2, "setup_s": setup_s,
            "autotune": next((c for c in out_tune if c["chosen"]), None),
-           "targets_counted_as": "N r per weight request, T per target batch"}
-    for prec in (precision, "simt_fp32"):
-        tree.set_precision(prec)
-        srv = serve.Server(tree, Wres, n_slots=2)
-        serve.replay(srv, [(0.0, "weights", pool[:, :16]), (0.0, "targets", Y[:1000])])   # warm-up
-        srv.completed.clear()
-        srv.n_batches = 0
-        reqs = serve.replay(srv, stream)
-        st = serve.latency_stats(reqs, w.N)
-        st["peak_concurrent_batches"] = srv.peak_concurrency
-        st["batches"] = srv.n_batches
-        srv.close()
-        out[prec] = st
-    if precision != "simt_fp32":
-        out["split_over_fp32_targets_per_s"] = out[precision]["targets_per_s"] / out["simt_fp32"]["targets_per_s"]
+           "targets_counted_as": "N r per weight request, T per target batch",
+           "mean_request_targets": mean_t}
+    warm_y = torch.from_numpy(wl.manifold_queries(1000, w.d, w.k_intr, w.noise, w.seed, w.seed + 5)).pin_memory()
+    warm = [(0.0, "weights", pool[:, :16]), (0.0, "targets", warm_y)]
+    tree.set_precision(precision)
+    stream, _ = _serve_stream(w, args.serve_requests, SERVE_RATE, w.seed, pool, dev)
+    out[precision] = {"arrivals_per_s": SERVE_RATE, **_serve_run(tree, Wres, stream, w.N, warm)}
+    cap = out[precision]["targets_per_s"]
+    rate = args.serve_load * cap / mean_t
+    stream, _ = _serve_stream(w, args.serve_requests, rate, w.seed + 1, pool, dev)
+    out[precision + "_sustained"] = {"arrivals_per_s": rate, "load_of_capacity": args.serve_load,
+                                     **_serve_run(tree, Wres, stream, w.N, warm)}
+    if precision != "simt_fp32" and args.serve_requests_fp32 > 0:
+        tree.set_precision("simt_fp32")
+        stream, _ = _serve_stream(w, args.serve_requests_fp32, SERVE_RATE, w.seed, pool, dev)
+        out["simt_fp32"] = {"arrivals_per_s": SERVE_RATE, **_serve_run(tree, Wres, stream, w.N, warm)}
+        out["split_over_fp32_targets_per_s"] = cap / out["simt_fp32"]["targets_per_s"]
     tree.close()
     return out
 
@@ -609,8 +679,15 @@ def main():
     d = w.d
     sec = ms_kernel / 1e3
     smax = (clk or {}).get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0
-    roof = roofline(P, d, r, args.precision, sec, peaks, smax)
+    g16 = args.precision == "fp16x3" and d <= 64 and info["fp16_centering"] == 2
+    roof = roofline(P, d, r, args.precision, sec, peaks, smax, arg_on_tensor=g16, weights_on_tensor=g16 and r > 4)
     roof["traffic"] = None
+    # the plain-FP32 comparator (the serving comparison's other side) against
+    # its own roofline: one Evaluate kernel launch timed in accuracy()
+    fp32_cmp = None
+    if acc.get("fp32_kernel_ms"):
+        rf = roofline(P, d, r, "simt_fp32", acc["fp32_kernel_ms"] / 1e3, peaks, smax)
+        fp32_cmp = {"kernel": "eval_simt_kernel", "ms": acc["fp32_kernel_ms"], "roofline": rf}
     roof["kernel"] = ("eval_simt_kernel" if args.precision == "simt_fp32" else
                       "eval_tcw_kernel" if d > 64 else
                       ("eval_g16_kernel" if info["fp16_centering"] == 2 else "eval_tc16_kernel")
@@ -648,7 +725,7 @@ def main():
             "eps2_vs_direct": acc["eps2_vs_direct"], "eps_kappa_vs_direct": acc["eps_kappa_vs_direct"],
             "hr": acc.get("hr"),
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk, "roofline": roof,
-            "cpu_baseline": cpu, "serving": None,
+            "cpu_baseline": cpu, "serving": None, "fp32_comparator": fp32_cmp,
             "autotune": {"chosen": next((c for c in tune if c["chosen"]), None), "candidates": tune},
             "work": {"pairs_algorithmic": P, "pairs_computed": info["pairs_computed"],
                      "near_per_target": info["near_total"] / N, "far_per_target": info["far_total"] / N,
@@ -662,6 +739,8 @@ def main():
     del Xd, Wd, U
     if rank == 0 and world == 1 and args.serve_requests > 0:
         line["serving"] = serving(args, dev, args.precision)
+        if fp32_cmp:
+            line["serving"]["fp32_comparator_roofline_frac"] = fp32_cmp["roofline"]["frac"]
     if rank == 0 and world == 1 and extra_default(args):
         try:
             line["prune_table"] = prune_table(dev)

@@ -340,10 +340,11 @@ askit_status askit_footprint(askit_tree t, int32_t kind, int64_t n, int32_t r, s
  *     neighbors up to the last rank z whose kernel value exceeds e^-kappa_cut,
  *     kappa_i = 1 + max{z : c D(i, N_i[z]) / h^2 < kappa_cut} (0 if none),
  *     decided in FP64; out-of-sample targets likewise (0: all kappa).
- * Blocks until the lists are rebuilt (waits for the device first).  The
- * weights of the tree and of every weight context must be set again before
- * they are evaluated (NOT_READY otherwise when the lists grew), and graphs
- * captured before must be destroyed.
+ * Blocks until the lists are rebuilt (waits for the device first).  Skeleton
+ * weights do not depend on the lists and stay valid; a weight context (the
+ * tree's own included) whose partial-sum buffer is smaller than the new
+ * lists returns NOT_READY from its evaluations until its weights are set
+ * again.  Graphs captured before must be destroyed.
  */
 askit_status askit_set_pruning(askit_tree t, int32_t far_height, double kappa_cut, void *stream);
 

@@ -151,7 +151,7 @@ struct WeightCtx {
     float *Ws = nullptr;       // [rows of the skeleton pool, r] skeleton weights
     float *partial = nullptr;  // [in-sample entries, r_cap]
     float4 *colv = nullptr;    // [n_sub, 128] per-sub-block column data (16-bit tensor-core path)
-    float *colw = nullptr;     // [n_sub, 128, 16] per-sub-block weights (r > 1)
+    float *colw = nullptr;     // [n_sub, 128 * 16 + 16] per-sub-block weights (r > 1)
     int64_t ent_cap = 0;       // entries the partial sums hold
     bool ready = false;
     DevArena arena;

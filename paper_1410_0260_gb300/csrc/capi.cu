@@ -989,6 +989,9 @@ askit_status askit_footprint(askit_tree t, int32_t kind, int64_t n, int32_t r, s
     if (kind == 0) {
         // a weight context: W in tree order, skeleton weights, partials
         b = sizeof(float) * ((size_t)t->N_pad * r + (size_t)srows * r + (size_t)t->wl_entries_max * r);
+        // the 16-bit tensor-core kernels' per-sub-block column data and weights
+        if (t->n_sub > 0 && t->d <= TC_K)
+            b += sizeof(float4) * (size_t)t->n_sub * 128 + (r > 1 ? sizeof(float) * (size_t)t->n_sub * (128 * 16 + 16) : 0);
     } else {
         // an out-of-sample batch of n targets: queries, kNN, prune sets and
         // work lists (entries estimated from the in-sample rate, doubled)

@@ -21,7 +21,14 @@
 //     m_j = -sc_j / tau, v_j = -sc_j n_j / kappa (tau, kappa powers of 2
 //     balancing the factors), whose product is -sc_j (n_i + n_j) to the
 //     split's precision.
-// So the epilogue is an ex2 on MUFU and one weight FMA per pair.  The price
+// So the epilogue is an ex2 on MUFU and, for r <= 4, r weight FMAs per pair.
+// For r > 4 the weight sums run on the tensor cores as well: the epilogue
+// writes k 2^14, split into FP16 hi + lo, back over the argument's TMEM
+// columns, and a second MMA with A read from TMEM multiplies it with the
+// sub-block's weights, split the same way after scaling every vector by a
+// power of 2 (hi*lo + lo*hi + hi*hi, FP32 accumulation), into a 16-column
+// accumulator: one ex2 and a few conversions per pair instead of r FMAs and
+// r/4 shared-memory loads of the weights.  The price
 // is precision: the terms 2 sc (x - xbar).(y - xbar) and sc n are of the size
 // of sc R^2 (R = the data's spread around xbar) and are rounded in FP32, so
 // the exponent carries an error of a few 2^-24 sc R^2; the per-sub-block
@@ -41,11 +48,15 @@
 // One CTA per SM, 352 threads:
 //   warps 0-7  two epilogue groups, each summing whole sub-blocks (alternate
 //              items, or the two sub-blocks of a paired item): tcgen05.ld of
-//              their 32 TMEM lanes (two buffers), ex2 on MUFU, weight sums,
-//              one partial sum per (target, sub-block) entry;
+//              their 32 TMEM lanes (two buffers), ex2 on MUFU, weight sums
+//              (r > 4: the split exponentials stored back to TMEM, then the
+//              weight MMA's sums loaded), one partial sum per (target,
+//              sub-block) entry;
 //   warp 8     TMEM allocation; lane 0 loads each sub-block (TMA tiles of its
 //              split rows, bulk copies of its norm block and weights) and
-//              issues the tcgen05.mma instructions;
+//              issues the tcgen05.mma instructions (r > 4: an item's weight
+//              MMAs two items after its argument MMAs, once the epilogue has
+//              stored its exponentials);
 //   warps 9-10 copy each item's target rows into NA stages (NA - 2 items'
 //              copies in flight).
 // Every mbarrier wait is bounded (ASK_DEV_TIMEOUT on expiry, all roles leave,
@@ -66,7 +77,7 @@ constexpr int G_ROWS = 128;
 constexpr int G_REGION = G_ROWS * 128;   // 128 rows x 128 bytes (64 FP16), 128-byte swizzle
 constexpr int GX_REGION = G_ROWS * 32;   // 128 rows x 32 bytes (16 FP16): the norm block
 constexpr int GX_K = 16;                 // columns of the norm block
-constexpr uint32_t G_TMEM_COLS = 512;    // four 128-column (two 256-column) FP32 accumulators
+constexpr uint32_t G_TMEM_COLS = 512;    // 4 x 128 (2 x 256) columns; r > 4: 3 x 128 + 3 x 16
 
 // Shared-memory descriptor of a K-major operand without swizzle: 8-row x
 // 16-byte core matrices stored contiguously, the next core matrix along K
@@ -81,17 +92,38 @@ __host__ __device__ __forceinline__ uint32_t nx_off(int r, int c) {
     return (uint32_t)((r >> 3) * 256 + c * 128 + (r & 7) * 16);
 }
 
-// NA: target-row stages; NB: sub-blocks per item (1, or 2 for paired items);
-// NACC = 4 / NB TMEM accumulators of 128 NB columns.
+// Weights of a sub-block for the weight MMA (r > 4): W' = w 2^-e_z split into
+// FP16 hi and lo, each [16 vectors x 128 source rows] K-major without swizzle
+// (core matrices of 8 vectors x 8 rows; the next along the rows 128 bytes on,
+// the next 8 vectors 2048 bytes on), then 16 FP32 factors 2^(e_z - G_KSHIFT).
+constexpr int GW_SPLIT = 4096;                  // bytes of one split
+constexpr int GW_BYTES = 2 * GW_SPLIT + 64;     // hi, lo, factors
+constexpr int G_KSHIFT = 14;                    // exponentials enter the MMA as k 2^14
+__host__ __device__ __forceinline__ uint32_t gw_off(int z, int row) {
+    return (uint32_t)((z >> 3) * 2048 + (row >> 3) * 128 + (z & 7) * 16 + (row & 7) * 2);
+}
+__device__ __forceinline__ uint64_t gw_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(2048 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// NA: target-row stages; NB: sub-blocks per item (1, or 2 for paired items).
+// r <= 4 (WMMA false): NACC = 4 / NB TMEM accumulators of 128 NB columns and
+// the weight sums on the FP32 pipe.  r > 4 (WMMA, NB = 1): three 128-column
+// accumulators for the exponent's argument (later overwritten by the split
+// exponentials, the A operand of the weight MMA) and three 16-column
+// accumulators of the weight sums from column 384.
 template <int RC, int NA, int NB>
 struct SG {
-    static constexpr int NACC = 4 / NB;
+    static constexpr bool WMMA = RC > 4;
+    static_assert(!WMMA || NB == 1, "weight MMAs take single sub-blocks");
+    static constexpr int NACC = WMMA ? 3 : 4 / NB;
     static constexpr int B_HI = 0, B_LO = NB * G_REGION;    // NB x 128 rows each, contiguous
     static constexpr int B_X = 2 * NB * G_REGION;           // NB x 128 rows of the norm block
     static constexpr int A0 = B_X + NB * GX_REGION;         // stage s at A0 + s ASTAGE: hi, lo, norm block
     static constexpr int ASTAGE = 2 * G_REGION + GX_REGION;
     static constexpr int BLK = A0 + NA * ASTAGE;            // [2] per-block weight slots
-    static constexpr int BLKSLOT = NB * 128 * RC * 4;       // float [128 NB][RC]
+    static constexpr int BLKSLOT = WMMA ? GW_BYTES : NB * 128 * RC * 4;   // float [128 NB][RC], or split weights
     static constexpr int BAR = BLK + 2 * BLKSLOT;           // 40 mbarriers
     static constexpr int MISC = BAR + 40 * 8;               // tmem address, abort flag
     static constexpr int BYTES = MISC + 16;
@@ -139,6 +171,8 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
     auto BAR_BLK_EMPTY = [&](int s) { return bar0 + 8 * (12 + s); };  // epilogue done with slot s (NEPI)
     auto BAR_T_FULL = [&](int a) { return bar0 + 8 * (16 + a); };     // accumulator a complete (commit)
     auto BAR_T_EMPTY = [&](int a) { return bar0 + 8 * (20 + a); };    // epilogue drained accumulator a (NITEM)
+    auto BAR_K_READY = [&](int a) { return bar0 + 8 * (24 + a); };    // split exponentials of a in TMEM (128)
+    auto BAR_W_FULL = [&](int a) { return bar0 + 8 * (28 + a); };     // weight sums of a complete (commit)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + S::MISC);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + S::MISC + 4);
 
@@ -157,6 +191,10 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
         for (int a = 0; a < NACC; ++a) {
             mbar_init(BAR_T_FULL(a), 1);
             mbar_init(BAR_T_EMPTY(a), NITEM);
+            if constexpr (S::WMMA) {
+                mbar_init(BAR_K_READY(a), 128);
+                mbar_init(BAR_W_FULL(a), 1);
+            }
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -215,6 +253,73 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                 const int e_out = (NB == 2 && eg == 1) ? (pb >= 0 ? args.items[f0 + (it - i0)].e0 : 0) : item.e0;
                 if (!mbar_wait(BAR_T_FULL(a4), (li / NACC) & 1, abort_flag, args.status, args.spin)) goto epi_done;
                 tc_fence_after();
+                if constexpr (S::WMMA) {
+                    // k 2^14 split into FP16 hi + lo, stored over the argument
+                    // columns it came from: chunk c's 32 columns take its 32 hi
+                    // values (two per column), then its 32 lo values; the MMA
+                    // warp multiplies them with the sub-block's split weights
+                    const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a4 * 128);
+                    if (q * 32 < item.cnt) {   // warp-uniform
+                        auto split_store = [&](int c, const uint32_t (&gr)[32]) {
+                            uint32_t hw[16], lw[16];
+#pragma unroll
+                            for (int m = 0; m < 16; ++m) {
+                                const float k0 = ex2_approx(__uint_as_float(gr[2 * m])) * (float)(1 << G_KSHIFT);
+                                const float k1 = ex2_approx(__uint_as_float(gr[2 * m + 1])) * (float)(1 << G_KSHIFT);
+                                const __half2 h = __floats2half2_rn(k0, k1);
+                                const float2 hf = __half22float2(h);
+                                const __half2 l = __floats2half2_rn(k0 - hf.x, k1 - hf.y);
+                                hw[m] = *reinterpret_cast<const uint32_t *>(&h);
+                                lw[m] = *reinterpret_cast<const uint32_t *>(&l);
+                            }
+                            tmem_st16(tbase + (uint32_t)(c * 32), hw);
+                            tmem_st16(tbase + (uint32_t)(c * 32 + 16), lw);
+                        };
+                        // chunk c + 1's load is in flight while chunk c is split;
+                        // a chunk's stores go to its own (already loaded) columns
+                        uint32_t ga[32], gb[32];
+                        tmem_ld32_async(tbase, ga);
+                        tmem_wait_pin(ga);
+#pragma unroll 1
+                        for (int c = 0; c < c_hi; c += 2) {
+                            const bool h1 = c + 1 < c_hi, h2 = c + 2 < c_hi;   // warp-uniform
+                            if (h1) tmem_ld32_async(tbase + (uint32_t)((c + 1) * 32), gb);
+                            split_store(c, ga);
+                            if (h1) {
+                                tmem_wait_pin(gb);
+                                if (h2) tmem_ld32_async(tbase + (uint32_t)((c + 2) * 32), ga);
+                                split_store(c + 1, gb);
+                                if (h2) tmem_wait_pin(ga);
+                            }
+                        }
+                        tmem_st_wait();
+                    }
+                    tc_fence_before();
+                    mbar_arrive(BAR_K_READY(a4));
+                    if (!mbar_wait(BAR_W_FULL(a4), (li / NACC) & 1, abort_flag, args.status, args.spin)) goto epi_done;
+                    tc_fence_after();
+                    float u[16];
+                    if (q * 32 < item.cnt)
+                        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(3 * 128 + a4 * 16), u);
+                    tc_fence_before();
+                    mbar_arrive(BAR_T_EMPTY(a4));
+                    if (row < item.cnt) {
+                        // the sums of w' k 2^14 back to w k: the sub-block's factors
+                        const float *fac = cwp + 2 * GW_SPLIT / 4;
+                        float *p = args.partial + (int64_t)(item.e0 + row) * args.r;
+                        if (args.r == 16) {
+#pragma unroll
+                            for (int z = 0; z < 16; z += 4)
+                                *reinterpret_cast<float4 *>(p + z) = make_float4(u[z] * fac[z], u[z + 1] * fac[z + 1],
+                                                                                 u[z + 2] * fac[z + 2], u[z + 3] * fac[z + 3]);
+                        } else {
+#pragma unroll
+                            for (int z = 0; z < 16; ++z)
+                                if (z < args.r) p[z] = u[z] * fac[z];
+                        }
+                    }
+                    continue;
+                }
                 float acc[RC];
 #pragma unroll
                 for (int z = 0; z < RC; ++z) acc[z] = 0.f;
@@ -400,7 +505,40 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
         int li = 0, lb = 0, b_issued = 0;
         int blk_last[2] = {-1, -1};   // last block whose weights went to slot 0 / 1
         int li_done = -1;             // last item whose MMAs were committed
+        // r > 4: the weight MMAs of an item wait for the epilogue's split
+        // exponentials, so they are issued two items behind its argument
+        // MMAs, from a queue of (item, weight slot, K steps, block)
+        int wq_li[4], wq_bs[4], wq_nk[4], wq_lb[4];
+        int wq_h = 0, wq_n = 0, w_done = -1;
+        auto issue_w = [&]() -> bool {
+            const int e = wq_h & 3, pli = wq_li[e], a = pli % NACC;
+            if (!mbar_wait(BAR_K_READY(a), (pli / NACC) & 1, abort_flag, args.status, args.spin)) return false;
+            tc_fence_after();
+            constexpr uint32_t idesc_w = make_idesc(0u, G_ROWS, 16);
+            const uint32_t dw = tmem + (uint32_t)(3 * 128 + a * 16), ak = tmem + (uint32_t)(a * 128);
+            const uint32_t wh = sbase + S::BLK + wq_bs[e] * S::BLKSLOT, wl = wh + GW_SPLIT;
+            // 16 source rows per MMA; the cross products first, then hi * hi
+            for (int ks = 0; ks < wq_nk[e]; ++ks) {
+                const uint32_t ch = (uint32_t)(32 * (ks >> 1) + 8 * (ks & 1));
+                tc_mma_ts(dw, ak + ch + 16, gw_desc(wh + 256 * ks), idesc_w, ks > 0);   // k lo * w' hi
+                tc_mma_ts(dw, ak + ch, gw_desc(wl + 256 * ks), idesc_w, 1);             // k hi * w' lo
+            }
+            for (int ks = 0; ks < wq_nk[e]; ++ks) {
+                const uint32_t ch = (uint32_t)(32 * (ks >> 1) + 8 * (ks & 1));
+                tc_mma_ts(dw, ak + ch, gw_desc(wh + 256 * ks), idesc_w, 1);             // k hi * w' hi
+            }
+            tc_commit(BAR_W_FULL(a));
+            w_done = pli;
+            ++wq_h;
+            --wq_n;
+            return true;
+        };
         for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci, ++lb) {
+            // the weight slot about to be reused was read by the weight MMAs
+            // of the block two back: issue those first
+            if constexpr (S::WMMA)
+                while (wq_n > 0 && wq_lb[wq_h & 3] <= lb - 2)
+                    if (!issue_w()) goto mma_done;
             const int b = args.cta_blocks[ci];
             const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
             const EvalItem first = args.items[i0];
@@ -427,9 +565,10 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
             }
             bulk_copy(sbase + S::B_X, args.bx + (int64_t)first.cidx * G_ROWS * GX_K, (uint32_t)(nsb * GX_REGION),
                       BAR_B_FULL);
-            const uint32_t wbytes = (uint32_t)(nsb * 128 * RC * 4);
+            const uint32_t wbytes = S::WMMA ? (uint32_t)GW_BYTES : (uint32_t)(nsb * 128 * RC * 4);
             mbar_expect_tx(BAR_BLK_FULL(bs), wbytes);
-            bulk_copy(sbase + S::BLK + bs * S::BLKSLOT, args.colw + (int64_t)first.cidx * 128 * RC, wbytes,
+            bulk_copy(sbase + S::BLK + bs * S::BLKSLOT,
+                      reinterpret_cast<const uint8_t *>(args.colw) + (int64_t)first.cidx * S::BLKSLOT / NB, wbytes,
                       BAR_BLK_FULL(bs));
             for (int it = i0; it < i1; ++it, ++li) {
                 const int sa = li % NA, a4 = li % NACC;
@@ -461,8 +600,21 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                 tc_commit(BAR_T_FULL(a4));
                 if (it == i1 - 1) tc_commit(BAR_B_EMPTY);
                 li_done = li;
+                if constexpr (S::WMMA) {
+                    const int e = (wq_h + wq_n) & 3;
+                    wq_li[e] = li;
+                    wq_bs[e] = bs;
+                    wq_nk[e] = 2 * ((ncols + 31) >> 5);   // the 32-column chunks the epilogue split
+                    wq_lb[e] = lb;
+                    ++wq_n;
+                    while (wq_n > 2)
+                        if (!issue_w()) goto mma_done;
+                }
             }
         }
+        if constexpr (S::WMMA)
+            while (wq_n > 0)
+                if (!issue_w()) goto mma_done;
     mma_done:
         // after an abort: the last sub-block's tiles and the latest weights of
         // each slot may still be landing, and MMAs may still be writing TMEM
@@ -472,6 +624,7 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
         for (int k = 0; k < 2; ++k)
             if (blk_last[k] >= 0) mbar_drain(BAR_BLK_FULL(k), (blk_last[k] >> 1) & 1);
         if (li_done >= 0) mbar_drain(BAR_T_FULL(li_done % NACC), (li_done / NACC) & 1);
+        if (S::WMMA && w_done >= 0) mbar_drain(BAR_W_FULL(w_done % NACC), (w_done / NACC) & 1);
     }
     tc_fence_before();
     __syncthreads();
@@ -495,6 +648,47 @@ __global__ void g16_cols_kernel(const int64_t *sb_row0, const int32_t *sb_nr, in
     const float *w = (far ? Ws : Wt) + row * r;
 #pragma unroll
     for (int z = 0; z < RC; ++z) colw[(b * 128 + t) * RC + z] = (valid && z < r) ? w[z] : 0.f;
+}
+
+// Split weights of every sub-block for the weight MMA (r > 4): thread t of
+// block b takes source row t.  Per vector z the sub-block's largest |w| sets
+// e_z with max |w| 2^-e_z in [2^13, 2^14); w' = w 2^-e_z (exact) is split into
+// FP16 hi = rn(w') and lo = rn(w' - hi), and the factor 2^(e_z - 14) turns the
+// MMA's sums of (k 2^14) w' back into sums of k w.  Rows past the sub-block
+// and vectors past r are zero.
+__global__ void g16_wcols_kernel(const int64_t *sb_row0, const int32_t *sb_nr, int64_t n_leaf_sub, const float *Wt,
+                                 const float *Ws, int r, uint8_t *colw) {
+    __shared__ float wmax[4][16];
+    const int64_t b = blockIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const bool valid = t < sb_nr[b];
+    const float *w = (b >= n_leaf_sub ? Ws : Wt) + (sb_row0[b] + t) * r;
+    float v[16];
+#pragma unroll
+    for (int z = 0; z < 16; ++z) {
+        v[z] = (valid && z < r) ? w[z] : 0.f;
+        float m = fabsf(v[z]);
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) wmax[warp][z] = m;
+    }
+    __syncthreads();
+    uint8_t *out = colw + b * GW_BYTES;
+#pragma unroll
+    for (int z = 0; z < 16; ++z) {
+        const float m = fmaxf(fmaxf(wmax[0][z], wmax[1][z]), fmaxf(wmax[2][z], wmax[3][z]));
+        int e = 0;
+        if (m > 0.f) {
+            int ex;
+            frexpf(m, &ex);              // m = f 2^ex, f in [1/2, 1)
+            e = ex - G_KSHIFT;
+        }
+        const float wp = ldexpf(v[z], -e);
+        const __half hi = __float2half_rn(wp);
+        const __half lo = __float2half_rn(wp - __half2float(hi));
+        *reinterpret_cast<__half *>(out + gw_off(z, t)) = hi;
+        *reinterpret_cast<__half *>(out + GW_SPLIT + gw_off(z, t)) = lo;
+        if (t == 0) reinterpret_cast<float *>(out + 2 * GW_SPLIT)[z] = ldexpf(1.f, e - G_KSHIFT);
+    }
 }
 
 // Tensor maps over the tree's split source rows (64 x 128 boxes, 128-byte
@@ -541,9 +735,15 @@ template <int RC>
 askit_status run_g16(askit_tree t, const WeightCtx &c, G16State *st, G16Args a, const WorkLists &w,
                      cudaStream_t s) {
     // weights in the sub-blocks' row order: r = 1 in the first 128 floats of
-    // each sub-block's column-data slot, r > 1 in the per-sub-block weights
+    // each sub-block's column-data slot, 1 < r <= 4 in the per-sub-block
+    // weights, r > 4 split for the weight MMA
     float *colw = RC == 1 ? reinterpret_cast<float *>(c.colv) : c.colw;
-    g16_cols_kernel<RC><<<(unsigned)t->n_sub, 128, 0, s>>>(t->sb_row0, t->sb_nr, t->n_leaf_sub, c.Wt, c.Ws, c.r, colw);
+    if constexpr (SG<RC, 3, 1>::WMMA)
+        g16_wcols_kernel<<<(unsigned)t->n_sub, 128, 0, s>>>(t->sb_row0, t->sb_nr, t->n_leaf_sub, c.Wt, c.Ws, c.r,
+                                                            reinterpret_cast<uint8_t *>(colw));
+    else
+        g16_cols_kernel<RC><<<(unsigned)t->n_sub, 128, 0, s>>>(t->sb_row0, t->sb_nr, t->n_leaf_sub, c.Wt, c.Ws, c.r,
+                                                               colw);
     ASK_LAUNCH();
     a.colw = colw;
     ASK_TRY(ktimer_mark(t, s, false));

@@ -4,12 +4,16 @@
 //   U_i = union over j in {i} U N_i of the ancestors of leaf(j)
 // (eq. (2.5): those nodes cannot be pruned).  The leaves of U_i are summed
 // directly (Near(i)); every child of a node of U_i that is not itself in U_i
-// is pruned and contributes through its skeleton (Far(i)).  The GPU groups
-// targets into tiles of 128 consecutive rows and turns the union of the
-// tile's Near and Far sets into work items (tile, source block, 128-bit mask
-// of the targets that need the block); one persistent kernel then runs all
-// items.  Source blocks are contiguous rows: a leaf's points in the
-// tree-ordered coordinate array, or a node's skeleton in the skeleton pool.
+// is pruned and contributes through its skeleton (Far(i)).  The GPU forms
+// every (target, source sub-block) pair of these sets -- an entry -- sorts
+// the entries by (sub-block, target) and cuts each sub-block's run into work
+// items of at most 128 targets (EvalItem: the sub-block's rows, the item's
+// first entry and count), so every item is a dense tile of targets that all
+// need the whole sub-block; one persistent kernel then runs all items and
+// writes one partial sum per entry, reduced per target in a fixed order.
+// Source sub-blocks are at most 128 contiguous rows: of a leaf's points in
+// the tree-ordered coordinate array, or of a node's skeleton in the
+// skeleton pool.
 #include <limits.h>
 #include <math.h>
 

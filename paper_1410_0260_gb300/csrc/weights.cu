@@ -135,7 +135,9 @@ askit_status weights_reserve(askit_tree t, WeightCtx &c, int r, cudaStream_t s) 
     // per-sub-block column data of the 16-bit tensor-core kernel
     if (t->n_sub > 0 && t->d <= TC_K) {
         ASK_TRY(c.arena.alloc(&c.colv, (size_t)t->n_sub * 128));
-        if (r > 1) ASK_TRY(c.arena.alloc(&c.colw, (size_t)t->n_sub * 128 * 16));
+        // [n_sub, 128, 16] floats, or (r > 4, the global-centered kernel's
+        // weight MMA) split FP16 weights and 16 factors per sub-block
+        if (r > 1) ASK_TRY(c.arena.alloc(&c.colw, (size_t)t->n_sub * (128 * 16 + 16)));
     }
     ASK_CUDA(cudaMemsetAsync(c.Wt, 0, sizeof(float) * t->N_pad * r, s));
     ASK_CUDA(cudaMemsetAsync(c.Ws, 0, sizeof(float) * srows * r, s));

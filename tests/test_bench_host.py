@@ -31,10 +31,16 @@ def test_fma_bound_for_sixteen_weight_vectors():
 
 
 def test_mufu_bound_when_the_contraction_is_short():
-    # d = 8: three split products of length 8 take less than one ex2
-    roof = bench.roofline(1e9, 8, 1, "fp16x3", 1e-3, PEAKS, 2070.0)
+    # d = 4: three split products of length 4 take less than one ex2
+    roof = bench.roofline(1e9, 4, 1, "fp16x3", 1e-3, PEAKS, 2070.0)
     assert roof["bound"] == "alu" and roof["unit"] == "Tex2/s"
-    assert roof["peak"] == pytest.approx(152 * 16 * 2070e6 / 1e12)
+    assert roof["peak"] == pytest.approx(152 * 32 * 2070e6 / 1e12)
+
+
+def test_tensor_bound_at_d64_with_the_full_ex2_rate():
+    # 384 tensor flops a pair at the measured bf16 rate outlast one ex2 at 32/clk/SM
+    roof = bench.roofline(12.5e9, 64, 1, "fp16x3", 3.5e-3, PEAKS, 2070.0, arg_on_tensor=True)
+    assert roof["bound"] == "tensor"
 
 
 def test_tf32_peak_and_plain_fp32():
@@ -52,3 +58,28 @@ def test_traffic_record_follows_the_kernel_source():
         got = bench.measured_traffic(kernel, r["workload"])
         assert got == (r["bytes_per_launch"] if current else None)
         assert bench.measured_traffic(kernel, r["workload"] + " (another size)") is None
+
+
+def test_fma_count_when_the_tensor_cores_form_the_argument():
+    # the global-centered kernel: only the r weight FMAs remain in the epilogue
+    P, sec = 4.392e11, 0.9
+    roof = bench.roofline(P, 64, 16, "fp16x3", sec, PEAKS, 2070.0, arg_on_tensor=True)
+    assert roof["bound"] == "alu" and roof["achieved"] == pytest.approx(P * 16 / sec / 1e12)
+
+
+def test_mean_request_targets_matches_the_request_stream():
+    """The sustained serving rate divides capacity by the mean request size:
+    the closed form must agree with the stream's own draws."""
+    from paper_1410_0260_gb300 import workloads as wl
+    N = 1 << 21
+    spec = wl.request_stream(100_000, 200.0, seed=3)
+    sample = sum(N * s if k == "weights" else s for _, k, s in spec) / len(spec)
+    assert bench._mean_request_targets(N) == pytest.approx(sample, rel=0.02)
+
+
+def test_weight_sums_on_the_tensor_cores():
+    # r = 16 with the weight MMA: 3 x 2 x (64 + 16) tensor flops a pair, no FMAs
+    P, sec = 4.392e11, 0.44
+    roof = bench.roofline(P, 64, 16, "fp16x3", sec, PEAKS, 2070.0, arg_on_tensor=True, weights_on_tensor=True)
+    assert roof["bound"] == "tensor"
+    assert roof["achieved"] == pytest.approx(P * 3 * 2 * 80 / sec / 1e12)

@@ -277,6 +277,14 @@ def test_multi_rhs_16_on_the_8m_recipe_shape():
     for prec in ("simt_fp32", "fp16x3", "fp16x3_block", "bf16x3"):
         Ug, Uo = eval_both(otree, gtree, W, prec)
         assert_u(Ug, Uo, TOL[prec], prec)
+    # r = 6 (partial sums stored one by one) with columns six decades apart:
+    # each weight vector is scaled on its own before the split, so each
+    # column holds the tolerance by itself
+    W6 = (W[:, :6] * (10.0 ** np.arange(-3, 3))).astype(np.float32)
+    for prec in ("simt_fp32", "fp16x3", "fp16x3_block"):
+        Ug, Uo = eval_both(otree, gtree, W6, prec)
+        for z in range(6):
+            assert_u(Ug[:, z], Uo[:, z], TOL[prec], (prec, z))
 
 
 def test_d1000_variable_bandwidth_on_the_1000d_recipe_shape():
