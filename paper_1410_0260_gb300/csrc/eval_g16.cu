@@ -26,9 +26,12 @@
 // writes k 2^14, split into FP16 hi + lo, back over the argument's TMEM
 // columns, and a second MMA with A read from TMEM multiplies it with the
 // sub-block's weights, split the same way after scaling every vector by a
-// power of 2 (hi*lo + lo*hi + hi*hi, FP32 accumulation), into a 16-column
-// accumulator: one ex2 and a few conversions per pair instead of r FMAs and
-// r/4 shared-memory loads of the weights.  The price
+// power of 2 (k hi against [w' hi | w' lo] and k lo against w' hi, FP32
+// accumulation), into a 32-column accumulator whose halves the epilogue adds:
+// one ex2 and a few conversions per pair instead of r FMAs and r/4
+// shared-memory loads of the weights.  An argument accumulator is free again
+// once its item's weight MMAs have read it, so the tensor cores never wait
+// for the epilogue's write-out.  The price
 // is precision: the terms 2 sc (x - xbar).(y - xbar) and sc n are of the size
 // of sc R^2 (R = the data's spread around xbar) and are rounded in FP32, so
 // the exponent carries an error of a few 2^-24 sc R^2; the per-sub-block
@@ -77,7 +80,7 @@ constexpr int G_ROWS = 128;
 constexpr int G_REGION = G_ROWS * 128;   // 128 rows x 128 bytes (64 FP16), 128-byte swizzle
 constexpr int GX_REGION = G_ROWS * 32;   // 128 rows x 32 bytes (16 FP16): the norm block
 constexpr int GX_K = 16;                 // columns of the norm block
-constexpr uint32_t G_TMEM_COLS = 512;    // 4 x 128 (2 x 256) columns; r > 4: 3 x 128 + 3 x 16
+constexpr uint32_t G_TMEM_COLS = 512;    // 4 x 128 (2 x 256) columns; r > 4: 3 x 128 + 4 x 32
 
 // Shared-memory descriptor of a K-major operand without swizzle: 8-row x
 // 16-byte core matrices stored contiguously, the next core matrix along K
@@ -99,6 +102,7 @@ __host__ __device__ __forceinline__ uint32_t nx_off(int r, int c) {
 constexpr int GW_SPLIT = 4096;                  // bytes of one split
 constexpr int GW_BYTES = 2 * GW_SPLIT + 64;     // hi, lo, factors
 constexpr int G_KSHIFT = 14;                    // exponentials enter the MMA as k 2^14
+constexpr int GW_NDW = 4;                       // weight-sum accumulators (32 columns each)
 __host__ __device__ __forceinline__ uint32_t gw_off(int z, int row) {
     return (uint32_t)((z >> 3) * 2048 + (row >> 3) * 128 + (z & 7) * 16 + (row & 7) * 2);
 }
@@ -111,8 +115,9 @@ __device__ __forceinline__ uint64_t gw_desc(uint32_t saddr) {
 // r <= 4 (WMMA false): NACC = 4 / NB TMEM accumulators of 128 NB columns and
 // the weight sums on the FP32 pipe.  r > 4 (WMMA, NB = 1): three 128-column
 // accumulators for the exponent's argument (later overwritten by the split
-// exponentials, the A operand of the weight MMA) and three 16-column
-// accumulators of the weight sums from column 384.
+// exponentials, the A operand of the weight MMA) and GW_NDW 32-column
+// accumulators of the weight sums from column 384 (columns 0-15: k hi w' hi +
+// k lo w' hi, 16-31: k hi w' lo).
 template <int RC, int NA, int NB>
 struct SG {
     static constexpr bool WMMA = RC > 4;
@@ -170,9 +175,12 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
     auto BAR_BLK_FULL = [&](int s) { return bar0 + 8 * (10 + s); };   // weights of slot s landed
     auto BAR_BLK_EMPTY = [&](int s) { return bar0 + 8 * (12 + s); };  // epilogue done with slot s (NEPI)
     auto BAR_T_FULL = [&](int a) { return bar0 + 8 * (16 + a); };     // accumulator a complete (commit)
-    auto BAR_T_EMPTY = [&](int a) { return bar0 + 8 * (20 + a); };    // epilogue drained accumulator a (NITEM)
+    // accumulator a free: drained by the epilogue (NITEM), or, r > 4, read by
+    // the item's weight MMAs (commit)
+    auto BAR_T_EMPTY = [&](int a) { return bar0 + 8 * (20 + a); };
     auto BAR_K_READY = [&](int a) { return bar0 + 8 * (24 + a); };    // split exponentials of a in TMEM (128)
-    auto BAR_W_FULL = [&](int a) { return bar0 + 8 * (28 + a); };     // weight sums of a complete (commit)
+    auto BAR_DW_FULL = [&](int k) { return bar0 + 8 * (28 + k); };    // weight sums k complete (commit)
+    auto BAR_DW_EMPTY = [&](int k) { return bar0 + 8 * (32 + k); };   // weight sums k read (128)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + S::MISC);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + S::MISC + 4);
 
@@ -190,12 +198,14 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
         mbar_init(BAR_B_EMPTY, 1);
         for (int a = 0; a < NACC; ++a) {
             mbar_init(BAR_T_FULL(a), 1);
-            mbar_init(BAR_T_EMPTY(a), NITEM);
-            if constexpr (S::WMMA) {
-                mbar_init(BAR_K_READY(a), 128);
-                mbar_init(BAR_W_FULL(a), 1);
-            }
+            mbar_init(BAR_T_EMPTY(a), S::WMMA ? 1 : NITEM);
+            if constexpr (S::WMMA) mbar_init(BAR_K_READY(a), 128);
         }
+        if constexpr (S::WMMA)
+            for (int k = 0; k < GW_NDW; ++k) {
+                mbar_init(BAR_DW_FULL(k), 1);
+                mbar_init(BAR_DW_EMPTY(k), 128);
+            }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -228,6 +238,42 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
         const int q = warp & 3;                    // this warp's TMEM lane quadrant
         const int row = q * 32 + lane;             // TMEM lane = target row of the item
         const int eg = warp >> 2;                  // group
+        // r > 4: an item's weight sums are written out after the group has
+        // split its next item of the same block (their MMAs are issued after
+        // that item's argument MMAs), or at the end of the block
+        int pend_li = -1, pend_e0 = 0, pend_cnt = 0;
+        auto wout = [&](int pl, int e0, int cnt, const float *cw) -> bool {
+            const int k = pl % GW_NDW;
+            if (!mbar_wait(BAR_DW_FULL(k), (pl / GW_NDW) & 1, abort_flag, args.status, args.spin)) return false;
+            tc_fence_after();
+            uint32_t g[32];
+            if (q * 32 < cnt) {   // warp-uniform
+                tmem_ld32_async(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(3 * 128 + k * 32), g);
+                tmem_wait_pin(g);
+            }
+            tc_fence_before();
+            mbar_arrive(BAR_DW_EMPTY(k));
+            if (row < cnt) {
+                // the sums of w' k 2^14 back to w k: the sub-block's factors
+                const float4 *fac = reinterpret_cast<const float4 *>(cw + 2 * GW_SPLIT / 4);
+                float *p = args.partial + (int64_t)(e0 + row) * args.r;
+                auto u = [&](int z, float f) { return (__uint_as_float(g[z]) + __uint_as_float(g[16 + z])) * f; };
+#pragma unroll
+                for (int z = 0; z < 16; z += 4) {
+                    const float4 f = fac[z / 4];
+                    const float4 v = make_float4(u(z, f.x), u(z + 1, f.y), u(z + 2, f.z), u(z + 3, f.w));
+                    if (args.r == 16) {
+                        *reinterpret_cast<float4 *>(p + z) = v;
+                    } else {
+                        if (z < args.r) p[z] = v.x;
+                        if (z + 1 < args.r) p[z + 1] = v.y;
+                        if (z + 2 < args.r) p[z + 2] = v.z;
+                        if (z + 3 < args.r) p[z + 3] = v.w;
+                    }
+                }
+            }
+            return true;
+        };
         int li = 0, lb = 0;
         for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci, ++lb) {
             const int b = args.cta_blocks[ci];
@@ -275,49 +321,24 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                             tmem_st16(tbase + (uint32_t)(c * 32), hw);
                             tmem_st16(tbase + (uint32_t)(c * 32 + 16), lw);
                         };
-                        // chunk c + 1's load is in flight while chunk c is split;
-                        // a chunk's stores go to its own (already loaded) columns
-                        uint32_t ga[32], gb[32];
-                        tmem_ld32_async(tbase, ga);
-                        tmem_wait_pin(ga);
+                        // one chunk at a time (the other group's warp on the same
+                        // sub-partition covers the load's latency); a chunk's
+                        // stores go to its own, already loaded, columns
 #pragma unroll 1
-                        for (int c = 0; c < c_hi; c += 2) {
-                            const bool h1 = c + 1 < c_hi, h2 = c + 2 < c_hi;   // warp-uniform
-                            if (h1) tmem_ld32_async(tbase + (uint32_t)((c + 1) * 32), gb);
+                        for (int c = 0; c < c_hi; ++c) {
+                            uint32_t ga[32];
+                            tmem_ld32_async(tbase + (uint32_t)(c * 32), ga);
+                            tmem_wait_pin(ga);
                             split_store(c, ga);
-                            if (h1) {
-                                tmem_wait_pin(gb);
-                                if (h2) tmem_ld32_async(tbase + (uint32_t)((c + 2) * 32), ga);
-                                split_store(c + 1, gb);
-                                if (h2) tmem_wait_pin(ga);
-                            }
                         }
                         tmem_st_wait();
                     }
                     tc_fence_before();
                     mbar_arrive(BAR_K_READY(a4));
-                    if (!mbar_wait(BAR_W_FULL(a4), (li / NACC) & 1, abort_flag, args.status, args.spin)) goto epi_done;
-                    tc_fence_after();
-                    float u[16];
-                    if (q * 32 < item.cnt)
-                        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(3 * 128 + a4 * 16), u);
-                    tc_fence_before();
-                    mbar_arrive(BAR_T_EMPTY(a4));
-                    if (row < item.cnt) {
-                        // the sums of w' k 2^14 back to w k: the sub-block's factors
-                        const float *fac = cwp + 2 * GW_SPLIT / 4;
-                        float *p = args.partial + (int64_t)(item.e0 + row) * args.r;
-                        if (args.r == 16) {
-#pragma unroll
-                            for (int z = 0; z < 16; z += 4)
-                                *reinterpret_cast<float4 *>(p + z) = make_float4(u[z] * fac[z], u[z + 1] * fac[z + 1],
-                                                                                 u[z + 2] * fac[z + 2], u[z + 3] * fac[z + 3]);
-                        } else {
-#pragma unroll
-                            for (int z = 0; z < 16; ++z)
-                                if (z < args.r) p[z] = u[z] * fac[z];
-                        }
-                    }
+                    if (pend_li >= 0 && !wout(pend_li, pend_e0, pend_cnt, cwp)) goto epi_done;
+                    pend_li = li;
+                    pend_e0 = item.e0;
+                    pend_cnt = item.cnt;
                     continue;
                 }
                 float acc[RC];
@@ -394,6 +415,10 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                     for (int z = 0; z < RC; ++z)
                         if (z < args.r) p[z] = acc[z];
                 }
+            }
+            if constexpr (S::WMMA) {
+                if (pend_li >= 0 && !wout(pend_li, pend_e0, pend_cnt, cwp)) goto epi_done;
+                pend_li = -1;
             }
             mbar_arrive(BAR_BLK_EMPTY(bs));
         }
@@ -511,23 +536,23 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
         int wq_li[4], wq_bs[4], wq_nk[4], wq_lb[4];
         int wq_h = 0, wq_n = 0, w_done = -1;
         auto issue_w = [&]() -> bool {
-            const int e = wq_h & 3, pli = wq_li[e], a = pli % NACC;
+            const int e = wq_h & 3, pli = wq_li[e], a = pli % NACC, k = pli % GW_NDW;
             if (!mbar_wait(BAR_K_READY(a), (pli / NACC) & 1, abort_flag, args.status, args.spin)) return false;
+            if (!mbar_wait(BAR_DW_EMPTY(k), ((pli / GW_NDW) & 1) ^ 1, abort_flag, args.status, args.spin)) return false;
             tc_fence_after();
-            constexpr uint32_t idesc_w = make_idesc(0u, G_ROWS, 16);
-            const uint32_t dw = tmem + (uint32_t)(3 * 128 + a * 16), ak = tmem + (uint32_t)(a * 128);
-            const uint32_t wh = sbase + S::BLK + wq_bs[e] * S::BLKSLOT, wl = wh + GW_SPLIT;
-            // 16 source rows per MMA; the cross products first, then hi * hi
+            constexpr uint32_t idesc32 = make_idesc(0u, G_ROWS, 32), idesc16 = make_idesc(0u, G_ROWS, 16);
+            const uint32_t dw = tmem + (uint32_t)(3 * 128 + k * 32), ak = tmem + (uint32_t)(a * 128);
+            const uint32_t wh = sbase + S::BLK + wq_bs[e] * S::BLKSLOT;
+            // 16 source rows per step: k hi against [w' hi | w' lo] (N = 32:
+            // the lo split's rows follow the hi split's), then k lo against
+            // w' hi into the first 16 columns
             for (int ks = 0; ks < wq_nk[e]; ++ks) {
                 const uint32_t ch = (uint32_t)(32 * (ks >> 1) + 8 * (ks & 1));
-                tc_mma_ts(dw, ak + ch + 16, gw_desc(wh + 256 * ks), idesc_w, ks > 0);   // k lo * w' hi
-                tc_mma_ts(dw, ak + ch, gw_desc(wl + 256 * ks), idesc_w, 1);             // k hi * w' lo
+                tc_mma_ts(dw, ak + ch, gw_desc(wh + 256 * ks), idesc32, ks > 0);
+                tc_mma_ts(dw, ak + ch + 16, gw_desc(wh + 256 * ks), idesc16, 1);
             }
-            for (int ks = 0; ks < wq_nk[e]; ++ks) {
-                const uint32_t ch = (uint32_t)(32 * (ks >> 1) + 8 * (ks & 1));
-                tc_mma_ts(dw, ak + ch, gw_desc(wh + 256 * ks), idesc_w, 1);             // k hi * w' hi
-            }
-            tc_commit(BAR_W_FULL(a));
+            tc_commit(BAR_DW_FULL(k));
+            tc_commit(BAR_T_EMPTY(a));     // the argument's columns are free again
             w_done = pli;
             ++wq_h;
             --wq_n;
@@ -624,7 +649,7 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
         for (int k = 0; k < 2; ++k)
             if (blk_last[k] >= 0) mbar_drain(BAR_BLK_FULL(k), (blk_last[k] >> 1) & 1);
         if (li_done >= 0) mbar_drain(BAR_T_FULL(li_done % NACC), (li_done / NACC) & 1);
-        if (S::WMMA && w_done >= 0) mbar_drain(BAR_W_FULL(w_done % NACC), (w_done / NACC) & 1);
+        if (S::WMMA && w_done >= 0) mbar_drain(BAR_DW_FULL(w_done % GW_NDW), (w_done / GW_NDW) & 1);
     }
     tc_fence_before();
     __syncthreads();
