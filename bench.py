@@ -322,6 +322,45 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+FP64_INSTR_PER_S = 0.625e12   # GB300: 1.25 TFLOP/s FP64 counted with FMAs, one instruction per clock per lane
+
+
+def id_fp64_cost(tree, w, secs):
+    try:
+        return _id_fp64_cost(tree, w, secs)
+    except Exception as e:          # a diagnostic: never lose the bench line to it
+        return {"error": repr(e)}
+
+
+def _id_fp64_cost(tree, w, secs):
+    """FP64 operations of the skeletonization's ID (Section 2.1, as the
+    kernels run it: every product and sum a separate rounded instruction, no
+    FMA, so the pivots match the oracle's) from the skeleton structure, and
+    their rate against GB300's FP64 instruction rate over `secs` seconds (the
+    setup's skeleton stage, which also builds the node lists' samples)."""
+    from paper_1410_0260_gb300 import askit
+    s = tree.structure(askit.STRUCT_SKEL_S).astype(np.int64)
+    c = tree.structure(askit.STRUCT_NCOL).astype(np.int64)
+    N, L = w.N, tree.info()["L"]
+    ops = 0.0
+    for a in range(2, len(s)):
+        depth = a.bit_length() - 1
+        size = -(-N // (1 << depth))                   # the larger node size of the level
+        ell = min(w.s_max + 20, N - size, ) if N > size else 0
+        if ell <= 0 or c[a] <= 0:
+            continue
+        k = np.arange(min(s[a] + 1, ell, c[a]), dtype=np.float64)
+        # each pivot step: trailing norms (mul + add), and for the other
+        # columns the reflector's dot product and update (2 mul/add pairs)
+        ops += float(np.sum(2 * (ell - k) * (c[a] - k) + 4 * (ell - k) * np.maximum(c[a] - k - 1, 0)))
+        ops += float(s[a] * s[a] * (c[a] - s[a]))      # back substitution for P
+        ops += float(ell * c[a] * (3 * w.d + 30))      # the kernel block: distances and the exponential
+    return {"id_fp64_ops": ops, "id_fp64_instr_per_s": ops / secs if secs > 0 else None,
+            "id_fp64_frac": ops / secs / FP64_INSTR_PER_S if secs > 0 else None,
+            "fp64_peak_source": "1.25 TFLOP/s nominal FP64 = 0.625e12 instructions/s; the ID's canonical "
+                                "arithmetic issues no FMA"}
+
+
 def hit_rate(ids, ids_exact):
     """hr of Section 4: the mean fraction of the exact neighbors found."""
     hits = [len(set(a.tolist()) & set(b.tolist())) for a, b in zip(ids, ids_exact)]
@@ -430,6 +469,7 @@ def measure_config(args, dev, key, steps=3, warmup=2):
                     "items": info["n_items"], "target_batches": info["n_batches"],
                     "near_per_target": info["near_total"] / N, "far_per_target": info["far_total"] / N,
                     "setup_s": setup_s, "setup_stage_s": {k: round(v / 1e3, 3) for k, v in info["setup_ms"].items()},
+                    "skeleton_id": id_fp64_cost(tree, w, info["setup_ms"].get("skeletons", 0.0) / 1e3),
                     "device_gb": info["device_bytes"] / 1e9}}
     tree.close()
     del U, Wd
@@ -733,6 +773,7 @@ def main():
                      "target_batches": info["n_batches"],
                      "skeleton_rows": info["skel_total"], "setup_s": setup_s,
                      "setup_stage_s": {k: round(v / 1e3, 3) for k, v in info["setup_ms"].items()},
+                     "skeleton_id": id_fp64_cost(tree, w, info["setup_ms"].get("skeletons", 0.0) / 1e3),
                      "device_gb": info["device_bytes"] / 1e9}}
     graph.close()
     tree.close()

@@ -316,7 +316,9 @@ class Tree:
 
     def set_pruning(self, far_height: int = -1, kappa_cut: float = 0.0, stream=None):
         """Level-restricted far field (far_height >= 0) and adaptive kappa_i
-        (kappa_cut > 0); rebuilds the work lists -- set the weights again."""
+        (kappa_cut > 0); rebuilds the work lists.  Weights stay valid unless
+        the lists outgrow a weight context's partial sums: its evaluations
+        then raise NOT_READY until its weights are set again."""
         _check(load().askit_set_pruning(self._t, int(far_height), float(kappa_cut), _stream(stream)))
 
     def set_fp16_centering(self, mode: str = "auto"):

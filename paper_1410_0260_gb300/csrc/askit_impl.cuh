@@ -121,7 +121,7 @@ struct QuerySplit {
 struct WorkLists {
     int64_t T = 0, n_entries = 0, n_items = 0, n_blocks = 0;
     int64_t *off = nullptr;          // [T + 1] entries of target q: emission slots off[q] .. off[q+1)
-    int64_t *slot_of_emit = nullptr; // [n_entries] sorted position of each emitted entry
+    int32_t *slot_of_emit = nullptr; // [n_entries] sorted position of each emitted entry
     int32_t *tgt = nullptr;          // [n_entries] target slot of each sorted entry
     EvalItem *items = nullptr;       // [n_items], grouped by sub-block
     int32_t *block_off = nullptr;    // [n_blocks + 1] items of each sub-block

@@ -270,11 +270,11 @@ __global__ void emit_kernel(const int32_t *sets, int stride, const int32_t *set_
 
 // After sorting by (sub-block, target): slot of every emitted entry, the
 // target of every sorted entry, and the first entry of every sub-block.
-__global__ void scatter_kernel(const uint64_t *keys, const int64_t *emit_of, int64_t n, int64_t *slot_of_emit,
+__global__ void scatter_kernel(const uint64_t *keys, const int64_t *emit_of, int64_t n, int32_t *slot_of_emit,
                                int32_t *tgt, int64_t *bflag) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n) return;
-    slot_of_emit[emit_of[e]] = e;
+    slot_of_emit[emit_of[e]] = (int32_t)e;
     tgt[e] = (int32_t)(uint32_t)keys[e];
     bflag[e] = (e == 0 || (keys[e] >> 32) != (keys[e - 1] >> 32)) ? 1 : 0;
 }
@@ -321,14 +321,14 @@ __global__ void build_items_kernel(const uint64_t *keys, const int64_t *bflag, c
     items[iidx_excl[e]] = x;
 }
 
-__global__ void reduce_partials_kernel(const float *partial, const int64_t *off, const int64_t *slot_of_emit,
+__global__ void reduce_partials_kernel(const float *partial, const int64_t *off, const int32_t *slot_of_emit,
                                        int64_t T, int r, const int32_t *out_rows, float *U, int64_t ldu) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= T * r) return;
     int64_t q = t / r;
     int z = (int)(t % r);
     float acc = 0.f;
-    for (int64_t o = off[q]; o < off[q + 1]; ++o) acc += partial[slot_of_emit[o] * r + z];
+    for (int64_t o = off[q]; o < off[q + 1]; ++o) acc += partial[(int64_t)slot_of_emit[o] * r + z];
     U[(int64_t)out_rows[q] * ldu + z] = acc;
 }
 
@@ -675,6 +675,13 @@ askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, con
     cudaFreeAsync(tmp, s);
     tmp = nullptr;
     w.n_entries = total;
+    if (total >= ((int64_t)1 << 31)) {
+        // entry offsets (work items, slots) are 32-bit
+        askit_set_error("%lld (target, sub-block) entries in one work list; at most 2^31 - 1 (lower batch_entries)",
+                        (long long)total);
+        rc = ASKIT_ERR_UNSUPPORTED;
+        goto out;
+    }
     WCHK(cudaMallocAsync(&keys, sizeof(uint64_t) * total, s));
     WCHK(cudaMallocAsync(&keys_s, sizeof(uint64_t) * total, s));
     WCHK(cudaMallocAsync(&vals, sizeof(int64_t) * total, s));

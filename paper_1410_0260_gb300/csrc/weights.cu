@@ -18,27 +18,28 @@ __global__ void permute_in_kernel(const float *W, int64_t ldw, int r, const int3
     Wt[e] = W[(int64_t)perm[q] * ldw + z];
 }
 
-// Block (a, y) takes rows [32 y, 32 y + 32) of node a's w~_a (the levels
-// near the root have few nodes, so a node's rows are spread over blocks).
+// Block (a, y) takes rows [rows y, rows y + rows) of node a's w~_a: 32 rows
+// on the wide levels near the leaves, fewer (more blocks a node) on the
+// levels near the root, whose few nodes would otherwise leave the GPU idle.
+// A row's sum is formed the same way whatever the split.
 // The rows v(R) the node's P multiplies (gathered through its pivot order)
 // are staged in shared memory, in chunks of UP_KU rows and RC columns; warps
 // then take rows q of w~_a, lanes split the columns u of P and reduce with
 // shuffles (the same order for every split of the rows).
 constexpr int UP_KU = 1024;
-constexpr int UP_ROWS = 32;
 
 template <int RC>
 __host__ __device__ constexpr int up_stride() { return RC == 1 ? 1 : RC + 4; }   // padded: conflict-free float4 reads
 
 template <int RC>
-__global__ void upward_kernel(int64_t a0, bool leaf_level, int r, const int32_t *nstart, const int32_t *s,
+__global__ void upward_kernel(int64_t a0, bool leaf_level, int r, int rows, const int32_t *nstart, const int32_t *s,
                               const int32_t *ncol, const int64_t *pivoff, const int32_t *piv, const int64_t *poff,
                               const float *P32, const int64_t *spool, const float *Wt, float *Ws) {
     extern __shared__ float vs[];
     constexpr int STR = up_stride<RC>();
     const int64_t a = a0 + blockIdx.x;
     const int sa = s[a], c = ncol[a], nr = c - sa;
-    const int q0 = UP_ROWS * blockIdx.y, q1 = min(sa, q0 + UP_ROWS);
+    const int q0 = rows * blockIdx.y, q1 = min(sa, q0 + rows);
     if (q0 >= sa) return;                                 // block-uniform
     const int32_t *pv = piv + pivoff[a];
     const float *P = P32 + poff[a];
@@ -104,8 +105,10 @@ askit_status launch_upward(askit_tree t, WeightCtx &c, int depth, int r, cudaStr
         cudaFuncSetAttribute(upward_kernel<RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     ASK_CUDA(attr);
     const int64_t a0 = (int64_t)1 << depth;
-    const unsigned ny = (unsigned)((std::max(1, t->prm.s_max) + UP_ROWS - 1) / UP_ROWS);
-    upward_kernel<RC><<<dim3((unsigned)a0, ny), 256, smem, s>>>(a0, depth == t->L, r, t->nstart, t->d_s, t->d_ncol,
+    const int rows = a0 >= 512 ? 32 : (a0 >= 64 ? 8 : 2);     // rows of w~_a a block takes
+    const unsigned ny = (unsigned)((std::max(1, t->prm.s_max) + rows - 1) / rows);
+    const unsigned threads = 32u * (unsigned)std::min(8, rows);
+    upward_kernel<RC><<<dim3((unsigned)a0, ny), threads, smem, s>>>(a0, depth == t->L, r, rows, t->nstart, t->d_s, t->d_ncol,
                                                                 t->d_pivoff, t->piv, t->d_poff, t->P32, t->d_spool,
                                                                 c.Wt, c.Ws);
     ASK_LAUNCH();
