@@ -278,8 +278,9 @@ askit_status askit_graph_destroy(askit_graph g);
  * first), keeps the fastest for later evaluations of this tree, and reports
  * each candidate.  Candidates:
  *   schedule    0: sub-blocks dealt heaviest first to the least-loaded CTA;
- *               1: sub-blocks in tree order, cut into contiguous equal-cost
- *                  ranges (consecutive sub-blocks share targets: L2 reuse);
+ *               1: sub-blocks taken in tree order, each to the least-loaded
+ *                  CTA (the CTAs advance through the tree together, so the
+ *                  sub-blocks in flight share targets: L2 reuse);
  *   stages      target-row stages of the FP16x3 kernels (per sub-block
  *               centering: 2 or 3, 2 with paired items; global centering:
  *               3 or 4);

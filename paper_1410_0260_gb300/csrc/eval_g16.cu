@@ -132,7 +132,7 @@ struct SG {
     static constexpr int BAR = BLK + 2 * BLKSLOT;           // 40 mbarriers
     static constexpr int MISC = BAR + 40 * 8;               // tmem address, abort flag
     static constexpr int BYTES = MISC + 16;
-    static constexpr int THREADS = 352;
+    static constexpr int THREADS = WMMA ? 384 : 352;     // r > 4: warp 11 issues the weight MMAs
     static_assert(A0 % 1024 == 0 && ASTAGE % 1024 == 0, "swizzled stages need 1024-byte alignment");
 };
 
@@ -153,7 +153,7 @@ struct G16Args {
 };
 
 template <int RC, int NA, int NB>
-__global__ void __launch_bounds__(352, 1)
+__global__ void __launch_bounds__(SG<RC, NA, NB>::THREADS, 1)
 eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_constant__ CUtensorMap map_t_lo,
                 const __grid_constant__ CUtensorMap map_s_hi, const __grid_constant__ CUtensorMap map_s_lo,
                 const G16Args args) {
@@ -164,6 +164,7 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
     // (paired items)
     constexpr int NITEM = NB == 2 ? 256 : 128;
     constexpr int W_MMA = 8, W_CP0 = 9;          // MMA warp, first of the two copier warps
+    constexpr int W_WI = 11;                     // r > 4: the weight-MMA issuer
     static_assert(NA >= 3 && NA <= 4, "the copiers keep NA - 2 items in flight");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -339,8 +340,7 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                     pend_li = li;
                     pend_e0 = item.e0;
                     pend_cnt = item.cnt;
-                    continue;
-                }
+                } else {
                 float acc[RC];
 #pragma unroll
                 for (int z = 0; z < RC; ++z) acc[z] = 0.f;
@@ -415,6 +415,7 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                     for (int z = 0; z < RC; ++z)
                         if (z < args.r) p[z] = acc[z];
                 }
+                }
             }
             if constexpr (S::WMMA) {
                 if (pend_li >= 0 && !wout(pend_li, pend_e0, pend_cnt, cwp)) goto epi_done;
@@ -423,7 +424,7 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
             mbar_arrive(BAR_BLK_EMPTY(bs));
         }
     epi_done:;
-    } else if (warp >= W_CP0) {
+    } else if (warp >= W_CP0 && warp < W_CP0 + 2) {
         // ----------------------------------------------------- target-row copiers
         // Copier warp w takes rows 64 w .. 64 w + 63 of every item: lane l
         // holds the target slots of rows 64 w + 2 l and + 1.  Each 16-byte copy
@@ -530,40 +531,7 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
         int li = 0, lb = 0, b_issued = 0;
         int blk_last[2] = {-1, -1};   // last block whose weights went to slot 0 / 1
         int li_done = -1;             // last item whose MMAs were committed
-        // r > 4: the weight MMAs of an item wait for the epilogue's split
-        // exponentials, so they are issued two items behind its argument
-        // MMAs, from a queue of (item, weight slot, K steps, block)
-        int wq_li[4], wq_bs[4], wq_nk[4], wq_lb[4];
-        int wq_h = 0, wq_n = 0, w_done = -1;
-        auto issue_w = [&]() -> bool {
-            const int e = wq_h & 3, pli = wq_li[e], a = pli % NACC, k = pli % GW_NDW;
-            if (!mbar_wait(BAR_K_READY(a), (pli / NACC) & 1, abort_flag, args.status, args.spin)) return false;
-            if (!mbar_wait(BAR_DW_EMPTY(k), ((pli / GW_NDW) & 1) ^ 1, abort_flag, args.status, args.spin)) return false;
-            tc_fence_after();
-            constexpr uint32_t idesc32 = make_idesc(0u, G_ROWS, 32), idesc16 = make_idesc(0u, G_ROWS, 16);
-            const uint32_t dw = tmem + (uint32_t)(3 * 128 + k * 32), ak = tmem + (uint32_t)(a * 128);
-            const uint32_t wh = sbase + S::BLK + wq_bs[e] * S::BLKSLOT;
-            // 16 source rows per step: k hi against [w' hi | w' lo] (N = 32:
-            // the lo split's rows follow the hi split's), then k lo against
-            // w' hi into the first 16 columns
-            for (int ks = 0; ks < wq_nk[e]; ++ks) {
-                const uint32_t ch = (uint32_t)(32 * (ks >> 1) + 8 * (ks & 1));
-                tc_mma_ts(dw, ak + ch, gw_desc(wh + 256 * ks), idesc32, ks > 0);
-                tc_mma_ts(dw, ak + ch + 16, gw_desc(wh + 256 * ks), idesc16, 1);
-            }
-            tc_commit(BAR_DW_FULL(k));
-            tc_commit(BAR_T_EMPTY(a));     // the argument's columns are free again
-            w_done = pli;
-            ++wq_h;
-            --wq_n;
-            return true;
-        };
         for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci, ++lb) {
-            // the weight slot about to be reused was read by the weight MMAs
-            // of the block two back: issue those first
-            if constexpr (S::WMMA)
-                while (wq_n > 0 && wq_lb[wq_h & 3] <= lb - 2)
-                    if (!issue_w()) goto mma_done;
             const int b = args.cta_blocks[ci];
             const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
             const EvalItem first = args.items[i0];
@@ -625,21 +593,8 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                 tc_commit(BAR_T_FULL(a4));
                 if (it == i1 - 1) tc_commit(BAR_B_EMPTY);
                 li_done = li;
-                if constexpr (S::WMMA) {
-                    const int e = (wq_h + wq_n) & 3;
-                    wq_li[e] = li;
-                    wq_bs[e] = bs;
-                    wq_nk[e] = 2 * ((ncols + 31) >> 5);   // the 32-column chunks the epilogue split
-                    wq_lb[e] = lb;
-                    ++wq_n;
-                    while (wq_n > 2)
-                        if (!issue_w()) goto mma_done;
-                }
             }
         }
-        if constexpr (S::WMMA)
-            while (wq_n > 0)
-                if (!issue_w()) goto mma_done;
     mma_done:
         // after an abort: the last sub-block's tiles and the latest weights of
         // each slot may still be landing, and MMAs may still be writing TMEM
@@ -649,7 +604,44 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
         for (int k = 0; k < 2; ++k)
             if (blk_last[k] >= 0) mbar_drain(BAR_BLK_FULL(k), (blk_last[k] >> 1) & 1);
         if (li_done >= 0) mbar_drain(BAR_T_FULL(li_done % NACC), (li_done / NACC) & 1);
-        if (S::WMMA && w_done >= 0) mbar_drain(BAR_DW_FULL(w_done % GW_NDW), (w_done / GW_NDW) & 1);
+    } else if (S::WMMA && warp == W_WI && lane == 0) {
+        // ------------------------------------------ weight-MMA issuer (r > 4)
+        // A thread of its own: each tcgen05.mma costs its issuing thread about
+        // a hundred cycles, and an item's 16 small weight MMAs would otherwise
+        // delay the next item's argument MMAs.  Item by item: once the
+        // epilogue has stored the split exponentials (K_READY) and the item's
+        // weight-sum accumulator is free, 16 source rows per step: k hi
+        // against [w' hi | w' lo] (N = 32: the lo split's rows follow the hi
+        // split's), then k lo against w' hi into the first 16 columns.
+        constexpr uint32_t idesc32 = make_idesc(0u, G_ROWS, 32), idesc16 = make_idesc(0u, G_ROWS, 16);
+        int li = 0, lb = 0, w_done = -1;
+        for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci, ++lb) {
+            const int b = args.cta_blocks[ci];
+            const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
+            const int bs = lb & 1;
+            const int nk = 2 * (((args.items[i0].nrows & 0x7fffffff) + 31) >> 5);   // the chunks the epilogue split
+            if (!mbar_wait(BAR_BLK_FULL(bs), (lb >> 1) & 1, abort_flag, args.status, args.spin)) goto wi_done;
+            const uint32_t wh = sbase + S::BLK + bs * S::BLKSLOT;
+            for (int it = i0; it < i1; ++it, ++li) {
+                const int a = li % NACC, k = li % GW_NDW;
+                if (!mbar_wait(BAR_K_READY(a), (li / NACC) & 1, abort_flag, args.status, args.spin)) goto wi_done;
+                if (!mbar_wait(BAR_DW_EMPTY(k), ((li / GW_NDW) & 1) ^ 1, abort_flag, args.status, args.spin))
+                    goto wi_done;
+                tc_fence_after();
+                const uint32_t dw = tmem + (uint32_t)(3 * 128 + k * 32), ak = tmem + (uint32_t)(a * 128);
+                for (int ks = 0; ks < nk; ++ks) {
+                    const uint32_t ch = (uint32_t)(32 * (ks >> 1) + 8 * (ks & 1));
+                    tc_mma_ts(dw, ak + ch, gw_desc(wh + 256 * ks), idesc32, ks > 0);
+                    tc_mma_ts(dw, ak + ch + 16, gw_desc(wh + 256 * ks), idesc16, 1);
+                }
+                tc_commit(BAR_DW_FULL(k));
+                tc_commit(BAR_T_EMPTY(a));     // the argument's columns are free again
+                w_done = li;
+            }
+        }
+    wi_done:
+        // weight MMAs in flight after an abort finish before TMEM is freed
+        if (w_done >= 0) mbar_drain(BAR_DW_FULL(w_done % GW_NDW), (w_done / GW_NDW) & 1);
     }
     tc_fence_before();
     __syncthreads();

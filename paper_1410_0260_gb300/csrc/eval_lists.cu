@@ -749,9 +749,10 @@ askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, con
         // Two schedules over one persistent CTA per SM (a sub-block costs its
         // items plus a fixed reload of its source tile); askit_autotune picks.
         //  0: LPT -- heaviest first, each to the least-loaded CTA;
-        //  1: tree order -- sub-blocks sorted by their node's position, cut
-        //     into contiguous ranges of equal cost, so consecutive sub-blocks
-        //     of a CTA share most of their targets (L2 reuse of target rows).
+        //  1: tree order -- sub-blocks taken in their node's tree order, each
+        //     to the least-loaded CTA: the CTAs advance through the tree
+        //     together, so the sub-blocks in flight at any time on all SMs
+        //     share most of their targets (L2 reuse of target rows).
         int dev = 0, sms = 0;
         WCHK(cudaGetDevice(&dev));
         WCHK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -791,18 +792,27 @@ askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, con
             std::vector<int32_t> tord(nb);
             for (int64_t b = 0; b < nb; ++b) tord[b] = (int32_t)b;
             std::stable_sort(tord.begin(), tord.end(), [&](int32_t x, int32_t y) { return bpos[x] < bpos[y]; });
-            int64_t total = 0;
-            for (int64_t b = 0; b < nb; ++b) total += bcost((int32_t)b);
-            coff[1].assign(nc + 1, 0);
-            int c = 0;
-            int64_t acc = 0;
+            std::vector<std::vector<int32_t>> lists(nc);
+            std::vector<std::pair<int64_t, int>> heap;   // (load, cta), min-heap
+            for (int c = 0; c < nc; ++c) heap.push_back({0, c});
+            auto cmp = [](const std::pair<int64_t, int> &x, const std::pair<int64_t, int> &y) {
+                return x.first > y.first || (x.first == y.first && x.second > y.second);
+            };
+            std::make_heap(heap.begin(), heap.end(), cmp);
             for (int64_t q = 0; q < nb; ++q) {
-                cblk[1].push_back(tord[q]);
-                acc += bcost(tord[q]);
-                ++coff[1][c + 1];
-                if (c < nc - 1 && acc * nc >= (int64_t)(c + 1) * total) ++c;
+                std::pop_heap(heap.begin(), heap.end(), cmp);
+                auto top = heap.back();
+                heap.pop_back();
+                lists[top.second].push_back(tord[q]);
+                top.first += bcost(tord[q]);
+                heap.push_back(top);
+                std::push_heap(heap.begin(), heap.end(), cmp);
             }
-            for (int k = 0; k < nc; ++k) coff[1][k + 1] += coff[1][k];
+            coff[1].assign(nc + 1, 0);
+            for (int c = 0; c < nc; ++c) {
+                coff[1][c + 1] = coff[1][c] + (int32_t)lists[c].size();
+                cblk[1].insert(cblk[1].end(), lists[c].begin(), lists[c].end());
+            }
         }
         // Pairs: sub-blocks 2k and 2k+1 of one node need the same targets (a
         // target needing a node needs all its sub-blocks), so their items

@@ -16,15 +16,18 @@
 //
 // One CTA per SM, 448 threads:
 //   warps 0-7  loaders: thread t handles half (t >> 7) of target row t & 127
-//              of each K chunk: subtracts c_B, accumulates |a|^2, splits
+//              of each K chunk: loads its 32 FP32 values straight from HBM
+//              into registers one chunk ahead (the next item's row slot is
+//              read one item ahead), subtracts c_B, accumulates |a|^2, splits
 //              into FP16/BF16 hi + lo and stores both in the 128-byte
 //              swizzled K-major layout; they also write the item's column
 //              data (c log2(e) / h^2, |b|^2, w) for the epilogue;
 //   warps 8-11 epilogue (TMEM lane quadrant = warp & 3);
 //   warp 12    TMEM allocation; lane 0 issues the tcgen05.mma instructions;
-//   warp 13    producer: TMA tile::gather4 of the item's 128 target rows
-//              (one 64-column chunk), TMA tiled load of the sub-block's hi
-//              and lo chunk, and a bulk copy of c_B's chunk.
+//   warp 13    producer: TMA tiled load of the sub-block's hi and lo chunk
+//              and a bulk copy of c_B's chunk (a TMA tile::gather4 of the
+//              target rows cost about 75 issue cycles per four rows, several
+//              times the chunk's MMA time).
 // Two chunk stages in shared memory; two items' accumulators (main + cross)
 // fill all 512 TMEM columns, so the MMAs of item i+1 overlap the epilogue
 // of item i.  Every mbarrier wait is bounded: on timeout the kernel records
@@ -50,11 +53,9 @@ constexpr uint32_t W_TMEM_COLS = 512;           // [main acc 0, main acc 1, cros
 
 template <int RC>
 struct WSmem {
-    // one chunk stage: A hi, A lo, B hi, B lo, raw FP32 target rows, c_B chunk
+    // one chunk stage: A hi, A lo, B hi, B lo, c_B chunk
     static constexpr int A_HI = 0, A_LO = W_REGION, B_HI = 2 * W_REGION, B_LO = 3 * W_REGION;
-    static constexpr int RAW = 4 * W_REGION;
-    static constexpr int RAW_BYTES = W_ROWS * W_KC * 4;
-    static constexpr int CENTC = RAW + RAW_BYTES;
+    static constexpr int CENTC = 4 * W_REGION;
     static constexpr int STAGE = CENTC + 1024;   // c_B chunk (256 B), stage kept 1024-byte aligned
     static constexpr int ANORM = 2 * STAGE;      // float [2 acc][2 halves][128]
     static constexpr int COLV = ANORM + 2 * 2 * 128 * 4;   // float4 [2 acc][128]
@@ -62,7 +63,7 @@ struct WSmem {
     static constexpr int BAR = COLW + 2 * 128 * RC * 4;    // 12 mbarriers
     static constexpr int MISC = BAR + 12 * 8;              // tmem address, abort flag
     static constexpr int BYTES = MISC + 16;
-    static constexpr uint32_t TX = RAW_BYTES + 2 * W_REGION + W_KC * 4;   // bytes landing per chunk
+    static constexpr uint32_t TX = 2 * W_REGION + W_KC * 4;   // bytes landing per chunk
 };
 
 struct TcwArgs {
@@ -73,6 +74,8 @@ struct TcwArgs {
     int nkc;                  // K chunks (kw / 64)
     int kw;                   // row width of the pre-split arrays and of the centers
     const float *cent;        // [n_sub, kw]
+    const float *q;           // target rows [q_rows, ldq] FP32 (16-byte aligned)
+    int64_t ldq;              // = d_pad: columns past it read as zero
     const float *sc_t, *sc_s; // c log2(e) / h^2 per source row
     const float *nrm_t, *nrm_s;   // |y - c_B|^2 per source row
     const float *Wt, *Ws;
@@ -82,16 +85,11 @@ struct TcwArgs {
     int *status;
 };
 
-// GF(4) multiplication by a primitive element: x -> w x is a permutation of
-// {0,1,2,3} and so is x -> w x ^ x (= w^2 x), which makes both the loaders'
-// swizzled stores and their raw-row loads free of bank conflicts.
-__device__ __forceinline__ int gf4_mulw(int x) { return (0x1320 >> (4 * x)) & 3; }
-
 template <int P, int RC>
 __global__ void __launch_bounds__(W_THREADS, 1)
 eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_constant__ CUtensorMap map_t_lo,
                 const __grid_constant__ CUtensorMap map_s_hi, const __grid_constant__ CUtensorMap map_s_lo,
-                const __grid_constant__ CUtensorMap map_q, const TcwArgs args) {
+                const TcwArgs args) {
     using S = WSmem<RC>;
     constexpr uint32_t FMT = P == ASKIT_PREC_BF16X3 ? 1u : 0u;
     constexpr uint32_t IDESC = make_idesc(FMT, W_ROWS, W_ROWS);
@@ -139,7 +137,43 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
     if (warp < 8) {
         // ------------------------------------------------------------ loaders
         const int row = tid & 127, h = tid >> 7;
+        // this thread's 32 values of a chunk, straight from HBM: x_cur holds
+        // the chunk being split, x_nxt the next one (loaded before the waits
+        // of the current chunk); the next item's row slot is read one item
+        // ahead.  Columns past ldq (the ragged last chunk) read as zero.
+        float4 x_cur[8], x_nxt[8];
+        auto load_chunk = [&](int slot, bool valid, int kc, float4 (&x)[8]) {
+            const int64_t col = (int64_t)kc * W_KC + 32 * h;
+            if (valid && col < args.ldq) {
+                const float4 *src = reinterpret_cast<const float4 *>(args.q + (int64_t)slot * args.ldq + col);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) x[i] = __ldg(src + i);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) x[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        };
+        // the item after (ci, it) in this CTA's order, or ci == c_end
+        auto next_item = [&](int &ci, int &it) {
+            ++it;
+            while (ci < c_end && it >= args.block_off[args.cta_blocks[ci] + 1]) {
+                if (++ci < c_end) it = args.block_off[args.cta_blocks[ci]];
+            }
+        };
+        auto slot_of = [&](int ci, int it, bool &valid) -> int {
+            valid = false;
+            if (ci >= c_end) return 0;
+            const EvalItem nx = args.items[it];
+            valid = row < nx.cnt;
+            return valid ? args.tgt[nx.e0 + row] : 0;
+        };
         int g = 0, li = 0;
+        int cur_slot = 0;
+        bool cur_valid = false;
+        if (c_begin < c_end) {
+            cur_slot = slot_of(c_begin, args.block_off[args.cta_blocks[c_begin]], cur_valid);
+            load_chunk(cur_slot, cur_valid, 0, x_cur);
+        }
         for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci) {
             const int b = args.cta_blocks[ci];
             const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
@@ -155,6 +189,11 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                 const int a = li & 1;
                 const int cnt = args.items[it].cnt;
                 const bool has_tgt = row < cnt;
+                // the next item's row slot, for its first chunk's loads
+                int nci = ci, nit = it;
+                next_item(nci, nit);
+                bool nxt_valid = false;
+                const int nxt_slot = slot_of(nci, nit, nxt_valid);
                 if (!mbar_wait(BAR_T_EMPTY(a), ((li >> 1) & 1) ^ 1, abort_flag, args.status)) goto loader_done;
                 // column data of source row `row` for this item's slot:
                 // arg = g A + (C p + B) = -sc (p + q - 2 g / scale^2)
@@ -174,24 +213,20 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                 for (int kc = 0; kc < nkc; ++kc, ++g) {
                     const int s = g & 1;
                     const uint32_t par = (g >> 1) & 1;
+                    // the next chunk's values: this item's, or the next item's first
+                    if (kc + 1 < nkc) load_chunk(cur_slot, cur_valid, kc + 1, x_nxt);
+                    else load_chunk(nxt_slot, nxt_valid, 0, x_nxt);
                     if (!mbar_wait(BAR_MMA_DONE(s), par ^ 1, abort_flag, args.status)) goto loader_done;
                     if (!mbar_wait(BAR_L_FULL(s), par, abort_flag, args.status)) goto loader_done;
                     uint8_t *st = sm + s * S::STAGE;
-                    const float *raw = reinterpret_cast<const float *>(st + S::RAW) + row * W_KC;
-                    const float *cen = reinterpret_cast<const float *>(st + S::CENTC);
-                    const int flip = (row >> 2) & 1;
+                    const float4 *cen4 = reinterpret_cast<const float4 *>(st + S::CENTC);
 #pragma unroll
-                    for (int j2 = 0; j2 < 4; ++j2) {
-                        // swizzled 16-byte slot p of the row and the element chunk c16 it holds;
-                        // c16 >> 2 == h, so the two halves of a row split the chunk
-                        const int p = 4 * (h ^ flip) + (gf4_mulw(row & 3) ^ j2);
-                        const int c16 = p ^ (row & 7);
-                        const float4 x0 = *reinterpret_cast<const float4 *>(raw + 8 * c16 + 4 * flip);
-                        const float4 x1 = *reinterpret_cast<const float4 *>(raw + 8 * c16 + 4 * (flip ^ 1));
-                        const float4 m0 = *reinterpret_cast<const float4 *>(cen + 8 * c16 + 4 * flip);
-                        const float4 m1 = *reinterpret_cast<const float4 *>(cen + 8 * c16 + 4 * (flip ^ 1));
-                        const float4 xl = flip ? x1 : x0, xh = flip ? x0 : x1;   // elements 0-3, 4-7
-                        const float4 ml = flip ? m1 : m0, mh = flip ? m0 : m1;
+                    for (int jj = 0; jj < 4; ++jj) {
+                        // elements 8 c16 .. 8 c16 + 7 of the chunk; the 128-byte
+                        // swizzle puts them in 16-byte slot c16 ^ (row & 7)
+                        const int c16 = 4 * h + jj;
+                        const float4 xl = x_cur[2 * jj], xh = x_cur[2 * jj + 1];
+                        const float4 ml = cen4[2 * c16], mh = cen4[2 * c16 + 1];
                         float v[8] = {xl.x - ml.x, xl.y - ml.y, xl.z - ml.z, xl.w - ml.w,
                                       xh.x - mh.x, xh.y - mh.y, xh.z - mh.z, xh.w - mh.w};
                         if (!has_tgt) {
@@ -219,7 +254,7 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                                 lv[e] = *reinterpret_cast<const uint32_t *>(&ll);
                             }
                         }
-                        const int off = row * 128 + (p << 4);
+                        const int off = row * 128 + ((c16 ^ (row & 7)) << 4);
                         *reinterpret_cast<uint4 *>(st + S::A_HI + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
                         *reinterpret_cast<uint4 *>(st + S::A_LO + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
                     }
@@ -228,7 +263,11 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     mbar_arrive(BAR_A_FULL(s));
                     mbar_arrive(BAR_R_EMPTY(s));
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) x_cur[i] = x_nxt[i];
                 }
+                cur_slot = nxt_slot;
+                cur_valid = nxt_valid;
             }
         }
     loader_done:;
@@ -299,7 +338,7 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
             }
         }
     epi_done:;
-    } else if (warp == 13) {
+    } else if (warp == 13 && lane == 0) {
         // ------------------------------------------------------------ producer
         int g = 0, issued = 0;
         for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci) {
@@ -311,14 +350,6 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
             const CUtensorMap *ml = far ? &map_s_lo : &map_t_lo;
             const float *cb = args.cent + (int64_t)first.cidx * args.kw;
             for (int it = i0; it < i1; ++it) {
-                const EvalItem item = args.items[it];
-                const int t0 = args.tgt[item.e0];
-                int rr[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int rw = 4 * lane + i;   // rows past cnt repeat the first target
-                    rr[i] = rw < item.cnt ? args.tgt[item.e0 + rw] : t0;
-                }
                 for (int kc = 0; kc < nkc; ++kc, ++g) {
                     const int s = g & 1;
                     const uint32_t par = ((g >> 1) & 1) ^ 1;
@@ -326,15 +357,10 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                     if (!mbar_wait(BAR_MMA_DONE(s), par, abort_flag, args.status)) goto prod_done;
                     const uint32_t st = sbase + s * S::STAGE;
                     ++issued;
-                    if (lane == 0) mbar_expect_tx(BAR_L_FULL(s), S::TX);
-                    __syncwarp();
-                    tma_gather4(st + S::RAW + 4 * lane * W_KC * 4, &map_q, kc * W_KC, rr[0], rr[1], rr[2], rr[3],
-                                BAR_L_FULL(s));
-                    if (lane == 0) {
-                        tma_load_2d(st + S::B_HI, mh, kc * W_KC, first.row0, BAR_L_FULL(s));
-                        tma_load_2d(st + S::B_LO, ml, kc * W_KC, first.row0, BAR_L_FULL(s));
-                        bulk_copy(st + S::CENTC, cb + kc * W_KC, W_KC * 4, BAR_L_FULL(s));
-                    }
+                    mbar_expect_tx(BAR_L_FULL(s), S::TX);
+                    tma_load_2d(st + S::B_HI, mh, kc * W_KC, first.row0, BAR_L_FULL(s));
+                    tma_load_2d(st + S::B_LO, ml, kc * W_KC, first.row0, BAR_L_FULL(s));
+                    bulk_copy(st + S::CENTC, cb + kc * W_KC, W_KC * 4, BAR_L_FULL(s));
                 }
             }
         }
@@ -412,7 +438,7 @@ askit_status tcw_state(askit_tree t, int pi, TcwState **out) {
 }
 
 template <int P, int RC>
-askit_status launch_w(askit_tree t, TcwState *st, int pi, const CUtensorMap &map_q, const TcwArgs &a, int grid, cudaStream_t s) {
+askit_status launch_w(askit_tree t, TcwState *st, int pi, const TcwArgs &a, int grid, cudaStream_t s) {
     using S = WSmem<RC>;
     const size_t smem = S::BYTES + 1024;
     static bool attr_set = false;
@@ -426,7 +452,7 @@ askit_status launch_w(askit_tree t, TcwState *st, int pi, const CUtensorMap &map
     }
     ASK_TRY(ktimer_mark(t, s, false));
     eval_tcw_kernel<P, RC><<<(unsigned)grid, W_THREADS, smem, s>>>(st->map[pi][0], st->map[pi][1], st->map[pi][2],
-                                                                   st->map[pi][3], map_q, a);
+                                                                   st->map[pi][3], a);
     ASK_LAUNCH();
     return ktimer_mark(t, s, true);
 }
@@ -451,10 +477,14 @@ askit_status eval_tc_wide(askit_tree t, const WeightCtx &c, int precision, const
     const int pi = precision == ASKIT_PREC_BF16X3 ? 0 : 1;
     TcwState *st = nullptr;
     ASK_TRY(tcw_state(t, pi, &st));
-    CUtensorMap map_q;
-    ASK_TRY(encode_2d(st->encode, &map_q, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, Xq, q_rows, t->d_pad, W_KC, 1,
-                      CU_TENSOR_MAP_SWIZZLE_NONE));
+    if ((reinterpret_cast<uintptr_t>(Xq) & 15) != 0) {
+        askit_set_error("target rows must be 16-byte aligned");
+        return ASKIT_ERR_INVALID_ARG;
+    }
+    (void)q_rows;
     TcwArgs a;
+    a.q = Xq;
+    a.ldq = ldq;
     a.items = w.items;
     a.block_off = w.block_off;
     a.cta_off = w.cta_off;
@@ -475,13 +505,13 @@ askit_status eval_tc_wide(askit_tree t, const WeightCtx &c, int precision, const
     a.partial = partial;
     a.status = t->d_status;
     if (precision == ASKIT_PREC_BF16X3) {
-        if (c.r == 1) return launch_w<ASKIT_PREC_BF16X3, 1>(t, st, pi, map_q, a, w.n_ctas, s);
-        if (c.r <= 4) return launch_w<ASKIT_PREC_BF16X3, 4>(t, st, pi, map_q, a, w.n_ctas, s);
-        return launch_w<ASKIT_PREC_BF16X3, 16>(t, st, pi, map_q, a, w.n_ctas, s);
+        if (c.r == 1) return launch_w<ASKIT_PREC_BF16X3, 1>(t, st, pi, a, w.n_ctas, s);
+        if (c.r <= 4) return launch_w<ASKIT_PREC_BF16X3, 4>(t, st, pi, a, w.n_ctas, s);
+        return launch_w<ASKIT_PREC_BF16X3, 16>(t, st, pi, a, w.n_ctas, s);
     }
-    if (c.r == 1) return launch_w<ASKIT_PREC_FP16X3, 1>(t, st, pi, map_q, a, w.n_ctas, s);
-    if (c.r <= 4) return launch_w<ASKIT_PREC_FP16X3, 4>(t, st, pi, map_q, a, w.n_ctas, s);
-    return launch_w<ASKIT_PREC_FP16X3, 16>(t, st, pi, map_q, a, w.n_ctas, s);
+    if (c.r == 1) return launch_w<ASKIT_PREC_FP16X3, 1>(t, st, pi, a, w.n_ctas, s);
+    if (c.r <= 4) return launch_w<ASKIT_PREC_FP16X3, 4>(t, st, pi, a, w.n_ctas, s);
+    return launch_w<ASKIT_PREC_FP16X3, 16>(t, st, pi, a, w.n_ctas, s);
 }
 
 void eval_tc_wide_free(askit_tree t) {
