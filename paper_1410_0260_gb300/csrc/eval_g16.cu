@@ -132,7 +132,7 @@ struct SG {
     static constexpr int BAR = BLK + 2 * BLKSLOT;           // 40 mbarriers
     static constexpr int MISC = BAR + 40 * 8;               // tmem address, abort flag
     static constexpr int BYTES = MISC + 16;
-    static constexpr int THREADS = WMMA ? 384 : 352;     // r > 4: warp 11 issues the weight MMAs
+    static constexpr int THREADS = 384;    // warp 11: the second MMA issuer (r <= 4) or the weight MMAs' (r > 4)
     static_assert(A0 % 1024 == 0 && ASTAGE % 1024 == 0, "swizzled stages need 1024-byte alignment");
 };
 
@@ -164,7 +164,11 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
     // (paired items)
     constexpr int NITEM = NB == 2 ? 256 : 128;
     constexpr int W_MMA = 8, W_CP0 = 9;          // MMA warp, first of the two copier warps
-    constexpr int W_WI = 11;                     // r > 4: the weight-MMA issuer
+    constexpr int W_WI = 11;                     // r <= 4: odd items' argument MMAs; r > 4: the weight MMAs
+    // r <= 4: two threads issue the argument MMAs, alternate items (a
+    // tcgen05.mma costs its issuing thread about a hundred cycles, close to
+    // what a 128-row, 256-column, K = 16 MMA takes on the tensor core)
+    constexpr bool SPLIT = !S::WMMA;
     static_assert(NA >= 3 && NA <= 4, "the copiers keep NA - 2 items in flight");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -196,7 +200,7 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
             mbar_init(BAR_BLK_EMPTY(s), NEPI);
         }
         mbar_init(BAR_B_FULL, 1);
-        mbar_init(BAR_B_EMPTY, 1);
+        mbar_init(BAR_B_EMPTY, SPLIT ? 2 : 1);      // one commit per issuer and block
         for (int a = 0; a < NACC; ++a) {
             mbar_init(BAR_T_FULL(a), 1);
             mbar_init(BAR_T_EMPTY(a), S::WMMA ? 1 : NITEM);
@@ -227,6 +231,47 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const int c_begin = args.cta_off[blockIdx.x], c_end = args.cta_off[blockIdx.x + 1];
+
+    // The argument MMAs of item li (stage li % NA, accumulator li % NACC)
+    // against the block's sub-block tiles; false when a wait gave up.
+    auto issue_arg = [&](int li, uint32_t idesc) -> bool {
+        const int sa = li % NA, a4 = li % NACC;
+        if (!mbar_wait(BAR_A_FULL(sa), (li / NA) & 1, abort_flag, args.status, args.spin)) return false;
+        if (!mbar_wait(BAR_T_EMPTY(a4), ((li / NACC) & 1) ^ 1, abort_flag, args.status, args.spin)) return false;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem + (uint32_t)(a4 * 128 * NB);
+        const uint32_t a_hi = sbase + S::A0 + sa * S::ASTAGE, a_lo = a_hi + G_REGION;
+        const uint32_t a_x = a_hi + 2 * G_REGION;
+        const uint32_t b_hi = sbase + S::B_HI, b_lo = sbase + S::B_LO, b_x = sbase + S::B_X;
+        // the tensor core rounds each accumulation step to the running sum's
+        // precision: the small cross terms first, then the hi*hi products,
+        // then the norm block, which brings the sum down to the exponent's
+        // argument
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {   // K = 16 per MMA: 32 bytes into the 128-byte rows
+            const uint32_t off = (uint32_t)(k * 32);
+            tc_mma<ASKIT_PREC_FP16X3>(d_tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, k > 0);
+            tc_mma<ASKIT_PREC_FP16X3>(d_tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t off = (uint32_t)(k * 32);
+            tc_mma<ASKIT_PREC_FP16X3>(d_tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, 1);
+        }
+        tc_mma<ASKIT_PREC_FP16X3>(d_tmem, ns_desc(a_x), ns_desc(b_x), idesc, 1);
+        tc_commit(BAR_A_EMPTY(sa));
+        tc_commit(BAR_T_FULL(a4));
+        return true;
+    };
+    // N of a block's argument MMAs: every 32-column chunk the epilogue reads
+    // (a paired follower's columns follow the leader's), so no column it
+    // reads holds a stale accumulator
+    auto block_idesc = [&](int b, int i0) -> uint32_t {
+        const int pb = NB == 2 ? args.partner[b] : -1;
+        const int ncols = (args.items[i0].nrows & 0x7fffffff) +
+                          (pb >= 0 ? (args.items[args.block_off[pb]].nrows & 0x7fffffff) : 0);
+        return make_idesc(0u, G_ROWS, (ncols + 31) & ~31);
+    };
 
     if (warp < W_MMA) {
         // ----------------------------------------------------------- epilogue
@@ -541,10 +586,7 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
             // node: its rows, norm block and weights follow the leader's
             const int pb = NB == 2 ? args.partner[b] : -1;
             const int nsb = pb >= 0 ? 2 : 1;
-            const int ncols = (first.nrows & 0x7fffffff) + (pb >= 0 ? (args.items[args.block_off[pb]].nrows & 0x7fffffff) : 0);
-            // N covers every 32-column chunk the epilogue reads, so no column it
-            // reads holds a stale accumulator
-            const uint32_t idesc = make_idesc(0u, G_ROWS, (ncols + 31) & ~31);
+            const uint32_t idesc = block_idesc(b, i0);
             if (!mbar_wait(BAR_B_EMPTY, (lb & 1) ^ 1, abort_flag, args.status, args.spin)) goto mma_done;
             if (!mbar_wait(BAR_BLK_EMPTY(bs), ((lb >> 1) & 1) ^ 1, abort_flag, args.status, args.spin)) goto mma_done;
             b_issued = lb + 1;
@@ -563,37 +605,15 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
             bulk_copy(sbase + S::BLK + bs * S::BLKSLOT,
                       reinterpret_cast<const uint8_t *>(args.colw) + (int64_t)first.cidx * S::BLKSLOT / NB, wbytes,
                       BAR_BLK_FULL(bs));
+            // every block's tiles are waited for, items of this thread or not:
+            // a parity wait may fall at most one phase behind the loads
+            if (!mbar_wait(BAR_B_FULL, lb & 1, abort_flag, args.status, args.spin)) goto mma_done;
             for (int it = i0; it < i1; ++it, ++li) {
-                const int sa = li % NA, a4 = li % NACC;
-                if (!mbar_wait(BAR_A_FULL(sa), (li / NA) & 1, abort_flag, args.status, args.spin)) goto mma_done;
-                if (it == i0 && !mbar_wait(BAR_B_FULL, lb & 1, abort_flag, args.status, args.spin)) goto mma_done;
-                if (!mbar_wait(BAR_T_EMPTY(a4), ((li / NACC) & 1) ^ 1, abort_flag, args.status, args.spin)) goto mma_done;
-                tc_fence_after();
-                const uint32_t d_tmem = tmem + (uint32_t)(a4 * 128 * NB);
-                const uint32_t a_hi = sbase + S::A0 + sa * S::ASTAGE, a_lo = a_hi + G_REGION;
-                const uint32_t a_x = a_hi + 2 * G_REGION;
-                const uint32_t b_hi = sbase + S::B_HI, b_lo = sbase + S::B_LO, b_x = sbase + S::B_X;
-                // the tensor core rounds each accumulation step to the running
-                // sum's precision: the small cross terms first, then the hi*hi
-                // products, then the norm block, which brings the sum down to
-                // the exponent's argument
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {   // K = 16 per MMA: 32 bytes into the 128-byte rows
-                    const uint32_t off = (uint32_t)(k * 32);
-                    tc_mma<ASKIT_PREC_FP16X3>(d_tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, k > 0);
-                    tc_mma<ASKIT_PREC_FP16X3>(d_tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1);
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint32_t off = (uint32_t)(k * 32);
-                    tc_mma<ASKIT_PREC_FP16X3>(d_tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, 1);
-                }
-                tc_mma<ASKIT_PREC_FP16X3>(d_tmem, ns_desc(a_x), ns_desc(b_x), idesc, 1);
-                tc_commit(BAR_A_EMPTY(sa));
-                tc_commit(BAR_T_FULL(a4));
-                if (it == i1 - 1) tc_commit(BAR_B_EMPTY);
+                if (SPLIT && (li & 1)) continue;            // the second issuer's item
+                if (!issue_arg(li, idesc)) goto mma_done;
                 li_done = li;
             }
+            tc_commit(BAR_B_EMPTY);     // this thread's MMAs of the block have read the tiles
         }
     mma_done:
         // after an abort: the last sub-block's tiles and the latest weights of
@@ -603,6 +623,25 @@ eval_g16_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
         if (b_issued > 0) mbar_drain(BAR_B_FULL, (b_issued - 1) & 1);
         for (int k = 0; k < 2; ++k)
             if (blk_last[k] >= 0) mbar_drain(BAR_BLK_FULL(k), (blk_last[k] >> 1) & 1);
+        if (li_done >= 0) mbar_drain(BAR_T_FULL(li_done % NACC), (li_done / NACC) & 1);
+    } else if (SPLIT && warp == W_WI && lane == 0) {
+        // ---------------------------------------- second argument-MMA issuer
+        int li = 0, lb = 0, li_done = -1;
+        for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci, ++lb) {
+            const int b = args.cta_blocks[ci];
+            const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
+            const uint32_t idesc = block_idesc(b, i0);
+            // this block's tiles have landed (waited for even without items
+            // here, so that no later parity wait can pass on an old phase)
+            if (!mbar_wait(BAR_B_FULL, lb & 1, abort_flag, args.status, args.spin)) goto mma2_done;
+            for (int it = i0; it < i1; ++it, ++li) {
+                if (!(li & 1)) continue;                   // the first issuer's item
+                if (!issue_arg(li, idesc)) goto mma2_done;
+                li_done = li;
+            }
+            tc_commit(BAR_B_EMPTY);
+        }
+    mma2_done:
         if (li_done >= 0) mbar_drain(BAR_T_FULL(li_done % NACC), (li_done / NACC) & 1);
     } else if (S::WMMA && warp == W_WI && lane == 0) {
         // ------------------------------------------ weight-MMA issuer (r > 4)
