@@ -137,11 +137,12 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
     if (warp < 8) {
         // ------------------------------------------------------------ loaders
         const int row = tid & 127, h = tid >> 7;
-        // this thread's 32 values of a chunk, straight from HBM: x_cur holds
-        // the chunk being split, x_nxt the next one (loaded before the waits
-        // of the current chunk); the next item's row slot is read one item
-        // ahead.  Columns past ldq (the ragged last chunk) read as zero.
-        float4 x_cur[8], x_nxt[8];
+        // this thread's 32 values of a chunk, straight from HBM: one buffer
+        // holds the chunk being split, the other the next one (loaded before
+        // the waits of the current chunk); the next item's row slot is read
+        // one item ahead.  Columns past ldq (the ragged last chunk) read as
+        // zero.
+        float4 x_a[8], x_b[8];      // chunk g's values in x_a for even g, x_b for odd
         auto load_chunk = [&](int slot, bool valid, int kc, float4 (&x)[8]) {
             const int64_t col = (int64_t)kc * W_KC + 32 * h;
             if (valid && col < args.ldq) {
@@ -172,7 +173,7 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
         bool cur_valid = false;
         if (c_begin < c_end) {
             cur_slot = slot_of(c_begin, args.block_off[args.cta_blocks[c_begin]], cur_valid);
-            load_chunk(cur_slot, cur_valid, 0, x_cur);
+            load_chunk(cur_slot, cur_valid, 0, x_a);
         }
         for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci) {
             const int b = args.cta_blocks[ci];
@@ -210,14 +211,17 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                         colw[(a * 128 + row) * RC + z] = (has_src && z < args.r) ? __ldg(wrow + z) : 0.f;
                 }
                 float nn = 0.f;
-                for (int kc = 0; kc < nkc; ++kc, ++g) {
+                // one chunk: the next chunk's loads into `nxt`, then the split
+                // of `cur` (loaded a chunk earlier); the two buffers swap roles
+                // every chunk, so no register copy waits for a load in flight
+                auto chunk = [&](int kc, float4 (&cur)[8], float4 (&nxt)[8]) -> bool {
                     const int s = g & 1;
                     const uint32_t par = (g >> 1) & 1;
                     // the next chunk's values: this item's, or the next item's first
-                    if (kc + 1 < nkc) load_chunk(cur_slot, cur_valid, kc + 1, x_nxt);
-                    else load_chunk(nxt_slot, nxt_valid, 0, x_nxt);
-                    if (!mbar_wait(BAR_MMA_DONE(s), par ^ 1, abort_flag, args.status)) goto loader_done;
-                    if (!mbar_wait(BAR_L_FULL(s), par, abort_flag, args.status)) goto loader_done;
+                    if (kc + 1 < nkc) load_chunk(cur_slot, cur_valid, kc + 1, nxt);
+                    else load_chunk(nxt_slot, nxt_valid, 0, nxt);
+                    if (!mbar_wait(BAR_MMA_DONE(s), par ^ 1, abort_flag, args.status)) return false;
+                    if (!mbar_wait(BAR_L_FULL(s), par, abort_flag, args.status)) return false;
                     uint8_t *st = sm + s * S::STAGE;
                     const float4 *cen4 = reinterpret_cast<const float4 *>(st + S::CENTC);
 #pragma unroll
@@ -225,7 +229,7 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                         // elements 8 c16 .. 8 c16 + 7 of the chunk; the 128-byte
                         // swizzle puts them in 16-byte slot c16 ^ (row & 7)
                         const int c16 = 4 * h + jj;
-                        const float4 xl = x_cur[2 * jj], xh = x_cur[2 * jj + 1];
+                        const float4 xl = cur[2 * jj], xh = cur[2 * jj + 1];
                         const float4 ml = cen4[2 * c16], mh = cen4[2 * c16 + 1];
                         float v[8] = {xl.x - ml.x, xl.y - ml.y, xl.z - ml.z, xl.w - ml.w,
                                       xh.x - mh.x, xh.y - mh.y, xh.z - mh.z, xh.w - mh.w};
@@ -263,8 +267,11 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     mbar_arrive(BAR_A_FULL(s));
                     mbar_arrive(BAR_R_EMPTY(s));
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) x_cur[i] = x_nxt[i];
+                    return true;
+                };
+                for (int kc = 0; kc < nkc; ++kc, ++g) {
+                    const bool ok = (g & 1) ? chunk(kc, x_b, x_a) : chunk(kc, x_a, x_b);
+                    if (!ok) goto loader_done;
                 }
                 cur_slot = nxt_slot;
                 cur_valid = nxt_valid;
