@@ -210,7 +210,9 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                     for (int z = 0; z < RC; ++z)
                         colw[(a * 128 + row) * RC + z] = (has_src && z < args.r) ? __ldg(wrow + z) : 0.f;
                 }
-                float nn = 0.f;
+                float2 nn = make_float2(0.f, 0.f);   // |a|^2 of this half row: two interleaved sums
+                const float2 minus1 = make_float2(-1.f, -1.f);
+                const float2 scale2 = make_float2(args.f16_scale, args.f16_scale);
                 // one chunk: the next chunk's loads into `nxt`, then the split
                 // of `cur` (loaded a chunk earlier); the two buffers swap roles
                 // every chunk, so no register copy waits for a load in flight
@@ -229,31 +231,34 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                         // elements 8 c16 .. 8 c16 + 7 of the chunk; the 128-byte
                         // swizzle puts them in 16-byte slot c16 ^ (row & 7)
                         const int c16 = 4 * h + jj;
+                        // two elements per packed FP32 instruction: x - c as
+                        // fma(c, -1, x) (one rounding, as a subtraction), the
+                        // power-of-2 scale (exact), the residual after the hi
+                        // split (exact)
                         const float4 xl = cur[2 * jj], xh = cur[2 * jj + 1];
                         const float4 ml = cen4[2 * c16], mh = cen4[2 * c16 + 1];
-                        float v[8] = {xl.x - ml.x, xl.y - ml.y, xl.z - ml.z, xl.w - ml.w,
-                                      xh.x - mh.x, xh.y - mh.y, xh.z - mh.z, xh.w - mh.w};
+                        float2 v[4] = {__ffma2_rn(make_float2(ml.x, ml.y), minus1, make_float2(xl.x, xl.y)),
+                                       __ffma2_rn(make_float2(ml.z, ml.w), minus1, make_float2(xl.z, xl.w)),
+                                       __ffma2_rn(make_float2(mh.x, mh.y), minus1, make_float2(xh.x, xh.y)),
+                                       __ffma2_rn(make_float2(mh.z, mh.w), minus1, make_float2(xh.z, xh.w))};
                         if (!has_tgt) {
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) v[e] = 0.f;
+                            for (int e = 0; e < 4; ++e) v[e] = make_float2(0.f, 0.f);
                         }
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) nn = fmaf(v[e], v[e], nn);
+                        for (int e = 0; e < 4; ++e) nn = __ffma2_rn(v[e], v[e], nn);
                         uint32_t hv[4], lv[4];
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             if constexpr (P == ASKIT_PREC_FP16X3) {
-                                const float v0 = v[2 * e] * args.f16_scale, v1 = v[2 * e + 1] * args.f16_scale;
-                                const __half2 hh = __floats2half2_rn(v0, v1);
-                                const float2 hf = __half22float2(hh);
-                                const __half2 ll = __floats2half2_rn(v0 - hf.x, v1 - hf.y);
+                                const float2 w2 = __fmul2_rn(v[e], scale2);
+                                const __half2 hh = __float22half2_rn(w2);
+                                const __half2 ll = __float22half2_rn(__ffma2_rn(__half22float2(hh), minus1, w2));
                                 hv[e] = *reinterpret_cast<const uint32_t *>(&hh);
                                 lv[e] = *reinterpret_cast<const uint32_t *>(&ll);
                             } else {
-                                const float v0 = v[2 * e], v1 = v[2 * e + 1];
-                                const __nv_bfloat162 hh = __floats2bfloat162_rn(v0, v1);
-                                const float2 hf = __bfloat1622float2(hh);
-                                const __nv_bfloat162 ll = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+                                const __nv_bfloat162 hh = __float22bfloat162_rn(v[e]);
+                                const __nv_bfloat162 ll = __float22bfloat162_rn(__ffma2_rn(__bfloat1622float2(hh), minus1, v[e]));
                                 hv[e] = *reinterpret_cast<const uint32_t *>(&hh);
                                 lv[e] = *reinterpret_cast<const uint32_t *>(&ll);
                             }
@@ -262,7 +267,7 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                         *reinterpret_cast<uint4 *>(st + S::A_HI + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
                         *reinterpret_cast<uint4 *>(st + S::A_LO + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
                     }
-                    if (kc == nkc - 1) a_norm[(a * 2 + h) * 128 + row] = nn;
+                    if (kc == nkc - 1) a_norm[(a * 2 + h) * 128 + row] = nn.x + nn.y;
                     // generic-proxy stores -> visible to the tensor core's async proxy
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     mbar_arrive(BAR_A_FULL(s));
