@@ -48,7 +48,7 @@
 //
 // Work item = one source sub-block (or two sub-blocks of one node: a paired
 // 256-column item) against up to 128 targets needing it (eval_lists.cu).
-// One CTA per SM, 352 threads:
+// One CTA per SM, 384 threads:
 //   warps 0-7  two epilogue groups, each summing whole sub-blocks (alternate
 //              items, or the two sub-blocks of a paired item): tcgen05.ld of
 //              their 32 TMEM lanes (two buffers), ex2 on MUFU, weight sums
@@ -57,11 +57,14 @@
 //              sub-block) entry;
 //   warp 8     TMEM allocation; lane 0 loads each sub-block (TMA tiles of its
 //              split rows, bulk copies of its norm block and weights) and
-//              issues the tcgen05.mma instructions (r > 4: an item's weight
-//              MMAs two items after its argument MMAs, once the epilogue has
-//              stored its exponentials);
+//              issues the argument MMAs (r <= 4: of the even items; r > 4: of
+//              every item);
 //   warps 9-10 copy each item's target rows into NA stages (NA - 2 items'
-//              copies in flight).
+//              copies in flight);
+//   warp 11    lane 0 issues the odd items' argument MMAs (r <= 4), or every
+//              item's weight MMAs once the epilogue has stored its
+//              exponentials (r > 4): a tcgen05.mma costs its issuing thread
+//              about a hundred cycles.
 // Every mbarrier wait is bounded (ASK_DEV_TIMEOUT on expiry, all roles leave,
 // copies and MMAs in flight are waited for, TMEM is freed).
 #include <cuda.h>
