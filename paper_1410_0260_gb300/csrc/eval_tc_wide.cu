@@ -57,11 +57,15 @@ struct WSmem {
     static constexpr int A_HI = 0, A_LO = W_REGION, B_HI = 2 * W_REGION, B_LO = 3 * W_REGION;
     static constexpr int CENTC = 4 * W_REGION;
     static constexpr int STAGE = CENTC + 1024;   // c_B chunk (256 B), stage kept 1024-byte aligned
-    static constexpr int ANORM = 2 * STAGE;      // float [2 acc][2 halves][128]
+    // two buffers of a chunk's raw FP32 target rows [128 rows][64], copied by
+    // the loaders themselves (lanes along a row)
+    static constexpr int RAW0 = 2 * STAGE;
+    static constexpr int RAW_BYTES = W_ROWS * W_KC * 4;
+    static constexpr int ANORM = RAW0 + 2 * RAW_BYTES;   // float [2 acc][2 halves][128]
     static constexpr int COLV = ANORM + 2 * 2 * 128 * 4;   // float4 [2 acc][128]
     static constexpr int COLW = COLV + 2 * 128 * 16;       // float [2 acc][128][RC]
-    static constexpr int BAR = COLW + 2 * 128 * RC * 4;    // 12 mbarriers
-    static constexpr int MISC = BAR + 12 * 8;              // tmem address, abort flag
+    static constexpr int BAR = COLW + 2 * 128 * RC * 4;    // 16 mbarriers
+    static constexpr int MISC = BAR + 16 * 8;              // tmem address, abort flag
     static constexpr int BYTES = MISC + 16;
     static constexpr uint32_t TX = 2 * W_REGION + W_KC * 4;   // bytes landing per chunk
 };
@@ -85,6 +89,11 @@ struct TcwArgs {
     int *status;
 };
 
+// GF(4) multiplication by a primitive element: x -> w x is a permutation of
+// {0,1,2,3} and so is x -> w x ^ x (= w^2 x), which makes both the loaders'
+// swizzled stores and their raw-row reads free of bank conflicts.
+__device__ __forceinline__ int gf4_mulw(int x) { return (0x1320 >> (4 * x)) & 3; }
+
 template <int P, int RC>
 __global__ void __launch_bounds__(W_THREADS, 1)
 eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_constant__ CUtensorMap map_t_lo,
@@ -106,6 +115,8 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
     auto BAR_R_EMPTY = [&](int s) { return bar0 + 8 * (6 + s); };   // loaders done with raw/c_B of stage s (256)
     auto BAR_T_FULL = [&](int a) { return bar0 + 8 * (8 + a); };    // accumulators of item slot a complete
     auto BAR_T_EMPTY = [&](int a) { return bar0 + 8 * (10 + a); };  // epilogue drained slot a (128)
+    auto BAR_RAW_FULL = [&](int b) { return bar0 + 8 * (12 + b); }; // raw rows of buffer b landed (256 copiers)
+    auto BAR_RAW_FREE = [&](int b) { return bar0 + 8 * (14 + b); }; // buffer b split by every loader (256)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + S::MISC);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + S::MISC + 4);
 
@@ -118,6 +129,8 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
             mbar_init(BAR_R_EMPTY(s), 256);
             mbar_init(BAR_T_FULL(s), 1);
             mbar_init(BAR_T_EMPTY(s), 128);
+            mbar_init(BAR_RAW_FULL(s), 256);
+            mbar_init(BAR_RAW_FREE(s), 256);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -136,23 +149,40 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
 
     if (warp < 8) {
         // ------------------------------------------------------------ loaders
+        // Copies: loader warp lw brings rows 16 lw .. 16 lw + 15 of the next
+        // chunk into a raw buffer, two rows per instruction, 16 lanes along a
+        // row's 256 bytes (so an instruction touches 4 cache lines, not 32),
+        // zero-filled past ldq and for rows past the item's targets; each
+        // thread's arrival on RAW_FULL fires when its copies have landed.
+        // Split: thread (row, h) then centers, splits and stores its half of
+        // row `row` of the chunk (conflict-free order of the 16-byte reads).
         const int row = tid & 127, h = tid >> 7;
-        // this thread's 32 values of a chunk, straight from HBM: one buffer
-        // holds the chunk being split, the other the next one (loaded before
-        // the waits of the current chunk); the next item's row slot is read
-        // one item ahead.  Columns past ldq (the ragged last chunk) read as
-        // zero.
-        float4 x_a[8], x_b[8];      // chunk g's values in x_a for even g, x_b for odd
-        auto load_chunk = [&](int slot, bool valid, int kc, float4 (&x)[8]) {
-            const int64_t col = (int64_t)kc * W_KC + 32 * h;
-            if (valid && col < args.ldq) {
-                const float4 *src = reinterpret_cast<const float4 *>(args.q + (int64_t)slot * args.ldq + col);
+        const int lw = tid >> 5, cpiece = lane & 15;
+        int cs[8], ns[8];           // target slots of this lane's copy rows: current item, next item
+        uint32_t cmask = 0, nmask = 0;
+        auto copy_slots = [&](int ci, int it, int (&sl)[8], uint32_t &mask) {
+            mask = 0;
+            if (ci >= c_end) return;
+            const EvalItem nx = args.items[it];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) x[i] = __ldg(src + i);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) x[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = 0; i < 8; ++i) {
+                const int r = 16 * lw + 2 * i + (lane >> 4);
+                sl[i] = r < nx.cnt ? args.tgt[nx.e0 + r] : 0;
+                if (r < nx.cnt) mask |= 1u << i;
             }
+        };
+        auto issue_copies = [&](const int (&sl)[8], uint32_t mask, int kc, int buf) {
+            const uint32_t dst0 = sbase + S::RAW0 + buf * S::RAW_BYTES;
+            const int64_t col = (int64_t)kc * W_KC + 4 * cpiece;
+            const bool in_row = col < args.ldq;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int r = 16 * lw + 2 * i + (lane >> 4);
+                const bool ok = in_row && ((mask >> i) & 1u);
+                const float *src = ok ? args.q + (int64_t)sl[i] * args.ldq + col : args.q;
+                cp_async16_zfill(dst0 + (uint32_t)(r * W_KC * 4 + cpiece * 16), src, ok ? 16u : 0u);
+            }
+            cp_async_mbar_arrive(BAR_RAW_FULL(buf));
         };
         // the item after (ci, it) in this CTA's order, or ci == c_end
         auto next_item = [&](int &ci, int &it) {
@@ -161,19 +191,10 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                 if (++ci < c_end) it = args.block_off[args.cta_blocks[ci]];
             }
         };
-        auto slot_of = [&](int ci, int it, bool &valid) -> int {
-            valid = false;
-            if (ci >= c_end) return 0;
-            const EvalItem nx = args.items[it];
-            valid = row < nx.cnt;
-            return valid ? args.tgt[nx.e0 + row] : 0;
-        };
         int g = 0, li = 0;
-        int cur_slot = 0;
-        bool cur_valid = false;
         if (c_begin < c_end) {
-            cur_slot = slot_of(c_begin, args.block_off[args.cta_blocks[c_begin]], cur_valid);
-            load_chunk(cur_slot, cur_valid, 0, x_a);
+            copy_slots(c_begin, args.block_off[args.cta_blocks[c_begin]], cs, cmask);
+            issue_copies(cs, cmask, 0, 0);          // chunk 0 into buffer 0
         }
         for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci) {
             const int b = args.cta_blocks[ci];
@@ -190,11 +211,11 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                 const int a = li & 1;
                 const int cnt = args.items[it].cnt;
                 const bool has_tgt = row < cnt;
-                // the next item's row slot, for its first chunk's loads
+                // the next item's copy slots, one item ahead
                 int nci = ci, nit = it;
                 next_item(nci, nit);
-                bool nxt_valid = false;
-                const int nxt_slot = slot_of(nci, nit, nxt_valid);
+                copy_slots(nci, nit, ns, nmask);
+                const bool has_next = nci < c_end;
                 if (!mbar_wait(BAR_T_EMPTY(a), ((li >> 1) & 1) ^ 1, abort_flag, args.status)) goto loader_done;
                 // column data of source row `row` for this item's slot:
                 // arg = g A + (C p + B) = -sc (p + q - 2 g / scale^2)
@@ -210,79 +231,85 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                     for (int z = 0; z < RC; ++z)
                         colw[(a * 128 + row) * RC + z] = (has_src && z < args.r) ? __ldg(wrow + z) : 0.f;
                 }
-                float2 nn = make_float2(0.f, 0.f);   // |a|^2 of this half row: two interleaved sums
-                const float2 minus1 = make_float2(-1.f, -1.f);
-                const float2 scale2 = make_float2(args.f16_scale, args.f16_scale);
-                // one chunk: the next chunk's loads into `nxt`, then the split
-                // of `cur` (loaded a chunk earlier); the two buffers swap roles
-                // every chunk, so no register copy waits for a load in flight
-                auto chunk = [&](int kc, float4 (&cur)[8], float4 (&nxt)[8]) -> bool {
+                float nn = 0.f;
+                for (int kc = 0; kc < nkc; ++kc, ++g) {
                     const int s = g & 1;
                     const uint32_t par = (g >> 1) & 1;
-                    // the next chunk's values: this item's, or the next item's first
-                    if (kc + 1 < nkc) load_chunk(cur_slot, cur_valid, kc + 1, nxt);
-                    else load_chunk(nxt_slot, nxt_valid, 0, nxt);
-                    if (!mbar_wait(BAR_MMA_DONE(s), par ^ 1, abort_flag, args.status)) return false;
-                    if (!mbar_wait(BAR_L_FULL(s), par, abort_flag, args.status)) return false;
+                    // the next chunk's rows into the other raw buffer, once every
+                    // loader has split the chunk it held (chunk g - 1)
+                    const int nb = (g + 1) & 1;
+                    if (kc + 1 < nkc || has_next) {
+                        if (!mbar_wait(BAR_RAW_FREE(nb), (((g + 1) >> 1) & 1) ^ 1, abort_flag, args.status))
+                            goto loader_done;
+                        if (kc + 1 < nkc) issue_copies(cs, cmask, kc + 1, nb);
+                        else issue_copies(ns, nmask, 0, nb);
+                    }
+                    if (!mbar_wait(BAR_MMA_DONE(s), par ^ 1, abort_flag, args.status)) goto loader_done;
+                    if (!mbar_wait(BAR_L_FULL(s), par, abort_flag, args.status)) goto loader_done;
+                    if (!mbar_wait(BAR_RAW_FULL(s), par, abort_flag, args.status)) goto loader_done;
                     uint8_t *st = sm + s * S::STAGE;
-                    const float4 *cen4 = reinterpret_cast<const float4 *>(st + S::CENTC);
+                    const float *raw = reinterpret_cast<const float *>(sm + S::RAW0 + s * S::RAW_BYTES) + row * W_KC;
+                    const float *cen = reinterpret_cast<const float *>(st + S::CENTC);
+                    const int flip = (row >> 2) & 1;
 #pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        // elements 8 c16 .. 8 c16 + 7 of the chunk; the 128-byte
-                        // swizzle puts them in 16-byte slot c16 ^ (row & 7)
-                        const int c16 = 4 * h + jj;
-                        // two elements per packed FP32 instruction: x - c as
-                        // fma(c, -1, x) (one rounding, as a subtraction), the
-                        // power-of-2 scale (exact), the residual after the hi
-                        // split (exact)
-                        const float4 xl = cur[2 * jj], xh = cur[2 * jj + 1];
-                        const float4 ml = cen4[2 * c16], mh = cen4[2 * c16 + 1];
-                        float2 v[4] = {__ffma2_rn(make_float2(ml.x, ml.y), minus1, make_float2(xl.x, xl.y)),
-                                       __ffma2_rn(make_float2(ml.z, ml.w), minus1, make_float2(xl.z, xl.w)),
-                                       __ffma2_rn(make_float2(mh.x, mh.y), minus1, make_float2(xh.x, xh.y)),
-                                       __ffma2_rn(make_float2(mh.z, mh.w), minus1, make_float2(xh.z, xh.w))};
+                    for (int j2 = 0; j2 < 4; ++j2) {
+                        // swizzled 16-byte slot p of the row and the element chunk c16 it holds;
+                        // c16 >> 2 == h, so the two halves of a row split the chunk
+                        const int p = 4 * (h ^ flip) + (gf4_mulw(row & 3) ^ j2);
+                        const int c16 = p ^ (row & 7);
+                        const float4 x0 = *reinterpret_cast<const float4 *>(raw + 8 * c16 + 4 * flip);
+                        const float4 x1 = *reinterpret_cast<const float4 *>(raw + 8 * c16 + 4 * (flip ^ 1));
+                        const float4 m0 = *reinterpret_cast<const float4 *>(cen + 8 * c16 + 4 * flip);
+                        const float4 m1 = *reinterpret_cast<const float4 *>(cen + 8 * c16 + 4 * (flip ^ 1));
+                        const float4 xl = flip ? x1 : x0, xh = flip ? x0 : x1;   // elements 0-3, 4-7
+                        const float4 ml = flip ? m1 : m0, mh = flip ? m0 : m1;
+                        float v[8] = {xl.x - ml.x, xl.y - ml.y, xl.z - ml.z, xl.w - ml.w,
+                                      xh.x - mh.x, xh.y - mh.y, xh.z - mh.z, xh.w - mh.w};
                         if (!has_tgt) {
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) v[e] = make_float2(0.f, 0.f);
+                            for (int e = 0; e < 8; ++e) v[e] = 0.f;
                         }
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) nn = __ffma2_rn(v[e], v[e], nn);
+                        for (int e = 0; e < 8; ++e) nn = fmaf(v[e], v[e], nn);
                         uint32_t hv[4], lv[4];
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             if constexpr (P == ASKIT_PREC_FP16X3) {
-                                const float2 w2 = __fmul2_rn(v[e], scale2);
-                                const __half2 hh = __float22half2_rn(w2);
-                                const __half2 ll = __float22half2_rn(__ffma2_rn(__half22float2(hh), minus1, w2));
+                                const float v0 = v[2 * e] * args.f16_scale, v1 = v[2 * e + 1] * args.f16_scale;
+                                const __half2 hh = __floats2half2_rn(v0, v1);
+                                const float2 hf = __half22float2(hh);
+                                const __half2 ll = __floats2half2_rn(v0 - hf.x, v1 - hf.y);
                                 hv[e] = *reinterpret_cast<const uint32_t *>(&hh);
                                 lv[e] = *reinterpret_cast<const uint32_t *>(&ll);
                             } else {
-                                const __nv_bfloat162 hh = __float22bfloat162_rn(v[e]);
-                                const __nv_bfloat162 ll = __float22bfloat162_rn(__ffma2_rn(__bfloat1622float2(hh), minus1, v[e]));
+                                const float v0 = v[2 * e], v1 = v[2 * e + 1];
+                                const __nv_bfloat162 hh = __floats2bfloat162_rn(v0, v1);
+                                const float2 hf = __bfloat1622float2(hh);
+                                const __nv_bfloat162 ll = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
                                 hv[e] = *reinterpret_cast<const uint32_t *>(&hh);
                                 lv[e] = *reinterpret_cast<const uint32_t *>(&ll);
                             }
                         }
-                        const int off = row * 128 + ((c16 ^ (row & 7)) << 4);
+                        const int off = row * 128 + (p << 4);
                         *reinterpret_cast<uint4 *>(st + S::A_HI + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
                         *reinterpret_cast<uint4 *>(st + S::A_LO + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
                     }
-                    if (kc == nkc - 1) a_norm[(a * 2 + h) * 128 + row] = nn.x + nn.y;
+                    if (kc == nkc - 1) a_norm[(a * 2 + h) * 128 + row] = nn;
+                    mbar_arrive(BAR_RAW_FREE(s));
                     // generic-proxy stores -> visible to the tensor core's async proxy
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     mbar_arrive(BAR_A_FULL(s));
                     mbar_arrive(BAR_R_EMPTY(s));
-                    return true;
-                };
-                for (int kc = 0; kc < nkc; ++kc, ++g) {
-                    const bool ok = (g & 1) ? chunk(kc, x_b, x_a) : chunk(kc, x_a, x_b);
-                    if (!ok) goto loader_done;
                 }
-                cur_slot = nxt_slot;
-                cur_valid = nxt_valid;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) cs[i] = ns[i];
+                cmask = nmask;
             }
         }
-    loader_done:;
+    loader_done:
+        // no copy may land in shared memory after the CTA exits (also after
+        // an abort)
+        cp_async_wait<0>();
     } else if (warp < 12) {
         // ----------------------------------------------------------- epilogue
         const int row = tid - 256;
