@@ -287,11 +287,13 @@ askit_status askit_graph_destroy(askit_graph g);
  *   tiled_runs  1: runs of 8 consecutive target rows arrive in one tiled
  *               copy (per-sub-block FP16x3 kernel), 0: every row by
  *               tile::gather4;
- *   pairs       1: the FP16x3 kernel takes sub-blocks 2k and 2k+1 of a node
+ *   pairs       1: the FP16x3 kernels take sub-blocks 2k and 2k+1 of a node
  *               (same targets) in one 256-column item (schedule 2: the
- *               leaders dealt longest first), r <= 4.
- * Only the schedule varies for the other tensor-core kernels; the plain FP32
- * kernel has one configuration.  Schedules, stages and tiled runs change no
+ *               leaders dealt longest first), r <= 4; so does the K-chunked
+ *               kernel for d > 64 (FP16x3 and BF16x3, any r <= 16), which
+ *               then copies and splits each target row once for both.
+ * Only the schedule (and, for d > 64, pairs) varies for the other tensor-core
+ * kernels; the plain FP32 kernel has one configuration.  Schedules, stages and tiled runs change no
  * result bit (every work item is computed the same way; partials are reduced
  * in a fixed order); paired items sum both sub-blocks' columns in one
  * accumulator, which changes the FP32 summation order only.  `reps` timed evaluations per candidate after one warm-up; at most

@@ -49,6 +49,9 @@ constexpr int ASK_TILE_M = 128;
 // Source rows per sub-block (one tensor-core N tile); leaves and skeletons
 // longer than this are split into consecutive sub-blocks.
 constexpr int ASK_BLK_N = 128;
+// Items per segment of a sub-block's items (schedule of the K-chunked kernel's
+// paired items).
+constexpr int ASK_SEG_ITEMS = 16;
 // Columns of the tensor-core operand arrays (d <= TC_K).
 constexpr int TC_K = 64;
 // Default and largest entries of one in-sample work-list batch (entry
@@ -138,6 +141,15 @@ struct WorkLists {
     int n_ctas_sched[3] = {0, 0, 0};
     int32_t *partner = nullptr;      // [n_blocks] the paired follower of a leader block, else -1
     int64_t n_pairs = 0;
+    // segments: every sub-block's items cut into runs of at most
+    // ASK_SEG_ITEMS (a follower at its leader's cuts), the leaders' segments
+    // dealt block by block, heaviest first, to the least-loaded CTA (the
+    // K-chunked kernel's paired items: the CTAs work on few blocks at a time)
+    int64_t n_seg = 0;
+    int32_t *seg_off = nullptr;      // [n_seg + 1] items of each segment
+    int32_t *seg_partner = nullptr;  // [n_seg] the follower's segment, else -1
+    int32_t *seg_sched_off = nullptr;   // [n_ctas + 1]
+    int32_t *seg_sched = nullptr;       // [leader segments]
     int64_t pairs_alg = 0, pairs_cmp = 0, near_tot = 0, far_tot = 0;
 };
 
@@ -223,12 +235,13 @@ struct askit_tree_s {
     int64_t wl_entries = 0, wl_entries_max = 0;
 
     // tensor-core operands: every source sub-block centered on its own mean,
-    // split into hi + lo parts (TF32 and BF16), TC_K columns, and the squared
-    // norms of the centered rows
+    // split into hi + lo parts (TF32 and BF16), kw columns (TC_K, or d_pad
+    // for wide rows, whose 16-bit splits are stored as planes of 8-column K
+    // groups, [kw / 8][rows][8]), and the squared norms of the centered rows
     int64_t n_sub = 0;
     int32_t *leaf_cbase = nullptr; // [2^L] first sub-block of each leaf
     int32_t *node_cbase = nullptr; // [n_nodes] first sub-block of each skeleton
-    float *cent = nullptr;         // [n_sub, TC_K]
+    float *cent = nullptr;         // [n_sub, kw]
     float *Xt_hi = nullptr, *Xt_lo = nullptr, *Xs_hi = nullptr, *Xs_lo = nullptr;   // TF32 split
     uint16_t *Xt_bhi = nullptr, *Xt_blo = nullptr, *Xs_bhi = nullptr, *Xs_blo = nullptr; // BF16 split
     uint16_t *Xt_hhi = nullptr, *Xt_hlo = nullptr, *Xs_hhi = nullptr, *Xs_hlo = nullptr; // FP16 split (prescaled)

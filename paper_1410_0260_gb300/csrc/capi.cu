@@ -857,6 +857,10 @@ askit_status askit_autotune(askit_tree t, int32_t reps, void *stream, askit_tune
     if (fp16 && t->dw.r <= 4 && n_pairs > 0)
         for (int st = g16 ? st_lo : 2; st <= (g16 ? st_hi : 2); ++st)
             for (int ru = ru_lo; ru <= ru_hi; ++ru) cand.push_back({2, st, ru, 1, 0.0});
+    // the K-chunked kernel (d > TC_K, 16-bit splits) pairs at any r; its
+    // stages and runs are fixed
+    const bool wide = t->d > TC_K && (t->precision == ASKIT_PREC_FP16X3 || t->precision == ASKIT_PREC_BF16X3);
+    if (wide && n_pairs > 0) cand.push_back({2, t->tune_stages, t->tune_runs, 1, 0.0});
     float *U = nullptr;
     ASK_CUDA(cudaMallocAsync(&U, sizeof(float) * (size_t)t->N * std::max(1, t->dw.r), s));
     cudaEvent_t e0 = nullptr, e1 = nullptr;

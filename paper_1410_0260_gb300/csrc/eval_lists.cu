@@ -367,8 +367,12 @@ askit_status build_eval_operands(askit_tree t, cudaStream_t s) {
 // rows only): hi = the FP32 value with the 13 low mantissa bits cleared,
 // lo = x - hi; BF16: hi = bf16(x), lo = bf16(x - hi); FP16 likewise on the
 // prescaled value -- and the squared norms of the centered rows.  Rows are
-// kw wide (zeros past d); one warp per row, lanes across the columns.
-__global__ void tc_prep_kernel(const float *X, int d_pad, int kw, const int64_t *sb_row0, const int32_t *sb_nrows,
+// kw wide (zeros past d); one warp per row, lanes across the columns.  Wide
+// rows (kgplanes) store the 16-bit splits as planes of K groups,
+// [kw / 8][rows_total][8], so that a K chunk of consecutive rows is a few
+// contiguous runs (the wide kernel's TMA boxes).
+__global__ void tc_prep_kernel(const float *X, int d_pad, int kw, bool kgplanes, const int64_t *sb_row0,
+                               const int32_t *sb_nrows,
                                const int64_t *nd_row0, const int32_t *nd_nrows, int64_t rows_total, float f16_scale,
                                float *cent, float *Xhi, float *Xlo, uint16_t *Bhi, uint16_t *Blo, uint16_t *Hhi,
                                uint16_t *Hlo, float *nrmc) {
@@ -398,7 +402,7 @@ __global__ void tc_prep_kernel(const float *X, int d_pad, int kw, const int64_t 
         for (int k = lane; k < kw; k += 32) {
             const float x = (k < d_pad) ? X[row * d_pad + k] - c[k] : 0.f;
             nn += (double)x * x;
-            const int64_t o = row * kw + k;
+            const int64_t o = kgplanes ? (((int64_t)(k >> 3) * rows_total + row) << 3) + (k & 7) : row * kw + k;
             if (Xhi) {
                 const float hi = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
                 Xhi[o] = hi;
@@ -472,10 +476,10 @@ askit_status build_tc_operands(askit_tree t, cudaStream_t s) {
     ASK_CUDA(cudaMemcpyAsync(t->leaf_cbase, lcb.data(), sizeof(int32_t) * M, cudaMemcpyHostToDevice, s));
     ASK_CUDA(cudaMemcpyAsync(t->node_cbase, ncb.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice, s));
     // narrow rows (d <= TC_K) get TC_K columns and all three splits; wide
-    // rows are rounded up to a multiple of 64 columns and get the 16-bit
-    // splits only
+    // rows keep their d_pad columns (a multiple of 32, the K chunk of the
+    // wide kernel) and get the 16-bit splits only
     const bool wide = t->d > TC_K;
-    const int kw = wide ? (t->d_pad + 63) / 64 * 64 : TC_K;
+    const int kw = wide ? t->d_pad : TC_K;
     if (kw > 8192) return ASKIT_OK;     // no tensor-core operands (plain FP32 path only)
     t->kw = kw;
     ASK_TRY(t->arena.alloc(&t->sb_row0, std::max<int64_t>(1, t->n_sub)));
@@ -532,12 +536,12 @@ askit_status build_tc_operands(askit_tree t, cudaStream_t s) {
     }
     const size_t csm = sizeof(float) * kw;
     if (n_leaf_sub > 0)
-        tc_prep_kernel<<<(unsigned)n_leaf_sub, 256, csm, s>>>(t->Xt, t->d_pad, kw, d_r0, d_nr, d_nd0, d_ndn, t->N_pad,
+        tc_prep_kernel<<<(unsigned)n_leaf_sub, 256, csm, s>>>(t->Xt, t->d_pad, kw, wide, d_r0, d_nr, d_nd0, d_ndn, t->N_pad,
                                                             t->f16_scale, t->cent, t->Xt_hi, t->Xt_lo, t->Xt_bhi,
                                                             t->Xt_blo, t->Xt_hhi, t->Xt_hlo, t->nrmc_t);
     if (t->n_sub > n_leaf_sub)
         tc_prep_kernel<<<(unsigned)(t->n_sub - n_leaf_sub), 256, csm, s>>>(
-            t->Xs, t->d_pad, kw, d_r0 + n_leaf_sub, d_nr + n_leaf_sub, d_nd0 + n_leaf_sub, d_ndn + n_leaf_sub,
+            t->Xs, t->d_pad, kw, wide, d_r0 + n_leaf_sub, d_nr + n_leaf_sub, d_nd0 + n_leaf_sub, d_ndn + n_leaf_sub,
             t->srows, t->f16_scale, t->cent + n_leaf_sub * kw, t->Xs_hi, t->Xs_lo, t->Xs_bhi, t->Xs_blo, t->Xs_hhi,
             t->Xs_hlo, t->nrmc_s);
     ASK_LAUNCH();
@@ -874,6 +878,57 @@ askit_status build_work_lists(askit_tree t, const int32_t *sets, int stride, con
             }
             w.n_pairs = np;
         }
+        {
+            std::vector<int32_t> soff, sfirst(nb + 1, 0);
+            for (int64_t b = 0; b < nb; ++b) {
+                sfirst[b] = (int32_t)soff.size();
+                for (int32_t i = boff[b]; i < boff[b + 1]; i += ASK_SEG_ITEMS) soff.push_back(i);
+            }
+            sfirst[nb] = (int32_t)soff.size();
+            const int64_t nseg = (int64_t)soff.size();
+            soff.push_back(boff[nb]);
+            std::vector<int32_t> spart(std::max<int64_t>(1, nseg), -1);
+            for (int64_t b = 0; b < nb; ++b)
+                if (partner[b] >= 0)
+                    for (int32_t k = 0; k < sfirst[b + 1] - sfirst[b]; ++k) spart[sfirst[b] + k] = sfirst[partner[b]] + k;
+            std::vector<std::vector<int32_t>> lists(nc);
+            std::vector<std::pair<int64_t, int>> heap;
+            for (int c = 0; c < nc; ++c) heap.push_back({0, c});
+            auto cmp = [](const std::pair<int64_t, int> &x, const std::pair<int64_t, int> &y) {
+                return x.first > y.first || (x.first == y.first && x.second > y.second);
+            };
+            std::make_heap(heap.begin(), heap.end(), cmp);
+            for (int64_t q = 0; q < nb; ++q) {
+                const int32_t bq = order[q];
+                if (follower[bq]) continue;
+                for (int32_t sg = sfirst[bq]; sg < sfirst[bq + 1]; ++sg) {
+                    std::pop_heap(heap.begin(), heap.end(), cmp);
+                    auto top = heap.back();
+                    heap.pop_back();
+                    lists[top.second].push_back(sg);
+                    top.first += ((int64_t)(soff[sg + 1] - soff[sg]) * 4 + 3) * (partner[bq] >= 0 ? 2 : 1);
+                    heap.push_back(top);
+                    std::push_heap(heap.begin(), heap.end(), cmp);
+                }
+            }
+            std::vector<int32_t> so(nc + 1, 0), sl;
+            for (int c = 0; c < nc; ++c) {
+                so[c + 1] = so[c] + (int32_t)lists[c].size();
+                sl.insert(sl.end(), lists[c].begin(), lists[c].end());
+            }
+            w.n_seg = nseg;
+            WTRY(arena.alloc(&w.seg_off, nseg + 1));
+            WTRY(arena.alloc(&w.seg_partner, std::max<int64_t>(1, nseg)));
+            WTRY(arena.alloc(&w.seg_sched_off, nc + 1));
+            WTRY(arena.alloc(&w.seg_sched, std::max<size_t>(1, sl.size())));
+            WCHK(cudaMemcpyAsync(w.seg_off, soff.data(), sizeof(int32_t) * (nseg + 1), cudaMemcpyHostToDevice, s));
+            WCHK(cudaMemcpyAsync(w.seg_partner, spart.data(), sizeof(int32_t) * spart.size(), cudaMemcpyHostToDevice, s));
+            WCHK(cudaMemcpyAsync(w.seg_sched_off, so.data(), sizeof(int32_t) * (nc + 1), cudaMemcpyHostToDevice, s));
+            if (!sl.empty())
+                WCHK(cudaMemcpyAsync(w.seg_sched, sl.data(), sizeof(int32_t) * sl.size(), cudaMemcpyHostToDevice, s));
+            // the host vectors must outlive the copies
+            WCHK(cudaStreamSynchronize(s));
+        }
         w.n_ctas = nc;
         for (int k = 0; k < 3; ++k) {
             WTRY(arena.alloc(&w.sched_off[k], nc + 1));
@@ -967,7 +1022,7 @@ askit_status build_insample_lists(askit_tree t, const PruneSets &ps, cudaStream_
 void free_work_lists(WorkLists &w, DevArena &arena) {
     void *ptrs[] = {w.off, w.slot_of_emit, w.tgt, w.items, w.block_off, w.block_order, w.sched_off[0],
                     w.sched_off[1], w.sched_off[2], w.sched_blocks[0], w.sched_blocks[1], w.sched_blocks[2],
-                    w.partner};
+                    w.partner, w.seg_off, w.seg_partner, w.seg_sched_off, w.seg_sched};
     for (void *p : ptrs)
         if (p) arena.release(p);
     w = WorkLists();

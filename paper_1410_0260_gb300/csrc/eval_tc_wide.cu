@@ -1,9 +1,11 @@
 // Evaluate (Algorithm 4) on the tcgen05 tensor cores for wide points
-// (64 < d): the distance contraction runs over K = d in chunks of 64.
+// (64 < d): the distance contraction runs over K = d in chunks of 32.
 //
-// Work items are the same as for the narrow kernel (one source sub-block of
-// <= 128 rows against <= 128 targets that need it).  Here both sides are
-// centered on the sub-block's mean c_B:
+// Work items are the same as for the narrow kernels (one source sub-block of
+// <= 128 rows against <= 128 targets that need it), optionally paired: the
+// two sub-blocks of one node need the same targets and share the node's
+// center c_B, so one 256-column item serves both with a single copy and split
+// of its target rows.  Both sides are centered on c_B:
 //
 //     a = x - c_B (targets, split on chip),  b = y - c_B (sources, pre-split)
 //     r^2 = |a|^2 + |b|^2 - 2 a.b
@@ -14,24 +16,38 @@
 // epilogue adds the two, forms exp2(-c log2(e) r^2 / h_j^2) on MUFU.EX2 and
 // reduces against the weights.
 //
+// Operands in shared memory use the tensor core's layout without swizzle:
+// 8-row x 16-byte core matrices, a chunk's four K groups of 8 elements one
+// after another ([K group][rows][16 B]).  The pre-split sub-block rows are
+// stored in HBM as planes of K groups, so each split's chunk arrives in that
+// layout from one 3-D TMA box ({8 rows x 8 elements, rows / 8, 4 K
+// groups}); the
+// loaders write the split target rows the same way (16 bytes a row, no bank
+// conflicts).
+//
 // One CTA per SM, 448 threads:
-//   warps 0-7  loaders: thread t handles half (t >> 7) of target row t & 127
-//              of each K chunk: loads its 32 FP32 values straight from HBM
-//              into registers one chunk ahead (the next item's row slot is
-//              read one item ahead), subtracts c_B, accumulates |a|^2, splits
-//              into FP16/BF16 hi + lo and stores both in the 128-byte
-//              swizzled K-major layout; they also write the item's column
-//              data (c log2(e) / h^2, |b|^2, w) for the epilogue;
+//   warps 0-7  loaders.  Copy: warp w brings half w >> 2 of rows
+//              32 (w & 3) .. + 31 of a chunk's FP32 target rows into a raw
+//              buffer (4 lanes along a half row, 8 rows an instruction), three
+//              (r > 4: one) chunks ahead of the split;
+//              split: thread t takes half (t >> 7) of row t & 127 of the
+//              chunk, subtracts c_B (read from global memory), accumulates
+//              |a|^2, splits into FP16/BF16 hi + lo; they also write the
+//              item's column data (c log2(e) / h^2, |b|^2, w) for the
+//              epilogue, double-buffered so that they run on into the next
+//              item while the epilogue drains the last;
 //   warps 8-11 epilogue (TMEM lane quadrant = warp & 3);
 //   warp 12    TMEM allocation; lane 0 issues the tcgen05.mma instructions;
-//   warp 13    producer: TMA tiled load of the sub-block's hi and lo chunk
-//              and a bulk copy of c_B's chunk (a TMA tile::gather4 of the
-//              target rows cost about 75 issue cycles per four rows, several
-//              times the chunk's MMA time).
-// Two chunk stages in shared memory; two items' accumulators (main + cross)
-// fill all 512 TMEM columns, so the MMAs of item i+1 overlap the epilogue
-// of item i.  Every mbarrier wait is bounded: on timeout the kernel records
-// ASK_DEV_TIMEOUT, every role leaves its loop, and TMEM is freed.
+//   warp 13    producer: TMA of the sub-block's hi and lo chunk.
+// Chunk stages in two rings, released separately by the MMAs' commits: four
+// (r > 4: three) of the split targets, so that the loaders run on across an
+// item's end, and three of the sub-block's chunk, requested two chunks' MMAs
+// before it is needed.  Single sub-blocks: two items' accumulators (main +
+// cross) fill TMEM's 512 columns, so the MMAs of item i+1 overlap the
+// epilogue of item i; paired items: one item's 256-column accumulators fill
+// it.  Every mbarrier wait is bounded: on timeout the kernel records
+// ASK_DEV_TIMEOUT, every role leaves its loop, copies in flight are waited
+// for, and TMEM is freed.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -47,35 +63,54 @@ using namespace tcx;
 
 constexpr int W_THREADS = 448;
 constexpr int W_ROWS = 128;
-constexpr int W_KC = 64;                        // K elements per chunk (128 bytes of 16-bit)
-constexpr int W_REGION = W_ROWS * 128;          // 128 rows x 128 bytes, swizzled (16 KB)
-constexpr uint32_t W_TMEM_COLS = 512;           // [main acc 0, main acc 1, cross acc 0, cross acc 1]
+constexpr int W_KC = 32;                        // K elements per chunk
+constexpr int W_KG = 4;                         // K groups of 8 elements per chunk
+constexpr int W_REGION = W_ROWS * W_KC * 2;     // one 16-bit split of 128 rows (8 KB)
+constexpr uint32_t W_TMEM_COLS = 512;           // main accumulators, then cross accumulators
 
-template <int RC>
+// Shared-memory descriptor of a K-major operand without swizzle: the next
+// core matrix along K `lbo` bytes on, along M/N 128 bytes on (8 rows of 16
+// bytes); version bit 46, layout type 0.
+__device__ __forceinline__ uint64_t nsw_desc(uint32_t saddr, uint32_t lbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(128 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+template <int RC, int NB>
 struct WSmem {
-    // one chunk stage: A hi, A lo, B hi, B lo, c_B chunk
-    static constexpr int A_HI = 0, A_LO = W_REGION, B_HI = 2 * W_REGION, B_LO = 3 * W_REGION;
-    static constexpr int CENTC = 4 * W_REGION;
-    static constexpr int STAGE = CENTC + 1024;   // c_B chunk (256 B), stage kept 1024-byte aligned
-    // two buffers of a chunk's raw FP32 target rows [128 rows][64], copied by
-    // the loaders themselves (lanes along a row)
-    static constexpr int RAW0 = 2 * STAGE;
+    static constexpr int NSLOT = NB == 1 ? 2 : 1;   // items in flight in TMEM
+    static constexpr int NCOL = NB * W_ROWS;        // columns of an item
+    // Two rings of chunk stages, released separately by the MMAs' commits:
+    // NSA stages of the split targets (A hi, A lo: [4][128][16 B] each),
+    // NSB of the sub-block's (B hi, B lo: [4][NCOL][16 B] each).
+    static constexpr int NSA = RC <= 4 ? 4 : 3;
+    static constexpr int NSB = 3;
+    static constexpr int NRAW = RC <= 4 ? 3 : 2;    // raw target-row buffers: NRAW - 1 chunks read ahead
+    static constexpr int A_STAGE = 2 * W_REGION, B_STAGE = 2 * NB * W_REGION;
+    static constexpr int A_LO = W_REGION, B_LO = NB * W_REGION;   // within a stage
+    static constexpr int B0 = NSA * A_STAGE;
+    // NRAW buffers of a chunk's raw FP32 target rows [128 rows][32], a
+    // row's 16-byte pieces XOR-permuted by (row & 7) for conflict-free reads
+    static constexpr int RAW0 = B0 + NSB * B_STAGE;
     static constexpr int RAW_BYTES = W_ROWS * W_KC * 4;
-    static constexpr int ANORM = RAW0 + 2 * RAW_BYTES;   // float [2 acc][2 halves][128]
-    static constexpr int COLV = ANORM + 2 * 2 * 128 * 4;   // float4 [2 acc][128]
-    static constexpr int COLW = COLV + 2 * 128 * 16;       // float [2 acc][128][RC]
-    static constexpr int BAR = COLW + 2 * 128 * RC * 4;    // 16 mbarriers
-    static constexpr int MISC = BAR + 16 * 8;              // tmem address, abort flag
+    // the column data and |a|^2 of two items (item li in buffer li & 1), so
+    // that the loaders move on to the next item while the epilogue runs
+    static constexpr int ANORM = RAW0 + NRAW * RAW_BYTES;      // float [2][2 halves][128]
+    static constexpr int COLV = ANORM + 2 * 2 * 128 * 4;       // float4 [2][NCOL]
+    static constexpr int COLW = COLV + 2 * NCOL * 16;          // float [2][NCOL][RC]
+    static constexpr int BAR = COLW + 2 * NCOL * RC * 4;       // 32 mbarriers
+    static constexpr int MISC = BAR + 32 * 8;                  // tmem address, abort flag
     static constexpr int BYTES = MISC + 16;
-    static constexpr uint32_t TX = 2 * W_REGION + W_KC * 4;   // bytes landing per chunk
+    static constexpr uint32_t TX = 2 * NB * W_REGION;   // bytes landing per chunk
 };
 
 struct TcwArgs {
     const EvalItem *items;
     const int32_t *block_off;
     const int32_t *cta_off, *cta_blocks;
+    const int32_t *partner;   // [n_blocks] paired follower block, or -1 (NB == 2)
     const int32_t *tgt;       // entry -> target slot
-    int nkc;                  // K chunks (kw / 64)
+    int nkc;                  // K chunks (kw / 32)
     int kw;                   // row width of the pre-split arrays and of the centers
     const float *cent;        // [n_sub, kw]
     const float *q;           // target rows [q_rows, ldq] FP32 (16-byte aligned)
@@ -89,48 +124,47 @@ struct TcwArgs {
     int *status;
 };
 
-// GF(4) multiplication by a primitive element: x -> w x is a permutation of
-// {0,1,2,3} and so is x -> w x ^ x (= w^2 x), which makes both the loaders'
-// swizzled stores and their raw-row reads free of bank conflicts.
-__device__ __forceinline__ int gf4_mulw(int x) { return (0x1320 >> (4 * x)) & 3; }
-
-template <int P, int RC>
+template <int P, int RC, int NB>
 __global__ void __launch_bounds__(W_THREADS, 1)
 eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_constant__ CUtensorMap map_t_lo,
                 const __grid_constant__ CUtensorMap map_s_hi, const __grid_constant__ CUtensorMap map_s_lo,
+                const __grid_constant__ CUtensorMap map_t_hi1, const __grid_constant__ CUtensorMap map_t_lo1,
                 const TcwArgs args) {
-    using S = WSmem<RC>;
+    using S = WSmem<RC, NB>;
+    constexpr int NSLOT = S::NSLOT, NCOL = S::NCOL, NSA = S::NSA, NSB = S::NSB, NRAW = S::NRAW;
     constexpr uint32_t FMT = P == ASKIT_PREC_BF16X3 ? 1u : 0u;
-    constexpr uint32_t IDESC = make_idesc(FMT, W_ROWS, W_ROWS);
+    constexpr uint32_t IDESC = make_idesc(FMT, W_ROWS, NCOL);
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     const uint32_t sbase = smem_u32(sm);
     float *a_norm = reinterpret_cast<float *>(sm + S::ANORM);
     float4 *colv = reinterpret_cast<float4 *>(sm + S::COLV);
     float *colw = reinterpret_cast<float *>(sm + S::COLW);
     const uint32_t bar0 = sbase + S::BAR;
-    auto BAR_A_FULL = [&](int s) { return bar0 + 8 * s; };          // loaders stored A of stage s (256)
-    auto BAR_MMA_DONE = [&](int s) { return bar0 + 8 * (2 + s); };  // MMAs of stage s finished (commit)
-    auto BAR_L_FULL = [&](int s) { return bar0 + 8 * (4 + s); };    // raw rows, B and c_B of stage s landed
-    auto BAR_R_EMPTY = [&](int s) { return bar0 + 8 * (6 + s); };   // loaders done with raw/c_B of stage s (256)
-    auto BAR_T_FULL = [&](int a) { return bar0 + 8 * (8 + a); };    // accumulators of item slot a complete
-    auto BAR_T_EMPTY = [&](int a) { return bar0 + 8 * (10 + a); };  // epilogue drained slot a (128)
-    auto BAR_RAW_FULL = [&](int b) { return bar0 + 8 * (12 + b); }; // raw rows of buffer b landed (256 copiers)
-    auto BAR_RAW_FREE = [&](int b) { return bar0 + 8 * (14 + b); }; // buffer b split by every loader (256)
+    auto BAR_A_FULL = [&](int s) { return bar0 + 8 * s; };          // loaders stored A stage s (256)
+    auto BAR_A_FREE = [&](int s) { return bar0 + 8 * (4 + s); };    // MMAs reading A stage s finished (commit)
+    auto BAR_L_FULL = [&](int s) { return bar0 + 8 * (8 + s); };    // B stage s landed
+    auto BAR_B_FREE = [&](int s) { return bar0 + 8 * (12 + s); };   // MMAs reading B stage s finished (commit)
+    auto BAR_COL_EMPTY = [&](int c) { return bar0 + 8 * (16 + c); };// epilogue done with column buffer c (128)
+    auto BAR_T_FULL = [&](int a) { return bar0 + 8 * (18 + a); };   // accumulators of item slot a complete
+    auto BAR_T_EMPTY = [&](int a) { return bar0 + 8 * (20 + a); };  // epilogue drained slot a (128)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + S::MISC);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + S::MISC + 4);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < NSA; ++s) {
             mbar_init(BAR_A_FULL(s), 256);
-            mbar_init(BAR_MMA_DONE(s), 1);
+            mbar_init(BAR_A_FREE(s), 1);
+        }
+        for (int s = 0; s < NSB; ++s) {
             mbar_init(BAR_L_FULL(s), 1);
-            mbar_init(BAR_R_EMPTY(s), 256);
-            mbar_init(BAR_T_FULL(s), 1);
-            mbar_init(BAR_T_EMPTY(s), 128);
-            mbar_init(BAR_RAW_FULL(s), 256);
-            mbar_init(BAR_RAW_FREE(s), 256);
+            mbar_init(BAR_B_FREE(s), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(BAR_T_FULL(a), 1);
+            mbar_init(BAR_T_EMPTY(a), 128);
+            mbar_init(BAR_COL_EMPTY(a), 128);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -146,164 +180,188 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
     const uint32_t tmem = *tmem_slot;
     const int nkc = args.nkc;
     const int c_begin = args.cta_off[blockIdx.x], c_end = args.cta_off[blockIdx.x + 1];
+    // rows of the follower of block b's pair (0: none)
+    auto follower_rows = [&](int b, int &f0) -> int {
+        const int pb = NB == 2 ? args.partner[b] : -1;
+        f0 = pb >= 0 ? args.block_off[pb] : 0;
+        return pb >= 0 ? (args.items[f0].nrows & 0x7fffffff) : 0;
+    };
 
     if (warp < 8) {
         // ------------------------------------------------------------ loaders
-        // Copies: loader warp lw brings rows 16 lw .. 16 lw + 15 of the next
-        // chunk into a raw buffer, two rows per instruction, 16 lanes along a
-        // row's 256 bytes (so an instruction touches 4 cache lines, not 32),
-        // zero-filled past ldq and for rows past the item's targets; each
-        // thread's arrival on RAW_FULL fires when its copies have landed.
-        // Split: thread (row, h) then centers, splits and stores its half of
-        // row `row` of the chunk (conflict-free order of the 16-byte reads).
+        // Thread t splits half h = t >> 7 of row t & 127 of every chunk, so
+        // warp w splits half w >> 2 of rows 32 (w & 3) .. + 31; it also copies
+        // exactly those bytes (lanes: 4 pieces of 16 B along a half row x 8
+        // rows an instruction), so a raw buffer is private to the warp and
+        // its copies need no block-wide barrier: cp.async groups and
+        // __syncwarp.  Copies run NRAW - 1 chunks ahead of the split on a fill
+        // cursor of their own (item and chunk in this CTA's order); the copy
+        // slots of the item after the fill cursor's are read one item ahead.
         const int row = tid & 127, h = tid >> 7;
-        const int lw = tid >> 5, cpiece = lane & 15;
-        int cs[8], ns[8];           // target slots of this lane's copy rows: current item, next item
-        uint32_t cmask = 0, nmask = 0;
-        auto copy_slots = [&](int ci, int it, int (&sl)[8], uint32_t &mask) {
+        const int cpiece = 4 * h + (lane & 3);            // 16-byte piece of a row's 128-byte chunk
+        const int crow0 = 32 * (warp & 3) + (lane >> 2);  // copy rows crow0 + 8 i
+        struct Cur { int ci, it, i1; };    // cta_blocks index, item, end of its block
+        auto advance = [&](Cur &c) {
+            if (++c.it < c.i1) return;
+            while (++c.ci < c_end) {
+                const int b = args.cta_blocks[c.ci];
+                c.it = args.block_off[b];
+                c.i1 = args.block_off[b + 1];
+                if (c.it < c.i1) return;
+            }
+        };
+        auto copy_slots = [&](const Cur &c, int (&sl)[4], uint32_t &mask) {
             mask = 0;
-            if (ci >= c_end) return;
-            const EvalItem nx = args.items[it];
+            if (c.ci >= c_end) return;
+            const EvalItem nx = args.items[c.it];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int r = 16 * lw + 2 * i + (lane >> 4);
+            for (int i = 0; i < 4; ++i) {
+                const int r = crow0 + 8 * i;
                 sl[i] = r < nx.cnt ? args.tgt[nx.e0 + r] : 0;
                 if (r < nx.cnt) mask |= 1u << i;
             }
         };
-        auto issue_copies = [&](const int (&sl)[8], uint32_t mask, int kc, int buf) {
-            const uint32_t dst0 = sbase + S::RAW0 + buf * S::RAW_BYTES;
-            const int64_t col = (int64_t)kc * W_KC + 4 * cpiece;
-            const bool in_row = col < args.ldq;
+        Cur fc{c_begin - 1, 0, 0};
+        advance(fc);               // the CTA's first item
+        Cur nc = fc;
+        advance(nc);
+        int fs[4], ns[4];
+        uint32_t fmask = 0, nmask = 0;
+        copy_slots(fc, fs, fmask);
+        copy_slots(nc, ns, nmask);
+        int fkc = 0, gf = 0;       // fill cursor's chunk; chunks filled so far
+        // the fill cursor's chunk into raw buffer gf % NRAW (its last chunk,
+        // gf - NRAW, split by this warp); one cp.async group per call, empty
+        // past the CTA's last item
+        auto fill_one = [&]() {
+            if (fc.ci < c_end) {
+                const uint32_t dst0 = sbase + S::RAW0 + (gf % NRAW) * S::RAW_BYTES;
+                const int64_t col = (int64_t)fkc * W_KC + 4 * cpiece;
+                const bool in_row = col < args.ldq;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int r = 16 * lw + 2 * i + (lane >> 4);
-                const bool ok = in_row && ((mask >> i) & 1u);
-                const float *src = ok ? args.q + (int64_t)sl[i] * args.ldq + col : args.q;
-                cp_async16_zfill(dst0 + (uint32_t)(r * W_KC * 4 + cpiece * 16), src, ok ? 16u : 0u);
+                for (int i = 0; i < 4; ++i) {
+                    const int r = crow0 + 8 * i;
+                    const bool ok = in_row && ((fmask >> i) & 1u);
+                    const float *src = ok ? args.q + (int64_t)fs[i] * args.ldq + col : args.q;
+                    cp_async16_zfill(dst0 + (uint32_t)(r * W_KC * 4 + ((cpiece ^ (r & 7)) << 4)), src, ok ? 16u : 0u);
+                }
+                ++gf;
+                if (++fkc == nkc) {
+                    fkc = 0;
+                    fc = nc;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) fs[i] = ns[i];
+                    fmask = nmask;
+                    advance(nc);
+                    copy_slots(nc, ns, nmask);
+                }
             }
-            cp_async_mbar_arrive(BAR_RAW_FULL(buf));
-        };
-        // the item after (ci, it) in this CTA's order, or ci == c_end
-        auto next_item = [&](int &ci, int &it) {
-            ++it;
-            while (ci < c_end && it >= args.block_off[args.cta_blocks[ci] + 1]) {
-                if (++ci < c_end) it = args.block_off[args.cta_blocks[ci]];
-            }
+            cp_async_commit();
         };
         int g = 0, li = 0;
-        if (c_begin < c_end) {
-            copy_slots(c_begin, args.block_off[args.cta_blocks[c_begin]], cs, cmask);
-            issue_copies(cs, cmask, 0, 0);          // chunk 0 into buffer 0
-        }
-        for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci) {
+        for (int k = 0; k < NRAW - 1; ++k) fill_one();
+        const float2 neg1 = make_float2(-1.f, -1.f);
+        const float2 sc2 = make_float2(args.f16_scale, args.f16_scale);
+        // every exit below is taken by the whole warp (warp-wide votes), so
+        // that no __syncwarp waits for a lane that has left
+        for (int ci = c_begin; ci < c_end && !__shfl_sync(0xffffffffu, *abort_flag, 0); ++ci) {
             const int b = args.cta_blocks[ci];
             const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
             const EvalItem first = args.items[i0];
             const bool far = first.nrows < 0;
-            const int nrows = first.nrows & 0x7fffffff;
-            const bool has_src = row < nrows;
-            const int64_t srow = (int64_t)first.row0 + row;
+            int f0 = 0;
+            const int nrows_f = follower_rows(b, f0);
+            // the source column this thread describes: single sub-blocks,
+            // column `row` (half 0 only); pairs, column 128 h + row
+            const int col = NB == 2 ? 128 * h + row : row;
+            const bool writes_col = NB == 2 || h == 0;
+            const int nrows_c = (NB == 2 && h == 1) ? nrows_f : (first.nrows & 0x7fffffff);
+            const bool has_src = row < nrows_c;
+            const int64_t srow = (int64_t)first.row0 + (NB == 2 ? 128 * h : 0) + row;
             const float sc = has_src ? __ldg((far ? args.sc_s : args.sc_t) + srow) : 0.f;
             const float qn = has_src ? __ldg((far ? args.nrm_s : args.nrm_t) + srow) : 0.f;
             const float *wrow = (far ? args.Ws : args.Wt) + srow * args.r;
+            // c_B, read from global memory (the same 64 bytes for a warp)
+            const float4 *cen = reinterpret_cast<const float4 *>(args.cent + (int64_t)first.cidx * args.kw) + 4 * h;
             for (int it = i0; it < i1; ++it, ++li) {
-                const int a = li & 1;
+                const int cbuf = li & 1;
                 const int cnt = args.items[it].cnt;
                 const bool has_tgt = row < cnt;
-                // the next item's copy slots, one item ahead
-                int nci = ci, nit = it;
-                next_item(nci, nit);
-                copy_slots(nci, nit, ns, nmask);
-                const bool has_next = nci < c_end;
-                if (!mbar_wait(BAR_T_EMPTY(a), ((li >> 1) & 1) ^ 1, abort_flag, args.status)) goto loader_done;
-                // column data of source row `row` for this item's slot:
+                if (!__all_sync(0xffffffffu, mbar_wait(BAR_COL_EMPTY(cbuf), ((li >> 1) & 1) ^ 1, abort_flag, args.status)))
+                    goto loader_done;
+                // column data of source column `col` for this item's buffer:
                 // arg = g A + (C p + B) = -sc (p + q - 2 g / scale^2)
-                if (h == 0) {
-                    float *cp = reinterpret_cast<float *>(colv + a * 128 + 2 * (row >> 1));
-                    const int o = row & 1;
+                if (writes_col) {
+                    float *cp = reinterpret_cast<float *>(colv + cbuf * NCOL + 2 * (col >> 1));
+                    const int o = col & 1;
                     cp[0 + o] = 2.f * args.g_unscale * sc;
                     cp[2 + o] = -sc * qn;
                     cp[4 + o] = -sc;
                     cp[6 + o] = has_src ? __ldg(wrow) : 0.f;
-                } else if (RC > 1) {
+                    if (RC > 1) {
 #pragma unroll
-                    for (int z = 0; z < RC; ++z)
-                        colw[(a * 128 + row) * RC + z] = (has_src && z < args.r) ? __ldg(wrow + z) : 0.f;
-                }
-                float nn = 0.f;
-                for (int kc = 0; kc < nkc; ++kc, ++g) {
-                    const int s = g & 1;
-                    const uint32_t par = (g >> 1) & 1;
-                    // the next chunk's rows into the other raw buffer, once every
-                    // loader has split the chunk it held (chunk g - 1)
-                    const int nb = (g + 1) & 1;
-                    if (kc + 1 < nkc || has_next) {
-                        if (!mbar_wait(BAR_RAW_FREE(nb), (((g + 1) >> 1) & 1) ^ 1, abort_flag, args.status))
-                            goto loader_done;
-                        if (kc + 1 < nkc) issue_copies(cs, cmask, kc + 1, nb);
-                        else issue_copies(ns, nmask, 0, nb);
+                        for (int z = 0; z < RC; ++z)
+                            colw[(cbuf * NCOL + col) * RC + z] = (has_src && z < args.r) ? __ldg(wrow + z) : 0.f;
                     }
-                    if (!mbar_wait(BAR_MMA_DONE(s), par ^ 1, abort_flag, args.status)) goto loader_done;
-                    if (!mbar_wait(BAR_L_FULL(s), par, abort_flag, args.status)) goto loader_done;
-                    if (!mbar_wait(BAR_RAW_FULL(s), par, abort_flag, args.status)) goto loader_done;
-                    uint8_t *st = sm + s * S::STAGE;
-                    const float *raw = reinterpret_cast<const float *>(sm + S::RAW0 + s * S::RAW_BYTES) + row * W_KC;
-                    const float *cen = reinterpret_cast<const float *>(st + S::CENTC);
-                    const int flip = (row >> 2) & 1;
+                }
+                float2 nn2 = make_float2(0.f, 0.f);
+                for (int kc = 0; kc < nkc; ++kc, ++g) {
+                    const int s = g % NSA;
+                    const uint32_t par = (g / NSA) & 1;
+                    __syncwarp();                       // every lane done with chunk g - 1's buffer
+                    fill_one();                         // chunk g + NRAW - 1
+                    cp_async_wait<NRAW - 1>();          // this thread's copies of chunk g landed
+                    if (!__all_sync(0xffffffffu, mbar_wait(BAR_A_FREE(s), par ^ 1, abort_flag, args.status)))
+                        goto loader_done;
+                    __syncwarp();                       // ... and every lane's
+                    uint8_t *st = sm + s * S::A_STAGE;
+                    const uint8_t *raw = sm + S::RAW0 + (g % NRAW) * S::RAW_BYTES + row * W_KC * 4;
 #pragma unroll
-                    for (int j2 = 0; j2 < 4; ++j2) {
-                        // swizzled 16-byte slot p of the row and the element chunk c16 it holds;
-                        // c16 >> 2 == h, so the two halves of a row split the chunk
-                        const int p = 4 * (h ^ flip) + (gf4_mulw(row & 3) ^ j2);
-                        const int c16 = p ^ (row & 7);
-                        const float4 x0 = *reinterpret_cast<const float4 *>(raw + 8 * c16 + 4 * flip);
-                        const float4 x1 = *reinterpret_cast<const float4 *>(raw + 8 * c16 + 4 * (flip ^ 1));
-                        const float4 m0 = *reinterpret_cast<const float4 *>(cen + 8 * c16 + 4 * flip);
-                        const float4 m1 = *reinterpret_cast<const float4 *>(cen + 8 * c16 + 4 * (flip ^ 1));
-                        const float4 xl = flip ? x1 : x0, xh = flip ? x0 : x1;   // elements 0-3, 4-7
-                        const float4 ml = flip ? m1 : m0, mh = flip ? m0 : m1;
-                        float v[8] = {xl.x - ml.x, xl.y - ml.y, xl.z - ml.z, xl.w - ml.w,
-                                      xh.x - mh.x, xh.y - mh.y, xh.z - mh.z, xh.w - mh.w};
+                    for (int kg2 = 0; kg2 < 2; ++kg2) {
+                        // K group kg = 2 h + kg2: elements 8 kg .. 8 kg + 7 of the chunk,
+                        // raw pieces 2 kg and 2 kg + 1 (stored at piece ^ (row & 7))
+                        const int kg = 2 * h + kg2;
+                        const float4 xl = *reinterpret_cast<const float4 *>(raw + (((2 * kg) ^ (row & 7)) << 4));
+                        const float4 xh = *reinterpret_cast<const float4 *>(raw + (((2 * kg + 1) ^ (row & 7)) << 4));
+                        const float4 ml = __ldg(cen + 8 * kc + 2 * kg2), mh = __ldg(cen + 8 * kc + 2 * kg2 + 1);
+                        // a = x - c_B, two elements an instruction
+                        float2 v[4] = {__ffma2_rn(make_float2(ml.x, ml.y), neg1, make_float2(xl.x, xl.y)),
+                                       __ffma2_rn(make_float2(ml.z, ml.w), neg1, make_float2(xl.z, xl.w)),
+                                       __ffma2_rn(make_float2(mh.x, mh.y), neg1, make_float2(xh.x, xh.y)),
+                                       __ffma2_rn(make_float2(mh.z, mh.w), neg1, make_float2(xh.z, xh.w))};
                         if (!has_tgt) {
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) v[e] = 0.f;
+                            for (int e = 0; e < 4; ++e) v[e] = make_float2(0.f, 0.f);
                         }
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) nn = fmaf(v[e], v[e], nn);
                         uint32_t hv[4], lv[4];
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
+                            nn2 = __ffma2_rn(v[e], v[e], nn2);
                             if constexpr (P == ASKIT_PREC_FP16X3) {
-                                const float v0 = v[2 * e] * args.f16_scale, v1 = v[2 * e + 1] * args.f16_scale;
-                                const __half2 hh = __floats2half2_rn(v0, v1);
-                                const float2 hf = __half22float2(hh);
-                                const __half2 ll = __floats2half2_rn(v0 - hf.x, v1 - hf.y);
+                                const float2 vs = __fmul2_rn(v[e], sc2);
+                                const __half2 hh = __floats2half2_rn(vs.x, vs.y);
+                                const float2 r2 = __ffma2_rn(__half22float2(hh), neg1, vs);
+                                const __half2 ll = __floats2half2_rn(r2.x, r2.y);
                                 hv[e] = *reinterpret_cast<const uint32_t *>(&hh);
                                 lv[e] = *reinterpret_cast<const uint32_t *>(&ll);
                             } else {
-                                const float v0 = v[2 * e], v1 = v[2 * e + 1];
-                                const __nv_bfloat162 hh = __floats2bfloat162_rn(v0, v1);
-                                const float2 hf = __bfloat1622float2(hh);
-                                const __nv_bfloat162 ll = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+                                const __nv_bfloat162 hh = __floats2bfloat162_rn(v[e].x, v[e].y);
+                                const float2 r2 = __ffma2_rn(__bfloat1622float2(hh), neg1, v[e]);
+                                const __nv_bfloat162 ll = __floats2bfloat162_rn(r2.x, r2.y);
                                 hv[e] = *reinterpret_cast<const uint32_t *>(&hh);
                                 lv[e] = *reinterpret_cast<const uint32_t *>(&ll);
                             }
                         }
-                        const int off = row * 128 + (p << 4);
-                        *reinterpret_cast<uint4 *>(st + S::A_HI + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                        // core-matrix layout: K group kg, row `row`, 16 bytes
+                        const int off = kg * (W_ROWS * 16) + row * 16;
+                        *reinterpret_cast<uint4 *>(st + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
                         *reinterpret_cast<uint4 *>(st + S::A_LO + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
                     }
-                    if (kc == nkc - 1) a_norm[(a * 2 + h) * 128 + row] = nn;
-                    mbar_arrive(BAR_RAW_FREE(s));
+                    if (kc == nkc - 1) a_norm[(cbuf * 2 + h) * 128 + row] = nn2.x + nn2.y;
                     // generic-proxy stores -> visible to the tensor core's async proxy
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     mbar_arrive(BAR_A_FULL(s));
-                    mbar_arrive(BAR_R_EMPTY(s));
                 }
-#pragma unroll
-                for (int i = 0; i < 8; ++i) cs[i] = ns[i];
-                cmask = nmask;
             }
         }
     loader_done:
@@ -312,67 +370,86 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
         cp_async_wait<0>();
     } else if (warp < 12) {
         // ----------------------------------------------------------- epilogue
+        // Row `row` of every item; columns 0-127 belong to the item's
+        // sub-block (the leader of a pair), 128-255 to the pair's follower,
+        // each summed into its own entry's partial.
         const int row = tid - 256;
         const int q = warp & 3;
         int li = 0;
         for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci) {
             const int b = args.cta_blocks[ci];
-            for (int it = args.block_off[b]; it < args.block_off[b + 1]; ++it, ++li) {
-                const int a = li & 1;
+            const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
+            int f0 = 0;
+            const int nrows_f = follower_rows(b, f0);
+            for (int it = i0; it < i1; ++it, ++li) {
+                const int a = li % NSLOT, cbuf = li & 1;
                 const EvalItem item = args.items[it];
                 const int nrows = item.nrows & 0x7fffffff;
-                if (!mbar_wait(BAR_T_FULL(a), (li >> 1) & 1, abort_flag, args.status)) goto epi_done;
+                if (!mbar_wait(BAR_T_FULL(a), (li / NSLOT) & 1, abort_flag, args.status)) goto epi_done;
                 tc_fence_after();
-                float acc[RC];
+                float acc[NB][RC];
 #pragma unroll
-                for (int z = 0; z < RC; ++z) acc[z] = 0.f;
-                float2 acc2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                for (int hb = 0; hb < NB; ++hb)
+#pragma unroll
+                    for (int z = 0; z < RC; ++z) acc[hb][z] = 0.f;
                 if (q * 32 < item.cnt) {
-                    const float pt = a_norm[(a * 2) * 128 + row] + a_norm[(a * 2 + 1) * 128 + row];
+                    const float pt = a_norm[(cbuf * 2) * 128 + row] + a_norm[(cbuf * 2 + 1) * 128 + row];
                     const float2 pt2 = make_float2(pt, pt);
-                    const float4 *cv4 = colv + a * 128;
-                    const float *cwp = colw + a * 128 * RC;
+                    const float4 *cv4 = colv + cbuf * NCOL;
+                    const float *cwp = colw + cbuf * NCOL * RC;
                     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+#pragma unroll
+                    for (int hb = 0; hb < NB; ++hb) {
+                        const int ncols = hb == 0 ? nrows : nrows_f;
+                        float2 acc2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll 1
-                    for (int c = 0; c < 4 && c * 32 < nrows; ++c) {
-                        float g[32], gx[32];
-                        tmem_ld32(lane_base + (uint32_t)(a * 128 + c * 32), g);
-                        tmem_ld32(lane_base + (uint32_t)(256 + a * 128 + c * 32), gx);
+                        for (int c = 0; c < 4 && c * 32 < ncols; ++c) {
+                            const int cb = hb * 128 + c * 32;   // first column of the chunk
+                            float g[32], gx[32];
+                            tmem_ld32(lane_base + (uint32_t)(a * NCOL + cb), g);
+                            tmem_ld32(lane_base + (uint32_t)(256 + a * NCOL + cb), gx);
 #pragma unroll
-                        for (int jj = 0; jj < 32; ++jj) g[jj] += gx[jj];
-                        if constexpr (RC == 1) {
+                            for (int jj = 0; jj < 32; ++jj) g[jj] += gx[jj];
+                            if constexpr (RC == 1) {
 #pragma unroll
-                            for (int jj = 0; jj < 32; jj += 2) {
-                                const float4 ab = cv4[c * 32 + jj];
-                                const float4 cw = cv4[c * 32 + jj + 1];
-                                const float2 inner = __ffma2_rn(make_float2(cw.x, cw.y), pt2, make_float2(ab.z, ab.w));
-                                const float2 arg = __ffma2_rn(make_float2(g[jj], g[jj + 1]), make_float2(ab.x, ab.y), inner);
-                                const float2 k = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
-                                acc2[(jj >> 1) & 1] = __ffma2_rn(k, make_float2(cw.z, cw.w), acc2[(jj >> 1) & 1]);
-                            }
-                        } else {
+                                for (int jj = 0; jj < 32; jj += 2) {
+                                    const float4 ab = cv4[cb + jj];
+                                    const float4 cw = cv4[cb + jj + 1];
+                                    const float2 inner = __ffma2_rn(make_float2(cw.x, cw.y), pt2, make_float2(ab.z, ab.w));
+                                    const float2 arg = __ffma2_rn(make_float2(g[jj], g[jj + 1]), make_float2(ab.x, ab.y), inner);
+                                    const float2 k = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+                                    acc2[(jj >> 1) & 1] = __ffma2_rn(k, make_float2(cw.z, cw.w), acc2[(jj >> 1) & 1]);
+                                }
+                            } else {
 #pragma unroll
-                            for (int jj = 0; jj < 32; ++jj) {
-                                const int j = c * 32 + jj;
-                                const float4 ab = cv4[j & ~1];
-                                const float4 cw = cv4[(j & ~1) + 1];
-                                const bool o = j & 1;
-                                const float A = o ? ab.y : ab.x, B = o ? ab.w : ab.z, Cc = o ? cw.y : cw.x;
-                                const float k = ex2_approx(fmaf(g[jj], A, fmaf(Cc, pt, B)));
+                                for (int jj = 0; jj < 32; ++jj) {
+                                    const int j = cb + jj;
+                                    const float4 ab = cv4[j & ~1];
+                                    const float4 cw = cv4[(j & ~1) + 1];
+                                    const bool o = j & 1;
+                                    const float A = o ? ab.y : ab.x, B = o ? ab.w : ab.z, Cc = o ? cw.y : cw.x;
+                                    const float k = ex2_approx(fmaf(g[jj], A, fmaf(Cc, pt, B)));
 #pragma unroll
-                                for (int z = 0; z < RC; ++z) acc[z] = fmaf(k, cwp[j * RC + z], acc[z]);
+                                    for (int z = 0; z < RC; ++z) acc[hb][z] = fmaf(k, cwp[j * RC + z], acc[hb][z]);
+                                }
                             }
                         }
+                        if constexpr (RC == 1) acc[hb][0] = (acc2[0].x + acc2[0].y) + (acc2[1].x + acc2[1].y);
                     }
-                    if constexpr (RC == 1) acc[0] = (acc2[0].x + acc2[0].y) + (acc2[1].x + acc2[1].y);
                 }
                 tc_fence_before();
                 mbar_arrive(BAR_T_EMPTY(a));
+                mbar_arrive(BAR_COL_EMPTY(cbuf));
                 if (row < item.cnt) {
-                    float *p = args.partial + (int64_t)(item.e0 + row) * args.r;
 #pragma unroll
-                    for (int z = 0; z < RC; ++z)
-                        if (z < args.r) p[z] = acc[z];
+                    for (int hb = 0; hb < NB; ++hb) {
+                        if (hb == 1 && nrows_f == 0) break;
+                        const int e0 = hb == 0 ? item.e0 : args.items[f0 + (it - i0)].e0;
+                        float *p = args.partial + (int64_t)(e0 + row) * args.r;
+#pragma unroll
+                        for (int z = 0; z < RC; ++z)
+                            if (z < args.r) p[z] = acc[hb][z];
+                    }
                 }
             }
         }
@@ -385,53 +462,58 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
             const int i0 = args.block_off[b], i1 = args.block_off[b + 1];
             const EvalItem first = args.items[i0];
             const bool far = first.nrows < 0;
-            const CUtensorMap *mh = far ? &map_s_hi : &map_t_hi;
-            const CUtensorMap *ml = far ? &map_s_lo : &map_t_lo;
-            const float *cb = args.cent + (int64_t)first.cidx * args.kw;
+            // 8-row groups where the sub-block starts on one (every skeleton),
+            // else single rows (a leaf anywhere in tree order)
+            const bool rg = (first.row0 & 7) == 0;
+            const CUtensorMap *mh = far ? &map_s_hi : (rg ? &map_t_hi : &map_t_hi1);
+            const CUtensorMap *ml = far ? &map_s_lo : (rg ? &map_t_lo : &map_t_lo1);
+            const int y = rg ? first.row0 >> 3 : first.row0;
             for (int it = i0; it < i1; ++it) {
                 for (int kc = 0; kc < nkc; ++kc, ++g) {
-                    const int s = g & 1;
-                    const uint32_t par = ((g >> 1) & 1) ^ 1;
-                    if (!mbar_wait(BAR_R_EMPTY(s), par, abort_flag, args.status)) goto prod_done;
-                    if (!mbar_wait(BAR_MMA_DONE(s), par, abort_flag, args.status)) goto prod_done;
-                    const uint32_t st = sbase + s * S::STAGE;
+                    const int s = g % NSB;
+                    const uint32_t par = ((g / NSB) & 1) ^ 1;
+                    if (!mbar_wait(BAR_B_FREE(s), par, abort_flag, args.status)) goto prod_done;
+                    const uint32_t st = sbase + S::B0 + s * S::B_STAGE;
                     ++issued;
                     mbar_expect_tx(BAR_L_FULL(s), S::TX);
-                    tma_load_2d(st + S::B_HI, mh, kc * W_KC, first.row0, BAR_L_FULL(s));
-                    tma_load_2d(st + S::B_LO, ml, kc * W_KC, first.row0, BAR_L_FULL(s));
-                    bulk_copy(st + S::CENTC, cb + kc * W_KC, W_KC * 4, BAR_L_FULL(s));
+                    // [4 K groups][NCOL rows][16 B]: the core-matrix layout (a
+                    // pair's follower rows follow the leader's)
+                    tma_load_3d(st, mh, 0, y, kc * W_KG, BAR_L_FULL(s));
+                    tma_load_3d(st + S::B_LO, ml, 0, y, kc * W_KG, BAR_L_FULL(s));
                 }
             }
         }
     prod_done:
-        // copies of the last two chunks may still be landing after an abort
-        for (int gg = issued > 2 ? issued - 2 : 0; gg < issued; ++gg) mbar_drain(BAR_L_FULL(gg & 1), (gg >> 1) & 1);
+        // copies of the last NSB chunks may still be landing after an abort
+        for (int gg = issued > NSB ? issued - NSB : 0; gg < issued; ++gg)
+            mbar_drain(BAR_L_FULL(gg % NSB), (gg / NSB) & 1);
     } else if (warp == 12 && lane == 0) {
         // ------------------------------------------------------------ MMA issuer
         int g = 0, li = 0;
         for (int ci = c_begin; ci < c_end && !*abort_flag; ++ci) {
             const int b = args.cta_blocks[ci];
             for (int it = args.block_off[b]; it < args.block_off[b + 1]; ++it, ++li) {
-                const int a = li & 1;
-                const uint32_t d_main = tmem + (uint32_t)(a * 128), d_cross = tmem + (uint32_t)(256 + a * 128);
+                const int a = li % NSLOT;
+                const uint32_t d_main = tmem + (uint32_t)(a * NCOL), d_cross = tmem + (uint32_t)(256 + a * NCOL);
                 for (int kc = 0; kc < nkc; ++kc, ++g) {
-                    const int s = g & 1;
-                    const uint32_t par = (g >> 1) & 1;
-                    if (!mbar_wait(BAR_A_FULL(s), par, abort_flag, args.status)) goto mma_done;
-                    if (!mbar_wait(BAR_L_FULL(s), par, abort_flag, args.status)) goto mma_done;
-                    if (kc == 0 && !mbar_wait(BAR_T_EMPTY(a), ((li >> 1) & 1) ^ 1, abort_flag, args.status))
+                    const int sa = g % NSA, sb = g % NSB;
+                    if (!mbar_wait(BAR_A_FULL(sa), (g / NSA) & 1, abort_flag, args.status)) goto mma_done;
+                    if (!mbar_wait(BAR_L_FULL(sb), (g / NSB) & 1, abort_flag, args.status)) goto mma_done;
+                    if (kc == 0 && !mbar_wait(BAR_T_EMPTY(a), ((li / NSLOT) & 1) ^ 1, abort_flag, args.status))
                         goto mma_done;
                     tc_fence_after();
-                    const uint32_t st = sbase + s * S::STAGE;
-                    const uint32_t a_hi = st + S::A_HI, a_lo = st + S::A_LO, b_hi = st + S::B_HI, b_lo = st + S::B_LO;
+                    const uint32_t a_hi = sbase + sa * S::A_STAGE, a_lo = a_hi + S::A_LO;
+                    const uint32_t b_hi = sbase + S::B0 + sb * S::B_STAGE, b_lo = b_hi + S::B_LO;
+                    constexpr uint32_t LA = W_ROWS * 16, LB = NCOL * 16;   // bytes between K groups
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {   // K = 16 per MMA: 32 bytes into the 128-byte rows
-                        const uint32_t off = (uint32_t)(k * 32);
-                        tc_mma<P>(d_cross, sw128_desc(a_hi + off), sw128_desc(b_lo + off), IDESC, (kc | k) != 0);
-                        tc_mma<P>(d_cross, sw128_desc(a_lo + off), sw128_desc(b_hi + off), IDESC, 1);
-                        tc_mma<P>(d_main, sw128_desc(a_hi + off), sw128_desc(b_hi + off), IDESC, (kc | k) != 0);
+                    for (int k = 0; k < 2; ++k) {   // K = 16 per MMA: two K groups
+                        const uint32_t oa = (uint32_t)(2 * k) * LA, ob = (uint32_t)(2 * k) * LB;
+                        tc_mma<P>(d_cross, nsw_desc(a_hi + oa, LA), nsw_desc(b_lo + ob, LB), IDESC, (kc | k) != 0);
+                        tc_mma<P>(d_cross, nsw_desc(a_lo + oa, LA), nsw_desc(b_hi + ob, LB), IDESC, 1);
+                        tc_mma<P>(d_main, nsw_desc(a_hi + oa, LA), nsw_desc(b_hi + ob, LB), IDESC, (kc | k) != 0);
                     }
-                    tc_commit(BAR_MMA_DONE(s));
+                    tc_commit(BAR_A_FREE(sa));
+                    tc_commit(BAR_B_FREE(sb));
                     if (kc == nkc - 1) tc_commit(BAR_T_FULL(a));
                 }
             }
@@ -446,15 +528,38 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
     }
 }
 
-// Tensor maps of the pre-split source arrays ([rows, kw] 16-bit; boxes of
-// 64 x 128, 128-byte swizzle) for BF16 (index 0) and FP16 (index 1).
+// 3-D tensor maps of the pre-split source arrays (16-bit planes of K groups,
+// [kw / 8][rows][8]), each box four contiguous runs of 2 or 4 KB landing in
+// the core-matrix layout:
+//   row groups: {64 elements = 8 rows of a K group, rows / 8, kw / 8 K
+//     groups}, boxes {64, 16 NB, 4} (128-byte requests), for sub-blocks that
+//     start on a multiple of 8 rows (skeletons start on multiples of 32);
+//   rows: {8, rows, kw / 8}, boxes {8, 128 NB, 4} (16-byte requests), for
+//     leaf sub-blocks that do not.
+// [precision (BF16, FP16)][NB - 1][t_hi, t_lo, s_hi, s_lo (row groups), t_hi, t_lo (rows)].
 struct TcwState {
-    CUtensorMap map[2][4];   // [t_hi, t_lo, s_hi, s_lo]
+    CUtensorMap map[2][2][6];
     bool ready[2] = {false, false};
     EncodeTiledFn encode = nullptr;
 };
 
 std::mutex g_tcw_mu;
+
+askit_status encode_kgroups(EncodeTiledFn fn, CUtensorMap *m, CUtensorMapDataType ty, const void *base, int64_t rows,
+                            int64_t kw, int box_rows, bool row_groups) {
+    const int rg = row_groups ? 8 : 1;
+    cuuint64_t dims[3] = {(cuuint64_t)(8 * rg), (cuuint64_t)(rows / rg), (cuuint64_t)(kw / 8)};
+    cuuint64_t strides[2] = {(cuuint64_t)(16 * rg), (cuuint64_t)rows * 16};  // bytes: next row (group), next K group
+    cuuint32_t box[3] = {(cuuint32_t)(8 * rg), (cuuint32_t)(box_rows / rg), (cuuint32_t)W_KG};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, ty, 3, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        askit_set_error("cuTensorMapEncodeTiled (K groups) failed (%d)", (int)r);
+        return ASKIT_ERR_CUDA;
+    }
+    return ASKIT_OK;
+}
 
 askit_status tcw_state(askit_tree t, int pi, TcwState **out) {
     std::lock_guard<std::mutex> lock(g_tcw_mu);
@@ -467,33 +572,44 @@ askit_status tcw_state(askit_tree t, int pi, TcwState **out) {
                               pi == 0 ? (void *)t->Xt_blo : (void *)t->Xt_hlo,
                               pi == 0 ? (void *)t->Xs_bhi : (void *)t->Xs_hhi,
                               pi == 0 ? (void *)t->Xs_blo : (void *)t->Xs_hlo};
-        for (int i = 0; i < 4; ++i)
-            ASK_TRY(encode_2d(st->encode, &st->map[pi][i], ty, 2, arr[i], i < 2 ? t->N_pad : t->srows, t->kw, W_KC,
-                              W_ROWS, CU_TENSOR_MAP_SWIZZLE_128B));
+        for (int nb = 0; nb < 2; ++nb)
+            for (int i = 0; i < 6; ++i)
+                ASK_TRY(encode_kgroups(st->encode, &st->map[pi][nb][i], ty, arr[i & 3],
+                                       (i & 3) < 2 ? t->N_pad : t->srows, t->kw, W_ROWS * (nb + 1), i < 4));
         st->ready[pi] = true;
     }
     *out = st;
     return ASKIT_OK;
 }
 
-template <int P, int RC>
+template <int P, int RC, int NB>
 askit_status launch_w(askit_tree t, TcwState *st, int pi, const TcwArgs &a, int grid, cudaStream_t s) {
-    using S = WSmem<RC>;
-    const size_t smem = S::BYTES + 1024;
-    static bool attr_set = false;
-    {
-        std::lock_guard<std::mutex> lock(g_tcw_mu);
-        if (!attr_set) {
-            ASK_CUDA(cudaFuncSetAttribute(eval_tcw_kernel<P, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-            attr_set = true;
-        }
-    }
+    using S = WSmem<RC, NB>;
+    constexpr size_t smem = S::BYTES + 128;
+    static_assert(smem <= 232448, "shared-memory plan exceeds 227 KB");
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(eval_tcw_kernel<P, RC, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    ASK_CUDA(attr);
     ASK_TRY(ktimer_mark(t, s, false));
-    eval_tcw_kernel<P, RC><<<(unsigned)grid, W_THREADS, smem, s>>>(st->map[pi][0], st->map[pi][1], st->map[pi][2],
-                                                                   st->map[pi][3], a);
+    const CUtensorMap *m = st->map[pi][NB - 1];
+    eval_tcw_kernel<P, RC, NB><<<(unsigned)grid, W_THREADS, smem, s>>>(m[0], m[1], m[2], m[3], m[4], m[5], a);
     ASK_LAUNCH();
     return ktimer_mark(t, s, true);
+}
+
+template <int P, int RC>
+askit_status run_w(askit_tree t, TcwState *st, int pi, TcwArgs a, const WorkLists &w, cudaStream_t s) {
+    // paired items: the two sub-blocks of a node (same targets, same center)
+    // in one 256-column item, on the segments' schedule (several CTAs on one
+    // block at a time, so that its source rows stay in L2 across its items)
+    if (t->tune_pairs && w.seg_sched_off) {
+        a.block_off = w.seg_off;
+        a.partner = w.seg_partner;
+        a.cta_off = w.seg_sched_off;
+        a.cta_blocks = w.seg_sched;
+        return launch_w<P, RC, 2>(t, st, pi, a, w.n_ctas, s);
+    }
+    return launch_w<P, RC, 1>(t, st, pi, a, w.n_ctas, s);
 }
 
 }  // namespace
@@ -513,14 +629,14 @@ askit_status eval_tc_wide(askit_tree t, const WeightCtx &c, int precision, const
         askit_set_error("target rows must have d_pad columns and the wide operands must exist");
         return ASKIT_ERR_INVALID_ARG;
     }
-    const int pi = precision == ASKIT_PREC_BF16X3 ? 0 : 1;
-    TcwState *st = nullptr;
-    ASK_TRY(tcw_state(t, pi, &st));
-    if ((reinterpret_cast<uintptr_t>(Xq) & 15) != 0) {
-        askit_set_error("target rows must be 16-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(Xq) & 15) != 0 || t->kw % W_KC != 0) {
+        askit_set_error("target rows must be 16-byte aligned and the row width a multiple of %d", W_KC);
         return ASKIT_ERR_INVALID_ARG;
     }
     (void)q_rows;
+    const int pi = precision == ASKIT_PREC_BF16X3 ? 0 : 1;
+    TcwState *st = nullptr;
+    ASK_TRY(tcw_state(t, pi, &st));
     TcwArgs a;
     a.q = Xq;
     a.ldq = ldq;
@@ -528,6 +644,7 @@ askit_status eval_tc_wide(askit_tree t, const WeightCtx &c, int precision, const
     a.block_off = w.block_off;
     a.cta_off = w.cta_off;
     a.cta_blocks = w.cta_blocks;
+    a.partner = nullptr;
     a.tgt = w.tgt;
     a.nkc = t->kw / W_KC;
     a.kw = t->kw;
@@ -544,13 +661,13 @@ askit_status eval_tc_wide(askit_tree t, const WeightCtx &c, int precision, const
     a.partial = partial;
     a.status = t->d_status;
     if (precision == ASKIT_PREC_BF16X3) {
-        if (c.r == 1) return launch_w<ASKIT_PREC_BF16X3, 1>(t, st, pi, a, w.n_ctas, s);
-        if (c.r <= 4) return launch_w<ASKIT_PREC_BF16X3, 4>(t, st, pi, a, w.n_ctas, s);
-        return launch_w<ASKIT_PREC_BF16X3, 16>(t, st, pi, a, w.n_ctas, s);
+        if (c.r == 1) return run_w<ASKIT_PREC_BF16X3, 1>(t, st, pi, a, w, s);
+        if (c.r <= 4) return run_w<ASKIT_PREC_BF16X3, 4>(t, st, pi, a, w, s);
+        return run_w<ASKIT_PREC_BF16X3, 16>(t, st, pi, a, w, s);
     }
-    if (c.r == 1) return launch_w<ASKIT_PREC_FP16X3, 1>(t, st, pi, a, w.n_ctas, s);
-    if (c.r <= 4) return launch_w<ASKIT_PREC_FP16X3, 4>(t, st, pi, a, w.n_ctas, s);
-    return launch_w<ASKIT_PREC_FP16X3, 16>(t, st, pi, a, w.n_ctas, s);
+    if (c.r == 1) return run_w<ASKIT_PREC_FP16X3, 1>(t, st, pi, a, w, s);
+    if (c.r <= 4) return run_w<ASKIT_PREC_FP16X3, 4>(t, st, pi, a, w, s);
+    return run_w<ASKIT_PREC_FP16X3, 16>(t, st, pi, a, w, s);
 }
 
 void eval_tc_wide_free(askit_tree t) {

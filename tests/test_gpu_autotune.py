@@ -87,8 +87,9 @@ def test_autotune_needs_weights():
 
 
 def test_wide_kernel_schedules_match_the_oracle():
-    """d = 100 (rows padded to 128: two K chunks of 64, the second partly
-    outside the rows): both schedules, r = 1 and 3, against the oracle."""
+    """d = 100 (rows padded to 128: four K chunks of 32, the last partly
+    outside the rows): both schedules and paired items, r = 1 and 3, against
+    the oracle; the autotuner offers the paired items as a third candidate."""
     import oracle
     from paper_1410_0260_gb300 import askit, workloads
     X = workloads.mixture(3000, 100, 4, 3.0, seed=31)
@@ -107,4 +108,14 @@ def test_wide_kernel_schedules_match_the_oracle():
             assert np.linalg.norm(U - Uo) / np.linalg.norm(Uo) <= 1e-4, sched
             outs.append(U)
         assert np.array_equal(outs[0], outs[1])
+        # paired 256-column items: each target row copied and split once for
+        # both sub-blocks of a node; the sums differ by FP32 rounding only
+        gt.set_launch("lpt", 3, True, True)
+        U = gt.evaluate().cpu().numpy()
+        assert np.linalg.norm(U - Uo) / np.linalg.norm(Uo) <= 1e-4
+        assert np.linalg.norm(U - outs[0]) / np.linalg.norm(outs[0]) <= 1e-6
+        gt.set_launch("lpt", 3, True, False)
+    cands = gt.autotune(reps=1)
+    assert len(cands) == 3 and sum(c["pairs"] for c in cands) == 1
+    assert sum(c["chosen"] for c in cands) == 1
     gt.close()

@@ -305,8 +305,8 @@ def test_d1000_variable_bandwidth_on_the_1000d_recipe_shape():
 
 
 def test_wide_rows_with_a_ragged_last_chunk():
-    """d = 72 (rows padded to 96, K chunks of 64: the second chunk half outside
-    the rows), ragged leaves, r = 3, out-of-sample targets."""
+    """d = 72 (rows padded to 96: three K chunks of 32, the last three
+    quarters padding), ragged leaves, r = 3, out-of-sample targets."""
     X = wl.mixture(3001, 72, 5, 3.0, seed=21)
     W = np.random.default_rng(6).standard_normal((3001, 3)).astype(np.float32)
     kw = dict(leaf_size=100, kappa=12, knn_mode=0, s_max=48, id_tol=1e-5, h=4.0, seed=8)
