@@ -31,18 +31,18 @@
 //              buffer (4 lanes along a half row, 8 rows an instruction), three
 //              (r > 4: one) chunks ahead of the split;
 //              split: thread t takes half (t >> 7) of row t & 127 of the
-//              chunk, subtracts c_B (read from global memory), accumulates
-//              |a|^2, splits into FP16/BF16 hi + lo; they also write the
-//              item's column data (c log2(e) / h^2, |b|^2, w) for the
-//              epilogue, double-buffered so that they run on into the next
-//              item while the epilogue drains the last;
+//              chunk, subtracts c_B (from the warp's copy of its half of c_B
+//              in shared memory; from global memory past kw = 1024 or r = 4),
+//              accumulates |a|^2, splits into FP16/BF16 hi + lo; they also
+//              write the item's column data (c log2(e) / h^2, |b|^2, w) for
+//              the epilogue, double-buffered so that they run on into the
+//              next item while the epilogue drains the last;
 //   warps 8-11 epilogue (TMEM lane quadrant = warp & 3);
 //   warp 12    TMEM allocation; lane 0 issues the tcgen05.mma instructions;
 //   warp 13    producer: TMA of the sub-block's hi and lo chunk.
-// Chunk stages in two rings, released separately by the MMAs' commits: four
-// (r > 4: three) of the split targets, so that the loaders run on across an
-// item's end, and three of the sub-block's chunk, requested two chunks' MMAs
-// before it is needed.  Single sub-blocks: two items' accumulators (main +
+// Chunk stages in two rings, released separately by the MMAs' commits: three
+// of the split targets and three of the sub-block's chunk, requested two
+// chunks' MMAs before it is needed.  Single sub-blocks: two items' accumulators (main +
 // cross) fill TMEM's 512 columns, so the MMAs of item i+1 overlap the
 // epilogue of item i; paired items: one item's 256-column accumulators fill
 // it.  Every mbarrier wait is bounded: on timeout the kernel records
@@ -83,9 +83,12 @@ struct WSmem {
     // Two rings of chunk stages, released separately by the MMAs' commits:
     // NSA stages of the split targets (A hi, A lo: [4][128][16 B] each),
     // NSB of the sub-block's (B hi, B lo: [4][NCOL][16 B] each).
-    static constexpr int NSA = RC <= 4 ? 4 : 3;
+    static constexpr int NSA = 3;
     static constexpr int NSB = 3;
     static constexpr int NRAW = RC <= 4 ? 3 : 2;    // raw target-row buffers: NRAW - 1 chunks read ahead
+    // each loader warp's copy of its half of c_B (kw / 2 floats) while kw <=
+    // CEN_KW; else c_B is read from global memory
+    static constexpr int CEN_KW = RC <= 4 ? 1024 : 0;
     static constexpr int A_STAGE = 2 * W_REGION, B_STAGE = 2 * NB * W_REGION;
     static constexpr int A_LO = W_REGION, B_LO = NB * W_REGION;   // within a stage
     static constexpr int B0 = NSA * A_STAGE;
@@ -95,7 +98,8 @@ struct WSmem {
     static constexpr int RAW_BYTES = W_ROWS * W_KC * 4;
     // the column data and |a|^2 of two items (item li in buffer li & 1), so
     // that the loaders move on to the next item while the epilogue runs
-    static constexpr int ANORM = RAW0 + NRAW * RAW_BYTES;      // float [2][2 halves][128]
+    static constexpr int CENW = RAW0 + NRAW * RAW_BYTES;       // float [8 warps][CEN_KW / 2]
+    static constexpr int ANORM = CENW + 8 * CEN_KW * 2;        // float [2][2 halves][128]
     static constexpr int COLV = ANORM + 2 * 2 * 128 * 4;       // float4 [2][NCOL]
     static constexpr int COLW = COLV + 2 * NCOL * 16;          // float [2][NCOL][RC]
     static constexpr int BAR = COLW + 2 * NCOL * RC * 4;       // 32 mbarriers
@@ -281,8 +285,17 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
             const float sc = has_src ? __ldg((far ? args.sc_s : args.sc_t) + srow) : 0.f;
             const float qn = has_src ? __ldg((far ? args.nrm_s : args.nrm_t) + srow) : 0.f;
             const float *wrow = (far ? args.Ws : args.Wt) + srow * args.r;
-            // c_B, read from global memory (the same 64 bytes for a warp)
+            // c_B: this thread's 16 elements of chunk kc at cen[8 kc .. 8 kc + 3]
+            // (global memory; the same 64 bytes for a warp), or at
+            // cenw[4 kc .. 4 kc + 3] in the warp's copy
             const float4 *cen = reinterpret_cast<const float4 *>(args.cent + (int64_t)first.cidx * args.kw) + 4 * h;
+            float4 *cenw = reinterpret_cast<float4 *>(sm + S::CENW) + warp * (S::CEN_KW / 8);
+            const bool cen_sm = args.kw <= S::CEN_KW;
+            if (cen_sm) {
+                __syncwarp();                   // no lane still reads the last segment's copy
+                for (int q = lane; q < 4 * nkc; q += 32) cenw[q] = __ldg(cen + 8 * (q >> 2) + (q & 3));
+                __syncwarp();
+            }
             for (int it = i0; it < i1; ++it, ++li) {
                 const int cbuf = li & 1;
                 const int cnt = args.items[it].cnt;
@@ -323,7 +336,14 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                         const int kg = 2 * h + kg2;
                         const float4 xl = *reinterpret_cast<const float4 *>(raw + (((2 * kg) ^ (row & 7)) << 4));
                         const float4 xh = *reinterpret_cast<const float4 *>(raw + (((2 * kg + 1) ^ (row & 7)) << 4));
-                        const float4 ml = __ldg(cen + 8 * kc + 2 * kg2), mh = __ldg(cen + 8 * kc + 2 * kg2 + 1);
+                        float4 ml, mh;
+                        if (cen_sm) {
+                            ml = cenw[4 * kc + 2 * kg2];
+                            mh = cenw[4 * kc + 2 * kg2 + 1];
+                        } else {
+                            ml = __ldg(cen + 8 * kc + 2 * kg2);
+                            mh = __ldg(cen + 8 * kc + 2 * kg2 + 1);
+                        }
                         // a = x - c_B, two elements an instruction
                         float2 v[4] = {__ffma2_rn(make_float2(ml.x, ml.y), neg1, make_float2(xl.x, xl.y)),
                                        __ffma2_rn(make_float2(ml.z, ml.w), neg1, make_float2(xl.z, xl.w)),
