@@ -51,7 +51,7 @@ constexpr int ASK_TILE_M = 128;
 constexpr int ASK_BLK_N = 128;
 // Items per segment of a sub-block's items (schedule of the K-chunked kernel's
 // paired items).
-constexpr int ASK_SEG_ITEMS = 16;
+constexpr int ASK_SEG_ITEMS = 8;
 // Columns of the tensor-core operand arrays (d <= TC_K).
 constexpr int TC_K = 64;
 // Default and largest entries of one in-sample work-list batch (entry

@@ -418,29 +418,63 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                     const float4 *cv4 = colv + cbuf * NCOL;
                     const float *cwp = colw + cbuf * NCOL * RC;
                     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+                    if constexpr (RC == 1) {
+                        // 16-column steps; the next step's TMEM loads (main in
+                        // r[0..15], cross in r[16..31]) are in flight while this
+                        // step's columns are summed
 #pragma unroll
-                    for (int hb = 0; hb < NB; ++hb) {
-                        const int ncols = hb == 0 ? nrows : nrows_f;
-                        float2 acc2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll 1
-                        for (int c = 0; c < 4 && c * 32 < ncols; ++c) {
-                            const int cb = hb * 128 + c * 32;   // first column of the chunk
-                            float g[32], gx[32];
-                            tmem_ld32(lane_base + (uint32_t)(a * NCOL + cb), g);
-                            tmem_ld32(lane_base + (uint32_t)(256 + a * NCOL + cb), gx);
+                        for (int hb = 0; hb < NB; ++hb) {
+                            const int nst = ((hb == 0 ? nrows : nrows_f) + 15) >> 4;
+                            float2 acc2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                            uint32_t ra[32], rb[32];
+                            auto issue = [&](int c, uint32_t (&r)[32]) {
+                                const uint32_t col = (uint32_t)(a * NCOL + hb * 128 + 16 * c);
+                                tmem_ld16_async_at<0>(lane_base + col, r);
+                                tmem_ld16_async_at<16>(lane_base + 256 + col, r);
+                            };
+                            auto sum = [&](int c, const uint32_t (&r)[32]) {
+                                const int cb = hb * 128 + 16 * c;
 #pragma unroll
-                            for (int jj = 0; jj < 32; ++jj) g[jj] += gx[jj];
-                            if constexpr (RC == 1) {
-#pragma unroll
-                                for (int jj = 0; jj < 32; jj += 2) {
+                                for (int jj = 0; jj < 16; jj += 2) {
                                     const float4 ab = cv4[cb + jj];
                                     const float4 cw = cv4[cb + jj + 1];
+                                    const float2 gg = make_float2(__uint_as_float(r[jj]) + __uint_as_float(r[16 + jj]),
+                                                                  __uint_as_float(r[jj + 1]) + __uint_as_float(r[17 + jj]));
                                     const float2 inner = __ffma2_rn(make_float2(cw.x, cw.y), pt2, make_float2(ab.z, ab.w));
-                                    const float2 arg = __ffma2_rn(make_float2(g[jj], g[jj + 1]), make_float2(ab.x, ab.y), inner);
+                                    const float2 arg = __ffma2_rn(gg, make_float2(ab.x, ab.y), inner);
                                     const float2 k = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
                                     acc2[(jj >> 1) & 1] = __ffma2_rn(k, make_float2(cw.z, cw.w), acc2[(jj >> 1) & 1]);
                                 }
-                            } else {
+                            };
+                            if (nst > 0) {
+                                issue(0, ra);
+                                tmem_wait_pin(ra);
+                            }
+#pragma unroll 1
+                            for (int c = 0; c < nst; c += 2) {
+                                if (c + 1 < nst) issue(c + 1, rb);
+                                sum(c, ra);
+                                if (c + 1 < nst) {
+                                    tmem_wait_pin(rb);
+                                    if (c + 2 < nst) issue(c + 2, ra);
+                                    sum(c + 1, rb);
+                                    if (c + 2 < nst) tmem_wait_pin(ra);
+                                }
+                            }
+                            acc[hb][0] = (acc2[0].x + acc2[0].y) + (acc2[1].x + acc2[1].y);
+                        }
+                    } else {
+#pragma unroll
+                        for (int hb = 0; hb < NB; ++hb) {
+                            const int ncols = hb == 0 ? nrows : nrows_f;
+#pragma unroll 1
+                            for (int c = 0; c < 4 && c * 32 < ncols; ++c) {
+                                const int cb = hb * 128 + c * 32;   // first column of the chunk
+                                float g[32], gx[32];
+                                tmem_ld32(lane_base + (uint32_t)(a * NCOL + cb), g);
+                                tmem_ld32(lane_base + (uint32_t)(256 + a * NCOL + cb), gx);
+#pragma unroll
+                                for (int jj = 0; jj < 32; ++jj) g[jj] += gx[jj];
 #pragma unroll
                                 for (int jj = 0; jj < 32; ++jj) {
                                     const int j = cb + jj;
@@ -454,7 +488,6 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
                                 }
                             }
                         }
-                        if constexpr (RC == 1) acc[hb][0] = (acc2[0].x + acc2[0].y) + (acc2[1].x + acc2[1].y);
                     }
                 }
                 tc_fence_before();

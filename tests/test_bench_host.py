@@ -43,6 +43,17 @@ def test_tensor_bound_at_d64_with_the_full_ex2_rate():
     assert roof["bound"] == "tensor"
 
 
+def test_long_timed_regions_take_the_sustained_peak():
+    # 1M x 1000: 5.15e10 pairs in 176 ms per launch, timed inside seconds-long steps
+    peaks = {"bf16_tflops": 1896.9, "bf16_tflops_sustained": 1726.1}
+    burst = bench.roofline(5.15e10, 1000, 1, "fp16x3", 0.176, peaks, 2070.0)
+    sus = bench.roofline(5.15e10, 1000, 1, "fp16x3", 0.176, peaks, 2070.0, sustained=True)
+    assert burst["peak"] == 1896.9 and sus["peak"] == 1726.1
+    assert sus["achieved"] == burst["achieved"] and "sustained" in sus["peak_source"]
+    # without a sustained figure the burst one stands
+    assert bench.roofline(5.15e10, 1000, 1, "fp16x3", 0.176, PEAKS, 2070.0, sustained=True)["peak"] == 1908.7
+
+
 def test_tf32_peak_and_plain_fp32():
     roof = bench.roofline(1e10, 64, 1, "tf32x3", 1e-2, PEAKS, 2070.0)
     assert roof["peak"] == pytest.approx(1908.7 * 1.1 / 2.25)
