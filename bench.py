@@ -467,6 +467,7 @@ def measure_config(args, dev, key, steps=3, warmup=2):
                       "eval_g16_kernel" if info["fp16_centering"] == 2 else "eval_tc16_kernel")
     roof["ms_per_launch"] = k_ms / max(1, k_launches)
     roof["launches_per_evaluate"] = k_launches // steps
+    roof["traffic"] = measured_traffic(roof["kernel"], w.name)
     out = {"workload": w.name, "N": N, "d": w.d, "r": r, "m": w.leaf_size, "kappa": w.kappa, "s_max": w.s_max,
            "h": w.h if w.bw_mode == 0 else "distance to neighbor %d" % w.bw_k, "precision": args.precision,
            "evaluate_ms": ms_eval, "targets_per_s": N / (ms_eval / 1e3), "targets_x_rhs_per_s": N * r / (ms_eval / 1e3),
