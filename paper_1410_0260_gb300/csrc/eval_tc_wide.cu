@@ -200,7 +200,8 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
         // its copies need no block-wide barrier: cp.async groups and
         // __syncwarp.  Copies run NRAW - 1 chunks ahead of the split on a fill
         // cursor of their own (item and chunk in this CTA's order); the copy
-        // slots of the item after the fill cursor's are read one item ahead.
+        // slots of the item after the fill cursor's are read one item ahead,
+        // and the header of the item after that one item before them.
         const int row = tid & 127, h = tid >> 7;
         const int cpiece = 4 * h + (lane & 3);            // 16-byte piece of a row's 128-byte chunk
         const int crow0 = 32 * (warp & 3) + (lane >> 2);  // copy rows crow0 + 8 i
@@ -233,6 +234,12 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
         uint32_t fmask = 0, nmask = 0;
         copy_slots(fc, fs, fmask);
         copy_slots(nc, ns, nmask);
+        // the header (first entry, count) of the item after nc, read one item
+        // before its slots, so that no slot load waits on it
+        Cur hc = nc;
+        advance(hc);
+        int2 nh = make_int2(0, 0);
+        if (hc.ci < c_end) nh = make_int2(args.items[hc.it].e0, args.items[hc.it].cnt);
         int fkc = 0, gf = 0;       // fill cursor's chunk; chunks filled so far
         // the fill cursor's chunk into raw buffer gf % NRAW (its last chunk,
         // gf - NRAW, split by this warp); one cp.async group per call, empty
@@ -256,8 +263,18 @@ eval_tcw_kernel(const __grid_constant__ CUtensorMap map_t_hi, const __grid_const
 #pragma unroll
                     for (int i = 0; i < 4; ++i) fs[i] = ns[i];
                     fmask = nmask;
-                    advance(nc);
-                    copy_slots(nc, ns, nmask);
+                    nc = hc;
+                    nmask = 0;
+                    if (nc.ci < c_end) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int r = crow0 + 8 * i;
+                            ns[i] = r < nh.y ? args.tgt[nh.x + r] : 0;
+                            if (r < nh.y) nmask |= 1u << i;
+                        }
+                    }
+                    advance(hc);
+                    if (hc.ci < c_end) nh = make_int2(args.items[hc.it].e0, args.items[hc.it].cnt);
                 }
             }
             cp_async_commit();
