@@ -141,9 +141,9 @@ def roofline(P, d, r, precision, sec, peaks, smax_mhz, arg_on_tensor=False, weig
     the epilogue unless the tensor cores take the weight sums, plus 2 for the
     exponent's argument unless the tensor cores form it); plain FP32 is bound
     by its 2d lane operations per pair.  The tensor peak is the measured
-    bf16 GEMM rate: the burst figure for a short timed region, the sustained
-    one (seconds of back-to-back GEMMs under the power cap) when the kernel
-    is timed inside a long step (`sustained`)."""
+    bf16 GEMM rate: the burst figure, or the sustained one (seconds of
+    back-to-back GEMMs under the power cap) when the kernel is timed inside
+    a long step (`sustained`, see long_step)."""
     mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * smax_mhz * 1e6
     lane_peak = SM_COUNT * FP32_LANES_PER_SM * smax_mhz * 1e6
     if precision == "simt_fp32":
@@ -176,6 +176,14 @@ def roofline(P, d, r, precision, sec, peaks, smax_mhz, arg_on_tensor=False, weig
                     "peak_source": "MUFU ex2: 152 SMs x 32/clk x max SM clock"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     return roof
+
+
+def long_step(ms_evaluate):
+    """A step whose Evaluate call takes 100 ms or more keeps the GPU busy back
+    to back for seconds over the warm-up and timed steps, as the sustained
+    GEMM loop of the measured peaks does: its kernel is rated against the
+    sustained tensor peak."""
+    return ms_evaluate >= 100.0
 
 
 def measured_traffic(kernel, workload_name):
@@ -445,6 +453,8 @@ def measure_config(args, dev, key, steps=3, warmup=2):
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     e0.record(stream)
     for _ in range(steps):
         tree.evaluate(U)
@@ -455,14 +465,14 @@ def measure_config(args, dev, key, steps=3, warmup=2):
     for _ in range(steps):
         tree.evaluate(U)
     k_ms, k_launches = tree.kernel_timing(False)
+    clk = clocks.stop()
     tree.sync()
     acc = accuracy(tree, args.precision, U, w, dev)
     peaks = measured_peaks()
     g16 = args.precision == "fp16x3" and w.d <= 64 and info["fp16_centering"] == 2
-    # a timed region of a second or more runs under the power cap: sustained peak
     roof = roofline(info["pairs_algorithmic"], w.d, r, args.precision, k_ms / steps / 1e3, peaks,
                     (peaks or {}).get("sm_max_mhz") or 2070.0, arg_on_tensor=g16, weights_on_tensor=g16 and r > 4,
-                    sustained=steps * ms_eval >= 1000.0)
+                    sustained=long_step(ms_eval))
     roof["kernel"] = ("eval_tcw_kernel" if w.d > 64 else
                       "eval_g16_kernel" if info["fp16_centering"] == 2 else "eval_tc16_kernel")
     roof["ms_per_launch"] = k_ms / max(1, k_launches)
@@ -471,7 +481,7 @@ def measure_config(args, dev, key, steps=3, warmup=2):
     out = {"workload": w.name, "N": N, "d": w.d, "r": r, "m": w.leaf_size, "kappa": w.kappa, "s_max": w.s_max,
            "h": w.h if w.bw_mode == 0 else "distance to neighbor %d" % w.bw_k, "precision": args.precision,
            "evaluate_ms": ms_eval, "targets_per_s": N / (ms_eval / 1e3), "targets_x_rhs_per_s": N * r / (ms_eval / 1e3),
-           **acc, "rel_err_ok": acc["rel_err_vs_fp32"] <= 1e-4, "roofline": roof,
+           **acc, "rel_err_ok": acc["rel_err_vs_fp32"] <= 1e-4, "roofline": roof, "clocks": clk,
            "autotune": next((c for c in tune if c["chosen"]), None),
            "fp16_centering": info["fp16_centering"], "fp16_rho": info["fp16_rho"],
            "work": {"pairs_algorithmic": info["pairs_algorithmic"], "entries": info["n_entries"],
@@ -730,7 +740,7 @@ def main():
     smax = (clk or {}).get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0
     g16 = args.precision == "fp16x3" and d <= 64 and info["fp16_centering"] == 2
     roof = roofline(P, d, r, args.precision, sec, peaks, smax, arg_on_tensor=g16, weights_on_tensor=g16 and r > 4,
-                    sustained=args.steps * ms_step >= 1000.0)
+                    sustained=long_step(ms_eval))
     roof["traffic"] = None
     # the plain-FP32 comparator (the serving comparison's other side) against
     # its own roofline: one Evaluate kernel launch timed in accuracy()

@@ -52,6 +52,8 @@ def test_long_timed_regions_take_the_sustained_peak():
     assert sus["achieved"] == burst["achieved"] and "sustained" in sus["peak_source"]
     # without a sustained figure the burst one stands
     assert bench.roofline(5.15e10, 1000, 1, "fp16x3", 0.176, PEAKS, 2070.0, sustained=True)["peak"] == 1908.7
+    # 1M x 64 steps (4.4 ms) are short; 8M and 1M x 1000 Evaluates (290-380 ms) are long
+    assert not bench.long_step(4.4) and bench.long_step(290.0) and bench.long_step(380.0)
 
 
 def test_tf32_peak_and_plain_fp32():
